@@ -1,0 +1,1267 @@
+/*
+ * fr_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, FP64 reference ("the oracle") for one right-hand-side (RHS) evaluation of the
+ * flux-reconstruction (FR) discretisation of the compressible Navier-Stokes equations with flux
+ * anti-aliasing (over-integration of the flux at element quadrature points), on affine hexahedra
+ * and prisms, plus the classical RK4 step around it.
+ *
+ * Only the test-suite, the package smoke check and the CPU-baseline leg of the benchmark may load
+ * the library built from this file. It shares no code with the GPU library.
+ *
+ * How it follows the paper (Akkurt, Witherden, Vincent, "Cache blocking for flux reconstruction:
+ * extension to Navier-Stokes equations and anti-aliasing"):
+ *   - operators are DENSE per element type, built from a modal orthonormal basis and a nodal
+ *     Vandermonde matrix (Sec. 2.2 operator definitions M0..M10); there is no sum factorisation;
+ *   - one loop per paper kernel, in the paper's execution order (Sec. 3):
+ *       disu, con_u, tgradpcoru, tgradcoru, gradcoru, gradcoru_fpts, gradcoru_qpts, uqpts,
+ *       tdisf, tdivtpcorf, comm_flux, tdivtconf, negdivconf.
+ *
+ * Readings where the paper is silent or garbled (each one stated where it is used):
+ *   G1  temperature T = p/(rho R); the heat flux is mu*gamma/((gamma-1)Pr) grad(p/rho).
+ *   G3  the LDG penalty tau(uL-uR) is dissipative in the total flux f = fe - fv.
+ *   G4  M7 is Nq x Nu and M8 is Nu x Nq (the index definitions, not the printed dims).
+ *   G5  the gradient is of the physical solution u (equivalent for affine elements).
+ *   R2  hex flux points: n x n Gauss-Legendre (GL) points per face.
+ *   R3  correction functions are the DG-equivalent ones: lift = M^-1 E with the exact mass
+ *       matrix M and E = int_face l_zeta l^face_sigma dS (reference measure).
+ *   R4  Rusanov: F = 1/2 n.(fe_L + fe_R) + 1/2 s (uL - uR), s = max(|vL.n|+cL, |vR.n|+cR).
+ *   R5  the L side of a flux-point pair is the element with the smaller global index (hexes
+ *       before prisms); a self-pair takes the smaller local face number as L.
+ *   R6  transformed common flux D = |n_s| F with n_s = detJ J^-T n~; each side uses its own |n_s|.
+ *   R7  prism solution points: the paper's Williams-Shunn triangle points x GL points in z.
+ *   R8  prism quadrature: collapsed (Duffy) k x k GL triangle rule x m GL points in z.
+ *   R11 orthonormal bases: normalised Legendre on lines; Gram-Schmidt of monomials on triangles.
+ *
+ * Parity pins: see tests/test_oracle_*.py. Parity for the prism element and for the R4/R5
+ * readings is unpinned beyond invariants (freestream, conservation, polynomial exactness).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <stdio.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define NV 5
+#define ND 3
+
+/* ---------------------------------------------------------------------------------------------
+ * Small dense linear algebra
+ * ------------------------------------------------------------------------------------------- */
+
+/* In-place inverse of the n x n row-major matrix a by Gauss-Jordan elimination with partial
+ * pivoting. Returns 0 on success, -1 if the matrix is numerically singular. */
+static int mat_inverse(int n, double *a)
+{
+    double *b = (double *)calloc((size_t)n * 2 * n, sizeof(double));
+    int w = 2 * n;
+    for (int i = 0; i < n; i++) {
+        for (int j = 0; j < n; j++) b[i * w + j] = a[i * n + j];
+        b[i * w + n + i] = 1.0;
+    }
+    for (int c = 0; c < n; c++) {
+        int piv = c;
+        for (int r = c + 1; r < n; r++)
+            if (fabs(b[r * w + c]) > fabs(b[piv * w + c])) piv = r;
+        if (fabs(b[piv * w + c]) < 1e-300) { free(b); return -1; }
+        if (piv != c)
+            for (int j = 0; j < w; j++) { double t = b[c * w + j]; b[c * w + j] = b[piv * w + j]; b[piv * w + j] = t; }
+        double d = b[c * w + c];
+        for (int j = 0; j < w; j++) b[c * w + j] /= d;
+        for (int r = 0; r < n; r++) {
+            if (r == c) continue;
+            double f = b[r * w + c];
+            if (f == 0.0) continue;
+            for (int j = 0; j < w; j++) b[r * w + j] -= f * b[c * w + j];
+        }
+    }
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) a[i * n + j] = b[i * w + n + j];
+    free(b);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * One-dimensional building blocks
+ * ------------------------------------------------------------------------------------------- */
+
+/* Legendre polynomials P_0..P_n and their derivatives at x, from the three-term recurrence
+ * (r+1) P_{r+1} = (2r+1) x P_r - r P_{r-1} and P'_{r+1} = P'_{r-1} + (2r+1) P_r. */
+static void legendre_all(int n, double x, double *P, double *dP)
+{
+    P[0] = 1.0; dP[0] = 0.0;
+    if (n >= 1) { P[1] = x; dP[1] = 1.0; }
+    for (int r = 1; r < n; r++) {
+        P[r + 1] = ((2 * r + 1) * x * P[r] - r * P[r - 1]) / (r + 1);
+        dP[r + 1] = dP[r - 1] + (2 * r + 1) * P[r];
+    }
+}
+
+/* n-point Gauss-Legendre rule on [-1,1]: nodes are the roots of P_n (Newton iteration from a
+ * cosine guess), weights 2/((1-x^2) P_n'(x)^2). Nodes are returned in increasing order. */
+void or_gauss_legendre(int n, double *x, double *w)
+{
+    double P[64], dP[64];
+    for (int i = 0; i < n; i++) {
+        double r = -cos(M_PI * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; it++) {
+            legendre_all(n, r, P, dP);
+            double dr = P[n] / dP[n];
+            r -= dr;
+            if (fabs(dr) < 1e-16) break;
+        }
+        legendre_all(n, r, P, dP);
+        x[i] = r;
+        w[i] = 2.0 / ((1.0 - r * r) * dP[n] * dP[n]);
+    }
+}
+
+/* Lagrange basis polynomial a on the nodes xs[0..n-1], evaluated at x (product formula). */
+static double lagrange1d(int n, const double *xs, int a, double x)
+{
+    double v = 1.0;
+    for (int b = 0; b < n; b++)
+        if (b != a) v *= (x - xs[b]) / (xs[a] - xs[b]);
+    return v;
+}
+
+/* Collapsed (Duffy) k x k rule on the reference triangle (-1,-1),(1,-1),(-1,1):
+ * x = (1+a)(1-b)/2 - 1, y = b, weight w_a w_b (1-b)/2, exact for total degree 2k-2.
+ * Point index ia + k*ib. */
+void or_tri_rule(int k, double *xy, double *w)
+{
+    double g[32], gw[32];
+    or_gauss_legendre(k, g, gw);
+    for (int ib = 0; ib < k; ib++)
+        for (int ia = 0; ia < k; ia++) {
+            int q = ia + k * ib;
+            double a = g[ia], b = g[ib];
+            xy[2 * q + 0] = 0.5 * (1.0 + a) * (1.0 - b) - 1.0;
+            xy[2 * q + 1] = b;
+            w[q] = gw[ia] * gw[ib] * 0.5 * (1.0 - b);
+        }
+}
+
+/* Williams-Shunn triangle solution points as printed in the paper's prism figures
+ * (Fig. "Solution points for prism elements with polynomial orders p=2 and p=3"). */
+static const double WS_P2[6][2] = {
+    {-0.81684757298044, 0.63369514596088},   {0.63369514596088, -0.81684757298044},
+    {-0.81684757298044, -0.81684757298044},  {-0.108103018168072, -0.783793963663856},
+    {-0.783793963663856, -0.108103018168072}, {-0.108103018168072, -0.108103018168072}};
+static const double WS_P3[10][2] = {
+    {-0.333333333333333, -0.333333333333333}, {-0.888871894660414, 0.777743789320828},
+    {0.777743789320828, -0.888871894660414},  {-0.888871894660414, -0.888871894660414},
+    {0.268421495491446, -0.408932576528214},  {-0.859488918963232, -0.408932576528214},
+    {-0.408932576528214, -0.859488918963232}, {0.268421495491446, -0.859488918963232},
+    {-0.859488918963232, 0.268421495491446},  {-0.408932576528214, 0.268421495491446}};
+
+/* Copies the printed triangle points for order p into xy; returns the count or -1. */
+int or_tri_solution_points(int p, double *xy)
+{
+    if (p == 2) { memcpy(xy, WS_P2, sizeof(WS_P2)); return 6; }
+    if (p == 3) { memcpy(xy, WS_P3, sizeof(WS_P3)); return 10; }
+    return -1;
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Orthonormal modal bases (reading R11)
+ * ------------------------------------------------------------------------------------------- */
+
+typedef struct {
+    int p, nt;          /* order, number of triangle modes (p+1)(p+2)/2 */
+    int *mi, *mj;       /* monomial exponents x^i y^j, graded order */
+    double *c;          /* [nt][nt] coefficients: phi_t = sum_k c[t][k] x^mi[k] y^mj[k] */
+} tri_basis;
+
+static double ipow(double x, int k) { double v = 1.0; for (int i = 0; i < k; i++) v *= x; return v; }
+
+static void tri_basis_eval(const tri_basis *tb, double x, double y, double *phi, double *dphx, double *dphy)
+{
+    for (int t = 0; t < tb->nt; t++) {
+        double v = 0, vx = 0, vy = 0;
+        for (int k = 0; k < tb->nt; k++) {
+            int i = tb->mi[k], j = tb->mj[k];
+            double ck = tb->c[t * tb->nt + k];
+            v += ck * ipow(x, i) * ipow(y, j);
+            if (i > 0) vx += ck * i * ipow(x, i - 1) * ipow(y, j);
+            if (j > 0) vy += ck * j * ipow(x, i) * ipow(y, j - 1);
+        }
+        phi[t] = v;
+        if (dphx) dphx[t] = vx;
+        if (dphy) dphy[t] = vy;
+    }
+}
+
+/* Gram-Schmidt (modified, two passes) of the monomials x^i y^j, i+j <= p, under the collapsed
+ * rule of strength 2p+2 on the reference triangle. */
+static void tri_basis_init(tri_basis *tb, int p)
+{
+    int nt = (p + 1) * (p + 2) / 2;
+    tb->p = p; tb->nt = nt;
+    tb->mi = (int *)malloc(nt * sizeof(int));
+    tb->mj = (int *)malloc(nt * sizeof(int));
+    tb->c = (double *)calloc((size_t)nt * nt, sizeof(double));
+    int k = 0;
+    for (int d = 0; d <= p; d++)
+        for (int i = d; i >= 0; i--) { tb->mi[k] = i; tb->mj[k] = d - i; k++; }
+    int kq = p + 2, nq = kq * kq;
+    double *xy = (double *)malloc(2 * nq * sizeof(double)), *w = (double *)malloc(nq * sizeof(double));
+    or_tri_rule(kq, xy, w);
+    double *val = (double *)malloc((size_t)nt * nq * sizeof(double)); /* values of current vectors */
+    for (int t = 0; t < nt; t++) {
+        double *ct = tb->c + t * nt;
+        ct[t] = 1.0;
+        for (int q = 0; q < nq; q++) val[t * nq + q] = ipow(xy[2 * q], tb->mi[t]) * ipow(xy[2 * q + 1], tb->mj[t]);
+        for (int pass = 0; pass < 2; pass++)
+            for (int s = 0; s < t; s++) {
+                double ip = 0;
+                for (int q = 0; q < nq; q++) ip += w[q] * val[t * nq + q] * val[s * nq + q];
+                for (int kk = 0; kk < nt; kk++) ct[kk] -= ip * tb->c[s * nt + kk];
+                for (int q = 0; q < nq; q++) val[t * nq + q] -= ip * val[s * nq + q];
+            }
+        double nrm = 0;
+        for (int q = 0; q < nq; q++) nrm += w[q] * val[t * nq + q] * val[t * nq + q];
+        nrm = sqrt(nrm);
+        for (int kk = 0; kk < nt; kk++) ct[kk] /= nrm;
+        for (int q = 0; q < nq; q++) val[t * nq + q] /= nrm;
+    }
+    free(xy); free(w); free(val);
+}
+
+static void tri_basis_free(tri_basis *tb) { free(tb->mi); free(tb->mj); free(tb->c); }
+
+/* ---------------------------------------------------------------------------------------------
+ * Element types and their dense operators
+ * ------------------------------------------------------------------------------------------- */
+
+enum { ET_HEX = 0, ET_PRI = 1 };
+
+typedef struct {
+    int kind;           /* 0 = quad, 1 = triangle */
+    int npts;
+    double nref[3];     /* unit outward reference normal */
+    double dS;          /* reference surface measure per unit (s,t) parameter area */
+} face_info;
+
+typedef struct {
+    int type, p, n1, m1;    /* type, order, 1D solution points, 1D quadrature points */
+    int nu, nf, nq, nmodes, nfaces;
+    face_info faces[6];
+    int *fpt_face;          /* [nf] face of each flux point */
+    double *xu, *xf, *xq, *wq; /* ref coordinates [n][3], quadrature weights [nq] */
+    double *fparam;         /* [nf][2] face parameters (s,t) of flux points */
+    double *nref;           /* [nf][3] */
+    double *M0;             /* [nf][nu]  disu: l_zeta(x^f_sigma) */
+    double *Dm;             /* [3][nu][nu] d/dx~_d l_nu at x^u_zeta (M4 = M1) */
+    double *M3;             /* [nu][nf]  DG-equivalent lift (div g), reading R3 */
+    double *M7;             /* [nq][nu]  l_zeta(x^q_sigma) */
+    double *M8;             /* [nu][nq]  sum_nu psi(x^u) w^q psi(x^q) */
+    double *Agrad;          /* [3][nu][nu] M4 - M6 M0 (per direction) */
+    double *Adiv;           /* [nu][3][nu] M1 - M3 M2 */
+    double *Wu;             /* [nu] int l_zeta over the reference element */
+    tri_basis tb;           /* prism only */
+    double g1[16], g1w[16]; /* 1D GL solution nodes */
+} etype_t;
+
+/* Modal orthonormal basis and its reference gradient at a point. */
+static void modal_eval(const etype_t *et, const double *X, double *psi, double *dpsi /* [3][nmodes] or NULL */)
+{
+    int p = et->p, n1 = p + 1;
+    double Px[32], dPx[32], Py[32], dPy[32], Pz[32], dPz[32];
+    legendre_all(p, X[2], Pz, dPz);
+    for (int r = 0; r <= p; r++) { double s = sqrt(r + 0.5); Pz[r] *= s; dPz[r] *= s; }
+    if (et->type == ET_HEX) {
+        legendre_all(p, X[0], Px, dPx);
+        legendre_all(p, X[1], Py, dPy);
+        for (int r = 0; r <= p; r++) {
+            double s = sqrt(r + 0.5);
+            Px[r] *= s; dPx[r] *= s; Py[r] *= s; dPy[r] *= s;
+        }
+        for (int c = 0; c < n1; c++)
+            for (int b = 0; b < n1; b++)
+                for (int a = 0; a < n1; a++) {
+                    int nu = a + n1 * b + n1 * n1 * c;
+                    psi[nu] = Px[a] * Py[b] * Pz[c];
+                    if (dpsi) {
+                        dpsi[0 * et->nmodes + nu] = dPx[a] * Py[b] * Pz[c];
+                        dpsi[1 * et->nmodes + nu] = Px[a] * dPy[b] * Pz[c];
+                        dpsi[2 * et->nmodes + nu] = Px[a] * Py[b] * dPz[c];
+                    }
+                }
+    } else {
+        int nt = et->tb.nt;
+        double phi[64], phx[64], phy[64];
+        tri_basis_eval(&et->tb, X[0], X[1], phi, phx, phy);
+        for (int c = 0; c < n1; c++)
+            for (int t = 0; t < nt; t++) {
+                int nu = t + nt * c;
+                psi[nu] = phi[t] * Pz[c];
+                if (dpsi) {
+                    dpsi[0 * et->nmodes + nu] = phx[t] * Pz[c];
+                    dpsi[1 * et->nmodes + nu] = phy[t] * Pz[c];
+                    dpsi[2 * et->nmodes + nu] = phi[t] * dPz[c];
+                }
+            }
+    }
+}
+
+/* Maps face parameters (s,t) of face f to reference coordinates X. */
+static void face_map(const etype_t *et, int f, double s, double t, double *X)
+{
+    if (et->type == ET_HEX) {
+        int d = f / 2; double side = (f % 2) ? 1.0 : -1.0;
+        int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+        X[d] = side; X[t1] = s; X[t2] = t;
+    } else {
+        switch (f) {
+        case 0: X[0] = s; X[1] = t; X[2] = -1.0; break;   /* triangle z = -1 */
+        case 1: X[0] = s; X[1] = t; X[2] = 1.0; break;    /* triangle z = +1 */
+        case 2: X[0] = s; X[1] = -1.0; X[2] = t; break;   /* quad y = -1 */
+        case 3: X[0] = -s; X[1] = s; X[2] = t; break;     /* quad x + y = 0 */
+        default: X[0] = -1.0; X[1] = s; X[2] = t; break;  /* quad x = -1 */
+        }
+    }
+}
+
+/* Face nodal basis function j of face f (quad: GL Lagrange in s,t; triangle: nodal basis on the
+ * triangle solution points), evaluated at face parameters (s,t). */
+static double face_nodal(const etype_t *et, int f, int j, double s, double t, const double *TVinv)
+{
+    if (et->faces[f].kind == 0) {
+        int n1 = et->n1;
+        return lagrange1d(n1, et->g1, j % n1, s) * lagrange1d(n1, et->g1, j / n1, t);
+    }
+    int nt = et->tb.nt;
+    double phi[64];
+    tri_basis_eval(&et->tb, s, t, phi, NULL, NULL);
+    double v = 0;
+    for (int k = 0; k < nt; k++) v += phi[k] * TVinv[k * nt + j];
+    return v;
+}
+
+static int etype_init(etype_t *et, int type, int p, int m, int tri_k)
+{
+    memset(et, 0, sizeof(*et));
+    et->type = type; et->p = p; et->n1 = p + 1; et->m1 = m;
+    int n1 = p + 1;
+    or_gauss_legendre(n1, et->g1, et->g1w);
+    double gq[32], gqw[32];
+    or_gauss_legendre(m, gq, gqw);
+    double txy[2 * 64];
+    int nt = 0;
+    if (type == ET_HEX) {
+        et->nu = n1 * n1 * n1; et->nmodes = et->nu; et->nfaces = 6;
+        et->nq = m * m * m;
+        for (int f = 0; f < 6; f++) {
+            et->faces[f].kind = 0; et->faces[f].npts = n1 * n1; et->faces[f].dS = 1.0;
+            memset(et->faces[f].nref, 0, sizeof(double) * 3);
+            et->faces[f].nref[f / 2] = (f % 2) ? 1.0 : -1.0;
+        }
+    } else {
+        nt = or_tri_solution_points(p, txy);
+        if (nt < 0) return -1;
+        tri_basis_init(&et->tb, p);
+        et->nu = nt * n1; et->nmodes = et->nu; et->nfaces = 5;
+        if (tri_k < 1) tri_k = m;
+        et->nq = tri_k * tri_k * m;
+        double r2 = 1.0 / sqrt(2.0);
+        face_info fi[5] = {
+            {1, nt, {0, 0, -1}, 1.0}, {1, nt, {0, 0, 1}, 1.0},
+            {0, n1 * n1, {0, -1, 0}, 1.0}, {0, n1 * n1, {r2, r2, 0}, sqrt(2.0)},
+            {0, n1 * n1, {-1, 0, 0}, 1.0}};
+        for (int f = 0; f < 5; f++) et->faces[f] = fi[f];
+    }
+    int nf = 0;
+    for (int f = 0; f < et->nfaces; f++) nf += et->faces[f].npts;
+    et->nf = nf;
+    int nu = et->nu, nq = et->nq;
+
+    et->xu = (double *)malloc(nu * 3 * sizeof(double));
+    et->xf = (double *)malloc(nf * 3 * sizeof(double));
+    et->fparam = (double *)malloc(nf * 2 * sizeof(double));
+    et->nref = (double *)malloc(nf * 3 * sizeof(double));
+    et->fpt_face = (int *)malloc(nf * sizeof(int));
+    et->xq = (double *)malloc(nq * 3 * sizeof(double));
+    et->wq = (double *)malloc(nq * sizeof(double));
+
+    /* solution points (R1, R7) */
+    if (type == ET_HEX) {
+        for (int k = 0; k < n1; k++)
+            for (int j = 0; j < n1; j++)
+                for (int i = 0; i < n1; i++) {
+                    int z = i + n1 * j + n1 * n1 * k;
+                    et->xu[3 * z] = et->g1[i]; et->xu[3 * z + 1] = et->g1[j]; et->xu[3 * z + 2] = et->g1[k];
+                }
+    } else {
+        for (int k = 0; k < n1; k++)
+            for (int t = 0; t < nt; t++) {
+                int z = t + nt * k;
+                et->xu[3 * z] = txy[2 * t]; et->xu[3 * z + 1] = txy[2 * t + 1]; et->xu[3 * z + 2] = et->g1[k];
+            }
+    }
+    /* flux points (R2, R7) */
+    {
+        int s = 0;
+        for (int f = 0; f < et->nfaces; f++) {
+            for (int j = 0; j < et->faces[f].npts; j++, s++) {
+                double ps, pt;
+                if (et->faces[f].kind == 0) { ps = et->g1[j % n1]; pt = et->g1[j / n1]; }
+                else { ps = txy[2 * j]; pt = txy[2 * j + 1]; }
+                et->fparam[2 * s] = ps; et->fparam[2 * s + 1] = pt;
+                face_map(et, f, ps, pt, et->xf + 3 * s);
+                for (int d = 0; d < 3; d++) et->nref[3 * s + d] = et->faces[f].nref[d];
+                et->fpt_face[s] = f;
+            }
+        }
+    }
+    /* volume quadrature (hex: GL^3; prism: R8) */
+    if (type == ET_HEX) {
+        for (int c = 0; c < m; c++)
+            for (int b = 0; b < m; b++)
+                for (int a = 0; a < m; a++) {
+                    int q = a + m * b + m * m * c;
+                    et->xq[3 * q] = gq[a]; et->xq[3 * q + 1] = gq[b]; et->xq[3 * q + 2] = gq[c];
+                    et->wq[q] = gqw[a] * gqw[b] * gqw[c];
+                }
+    } else {
+        int nt2 = tri_k * tri_k;
+        double *txq = (double *)malloc(2 * nt2 * sizeof(double)), *twq = (double *)malloc(nt2 * sizeof(double));
+        or_tri_rule(tri_k, txq, twq);
+        for (int c = 0; c < m; c++)
+            for (int t = 0; t < nt2; t++) {
+                int q = t + nt2 * c;
+                et->xq[3 * q] = txq[2 * t]; et->xq[3 * q + 1] = txq[2 * t + 1]; et->xq[3 * q + 2] = gq[c];
+                et->wq[q] = twq[t] * gqw[c];
+            }
+        free(txq); free(twq);
+    }
+
+    /* Nodal basis: V[zeta][nu] = psi_nu(x_zeta); l_zeta(x) = sum_nu psi_nu(x) Vinv[nu][zeta]. */
+    int nm = et->nmodes;
+    double *V = (double *)malloc((size_t)nu * nm * sizeof(double));
+    double *psi = (double *)malloc(nm * sizeof(double)), *dpsi = (double *)malloc(3 * nm * sizeof(double));
+    for (int z = 0; z < nu; z++) {
+        modal_eval(et, et->xu + 3 * z, psi, NULL);
+        for (int v = 0; v < nm; v++) V[z * nm + v] = psi[v];
+    }
+    double *Vinv = (double *)malloc((size_t)nu * nm * sizeof(double));
+    memcpy(Vinv, V, (size_t)nu * nm * sizeof(double));
+    if (mat_inverse(nu, Vinv)) return -2;
+
+    et->M0 = (double *)calloc((size_t)nf * nu, sizeof(double));
+    et->Dm = (double *)calloc((size_t)3 * nu * nu, sizeof(double));
+    et->M7 = (double *)calloc((size_t)nq * nu, sizeof(double));
+    et->M8 = (double *)calloc((size_t)nu * nq, sizeof(double));
+    et->M3 = (double *)calloc((size_t)nu * nf, sizeof(double));
+    et->Wu = (double *)calloc(nu, sizeof(double));
+
+    /* M0 (disu) */
+    for (int s = 0; s < nf; s++) {
+        modal_eval(et, et->xf + 3 * s, psi, NULL);
+        for (int z = 0; z < nu; z++) {
+            double v = 0;
+            for (int k = 0; k < nm; k++) v += psi[k] * Vinv[k * nu + z];
+            et->M0[s * nu + z] = v;
+        }
+    }
+    /* M4 = M1: derivative of the nodal basis at solution points */
+    for (int zp = 0; zp < nu; zp++) {
+        modal_eval(et, et->xu + 3 * zp, psi, dpsi);
+        for (int d = 0; d < 3; d++)
+            for (int z = 0; z < nu; z++) {
+                double v = 0;
+                for (int k = 0; k < nm; k++) v += dpsi[d * nm + k] * Vinv[k * nu + z];
+                et->Dm[(d * nu + zp) * nu + z] = v;
+            }
+    }
+    /* M7 (uqpts) and M8 (L2 projection, reading G4 for its shape) */
+    double *PQ = (double *)malloc((size_t)nq * nm * sizeof(double));
+    for (int q = 0; q < nq; q++) {
+        modal_eval(et, et->xq + 3 * q, psi, NULL);
+        for (int k = 0; k < nm; k++) PQ[q * nm + k] = psi[k];
+        for (int z = 0; z < nu; z++) {
+            double v = 0;
+            for (int k = 0; k < nm; k++) v += psi[k] * Vinv[k * nu + z];
+            et->M7[q * nu + z] = v;
+        }
+    }
+    for (int z = 0; z < nu; z++)
+        for (int q = 0; q < nq; q++) {
+            double v = 0;
+            for (int k = 0; k < nm; k++) v += V[z * nm + k] * et->wq[q] * PQ[q * nm + k];
+            et->M8[z * nq + q] = v;
+        }
+    /* quadrature weights of the nodal basis: W_zeta = sum_q w_q l_zeta(x_q) */
+    for (int z = 0; z < nu; z++) {
+        double v = 0;
+        for (int q = 0; q < nq; q++) v += et->wq[q] * et->M7[q * nu + z];
+        et->Wu[z] = v;
+    }
+
+    /* Lift (reading R3): Minv = V V^T in the orthonormal basis; E by face quadrature. */
+    {
+        double *TVinv = NULL;
+        if (type == ET_PRI) {
+            TVinv = (double *)malloc(nt * nt * sizeof(double));
+            double phi[64];
+            for (int a = 0; a < nt; a++) {
+                tri_basis_eval(&et->tb, txy[2 * a], txy[2 * a + 1], phi, NULL, NULL);
+                for (int k = 0; k < nt; k++) TVinv[a * nt + k] = phi[k];
+            }
+            if (mat_inverse(nt, TVinv)) return -3;
+        }
+        double *E = (double *)calloc((size_t)nu * nf, sizeof(double));
+        int kq = p + 2;
+        double gf[32], gfw[32];
+        or_gauss_legendre(kq, gf, gfw);
+        double *tq = (double *)malloc(2 * kq * kq * sizeof(double)), *tw = (double *)malloc(kq * kq * sizeof(double));
+        or_tri_rule(kq, tq, tw);
+        int s0 = 0;
+        for (int f = 0; f < et->nfaces; f++) {
+            int npf = et->faces[f].npts;
+            int nfq = (et->faces[f].kind == 0) ? kq * kq : kq * kq;
+            for (int iq = 0; iq < nfq; iq++) {
+                double s, t, wgt;
+                if (et->faces[f].kind == 0) { s = gf[iq % kq]; t = gf[iq / kq]; wgt = gfw[iq % kq] * gfw[iq / kq]; }
+                else { s = tq[2 * iq]; t = tq[2 * iq + 1]; wgt = tw[iq]; }
+                wgt *= et->faces[f].dS;
+                double X[3];
+                face_map(et, f, s, t, X);
+                modal_eval(et, X, psi, NULL);
+                for (int j = 0; j < npf; j++) {
+                    double lf = face_nodal(et, f, j, s, t, TVinv);
+                    for (int z = 0; z < nu; z++) {
+                        double lz = 0;
+                        for (int k = 0; k < nm; k++) lz += psi[k] * Vinv[k * nu + z];
+                        E[z * nf + s0 + j] += wgt * lz * lf;
+                    }
+                }
+            }
+            s0 += npf;
+        }
+        for (int z = 0; z < nu; z++)
+            for (int s = 0; s < nf; s++) {
+                double v = 0;
+                for (int zp = 0; zp < nu; zp++) {
+                    double minv = 0;
+                    for (int k = 0; k < nm; k++) minv += V[z * nm + k] * V[zp * nm + k];
+                    v += minv * E[zp * nf + s];
+                }
+                et->M3[z * nf + s] = v;
+            }
+        free(E); free(tq); free(tw); free(TVinv);
+    }
+
+    /* tgradpcoru operator M4 - M6 M0 with (M6)_d[zeta][sigma] = M3[zeta][sigma] n~_d(sigma) */
+    et->Agrad = (double *)calloc((size_t)3 * nu * nu, sizeof(double));
+    for (int d = 0; d < 3; d++)
+        for (int z = 0; z < nu; z++)
+            for (int zz = 0; zz < nu; zz++) {
+                double v = et->Dm[(d * nu + z) * nu + zz];
+                for (int s = 0; s < nf; s++) v -= et->M3[z * nf + s] * et->nref[3 * s + d] * et->M0[s * nu + zz];
+                et->Agrad[(d * nu + z) * nu + zz] = v;
+            }
+    /* tdivtpcorf operator M1 - M3 M2 with (M2)[sigma][(d,zeta)] = l_zeta(x^f_sigma) n~_d(sigma) */
+    et->Adiv = (double *)calloc((size_t)nu * 3 * nu, sizeof(double));
+    for (int z = 0; z < nu; z++)
+        for (int d = 0; d < 3; d++)
+            for (int zz = 0; zz < nu; zz++) {
+                double v = et->Dm[(d * nu + z) * nu + zz];
+                for (int s = 0; s < nf; s++) v -= et->M3[z * nf + s] * et->M0[s * nu + zz] * et->nref[3 * s + d];
+                et->Adiv[(z * 3 + d) * nu + zz] = v;
+            }
+    free(V); free(Vinv); free(psi); free(dpsi); free(PQ);
+    return 0;
+}
+
+static void etype_free(etype_t *et)
+{
+    free(et->fpt_face); free(et->xu); free(et->xf); free(et->xq); free(et->wq); free(et->fparam);
+    free(et->nref); free(et->M0); free(et->Dm); free(et->M3); free(et->M7); free(et->M8);
+    free(et->Agrad); free(et->Adiv); free(et->Wu);
+    if (et->type == ET_PRI) tri_basis_free(&et->tb);
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Mesh, metrics and interface pairs
+ * ------------------------------------------------------------------------------------------- */
+
+typedef struct {
+    double gamma, Pr, mu, beta, tau;
+} phys_params;
+
+typedef struct {
+    phys_params ph;
+    etype_t et[2];
+    int has[2];
+    int n_hex, n_pri, ne;
+    double period[3];
+    double *x0;     /* [ne][3] reference origin: x = x0 + J (xi + 1) */
+    double *J;      /* [ne][9] row-major dx_i/dxi_j */
+    double *Jinv;   /* [ne][9] dxi_i/dx_j */
+    double *detJ;   /* [ne] */
+    long *uoff, *foff; /* per element offset into [elem][var][pt] solution and flux-point arrays */
+    long nU, nF;       /* total solution and flux-point values (times NV) */
+    long nfpt;         /* total flux points */
+    long *fpt_base;    /* per element first global flux point */
+    int *fpt_elem;     /* [nfpt] element of global flux point */
+    long npair;
+    long *pairL, *pairR; /* global flux points of each pair, L per reading R5 */
+    /* work arrays */
+    double *UF, *CF, *DF, *Q, *QF, *Rt;
+    int nthreads;
+} oracle_t;
+
+static const etype_t *ET(const oracle_t *o, int e) { return &o->et[e < o->n_hex ? ET_HEX : ET_PRI]; }
+
+static double pdist(const oracle_t *o, const double *a, const double *b)
+{
+    double s = 0;
+    for (int d = 0; d < 3; d++) {
+        double x = a[d] - b[d];
+        if (o->period[d] > 0) x -= o->period[d] * floor(x / o->period[d] + 0.5);
+        s += x * x;
+    }
+    return sqrt(s);
+}
+
+static void phys_coord(const oracle_t *o, int e, const double *X, double *x)
+{
+    for (int i = 0; i < 3; i++) {
+        x[i] = o->x0[3 * e + i];
+        for (int j = 0; j < 3; j++) x[i] += o->J[9 * e + 3 * i + j] * (X[j] + 1.0);
+    }
+}
+
+static void inv3(const double *a, double *b, double *det)
+{
+    double d = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) + a[2] * (a[3] * a[7] - a[4] * a[6]);
+    b[0] = (a[4] * a[8] - a[5] * a[7]) / d; b[1] = (a[2] * a[7] - a[1] * a[8]) / d; b[2] = (a[1] * a[5] - a[2] * a[4]) / d;
+    b[3] = (a[5] * a[6] - a[3] * a[8]) / d; b[4] = (a[0] * a[8] - a[2] * a[6]) / d; b[5] = (a[2] * a[3] - a[0] * a[5]) / d;
+    b[6] = (a[3] * a[7] - a[4] * a[6]) / d; b[7] = (a[1] * a[6] - a[0] * a[7]) / d; b[8] = (a[0] * a[4] - a[1] * a[3]) / d;
+    *det = d;
+}
+
+/* Error codes (match the GPU library's status numbers for convenience in tests). */
+#define OR_OK 0
+#define OR_EINVAL 1
+#define OR_EMESH 4
+#define OR_EUNSUPPORTED 7
+
+void or_destroy(void *h);
+
+void *or_create(int p, int m, int tri_k, double gamma, double Pr, double mu, double beta, double tau,
+                int n_hex, int n_pri, int n_verts, const double *verts, const int *hex_v, const int *pri_v,
+                const double *period, int *err)
+{
+    *err = OR_OK;
+    if (p < 1 || m < 1 || n_hex < 0 || n_pri < 0 || n_hex + n_pri == 0) { *err = OR_EINVAL; return NULL; }
+    oracle_t *o = (oracle_t *)calloc(1, sizeof(oracle_t));
+    o->ph.gamma = gamma; o->ph.Pr = Pr; o->ph.mu = mu; o->ph.beta = beta; o->ph.tau = tau;
+    o->n_hex = n_hex; o->n_pri = n_pri; o->ne = n_hex + n_pri;
+    for (int d = 0; d < 3; d++) o->period[d] = period ? period[d] : 0.0;
+    o->nthreads = 1;
+    if (n_hex > 0) { if (etype_init(&o->et[ET_HEX], ET_HEX, p, m, tri_k)) { *err = OR_EUNSUPPORTED; free(o); return NULL; } o->has[ET_HEX] = 1; }
+    if (n_pri > 0) { if (etype_init(&o->et[ET_PRI], ET_PRI, p, m, tri_k)) { *err = OR_EUNSUPPORTED; or_destroy(o); return NULL; } o->has[ET_PRI] = 1; }
+    int ne = o->ne;
+    o->x0 = (double *)malloc(3 * ne * sizeof(double));
+    o->J = (double *)malloc(9 * ne * sizeof(double));
+    o->Jinv = (double *)malloc(9 * ne * sizeof(double));
+    o->detJ = (double *)malloc(ne * sizeof(double));
+    o->uoff = (long *)malloc(ne * sizeof(long));
+    o->foff = (long *)malloc(ne * sizeof(long));
+    o->fpt_base = (long *)malloc(ne * sizeof(long));
+    long uo = 0, fo = 0, fb = 0;
+    for (int e = 0; e < ne; e++) {
+        const etype_t *et = ET(o, e);
+        o->uoff[e] = uo; o->foff[e] = fo; o->fpt_base[e] = fb;
+        uo += (long)NV * et->nu; fo += (long)NV * et->nf; fb += et->nf;
+        /* affine map from vertices; reject non-affine or inverted elements */
+        const double *v[8];
+        int nv = (e < n_hex) ? 8 : 6;
+        for (int k = 0; k < nv; k++) {
+            int vi = (e < n_hex) ? hex_v[8 * e + k] : pri_v[6 * (e - n_hex) + k];
+            if (vi < 0 || vi >= n_verts) { *err = OR_EMESH; or_destroy(o); return NULL; }
+            v[k] = verts + 3 * vi;
+        }
+        int c1 = 1, c2 = 2, c3 = (e < n_hex) ? 4 : 3;
+        double scale = 0;
+        for (int i = 0; i < 3; i++) {
+            o->x0[3 * e + i] = v[0][i];
+            o->J[9 * e + 3 * i + 0] = 0.5 * (v[c1][i] - v[0][i]);
+            o->J[9 * e + 3 * i + 1] = 0.5 * (v[c2][i] - v[0][i]);
+            o->J[9 * e + 3 * i + 2] = 0.5 * (v[c3][i] - v[0][i]);
+            scale += fabs(v[c1][i] - v[0][i]) + fabs(v[c2][i] - v[0][i]) + fabs(v[c3][i] - v[0][i]);
+        }
+        /* affinity: every vertex equals the affine image of its reference corner */
+        for (int k = 0; k < nv; k++) {
+            double X[3];
+            if (e < n_hex) { X[0] = (k & 1) ? 1 : -1; X[1] = (k & 2) ? 1 : -1; X[2] = (k & 4) ? 1 : -1; }
+            else {
+                static const double pc[6][3] = {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}, {1, -1, 1}, {-1, 1, 1}};
+                X[0] = pc[k][0]; X[1] = pc[k][1]; X[2] = pc[k][2];
+            }
+            double x[3];
+            phys_coord(o, e, X, x);
+            for (int i = 0; i < 3; i++)
+                if (fabs(x[i] - v[k][i]) > 1e-10 * scale) { *err = OR_EUNSUPPORTED; or_destroy(o); return NULL; }
+        }
+        inv3(o->J + 9 * e, o->Jinv + 9 * e, &o->detJ[e]);
+        if (!(o->detJ[e] > 0)) { *err = OR_EMESH; or_destroy(o); return NULL; }
+    }
+    o->nU = uo; o->nF = fo; o->nfpt = fb;
+    o->fpt_elem = (int *)malloc(fb * sizeof(int));
+    for (int e = 0; e < ne; e++)
+        for (int s = 0; s < ET(o, e)->nf; s++) o->fpt_elem[o->fpt_base[e] + s] = e;
+
+    /* Interface pairing by physical coordinates (brute force over faces, then over points). */
+    int nfaces_tot = 0;
+    for (int e = 0; e < ne; e++) nfaces_tot += ET(o, e)->nfaces;
+    int *fe = (int *)malloc(nfaces_tot * sizeof(int)), *ff = (int *)malloc(nfaces_tot * sizeof(int));
+    int *fs0 = (int *)malloc(nfaces_tot * sizeof(int));
+    double *fc = (double *)malloc(3 * nfaces_tot * sizeof(double));
+    double *fsize = (double *)malloc(nfaces_tot * sizeof(double));
+    int *mate = (int *)malloc(nfaces_tot * sizeof(int));
+    {
+        int k = 0;
+        for (int e = 0; e < ne; e++) {
+            const etype_t *et = ET(o, e);
+            int s0 = 0;
+            for (int f = 0; f < et->nfaces; f++) {
+                fe[k] = e; ff[k] = f; fs0[k] = s0; mate[k] = -1;
+                /* reference face centroid: mean of the face points is not needed; use first point
+                 * coordinates of every point to build a centroid */
+                double c[3] = {0, 0, 0};
+                double first[3];
+                for (int j = 0; j < et->faces[f].npts; j++) {
+                    double x[3];
+                    phys_coord(o, e, et->xf + 3 * (s0 + j), x);
+                    if (j == 0) memcpy(first, x, sizeof(first));
+                    /* unwrap against the first point so the centroid is meaningful across a period */
+                    for (int d = 0; d < 3; d++) {
+                        double dx = x[d] - first[d];
+                        if (o->period[d] > 0) dx -= o->period[d] * floor(dx / o->period[d] + 0.5);
+                        c[d] += first[d] + dx;
+                    }
+                }
+                for (int d = 0; d < 3; d++) fc[3 * k + d] = c[d] / et->faces[f].npts;
+                fsize[k] = pow(fabs(o->detJ[e]), 1.0 / 3.0);
+                s0 += et->faces[f].npts;
+                k++;
+            }
+        }
+    }
+    for (int a = 0; a < nfaces_tot; a++) {
+        if (mate[a] >= 0) continue;
+        for (int b = a + 1; b < nfaces_tot; b++) {
+            if (mate[b] >= 0) continue;
+            if (pdist(o, fc + 3 * a, fc + 3 * b) < 1e-8 * fsize[a]) { mate[a] = b; mate[b] = a; break; }
+        }
+        if (mate[a] < 0) {
+            /* a face may pair with itself only if the mesh has a period of one element; that
+             * cannot happen for a single face, so an unmatched face is a mesh error */
+            *err = OR_EMESH; free(fe); free(ff); free(fs0); free(fc); free(fsize); free(mate); or_destroy(o); return NULL;
+        }
+    }
+    o->npair = o->nfpt / 2;
+    o->pairL = (long *)malloc(o->npair * sizeof(long));
+    o->pairR = (long *)malloc(o->npair * sizeof(long));
+    long ip = 0;
+    for (int a = 0; a < nfaces_tot; a++) {
+        int b = mate[a];
+        if (b < a) continue;
+        int ea = fe[a], eb = fe[b];
+        const etype_t *ta = ET(o, ea), *tb = ET(o, eb);
+        if (ta->faces[ff[a]].npts != tb->faces[ff[b]].npts) { *err = OR_EMESH; break; }
+        int np = ta->faces[ff[a]].npts;
+        /* reading R5: L = smaller element index; self-pair -> smaller local face */
+        int aL = (ea < eb || (ea == eb && ff[a] < ff[b]));
+        for (int j = 0; j < np; j++) {
+            double xa[3];
+            phys_coord(o, ea, ta->xf + 3 * (fs0[a] + j), xa);
+            int found = -1;
+            for (int jj = 0; jj < np; jj++) {
+                double xb[3];
+                phys_coord(o, eb, tb->xf + 3 * (fs0[b] + jj), xb);
+                if (pdist(o, xa, xb) < 1e-8 * fsize[a]) { found = jj; break; }
+            }
+            if (found < 0) { *err = OR_EMESH; break; }
+            long ga = o->fpt_base[ea] + fs0[a] + j, gb = o->fpt_base[eb] + fs0[b] + found;
+            o->pairL[ip] = aL ? ga : gb;
+            o->pairR[ip] = aL ? gb : ga;
+            ip++;
+        }
+        if (*err) break;
+    }
+    free(fe); free(ff); free(fs0); free(fc); free(fsize); free(mate);
+    if (*err || ip != o->npair) { if (!*err) *err = OR_EMESH; or_destroy(o); return NULL; }
+
+    o->UF = (double *)calloc(o->nF, sizeof(double));
+    o->CF = (double *)calloc(o->nF, sizeof(double));
+    o->DF = (double *)calloc(o->nF, sizeof(double));
+    o->QF = (double *)calloc(3 * o->nF, sizeof(double));
+    o->Q = (double *)calloc(3 * o->nU, sizeof(double));
+    o->Rt = (double *)calloc(o->nU, sizeof(double));
+    return o;
+}
+
+void or_destroy(void *h)
+{
+    oracle_t *o = (oracle_t *)h;
+    if (!o) return;
+    for (int t = 0; t < 2; t++) if (o->has[t]) etype_free(&o->et[t]);
+    free(o->x0); free(o->J); free(o->Jinv); free(o->detJ); free(o->uoff); free(o->foff);
+    free(o->fpt_base); free(o->fpt_elem); free(o->pairL); free(o->pairR);
+    free(o->UF); free(o->CF); free(o->DF); free(o->QF); free(o->Q); free(o->Rt);
+    free(o);
+}
+
+void or_set_threads(void *h, int n) { ((oracle_t *)h)->nthreads = n > 0 ? n : 1; }
+
+long or_num_values(void *h) { return ((oracle_t *)h)->nU; }
+long or_num_fvalues(void *h) { return ((oracle_t *)h)->nF; }
+long or_num_pairs(void *h) { return ((oracle_t *)h)->npair; }
+
+/* Physical coordinates of every solution point, layout [elem][pt][3]. */
+void or_sol_coords(void *h, double *xyz)
+{
+    oracle_t *o = (oracle_t *)h;
+    long k = 0;
+    for (int e = 0; e < o->ne; e++) {
+        const etype_t *et = ET(o, e);
+        for (int z = 0; z < et->nu; z++, k++) phys_coord(o, e, et->xu + 3 * z, xyz + 3 * k);
+    }
+}
+
+/* Physical coordinates of every flux point, layout [elem][fpt][3]. */
+void or_flux_coords(void *h, double *xyz)
+{
+    oracle_t *o = (oracle_t *)h;
+    long k = 0;
+    for (int e = 0; e < o->ne; e++) {
+        const etype_t *et = ET(o, e);
+        for (int s = 0; s < et->nf; s++, k++) phys_coord(o, e, et->xf + 3 * s, xyz + 3 * k);
+    }
+}
+
+/* Pair list (global flux point ids), for tests. */
+void or_pairs(void *h, long *L, long *R)
+{
+    oracle_t *o = (oracle_t *)h;
+    memcpy(L, o->pairL, o->npair * sizeof(long));
+    memcpy(R, o->pairR, o->npair * sizeof(long));
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Physics: inviscid and viscous fluxes (Sec. 2.1, Eqs. for f^e and f^v)
+ * ------------------------------------------------------------------------------------------- */
+
+/* f[d][alpha], d = direction */
+static void flux_inviscid(const phys_params *ph, const double *u, double f[3][NV], double *p_out)
+{
+    double rho = u[0], vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho, E = u[4];
+    double p = (ph->gamma - 1.0) * (E - 0.5 * rho * (vx * vx + vy * vy + vz * vz));
+    double v[3] = {vx, vy, vz};
+    for (int d = 0; d < 3; d++) {
+        f[d][0] = rho * v[d];
+        f[d][1] = rho * v[d] * vx + (d == 0 ? p : 0.0);
+        f[d][2] = rho * v[d] * vy + (d == 1 ? p : 0.0);
+        f[d][3] = rho * v[d] * vz + (d == 2 ? p : 0.0);
+        f[d][4] = v[d] * (E + p);
+    }
+    if (p_out) *p_out = p;
+}
+
+/* Viscous flux f^v(u, q), q[alpha][d] = physical gradient. Stress tensor per Sec. 2.1 and heat
+ * flux per reading G1: phi = mu gamma/((gamma-1) Pr) grad(p/rho). */
+static void flux_viscous(const phys_params *ph, const double *u, const double q[NV][3], double f[3][NV])
+{
+    double rho = u[0], v[3] = {u[1] / rho, u[2] / rho, u[3] / rho}, E = u[4];
+    double dv[3][3]; /* dv[i][d] = d v_i / d x_d */
+    for (int i = 0; i < 3; i++)
+        for (int d = 0; d < 3; d++) dv[i][d] = (q[1 + i][d] - v[i] * q[0][d]) / rho;
+    double div = dv[0][0] + dv[1][1] + dv[2][2];
+    double mu = ph->mu, g = ph->gamma;
+    double T[3][3];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+            T[i][j] = mu * (dv[j][i] + dv[i][j]) - (i == j ? 2.0 / 3.0 * mu * div : 0.0);
+    double phi[3];
+    for (int d = 0; d < 3; d++) {
+        double dEr = (q[4][d] - (E / rho) * q[0][d]) / rho;            /* d(E/rho) */
+        double dke = v[0] * dv[0][d] + v[1] * dv[1][d] + v[2] * dv[2][d]; /* d(|v|^2/2) */
+        double dpr = (g - 1.0) * (dEr - dke);                            /* d(p/rho) */
+        phi[d] = mu * g / ((g - 1.0) * ph->Pr) * dpr;
+    }
+    for (int d = 0; d < 3; d++) {
+        f[d][0] = 0.0;
+        f[d][1] = T[0][d];
+        f[d][2] = T[1][d];
+        f[d][3] = T[2][d];
+        f[d][4] = v[0] * T[0][d] + v[1] * T[1][d] + v[2] * T[2][d] + phi[d];
+    }
+}
+
+/* Physical outward normal scaling of flux point s of element e: n_s = detJ J^-T n~. */
+static void normal_scaled(const oracle_t *o, int e, const double *nref, double *ns)
+{
+    for (int k = 0; k < 3; k++) {
+        ns[k] = 0;
+        for (int d = 0; d < 3; d++) ns[k] += o->Jinv[9 * e + 3 * d + k] * nref[d];
+        ns[k] *= o->detJ[e];
+    }
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * The RHS: one loop per paper kernel, in the paper's execution order
+ * ------------------------------------------------------------------------------------------- */
+
+/* Optional intermediates for stage-level parity checks (all may be NULL):
+ *   uf, cf, df: [elem][var][fpt]   qu: [elem][var][dim][pt] physical gradient at solution points
+ *   qf: [elem][var][dim][fpt]      fu: [elem][var][dim][pt] projected transformed flux F~(u) */
+typedef struct { double *uf, *cf, *qu, *qf, *fu, *df; } or_stages;
+
+static int rhs_impl(oracle_t *o, const double *U, double *R, or_stages *st)
+{
+    const phys_params *ph = &o->ph;
+    int ne = o->ne;
+#ifdef _OPENMP
+    omp_set_num_threads(o->nthreads);
+#endif
+
+    /* 1. disu: U^(f) = M0 U^(u) */
+#pragma omp parallel for schedule(static)
+    for (int e = 0; e < ne; e++) {
+        const etype_t *et = ET(o, e);
+        const double *u = U + o->uoff[e];
+        double *uf = o->UF + o->foff[e];
+        for (int a = 0; a < NV; a++)
+            for (int s = 0; s < et->nf; s++) {
+                double v = 0;
+                for (int z = 0; z < et->nu; z++) v += et->M0[s * et->nu + z] * u[a * et->nu + z];
+                uf[a * et->nf + s] = v;
+            }
+    }
+
+    /* 2. con_u: C = (1/2 - beta) uL + (1/2 + beta) uR, assigned to both points of a pair */
+#pragma omp parallel for schedule(static)
+    for (long ip = 0; ip < o->npair; ip++) {
+        long gL = o->pairL[ip], gR = o->pairR[ip];
+        int eL = o->fpt_elem[gL], eR = o->fpt_elem[gR];
+        int sL = (int)(gL - o->fpt_base[eL]), sR = (int)(gR - o->fpt_base[eR]);
+        int nfL = ET(o, eL)->nf, nfR = ET(o, eR)->nf;
+        for (int a = 0; a < NV; a++) {
+            double uL = o->UF[o->foff[eL] + a * nfL + sL], uR = o->UF[o->foff[eR] + a * nfR + sR];
+            double c = (0.5 - ph->beta) * uL + (0.5 + ph->beta) * uR;
+            o->CF[o->foff[eL] + a * nfL + sL] = c;
+            o->CF[o->foff[eR] + a * nfR + sR] = c;
+        }
+    }
+
+    /* 3.-5. tgradpcoru (Q~ = (M4 - M6 M0) U), tgradcoru (Q~ += M6 C), gradcoru (q = J^-T q~) */
+#pragma omp parallel for schedule(static)
+    for (int e = 0; e < ne; e++) {
+        const etype_t *et = ET(o, e);
+        int nu = et->nu, nf = et->nf;
+        const double *u = U + o->uoff[e];
+        const double *cf = o->CF + o->foff[e];
+        double *q = o->Q + 3 * o->uoff[e];
+        double *qt = (double *)malloc(3 * nu * sizeof(double));
+        for (int a = 0; a < NV; a++) {
+            for (int d = 0; d < 3; d++)
+                for (int z = 0; z < nu; z++) {
+                    double v = 0;
+                    for (int zz = 0; zz < nu; zz++) v += et->Agrad[(d * nu + z) * nu + zz] * u[a * nu + zz];
+                    qt[d * nu + z] = v;
+                }
+            for (int d = 0; d < 3; d++)
+                for (int z = 0; z < nu; z++) {
+                    double v = 0;
+                    for (int s = 0; s < nf; s++) v += et->M3[z * nf + s] * et->nref[3 * s + d] * cf[a * nf + s];
+                    qt[d * nu + z] += v;
+                }
+            for (int z = 0; z < nu; z++)
+                for (int k = 0; k < 3; k++) {
+                    double v = 0;
+                    for (int d = 0; d < 3; d++) v += o->Jinv[9 * e + 3 * d + k] * qt[d * nu + z];
+                    q[(a * 3 + k) * nu + z] = v;
+                }
+        }
+        free(qt);
+    }
+
+    /* 6. gradcoru_fpts: Q^(f) = (I3 (x) M0) Q^(u) */
+#pragma omp parallel for schedule(static)
+    for (int e = 0; e < ne; e++) {
+        const etype_t *et = ET(o, e);
+        int nu = et->nu, nf = et->nf;
+        const double *q = o->Q + 3 * o->uoff[e];
+        double *qf = o->QF + 3 * o->foff[e];
+        for (int ad = 0; ad < 3 * NV; ad++)
+            for (int s = 0; s < nf; s++) {
+                double v = 0;
+                for (int z = 0; z < nu; z++) v += et->M0[s * nu + z] * q[ad * nu + z];
+                qf[ad * nf + s] = v;
+            }
+    }
+
+    /* 7.-10. gradcoru_qpts, uqpts, tdisf, tdivtpcorf (per element, with local work arrays) */
+#pragma omp parallel for schedule(static)
+    for (int e = 0; e < ne; e++) {
+        const etype_t *et = ET(o, e);
+        int nu = et->nu, nq = et->nq, nf = et->nf;
+        const double *u = U + o->uoff[e];
+        const double *q = o->Q + 3 * o->uoff[e];
+        double *qq = (double *)malloc((size_t)3 * NV * nq * sizeof(double));
+        double *uq = (double *)malloc((size_t)NV * nq * sizeof(double));
+        double *fq = (double *)malloc((size_t)3 * NV * nq * sizeof(double));
+        double *fu = (double *)malloc((size_t)3 * NV * nu * sizeof(double));
+        /* 7. gradcoru_qpts: Q^(q) = (I3 (x) M7) Q^(u) */
+        for (int ad = 0; ad < 3 * NV; ad++)
+            for (int s = 0; s < nq; s++) {
+                double v = 0;
+                for (int z = 0; z < nu; z++) v += et->M7[s * nu + z] * q[ad * nu + z];
+                qq[ad * nq + s] = v;
+            }
+        /* 8. uqpts: U^(q) = M7 U^(u) */
+        for (int a = 0; a < NV; a++)
+            for (int s = 0; s < nq; s++) {
+                double v = 0;
+                for (int z = 0; z < nu; z++) v += et->M7[s * nu + z] * u[a * nu + z];
+                uq[a * nq + s] = v;
+            }
+        /* 9. tdisf: F~(q) = detJ J^-1 f(U^(q), Q^(q)), with f = fe - fv */
+        for (int s = 0; s < nq; s++) {
+            double us[NV], qs[NV][3], fe[3][NV], fv[3][NV];
+            for (int a = 0; a < NV; a++) {
+                us[a] = uq[a * nq + s];
+                for (int d = 0; d < 3; d++) qs[a][d] = qq[(a * 3 + d) * nq + s];
+            }
+            flux_inviscid(ph, us, fe, NULL);
+            flux_viscous(ph, us, qs, fv);
+            for (int a = 0; a < NV; a++)
+                for (int d = 0; d < 3; d++) {
+                    double v = 0;
+                    for (int k = 0; k < 3; k++) v += o->Jinv[9 * e + 3 * d + k] * (fe[k][a] - fv[k][a]);
+                    fq[(a * 3 + d) * nq + s] = o->detJ[e] * v;
+                }
+        }
+        /* 10. tdivtpcorf: R~ = (M1 - M3 M2) M9 F~(q), with M9 = I3 (x) M8 */
+        for (int ad = 0; ad < 3 * NV; ad++)
+            for (int z = 0; z < nu; z++) {
+                double v = 0;
+                for (int s = 0; s < nq; s++) v += et->M8[z * nq + s] * fq[ad * nq + s];
+                fu[ad * nu + z] = v;
+            }
+        double *rt = o->Rt + o->uoff[e];
+        for (int a = 0; a < NV; a++)
+            for (int z = 0; z < nu; z++) {
+                double v = 0;
+                for (int d = 0; d < 3; d++)
+                    for (int zz = 0; zz < nu; zz++) v += et->Adiv[(z * 3 + d) * nu + zz] * fu[(a * 3 + d) * nu + zz];
+                rt[a * nu + z] = v;
+            }
+        if (st && st->fu) memcpy(st->fu + 3 * o->uoff[e], fu, (size_t)3 * NV * nu * sizeof(double));
+        (void)nf;
+        free(qq); free(uq); free(fq); free(fu);
+    }
+
+    /* 11. comm_flux: Rusanov (reading R4) + LDG viscous flux (G3), D_L = |n_sL| F, D_R = -|n_sR| F */
+#pragma omp parallel for schedule(static)
+    for (long ip = 0; ip < o->npair; ip++) {
+        long gL = o->pairL[ip], gR = o->pairR[ip];
+        int eL = o->fpt_elem[gL], eR = o->fpt_elem[gR];
+        int sL = (int)(gL - o->fpt_base[eL]), sR = (int)(gR - o->fpt_base[eR]);
+        const etype_t *tL = ET(o, eL), *tR = ET(o, eR);
+        int nfL = tL->nf, nfR = tR->nf;
+        double uL[NV], uR[NV], qL[NV][3], qR[NV][3];
+        for (int a = 0; a < NV; a++) {
+            uL[a] = o->UF[o->foff[eL] + a * nfL + sL];
+            uR[a] = o->UF[o->foff[eR] + a * nfR + sR];
+            for (int d = 0; d < 3; d++) {
+                qL[a][d] = o->QF[3 * o->foff[eL] + (a * 3 + d) * nfL + sL];
+                qR[a][d] = o->QF[3 * o->foff[eR] + (a * 3 + d) * nfR + sR];
+            }
+        }
+        double nsL[3], nsR[3];
+        normal_scaled(o, eL, tL->nref + 3 * sL, nsL);
+        normal_scaled(o, eR, tR->nref + 3 * sR, nsR);
+        double magL = sqrt(nsL[0] * nsL[0] + nsL[1] * nsL[1] + nsL[2] * nsL[2]);
+        double magR = sqrt(nsR[0] * nsR[0] + nsR[1] * nsR[1] + nsR[2] * nsR[2]);
+        double n[3] = {nsL[0] / magL, nsL[1] / magL, nsL[2] / magL};
+        double feL[3][NV], feR[3][NV], fvL[3][NV], fvR[3][NV], pL, pR;
+        flux_inviscid(ph, uL, feL, &pL);
+        flux_inviscid(ph, uR, feR, &pR);
+        flux_viscous(ph, uL, qL, fvL);
+        flux_viscous(ph, uR, qR, fvR);
+        double vnL = (uL[1] * n[0] + uL[2] * n[1] + uL[3] * n[2]) / uL[0];
+        double vnR = (uR[1] * n[0] + uR[2] * n[1] + uR[3] * n[2]) / uR[0];
+        double cL = sqrt(ph->gamma * pL / uL[0]), cR = sqrt(ph->gamma * pR / uR[0]);
+        double sL_ = fabs(vnL) + cL, sR_ = fabs(vnR) + cR;
+        double smax = sL_ > sR_ ? sL_ : sR_;
+        for (int a = 0; a < NV; a++) {
+            double fnL = 0, fnR = 0, fvnL = 0, fvnR = 0;
+            for (int d = 0; d < 3; d++) {
+                fnL += n[d] * feL[d][a]; fnR += n[d] * feR[d][a];
+                fvnL += n[d] * fvL[d][a]; fvnR += n[d] * fvR[d][a];
+            }
+            double Finv = 0.5 * (fnL + fnR) + 0.5 * smax * (uL[a] - uR[a]);
+            double Fvis = (0.5 + ph->beta) * fvnL + (0.5 - ph->beta) * fvnR;
+            double F = Finv - Fvis + ph->tau * (uL[a] - uR[a]);
+            o->DF[o->foff[eL] + a * nfL + sL] = magL * F;
+            o->DF[o->foff[eR] + a * nfR + sR] = -magR * F;
+        }
+    }
+
+    /* 12.-13. tdivtconf (R~ += M3 D) and negdivconf (R = -R~ / detJ) */
+#pragma omp parallel for schedule(static)
+    for (int e = 0; e < ne; e++) {
+        const etype_t *et = ET(o, e);
+        int nu = et->nu, nf = et->nf;
+        const double *df = o->DF + o->foff[e];
+        double *rt = o->Rt + o->uoff[e];
+        double *r = R + o->uoff[e];
+        for (int a = 0; a < NV; a++)
+            for (int z = 0; z < nu; z++) {
+                double v = 0;
+                for (int s = 0; s < nf; s++) v += et->M3[z * nf + s] * df[a * nf + s];
+                rt[a * nu + z] += v;
+                r[a * nu + z] = -rt[a * nu + z] / o->detJ[e];
+            }
+    }
+
+    if (st) {
+        if (st->uf) memcpy(st->uf, o->UF, o->nF * sizeof(double));
+        if (st->cf) memcpy(st->cf, o->CF, o->nF * sizeof(double));
+        if (st->df) memcpy(st->df, o->DF, o->nF * sizeof(double));
+        if (st->qu) memcpy(st->qu, o->Q, 3 * o->nU * sizeof(double));
+        if (st->qf) memcpy(st->qf, o->QF, 3 * o->nF * sizeof(double));
+    }
+    return OR_OK;
+}
+
+int or_rhs(void *h, const double *U, double *R) { return rhs_impl((oracle_t *)h, U, R, NULL); }
+
+int or_rhs_stages(void *h, const double *U, double *R, double *uf, double *cf, double *qu, double *qf,
+                  double *fu, double *df)
+{
+    or_stages st = {uf, cf, qu, qf, fu, df};
+    return rhs_impl((oracle_t *)h, U, R, &st);
+}
+
+/* Classical four-stage RK4 on the semi-discrete system du/dt = R(u). */
+int or_rk4(void *h, double *U, double dt, int nsteps)
+{
+    oracle_t *o = (oracle_t *)h;
+    long n = o->nU;
+    double *k = (double *)malloc(n * sizeof(double)), *us = (double *)malloc(n * sizeof(double));
+    double *acc = (double *)malloc(n * sizeof(double));
+    static const double c[4] = {0.0, 0.5, 0.5, 1.0}, b[4] = {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6};
+    for (int step = 0; step < nsteps; step++) {
+        for (long i = 0; i < n; i++) acc[i] = 0.0;
+        for (int s = 0; s < 4; s++) {
+            if (s == 0) memcpy(us, U, n * sizeof(double));
+            else for (long i = 0; i < n; i++) us[i] = U[i] + c[s] * dt * k[i];
+            rhs_impl(o, us, k, NULL);
+            for (long i = 0; i < n; i++) acc[i] += b[s] * k[i];
+        }
+        for (long i = 0; i < n; i++) U[i] += dt * acc[i];
+    }
+    free(k); free(us); free(acc);
+    return OR_OK;
+}
+
+/* Diagnostics of a state U and its RHS R (R may be NULL):
+ * out[0] = |Omega| = sum W detJ, out[1] = E_k = (1/|Omega|) sum W detJ rho|v|^2/2,
+ * out[2] = eps = -dE_k/dt = -(1/|Omega|) sum W detJ (v.R_rhov - |v|^2/2 R_rho),
+ * out[3..7] = sum W detJ R_alpha, out[8..12] = sum W detJ |R_alpha|. */
+void or_diagnostics(void *h, const double *U, const double *R, double *out)
+{
+    oracle_t *o = (oracle_t *)h;
+    for (int i = 0; i < 13; i++) out[i] = 0.0;
+    for (int e = 0; e < o->ne; e++) {
+        const etype_t *et = ET(o, e);
+        const double *u = U + o->uoff[e];
+        const double *r = R ? R + o->uoff[e] : NULL;
+        for (int z = 0; z < et->nu; z++) {
+            double w = et->Wu[z] * o->detJ[e];
+            double rho = u[z], v[3] = {u[et->nu + z] / rho, u[2 * et->nu + z] / rho, u[3 * et->nu + z] / rho};
+            double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+            out[0] += w;
+            out[1] += w * 0.5 * rho * v2;
+            if (r) {
+                double dke = v[0] * r[et->nu + z] + v[1] * r[2 * et->nu + z] + v[2] * r[3 * et->nu + z] - 0.5 * v2 * r[z];
+                out[2] -= w * dke;
+                for (int a = 0; a < NV; a++) { out[3 + a] += w * r[a * et->nu + z]; out[8 + a] += w * fabs(r[a * et->nu + z]); }
+            }
+        }
+    }
+    out[1] /= out[0];
+    out[2] /= out[0];
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Operator export for pins
+ * ------------------------------------------------------------------------------------------- */
+
+/* dims[0..3] = nu, nf, nq, nfaces for element type t; returns -1 if absent. */
+int or_etype_dims(void *h, int t, int *dims)
+{
+    oracle_t *o = (oracle_t *)h;
+    if (t < 0 || t > 1 || !o->has[t]) return -1;
+    const etype_t *et = &o->et[t];
+    dims[0] = et->nu; dims[1] = et->nf; dims[2] = et->nq; dims[3] = et->nfaces;
+    return 0;
+}
+
+/* which: 0 xu[nu][3], 1 xf[nf][3], 2 nref[nf][3], 3 xq[nq][3], 4 wq[nq], 5 M0[nf][nu],
+ * 6 D[3][nu][nu], 7 M3 lift[nu][nf], 8 M7[nq][nu], 9 M8[nu][nq], 10 Wu[nu],
+ * 11 Agrad[3][nu][nu], 12 Adiv[nu][3][nu], 13 fpt_face[nf] (as doubles) */
+int or_get_operator(void *h, int t, int which, double *out)
+{
+    oracle_t *o = (oracle_t *)h;
+    if (t < 0 || t > 1 || !o->has[t]) return -1;
+    const etype_t *et = &o->et[t];
+    int nu = et->nu, nf = et->nf, nq = et->nq;
+    switch (which) {
+    case 0: memcpy(out, et->xu, 3 * nu * sizeof(double)); break;
+    case 1: memcpy(out, et->xf, 3 * nf * sizeof(double)); break;
+    case 2: memcpy(out, et->nref, 3 * nf * sizeof(double)); break;
+    case 3: memcpy(out, et->xq, 3 * nq * sizeof(double)); break;
+    case 4: memcpy(out, et->wq, nq * sizeof(double)); break;
+    case 5: memcpy(out, et->M0, (size_t)nf * nu * sizeof(double)); break;
+    case 6: memcpy(out, et->Dm, (size_t)3 * nu * nu * sizeof(double)); break;
+    case 7: memcpy(out, et->M3, (size_t)nu * nf * sizeof(double)); break;
+    case 8: memcpy(out, et->M7, (size_t)nq * nu * sizeof(double)); break;
+    case 9: memcpy(out, et->M8, (size_t)nu * nq * sizeof(double)); break;
+    case 10: memcpy(out, et->Wu, nu * sizeof(double)); break;
+    case 11: memcpy(out, et->Agrad, (size_t)3 * nu * nu * sizeof(double)); break;
+    case 12: memcpy(out, et->Adiv, (size_t)3 * nu * nu * sizeof(double)); break;
+    case 13: for (int s = 0; s < nf; s++) out[s] = et->fpt_face[s]; break;
+    default: return -1;
+    }
+    return 0;
+}
+
+/* Element geometry export: J[9], Jinv[9], detJ for element e. */
+int or_element_geometry(void *h, int e, double *J, double *Jinv, double *detJ)
+{
+    oracle_t *o = (oracle_t *)h;
+    if (e < 0 || e >= o->ne) return -1;
+    memcpy(J, o->J + 9 * e, 9 * sizeof(double));
+    memcpy(Jinv, o->Jinv + 9 * e, 9 * sizeof(double));
+    *detJ = o->detJ[e];
+    return 0;
+}
+
+/* Orthonormal triangle basis values at (x,y), for pins (nt = (p+1)(p+2)/2 values). */
+int or_tri_basis_values(int p, int npts, const double *xy, double *out)
+{
+    tri_basis tb;
+    tri_basis_init(&tb, p);
+    for (int i = 0; i < npts; i++) tri_basis_eval(&tb, xy[2 * i], xy[2 * i + 1], out + (size_t)i * tb.nt, NULL, NULL);
+    tri_basis_free(&tb);
+    return 0;
+}
