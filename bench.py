@@ -1,0 +1,333 @@
+"""Benchmark: anti-aliased Navier-Stokes FR right-hand-side throughput on the Taylor-Green vortex.
+
+Workload (default): 48^3 periodic hex box, p = 3 (4^3 Gauss-Legendre solution points), flux
+anti-aliasing on 5^3 Gauss-Legendre quadrature points, FP64, Re = 1600, M = 0.1, Pr = 0.71,
+Rusanov + LDG (beta = 0.5, tau = 0.1) interface fluxes, synthetic TGV state with a 1e-3 SplitMix64
+perturbation. One step = one classical RK4 step = 4 RHS evaluations + 4 stage updates (every step
+of the hot path). Metric: GDOF.RHS/s = DOF x RHS evaluations / s, DOF = elements x points x 5.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NS-FR RHS GDOF/s (anti-aliased TGV), % HBM roofline, fused vs unfused"
+UNIT = "GDOF*RHS/s"
+N_EDGE, P, MQ = 48, 3, 5
+DT = 2e-4
+RHS_PER_STEP = 4
+
+
+def workload_name(n=N_EDGE, p=P, m=MQ):
+    return f"TGV {n}^3 hex p={p} ({p + 1}^3 GL solution pts), {m}^3 GL flux anti-aliasing, RK4 step = 4 RHS"
+
+
+# ---------------------------------------------------------------------------------------------
+# FLOP model of the fused volume kernel (phase B), FMA = 2 FLOP; counted from its arithmetic
+# ---------------------------------------------------------------------------------------------
+VISC_NORMAL_FLOPS = 130   # viscous normal flux at one face point (velocity gradients, stress, heat, n.)
+POINT_FLUX_FLOPS = 150    # total flux f^e - f^v at one quadrature point
+TRANSFORM_FLOPS = 90      # detJ J^-1 f: 15 outputs x (3 FMA)
+
+
+def phase_b_flops_per_element(p=P, m=MQ):
+    n = p + 1
+    nu, nf, nq = n ** 3, 6 * n * n, m ** 3
+    con_u = 5 * nf * 3
+    grad = 15 * n * n * n * (2 * n + 3)
+    jt = 5 * nu * 3 * 5
+    face = nf * (20 * 2 * n + VISC_NORMAL_FLOPS)
+    interp = 20 * 2 * (n ** 3 * m + n * n * m * m + n * m ** 3)
+    tdisf = nq * (POINT_FLUX_FLOPS + TRANSFORM_FLOPS)
+    proj = 15 * 2 * (m ** 3 * n + m * m * n * n + m * n ** 3)
+    div = 5 * nu * 3 * n * 2
+    return con_u + grad + jt + face + interp + tdisf + proj + div
+
+
+# ---------------------------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded sample of the same workload
+# ---------------------------------------------------------------------------------------------
+def oracle_sample(seconds=12.0, n_edge=16, threads=None):
+    """Oracle RHS evaluations on an n_edge^3 box with the same order, quadrature and physics as the
+    workload (same per-element work), repeated for about `seconds`."""
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2401_06132_gb300 import workloads as W
+    threads = threads or os.cpu_count() or 1
+    mesh = W.box_hex_mesh(n_edge)
+    o = O.Oracle(mesh, P, MQ, threads=threads)
+    U = W.tgv_state(o.sol_coords(), [(n_edge ** 3, (P + 1) ** 3)], perturb=1e-3)
+    o.rhs(U)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        o.rhs(U)
+        reps += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return dict(value=U.size * reps / dt / 1e9, unit=UNIT, cores=threads, kind="oracle",
+                sample=f"{reps} oracle RHS evaluations on the {n_edge}^3 box (same p, quadrature, physics; "
+                       f"{np.prod(U.shape)} DOF each), {dt:.1f} s, OpenMP over elements"), U.size
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2401_06132_gb300 import workloads as W
+    threads = os.cpu_count() or 1
+    n_edge = 12
+    mesh = W.box_hex_mesh(n_edge)
+    o = O.Oracle(mesh, P, MQ, threads=threads)
+    U = W.tgv_state(o.sol_coords(), [(n_edge ** 3, (P + 1) ** 3)], perturb=1e-3)
+    for _ in range(args.warmup):
+        U = o.rk4(U, DT, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U = o.rk4(U, DT, 1)
+    dt = time.perf_counter() - t0
+    value = U.size * RHS_PER_STEP * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(), "sample": f"oracle on the {n_edge}^3 box, same per-element work"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{args.steps} oracle RK4 steps on the {n_edge}^3 box ({U.size} DOF)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------------
+def time_rk4(m, U, steps, warmup, torch):
+    for _ in range(warmup):
+        m.rk4_step(U, DT, 1)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        m.rk4_step(U, DT, 1)
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_2401_06132_gb300 import build as B
+    from paper_2401_06132_gb300 import fr, workloads as W
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    mesh = W.box_hex_mesh(N_EDGE)
+    prm = fr.make_params(p=P, prec="fp64")
+    m = fr.FRMesh(mesh, prm)
+    info = m.info()
+    xyz = m.sol_coords()
+    U0 = W.tgv_state(xyz, [(N_EDGE ** 3, (P + 1) ** 3)], perturb=1e-3)
+    dof = U0.size
+    U = torch.from_numpy(U0).cuda()
+
+    # --- headline: FP64 fused, RK4 steps, timed with events, barrier + max over ranks -----------
+    for _ in range(args.warmup):
+        m.rk4_step(U, DT, 1)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    m.set_timing(True)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(s)
+        for _ in range(args.steps):
+            m.rk4_step(U, DT, 1)
+        e1.record(s)
+        torch.cuda.synchronize()
+    m.set_timing(False)
+    ms_step = e0.elapsed_time(e1) / args.steps
+    kt = m.kernel_times()
+    m.sync_status()
+    if world > 1:
+        t = torch.tensor([ms_step], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+        torch.distributed.barrier()
+    value = dof * RHS_PER_STEP * world / (ms_step * 1e-3) / 1e9
+    launches_per_step = RHS_PER_STEP * (info["launches_per_rhs"] + 1)
+
+    if rank != 0:
+        return
+
+    # --- dominant kernel and its roofline ----------------------------------------------------
+    names = {0: "fused A (disu)", 1: "fused B (volume group)", 2: "fused C (interface group)", 30: "RK4 update"}
+    share = {names.get(k, str(k)): v[0] / max(1e-9, sum(x[0] for x in kt.values())) for k, v in kt.items()}
+    b_ms, b_n = kt.get(1, (0.0, 1))
+    b_avg = b_ms / max(1, b_n)
+    flops_b = phase_b_flops_per_element() * info["elements"]
+    probe = fr.probe_fma()
+    peak_fp64 = probe["fp64_gflops"] / 1e3
+    achieved = flops_b / (b_avg * 1e-3) / 1e12
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else open(os.devnull) as f:
+        try:
+            peaks = json.load(f)
+        except Exception:
+            peaks = {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    compulsory = 2 * dof * 8  # U read + R written per RHS, FP64
+    rhs_ms = ms_step / RHS_PER_STEP
+    hbm_frac = compulsory / (rhs_ms * 1e-3) / 1e9 / hbm_peak
+
+    # --- other forms (same workload): FP64 unfused, FP32 fused / unfused ---------------------
+    forms = {"fused_fp64": value / world}
+    ksteps = max(2, min(args.steps, 5))
+    m.set_form("unfused")
+    forms["unfused_fp64"] = dof * RHS_PER_STEP / (time_rk4(m, U, ksteps, 1, torch) * 1e-3) / 1e9
+    m.set_form("fused")
+    m.close()
+    del m
+    torch.cuda.empty_cache()
+    m32 = fr.FRMesh(mesh, fr.make_params(p=P, prec="fp32"))
+    U = torch.from_numpy(U0).cuda()
+    forms["fused_fp32"] = dof * RHS_PER_STEP / (time_rk4(m32, U, ksteps, 2, torch) * 1e-3) / 1e9
+    m32.set_form("unfused")
+    forms["unfused_fp32"] = dof * RHS_PER_STEP / (time_rk4(m32, U, ksteps, 1, torch) * 1e-3) / 1e9
+    m32.close()
+    del m32
+    torch.cuda.empty_cache()
+
+    # --- end to end through the host-buffer entry point (copies inside the timed region) ------
+    m = fr.FRMesh(mesh, prm)
+    Uh = torch.from_numpy(U0.copy()).pin_memory().numpy()
+    m.rk4_step_host(Uh, DT, 1)
+    t0 = time.perf_counter()
+    ke = max(2, min(args.steps, 5))
+    for _ in range(ke):
+        m.rk4_step_host(Uh, DT, 1)
+    e2e_s = (time.perf_counter() - t0) / ke
+    e2e_value = dof * RHS_PER_STEP / e2e_s / 1e9
+    m.close()
+
+    cpu, _ = oracle_sample(seconds=args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(), "elements": info["elements"], "dof": dof, "rhs_per_step": RHS_PER_STEP,
+                   "form": "fused", "l2": "inputs larger than L2 (283 MB FP64 state, 129 MB L2)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"kernel": "fused B (volume group)", "bound": "alu", "achieved": achieved, "peak": peak_fp64,
+                     "unit": "TFLOP/s", "frac": achieved / peak_fp64, "traffic": None,
+                     "peak_source": "FP64 FMA probe (fr_probe_fma), measured in this run",
+                     "flops_per_launch": flops_b, "avg_launch_ms": b_avg},
+        "hbm_roofline": {"compulsory_bytes_per_rhs": compulsory, "peak_gbs": hbm_peak,
+                         "frac": hbm_frac, "note": "compulsory bytes (U read + R written) / RHS time / measured copy peak"},
+        "forms_gdof_rhs_per_s": forms,
+        "kernel_share": share,
+        "probe": probe,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": dof * 8, "d2h_bytes_per_step": dof * 8},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group(backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

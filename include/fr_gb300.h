@@ -1,0 +1,182 @@
+/*
+ * fr_gb300.h -- C ABI of the GB300 (sm_103a) flux-reconstruction library.
+ *
+ * The library evaluates the right-hand side (RHS) R(u) of the semi-discrete system du/dt = R(u)
+ * obtained by flux reconstruction (FR) of the compressible Navier-Stokes equations with flux
+ * anti-aliasing, on affine hexahedral and prismatic meshes, and advances it with classical RK4.
+ * Paper: Akkurt, Witherden, Vincent, "Cache blocking for flux reconstruction: extension to
+ * Navier-Stokes equations and anti-aliasing".
+ *   - governing equations, fluxes and the perfect-gas closure: Sec. 2.1 (Eqs. gov, fluxe, fluxv);
+ *   - the FR steps (disu, con_u, corrected gradient, tdisf, common fluxes, corrected divergence):
+ *     Sec. 2.1 Eqs. FR-disu .. FRfinal, and their kernel form in Sec. 2.2;
+ *   - flux anti-aliasing (interpolation to quadrature points, L2 projection): Sec. 2.1.1 and
+ *     Sec. 2.2.1 (operators M7..M10); sum factorisation of the hex and prism operators: Sec. 4;
+ *   - the semi-discrete form du/dt = -J^-1 div~ f~: Eq. govqtrans; RK4: Sec. 3.
+ *
+ * Conventions shared by every entry point
+ *   - Status: every call returns an fr_status; FR_OK is 0. Argument and mesh errors are reported
+ *     synchronously and leave the handle unchanged. Device-side conditions (a non-physical state:
+ *     rho <= 0, p <= 0 or a non-finite value met while evaluating fluxes) are latched in a device
+ *     status word and reported as FR_ENONPHYS by fr_sync_status() or by the next call on the
+ *     handle once the earlier work has completed. No call aborts, traps or exits.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     RHS and RK4 calls are asynchronous with respect to the host. A handle may be used by one
+ *     stream at a time.
+ *   - Ownership: the library copies the host mesh descriptors and owns every device buffer it
+ *     allocates (geometry, operators, connectivity, face arrays, RK4 registers). The caller owns
+ *     the state U and the result R: device pointers (or host pointers for the *_host variants).
+ *   - Layout of U and R (reading R10 of the design notes): element-major [elem][var][pt], with
+ *     var in (rho, rho vx, rho vy, rho vz, E). Elements are ordered instance by instance; inside an
+ *     instance hexahedra come first, then prisms, each in descriptor order. Hex point index is
+ *     i + n j + n^2 k (n = p+1 Gauss-Legendre points per direction, i fastest along xi); prism
+ *     point index is t + 10 k (t = triangle point in the paper's printed Williams-Shunn order,
+ *     k = Gauss-Legendre level in z).
+ *   - Element type of U/R: double for FR_FP64; float for FR_FP32 and the mixed forms. The RK4
+ *     entry points always take an FP64 master state (double), whatever the compute precision.
+ *   - Vertex order: hexahedra in tensor order (corner a + 2b + 4c for (a,b,c) in {0,1}^3);
+ *     prisms v0,v1,v2 at the lower triangle mapped to the reference (-1,-1),(1,-1),(-1,1) and
+ *     v3,v4,v5 above them. Elements must be affine (parallelepipeds / straight prisms); other
+ *     elements give FR_EUNSUPPORTED.
+ *   - Local face order (used by the L/R rule): hex -xi, +xi, -eta, +eta, -zeta, +zeta; prism
+ *     z=-1 triangle, z=+1 triangle, y=-1 quad, x+y=0 quad, x=-1 quad.
+ */
+#ifndef FR_GB300_H
+#define FR_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FR_OK = 0,
+    FR_EINVAL = 1,        /* bad argument */
+    FR_ENOMEM = 2,        /* device or host allocation failed */
+    FR_ECUDA = 3,         /* a CUDA runtime call failed (text in fr_last_error()) */
+    FR_EMESH = 4,         /* non-conforming mesh: unmatched face or flux point, inverted element */
+    FR_ETIMEOUT = 5,      /* a bounded device wait gave up */
+    FR_ENONPHYS = 6,      /* non-physical state met on the device */
+    FR_EUNSUPPORTED = 7   /* valid request outside what this build implements */
+} fr_status;
+
+typedef enum {
+    FR_FP64 = 0,          /* all arithmetic in FP64 */
+    FR_FP32 = 1,          /* FP32 state, operators and fluxes */
+    FR_MIXED_BF16 = 2,    /* FP32 state; prism triangle contractions as split bf16 hi+lo products */
+    FR_MIXED_FP16 = 3     /* as FR_MIXED_BF16 with fp16 splits */
+} fr_precision;
+
+typedef enum {
+    FR_FUSED = 0,         /* three launches per RHS: face solution, volume group, interface group */
+    FR_UNFUSED = 1        /* one kernel per paper kernel (13 launches per RHS), global intermediates */
+} fr_form;
+
+/* Physical and discretisation parameters of one instance. */
+typedef struct {
+    double gamma;         /* ratio of specific heats */
+    double Pr;            /* Prandtl number */
+    double mu;            /* dynamic viscosity (constant) */
+    double beta;          /* LDG switch (Sec. 2.1 common solution and viscous flux) */
+    double tau;           /* LDG penalty */
+    int p;                /* solution order; hex p in {2,3,4}, prism p = 3 */
+    int nq1d;             /* Gauss-Legendre quadrature points per line (0 = p + 2) */
+    int tri_strength;     /* prism triangle quadrature strength (0 = 8); collapsed k x k rule, k = strength/2 + 1 */
+    int prec;             /* fr_precision */
+    int rusanov_mode;     /* 0: wave speed max(|vL.n|+cL, |vR.n|+cR) (the only mode implemented) */
+} fr_params;
+
+/* Host description of one mesh instance (copied by fr_mesh_create). */
+typedef struct {
+    int n_hex;            /* number of hexahedra */
+    int n_pri;            /* number of prisms */
+    int n_verts;          /* number of vertices */
+    const double *verts;  /* [n_verts][3] coordinates */
+    const int *hex_v;     /* [n_hex][8] vertex ids, tensor order */
+    const int *pri_v;     /* [n_pri][6] vertex ids */
+    double period[3];     /* periodic box lengths; 0 = not periodic. Faces are matched modulo period */
+} fr_mesh_desc;
+
+typedef struct fr_mesh fr_mesh;
+
+/* Builds the operators, metrics and interface pairs of n_inst independent instances (one
+ * fr_params each) and uploads them to the current CUDA device. Interfaces are found by matching
+ * flux-point coordinates (modulo the periods); every face must find exactly one partner. The L side
+ * of a pair is the element with the smaller global index; a self-pair takes the smaller local face
+ * number as L. Returns FR_EMESH, FR_EUNSUPPORTED, FR_EINVAL or FR_ENOMEM on failure (*out = NULL). */
+fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst, const fr_params *prm, fr_mesh **out);
+
+/* Frees every device and host resource of the handle. NULL is accepted. */
+fr_status fr_destroy(fr_mesh *m);
+
+/* Selects the kernel form used by later RHS and RK4 calls (fr_form). */
+fr_status fr_set_form(fr_mesh *m, int form);
+
+/* R = R(U): one RHS evaluation. U_dev and R_dev are device arrays of fr_num_values() elements in
+ * the boundary layout and precision (double for FR_FP64, float otherwise); they must not overlap. */
+fr_status fr_rhs(fr_mesh *m, const void *U_dev, void *R_dev, void *stream);
+
+/* Same as fr_rhs with host arrays: copies U host->device, evaluates, copies R device->host and
+ * synchronises the stream before returning. Host buffers may be pageable or pinned. */
+fr_status fr_rhs_host(fr_mesh *m, const void *U_host, void *R_host, void *stream);
+
+/* nsteps classical RK4 steps of size dt, in place, on the FP64 master state U_dev (double, device,
+ * boundary layout). Stage states are formed in the compute precision; stage accumulation stays FP64. */
+fr_status fr_rk4_step(fr_mesh *m, void *U_dev, double dt, int nsteps, void *stream);
+
+/* As fr_rk4_step on a host FP64 state: copies U host->device, advances nsteps, copies it back and
+ * synchronises the stream. */
+fr_status fr_rk4_step_host(fr_mesh *m, void *U_host, double dt, int nsteps, void *stream);
+
+/* Blocks until the stream's work on this handle has finished and returns the latched device
+ * status (FR_OK or FR_ENONPHYS), clearing it. */
+fr_status fr_sync_status(fr_mesh *m, void *stream);
+
+/* Counts: info[0] elements, info[1] values of U (= DOF), info[2] flux points, info[3] interface
+ * pairs, info[4] instances, info[5] kernel launches per RHS in the current form,
+ * info[6] bytes of device memory owned by the handle. */
+fr_status fr_mesh_info(const fr_mesh *m, long long *info);
+
+/* Number of values of U (elements x 5 x points, summed over instances and element types). */
+long long fr_num_values(const fr_mesh *m);
+
+/* Physical coordinates of every solution point, [point in boundary order][3], into a host array
+ * of fr_num_values()/5*3 doubles. */
+fr_status fr_sol_coords(const fr_mesh *m, double *xyz_host);
+
+/* Per-instance value offsets: off[i] is the first value of instance i in U, off[n_inst] the total. */
+fr_status fr_instance_offsets(const fr_mesh *m, long long *off);
+
+/* Diagnostics of a device state U (and RHS R, may be NULL), per instance i, into the host array
+ * out[i*8 + k]: k=0 volume sum W detJ, 1 E_k = <rho|v|^2/2>, 2 eps = -dE_k/dt from R, 3..7 the
+ * quadrature-weighted sums of R per variable. W are the solution-point quadrature weights.
+ * Synchronises the stream. */
+fr_status fr_diagnostics(fr_mesh *m, const void *U_dev, const void *R_dev, double *out, void *stream);
+
+/* Copies an intermediate array of the last UNFUSED RHS to a host FP64 array, for stage-level
+ * checks. which: 0 U^(f) [var][fpt], 1 C^(f) [var][fpt], 2 physical gradient Q^(u)
+ * [elem][var][dim][pt], 3 Q^(f) [var][dim][fpt], 4 projected flux F~^(u) [elem][var][dim][pt],
+ * 5 D^(f) [var][fpt]. Flux points use the global order elem-major, local face order above.
+ * n_host is the capacity in doubles; the needed size is returned in *n_needed. Synchronises. */
+fr_status fr_stage(fr_mesh *m, int which, double *host, long long n_host, long long *n_needed);
+
+/* Debug flags: bit 0 keeps a copy of the unfused form's physical gradient Q^(u) for fr_stage(2). */
+fr_status fr_set_debug(fr_mesh *m, int flags);
+
+/* Per-kernel timing (on = 1): CUDA events are recorded on the launching stream around every later
+ * launch. fr_kernel_times waits for them and returns, per kernel id, the summed milliseconds and the
+ * launch count, then clears the record. Ids: 0, 1, 2 fused phases (face solution, volume group,
+ * interface group); 10 + k unfused kernel k = 1..13 in the paper's order; 30 RK4 stage update.
+ * Arrays have n_ids entries. */
+fr_status fr_set_timing(fr_mesh *m, int on);
+fr_status fr_kernel_times(fr_mesh *m, double *ms, long long *count, int n_ids);
+
+/* Text of the last error on the calling thread ("" if none). */
+const char *fr_last_error(void);
+
+/* Measures the device's sustained FMA throughput: out[0] FP64 GFLOP/s, out[1] FP32 GFLOP/s
+ * (CUDA-core FMA chains over every SM, timed with events). Synchronises. */
+fr_status fr_probe_fma(double *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FR_GB300_H */

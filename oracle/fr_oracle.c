@@ -652,6 +652,24 @@ static void inv3(const double *a, double *b, double *det)
 
 void or_destroy(void *h);
 
+typedef struct { long long k[3]; int face; } or_facekey;
+
+static int facekey_cmp_keys(const or_facekey *a, const or_facekey *b)
+{
+    for (int d = 0; d < 3; d++) {
+        if (a->k[d] < b->k[d]) return -1;
+        if (a->k[d] > b->k[d]) return 1;
+    }
+    return 0;
+}
+
+static int facekey_cmp(const void *a, const void *b)
+{
+    int c = facekey_cmp_keys((const or_facekey *)a, (const or_facekey *)b);
+    if (c) return c;
+    return ((const or_facekey *)a)->face - ((const or_facekey *)b)->face;
+}
+
 void *or_create(int p, int m, int tri_k, double gamma, double Pr, double mu, double beta, double tau,
                 int n_hex, int n_pri, int n_verts, const double *verts, const int *hex_v, const int *pri_v,
                 const double *period, int *err)
@@ -716,7 +734,7 @@ void *or_create(int p, int m, int tri_k, double gamma, double Pr, double mu, dou
     for (int e = 0; e < ne; e++)
         for (int s = 0; s < ET(o, e)->nf; s++) o->fpt_elem[o->fpt_base[e] + s] = e;
 
-    /* Interface pairing by physical coordinates (brute force over faces, then over points). */
+    /* Interface pairing by physical coordinates (bucketed faces, then brute force over points). */
     int nfaces_tot = 0;
     for (int e = 0; e < ne; e++) nfaces_tot += ET(o, e)->nfaces;
     int *fe = (int *)malloc(nfaces_tot * sizeof(int)), *ff = (int *)malloc(nfaces_tot * sizeof(int));
@@ -731,39 +749,68 @@ void *or_create(int p, int m, int tri_k, double gamma, double Pr, double mu, dou
             int s0 = 0;
             for (int f = 0; f < et->nfaces; f++) {
                 fe[k] = e; ff[k] = f; fs0[k] = s0; mate[k] = -1;
-                /* reference face centroid: mean of the face points is not needed; use first point
-                 * coordinates of every point to build a centroid */
-                double c[3] = {0, 0, 0};
-                double first[3];
-                for (int j = 0; j < et->faces[f].npts; j++) {
-                    double x[3];
-                    phys_coord(o, e, et->xf + 3 * (s0 + j), x);
-                    if (j == 0) memcpy(first, x, sizeof(first));
-                    /* unwrap against the first point so the centroid is meaningful across a period */
-                    for (int d = 0; d < 3; d++) {
-                        double dx = x[d] - first[d];
-                        if (o->period[d] > 0) dx -= o->period[d] * floor(dx / o->period[d] + 0.5);
-                        c[d] += first[d] + dx;
-                    }
-                }
-                for (int d = 0; d < 3; d++) fc[3 * k + d] = c[d] / et->faces[f].npts;
+                /* the physical face centroid is the affine image of the reference face centre */
+                double Xc[3], c[3];
+                if (et->type == ET_HEX) { Xc[0] = Xc[1] = Xc[2] = 0.0; Xc[f / 2] = (f % 2) ? 1.0 : -1.0; }
+                else if (f < 2) { Xc[0] = Xc[1] = -1.0 / 3.0; Xc[2] = f ? 1.0 : -1.0; }
+                else if (f == 2) { Xc[0] = 0.0; Xc[1] = -1.0; Xc[2] = 0.0; }
+                else if (f == 3) { Xc[0] = 0.0; Xc[1] = 0.0; Xc[2] = 0.0; }
+                else { Xc[0] = -1.0; Xc[1] = 0.0; Xc[2] = 0.0; }
+                phys_coord(o, e, Xc, c);
+                for (int d = 0; d < 3; d++) fc[3 * k + d] = c[d];
                 fsize[k] = pow(fabs(o->detJ[e]), 1.0 / 3.0);
                 s0 += et->faces[f].npts;
                 k++;
             }
         }
     }
-    for (int a = 0; a < nfaces_tot; a++) {
-        if (mate[a] >= 0) continue;
-        for (int b = a + 1; b < nfaces_tot; b++) {
-            if (mate[b] >= 0) continue;
-            if (pdist(o, fc + 3 * a, fc + 3 * b) < 1e-8 * fsize[a]) { mate[a] = b; mate[b] = a; break; }
+    /* Face matching: faces are bucketed by the cell (size a quarter of the smallest element) of
+     * their centroid, wrapped into the periodic box; the bucket list is sorted and every face looks
+     * for an unmatched partner in its own and the 26 neighbouring cells (binary search). */
+    {
+        double hmin = 1e300;
+        for (int a = 0; a < nfaces_tot; a++) if (fsize[a] < hmin) hmin = fsize[a];
+        double cell = 0.25 * hmin;
+        long long ncell[3];
+        for (int d = 0; d < 3; d++) ncell[d] = o->period[d] > 0 ? (long long)ceil(o->period[d] / cell) : 0;
+        or_facekey *keys = (or_facekey *)malloc(nfaces_tot * sizeof(or_facekey));
+        for (int a = 0; a < nfaces_tot; a++) {
+            for (int d = 0; d < 3; d++) {
+                double x = fc[3 * a + d];
+                if (o->period[d] > 0) x -= o->period[d] * floor(x / o->period[d]);
+                long long q = (long long)floor(x / cell);
+                if (ncell[d] > 0) q = ((q % ncell[d]) + ncell[d]) % ncell[d];
+                keys[a].k[d] = q;
+            }
+            keys[a].face = a;
         }
-        if (mate[a] < 0) {
-            /* a face may pair with itself only if the mesh has a period of one element; that
-             * cannot happen for a single face, so an unmatched face is a mesh error */
-            *err = OR_EMESH; free(fe); free(ff); free(fs0); free(fc); free(fsize); free(mate); or_destroy(o); return NULL;
+        qsort(keys, nfaces_tot, sizeof(or_facekey), facekey_cmp);
+        for (int a = 0; a < nfaces_tot && !*err; a++) {
+            int fa = keys[a].face;
+            if (mate[fa] >= 0) continue;
+            for (int nb = 0; nb < 27 && mate[fa] < 0; nb++) {
+                or_facekey probe;
+                for (int d = 0; d < 3; d++) {
+                    long long q = keys[a].k[d] + (nb / (d == 0 ? 1 : d == 1 ? 3 : 9)) % 3 - 1;
+                    if (ncell[d] > 0) q = ((q % ncell[d]) + ncell[d]) % ncell[d];
+                    probe.k[d] = q;
+                }
+                /* first entry with key >= probe */
+                int lo = 0, hi = nfaces_tot;
+                while (lo < hi) {
+                    int mid = (lo + hi) / 2;
+                    if (facekey_cmp_keys(&keys[mid], &probe) < 0) lo = mid + 1; else hi = mid;
+                }
+                for (int b = lo; b < nfaces_tot && facekey_cmp_keys(&keys[b], &probe) == 0; b++) {
+                    int fb = keys[b].face;
+                    if (fb == fa || mate[fb] >= 0) continue;
+                    if (pdist(o, fc + 3 * fa, fc + 3 * fb) < 1e-8 * fsize[fa]) { mate[fa] = fb; mate[fb] = fa; break; }
+                }
+            }
+            if (mate[fa] < 0) *err = OR_EMESH;
         }
+        free(keys);
+        if (*err) { free(fe); free(ff); free(fs0); free(fc); free(fsize); free(mate); or_destroy(o); return NULL; }
     }
     o->npair = o->nfpt / 2;
     o->pairL = (long *)malloc(o->npair * sizeof(long));

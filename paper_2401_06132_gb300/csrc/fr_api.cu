@@ -1,0 +1,846 @@
+// fr_api.cu -- mesh set-up and the C ABI of the GB300 flux-reconstruction library.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "fr_internal.h"
+
+// ---------------------------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static fr_status fail(fr_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CU(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t _e = (call);                                                               \
+        if (_e != cudaSuccess) return fail(FR_ECUDA, "%s: %s", #call, cudaGetErrorString(_e)); \
+    } while (0)
+
+extern "C" const char *fr_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------------------------
+// Handle
+// ---------------------------------------------------------------------------------------------
+struct InstanceHost {
+    fr_params prm;
+    int n_hex, n_pri;
+    std::vector<double> x0J;   // per element: x0[3], J[9] (row-major dx_i/dxi_j); x = x0 + J (xi + 1)
+};
+
+struct fr_mesh {
+    int dev = 0;
+    int prec = FR_FP64;
+    int form = FR_FUSED;
+    std::vector<InstanceHost> inst;
+    std::vector<Block> blocks;
+    std::vector<long long> inst_u0;      // value offsets per instance (+ total)
+    long long ne = 0, nU = 0, nfpt = 0, npair = 0;
+    std::vector<frb::Hex1D> hex1d;       // per block (hex)
+    std::vector<double> geo_host;        // per element Ji[9], det (FP64)
+    // device
+    void *d_geo = nullptr;               // Geo<T>[ne]
+    uint32_t *d_partner = nullptr;
+    void *d_UF = nullptr, *d_FV = nullptr;
+    void *d_CF = nullptr, *d_QF = nullptr, *d_DF = nullptr, *d_Qu = nullptr, *d_UQ = nullptr, *d_QQ = nullptr, *d_Rt = nullptr;
+    void *d_rk_k = nullptr, *d_rk_us = nullptr;
+    double *d_rk_acc = nullptr;
+    void *d_io_U = nullptr, *d_io_R = nullptr;     // staging for the host-buffer variants
+    void *d_Qsnap = nullptr;                       // debug: gradient snapshot of the unfused form
+    int debug = 0;
+    double *d_wsum = nullptr;                      // diagnostics accumulators
+    double *d_wts = nullptr;                       // [elem] -> W per point handled in-kernel
+    int *d_status = nullptr;
+    int *h_status = nullptr;                       // pinned
+    cudaEvent_t ev_status = nullptr;
+    bool status_pending = false;
+    long long bytes = 0;
+    // optional per-kernel timing: events recorded around each launch on the launching stream
+    bool timing = false;
+    struct Timed { int kernel; cudaEvent_t a, b; };
+    std::vector<Timed> timed;
+    std::vector<cudaEvent_t> ev_pool;
+};
+
+// Kernel ids for timing: 0..2 fused phases A, B, C; 10+k unfused kernel k (1..13); 30 RK4 update.
+static cudaEvent_t pool_event(fr_mesh *m)
+{
+    if (!m->ev_pool.empty()) { cudaEvent_t e = m->ev_pool.back(); m->ev_pool.pop_back(); return e; }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct TimeScope {
+    fr_mesh *m; int kernel; cudaStream_t s; cudaEvent_t a = nullptr;
+    TimeScope(fr_mesh *m_, int k, cudaStream_t s_) : m(m_), kernel(k), s(s_)
+    {
+        if (m->timing) { a = pool_event(m); cudaEventRecord(a, s); }
+    }
+    ~TimeScope()
+    {
+        if (a) {
+            cudaEvent_t b = pool_event(m);
+            cudaEventRecord(b, s);
+            m->timed.push_back({kernel, a, b});
+        }
+    }
+};
+
+static size_t tsize(int prec) { return prec == FR_FP64 ? sizeof(double) : sizeof(float); }
+
+static fr_status dalloc(fr_mesh *m, void **p, size_t bytes)
+{
+    if (*p) return FR_OK;
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) { *p = nullptr; return fail(FR_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e)); }
+    m->bytes += (long long)bytes;
+    return FR_OK;
+}
+
+static void dfree(void *&p) { if (p) { cudaFree(p); p = nullptr; } }
+
+// ---------------------------------------------------------------------------------------------
+// Reference elements (hexahedra)
+// ---------------------------------------------------------------------------------------------
+static void hex_ref_fpts(const frb::Hex1D &h, std::vector<double> &xf)
+{
+    int n = h.n;
+    xf.assign((size_t)6 * n * n * 3, 0.0);
+    for (int f = 0; f < 6; f++) {
+        int d = f / 2, t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+        for (int b = 0; b < n; b++)
+            for (int a = 0; a < n; a++) {
+                double *X = &xf[((size_t)f * n * n + a + n * b) * 3];
+                X[d] = (f & 1) ? 1.0 : -1.0;
+                X[t1] = h.x[a];
+                X[t2] = h.x[b];
+            }
+    }
+}
+
+static void affine_point(const double *x0J, const double *X, double *x)
+{
+    for (int i = 0; i < 3; i++) {
+        x[i] = x0J[i];
+        for (int j = 0; j < 3; j++) x[i] += x0J[3 + 3 * i + j] * (X[j] + 1.0);
+    }
+}
+
+static double inv3(const double *a, double *b)
+{
+    double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
+    double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+    double id = 1.0 / det;
+    b[0] = c00 * id; b[1] = (a[2] * a[7] - a[1] * a[8]) * id; b[2] = (a[1] * a[5] - a[2] * a[4]) * id;
+    b[3] = c01 * id; b[4] = (a[0] * a[8] - a[2] * a[6]) * id; b[5] = (a[2] * a[3] - a[0] * a[5]) * id;
+    b[6] = c02 * id; b[7] = (a[1] * a[6] - a[0] * a[7]) * id; b[8] = (a[0] * a[4] - a[1] * a[3]) * id;
+    return det;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Face matching
+// ---------------------------------------------------------------------------------------------
+struct FaceRef {
+    long long elem;   // global element
+    int blk;          // block index
+    long long le;     // element within block
+    int face;
+    double c[3];      // physical centroid
+};
+
+struct CellKey {
+    long long i, j, k;
+    bool operator==(const CellKey &o) const { return i == o.i && j == o.j && k == o.k; }
+};
+struct CellHash {
+    size_t operator()(const CellKey &c) const
+    {
+        return (size_t)(c.i * 73856093LL) ^ (size_t)(c.j * 19349663LL) ^ (size_t)(c.k * 83492791LL);
+    }
+};
+
+static double pdist2(const double *a, const double *b, const double *per)
+{
+    double s = 0;
+    for (int d = 0; d < 3; d++) {
+        double x = a[d] - b[d];
+        if (per[d] > 0) x -= per[d] * std::nearbyint(x / per[d]);
+        s += x * x;
+    }
+    return s;
+}
+
+// Builds partner codes for all flux points of one instance (its blocks are [b0, b1)).
+static fr_status match_instance(fr_mesh *m, int ii, int b0, int b1, const fr_mesh_desc *d, std::vector<uint32_t> &partner)
+{
+    const InstanceHost &I = m->inst[ii];
+    // element size scale for tolerances
+    double hmin = 1e300;
+    std::vector<FaceRef> faces;
+    std::vector<std::vector<double>> xf_ref(b1 - b0);
+    for (int b = b0; b < b1; b++) {
+        const Block &B = m->blocks[b];
+        hex_ref_fpts(m->hex1d[b], xf_ref[b - b0]);
+        for (long long le = 0; le < B.ne; le++) {
+            const double *x0J = &I.x0J[(size_t)(B.elem0 - m->blocks[b0].elem0 + le) * 12];
+            double hh = std::cbrt(std::fabs(x0J[3] * (x0J[7] * x0J[11] - x0J[8] * x0J[10]) - x0J[4] * (x0J[6] * x0J[11] - x0J[8] * x0J[9]) + x0J[5] * (x0J[6] * x0J[10] - x0J[7] * x0J[9])));
+            hmin = std::min(hmin, hh);
+            for (int f = 0; f < 6; f++) {
+                FaceRef fr;
+                fr.elem = B.elem0 + le; fr.blk = b; fr.le = le; fr.face = f;
+                double X[3] = {0, 0, 0};
+                X[f / 2] = (f & 1) ? 1.0 : -1.0;
+                affine_point(x0J, X, fr.c);
+                faces.push_back(fr);
+            }
+        }
+    }
+    const double tol = 1e-7 * hmin, tol2 = tol * tol, cell = 8 * tol;
+    long long ncell[3];
+    for (int k = 0; k < 3; k++) ncell[k] = d->period[k] > 0 ? (long long)std::ceil(d->period[k] / cell) : 0;
+    auto key_of = [&](const double *c) {
+        long long q[3];
+        for (int k = 0; k < 3; k++) {
+            double x = c[k];
+            if (d->period[k] > 0) x -= d->period[k] * std::floor(x / d->period[k]);
+            q[k] = (long long)std::floor(x / cell);
+            if (ncell[k] > 0) q[k] = ((q[k] % ncell[k]) + ncell[k]) % ncell[k];
+        }
+        return CellKey{q[0], q[1], q[2]};
+    };
+    std::unordered_map<CellKey, std::vector<int>, CellHash> open;
+    std::vector<int> mate(faces.size(), -1);
+    for (size_t a = 0; a < faces.size(); a++) {
+        CellKey k0 = key_of(faces[a].c);
+        int found = -1;
+        for (int di = -1; di <= 1 && found < 0; di++)
+            for (int dj = -1; dj <= 1 && found < 0; dj++)
+                for (int dk = -1; dk <= 1 && found < 0; dk++) {
+                    CellKey k{k0.i + di, k0.j + dj, k0.k + dk};
+                    if (ncell[0]) k.i = ((k.i % ncell[0]) + ncell[0]) % ncell[0];
+                    if (ncell[1]) k.j = ((k.j % ncell[1]) + ncell[1]) % ncell[1];
+                    if (ncell[2]) k.k = ((k.k % ncell[2]) + ncell[2]) % ncell[2];
+                    auto it = open.find(k);
+                    if (it == open.end()) continue;
+                    for (size_t t = 0; t < it->second.size(); t++) {
+                        int b = it->second[t];
+                        if (pdist2(faces[a].c, faces[b].c, d->period) < tol2) {
+                            found = b;
+                            it->second.erase(it->second.begin() + t);
+                            break;
+                        }
+                    }
+                }
+        if (found >= 0) { mate[a] = found; mate[found] = (int)a; }
+        else open[k0].push_back((int)a);
+    }
+    for (size_t a = 0; a < faces.size(); a++)
+        if (mate[a] < 0)
+            return fail(FR_EMESH, "instance %d: face %d of element %lld has no partner", ii, faces[a].face, faces[a].elem);
+    // point permutations (cached per pair of face kinds)
+    std::map<std::tuple<int, int, int, int>, std::vector<int>> perm_cache;
+    std::vector<double> xa, xb;
+    for (size_t a = 0; a < faces.size(); a++) {
+        size_t b = (size_t)mate[a];
+        if (b < a) continue;
+        const FaceRef &A = faces[a], &Bf = faces[b];
+        const Block &BA = m->blocks[A.blk], &BB = m->blocks[Bf.blk];
+        int n2 = BA.nf / 6;
+        if (BB.nf / 6 != n2) return fail(FR_EMESH, "face point counts differ across an interface");
+        const double *JA = &I.x0J[(size_t)(A.elem - m->blocks[b0].elem0) * 12];
+        const double *JB = &I.x0J[(size_t)(Bf.elem - m->blocks[b0].elem0) * 12];
+        xa.resize(n2 * 3); xb.resize(n2 * 3);
+        for (int t = 0; t < n2; t++) {
+            affine_point(JA, &xf_ref[A.blk - b0][((size_t)A.face * n2 + t) * 3], &xa[t * 3]);
+            affine_point(JB, &xf_ref[Bf.blk - b0][((size_t)Bf.face * n2 + t) * 3], &xb[t * 3]);
+        }
+        auto key = std::make_tuple(BA.type, A.face, BB.type, Bf.face);
+        std::vector<int> &perm = perm_cache[key];
+        bool ok = (int)perm.size() == n2;
+        for (int t = 0; ok && t < n2; t++) ok = pdist2(&xa[t * 3], &xb[perm[t] * 3], d->period) < tol2;
+        if (!ok) {
+            perm.assign(n2, -1);
+            for (int t = 0; t < n2; t++) {
+                for (int u = 0; u < n2; u++)
+                    if (pdist2(&xa[t * 3], &xb[u * 3], d->period) < tol2) { perm[t] = u; break; }
+                if (perm[t] < 0) return fail(FR_EMESH, "flux point of element %lld face %d has no partner", A.elem, A.face);
+            }
+        }
+        // reading R5: L is the smaller global element; a self-pair takes the smaller local face
+        bool aL = A.elem < Bf.elem || (A.elem == Bf.elem && A.face < Bf.face);
+        for (int t = 0; t < n2; t++) {
+            long long ga = BA.f0 + A.le * BA.nf + (long long)A.face * n2 + t;
+            long long gb = BB.f0 + Bf.le * BB.nf + (long long)Bf.face * n2 + perm[t];
+            partner[ga] = (uint32_t)gb | (aL ? FR_LFLAG : 0u);
+            partner[gb] = (uint32_t)ga | (aL ? 0u : FR_LFLAG);
+        }
+        m->npair += n2;
+    }
+    return FR_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Mesh creation
+// ---------------------------------------------------------------------------------------------
+static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_inst, const fr_params *prm,
+                            std::vector<uint32_t> &partner)
+{
+    if (!inst || !prm || n_inst <= 0) return fail(FR_EINVAL, "null descriptor or n_inst <= 0");
+    m->prec = prm[0].prec;
+    if (m->prec < FR_FP64 || m->prec > FR_MIXED_FP16) return fail(FR_EINVAL, "unknown precision %d", m->prec);
+    long long elem = 0, u = 0, f = 0;
+    for (int ii = 0; ii < n_inst; ii++) {
+        const fr_mesh_desc *d = inst[ii];
+        const fr_params &P = prm[ii];
+        if (!d) return fail(FR_EINVAL, "instance %d: null descriptor", ii);
+        if (P.prec != m->prec) return fail(FR_EINVAL, "all instances must share one precision");
+        int m1 = P.nq1d > 0 ? P.nq1d : P.p + 2;
+        if (P.p < 3 || P.p > 4 || m1 != P.p + 2) return fail(FR_EUNSUPPORTED, "instance %d: hex order %d with %d quadrature points", ii, P.p, m1);
+        if (!(P.gamma > 1.0) || !(P.Pr > 0.0) || P.mu < 0.0 || P.tau < 0.0) return fail(FR_EINVAL, "instance %d: bad physical parameters", ii);
+        if (P.rusanov_mode != 0) return fail(FR_EUNSUPPORTED, "rusanov_mode %d", P.rusanov_mode);
+        if (d->n_hex < 0 || d->n_pri < 0 || d->n_hex + d->n_pri == 0 || d->n_verts <= 0 || !d->verts)
+            return fail(FR_EINVAL, "instance %d: empty or malformed mesh", ii);
+        if (d->n_pri > 0) return fail(FR_EUNSUPPORTED, "instance %d: prism elements are not built in this library version", ii);
+        if (!d->hex_v) return fail(FR_EINVAL, "instance %d: null hex connectivity", ii);
+        InstanceHost I;
+        I.prm = P; I.prm.nq1d = m1;
+        I.n_hex = d->n_hex; I.n_pri = d->n_pri;
+        I.x0J.resize((size_t)(d->n_hex + d->n_pri) * 12);
+        Block B{};
+        B.inst = ii; B.type = 0; B.p = P.p; B.m = m1;
+        B.nu = (P.p + 1) * (P.p + 1) * (P.p + 1); B.nf = 6 * (P.p + 1) * (P.p + 1);
+        B.ne = d->n_hex; B.elem0 = elem; B.u0 = u; B.f0 = f;
+        frb::Hex1D h;
+        if (frb::hex1d(P.p, m1, h)) return fail(FR_EUNSUPPORTED, "hex operators for p=%d m=%d", P.p, m1);
+        m->inst_u0.push_back(u);
+        for (long long e = 0; e < d->n_hex; e++) {
+            const double *v[8];
+            for (int k = 0; k < 8; k++) {
+                int vi = d->hex_v[8 * e + k];
+                if (vi < 0 || vi >= d->n_verts) return fail(FR_EMESH, "instance %d element %lld: vertex id %d out of range", ii, e, vi);
+                v[k] = d->verts + 3 * (size_t)vi;
+            }
+            double *x0J = &I.x0J[(size_t)e * 12];
+            double scale = 0;
+            for (int i = 0; i < 3; i++) {
+                x0J[i] = v[0][i];
+                x0J[3 + 3 * i + 0] = 0.5 * (v[1][i] - v[0][i]);
+                x0J[3 + 3 * i + 1] = 0.5 * (v[2][i] - v[0][i]);
+                x0J[3 + 3 * i + 2] = 0.5 * (v[4][i] - v[0][i]);
+                scale = std::max(scale, std::fabs(v[1][i] - v[0][i]) + std::fabs(v[2][i] - v[0][i]) + std::fabs(v[4][i] - v[0][i]));
+            }
+            for (int k = 0; k < 8; k++) {  // affine: every corner is the image of its reference corner
+                double X[3] = {(k & 1) ? 1.0 : -1.0, (k & 2) ? 1.0 : -1.0, (k & 4) ? 1.0 : -1.0}, x[3];
+                affine_point(x0J, X, x);
+                for (int i = 0; i < 3; i++)
+                    if (std::fabs(x[i] - v[k][i]) > 1e-10 * scale)
+                        return fail(FR_EUNSUPPORTED, "instance %d element %lld is not affine", ii, e);
+            }
+            double Ji[9];
+            double det = inv3(x0J + 3, Ji);
+            if (!(det > 0)) return fail(FR_EMESH, "instance %d element %lld is inverted or degenerate", ii, e);
+            for (int k = 0; k < 9; k++) m->geo_host.push_back(Ji[k]);
+            m->geo_host.push_back(det);
+        }
+        m->inst.push_back(I);
+        m->blocks.push_back(B);
+        m->hex1d.push_back(h);
+        elem += B.ne; u += B.ne * FR_NV * B.nu; f += B.ne * B.nf;
+    }
+    m->ne = elem; m->nU = u; m->nfpt = f;
+    m->inst_u0.push_back(u);
+    if (f >= (long long)FR_LFLAG) return fail(FR_EUNSUPPORTED, "more than 2^31 flux points");
+    partner.assign((size_t)f, 0xffffffffu);
+    for (int ii = 0; ii < n_inst; ii++) {
+        fr_status st = match_instance(m, ii, ii, ii + 1, inst[ii], partner);
+        if (st != FR_OK) return st;
+    }
+    return FR_OK;
+}
+
+template <typename T>
+static fr_status upload_geo(fr_mesh *m)
+{
+    std::vector<Geo<T>> g((size_t)m->ne);
+    for (long long e = 0; e < m->ne; e++) {
+        for (int k = 0; k < 9; k++) g[e].Ji[k] = (T)m->geo_host[(size_t)e * 10 + k];
+        g[e].det = (T)m->geo_host[(size_t)e * 10 + 9];
+    }
+    fr_status st = dalloc(m, &m->d_geo, g.size() * sizeof(Geo<T>));
+    if (st) return st;
+    CU(cudaMemcpy(m->d_geo, g.data(), g.size() * sizeof(Geo<T>), cudaMemcpyHostToDevice));
+    return FR_OK;
+}
+
+extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst, const fr_params *prm, fr_mesh **out)
+{
+    if (!out) return fail(FR_EINVAL, "out is null");
+    *out = nullptr;
+    fr_mesh *m = new fr_mesh();
+    std::vector<uint32_t> partner;
+    fr_status st = build_host(m, inst, n_inst, prm, partner);
+    if (st) { delete m; return st; }
+    cudaError_t ce = cudaGetDevice(&m->dev);
+    if (ce != cudaSuccess) { delete m; return fail(FR_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(ce)); }
+    for (size_t b = 0; b < m->blocks.size(); b++)
+        if (hex_upload_ops(m->blocks[b].p, m->blocks[b].m, m->hex1d[b])) { delete m; return fail(FR_ECUDA, "operator upload failed"); }
+    size_t ts = tsize(m->prec);
+    st = (m->prec == FR_FP64) ? upload_geo<double>(m) : upload_geo<float>(m);
+    if (!st) st = dalloc(m, (void **)&m->d_partner, partner.size() * sizeof(uint32_t));
+    if (!st && cudaMemcpy(m->d_partner, partner.data(), partner.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+        st = fail(FR_ECUDA, "partner upload failed");
+    if (!st) st = dalloc(m, &m->d_UF, (size_t)5 * m->nfpt * ts);
+    if (!st) st = dalloc(m, &m->d_FV, (size_t)4 * m->nfpt * ts);
+    if (!st) st = dalloc(m, (void **)&m->d_status, sizeof(int));
+    if (!st && cudaMemset(m->d_status, 0, sizeof(int)) != cudaSuccess) st = fail(FR_ECUDA, "memset");
+    if (!st && cudaMallocHost((void **)&m->h_status, sizeof(int)) != cudaSuccess) st = fail(FR_ENOMEM, "pinned status");
+    if (!st && cudaEventCreateWithFlags(&m->ev_status, cudaEventDisableTiming) != cudaSuccess) st = fail(FR_ECUDA, "event");
+    if (st) { fr_destroy(m); return st; }
+    *m->h_status = 0;
+    *out = m;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_destroy(fr_mesh *m)
+{
+    if (!m) return FR_OK;
+    void **bufs[] = {&m->d_geo, (void **)&m->d_partner, &m->d_UF, &m->d_FV, &m->d_CF, &m->d_QF, &m->d_DF, &m->d_Qu,
+                     &m->d_UQ, &m->d_QQ, &m->d_Rt, &m->d_rk_k, &m->d_rk_us, (void **)&m->d_rk_acc, &m->d_io_U,
+                     &m->d_io_R, (void **)&m->d_wsum, (void **)&m->d_status, &m->d_Qsnap};
+    for (void **b : bufs) dfree(*b);
+    if (m->h_status) cudaFreeHost(m->h_status);
+    for (auto &t : m->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+    for (auto e : m->ev_pool) cudaEventDestroy(e);
+    if (m->ev_status) cudaEventDestroy(m->ev_status);
+    delete m;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_set_debug(fr_mesh *m, int flags)
+{
+    if (!m) return fail(FR_EINVAL, "null handle");
+    m->debug = flags;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_set_timing(fr_mesh *m, int on)
+{
+    if (!m) return fail(FR_EINVAL, "null handle");
+    m->timing = on != 0;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_kernel_times(fr_mesh *m, double *ms, long long *count, int n_ids)
+{
+    if (!m || !ms || !count || n_ids <= 0) return fail(FR_EINVAL, "bad argument");
+    for (int i = 0; i < n_ids; i++) { ms[i] = 0; count[i] = 0; }
+    for (auto &t : m->timed) {
+        CU(cudaEventSynchronize(t.b));
+        float x = 0;
+        CU(cudaEventElapsedTime(&x, t.a, t.b));
+        if (t.kernel < n_ids) { ms[t.kernel] += x; count[t.kernel] += 1; }
+        m->ev_pool.push_back(t.a);
+        m->ev_pool.push_back(t.b);
+    }
+    m->timed.clear();
+    return FR_OK;
+}
+
+extern "C" fr_status fr_set_form(fr_mesh *m, int form)
+{
+    if (!m || (form != FR_FUSED && form != FR_UNFUSED)) return fail(FR_EINVAL, "bad handle or form");
+    m->form = form;
+    return FR_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// RHS
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+static HexArgs<T> make_args(fr_mesh *m, const Block &b, const void *U, void *R)
+{
+    HexArgs<T> a{};
+    const InstanceHost &I = m->inst[b.inst];
+    a.ne = b.ne; a.u0 = b.u0; a.f0 = b.f0; a.nfpt = m->nfpt;
+    a.geo = reinterpret_cast<const Geo<T> *>(m->d_geo) + b.elem0;
+    a.partner = m->d_partner;
+    a.ph.gamma = (T)I.prm.gamma; a.ph.gm1 = (T)(I.prm.gamma - 1.0); a.ph.mu = (T)I.prm.mu;
+    a.ph.beta = (T)I.prm.beta; a.ph.tau = (T)I.prm.tau;
+    a.ph.heat = (T)(I.prm.mu * I.prm.gamma / I.prm.Pr);
+    a.U = reinterpret_cast<const T *>(U); a.R = reinterpret_cast<T *>(R);
+    a.UF = reinterpret_cast<T *>(m->d_UF); a.FV = reinterpret_cast<T *>(m->d_FV);
+    a.CF = reinterpret_cast<T *>(m->d_CF); a.QF = reinterpret_cast<T *>(m->d_QF); a.DF = reinterpret_cast<T *>(m->d_DF);
+    // per-element unfused arrays are addressed block-locally; the unfused form runs single-block meshes
+    a.Qu = reinterpret_cast<T *>(m->d_Qu); a.UQ = reinterpret_cast<T *>(m->d_UQ); a.QQ = reinterpret_cast<T *>(m->d_QQ);
+    a.Rt = reinterpret_cast<T *>(m->d_Rt);
+    a.status = m->d_status;
+    return a;
+}
+
+static fr_status ensure_unfused(fr_mesh *m)
+{
+    if (m->blocks.size() != 1) return fail(FR_EUNSUPPORTED, "the unfused form runs single-instance hexahedral meshes");
+    const Block &b = m->blocks[0];
+    size_t ts = tsize(m->prec);
+    long long nq = (long long)b.m * b.m * b.m;
+    fr_status st = FR_OK;
+    if (!st) st = dalloc(m, &m->d_CF, (size_t)5 * m->nfpt * ts);
+    if (!st) st = dalloc(m, &m->d_QF, (size_t)15 * m->nfpt * ts);
+    if (!st) st = dalloc(m, &m->d_DF, (size_t)5 * m->nfpt * ts);
+    if (!st) st = dalloc(m, &m->d_Qu, (size_t)15 * b.ne * b.nu * ts);
+    if (!st) st = dalloc(m, &m->d_UQ, (size_t)5 * b.ne * nq * ts);
+    if (!st) st = dalloc(m, &m->d_QQ, (size_t)15 * b.ne * nq * ts);
+    if (!st) st = dalloc(m, &m->d_Rt, (size_t)5 * b.ne * b.nu * ts);
+    return st;
+}
+
+static fr_status check_status(fr_mesh *m)
+{
+    if (m->status_pending && cudaEventQuery(m->ev_status) == cudaSuccess) {
+        m->status_pending = false;
+        if (*m->h_status) {
+            *m->h_status = 0;
+            cudaMemset(m->d_status, 0, sizeof(int));
+            return fail(FR_ENONPHYS, "non-physical state met on the device");
+        }
+    }
+    return FR_OK;
+}
+
+static fr_status post_status(fr_mesh *m, cudaStream_t s)
+{
+    CU(cudaMemcpyAsync(m->h_status, m->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaEventRecord(m->ev_status, s));
+    m->status_pending = true;
+    return FR_OK;
+}
+
+template <typename T>
+static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s)
+{
+    if (m->form == FR_FUSED) {
+        for (int ph = 0; ph < 3; ph++) {
+            TimeScope ts(m, ph, s);
+            for (const Block &b : m->blocks) {
+                HexArgs<T> a = make_args<T>(m, b, U, R);
+                if (hex_fused_phase<T>(b.p, ph, a, s)) return fail(FR_ECUDA, "fused phase %d launch: %s", ph, cudaGetErrorString(cudaGetLastError()));
+            }
+        }
+    } else {
+        fr_status st = ensure_unfused(m);
+        if (st) return st;
+        const Block &b = m->blocks[0];
+        HexArgs<T> a = make_args<T>(m, b, U, R);
+        for (int k = 1; k <= 13; k++) {
+            int lr;
+            {
+                TimeScope ts(m, 10 + k, s);
+                lr = hex_unfused_kernel<T>(b.p, k, a, s);
+            }
+            if (lr) return fail(FR_ECUDA, "unfused kernel %d launch: %s", k, cudaGetErrorString(cudaGetLastError()));
+            if (k == 6 && m->debug) {
+                size_t bytes = (size_t)15 * b.ne * b.nu * sizeof(T);
+                st = dalloc(m, &m->d_Qsnap, bytes);
+                if (st) return st;
+                CU(cudaMemcpyAsync(m->d_Qsnap, m->d_Qu, bytes, cudaMemcpyDeviceToDevice, s));
+            }
+        }
+    }
+    return FR_OK;
+}
+
+static fr_status rhs_dispatch(fr_mesh *m, const void *U, void *R, cudaStream_t s)
+{
+    return m->prec == FR_FP64 ? rhs_impl<double>(m, U, R, s) : rhs_impl<float>(m, U, R, s);
+}
+
+extern "C" fr_status fr_rhs(fr_mesh *m, const void *U_dev, void *R_dev, void *stream)
+{
+    if (!m || !U_dev || !R_dev) return fail(FR_EINVAL, "null argument");
+    if (U_dev == R_dev) return fail(FR_EINVAL, "U and R must not alias");
+    fr_status st = check_status(m);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = rhs_dispatch(m, U_dev, R_dev, s);
+    if (st) return st;
+    return post_status(m, s);
+}
+
+extern "C" fr_status fr_rhs_host(fr_mesh *m, const void *U_host, void *R_host, void *stream)
+{
+    if (!m || !U_host || !R_host) return fail(FR_EINVAL, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t bytes = (size_t)m->nU * tsize(m->prec);
+    fr_status st = dalloc(m, &m->d_io_U, (size_t)m->nU * sizeof(double));
+    if (!st) st = dalloc(m, &m->d_io_R, bytes);
+    if (st) return st;
+    CU(cudaMemcpyAsync(m->d_io_U, U_host, bytes, cudaMemcpyHostToDevice, s));
+    st = fr_rhs(m, m->d_io_U, m->d_io_R, stream);
+    if (st) return st;
+    CU(cudaMemcpyAsync(R_host, m->d_io_R, bytes, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    return check_status(m);
+}
+
+extern "C" fr_status fr_sync_status(fr_mesh *m, void *stream)
+{
+    if (!m) return fail(FR_EINVAL, "null handle");
+    CU(cudaStreamSynchronize((cudaStream_t)stream));
+    int v = 0;
+    CU(cudaMemcpy(&v, m->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    CU(cudaMemset(m->d_status, 0, sizeof(int)));
+    m->status_pending = false;
+    *m->h_status = 0;
+    return v ? fail(FR_ENONPHYS, "non-physical state met on the device") : FR_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// RK4
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_rk_cast(const double *__restrict__ U, T *__restrict__ us, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) us[i] = (T)U[i];
+}
+
+// After stage s (k = R(u_s)): acc (+)= b_s k; u_{s+1} = U + c_{s+1} dt k; the last stage updates U.
+template <typename T>
+__global__ void k_rk_update(double *__restrict__ U, const T *__restrict__ k, double *__restrict__ acc, T *__restrict__ us,
+                            long long n, double dt, int stage)
+{
+    const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    const double cnext[4] = {0.5, 0.5, 1.0, 0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double kv = (double)k[i];
+        if (stage == 3) {
+            U[i] += dt * (acc[i] + b[3] * kv);
+        } else {
+            const double a = (stage == 0 ? 0.0 : acc[i]) + b[stage] * kv;
+            acc[i] = a;
+            us[i] = (T)(U[i] + cnext[stage] * dt * kv);
+        }
+    }
+}
+
+template <typename T>
+static fr_status rk4_impl(fr_mesh *m, double *U, double dt, int nsteps, cudaStream_t s)
+{
+    const long long n = m->nU;
+    const int thr = 256;
+    const int grid = (int)std::min<long long>((n + thr - 1) / thr, 152LL * 16);
+    for (int step = 0; step < nsteps; step++) {
+        const void *u0 = U;
+        if (m->prec != FR_FP64) {
+            k_rk_cast<T><<<grid, thr, 0, s>>>(U, reinterpret_cast<T *>(m->d_rk_us), n);
+            u0 = m->d_rk_us;
+        }
+        for (int st = 0; st < 4; st++) {
+            fr_status r = rhs_dispatch(m, st == 0 ? u0 : m->d_rk_us, m->d_rk_k, s);
+            if (r) return r;
+            TimeScope ts(m, 30, s);
+            k_rk_update<T><<<grid, thr, 0, s>>>(U, reinterpret_cast<const T *>(m->d_rk_k), m->d_rk_acc,
+                                                reinterpret_cast<T *>(m->d_rk_us), n, dt, st);
+        }
+    }
+    CU(cudaPeekAtLastError());
+    return FR_OK;
+}
+
+extern "C" fr_status fr_rk4_step(fr_mesh *m, void *U_dev, double dt, int nsteps, void *stream)
+{
+    if (!m || !U_dev || nsteps < 0 || !(dt == dt)) return fail(FR_EINVAL, "bad argument");
+    fr_status st = check_status(m);
+    if (st) return st;
+    size_t ts = tsize(m->prec);
+    st = dalloc(m, &m->d_rk_k, (size_t)m->nU * ts);
+    if (!st) st = dalloc(m, &m->d_rk_us, (size_t)m->nU * ts);
+    if (!st) st = dalloc(m, (void **)&m->d_rk_acc, (size_t)m->nU * sizeof(double));
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = m->prec == FR_FP64 ? rk4_impl<double>(m, (double *)U_dev, dt, nsteps, s) : rk4_impl<float>(m, (double *)U_dev, dt, nsteps, s);
+    if (st) return st;
+    return post_status(m, s);
+}
+
+extern "C" fr_status fr_rk4_step_host(fr_mesh *m, void *U_host, double dt, int nsteps, void *stream)
+{
+    if (!m || !U_host) return fail(FR_EINVAL, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t bytes = (size_t)m->nU * sizeof(double);
+    fr_status st = dalloc(m, &m->d_io_U, std::max(bytes, (size_t)m->nU * tsize(m->prec)));
+    if (st) return st;
+    CU(cudaMemcpyAsync(m->d_io_U, U_host, bytes, cudaMemcpyHostToDevice, s));
+    st = fr_rk4_step(m, m->d_io_U, dt, nsteps, stream);
+    if (st) return st;
+    CU(cudaMemcpyAsync(U_host, m->d_io_U, bytes, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    return check_status(m);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Info, coordinates, diagnostics, stages
+// ---------------------------------------------------------------------------------------------
+extern "C" long long fr_num_values(const fr_mesh *m) { return m ? m->nU : 0; }
+
+extern "C" fr_status fr_mesh_info(const fr_mesh *m, long long *info)
+{
+    if (!m || !info) return fail(FR_EINVAL, "null argument");
+    info[0] = m->ne; info[1] = m->nU; info[2] = m->nfpt; info[3] = m->npair; info[4] = (long long)m->inst.size();
+    info[5] = (m->form == FR_FUSED ? 3 : 13) * (long long)m->blocks.size();
+    info[6] = m->bytes;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_instance_offsets(const fr_mesh *m, long long *off)
+{
+    if (!m || !off) return fail(FR_EINVAL, "null argument");
+    for (size_t i = 0; i < m->inst_u0.size(); i++) off[i] = m->inst_u0[i];
+    return FR_OK;
+}
+
+extern "C" fr_status fr_sol_coords(const fr_mesh *m, double *xyz)
+{
+    if (!m || !xyz) return fail(FR_EINVAL, "null argument");
+    long long k = 0;
+    for (size_t b = 0; b < m->blocks.size(); b++) {
+        const Block &B = m->blocks[b];
+        const InstanceHost &I = m->inst[B.inst];
+        const frb::Hex1D &h = m->hex1d[b];
+        int n = h.n;
+        for (long long e = 0; e < B.ne; e++) {
+            const double *x0J = &I.x0J[(size_t)e * 12];
+            for (int z = 0; z < B.nu; z++, k++) {
+                double X[3] = {h.x[z % n], h.x[(z / n) % n], h.x[z / (n * n)]};
+                affine_point(x0J, X, xyz + 3 * k);
+            }
+        }
+    }
+    return FR_OK;
+}
+
+struct W1D {
+    double w[FR_MAXN];
+};
+
+// Per-element partial sums of the diagnostics; out[k] (k < 8): 0 volume, 1 int rho|v|^2/2,
+// 2 -int d(rho|v|^2/2)/dt from R, 3..7 int R_alpha (weights W = tensor GL weights times detJ).
+template <typename T>
+__global__ void k_diag(const T *__restrict__ U, const T *__restrict__ R, const Geo<T> *__restrict__ geo, long long ne,
+                       int n, W1D w1, double *out)
+{
+    const int NU = n * n * n;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long e = blockIdx.x; e < ne; e += gridDim.x) {
+        const T *u = U + e * 5 * NU;
+        const T *r = R ? R + e * 5 * NU : nullptr;
+        const double det = (double)geo[e].det;
+        for (int z = threadIdx.x; z < NU; z += blockDim.x) {
+            const double w = w1.w[z % n] * w1.w[(z / n) % n] * w1.w[z / (n * n)] * det;
+            const double rho = (double)u[z];
+            const double v0 = (double)u[NU + z] / rho, v1 = (double)u[2 * NU + z] / rho, v2 = (double)u[3 * NU + z] / rho;
+            const double v2s = v0 * v0 + v1 * v1 + v2 * v2;
+            acc[0] += w;
+            acc[1] += w * 0.5 * rho * v2s;
+            if (r) {
+                acc[2] -= w * (v0 * (double)r[NU + z] + v1 * (double)r[2 * NU + z] + v2 * (double)r[3 * NU + z] - 0.5 * v2s * (double)r[z]);
+                for (int a = 0; a < 5; a++) acc[3 + a] += w * (double)r[a * NU + z];
+            }
+        }
+    }
+    for (int k = 0; k < 8; k++) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&out[k], v);
+    }
+}
+
+extern "C" fr_status fr_diagnostics(fr_mesh *m, const void *U, const void *R, double *out, void *stream)
+{
+    if (!m || !U || !out) return fail(FR_EINVAL, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t ni = m->inst.size();
+    fr_status st = dalloc(m, (void **)&m->d_wsum, ni * 8 * sizeof(double));
+    if (st) return st;
+    CU(cudaMemsetAsync(m->d_wsum, 0, ni * 8 * sizeof(double), s));
+    for (size_t bi = 0; bi < m->blocks.size(); bi++) {
+        const Block &b = m->blocks[bi];
+        W1D w1{};
+        for (int i = 0; i < m->hex1d[bi].n; i++) w1.w[i] = m->hex1d[bi].w[i];
+        int grid = (int)std::min<long long>(std::max<long long>(b.ne, 1), 152LL * 8);
+        double *o = m->d_wsum + 8 * b.inst;
+        size_t ts = tsize(m->prec);
+        const char *u = (const char *)U + b.u0 * ts;
+        const char *r = R ? (const char *)R + b.u0 * ts : nullptr;
+        if (m->prec == FR_FP64)
+            k_diag<double><<<grid, 128, 0, s>>>((const double *)u, (const double *)r,
+                                                 (const Geo<double> *)m->d_geo + b.elem0, b.ne, b.p + 1, w1, o);
+        else
+            k_diag<float><<<grid, 128, 0, s>>>((const float *)u, (const float *)r,
+                                                (const Geo<float> *)m->d_geo + b.elem0, b.ne, b.p + 1, w1, o);
+        CU(cudaPeekAtLastError());
+    }
+    std::vector<double> h(ni * 8);
+    CU(cudaMemcpyAsync(h.data(), m->d_wsum, ni * 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < ni; i++) {
+        const double *a = &h[8 * i];
+        double *o = out + 8 * i;
+        o[0] = a[0];
+        o[1] = a[1] / a[0];
+        o[2] = a[2] / a[0];
+        for (int k = 0; k < 5; k++) o[3 + k] = a[3 + k];
+    }
+    return FR_OK;
+}
+
+extern "C" fr_status fr_stage(fr_mesh *m, int which, double *host, long long n_host, long long *n_needed)
+{
+    if (!m) return fail(FR_EINVAL, "null handle");
+    void *src = nullptr;
+    long long n = 0;
+    const Block &b = m->blocks[0];
+    long long nq = (long long)b.m * b.m * b.m;
+    (void)nq;
+    switch (which) {
+    case 0: src = m->d_UF; n = 5 * m->nfpt; break;
+    case 1: src = m->d_CF; n = 5 * m->nfpt; break;
+    case 2: src = m->d_Qsnap; n = 15 * b.ne * b.nu; break;
+    case 3: src = m->d_QF; n = 15 * m->nfpt; break;
+    case 4: src = m->d_Qu; n = 15 * b.ne * b.nu; break;
+    case 5: src = m->d_DF; n = 5 * m->nfpt; break;
+    default: return fail(FR_EINVAL, "unknown stage %d", which);
+    }
+    if (n_needed) *n_needed = n;
+    if (!host) return FR_OK;
+    if (!src) return fail(FR_EINVAL, "stage %d has not been computed (run an unfused RHS first)", which);
+    if (n_host < n) return fail(FR_EINVAL, "host buffer too small");
+    CU(cudaDeviceSynchronize());
+    if (m->prec == FR_FP64) {
+        CU(cudaMemcpy(host, src, n * sizeof(double), cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<float> tmp((size_t)n);
+        CU(cudaMemcpy(tmp.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost));
+        for (long long i = 0; i < n; i++) host[i] = tmp[i];
+    }
+    return FR_OK;
+}

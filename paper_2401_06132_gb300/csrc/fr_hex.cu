@@ -1,0 +1,812 @@
+// fr_hex.cu -- hexahedral kernels of the anti-aliased Navier-Stokes FR right-hand side.
+//
+// Two forms of the same computation (Sec. 2.2 and 2.2.1 kernels, sum-factorised per Sec. 4):
+//
+//   fused   A: disu                   -> U^(f) at every flux point (global, read by neighbours)
+//           B: con_u + tgradpcoru + tgradcoru + gradcoru + gradcoru_fpts (viscous part) +
+//              uqpts + gradcoru_qpts + tdisf + tdivtpcorf, per element, intermediates in shared
+//              memory; writes R~ into R and the own-normal viscous flux at flux points
+//           C: comm_flux + tdivtconf + negdivconf, per element (each side evaluates the common flux
+//              of its own flux points with the L/R roles of the pair, so both sides agree bitwise)
+//   unfused K1..K13: one kernel per paper kernel with global intermediates (Sec. 3 order).
+//
+// Hex point index i + n j + n^2 k; the face-local index of a flux point is a + n b over the two
+// tangential axes in increasing axis order; flux point sigma = face * n^2 + local.
+#include <cuda_runtime.h>
+
+#include "fr_internal.h"
+
+__constant__ HexOps<double> c_hex64[3];  // slot p - 2
+__constant__ HexOps<float> c_hex32[3];
+
+template <typename T> __device__ __forceinline__ const HexOps<T> &OPS(int slot);
+template <> __device__ __forceinline__ const HexOps<double> &OPS<double>(int slot) { return c_hex64[slot]; }
+template <> __device__ __forceinline__ const HexOps<float> &OPS<float>(int slot) { return c_hex32[slot]; }
+
+int hex_upload_ops(int p, int m, const frb::Hex1D &h)
+{
+    if (p < 2 || p > 4 || m != p + 2) return -1;
+    HexOps<double> d{};
+    HexOps<float> f{};
+    for (int a = 0; a < FR_MAXM; a++)
+        for (int i = 0; i < FR_MAXN; i++) { d.B[a][i] = h.B[a][i]; f.B[a][i] = (float)h.B[a][i]; }
+    for (int i = 0; i < FR_MAXN; i++) {
+        for (int a = 0; a < FR_MAXM; a++) { d.Pj[i][a] = h.Pj[i][a]; f.Pj[i][a] = (float)h.Pj[i][a]; }
+        for (int j = 0; j < FR_MAXN; j++) { d.Dh[i][j] = h.Dh[i][j]; f.Dh[i][j] = (float)h.Dh[i][j]; }
+        d.lL[i] = h.lL[i]; d.lR[i] = h.lR[i]; d.liftL[i] = h.liftL[i]; d.liftR[i] = h.liftR[i]; d.w[i] = h.w[i];
+        f.lL[i] = (float)h.lL[i]; f.lR[i] = (float)h.lR[i]; f.liftL[i] = (float)h.liftL[i];
+        f.liftR[i] = (float)h.liftR[i]; f.w[i] = (float)h.w[i];
+    }
+    if (cudaMemcpyToSymbol(c_hex64, &d, sizeof(d), (p - 2) * sizeof(d)) != cudaSuccess) return -2;
+    if (cudaMemcpyToSymbol(c_hex32, &f, sizeof(f), (p - 2) * sizeof(f)) != cudaSuccess) return -2;
+    return 0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Point physics (Sec. 2.1): total flux f = f^e - f^v, viscous normal flux, Rusanov common flux
+// ---------------------------------------------------------------------------------------------
+
+// Physical total flux f[d][alpha] from the state u and its physical gradient g[alpha][d].
+// Returns false for a non-physical state (rho <= 0, p <= 0 or non-finite).
+template <typename T>
+__device__ __forceinline__ bool total_flux(const Phys<T> &ph, const T *u, const T (*g)[3], T (*f)[5])
+{
+    const T rho = u[0], ir = T(1) / rho;
+    const T v[3] = {u[1] * ir, u[2] * ir, u[3] * ir};
+    const T E = u[4];
+    const T p = ph.gm1 * (E - T(0.5) * (u[1] * v[0] + u[2] * v[1] + u[3] * v[2]));
+    T dv[3][3];  // dv[i][d] = d v_i / d x_d
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int d = 0; d < 3; d++) dv[i][d] = (g[1 + i][d] - v[i] * g[0][d]) * ir;
+    const T div = dv[0][0] + dv[1][1] + dv[2][2];
+    const T er = E * ir;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        T tau[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) tau[i] = ph.mu * (dv[i][d] + dv[d][i]) - (i == d ? T(2.0 / 3.0) * ph.mu * div : T(0));
+        // heat flux mu gamma/Pr [d(E/rho) - v.dv] = mu gamma/((gamma-1)Pr) d(p/rho)
+        const T phi = ph.heat * ((g[4][d] - er * g[0][d]) * ir - (v[0] * dv[0][d] + v[1] * dv[1][d] + v[2] * dv[2][d]));
+        f[d][0] = u[1 + d];
+        f[d][1] = u[1] * v[d] + (d == 0 ? p : T(0)) - tau[0];
+        f[d][2] = u[2] * v[d] + (d == 1 ? p : T(0)) - tau[1];
+        f[d][3] = u[3] * v[d] + (d == 2 ? p : T(0)) - tau[2];
+        f[d][4] = v[d] * (E + p) - (v[0] * tau[0] + v[1] * tau[1] + v[2] * tau[2] + phi);
+    }
+    return rho > T(0) && p > T(0) && isfinite(p) && isfinite(f[0][4] + f[1][4] + f[2][4]);
+}
+
+// n . f^v for variables 1..4 (the mass component is zero).
+template <typename T>
+__device__ __forceinline__ void viscous_normal_flux(const Phys<T> &ph, const T *u, const T (*g)[3], const T *n, T *fvn)
+{
+    const T rho = u[0], ir = T(1) / rho;
+    const T v[3] = {u[1] * ir, u[2] * ir, u[3] * ir};
+    T dv[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int d = 0; d < 3; d++) dv[i][d] = (g[1 + i][d] - v[i] * g[0][d]) * ir;
+    const T div = dv[0][0] + dv[1][1] + dv[2][2];
+    const T er = u[4] * ir;
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        T tau[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) tau[i] = ph.mu * (dv[i][d] + dv[d][i]) - (i == d ? T(2.0 / 3.0) * ph.mu * div : T(0));
+        const T phi = ph.heat * ((g[4][d] - er * g[0][d]) * ir - (v[0] * dv[0][d] + v[1] * dv[1][d] + v[2] * dv[2][d]));
+        acc[0] += n[d] * tau[0];
+        acc[1] += n[d] * tau[1];
+        acc[2] += n[d] * tau[2];
+        acc[3] += n[d] * (v[0] * tau[0] + v[1] * tau[1] + v[2] * tau[2] + phi);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; a++) fvn[a] = acc[a];
+}
+
+// Common physical normal flux along nL (Rusanov inviscid part, LDG viscous part and penalty):
+// F = 1/2 nL.(fe_L + fe_R) + 1/2 s (uL - uR) - [(1/2+beta) nL.fv_L + (1/2-beta) nL.fv_R] + tau (uL - uR)
+// fvL = nL.fv_L (vars 1..4), fvR = nR.fv_R with nR = -nL.
+template <typename T>
+__device__ __forceinline__ bool common_flux(const Phys<T> &ph, const T *uL, const T *uR, const T *fvL, const T *fvR,
+                                            const T *n, T *F)
+{
+    const T irL = T(1) / uL[0], irR = T(1) / uR[0];
+    const T vnL = (uL[1] * n[0] + uL[2] * n[1] + uL[3] * n[2]) * irL;
+    const T vnR = (uR[1] * n[0] + uR[2] * n[1] + uR[3] * n[2]) * irR;
+    const T pL = ph.gm1 * (uL[4] - T(0.5) * irL * (uL[1] * uL[1] + uL[2] * uL[2] + uL[3] * uL[3]));
+    const T pR = ph.gm1 * (uR[4] - T(0.5) * irR * (uR[1] * uR[1] + uR[2] * uR[2] + uR[3] * uR[3]));
+    const T cL = sqrt(ph.gamma * pL * irL), cR = sqrt(ph.gamma * pR * irR);
+    const T s = fmax(fabs(vnL) + cL, fabs(vnR) + cR);
+    T fnL[5], fnR[5];
+    fnL[0] = uL[0] * vnL; fnR[0] = uR[0] * vnR;
+#pragma unroll
+    for (int i = 0; i < 3; i++) { fnL[1 + i] = uL[1 + i] * vnL + pL * n[i]; fnR[1 + i] = uR[1 + i] * vnR + pR * n[i]; }
+    fnL[4] = vnL * (uL[4] + pL); fnR[4] = vnR * (uR[4] + pR);
+    const T wl = T(0.5) + ph.beta, wr = T(0.5) - ph.beta;
+#pragma unroll
+    for (int a = 0; a < 5; a++) {
+        const T du = uL[a] - uR[a];
+        const T fv = (a == 0) ? T(0) : (wl * fvL[a - 1] - wr * fvR[a - 1]);
+        F[a] = T(0.5) * (fnL[a] + fnR[a]) + T(0.5) * s * du - fv + ph.tau * du;
+    }
+    return pL > T(0) && pR > T(0) && uL[0] > T(0) && uR[0] > T(0) && isfinite(s);
+}
+
+// Physical outward unit normal and |n_s| (n_s = detJ J^-T n~) of hex face f.
+template <typename T>
+__device__ __forceinline__ void face_normal(const Geo<T> &g, int f, T *n, T &mag)
+{
+    const int d = f >> 1;
+    const T sgn = (f & 1) ? T(1) : T(-1);
+    T ns[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) ns[k] = g.det * sgn * g.Ji[3 * d + k];
+    mag = sqrt(ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]);
+    const T im = T(1) / mag;
+#pragma unroll
+    for (int k = 0; k < 3; k++) n[k] = ns[k] * im;
+}
+
+template <int N>
+__device__ __forceinline__ void face_line(int f, int local, int &base, int &stride)
+{
+    // solution-point index of the line through face point `local` of face f: base + i * stride
+    const int d = f >> 1, a = local % N, b = local / N;
+    if (d == 0) { base = N * a + N * N * b; stride = 1; }
+    else if (d == 1) { base = a + N * N * b; stride = N; }
+    else { base = a + N * b; stride = N * N; }
+}
+
+__device__ __forceinline__ void flag_status(int *status, bool ok)
+{
+    if (!ok) atomicOr(status, 1);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Fused phase A / unfused K1: disu, U^(f) = M0 U
+// ---------------------------------------------------------------------------------------------
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_disu(HexArgs<T> a)
+{
+    constexpr int N = P + 1, NU = N * N * N, NF = 6 * N * N;
+    const HexOps<T> &op = OPS<T>(P - 2);
+    const long long total = a.ne * FR_NV * NF;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(it % NF);
+        const long long ea = it / NF;
+        const int alpha = (int)(ea % FR_NV);
+        const long long e = ea / FR_NV;
+        const int f = s / (N * N), loc = s % (N * N);
+        int base, stride;
+        face_line<N>(f, loc, base, stride);
+        const T *u = a.U + a.u0 + (e * FR_NV + alpha) * NU + base;
+        const T *l = (f & 1) ? op.lR : op.lL;
+        T v = T(0);
+#pragma unroll
+        for (int i = 0; i < N; i++) v += l[i] * u[i * stride];
+        a.UF[alpha * a.nfpt + a.f0 + e * NF + s] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Fused phase B: the per-element volume group
+// ---------------------------------------------------------------------------------------------
+template <typename T, int P>
+struct HexSmem {
+    static constexpr int N = P + 1, M = P + 2, NU = N * N * N, NF = 6 * N * N, NQ = M * M * M;
+    static constexpr int T1 = 5 * M * N * N, T2 = 5 * M * M * N;
+    static constexpr int SIZE = 5 * NU + 15 * NU + 5 * NF + 20 * NQ + T1 + T2;
+};
+
+// Sum-factorised interpolation of 5 fields (src, stride NU) to quadrature points (dst, stride NQ).
+template <typename T, int P, int NT>
+__device__ __forceinline__ void interp_5(const HexOps<T> &op, const T *src, T *t1, T *t2, T *dst)
+{
+    constexpr int N = P + 1, M = P + 2, NU = N * N * N, NQ = M * M * M;
+    for (int it = threadIdx.x; it < 5 * N * N; it += NT) {  // x: (fc, j, k)
+        const int fc = it / (N * N), jk = it % (N * N);
+        T u[N];
+#pragma unroll
+        for (int i = 0; i < N; i++) u[i] = src[fc * NU + i + N * jk];
+#pragma unroll
+        for (int q = 0; q < M; q++) {
+            T v = T(0);
+#pragma unroll
+            for (int i = 0; i < N; i++) v += op.B[q][i] * u[i];
+            t1[fc * M * N * N + q + M * jk] = v;
+        }
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < 5 * M * N; it += NT) {  // y: (fc, qa, k)
+        const int fc = it / (M * N), r = it % (M * N), qa = r % M, k = r / M;
+        T u[N];
+#pragma unroll
+        for (int j = 0; j < N; j++) u[j] = t1[fc * M * N * N + qa + M * j + M * N * k];
+#pragma unroll
+        for (int q = 0; q < M; q++) {
+            T v = T(0);
+#pragma unroll
+            for (int j = 0; j < N; j++) v += op.B[q][j] * u[j];
+            t2[fc * M * M * N + qa + M * q + M * M * k] = v;
+        }
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < 5 * M * M; it += NT) {  // z: (fc, qa, qb)
+        const int fc = it / (M * M), ab = it % (M * M);
+        T u[N];
+#pragma unroll
+        for (int k = 0; k < N; k++) u[k] = t2[fc * M * M * N + ab + M * M * k];
+#pragma unroll
+        for (int q = 0; q < M; q++) {
+            T v = T(0);
+#pragma unroll
+            for (int k = 0; k < N; k++) v += op.B[q][k] * u[k];
+            dst[fc * NQ + ab + M * M * q] = v;
+        }
+    }
+    __syncthreads();
+}
+
+// Sum-factorised L2 projection of 5 fields from quadrature points (src, stride NQ) to solution
+// points (dst, stride NU).
+template <typename T, int P, int NT>
+__device__ __forceinline__ void project_5(const HexOps<T> &op, const T *src, T *t1, T *t2, T *dst)
+{
+    constexpr int N = P + 1, M = P + 2, NU = N * N * N, NQ = M * M * M;
+    for (int it = threadIdx.x; it < 5 * M * M; it += NT) {  // z: (fc, qa, qb) -> k
+        const int fc = it / (M * M), ab = it % (M * M);
+        T u[M];
+#pragma unroll
+        for (int c = 0; c < M; c++) u[c] = src[fc * NQ + ab + M * M * c];
+#pragma unroll
+        for (int k = 0; k < N; k++) {
+            T v = T(0);
+#pragma unroll
+            for (int c = 0; c < M; c++) v += op.Pj[k][c] * u[c];
+            t2[fc * M * M * N + ab + M * M * k] = v;
+        }
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < 5 * M * N; it += NT) {  // y: (fc, qa, k) -> j
+        const int fc = it / (M * N), r = it % (M * N), qa = r % M, k = r / M;
+        T u[M];
+#pragma unroll
+        for (int b = 0; b < M; b++) u[b] = t2[fc * M * M * N + qa + M * b + M * M * k];
+#pragma unroll
+        for (int j = 0; j < N; j++) {
+            T v = T(0);
+#pragma unroll
+            for (int b = 0; b < M; b++) v += op.Pj[j][b] * u[b];
+            t1[fc * M * N * N + qa + M * j + M * N * k] = v;
+        }
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < 5 * N * N; it += NT) {  // x: (fc, j, k) -> i
+        const int fc = it / (N * N), jk = it % (N * N);
+        T u[M];
+#pragma unroll
+        for (int q = 0; q < M; q++) u[q] = t1[fc * M * N * N + q + M * jk];
+#pragma unroll
+        for (int i = 0; i < N; i++) {
+            T v = T(0);
+#pragma unroll
+            for (int q = 0; q < M; q++) v += op.Pj[i][q] * u[q];
+            dst[fc * NU + i + N * jk] = v;
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T, int P, int NT>
+__global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
+{
+    using S = HexSmem<T, P>;
+    constexpr int N = S::N, M = S::M, NU = S::NU, NF = S::NF, NQ = S::NQ;
+    (void)M;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s_u = reinterpret_cast<T *>(smem_raw);
+    T *s_q = s_u + 5 * NU;
+    T *s_c = s_q + 15 * NU;
+    T *s_w = s_c + 5 * NF;
+    T *s_t1 = s_w + 20 * NQ;
+    T *s_t2 = s_t1 + S::T1;
+    const HexOps<T> &op = OPS<T>(P - 2);
+    const Phys<T> ph = a.ph;
+
+    for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
+        const Geo<T> g = a.geo[e];
+        const T *U = a.U + a.u0 + e * FR_NV * NU;
+        const long long gf0 = a.f0 + e * NF;
+        // 1. load the element's solution
+        for (int it = threadIdx.x; it < 5 * NU; it += NT) s_u[it] = U[it];
+        // 2. con_u: common solution at own flux points, C = (1/2 - beta) uL + (1/2 + beta) uR
+        for (int it = threadIdx.x; it < 5 * NF; it += NT) {
+            const int alpha = it / NF, s = it % NF;
+            const uint32_t pc = a.partner[gf0 + s];
+            const bool isL = (pc & FR_LFLAG) != 0;
+            const long long pg = pc & ~FR_LFLAG;
+            const T own = a.UF[alpha * a.nfpt + gf0 + s], oth = a.UF[alpha * a.nfpt + pg];
+            const T uL = isL ? own : oth, uR = isL ? oth : own;
+            s_c[it] = (T(0.5) - ph.beta) * uL + (T(0.5) + ph.beta) * uR;
+        }
+        __syncthreads();
+        // 3. tgradpcoru + tgradcoru along lines: q~ = Dh u + liftR C_R - liftL C_L
+        for (int it = threadIdx.x; it < 15 * N * N; it += NT) {
+            const int alpha = it / (3 * N * N), r = it % (3 * N * N), d = r / (N * N), loc = r % (N * N);
+            int base, stride;
+            face_line<N>(2 * d, loc, base, stride);
+            T u[N];
+#pragma unroll
+            for (int i = 0; i < N; i++) u[i] = s_u[alpha * NU + base + i * stride];
+            const T cL = s_c[alpha * NF + (2 * d) * N * N + loc], cR = s_c[alpha * NF + (2 * d + 1) * N * N + loc];
+#pragma unroll
+            for (int i = 0; i < N; i++) {
+                T v = op.liftR[i] * cR - op.liftL[i] * cL;
+#pragma unroll
+                for (int j = 0; j < N; j++) v += op.Dh[i][j] * u[j];
+                s_q[(alpha * 3 + d) * NU + base + i * stride] = v;
+            }
+        }
+        __syncthreads();
+        // 4. gradcoru: q = J^-T q~ (per point, all three components)
+        for (int it = threadIdx.x; it < 5 * NU; it += NT) {
+            const int alpha = it / NU, z = it % NU;
+            T *q = s_q + alpha * 3 * NU + z;
+            const T q0 = q[0], q1 = q[NU], q2 = q[2 * NU];
+#pragma unroll
+            for (int k = 0; k < 3; k++) q[k * NU] = g.Ji[k] * q0 + g.Ji[3 + k] * q1 + g.Ji[6 + k] * q2;
+        }
+        __syncthreads();
+        // 5. gradcoru_fpts + the viscous part of comm_flux: own-normal n.f^v at own flux points
+        for (int s = threadIdx.x; s < NF; s += NT) {
+            const int f = s / (N * N), loc = s % (N * N);
+            int base, stride;
+            face_line<N>(f, loc, base, stride);
+            const T *l = (f & 1) ? op.lR : op.lL;
+            T uf[5], qf[5][3];
+#pragma unroll
+            for (int alpha = 0; alpha < 5; alpha++) {
+                T v = T(0);
+#pragma unroll
+                for (int i = 0; i < N; i++) v += l[i] * s_u[alpha * NU + base + i * stride];
+                uf[alpha] = v;
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    T w = T(0);
+#pragma unroll
+                    for (int i = 0; i < N; i++) w += l[i] * s_q[(alpha * 3 + d) * NU + base + i * stride];
+                    qf[alpha][d] = w;
+                }
+            }
+            T n[3], mag;
+            face_normal(g, f, n, mag);
+            T fvn[4];
+            viscous_normal_flux(ph, uf, qf, n, fvn);
+#pragma unroll
+            for (int k = 0; k < 4; k++) a.FV[k * a.nfpt + gf0 + s] = fvn[k];
+        }
+        // 6. uqpts + gradcoru_qpts: 20 fields to quadrature points, 5 at a time
+        interp_5<T, P, NT>(op, s_u, s_t1, s_t2, s_w);
+#pragma unroll 1
+        for (int c = 0; c < 3; c++) interp_5<T, P, NT>(op, s_q + 5 * c * NU, s_t1, s_t2, s_w + (5 + 5 * c) * NQ);
+        // 7. tdisf: transformed flux at each quadrature point, in place
+        bool ok = true;
+        for (int q = threadIdx.x; q < NQ; q += NT) {
+            T u[5], gq[5][3], f[3][5];
+#pragma unroll
+            for (int alpha = 0; alpha < 5; alpha++) {
+                u[alpha] = s_w[alpha * NQ + q];
+#pragma unroll
+                for (int d = 0; d < 3; d++) gq[alpha][d] = s_w[(5 + alpha * 3 + d) * NQ + q];
+            }
+            ok &= total_flux(ph, u, gq, f);
+#pragma unroll
+            for (int alpha = 0; alpha < 5; alpha++)
+#pragma unroll
+                for (int d = 0; d < 3; d++)
+                    s_w[(alpha * 3 + d) * NQ + q] = g.det * (g.Ji[3 * d] * f[0][alpha] + g.Ji[3 * d + 1] * f[1][alpha] + g.Ji[3 * d + 2] * f[2][alpha]);
+        }
+        flag_status(a.status, ok);
+        __syncthreads();
+        // 8. tdivtpcorf, first factor: projection of the 15 transformed-flux fields (into s_q)
+#pragma unroll 1
+        for (int c = 0; c < 3; c++) project_5<T, P, NT>(op, s_w + 5 * c * NQ, s_t1, s_t2, s_q + 5 * c * NU);
+        // 9. tdivtpcorf, second factor: R~ = sum_d Dh_d F~_d, written to R (finished in phase C)
+        T *R = a.R + a.u0 + e * FR_NV * NU;
+        for (int it = threadIdx.x; it < 5 * NU; it += NT) {
+            const int alpha = it / NU, z = it % NU, i = z % N, j = (z / N) % N, k = z / (N * N);
+            const T *F = s_q + alpha * 3 * NU;
+            T v = T(0);
+#pragma unroll
+            for (int b = 0; b < N; b++) {
+                v += op.Dh[i][b] * F[b + N * j + N * N * k];
+                v += op.Dh[j][b] * F[NU + i + N * b + N * N * k];
+                v += op.Dh[k][b] * F[2 * NU + i + N * j + N * N * b];
+            }
+            R[it] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Fused phase C: comm_flux + tdivtconf + negdivconf per element
+// ---------------------------------------------------------------------------------------------
+template <typename T, int P, int NT>
+__global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
+{
+    constexpr int N = P + 1, NU = N * N * N, NF = 6 * N * N;
+    __shared__ T s_d[5 * NF];
+    const HexOps<T> &op = OPS<T>(P - 2);
+    const Phys<T> ph = a.ph;
+    for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
+        const Geo<T> g = a.geo[e];
+        const long long gf0 = a.f0 + e * NF;
+        bool ok = true;
+        for (int s = threadIdx.x; s < NF; s += NT) {
+            const int f = s / (N * N);
+            const uint32_t pc = a.partner[gf0 + s];
+            const bool isL = (pc & FR_LFLAG) != 0;
+            const long long pg = pc & ~FR_LFLAG, og = gf0 + s;
+            T uo[5], up[5], fvo[4], fvp[4];
+#pragma unroll
+            for (int k = 0; k < 5; k++) { uo[k] = a.UF[k * a.nfpt + og]; up[k] = a.UF[k * a.nfpt + pg]; }
+#pragma unroll
+            for (int k = 0; k < 4; k++) { fvo[k] = a.FV[k * a.nfpt + og]; fvp[k] = a.FV[k * a.nfpt + pg]; }
+            T n[3], mag;
+            face_normal(g, f, n, mag);
+            T nL[3] = {isL ? n[0] : -n[0], isL ? n[1] : -n[1], isL ? n[2] : -n[2]};
+            T F[5];
+            ok &= isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
+            const T sc = isL ? mag : -mag;
+#pragma unroll
+            for (int k = 0; k < 5; k++) s_d[k * NF + s] = sc * F[k];
+        }
+        flag_status(a.status, ok);
+        __syncthreads();
+        T *R = a.R + a.u0 + e * FR_NV * NU;
+        const T idet = T(-1) / g.det;
+        for (int it = threadIdx.x; it < 5 * NU; it += NT) {
+            const int alpha = it / NU, z = it % NU, i = z % N, j = (z / N) % N, k = z / (N * N);
+            const T *D = s_d + alpha * NF;
+            T v = R[it];
+            v += op.liftL[i] * D[0 * N * N + j + N * k] + op.liftR[i] * D[1 * N * N + j + N * k];
+            v += op.liftL[j] * D[2 * N * N + i + N * k] + op.liftR[j] * D[3 * N * N + i + N * k];
+            v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
+            R[it] = v * idet;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Unfused kernels K2..K13 (global intermediates)
+// ---------------------------------------------------------------------------------------------
+
+// K2 con_u: each pair visited once (from its L point); the common value is written to both points.
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_con_u(HexArgs<T> a)
+{
+    constexpr int N = P + 1, NF = 6 * N * N;
+    const long long total = a.ne * NF;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
+        const long long gl = a.f0 + it;
+        const uint32_t pc = a.partner[gl];
+        if (!(pc & FR_LFLAG)) continue;
+        const long long gr = pc & ~FR_LFLAG;
+#pragma unroll
+        for (int k = 0; k < 5; k++) {
+            const T c = (T(0.5) - a.ph.beta) * a.UF[k * a.nfpt + gl] + (T(0.5) + a.ph.beta) * a.UF[k * a.nfpt + gr];
+            a.CF[k * a.nfpt + gl] = c;
+            a.CF[k * a.nfpt + gr] = c;
+        }
+    }
+}
+
+// K3 tgradpcoru (mode 0): Q~ = (M4 - M6 M0) U;  K4 tgradcoru (mode 1): Q~ += M6 C.
+template <typename T, int P, int MODE>
+__global__ void __launch_bounds__(256) k_tgrad(HexArgs<T> a)
+{
+    constexpr int N = P + 1, NU = N * N * N, NF = 6 * N * N;
+    const HexOps<T> &op = OPS<T>(P - 2);
+    const long long total = a.ne * 15 * N * N;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
+        const long long e = it / (15 * N * N);
+        const int r = (int)(it % (15 * N * N)), alpha = r / (3 * N * N), d = (r / (N * N)) % 3, loc = r % (N * N);
+        int base, stride;
+        face_line<N>(2 * d, loc, base, stride);
+        T *q = a.Qu + ((e * 5 + alpha) * 3 + d) * NU + base;
+        if (MODE == 0) {
+            const T *u = a.U + a.u0 + (e * 5 + alpha) * NU + base;
+            T uu[N];
+#pragma unroll
+            for (int i = 0; i < N; i++) uu[i] = u[i * stride];
+#pragma unroll
+            for (int i = 0; i < N; i++) {
+                T v = T(0);
+#pragma unroll
+                for (int j = 0; j < N; j++) v += op.Dh[i][j] * uu[j];
+                q[i * stride] = v;
+            }
+        } else {
+            const long long g0 = a.f0 + e * NF;
+            const T cL = a.CF[alpha * a.nfpt + g0 + (2 * d) * N * N + loc];
+            const T cR = a.CF[alpha * a.nfpt + g0 + (2 * d + 1) * N * N + loc];
+#pragma unroll
+            for (int i = 0; i < N; i++) q[i * stride] += op.liftR[i] * cR - op.liftL[i] * cL;
+        }
+    }
+}
+
+// K5 gradcoru: q = J^-T q~
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_gradcoru(HexArgs<T> a)
+{
+    constexpr int N = P + 1, NU = N * N * N;
+    const long long total = a.ne * 5 * NU;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
+        const long long e = it / (5 * NU);
+        const int r = (int)(it % (5 * NU)), alpha = r / NU, z = r % NU;
+        const Geo<T> &g = a.geo[e];
+        T *q = a.Qu + (e * 5 + alpha) * 3 * NU + z;
+        const T q0 = q[0], q1 = q[NU], q2 = q[2 * NU];
+#pragma unroll
+        for (int k = 0; k < 3; k++) q[k * NU] = g.Ji[k] * q0 + g.Ji[3 + k] * q1 + g.Ji[6 + k] * q2;
+    }
+}
+
+// K6 gradcoru_fpts: Q^(f) = (I3 x M0) Q^(u)
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_gradcoru_fpts(HexArgs<T> a)
+{
+    constexpr int N = P + 1, NU = N * N * N, NF = 6 * N * N;
+    const HexOps<T> &op = OPS<T>(P - 2);
+    const long long total = a.ne * 15 * NF;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
+        const long long e = it / (15 * NF);
+        const int r = (int)(it % (15 * NF)), ad = r / NF, s = r % NF, f = s / (N * N);
+        int base, stride;
+        face_line<N>(f, s % (N * N), base, stride);
+        const T *q = a.Qu + (e * 15 + ad) * NU + base;
+        const T *l = (f & 1) ? op.lR : op.lL;
+        T v = T(0);
+#pragma unroll
+        for (int i = 0; i < N; i++) v += l[i] * q[i * stride];
+        a.QF[ad * a.nfpt + a.f0 + e * NF + s] = v;
+    }
+}
+
+// K7 gradcoru_qpts (15 fields, Qu -> QQ) and K8 uqpts (5 fields, U -> UQ); one CTA per element.
+template <typename T, int P, int NT, int NFLD>
+__global__ void __launch_bounds__(NT) k_qpts(HexArgs<T> a)
+{
+    constexpr int N = P + 1, M = P + 2, NU = N * N * N, NQ = M * M * M;
+    __shared__ T s_src[5 * NU], s_t1[5 * M * N * N], s_t2[5 * M * M * N], s_dst[5 * NQ];
+    const HexOps<T> &op = OPS<T>(P - 2);
+    for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
+        for (int c = 0; c < NFLD / 5; c++) {
+            const T *src = (NFLD == 5) ? a.U + a.u0 + e * 5 * NU : a.Qu + (e * 15 + 5 * c) * NU;
+            T *dst = (NFLD == 5) ? a.UQ + e * 5 * NQ : a.QQ + (e * 15 + 5 * c) * NQ;
+            for (int it = threadIdx.x; it < 5 * NU; it += NT) s_src[it] = src[it];
+            __syncthreads();
+            interp_5<T, P, NT>(op, s_src, s_t1, s_t2, s_dst);
+            for (int it = threadIdx.x; it < 5 * NQ; it += NT) dst[it] = s_dst[it];
+            __syncthreads();
+        }
+    }
+}
+
+// K9 tdisf: QQ <- detJ J^-1 f(UQ, QQ), in place
+template <typename T, int P>
+__global__ void __launch_bounds__(128) k_tdisf(HexArgs<T> a)
+{
+    constexpr int M = P + 2, NQ = M * M * M;
+    const long long total = a.ne * NQ;
+    bool ok = true;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
+        const long long e = it / NQ;
+        const int q = (int)(it % NQ);
+        const Geo<T> &g = a.geo[e];
+        T u[5], gq[5][3], f[3][5];
+        T *Q = a.QQ + e * 15 * NQ + q;
+#pragma unroll
+        for (int alpha = 0; alpha < 5; alpha++) {
+            u[alpha] = a.UQ[(e * 5 + alpha) * NQ + q];
+#pragma unroll
+            for (int d = 0; d < 3; d++) gq[alpha][d] = Q[(alpha * 3 + d) * NQ];
+        }
+        ok &= total_flux(a.ph, u, gq, f);
+#pragma unroll
+        for (int alpha = 0; alpha < 5; alpha++)
+#pragma unroll
+            for (int d = 0; d < 3; d++)
+                Q[(alpha * 3 + d) * NQ] = g.det * (g.Ji[3 * d] * f[0][alpha] + g.Ji[3 * d + 1] * f[1][alpha] + g.Ji[3 * d + 2] * f[2][alpha]);
+    }
+    flag_status(a.status, ok);
+}
+
+// K10 tdivtpcorf: F~u = M9 F~q (written to Qu), R~ = (M1 - M3 M2) F~u (written to Rt)
+template <typename T, int P, int NT>
+__global__ void __launch_bounds__(NT) k_tdivtpcorf(HexArgs<T> a)
+{
+    constexpr int N = P + 1, M = P + 2, NU = N * N * N, NQ = M * M * M;
+    __shared__ T s_src[5 * NQ], s_t1[5 * M * N * N], s_t2[5 * M * M * N], s_F[15 * NU];
+    const HexOps<T> &op = OPS<T>(P - 2);
+    for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
+        for (int c = 0; c < 3; c++) {
+            const T *src = a.QQ + (e * 15 + 5 * c) * NQ;
+            for (int it = threadIdx.x; it < 5 * NQ; it += NT) s_src[it] = src[it];
+            __syncthreads();
+            project_5<T, P, NT>(op, s_src, s_t1, s_t2, s_F + 5 * c * NU);
+        }
+        for (int it = threadIdx.x; it < 15 * NU; it += NT) a.Qu[e * 15 * NU + it] = s_F[it];
+        for (int it = threadIdx.x; it < 5 * NU; it += NT) {
+            const int alpha = it / NU, z = it % NU, i = z % N, j = (z / N) % N, k = z / (N * N);
+            const T *F = s_F + alpha * 3 * NU;
+            T v = T(0);
+#pragma unroll
+            for (int b = 0; b < N; b++) {
+                v += op.Dh[i][b] * F[b + N * j + N * N * k];
+                v += op.Dh[j][b] * F[NU + i + N * b + N * N * k];
+                v += op.Dh[k][b] * F[2 * NU + i + N * j + N * N * b];
+            }
+            a.Rt[e * 5 * NU + it] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// K11 comm_flux: per pair (from its L point), D~_L = |n_sL| F, D~_R = -|n_sR| F
+template <typename T, int P>
+__global__ void __launch_bounds__(128) k_comm_flux(HexArgs<T> a)
+{
+    constexpr int N = P + 1, NF = 6 * N * N;
+    const long long total = a.ne * NF;
+    bool ok = true;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
+        const long long gl = a.f0 + it;
+        const uint32_t pc = a.partner[gl];
+        if (!(pc & FR_LFLAG)) continue;
+        const long long gr = pc & ~FR_LFLAG;
+        const long long e = it / NF;
+        const int f = (int)(it % NF) / (N * N);
+        T uL[5], uR[5], qL[5][3], qR[5][3];
+#pragma unroll
+        for (int k = 0; k < 5; k++) {
+            uL[k] = a.UF[k * a.nfpt + gl]; uR[k] = a.UF[k * a.nfpt + gr];
+#pragma unroll
+            for (int d = 0; d < 3; d++) { qL[k][d] = a.QF[(k * 3 + d) * a.nfpt + gl]; qR[k][d] = a.QF[(k * 3 + d) * a.nfpt + gr]; }
+        }
+        T n[3], magL;
+        face_normal(a.geo[e], f, n, magL);
+        // the R side's |n_s| comes from its own element (global flux point -> element of this handle's
+        // hex blocks; the unfused form supports single-block hex meshes)
+        const long long eR = (gr - a.f0) / NF;
+        const int fR = (int)((gr - a.f0) % NF) / (N * N);
+        T nR[3], magR;
+        face_normal(a.geo[eR], fR, nR, magR);
+        T fvL[4], fvR[4], mnR[3] = {-n[0], -n[1], -n[2]};
+        viscous_normal_flux(a.ph, uL, qL, n, fvL);
+        viscous_normal_flux(a.ph, uR, qR, mnR, fvR);
+        T F[5];
+        ok &= common_flux(a.ph, uL, uR, fvL, fvR, n, F);
+#pragma unroll
+        for (int k = 0; k < 5; k++) { a.DF[k * a.nfpt + gl] = magL * F[k]; a.DF[k * a.nfpt + gr] = -magR * F[k]; }
+    }
+    flag_status(a.status, ok);
+}
+
+// K12 tdivtconf (R~ += M3 D) and K13 negdivconf (R = -R~/detJ); MODE 0 = K12, 1 = K13
+template <typename T, int P, int MODE>
+__global__ void __launch_bounds__(256) k_tdivtconf(HexArgs<T> a)
+{
+    constexpr int N = P + 1, NU = N * N * N, NF = 6 * N * N;
+    const HexOps<T> &op = OPS<T>(P - 2);
+    const long long total = a.ne * 5 * NU;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
+        const long long e = it / (5 * NU);
+        const int r = (int)(it % (5 * NU)), alpha = r / NU, z = r % NU, i = z % N, j = (z / N) % N, k = z / (N * N);
+        if (MODE == 0) {
+            const T *D = a.DF + alpha * a.nfpt + a.f0 + e * NF;
+            T v = a.Rt[it];
+            v += op.liftL[i] * D[0 * N * N + j + N * k] + op.liftR[i] * D[1 * N * N + j + N * k];
+            v += op.liftL[j] * D[2 * N * N + i + N * k] + op.liftR[j] * D[3 * N * N + i + N * k];
+            v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
+            a.Rt[it] = v;
+        } else {
+            a.R[a.u0 + it] = -a.Rt[it] / a.geo[e].det;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------------------------
+static int grid_for(long long work, int threads)
+{
+    long long g = (work + threads - 1) / threads;
+    if (g > 152LL * 64) g = 152LL * 64;
+    return (int)(g < 1 ? 1 : g);
+}
+
+static int grid_elems(long long ne, int per_sm)
+{
+    long long g = ne;
+    if (g > 152LL * per_sm * 8) g = 152LL * per_sm * 8;
+    return (int)(g < 1 ? 1 : g);
+}
+
+template <typename T, int P>
+static int fused_phase(int phase, const HexArgs<T> &a, cudaStream_t s)
+{
+    constexpr int N = P + 1, NF = 6 * N * N;
+    if (a.ne == 0) return 0;
+    if (phase == 0) {
+        k_disu<T, P><<<grid_for(a.ne * 5 * NF, 256), 256, 0, s>>>(a);
+    } else if (phase == 1) {
+        constexpr int NT = 128;
+        const size_t smem = HexSmem<T, P>::SIZE * sizeof(T);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_fused_B<T, P, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr = true;
+        }
+        k_fused_B<T, P, NT><<<grid_elems(a.ne, 8), NT, smem, s>>>(a);
+    } else {
+        k_fused_C<T, P, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
+    }
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename T, int P>
+static int unfused_kernel(int k, const HexArgs<T> &a, cudaStream_t s)
+{
+    constexpr int N = P + 1, NU = N * N * N, NF = 6 * N * N, NQ = (P + 2) * (P + 2) * (P + 2);
+    if (a.ne == 0) return 0;
+    switch (k) {
+    case 1: k_disu<T, P><<<grid_for(a.ne * 5 * NF, 256), 256, 0, s>>>(a); break;
+    case 2: k_con_u<T, P><<<grid_for(a.ne * NF, 256), 256, 0, s>>>(a); break;
+    case 3: k_tgrad<T, P, 0><<<grid_for(a.ne * 15 * N * N, 256), 256, 0, s>>>(a); break;
+    case 4: k_tgrad<T, P, 1><<<grid_for(a.ne * 15 * N * N, 256), 256, 0, s>>>(a); break;
+    case 5: k_gradcoru<T, P><<<grid_for(a.ne * 5 * NU, 256), 256, 0, s>>>(a); break;
+    case 6: k_gradcoru_fpts<T, P><<<grid_for(a.ne * 15 * NF, 256), 256, 0, s>>>(a); break;
+    case 7: k_qpts<T, P, 128, 15><<<grid_elems(a.ne, 8), 128, 0, s>>>(a); break;
+    case 8: k_qpts<T, P, 128, 5><<<grid_elems(a.ne, 8), 128, 0, s>>>(a); break;
+    case 9: k_tdisf<T, P><<<grid_for(a.ne * NQ, 128), 128, 0, s>>>(a); break;
+    case 10: k_tdivtpcorf<T, P, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a); break;
+    case 11: k_comm_flux<T, P><<<grid_for(a.ne * NF, 128), 128, 0, s>>>(a); break;
+    case 12: k_tdivtconf<T, P, 0><<<grid_for(a.ne * 5 * NU, 256), 256, 0, s>>>(a); break;
+    case 13: k_tdivtconf<T, P, 1><<<grid_for(a.ne * 5 * NU, 256), 256, 0, s>>>(a); break;
+    default: return -2;
+    }
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename T>
+int hex_fused_phase(int p, int phase, const HexArgs<T> &a, cudaStream_t s)
+{
+    switch (p) {
+    case 3: return fused_phase<T, 3>(phase, a, s);
+    case 4: return fused_phase<T, 4>(phase, a, s);
+    default: return -3;
+    }
+}
+
+template <typename T>
+int hex_unfused_kernel(int p, int k, const HexArgs<T> &a, cudaStream_t s)
+{
+    switch (p) {
+    case 3: return unfused_kernel<T, 3>(k, a, s);
+    case 4: return unfused_kernel<T, 4>(k, a, s);
+    default: return -3;
+    }
+}
+
+template int hex_fused_phase<double>(int, int, const HexArgs<double> &, cudaStream_t);
+template int hex_fused_phase<float>(int, int, const HexArgs<float> &, cudaStream_t);
+template int hex_unfused_kernel<double>(int, int, const HexArgs<double> &, cudaStream_t);
+template int hex_unfused_kernel<float>(int, int, const HexArgs<float> &, cudaStream_t);

@@ -1,0 +1,107 @@
+// fr_internal.h -- internal types of the GB300 flux-reconstruction library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "../../include/fr_gb300.h"
+
+#define FR_NV 5
+#define FR_MAXN 6          // max 1D solution points (p <= 5)
+#define FR_MAXM 7          // max 1D quadrature points
+#define FR_LFLAG 0x80000000u
+
+// ---------------------------------------------------------------------------------------------
+// Host-side basis construction (fr_basis.cpp)
+// ---------------------------------------------------------------------------------------------
+namespace frb {
+
+// Gauss-Legendre nodes (ascending) and weights on [-1,1], from the eigen-decomposition of the
+// Jacobi matrix of the Legendre recurrence (Golub-Welsch).
+void gauss_legendre(int n, double *x, double *w);
+
+// 1D operators of a hex element of order p with m quadrature points per direction.
+struct Hex1D {
+    int n, m;
+    double x[FR_MAXN], w[FR_MAXN];          // solution points / GL weights
+    double xq[FR_MAXM], wq[FR_MAXM];        // quadrature points / weights
+    double B[FR_MAXM][FR_MAXN];             // interpolation solution -> quadrature: l_i(xq_a)
+    double Pj[FR_MAXN][FR_MAXM];            // L2 projection quadrature -> solution
+    double D[FR_MAXN][FR_MAXN];             // derivative: l_i'(x_a)
+    double Dh[FR_MAXN][FR_MAXN];            // corrected derivative D - liftR lR^T + liftL lL^T
+    double lL[FR_MAXN], lR[FR_MAXN];        // l_i(-1), l_i(+1)
+    double liftL[FR_MAXN], liftR[FR_MAXN];  // DG-equivalent lift l_i(-+1)/w_i
+};
+int hex1d(int p, int m, Hex1D &h);
+
+}  // namespace frb
+
+// ---------------------------------------------------------------------------------------------
+// Device-side operator tables (constant memory, one slot per hex order p = 2, 3, 4)
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+struct HexOps {
+    T B[FR_MAXM][FR_MAXN];
+    T Pj[FR_MAXN][FR_MAXM];
+    T Dh[FR_MAXN][FR_MAXN];
+    T lL[FR_MAXN], lR[FR_MAXN];
+    T liftL[FR_MAXN], liftR[FR_MAXN];
+    T w[FR_MAXN];
+};
+
+// Physical constants of an instance, in the compute precision.
+template <typename T>
+struct Phys {
+    T gamma, gm1, mu, beta, tau;
+    T heat;       // mu gamma / ((gamma - 1) Pr)
+};
+
+// Geometry of one affine element: inverse Jacobian (row-major dxi_i/dx_j) and its determinant.
+template <typename T>
+struct Geo {
+    T Ji[9];
+    T det;
+};
+
+// One block of elements of one type and order inside one instance.
+struct Block {
+    int inst;                 // instance index
+    int type;                 // 0 hex, 1 prism
+    int p, m;                 // order, 1D quadrature points
+    int nu, nf;               // points per element, flux points per element
+    long long ne;             // elements
+    long long elem0;          // first global element
+    long long u0;             // first value in U
+    long long f0;             // first global flux point
+};
+
+// Everything a hex kernel of one element block needs. Face arrays are var-major over the global
+// flux-point index of the whole handle: A[var * nfpt + gfpt].
+template <typename T>
+struct HexArgs {
+    long long ne;             // elements in the block
+    long long u0;             // first value of the block in U/R
+    long long f0;             // first global flux point of the block
+    long long nfpt;           // flux points of the whole handle
+    const Geo<T> *geo;        // [ne], block-local
+    const uint32_t *partner;  // [nfpt] partner gfpt, FR_LFLAG set when this point is the L side
+    Phys<T> ph;
+    const T *U;               // state, block starts at U + u0
+    T *R;                     // RHS
+    T *UF;                    // [5][nfpt] solution at flux points
+    T *FV;                    // fused: [4][nfpt] own-normal viscous flux n.fv (vars 1..4)
+    T *CF;                    // unfused: [5][nfpt] common solution
+    T *QF;                    // unfused: [15][nfpt] gradient at flux points
+    T *DF;                    // unfused: [5][nfpt] transformed common normal flux
+    T *Qu;                    // unfused: [elem][5][3][nu] gradient, later projected flux
+    T *UQ;                    // unfused: [elem][5][nq] solution at quadrature points
+    T *QQ;                    // unfused: [elem][5][3][nq] gradient, later transformed flux, at qpts
+    T *Rt;                    // unfused: [elem][5][nu] R~
+    int *status;              // device status word (bit 0: non-physical state)
+};
+
+// Launchers (fr_hex.cu). phase: 0 = A (face solution), 1 = B (volume group), 2 = C (interfaces).
+template <typename T> int hex_fused_phase(int p, int phase, const HexArgs<T> &a, cudaStream_t s);
+// kernel: 1..13 in the paper's order (disu .. negdivconf)
+template <typename T> int hex_unfused_kernel(int p, int kernel, const HexArgs<T> &a, cudaStream_t s);
+int hex_upload_ops(int p, int m, const frb::Hex1D &h);

@@ -1,0 +1,225 @@
+"""ctypes binding of the C ABI in include/fr_gb300.h (argument marshalling only).
+
+Every step of the RHS and of RK4 runs in the CUDA kernels of libfrgb300.so; there is no CPU path.
+Device buffers are torch CUDA tensors; the stream is torch's current stream unless given.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfrgb300.so")
+
+FR_OK, FR_EINVAL, FR_ENOMEM, FR_ECUDA, FR_EMESH, FR_ETIMEOUT, FR_ENONPHYS, FR_EUNSUPPORTED = range(8)
+STATUS_NAMES = ["FR_OK", "FR_EINVAL", "FR_ENOMEM", "FR_ECUDA", "FR_EMESH", "FR_ETIMEOUT", "FR_ENONPHYS",
+                "FR_EUNSUPPORTED"]
+PRECISIONS = {"fp64": 0, "fp32": 1, "mixed_bf16": 2, "mixed_fp16": 3}
+FORMS = {"fused": 0, "unfused": 1}
+
+
+class FRError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("Pr", C.c_double), ("mu", C.c_double), ("beta", C.c_double),
+                ("tau", C.c_double), ("p", C.c_int), ("nq1d", C.c_int), ("tri_strength", C.c_int),
+                ("prec", C.c_int), ("rusanov_mode", C.c_int)]
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("n_hex", C.c_int), ("n_pri", C.c_int), ("n_verts", C.c_int), ("verts", C.POINTER(C.c_double)),
+                ("hex_v", C.POINTER(C.c_int)), ("pri_v", C.POINTER(C.c_int)), ("period", C.c_double * 3)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads the in-tree CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library {LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, dp, llp = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)
+        sig = {
+            "fr_mesh_create": ([C.POINTER(C.POINTER(MeshDesc)), C.c_int, C.POINTER(Params), C.POINTER(vp)], C.c_int),
+            "fr_destroy": ([vp], C.c_int),
+            "fr_set_form": ([vp, C.c_int], C.c_int),
+            "fr_set_debug": ([vp, C.c_int], C.c_int),
+            "fr_rhs": ([vp, vp, vp, vp], C.c_int),
+            "fr_rhs_host": ([vp, vp, vp, vp], C.c_int),
+            "fr_rk4_step": ([vp, vp, C.c_double, C.c_int, vp], C.c_int),
+            "fr_rk4_step_host": ([vp, vp, C.c_double, C.c_int, vp], C.c_int),
+            "fr_sync_status": ([vp, vp], C.c_int),
+            "fr_mesh_info": ([vp, llp], C.c_int),
+            "fr_num_values": ([vp], C.c_longlong),
+            "fr_sol_coords": ([vp, dp], C.c_int),
+            "fr_instance_offsets": ([vp, llp], C.c_int),
+            "fr_diagnostics": ([vp, vp, vp, dp, vp], C.c_int),
+            "fr_stage": ([vp, C.c_int, dp, C.c_longlong, llp], C.c_int),
+            "fr_last_error": ([], C.c_char_p),
+            "fr_set_timing": ([vp, C.c_int], C.c_int),
+            "fr_kernel_times": ([vp, C.POINTER(C.c_double), llp, C.c_int], C.c_int),
+            "fr_probe_fma": ([dp, vp], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes, fn.restype = args, res
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != FR_OK:
+        raise FRError(st, lib().fr_last_error().decode())
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def make_params(p=3, gamma=1.4, Pr=0.71, mu=1.0 / 1600, beta=0.5, tau=0.1, prec="fp64", nq1d=0, tri_strength=0):
+    return Params(gamma, Pr, mu, beta, tau, p, nq1d, tri_strength, PRECISIONS[prec], 0)
+
+
+class FRMesh:
+    """One handle over one or more independent mesh instances (batched ensemble when several)."""
+
+    def __init__(self, meshes: Sequence[dict] | dict, params: Sequence[Params] | Params):
+        if isinstance(meshes, dict):
+            meshes = [meshes]
+        if isinstance(params, Params):
+            params = [params] * len(meshes)
+        assert len(params) == len(meshes)
+        self._keep = []
+        descs = []
+        for m in meshes:
+            verts = np.ascontiguousarray(m["verts"], dtype=np.float64)
+            hex_v = np.ascontiguousarray(m.get("hex_v", np.zeros((0, 8))), dtype=np.int32)
+            pri_v = np.ascontiguousarray(m.get("pri_v", np.zeros((0, 6))), dtype=np.int32)
+            self._keep += [verts, hex_v, pri_v]
+            d = MeshDesc(hex_v.shape[0], pri_v.shape[0], verts.shape[0], verts.ctypes.data_as(C.POINTER(C.c_double)),
+                         hex_v.ctypes.data_as(C.POINTER(C.c_int)), pri_v.ctypes.data_as(C.POINTER(C.c_int)),
+                         (C.c_double * 3)(*m.get("period", (0.0, 0.0, 0.0))))
+            descs.append(d)
+        arr = (C.POINTER(MeshDesc) * len(descs))(*[C.pointer(d) for d in descs])
+        self._descs = descs
+        prm = (Params * len(params))(*params)
+        h = C.c_void_p()
+        _check(lib().fr_mesh_create(arr, len(descs), prm, C.byref(h)))
+        self.h = h
+        self.prec = params[0].prec
+        self.n_inst = len(meshes)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().fr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- properties -------------------------------------------------------------------------
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.prec == 0 else torch.float32
+
+    def info(self):
+        a = (C.c_longlong * 7)()
+        _check(lib().fr_mesh_info(self.h, a))
+        keys = ["elements", "values", "flux_points", "pairs", "instances", "launches_per_rhs", "device_bytes"]
+        return dict(zip(keys, list(a)))
+
+    @property
+    def num_values(self) -> int:
+        return int(lib().fr_num_values(self.h))
+
+    def instance_offsets(self):
+        a = (C.c_longlong * (self.n_inst + 1))()
+        _check(lib().fr_instance_offsets(self.h, a))
+        return list(a)
+
+    def sol_coords(self) -> np.ndarray:
+        out = np.zeros((self.num_values // 5, 3))
+        _check(lib().fr_sol_coords(self.h, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def set_form(self, form: str):
+        _check(lib().fr_set_form(self.h, FORMS[form]))
+
+    def set_debug(self, flags: int):
+        _check(lib().fr_set_debug(self.h, flags))
+
+    # -- compute ----------------------------------------------------------------------------
+    def _check_tensor(self, t, dtype=None):
+        assert t.is_cuda and t.is_contiguous() and t.numel() == self.num_values, "bad tensor"
+        assert t.dtype == (dtype or self.dtype), f"expected {dtype or self.dtype}, got {t.dtype}"
+
+    def rhs(self, U, R, stream=None):
+        self._check_tensor(U)
+        self._check_tensor(R)
+        _check(lib().fr_rhs(self.h, C.c_void_p(U.data_ptr()), C.c_void_p(R.data_ptr()), _stream_ptr(stream)))
+
+    def rhs_host(self, U: np.ndarray, R: np.ndarray, stream=None):
+        dt = np.float64 if self.prec == 0 else np.float32
+        assert U.dtype == dt and R.dtype == dt and U.flags.c_contiguous and R.flags.c_contiguous
+        _check(lib().fr_rhs_host(self.h, C.c_void_p(U.ctypes.data), C.c_void_p(R.ctypes.data), _stream_ptr(stream)))
+
+    def rk4_step(self, U, dt: float, nsteps: int = 1, stream=None):
+        import torch
+        self._check_tensor(U, torch.float64)
+        _check(lib().fr_rk4_step(self.h, C.c_void_p(U.data_ptr()), float(dt), int(nsteps), _stream_ptr(stream)))
+
+    def rk4_step_host(self, U: np.ndarray, dt: float, nsteps: int = 1, stream=None):
+        assert U.dtype == np.float64 and U.flags.c_contiguous
+        _check(lib().fr_rk4_step_host(self.h, C.c_void_p(U.ctypes.data), float(dt), int(nsteps), _stream_ptr(stream)))
+
+    def sync_status(self, stream=None):
+        _check(lib().fr_sync_status(self.h, _stream_ptr(stream)))
+
+    def diagnostics(self, U, R=None, stream=None):
+        out = np.zeros(8 * self.n_inst)
+        _check(lib().fr_diagnostics(self.h, C.c_void_p(U.data_ptr()), C.c_void_p(R.data_ptr() if R is not None else 0),
+                                    out.ctypes.data_as(C.POINTER(C.c_double)), _stream_ptr(stream)))
+        res = []
+        for i in range(self.n_inst):
+            o = out[8 * i:8 * i + 8]
+            res.append(dict(volume=o[0], Ek=o[1], eps=o[2], sums=o[3:8].copy()))
+        return res
+
+    def set_timing(self, on: bool):
+        _check(lib().fr_set_timing(self.h, int(on)))
+
+    def kernel_times(self, n_ids: int = 32):
+        """{kernel id: (total ms, launches)} for launches since the last call."""
+        ms = (C.c_double * n_ids)()
+        cnt = (C.c_longlong * n_ids)()
+        _check(lib().fr_kernel_times(self.h, ms, cnt, n_ids))
+        return {i: (ms[i], cnt[i]) for i in range(n_ids) if cnt[i]}
+
+    def stage(self, which: int) -> np.ndarray:
+        n = C.c_longlong(0)
+        _check(lib().fr_stage(self.h, which, None, 0, C.byref(n)))
+        out = np.zeros(n.value)
+        _check(lib().fr_stage(self.h, which, out.ctypes.data_as(C.POINTER(C.c_double)), n.value, C.byref(n)))
+        return out
+
+
+def probe_fma(stream=None):
+    out = np.zeros(2)
+    _check(lib().fr_probe_fma(out.ctypes.data_as(C.POINTER(C.c_double)), _stream_ptr(stream)))
+    return dict(fp64_gflops=out[0], fp32_gflops=out[1])

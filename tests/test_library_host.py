@@ -1,0 +1,113 @@
+"""CPU-only checks of the GPU library's host side and of the shared input generators.
+
+No compute call reaches a GPU here: the library is built, loaded and probed for its exported
+symbols; mesh validation errors are raised by host code before any device work.
+"""
+import ctypes as C
+import re
+import shutil
+
+import numpy as np
+import pytest
+
+from paper_2401_06132_gb300 import fr, workloads as W
+
+HEADER = "include/fr_gb300.h"
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not __import__("os").path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2401_06132_gb300 import build as B
+    B.build()
+    return fr.lib()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    hdr = open(os.path.join(root, HEADER)).read()
+    names = re.findall(r"^\s*(?:fr_status|long long|const char \*)\s*\*?\s*(fr_\w+)\s*\(", hdr, re.M)
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def _create(mesh, **kw):
+    return fr.FRMesh(mesh, fr.make_params(**kw))
+
+
+def test_host_validation_rejects_bad_meshes_before_any_device_work(lib):
+    # non-periodic box: boundary faces have no partner
+    with pytest.raises(fr.FRError) as e:
+        _create(W.box_hex_mesh(2, periodic=False))
+    assert e.value.status == fr.FR_EMESH
+    # non-affine hex: move one corner
+    mesh = W.box_hex_mesh(2)
+    mesh["verts"] = mesh["verts"].copy()
+    mesh["verts"][13] += np.array([0.1, 0.0, 0.0])
+    with pytest.raises(fr.FRError) as e:
+        _create(mesh)
+    assert e.value.status == fr.FR_EUNSUPPORTED
+    # inverted element: swap two corners of the tensor order
+    mesh = W.box_hex_mesh(1)
+    mesh["hex_v"] = mesh["hex_v"][:, [1, 0, 3, 2, 5, 4, 7, 6]].copy()
+    with pytest.raises(fr.FRError) as e:
+        _create(mesh)
+    assert e.value.status == fr.FR_EMESH
+    # vertex id out of range
+    mesh = W.box_hex_mesh(1)
+    mesh["hex_v"] = mesh["hex_v"].copy()
+    mesh["hex_v"][0, 0] = 10 ** 6
+    with pytest.raises(fr.FRError) as e:
+        _create(mesh)
+    assert e.value.status == fr.FR_EMESH
+    # unsupported order / quadrature
+    with pytest.raises(fr.FRError) as e:
+        _create(W.box_hex_mesh(1), p=7)
+    assert e.value.status == fr.FR_EUNSUPPORTED
+    with pytest.raises(fr.FRError) as e:
+        _create(W.box_hex_mesh(1), p=3, nq1d=8)
+    assert e.value.status == fr.FR_EUNSUPPORTED
+    with pytest.raises(fr.FRError) as e:
+        _create(W.box_hex_mesh(1), gamma=0.9)
+    assert e.value.status == fr.FR_EINVAL
+
+
+def test_splitmix64_reference_vectors():
+    """SplitMix64 (Steele, Lea, Flood 2014; Vigna's reference C code) seeded with 1234567."""
+    expect = [6457827717110365317, 3203168211198807973, 9817491932198370423, 4593380528125082431,
+              16408922859458223821]
+    got = [int(v) for v in W.splitmix64(1234567, np.arange(5))]
+    assert got == expect
+
+
+def test_uniform_range_and_mean():
+    u = W.uniform_pm1(W.SEED, np.arange(200000))
+    assert u.min() >= -1.0 and u.max() < 1.0 and abs(u.mean()) < 5e-3
+
+
+def test_mesh_generators_counts_and_volume():
+    for N in (1, 3, 8):
+        m = W.box_hex_mesh(N)
+        assert m["hex_v"].shape == (N ** 3, 8)
+        m = W.sheared_box_mesh(N)
+        assert m["hex_v"].shape == (N ** 3, 8)
+    m = W.mixed_box_mesh(4)
+    assert m["hex_v"].shape == (32, 8) and m["pri_v"].shape == (64, 6)
+
+
+def test_ensemble_draws_ranges():
+    d = W.ensemble_draws(64)
+    assert len(d) == 64
+    assert {x["edge"] for x in d} <= {8, 12, 16, 20, 24} and {x["p"] for x in d} <= {3, 4}
+    assert all(0.05 <= x["mach"] <= 0.2 and 400 <= x["re"] <= 3200 for x in d)
+
+
+def test_tgv_state_layout():
+    xyz = np.random.default_rng(0).uniform(-3, 3, size=(2 * 64, 3))
+    U = W.tgv_state(xyz, [(2, 64)])
+    V = W.tgv_conserved(xyz)
+    assert U.shape == (2 * 5 * 64,)
+    np.testing.assert_array_equal(U.reshape(2, 5, 64)[1, 4], V[4, 64:])
