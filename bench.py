@@ -118,7 +118,7 @@ def oracle_sample(seconds=12.0, n_edge=16, threads=None):
     from paper_2401_06132_gb300 import workloads as W
     threads = threads or os.cpu_count() or 1
     mesh = W.box_hex_mesh(n_edge)
-    o = O.Oracle(mesh, P, MQ, threads=threads)
+    o = O.Oracle(mesh, P, MQ, threads=threads, p_ref=W.tgv_p0())
     U = W.tgv_state(o.sol_coords(), [(n_edge ** 3, (P + 1) ** 3)], perturb=1e-3)
     o.rhs(U)
     t0 = time.perf_counter()
@@ -142,7 +142,7 @@ def run_reference(args, rank, world):
     threads = os.cpu_count() or 1
     n_edge = 12
     mesh = W.box_hex_mesh(n_edge)
-    o = O.Oracle(mesh, P, MQ, threads=threads)
+    o = O.Oracle(mesh, P, MQ, threads=threads, p_ref=W.tgv_p0())
     U = W.tgv_state(o.sol_coords(), [(n_edge ** 3, (P + 1) ** 3)], perturb=1e-3)
     for _ in range(args.warmup):
         U = o.rk4(U, DT, 1)
@@ -192,7 +192,8 @@ def run_ours(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     mesh = W.box_hex_mesh(N_EDGE)
-    prm = fr.make_params(p=P, prec="fp64")
+    p0 = W.tgv_p0()
+    prm = fr.make_params(p=P, prec="fp64", p_ref=p0)
     m = fr.FRMesh(mesh, prm)
     info = m.info()
     xyz = m.sol_coords()
@@ -258,7 +259,7 @@ def run_ours(args, rank, world):
     m.close()
     del m
     torch.cuda.empty_cache()
-    m32 = fr.FRMesh(mesh, fr.make_params(p=P, prec="fp32"))
+    m32 = fr.FRMesh(mesh, fr.make_params(p=P, prec="fp32", p_ref=p0))
     U = torch.from_numpy(U0).cuda()
     forms["fused_fp32"] = dof * RHS_PER_STEP / (time_rk4(m32, U, ksteps, 2, torch) * 1e-3) / 1e9
     m32.set_form("unfused")

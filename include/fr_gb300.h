@@ -82,6 +82,11 @@ typedef struct {
     int tri_strength;     /* prism triangle quadrature strength (0 = 8); collapsed k x k rule, k = strength/2 + 1 */
     int prec;             /* fr_precision */
     int rusanov_mode;     /* 0: wave speed max(|vL.n|+cL, |vR.n|+cR) (the only mode implemented) */
+    double p_ref;         /* constant reference pressure removed from the momentum flux, in the volume
+                           * and at interfaces (0 = none). On affine elements this changes the RHS only
+                           * by rounding: a constant flux has zero divergence and its common flux
+                           * equals its own normal flux. It keeps the O(1/(gamma M^2)) pressure out of
+                           * the rounding of the momentum divergence. */
 } fr_params;
 
 /* Host description of one mesh instance (copied by fr_mesh_create). */
@@ -160,6 +165,12 @@ fr_status fr_stage(fr_mesh *m, int which, double *host, long long n_host, long l
 
 /* Debug flags: bit 0 keeps a copy of the unfused form's physical gradient Q^(u) for fr_stage(2). */
 fr_status fr_set_debug(fr_mesh *m, int flags);
+
+/* RK4 CUDA graphs (on = 1, the default): fr_rk4_step captures one step (stage states, RHS launches,
+ * stage updates) into a graph on first use and replays it once per step; it recaptures when the
+ * state pointer, dt, stream or kernel form changes. The legacy default stream and per-kernel timing
+ * use plain launches. */
+fr_status fr_set_graph(fr_mesh *m, int on);
 
 /* Per-kernel timing (on = 1): CUDA events are recorded on the launching stream around every later
  * launch. fr_kernel_times waits for them and returns, per kernel id, the summed milliseconds and the

@@ -590,6 +590,7 @@ static void etype_free(etype_t *et)
 
 typedef struct {
     double gamma, Pr, mu, beta, tau;
+    double p_ref;   /* constant reference pressure removed from the momentum flux (0 = none) */
 } phys_params;
 
 typedef struct {
@@ -670,14 +671,14 @@ static int facekey_cmp(const void *a, const void *b)
     return ((const or_facekey *)a)->face - ((const or_facekey *)b)->face;
 }
 
-void *or_create(int p, int m, int tri_k, double gamma, double Pr, double mu, double beta, double tau,
+void *or_create(int p, int m, int tri_k, double gamma, double Pr, double mu, double beta, double tau, double p_ref,
                 int n_hex, int n_pri, int n_verts, const double *verts, const int *hex_v, const int *pri_v,
                 const double *period, int *err)
 {
     *err = OR_OK;
     if (p < 1 || m < 1 || n_hex < 0 || n_pri < 0 || n_hex + n_pri == 0) { *err = OR_EINVAL; return NULL; }
     oracle_t *o = (oracle_t *)calloc(1, sizeof(oracle_t));
-    o->ph.gamma = gamma; o->ph.Pr = Pr; o->ph.mu = mu; o->ph.beta = beta; o->ph.tau = tau;
+    o->ph.gamma = gamma; o->ph.Pr = Pr; o->ph.mu = mu; o->ph.beta = beta; o->ph.tau = tau; o->ph.p_ref = p_ref;
     o->n_hex = n_hex; o->n_pri = n_pri; o->ne = n_hex + n_pri;
     for (int d = 0; d < 3; d++) o->period[d] = period ? period[d] : 0.0;
     o->nthreads = 1;
@@ -905,17 +906,20 @@ void or_pairs(void *h, long *L, long *R)
  * Physics: inviscid and viscous fluxes (Sec. 2.1, Eqs. for f^e and f^v)
  * ------------------------------------------------------------------------------------------- */
 
-/* f[d][alpha], d = direction */
+/* f[d][alpha], d = direction. A constant p_ref removed from the momentum flux (volume and
+ * interface alike) changes nothing in exact arithmetic on affine elements: a constant flux has zero
+ * divergence and its common flux equals its own normal flux, so the lifted jump vanishes. */
 static void flux_inviscid(const phys_params *ph, const double *u, double f[3][NV], double *p_out)
 {
     double rho = u[0], vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho, E = u[4];
     double p = (ph->gamma - 1.0) * (E - 0.5 * rho * (vx * vx + vy * vy + vz * vz));
+    double pm = p - ph->p_ref;
     double v[3] = {vx, vy, vz};
     for (int d = 0; d < 3; d++) {
         f[d][0] = rho * v[d];
-        f[d][1] = rho * v[d] * vx + (d == 0 ? p : 0.0);
-        f[d][2] = rho * v[d] * vy + (d == 1 ? p : 0.0);
-        f[d][3] = rho * v[d] * vz + (d == 2 ? p : 0.0);
+        f[d][1] = rho * v[d] * vx + (d == 0 ? pm : 0.0);
+        f[d][2] = rho * v[d] * vy + (d == 1 ? pm : 0.0);
+        f[d][3] = rho * v[d] * vz + (d == 2 ? pm : 0.0);
         f[d][4] = v[d] * (E + p);
     }
     if (p_out) *p_out = p;

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfrgb300.so")
-SOURCES = ["fr_api.cu", "fr_hex.cu", "fr_probe.cu", "fr_basis.cpp"]
+SOURCES = ["fr_api.cu", "fr_hex.cu", "fr_pri.cu", "fr_probe.cu", "fr_basis.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"] + ARCH
 
@@ -23,7 +23,7 @@ def nvcc() -> str:
 def _compile(src: str, extra) -> str:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
     path = os.path.join(CSRC, src)
-    deps = [path, os.path.join(CSRC, "fr_internal.h"), os.path.join(HERE, "..", "include", "fr_gb300.h")]
+    deps = [path, os.path.join(CSRC, "fr_internal.h"), os.path.join(CSRC, "fr_physics.cuh"), os.path.join(HERE, "..", "include", "fr_gb300.h")]
     if os.path.exists(obj) and all(os.path.getmtime(obj) >= os.path.getmtime(d) for d in deps):
         return obj
     cmd = [nvcc()] + NVCC_FLAGS + list(extra) + ["-c", path, "-o", obj]

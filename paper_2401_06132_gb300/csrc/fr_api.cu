@@ -47,6 +47,17 @@ struct InstanceHost {
     std::vector<double> x0J;   // per element: x0[3], J[9] (row-major dx_i/dxi_j); x = x0 + J (xi + 1)
 };
 
+// Blocks of one element type and order, launched together (one launch per phase).
+struct Group {
+    int type = 0, p = 0;
+    std::vector<int> blks;
+    long long ne = 0;
+    void *d_geo = nullptr;          // Geo<T> per element in group order (multi-block groups)
+    long long *d_eu0 = nullptr, *d_ef0 = nullptr;
+    int *d_eph = nullptr;
+    void *d_phtab = nullptr;        // Phys<T> per instance
+};
+
 struct fr_mesh {
     int dev = 0;
     int prec = FR_FP64;
@@ -55,7 +66,11 @@ struct fr_mesh {
     std::vector<Block> blocks;
     std::vector<long long> inst_u0;      // value offsets per instance (+ total)
     long long ne = 0, nU = 0, nfpt = 0, npair = 0;
-    std::vector<frb::Hex1D> hex1d;       // per block (hex)
+    std::vector<frb::Hex1D> hex1d;       // per block (hex; for prisms the z operators)
+    frb::Prism2D pri;                    // prism operators (p = 3)
+    bool has_pri = false;
+    void *d_priops = nullptr;            // PriOps<T> on the device
+    std::vector<Group> groups;
     std::vector<double> geo_host;        // per element Ji[9], det (FP64)
     // device
     void *d_geo = nullptr;               // Geo<T>[ne]
@@ -79,6 +94,13 @@ struct fr_mesh {
     struct Timed { int kernel; cudaEvent_t a, b; };
     std::vector<Timed> timed;
     std::vector<cudaEvent_t> ev_pool;
+    // CUDA graph of one RK4 step (captured on first use, replayed per step)
+    bool use_graph = true;
+    cudaGraphExec_t graph = nullptr;
+    const void *graph_U = nullptr;
+    double graph_dt = 0;
+    cudaStream_t graph_stream = nullptr;
+    int graph_form = -1;
 };
 
 // Kernel ids for timing: 0..2 fused phases A, B, C; 10+k unfused kernel k (1..13); 30 RK4 update.
@@ -136,6 +158,56 @@ static void hex_ref_fpts(const frb::Hex1D &h, std::vector<double> &xf)
                 X[t2] = h.x[b];
             }
     }
+}
+
+// Reference flux points, face point counts and face centres of a block's element type.
+struct RefFaces {
+    int nfaces;
+    int count[6], off[6];
+    double centre[6][3];
+    std::vector<double> xf;   // [nf][3]
+};
+
+static void ref_faces(const fr_mesh *m, int blk, RefFaces &r)
+{
+    const Block &B = m->blocks[blk];
+    if (B.type == 0) {
+        const frb::Hex1D &h = m->hex1d[blk];
+        int n2 = h.n * h.n;
+        r.nfaces = 6;
+        hex_ref_fpts(h, r.xf);
+        for (int f = 0; f < 6; f++) {
+            r.count[f] = n2; r.off[f] = f * n2;
+            r.centre[f][0] = r.centre[f][1] = r.centre[f][2] = 0.0;
+            r.centre[f][f / 2] = (f & 1) ? 1.0 : -1.0;
+        }
+        return;
+    }
+    const frb::Prism2D &P = m->pri;
+    static const int cnt[5] = {10, 10, 16, 16, 16};
+    static const double cen[5][3] = {{-1.0 / 3, -1.0 / 3, -1}, {-1.0 / 3, -1.0 / 3, 1}, {0, -1, 0}, {0, 0, 0}, {-1, 0, 0}};
+    r.nfaces = 5;
+    int o = 0;
+    for (int f = 0; f < 5; f++) {
+        r.count[f] = cnt[f]; r.off[f] = o; o += cnt[f];
+        for (int d = 0; d < 3; d++) r.centre[f][d] = cen[f][d];
+    }
+    r.xf.assign((size_t)68 * 3, 0.0);
+    for (int t = 0; t < 10; t++)
+        for (int f = 0; f < 2; f++) {
+            double *X = &r.xf[(size_t)(f * 10 + t) * 3];
+            X[0] = P.xt[t][0]; X[1] = P.xt[t][1]; X[2] = f ? 1.0 : -1.0;
+        }
+    for (int f = 0; f < 3; f++)
+        for (int b = 0; b < 4; b++)
+            for (int a = 0; a < 4; a++) {
+                double *X = &r.xf[(size_t)(20 + 16 * f + a + 4 * b) * 3];
+                double sp = P.z.x[a];
+                if (f == 0) { X[0] = sp; X[1] = -1.0; }
+                else if (f == 1) { X[0] = -sp; X[1] = sp; }
+                else { X[0] = -1.0; X[1] = sp; }
+                X[2] = P.z.x[b];
+            }
 }
 
 static void affine_point(const double *x0J, const double *X, double *x)
@@ -197,20 +269,18 @@ static fr_status match_instance(fr_mesh *m, int ii, int b0, int b1, const fr_mes
     // element size scale for tolerances
     double hmin = 1e300;
     std::vector<FaceRef> faces;
-    std::vector<std::vector<double>> xf_ref(b1 - b0);
+    std::vector<RefFaces> rf(b1 - b0);
     for (int b = b0; b < b1; b++) {
         const Block &B = m->blocks[b];
-        hex_ref_fpts(m->hex1d[b], xf_ref[b - b0]);
+        ref_faces(m, b, rf[b - b0]);
         for (long long le = 0; le < B.ne; le++) {
             const double *x0J = &I.x0J[(size_t)(B.elem0 - m->blocks[b0].elem0 + le) * 12];
             double hh = std::cbrt(std::fabs(x0J[3] * (x0J[7] * x0J[11] - x0J[8] * x0J[10]) - x0J[4] * (x0J[6] * x0J[11] - x0J[8] * x0J[9]) + x0J[5] * (x0J[6] * x0J[10] - x0J[7] * x0J[9])));
             hmin = std::min(hmin, hh);
-            for (int f = 0; f < 6; f++) {
+            for (int f = 0; f < rf[b - b0].nfaces; f++) {
                 FaceRef fr;
                 fr.elem = B.elem0 + le; fr.blk = b; fr.le = le; fr.face = f;
-                double X[3] = {0, 0, 0};
-                X[f / 2] = (f & 1) ? 1.0 : -1.0;
-                affine_point(x0J, X, fr.c);
+                affine_point(x0J, rf[b - b0].centre[f], fr.c);
                 faces.push_back(fr);
             }
         }
@@ -265,14 +335,15 @@ static fr_status match_instance(fr_mesh *m, int ii, int b0, int b1, const fr_mes
         if (b < a) continue;
         const FaceRef &A = faces[a], &Bf = faces[b];
         const Block &BA = m->blocks[A.blk], &BB = m->blocks[Bf.blk];
-        int n2 = BA.nf / 6;
-        if (BB.nf / 6 != n2) return fail(FR_EMESH, "face point counts differ across an interface");
+        const RefFaces &RA = rf[A.blk - b0], &RB = rf[Bf.blk - b0];
+        int n2 = RA.count[A.face];
+        if (RB.count[Bf.face] != n2) return fail(FR_EMESH, "element %lld face %d meets a face with a different point count", A.elem, A.face);
         const double *JA = &I.x0J[(size_t)(A.elem - m->blocks[b0].elem0) * 12];
         const double *JB = &I.x0J[(size_t)(Bf.elem - m->blocks[b0].elem0) * 12];
         xa.resize(n2 * 3); xb.resize(n2 * 3);
         for (int t = 0; t < n2; t++) {
-            affine_point(JA, &xf_ref[A.blk - b0][((size_t)A.face * n2 + t) * 3], &xa[t * 3]);
-            affine_point(JB, &xf_ref[Bf.blk - b0][((size_t)Bf.face * n2 + t) * 3], &xb[t * 3]);
+            affine_point(JA, &RA.xf[((size_t)RA.off[A.face] + t) * 3], &xa[t * 3]);
+            affine_point(JB, &RB.xf[((size_t)RB.off[Bf.face] + t) * 3], &xb[t * 3]);
         }
         auto key = std::make_tuple(BA.type, A.face, BB.type, Bf.face);
         std::vector<int> &perm = perm_cache[key];
@@ -289,8 +360,8 @@ static fr_status match_instance(fr_mesh *m, int ii, int b0, int b1, const fr_mes
         // reading R5: L is the smaller global element; a self-pair takes the smaller local face
         bool aL = A.elem < Bf.elem || (A.elem == Bf.elem && A.face < Bf.face);
         for (int t = 0; t < n2; t++) {
-            long long ga = BA.f0 + A.le * BA.nf + (long long)A.face * n2 + t;
-            long long gb = BB.f0 + Bf.le * BB.nf + (long long)Bf.face * n2 + perm[t];
+            long long ga = BA.f0 + A.le * BA.nf + RA.off[A.face] + t;
+            long long gb = BB.f0 + Bf.le * BB.nf + RB.off[Bf.face] + perm[t];
             partner[ga] = (uint32_t)gb | (aL ? FR_LFLAG : 0u);
             partner[gb] = (uint32_t)ga | (aL ? 0u : FR_LFLAG);
         }
@@ -302,6 +373,44 @@ static fr_status match_instance(fr_mesh *m, int ii, int b0, int b1, const fr_mes
 // ---------------------------------------------------------------------------------------------
 // Mesh creation
 // ---------------------------------------------------------------------------------------------
+// Affine map of one element from its vertices; rejects non-affine and inverted elements.
+static fr_status element_map(int ii, long long e, int type, const fr_mesh_desc *d, double *x0J, std::vector<double> &geo)
+{
+    const int nv = type == 0 ? 8 : 6;
+    const int *conn = type == 0 ? d->hex_v + 8 * e : d->pri_v + 6 * e;
+    const double *v[8];
+    for (int k = 0; k < nv; k++) {
+        int vi = conn[k];
+        if (vi < 0 || vi >= d->n_verts) return fail(FR_EMESH, "instance %d element %lld: vertex id %d out of range", ii, e, vi);
+        v[k] = d->verts + 3 * (size_t)vi;
+    }
+    const int c3 = type == 0 ? 4 : 3;   // corner along the third reference axis
+    double scale = 0;
+    for (int i = 0; i < 3; i++) {
+        x0J[i] = v[0][i];
+        x0J[3 + 3 * i + 0] = 0.5 * (v[1][i] - v[0][i]);
+        x0J[3 + 3 * i + 1] = 0.5 * (v[2][i] - v[0][i]);
+        x0J[3 + 3 * i + 2] = 0.5 * (v[c3][i] - v[0][i]);
+        scale = std::max(scale, std::fabs(v[1][i] - v[0][i]) + std::fabs(v[2][i] - v[0][i]) + std::fabs(v[c3][i] - v[0][i]));
+    }
+    static const double pc[6][3] = {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}, {1, -1, 1}, {-1, 1, 1}};
+    for (int k = 0; k < nv; k++) {  // affine: every corner is the image of its reference corner
+        double X[3], x[3];
+        if (type == 0) { X[0] = (k & 1) ? 1.0 : -1.0; X[1] = (k & 2) ? 1.0 : -1.0; X[2] = (k & 4) ? 1.0 : -1.0; }
+        else { X[0] = pc[k][0]; X[1] = pc[k][1]; X[2] = pc[k][2]; }
+        affine_point(x0J, X, x);
+        for (int i = 0; i < 3; i++)
+            if (std::fabs(x[i] - v[k][i]) > 1e-10 * scale)
+                return fail(FR_EUNSUPPORTED, "instance %d element %lld is not affine", ii, e);
+    }
+    double Ji[9];
+    double det = inv3(x0J + 3, Ji);
+    if (!(det > 0)) return fail(FR_EMESH, "instance %d element %lld is inverted or degenerate", ii, e);
+    for (int k = 0; k < 9; k++) geo.push_back(Ji[k]);
+    geo.push_back(det);
+    return FR_OK;
+}
+
 static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_inst, const fr_params *prm,
                             std::vector<uint32_t> &partner)
 {
@@ -309,72 +418,94 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
     m->prec = prm[0].prec;
     if (m->prec < FR_FP64 || m->prec > FR_MIXED_FP16) return fail(FR_EINVAL, "unknown precision %d", m->prec);
     long long elem = 0, u = 0, f = 0;
+    std::vector<int> bfirst;
     for (int ii = 0; ii < n_inst; ii++) {
         const fr_mesh_desc *d = inst[ii];
         const fr_params &P = prm[ii];
         if (!d) return fail(FR_EINVAL, "instance %d: null descriptor", ii);
         if (P.prec != m->prec) return fail(FR_EINVAL, "all instances must share one precision");
         int m1 = P.nq1d > 0 ? P.nq1d : P.p + 2;
-        if (P.p < 3 || P.p > 4 || m1 != P.p + 2) return fail(FR_EUNSUPPORTED, "instance %d: hex order %d with %d quadrature points", ii, P.p, m1);
-        if (!(P.gamma > 1.0) || !(P.Pr > 0.0) || P.mu < 0.0 || P.tau < 0.0) return fail(FR_EINVAL, "instance %d: bad physical parameters", ii);
+        if (P.p < 3 || P.p > 4 || m1 != P.p + 2) return fail(FR_EUNSUPPORTED, "instance %d: order %d with %d quadrature points", ii, P.p, m1);
+        if (!(P.gamma > 1.0) || !(P.Pr > 0.0) || P.mu < 0.0 || P.tau < 0.0 || !(P.p_ref == P.p_ref))
+            return fail(FR_EINVAL, "instance %d: bad physical parameters", ii);
         if (P.rusanov_mode != 0) return fail(FR_EUNSUPPORTED, "rusanov_mode %d", P.rusanov_mode);
         if (d->n_hex < 0 || d->n_pri < 0 || d->n_hex + d->n_pri == 0 || d->n_verts <= 0 || !d->verts)
             return fail(FR_EINVAL, "instance %d: empty or malformed mesh", ii);
-        if (d->n_pri > 0) return fail(FR_EUNSUPPORTED, "instance %d: prism elements are not built in this library version", ii);
-        if (!d->hex_v) return fail(FR_EINVAL, "instance %d: null hex connectivity", ii);
+        if (d->n_hex > 0 && !d->hex_v) return fail(FR_EINVAL, "instance %d: null hex connectivity", ii);
+        if (d->n_pri > 0 && !d->pri_v) return fail(FR_EINVAL, "instance %d: null prism connectivity", ii);
+        if (d->n_pri > 0 && (P.p != 3 || (P.tri_strength != 0 && P.tri_strength != 8)))
+            return fail(FR_EUNSUPPORTED, "instance %d: prisms are built for p = 3 with a strength-8 triangle rule", ii);
         InstanceHost I;
         I.prm = P; I.prm.nq1d = m1;
         I.n_hex = d->n_hex; I.n_pri = d->n_pri;
         I.x0J.resize((size_t)(d->n_hex + d->n_pri) * 12);
-        Block B{};
-        B.inst = ii; B.type = 0; B.p = P.p; B.m = m1;
-        B.nu = (P.p + 1) * (P.p + 1) * (P.p + 1); B.nf = 6 * (P.p + 1) * (P.p + 1);
-        B.ne = d->n_hex; B.elem0 = elem; B.u0 = u; B.f0 = f;
-        frb::Hex1D h;
-        if (frb::hex1d(P.p, m1, h)) return fail(FR_EUNSUPPORTED, "hex operators for p=%d m=%d", P.p, m1);
         m->inst_u0.push_back(u);
-        for (long long e = 0; e < d->n_hex; e++) {
-            const double *v[8];
-            for (int k = 0; k < 8; k++) {
-                int vi = d->hex_v[8 * e + k];
-                if (vi < 0 || vi >= d->n_verts) return fail(FR_EMESH, "instance %d element %lld: vertex id %d out of range", ii, e, vi);
-                v[k] = d->verts + 3 * (size_t)vi;
+        bfirst.push_back((int)m->blocks.size());
+        for (int type = 0; type < 2; type++) {
+            long long ne = type == 0 ? d->n_hex : d->n_pri;
+            if (ne == 0) continue;
+            Block B{};
+            B.inst = ii; B.type = type; B.p = P.p; B.m = m1;
+            frb::Hex1D h;
+            if (type == 0) {
+                if (frb::hex1d(P.p, m1, h)) return fail(FR_EUNSUPPORTED, "hex operators for p=%d m=%d", P.p, m1);
+                B.nu = (P.p + 1) * (P.p + 1) * (P.p + 1); B.nf = 6 * (P.p + 1) * (P.p + 1);
+            } else {
+                if (!m->has_pri) {
+                    if (frb::prism2d(m->pri)) return fail(FR_EUNSUPPORTED, "prism operators");
+                    m->has_pri = true;
+                }
+                h = m->pri.z;
+                B.nu = FR_PT * FR_PE; B.nf = 2 * FR_PT + 3 * FR_PE * FR_PE;
             }
-            double *x0J = &I.x0J[(size_t)e * 12];
-            double scale = 0;
-            for (int i = 0; i < 3; i++) {
-                x0J[i] = v[0][i];
-                x0J[3 + 3 * i + 0] = 0.5 * (v[1][i] - v[0][i]);
-                x0J[3 + 3 * i + 1] = 0.5 * (v[2][i] - v[0][i]);
-                x0J[3 + 3 * i + 2] = 0.5 * (v[4][i] - v[0][i]);
-                scale = std::max(scale, std::fabs(v[1][i] - v[0][i]) + std::fabs(v[2][i] - v[0][i]) + std::fabs(v[4][i] - v[0][i]));
+            B.ne = ne; B.elem0 = elem; B.u0 = u; B.f0 = f;
+            long long le0 = type == 0 ? 0 : d->n_hex;
+            for (long long e = 0; e < ne; e++) {
+                fr_status st = element_map(ii, e, type, d, &I.x0J[(size_t)(le0 + e) * 12], m->geo_host);
+                if (st) return st;
             }
-            for (int k = 0; k < 8; k++) {  // affine: every corner is the image of its reference corner
-                double X[3] = {(k & 1) ? 1.0 : -1.0, (k & 2) ? 1.0 : -1.0, (k & 4) ? 1.0 : -1.0}, x[3];
-                affine_point(x0J, X, x);
-                for (int i = 0; i < 3; i++)
-                    if (std::fabs(x[i] - v[k][i]) > 1e-10 * scale)
-                        return fail(FR_EUNSUPPORTED, "instance %d element %lld is not affine", ii, e);
-            }
-            double Ji[9];
-            double det = inv3(x0J + 3, Ji);
-            if (!(det > 0)) return fail(FR_EMESH, "instance %d element %lld is inverted or degenerate", ii, e);
-            for (int k = 0; k < 9; k++) m->geo_host.push_back(Ji[k]);
-            m->geo_host.push_back(det);
+            m->blocks.push_back(B);
+            m->hex1d.push_back(h);
+            elem += B.ne; u += B.ne * FR_NV * B.nu; f += B.ne * B.nf;
         }
         m->inst.push_back(I);
-        m->blocks.push_back(B);
-        m->hex1d.push_back(h);
-        elem += B.ne; u += B.ne * FR_NV * B.nu; f += B.ne * B.nf;
     }
     m->ne = elem; m->nU = u; m->nfpt = f;
     m->inst_u0.push_back(u);
+    bfirst.push_back((int)m->blocks.size());
     if (f >= (long long)FR_LFLAG) return fail(FR_EUNSUPPORTED, "more than 2^31 flux points");
     partner.assign((size_t)f, 0xffffffffu);
     for (int ii = 0; ii < n_inst; ii++) {
-        fr_status st = match_instance(m, ii, ii, ii + 1, inst[ii], partner);
+        fr_status st = match_instance(m, ii, bfirst[ii], bfirst[ii + 1], inst[ii], partner);
         if (st != FR_OK) return st;
     }
+    return FR_OK;
+}
+
+template <typename T>
+static fr_status upload_priops(fr_mesh *m)
+{
+    if (!m->has_pri) return FR_OK;
+    const frb::Prism2D &P = m->pri;
+    PriOps<T> o{};
+    for (int q = 0; q < FR_PQ; q++)
+        for (int t = 0; t < FR_PT; t++) { o.Bt[q][t] = (T)P.Bt[q][t]; o.Pt[t][q] = (T)P.Pt[t][q]; }
+    for (int t = 0; t < FR_PT; t++)
+        for (int u = 0; u < FR_PT; u++) { o.Dhx[t][u] = (T)P.Dhx[t][u]; o.Dhy[t][u] = (T)P.Dhy[t][u]; }
+    for (int f = 0; f < 3; f++) {
+        o.nf[f][0] = (T)P.nf[f][0]; o.nf[f][1] = (T)P.nf[f][1];
+        for (int a = 0; a < FR_PE; a++)
+            for (int t = 0; t < FR_PT; t++) { o.Ef[f][a][t] = (T)P.Ef[f][a][t]; o.Lf[f][t][a] = (T)P.Lf[f][t][a]; }
+    }
+    for (int c = 0; c < 5; c++)
+        for (int k = 0; k < FR_PE; k++) { o.Bz[c][k] = (T)P.z.B[c][k]; o.Pz[k][c] = (T)P.z.Pj[k][c]; }
+    for (int k = 0; k < FR_PE; k++) {
+        for (int j = 0; j < FR_PE; j++) o.Dhz[k][j] = (T)P.z.Dh[k][j];
+        o.lzL[k] = (T)P.z.lL[k]; o.lzR[k] = (T)P.z.lR[k]; o.liftzL[k] = (T)P.z.liftL[k]; o.liftzR[k] = (T)P.z.liftR[k];
+    }
+    fr_status st = dalloc(m, &m->d_priops, sizeof(o));
+    if (st) return st;
+    CU(cudaMemcpy(m->d_priops, &o, sizeof(o), cudaMemcpyHostToDevice));
     return FR_OK;
 }
 
@@ -392,6 +523,61 @@ static fr_status upload_geo(fr_mesh *m)
     return FR_OK;
 }
 
+template <typename T>
+static Phys<T> phys_of(const fr_params &P)
+{
+    Phys<T> ph;
+    ph.gamma = (T)P.gamma; ph.gm1 = (T)(P.gamma - 1.0); ph.mu = (T)P.mu;
+    ph.beta = (T)P.beta; ph.tau = (T)P.tau; ph.heat = (T)(P.mu * P.gamma / P.Pr); ph.pref = (T)P.p_ref;
+    return ph;
+}
+
+template <typename T>
+static fr_status build_groups(fr_mesh *m)
+{
+    for (size_t b = 0; b < m->blocks.size(); b++) {
+        const Block &B = m->blocks[b];
+        Group *g = nullptr;
+        for (Group &x : m->groups) if (x.type == B.type && x.p == B.p) g = &x;
+        if (!g) { m->groups.push_back(Group()); g = &m->groups.back(); g->type = B.type; g->p = B.p; }
+        g->blks.push_back((int)b);
+        g->ne += B.ne;
+    }
+    std::vector<Phys<T>> tab;
+    for (const InstanceHost &I : m->inst) tab.push_back(phys_of<T>(I.prm));
+    for (Group &g : m->groups) {
+        if (g.blks.size() < 2) continue;
+        std::vector<Geo<T>> geo;
+        std::vector<long long> eu0, ef0;
+        std::vector<int> eph;
+        for (int bi : g.blks) {
+            const Block &B = m->blocks[bi];
+            for (long long e = 0; e < B.ne; e++) {
+                Geo<T> x;
+                const double *src = &m->geo_host[(size_t)(B.elem0 + e) * 10];
+                for (int k = 0; k < 9; k++) x.Ji[k] = (T)src[k];
+                x.det = (T)src[9];
+                geo.push_back(x);
+                eu0.push_back(B.u0 + e * FR_NV * B.nu);
+                ef0.push_back(B.f0 + e * B.nf);
+                eph.push_back(B.inst);
+            }
+        }
+        fr_status st = dalloc(m, &g.d_geo, geo.size() * sizeof(Geo<T>));
+        if (!st) st = dalloc(m, (void **)&g.d_eu0, eu0.size() * sizeof(long long));
+        if (!st) st = dalloc(m, (void **)&g.d_ef0, ef0.size() * sizeof(long long));
+        if (!st) st = dalloc(m, (void **)&g.d_eph, eph.size() * sizeof(int));
+        if (!st) st = dalloc(m, &g.d_phtab, tab.size() * sizeof(Phys<T>));
+        if (st) return st;
+        CU(cudaMemcpy(g.d_geo, geo.data(), geo.size() * sizeof(Geo<T>), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(g.d_eu0, eu0.data(), eu0.size() * sizeof(long long), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(g.d_ef0, ef0.data(), ef0.size() * sizeof(long long), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(g.d_eph, eph.data(), eph.size() * sizeof(int), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(g.d_phtab, tab.data(), tab.size() * sizeof(Phys<T>), cudaMemcpyHostToDevice));
+    }
+    return FR_OK;
+}
+
 extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst, const fr_params *prm, fr_mesh **out)
 {
     if (!out) return fail(FR_EINVAL, "out is null");
@@ -403,9 +589,11 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
     cudaError_t ce = cudaGetDevice(&m->dev);
     if (ce != cudaSuccess) { delete m; return fail(FR_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(ce)); }
     for (size_t b = 0; b < m->blocks.size(); b++)
-        if (hex_upload_ops(m->blocks[b].p, m->blocks[b].m, m->hex1d[b])) { delete m; return fail(FR_ECUDA, "operator upload failed"); }
+        if (m->blocks[b].type == 0 && hex_upload_ops(m->blocks[b].p, m->blocks[b].m, m->hex1d[b])) { delete m; return fail(FR_ECUDA, "operator upload failed"); }
     size_t ts = tsize(m->prec);
     st = (m->prec == FR_FP64) ? upload_geo<double>(m) : upload_geo<float>(m);
+    if (!st) st = (m->prec == FR_FP64) ? upload_priops<double>(m) : upload_priops<float>(m);
+    if (!st) st = (m->prec == FR_FP64) ? build_groups<double>(m) : build_groups<float>(m);
     if (!st) st = dalloc(m, (void **)&m->d_partner, partner.size() * sizeof(uint32_t));
     if (!st && cudaMemcpy(m->d_partner, partner.data(), partner.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess)
         st = fail(FR_ECUDA, "partner upload failed");
@@ -424,12 +612,16 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
 extern "C" fr_status fr_destroy(fr_mesh *m)
 {
     if (!m) return FR_OK;
-    void **bufs[] = {&m->d_geo, (void **)&m->d_partner, &m->d_UF, &m->d_FV, &m->d_CF, &m->d_QF, &m->d_DF, &m->d_Qu,
+    void **bufs[] = {&m->d_priops, &m->d_geo, (void **)&m->d_partner, &m->d_UF, &m->d_FV, &m->d_CF, &m->d_QF, &m->d_DF, &m->d_Qu,
                      &m->d_UQ, &m->d_QQ, &m->d_Rt, &m->d_rk_k, &m->d_rk_us, (void **)&m->d_rk_acc, &m->d_io_U,
                      &m->d_io_R, (void **)&m->d_wsum, (void **)&m->d_status, &m->d_Qsnap};
     for (void **b : bufs) dfree(*b);
+    for (Group &g : m->groups) {
+        dfree(g.d_geo); dfree((void *&)g.d_eu0); dfree((void *&)g.d_ef0); dfree((void *&)g.d_eph); dfree(g.d_phtab);
+    }
     if (m->h_status) cudaFreeHost(m->h_status);
     for (auto &t : m->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+    if (m->graph) cudaGraphExecDestroy(m->graph);
     for (auto e : m->ev_pool) cudaEventDestroy(e);
     if (m->ev_status) cudaEventDestroy(m->ev_status);
     delete m;
@@ -440,6 +632,13 @@ extern "C" fr_status fr_set_debug(fr_mesh *m, int flags)
 {
     if (!m) return fail(FR_EINVAL, "null handle");
     m->debug = flags;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_set_graph(fr_mesh *m, int on)
+{
+    if (!m) return fail(FR_EINVAL, "null handle");
+    m->use_graph = on != 0;
     return FR_OK;
 }
 
@@ -484,9 +683,7 @@ static HexArgs<T> make_args(fr_mesh *m, const Block &b, const void *U, void *R)
     a.ne = b.ne; a.u0 = b.u0; a.f0 = b.f0; a.nfpt = m->nfpt;
     a.geo = reinterpret_cast<const Geo<T> *>(m->d_geo) + b.elem0;
     a.partner = m->d_partner;
-    a.ph.gamma = (T)I.prm.gamma; a.ph.gm1 = (T)(I.prm.gamma - 1.0); a.ph.mu = (T)I.prm.mu;
-    a.ph.beta = (T)I.prm.beta; a.ph.tau = (T)I.prm.tau;
-    a.ph.heat = (T)(I.prm.mu * I.prm.gamma / I.prm.Pr);
+    a.ph = phys_of<T>(I.prm);
     a.U = reinterpret_cast<const T *>(U); a.R = reinterpret_cast<T *>(R);
     a.UF = reinterpret_cast<T *>(m->d_UF); a.FV = reinterpret_cast<T *>(m->d_FV);
     a.CF = reinterpret_cast<T *>(m->d_CF); a.QF = reinterpret_cast<T *>(m->d_QF); a.DF = reinterpret_cast<T *>(m->d_DF);
@@ -499,7 +696,8 @@ static HexArgs<T> make_args(fr_mesh *m, const Block &b, const void *U, void *R)
 
 static fr_status ensure_unfused(fr_mesh *m)
 {
-    if (m->blocks.size() != 1) return fail(FR_EUNSUPPORTED, "the unfused form runs single-instance hexahedral meshes");
+    if (m->blocks.size() != 1 || m->blocks[0].type != 0)
+        return fail(FR_EUNSUPPORTED, "the unfused form runs single-instance hexahedral meshes");
     const Block &b = m->blocks[0];
     size_t ts = tsize(m->prec);
     long long nq = (long long)b.m * b.m * b.m;
@@ -541,9 +739,18 @@ static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s)
     if (m->form == FR_FUSED) {
         for (int ph = 0; ph < 3; ph++) {
             TimeScope ts(m, ph, s);
-            for (const Block &b : m->blocks) {
+            for (const Group &gr : m->groups) {
+                const Block &b = m->blocks[gr.blks[0]];
                 HexArgs<T> a = make_args<T>(m, b, U, R);
-                if (hex_fused_phase<T>(b.p, ph, a, s)) return fail(FR_ECUDA, "fused phase %d launch: %s", ph, cudaGetErrorString(cudaGetLastError()));
+                if (gr.blks.size() > 1) {
+                    a.ne = gr.ne; a.u0 = 0; a.f0 = 0;
+                    a.geo = reinterpret_cast<const Geo<T> *>(gr.d_geo);
+                    a.eu0 = gr.d_eu0; a.ef0 = gr.d_ef0; a.eph = gr.d_eph;
+                    a.phtab = reinterpret_cast<const Phys<T> *>(gr.d_phtab);
+                }
+                int lr = b.type == 0 ? hex_fused_phase<T>(b.p, ph, a, s)
+                                     : pri_fused_phase<T>(ph, a, reinterpret_cast<const PriOps<T> *>(m->d_priops), s);
+                if (lr) return fail(FR_ECUDA, "fused phase %d launch: %s", ph, cudaGetErrorString(cudaGetLastError()));
             }
         }
     } else {
@@ -643,26 +850,60 @@ __global__ void k_rk_update(double *__restrict__ U, const T *__restrict__ k, dou
 }
 
 template <typename T>
-static fr_status rk4_impl(fr_mesh *m, double *U, double dt, int nsteps, cudaStream_t s)
+static fr_status rk4_enqueue_step(fr_mesh *m, double *U, double dt, cudaStream_t s)
 {
     const long long n = m->nU;
     const int thr = 256;
     const int grid = (int)std::min<long long>((n + thr - 1) / thr, 152LL * 16);
-    for (int step = 0; step < nsteps; step++) {
-        const void *u0 = U;
-        if (m->prec != FR_FP64) {
-            k_rk_cast<T><<<grid, thr, 0, s>>>(U, reinterpret_cast<T *>(m->d_rk_us), n);
-            u0 = m->d_rk_us;
-        }
-        for (int st = 0; st < 4; st++) {
-            fr_status r = rhs_dispatch(m, st == 0 ? u0 : m->d_rk_us, m->d_rk_k, s);
-            if (r) return r;
-            TimeScope ts(m, 30, s);
-            k_rk_update<T><<<grid, thr, 0, s>>>(U, reinterpret_cast<const T *>(m->d_rk_k), m->d_rk_acc,
-                                                reinterpret_cast<T *>(m->d_rk_us), n, dt, st);
-        }
+    const void *u0 = U;
+    if (m->prec != FR_FP64) {
+        k_rk_cast<T><<<grid, thr, 0, s>>>(U, reinterpret_cast<T *>(m->d_rk_us), n);
+        u0 = m->d_rk_us;
+    }
+    for (int st = 0; st < 4; st++) {
+        fr_status r = rhs_dispatch(m, st == 0 ? u0 : m->d_rk_us, m->d_rk_k, s);
+        if (r) return r;
+        TimeScope ts(m, 30, s);
+        k_rk_update<T><<<grid, thr, 0, s>>>(U, reinterpret_cast<const T *>(m->d_rk_k), m->d_rk_acc,
+                                            reinterpret_cast<T *>(m->d_rk_us), n, dt, st);
     }
     CU(cudaPeekAtLastError());
+    return FR_OK;
+}
+
+template <typename T>
+static fr_status rk4_impl(fr_mesh *m, double *U, double dt, int nsteps, cudaStream_t s)
+{
+    // Graph replay needs a capturable stream: the legacy default stream (NULL) is not, and per-kernel
+    // timing records host-visible events, so both run the launches directly.
+    if (!m->use_graph || m->timing || s == nullptr) {
+        for (int step = 0; step < nsteps; step++) {
+            fr_status r = rk4_enqueue_step<T>(m, U, dt, s);
+            if (r) return r;
+        }
+        return FR_OK;
+    }
+    int done = 0;
+    if (!m->graph || m->graph_U != U || m->graph_dt != dt || m->graph_stream != s || m->graph_form != m->form) {
+        if (m->graph) { cudaGraphExecDestroy(m->graph); m->graph = nullptr; }
+        // one eager step first: lazy workspace allocation and first-launch kernel attributes happen
+        // outside the capture
+        fr_status r0 = rk4_enqueue_step<T>(m, U, dt, s);
+        if (r0) return r0;
+        done = 1;
+        if (nsteps <= 1) return FR_OK;
+        cudaGraph_t g = nullptr;
+        CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        fr_status r = rk4_enqueue_step<T>(m, U, dt, s);
+        cudaError_t ce = cudaStreamEndCapture(s, &g);
+        if (r) { if (g) cudaGraphDestroy(g); return r; }
+        if (ce != cudaSuccess) return fail(FR_ECUDA, "RK4 graph capture: %s", cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&m->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) { m->graph = nullptr; return fail(FR_ECUDA, "RK4 graph instantiate: %s", cudaGetErrorString(ce)); }
+        m->graph_U = U; m->graph_dt = dt; m->graph_stream = s; m->graph_form = m->form;
+    }
+    for (int step = done; step < nsteps; step++) CU(cudaGraphLaunch(m->graph, s));
     return FR_OK;
 }
 
@@ -706,7 +947,7 @@ extern "C" fr_status fr_mesh_info(const fr_mesh *m, long long *info)
 {
     if (!m || !info) return fail(FR_EINVAL, "null argument");
     info[0] = m->ne; info[1] = m->nU; info[2] = m->nfpt; info[3] = m->npair; info[4] = (long long)m->inst.size();
-    info[5] = (m->form == FR_FUSED ? 3 : 13) * (long long)m->blocks.size();
+    info[5] = m->form == FR_FUSED ? 3 * (long long)m->groups.size() : 13;
     info[6] = m->bytes;
     return FR_OK;
 }
@@ -727,10 +968,13 @@ extern "C" fr_status fr_sol_coords(const fr_mesh *m, double *xyz)
         const InstanceHost &I = m->inst[B.inst];
         const frb::Hex1D &h = m->hex1d[b];
         int n = h.n;
+        long long le0 = B.type == 0 ? 0 : I.n_hex;
         for (long long e = 0; e < B.ne; e++) {
-            const double *x0J = &I.x0J[(size_t)e * 12];
+            const double *x0J = &I.x0J[(size_t)(le0 + e) * 12];
             for (int z = 0; z < B.nu; z++, k++) {
-                double X[3] = {h.x[z % n], h.x[(z / n) % n], h.x[z / (n * n)]};
+                double X[3];
+                if (B.type == 0) { X[0] = h.x[z % n]; X[1] = h.x[(z / n) % n]; X[2] = h.x[z / (n * n)]; }
+                else { X[0] = m->pri.xt[z % FR_PT][0]; X[1] = m->pri.xt[z % FR_PT][1]; X[2] = h.x[z / FR_PT]; }
                 affine_point(x0J, X, xyz + 3 * k);
             }
         }
@@ -738,24 +982,23 @@ extern "C" fr_status fr_sol_coords(const fr_mesh *m, double *xyz)
     return FR_OK;
 }
 
-struct W1D {
-    double w[FR_MAXN];
+struct WPts {
+    double w[FR_MAXN * FR_MAXN * FR_MAXN];   // quadrature weight of every solution point
 };
 
 // Per-element partial sums of the diagnostics; out[k] (k < 8): 0 volume, 1 int rho|v|^2/2,
 // 2 -int d(rho|v|^2/2)/dt from R, 3..7 int R_alpha (weights W = tensor GL weights times detJ).
 template <typename T>
 __global__ void k_diag(const T *__restrict__ U, const T *__restrict__ R, const Geo<T> *__restrict__ geo, long long ne,
-                       int n, W1D w1, double *out)
+                       int NU, WPts wp, double *out)
 {
-    const int NU = n * n * n;
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (long long e = blockIdx.x; e < ne; e += gridDim.x) {
         const T *u = U + e * 5 * NU;
         const T *r = R ? R + e * 5 * NU : nullptr;
         const double det = (double)geo[e].det;
         for (int z = threadIdx.x; z < NU; z += blockDim.x) {
-            const double w = w1.w[z % n] * w1.w[(z / n) % n] * w1.w[z / (n * n)] * det;
+            const double w = wp.w[z] * det;
             const double rho = (double)u[z];
             const double v0 = (double)u[NU + z] / rho, v1 = (double)u[2 * NU + z] / rho, v2 = (double)u[3 * NU + z] / rho;
             const double v2s = v0 * v0 + v1 * v1 + v2 * v2;
@@ -784,8 +1027,11 @@ extern "C" fr_status fr_diagnostics(fr_mesh *m, const void *U, const void *R, do
     CU(cudaMemsetAsync(m->d_wsum, 0, ni * 8 * sizeof(double), s));
     for (size_t bi = 0; bi < m->blocks.size(); bi++) {
         const Block &b = m->blocks[bi];
-        W1D w1{};
-        for (int i = 0; i < m->hex1d[bi].n; i++) w1.w[i] = m->hex1d[bi].w[i];
+        WPts wp{};
+        const frb::Hex1D &h = m->hex1d[bi];
+        for (int z = 0; z < b.nu; z++)
+            wp.w[z] = b.type == 0 ? h.w[z % h.n] * h.w[(z / h.n) % h.n] * h.w[z / (h.n * h.n)]
+                                  : m->pri.wt[z % FR_PT] * h.w[z / FR_PT];
         int grid = (int)std::min<long long>(std::max<long long>(b.ne, 1), 152LL * 8);
         double *o = m->d_wsum + 8 * b.inst;
         size_t ts = tsize(m->prec);
@@ -793,10 +1039,10 @@ extern "C" fr_status fr_diagnostics(fr_mesh *m, const void *U, const void *R, do
         const char *r = R ? (const char *)R + b.u0 * ts : nullptr;
         if (m->prec == FR_FP64)
             k_diag<double><<<grid, 128, 0, s>>>((const double *)u, (const double *)r,
-                                                 (const Geo<double> *)m->d_geo + b.elem0, b.ne, b.p + 1, w1, o);
+                                                 (const Geo<double> *)m->d_geo + b.elem0, b.ne, b.nu, wp, o);
         else
             k_diag<float><<<grid, 128, 0, s>>>((const float *)u, (const float *)r,
-                                                (const Geo<float> *)m->d_geo + b.elem0, b.ne, b.p + 1, w1, o);
+                                                (const Geo<float> *)m->d_geo + b.elem0, b.ne, b.nu, wp, o);
         CU(cudaPeekAtLastError());
     }
     std::vector<double> h(ni * 8);

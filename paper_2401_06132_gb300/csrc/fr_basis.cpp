@@ -142,4 +142,146 @@ int hex1d(int p, int m, Hex1D &h)
     return 0;
 }
 
+// In-place inverse of a small dense matrix (Gauss-Jordan, partial pivoting); 0 on success.
+static int invert(int n, double *a)
+{
+    double aug[FR_PT][2 * FR_PT];
+    if (n > FR_PT) return -1;
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < 2 * n; j++) aug[i][j] = j < n ? a[i * n + j] : (j - n == i ? 1.0 : 0.0);
+    for (int c = 0; c < n; c++) {
+        int piv = c;
+        for (int r = c + 1; r < n; r++) if (std::fabs(aug[r][c]) > std::fabs(aug[piv][c])) piv = r;
+        if (std::fabs(aug[piv][c]) < 1e-300) return -1;
+        for (int j = 0; j < 2 * n; j++) { double t = aug[c][j]; aug[c][j] = aug[piv][j]; aug[piv][j] = t; }
+        double d = aug[c][c];
+        for (int j = 0; j < 2 * n; j++) aug[c][j] /= d;
+        for (int r = 0; r < n; r++) {
+            if (r == c || aug[r][c] == 0.0) continue;
+            double f = aug[r][c];
+            for (int j = 0; j < 2 * n; j++) aug[r][j] -= f * aug[c][j];
+        }
+    }
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) a[i * n + j] = aug[i][n + j];
+    return 0;
+}
+
+// Monomials x^i y^j with i + j <= 3 (10 of them), their x- and y-derivatives.
+static void monomials3(double x, double y, double *m, double *mx, double *my)
+{
+    int k = 0;
+    for (int d = 0; d <= 3; d++)
+        for (int j = 0; j <= d; j++) {
+            int i = d - j;
+            double xi = std::pow(x, i), yj = std::pow(y, j);
+            m[k] = xi * yj;
+            if (mx) mx[k] = i ? i * std::pow(x, i - 1) * yj : 0.0;
+            if (my) my[k] = j ? j * xi * std::pow(y, j - 1) : 0.0;
+            k++;
+        }
+}
+
+int prism2d(Prism2D &P)
+{
+    std::memset(&P, 0, sizeof(P));
+    // Williams-Shunn triangle points of order 3 as printed in the paper (Sec. 4.1 prism figures)
+    static const double ws[FR_PT][2] = {
+        {-0.333333333333333, -0.333333333333333}, {-0.888871894660414, 0.777743789320828},
+        {0.777743789320828, -0.888871894660414},  {-0.888871894660414, -0.888871894660414},
+        {0.268421495491446, -0.408932576528214},  {-0.859488918963232, -0.408932576528214},
+        {-0.408932576528214, -0.859488918963232}, {0.268421495491446, -0.859488918963232},
+        {-0.859488918963232, 0.268421495491446},  {-0.408932576528214, 0.268421495491446}};
+    std::memcpy(P.xt, ws, sizeof ws);
+    if (hex1d(3, 5, P.z)) return -1;
+    // collapsed 5 x 5 rule: x = (1+a)(1-b)/2 - 1, y = b, w = wa wb (1-b)/2
+    double g[5], gw[5];
+    gauss_legendre(5, g, gw);
+    for (int ib = 0; ib < 5; ib++)
+        for (int ia = 0; ia < 5; ia++) {
+            int q = ia + 5 * ib;
+            P.xq[q][0] = 0.5 * (1.0 + g[ia]) * (1.0 - g[ib]) - 1.0;
+            P.xq[q][1] = g[ib];
+            P.wq[q] = gw[ia] * gw[ib] * 0.5 * (1.0 - g[ib]);
+        }
+    // nodal basis from the monomial Vandermonde matrix: l_t = sum_k m_k C[k][t]
+    double V[FR_PT * FR_PT];
+    for (int t = 0; t < FR_PT; t++) monomials3(P.xt[t][0], P.xt[t][1], &V[t * FR_PT], nullptr, nullptr);
+    if (invert(FR_PT, V)) return -2;   // V now holds C = V^-1: C[k][t]
+    auto nodal = [&](double x, double y, double *l, double *lx, double *ly) {
+        double m[FR_PT], mx[FR_PT], my[FR_PT];
+        monomials3(x, y, m, mx, my);
+        for (int t = 0; t < FR_PT; t++) {
+            double a = 0, b = 0, c = 0;
+            for (int k = 0; k < FR_PT; k++) { a += m[k] * V[k * FR_PT + t]; b += mx[k] * V[k * FR_PT + t]; c += my[k] * V[k * FR_PT + t]; }
+            l[t] = a;
+            if (lx) lx[t] = b;
+            if (ly) ly[t] = c;
+        }
+    };
+    for (int q = 0; q < FR_PQ; q++) nodal(P.xq[q][0], P.xq[q][1], P.Bt[q], nullptr, nullptr);
+    for (int t = 0; t < FR_PT; t++) {
+        double l[FR_PT], lx[FR_PT], ly[FR_PT];
+        nodal(P.xt[t][0], P.xt[t][1], l, lx, ly);
+        for (int u = 0; u < FR_PT; u++) { P.Dx[t][u] = lx[u]; P.Dy[t][u] = ly[u]; }
+    }
+    // mass matrix (the rule is exact to degree 8 >= 6) and its inverse
+    double M[FR_PT * FR_PT];
+    for (int t = 0; t < FR_PT; t++)
+        for (int u = 0; u < FR_PT; u++) {
+            double v = 0;
+            for (int q = 0; q < FR_PQ; q++) v += P.wq[q] * P.Bt[q][t] * P.Bt[q][u];
+            M[t * FR_PT + u] = v;
+        }
+    for (int t = 0; t < FR_PT; t++) {
+        double v = 0;
+        for (int q = 0; q < FR_PQ; q++) v += P.wq[q] * P.Bt[q][t];
+        P.wt[t] = v;
+    }
+    if (invert(FR_PT, M)) return -3;
+    // L2 projection onto the nodal space: Pt = M^-1 Bt^T W
+    for (int t = 0; t < FR_PT; t++)
+        for (int q = 0; q < FR_PQ; q++) {
+            double v = 0;
+            for (int u = 0; u < FR_PT; u++) v += M[t * FR_PT + u] * P.Bt[q][u];
+            P.Pt[t][q] = v * P.wq[q];
+        }
+    // quad faces 2 (y = -1), 3 (x + y = 0), 4 (x = -1): edge parameter s runs over the GL points
+    const double r2 = 1.0 / std::sqrt(2.0);
+    const double nrm[3][2] = {{0.0, -1.0}, {r2, r2}, {-1.0, 0.0}};
+    const double jac[3] = {1.0, std::sqrt(2.0), 1.0};   // reference arc length per unit s
+    for (int f = 0; f < 3; f++) {
+        P.nf[f][0] = nrm[f][0];
+        P.nf[f][1] = nrm[f][1];
+        for (int a = 0; a < FR_PE; a++) {
+            double s = P.z.x[a], x, y;
+            if (f == 0) { x = s; y = -1.0; }
+            else if (f == 1) { x = -s; y = s; }
+            else { x = -1.0; y = s; }
+            nodal(x, y, P.Ef[f][a], nullptr, nullptr);
+        }
+        // E_edge[t][a] = int_edge l_t l_a ds = jac w_a l_t(edge point a) (GL exact for degree 6);
+        // lift L_f = M^-1 E_edge
+        for (int t = 0; t < FR_PT; t++)
+            for (int a = 0; a < FR_PE; a++) {
+                double v = 0;
+                for (int u = 0; u < FR_PT; u++) v += M[t * FR_PT + u] * jac[f] * P.z.w[a] * P.Ef[f][a][u];
+                P.Lf[f][t][a] = v;
+            }
+    }
+    // corrected in-plane derivatives (the factored M4 - M6 M0 and M1 - M3 M2 in the triangle plane)
+    for (int t = 0; t < FR_PT; t++)
+        for (int u = 0; u < FR_PT; u++) {
+            double cx = 0, cy = 0;
+            for (int f = 0; f < 3; f++)
+                for (int a = 0; a < FR_PE; a++) {
+                    cx += P.nf[f][0] * P.Lf[f][t][a] * P.Ef[f][a][u];
+                    cy += P.nf[f][1] * P.Lf[f][t][a] * P.Ef[f][a][u];
+                }
+            P.Dhx[t][u] = P.Dx[t][u] - cx;
+            P.Dhy[t][u] = P.Dy[t][u] - cy;
+        }
+    return 0;
+}
+
 }  // namespace frb

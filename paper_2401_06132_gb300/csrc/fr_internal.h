@@ -34,6 +34,26 @@ struct Hex1D {
 };
 int hex1d(int p, int m, Hex1D &h);
 
+// Prism of order 3: 10 triangle points (the paper's Williams-Shunn set) x 4 GL levels in z;
+// quadrature: collapsed 5 x 5 triangle rule x 5 GL points in z (125 points).
+#define FR_PT 10      // triangle solution points
+#define FR_PQ 25      // triangle quadrature points
+#define FR_PE 4       // points per triangle edge (and z levels)
+struct Prism2D {
+    double xt[FR_PT][2];          // triangle solution points
+    double wt[FR_PT];             // int l_t over the reference triangle
+    double xq[FR_PQ][2], wq[FR_PQ];
+    double Bt[FR_PQ][FR_PT];      // triangle interpolation solution -> quadrature points
+    double Pt[FR_PT][FR_PQ];      // triangle L2 projection quadrature -> solution points
+    double Dx[FR_PT][FR_PT], Dy[FR_PT][FR_PT];   // in-plane derivatives d l_t'/dx (x_t)
+    double Dhx[FR_PT][FR_PT], Dhy[FR_PT][FR_PT]; // corrected: D - sum_f n_f L_f E_f
+    double Ef[3][FR_PE][FR_PT];   // interpolation to the edge points of quad faces 2, 3, 4
+    double Lf[3][FR_PT][FR_PE];   // DG lift of quad faces 2, 3, 4 (triangle part; identity in z)
+    double nf[3][2];              // unit reference normals (x, y) of quad faces 2, 3, 4
+    Hex1D z;                      // 1D operators along z (p = 3, m = 5)
+};
+int prism2d(Prism2D &P);
+
 }  // namespace frb
 
 // ---------------------------------------------------------------------------------------------
@@ -49,11 +69,25 @@ struct HexOps {
     T w[FR_MAXN];
 };
 
+// Prism (p = 3) operator tables: triangle part dense, z part 1D.
+template <typename T>
+struct PriOps {
+    T Bt[FR_PQ][FR_PT];
+    T Pt[FR_PT][FR_PQ];
+    T Dhx[FR_PT][FR_PT], Dhy[FR_PT][FR_PT];
+    T Ef[3][FR_PE][FR_PT];
+    T Lf[3][FR_PT][FR_PE];
+    T nf[3][2];
+    T Bz[5][FR_PE], Pz[FR_PE][5], Dhz[FR_PE][FR_PE];
+    T lzL[FR_PE], lzR[FR_PE], liftzL[FR_PE], liftzR[FR_PE];
+};
+
 // Physical constants of an instance, in the compute precision.
 template <typename T>
 struct Phys {
     T gamma, gm1, mu, beta, tau;
     T heat;       // mu gamma / ((gamma - 1) Pr)
+    T pref;       // reference pressure removed from the momentum flux
 };
 
 // Geometry of one affine element: inverse Jacobian (row-major dxi_i/dx_j) and its determinant.
@@ -98,10 +132,36 @@ struct HexArgs {
     T *QQ;                    // unfused: [elem][5][3][nq] gradient, later transformed flux, at qpts
     T *Rt;                    // unfused: [elem][5][nu] R~
     int *status;              // device status word (bit 0: non-physical state)
+    // Batched launch over several blocks of one element type and order (all null for one block):
+    // per element its first value in U/R, its first global flux point and its instance's physics.
+    const long long *eu0;
+    const long long *ef0;
+    const int *eph;
+    const Phys<T> *phtab;
 };
+
+#ifdef __CUDACC__
+template <typename T>
+__device__ __forceinline__ long long elem_u0(const HexArgs<T> &a, long long e, int nu)
+{
+    return a.eu0 ? a.eu0[e] : a.u0 + e * FR_NV * nu;
+}
+template <typename T>
+__device__ __forceinline__ long long elem_f0(const HexArgs<T> &a, long long e, int nf)
+{
+    return a.ef0 ? a.ef0[e] : a.f0 + e * nf;
+}
+template <typename T>
+__device__ __forceinline__ Phys<T> elem_phys(const HexArgs<T> &a, long long e)
+{
+    return a.eph ? a.phtab[a.eph[e]] : a.ph;
+}
+#endif
 
 // Launchers (fr_hex.cu). phase: 0 = A (face solution), 1 = B (volume group), 2 = C (interfaces).
 template <typename T> int hex_fused_phase(int p, int phase, const HexArgs<T> &a, cudaStream_t s);
 // kernel: 1..13 in the paper's order (disu .. negdivconf)
 template <typename T> int hex_unfused_kernel(int p, int kernel, const HexArgs<T> &a, cudaStream_t s);
 int hex_upload_ops(int p, int m, const frb::Hex1D &h);
+// Prism kernels (fr_pri.cu); the operator tables are passed by device pointer.
+template <typename T> int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, cudaStream_t s);

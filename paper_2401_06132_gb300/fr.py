@@ -30,7 +30,7 @@ class FRError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("Pr", C.c_double), ("mu", C.c_double), ("beta", C.c_double),
                 ("tau", C.c_double), ("p", C.c_int), ("nq1d", C.c_int), ("tri_strength", C.c_int),
-                ("prec", C.c_int), ("rusanov_mode", C.c_int)]
+                ("prec", C.c_int), ("rusanov_mode", C.c_int), ("p_ref", C.c_double)]
 
 
 class MeshDesc(C.Structure):
@@ -67,6 +67,7 @@ def lib():
             "fr_stage": ([vp, C.c_int, dp, C.c_longlong, llp], C.c_int),
             "fr_last_error": ([], C.c_char_p),
             "fr_set_timing": ([vp, C.c_int], C.c_int),
+            "fr_set_graph": ([vp, C.c_int], C.c_int),
             "fr_kernel_times": ([vp, C.POINTER(C.c_double), llp, C.c_int], C.c_int),
             "fr_probe_fma": ([dp, vp], C.c_int),
         }
@@ -88,8 +89,9 @@ def _stream_ptr(stream):
     return C.c_void_p(s.cuda_stream)
 
 
-def make_params(p=3, gamma=1.4, Pr=0.71, mu=1.0 / 1600, beta=0.5, tau=0.1, prec="fp64", nq1d=0, tri_strength=0):
-    return Params(gamma, Pr, mu, beta, tau, p, nq1d, tri_strength, PRECISIONS[prec], 0)
+def make_params(p=3, gamma=1.4, Pr=0.71, mu=1.0 / 1600, beta=0.5, tau=0.1, prec="fp64", nq1d=0, tri_strength=0,
+                p_ref=0.0):
+    return Params(gamma, Pr, mu, beta, tau, p, nq1d, tri_strength, PRECISIONS[prec], 0, p_ref)
 
 
 class FRMesh:
@@ -200,6 +202,9 @@ class FRMesh:
             o = out[8 * i:8 * i + 8]
             res.append(dict(volume=o[0], Ek=o[1], eps=o[2], sums=o[3:8].copy()))
         return res
+
+    def set_graph(self, on: bool):
+        _check(lib().fr_set_graph(self.h, int(on)))
 
     def set_timing(self, on: bool):
         _check(lib().fr_set_timing(self.h, int(on)))

@@ -111,3 +111,24 @@ def test_tgv_state_layout():
     V = W.tgv_conserved(xyz)
     assert U.shape == (2 * 5 * 64,)
     np.testing.assert_array_equal(U.reshape(2, 5, 64)[1, 4], V[4, 64:])
+
+
+def test_host_validation_prisms(lib):
+    # prisms are built for p = 3 only
+    with pytest.raises(fr.FRError) as e:
+        _create(W.mixed_box_mesh(2), p=4)
+    assert e.value.status == fr.FR_EUNSUPPORTED
+    # a non-affine prism (top triangle sheared differently from the bottom one)
+    mesh = W.mixed_box_mesh(2)
+    mesh["verts"] = mesh["verts"].copy()
+    top = mesh["pri_v"][0, 4]
+    mesh["verts"][top] += np.array([0.05, 0.0, 0.0])
+    with pytest.raises(fr.FRError) as e:
+        _create(mesh)
+    assert e.value.status in (fr.FR_EUNSUPPORTED, fr.FR_EMESH)
+    # a prism mesh with one prism removed leaves faces without partners
+    mesh = W.mixed_box_mesh(2)
+    mesh["pri_v"] = mesh["pri_v"][1:].copy()
+    with pytest.raises(fr.FRError) as e:
+        _create(mesh)
+    assert e.value.status == fr.FR_EMESH

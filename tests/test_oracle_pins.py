@@ -493,3 +493,26 @@ def test_split_hex_into_prisms_matches_hex_on_linear_fields():
     d = o.diagnostics(U, o.rhs(U))
     assert abs(d["sums"][0]) <= 1e-12 * d["abs_sums"][0]
     assert abs(d["volume"] - (2 * np.pi) ** 3) < 1e-10
+
+
+@pytest.mark.parametrize("name", ["hex16", "mixed4", "sheared3"])
+def test_reference_pressure_is_an_identity(name):
+    """Removing a constant p_ref from the momentum flux, in the volume and at interfaces, changes the
+    RHS only by rounding on affine meshes (a constant flux has zero divergence and its common flux
+    equals its own normal flux). Removing it from the volume flux alone would change the RHS by
+    O(p_ref (p+1)^2/h); here the change must stay at the plain oracle's rounding floor."""
+    mesh = {"hex16": lambda: W.box_hex_mesh(16), "mixed4": lambda: W.mixed_box_mesh(4),
+            "sheared3": lambda: W.sheared_box_mesh(3)}[name]()
+    p0 = W.tgv_p0()
+    o0 = O.Oracle(mesh, 3, 5, threads=os.cpu_count())
+    o1 = O.Oracle(mesh, 3, 5, threads=os.cpu_count(), p_ref=p0)
+    U = _tgv(o0, mesh, perturb=1e-3)
+    R0, R1 = o0.rhs(U), o1.rhs(U)
+    blocks = _layout(o0, mesh)
+    off = 0
+    for ne, nu in blocks:
+        n = ne * 5 * nu
+        a, b = R0[off:off + n].reshape(ne, 5, nu), R1[off:off + n].reshape(ne, 5, nu)
+        rel = np.abs(a - b).max(axis=(0, 2)) / np.abs(a).max(axis=(0, 2))
+        assert rel.max() < 5e-12, rel
+        off += n
