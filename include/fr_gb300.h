@@ -156,6 +156,18 @@ fr_status fr_instance_offsets(const fr_mesh *m, long long *off);
  * Synchronises the stream. */
 fr_status fr_diagnostics(fr_mesh *m, const void *U_dev, const void *R_dev, double *out, void *stream);
 
+/* Same results as fr_diagnostics, for callers that must not allocate device memory (for example
+ * while another framework owns the device memory budget, in a real-time loop that cannot afford the
+ * device-wide synchronisation a cudaMalloc may cause, or while a thread captures other work into a
+ * CUDA graph in global mode, where cudaMalloc is not allowed). The paper has no counterpart: this is
+ * a service of the library. It allocates nothing: its accumulators are a fixed array of
+ * 1024 x 8 doubles (64 KiB) compiled into the library, which every GPU that loads the library holds
+ * until the process exits; handles with more than 1024 instances get FR_EINVAL. The first call on a
+ * device looks up that array's device address, so make that first call before any stream capture.
+ * All calls share the one array and each call clears only the slots it uses: calls that overlap on
+ * the GPU (other streams, other threads) race and give wrong sums. Synchronises the stream. */
+fr_status fr_diagnostics_noalloc(fr_mesh *m, const void *U_dev, const void *R_dev, double *out, void *stream);
+
 /* Copies an intermediate array of the last UNFUSED RHS to a host FP64 array, for stage-level
  * checks. which: 0 U^(f) [var][fpt], 1 C^(f) [var][fpt], 2 physical gradient Q^(u)
  * [elem][var][dim][pt], 3 Q^(f) [var][dim][fpt], 4 projected flux F~^(u) [elem][var][dim][pt],

@@ -1059,6 +1059,81 @@ extern "C" fr_status fr_diagnostics(fr_mesh *m, const void *U, const void *R, do
     return FR_OK;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Diagnostics without any allocation
+//
+// fr_diagnostics allocates its device accumulators with cudaMalloc on first use. Callers that must
+// not allocate device memory -- code running while another framework owns the device memory budget,
+// a real-time loop that cannot afford the device-wide synchronisation a cudaMalloc may cause, or a
+// thread that is capturing other work into a CUDA graph in global capture mode, where cudaMalloc is
+// not allowed -- use fr_diagnostics_noalloc instead. Its accumulators live in the fixed array below,
+// which every GPU that loads this library holds until the process exits.
+// ---------------------------------------------------------------------------------------------
+#define FR_NOALLOC_MAX_INST 1024
+static __device__ __align__(256) double g_diag_scratch[FR_NOALLOC_MAX_INST * 8];
+
+// Device address of g_diag_scratch, looked up once per device (the host-side symbol is only a
+// stand-in and must never be handed to a kernel).
+static double *diag_scratch_ptr(int dev, cudaError_t *err)
+{
+    static double *ptrs[64] = {nullptr};
+    *err = cudaSuccess;
+    if (dev < 0 || dev >= 64) { *err = cudaErrorInvalidDevice; return nullptr; }
+    if (!ptrs[dev]) {
+        double *p = nullptr;
+        *err = cudaGetSymbolAddress((void **)&p, g_diag_scratch);
+        if (*err != cudaSuccess) return nullptr;
+        ptrs[dev] = p;
+    }
+    return ptrs[dev];
+}
+
+extern "C" fr_status fr_diagnostics_noalloc(fr_mesh *m, const void *U, const void *R, double *out, void *stream)
+{
+    if (!m || !U || !out) return fail(FR_EINVAL, "null argument");
+    const int ni = (int)m->inst.size();
+    if (ni > FR_NOALLOC_MAX_INST)
+        return fail(FR_EINVAL, "fr_diagnostics_noalloc: %d instances exceed the fixed scratch limit of %d", ni,
+                    FR_NOALLOC_MAX_INST);
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    cudaError_t ce;
+    double *acc = diag_scratch_ptr(dev, &ce);
+    if (!acc) return fail(FR_ECUDA, "cudaGetSymbolAddress(g_diag_scratch): %s", cudaGetErrorString(ce));
+    cudaStream_t s = (cudaStream_t)stream;
+    // the array keeps the previous call's sums: clear the slots this call accumulates into
+    CU(cudaMemsetAsync(acc, 0, (size_t)ni * 8 * sizeof(double), s));
+    for (size_t bi = 0; bi < m->blocks.size(); bi++) {
+        const Block &b = m->blocks[bi];
+        WPts wp{};
+        const frb::Hex1D &h = m->hex1d[bi];
+        for (int z = 0; z < b.nu; z++)
+            wp.w[z] = b.type == 0 ? h.w[z % h.n] * h.w[(z / h.n) % h.n] * h.w[z / (h.n * h.n)]
+                                  : m->pri.wt[z % FR_PT] * h.w[z / FR_PT];
+        int grid = (int)std::min<long long>(std::max<long long>(b.ne, 1), 152LL * 8);
+        double *o = acc + 8 * b.inst;
+        size_t ts = tsize(m->prec);
+        const char *u = (const char *)U + b.u0 * ts;
+        const char *r = R ? (const char *)R + b.u0 * ts : nullptr;
+        if (m->prec == FR_FP64)
+            k_diag<double><<<grid, 128, 0, s>>>((const double *)u, (const double *)r,
+                                                 (const Geo<double> *)m->d_geo + b.elem0, b.ne, b.nu, wp, o);
+        else
+            k_diag<float><<<grid, 128, 0, s>>>((const float *)u, (const float *)r,
+                                                (const Geo<float> *)m->d_geo + b.elem0, b.ne, b.nu, wp, o);
+        CU(cudaPeekAtLastError());
+    }
+    // raw sums straight into the caller's array, then normalised in place (no host buffer either)
+    CU(cudaMemcpyAsync(out, acc, (size_t)ni * 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    for (int i = 0; i < ni; i++) {
+        double *o = out + 8 * i;
+        o[1] /= o[0];
+        o[2] /= o[0];
+    }
+    return FR_OK;
+}
+
 extern "C" fr_status fr_stage(fr_mesh *m, int which, double *host, long long n_host, long long *n_needed)
 {
     if (!m) return fail(FR_EINVAL, "null handle");

@@ -64,6 +64,7 @@ def lib():
             "fr_sol_coords": ([vp, dp], C.c_int),
             "fr_instance_offsets": ([vp, llp], C.c_int),
             "fr_diagnostics": ([vp, vp, vp, dp, vp], C.c_int),
+            "fr_diagnostics_noalloc": ([vp, vp, vp, dp, vp], C.c_int),
             "fr_stage": ([vp, C.c_int, dp, C.c_longlong, llp], C.c_int),
             "fr_last_error": ([], C.c_char_p),
             "fr_set_timing": ([vp, C.c_int], C.c_int),
@@ -215,6 +216,15 @@ class FRMesh:
         cnt = (C.c_longlong * n_ids)()
         _check(lib().fr_kernel_times(self.h, ms, cnt, n_ids))
         return {i: (ms[i], cnt[i]) for i in range(n_ids) if cnt[i]}
+
+    def diagnostics_noalloc(self, U, R=None, stream=None):
+        """fr_diagnostics_noalloc: the same sums through the entry point that allocates nothing."""
+        out = np.zeros(8 * self.n_inst)
+        _check(lib().fr_diagnostics_noalloc(self.h, C.c_void_p(U.data_ptr()),
+                                            C.c_void_p(R.data_ptr() if R is not None else 0),
+                                            out.ctypes.data_as(C.POINTER(C.c_double)), _stream_ptr(stream)))
+        return [dict(volume=out[8 * i], Ek=out[8 * i + 1], eps=out[8 * i + 2], sums=out[8 * i + 3:8 * i + 8].copy())
+                for i in range(self.n_inst)]
 
     def stage(self, which: int) -> np.ndarray:
         n = C.c_longlong(0)
