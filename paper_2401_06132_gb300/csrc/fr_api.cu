@@ -56,6 +56,8 @@ struct Group {
     long long *d_eu0 = nullptr, *d_ef0 = nullptr;
     int *d_eph = nullptr;
     void *d_phtab = nullptr;        // Phys<T> per instance
+    uint32_t *d_lpts = nullptr;     // L flux points of the group (element_in_group * 256 + local)
+    long long nlpts = 0;
 };
 
 struct fr_mesh {
@@ -71,6 +73,7 @@ struct fr_mesh {
     bool has_pri = false;
     void *d_priops = nullptr;            // PriOps<T> on the device
     std::vector<Group> groups;
+    bool split_c = false;              // interface phase as pair flux (C1) + lift (C2)
     std::vector<double> geo_host;        // per element Ji[9], det (FP64)
     // device
     void *d_geo = nullptr;               // Geo<T>[ne]
@@ -533,7 +536,7 @@ static Phys<T> phys_of(const fr_params &P)
 }
 
 template <typename T>
-static fr_status build_groups(fr_mesh *m)
+static fr_status build_groups(fr_mesh *m, const std::vector<uint32_t> &partner)
 {
     for (size_t b = 0; b < m->blocks.size(); b++) {
         const Block &B = m->blocks[b];
@@ -546,6 +549,20 @@ static fr_status build_groups(fr_mesh *m)
     std::vector<Phys<T>> tab;
     for (const InstanceHost &I : m->inst) tab.push_back(phys_of<T>(I.prm));
     for (Group &g : m->groups) {
+        // L points for the split interface phase
+        std::vector<uint32_t> lp;
+        long long eg = 0;
+        for (int bi : g.blks) {
+            const Block &B = m->blocks[bi];
+            for (long long e = 0; e < B.ne; e++, eg++)
+                for (int sp = 0; sp < B.nf; sp++)
+                    if (partner[(size_t)(B.f0 + e * B.nf + sp)] & FR_LFLAG) lp.push_back((uint32_t)(eg * 256 + sp));
+        }
+        if (eg >= (1LL << 24)) return fail(FR_EUNSUPPORTED, "more than 2^24 elements of one type and order");
+        g.nlpts = (long long)lp.size();
+        fr_status sl = dalloc(m, (void **)&g.d_lpts, lp.size() * sizeof(uint32_t));
+        if (sl) return sl;
+        CU(cudaMemcpy(g.d_lpts, lp.data(), lp.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
         if (g.blks.size() < 2) continue;
         std::vector<Geo<T>> geo;
         std::vector<long long> eu0, ef0;
@@ -593,7 +610,10 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
     size_t ts = tsize(m->prec);
     st = (m->prec == FR_FP64) ? upload_geo<double>(m) : upload_geo<float>(m);
     if (!st) st = (m->prec == FR_FP64) ? upload_priops<double>(m) : upload_priops<float>(m);
-    if (!st) st = (m->prec == FR_FP64) ? build_groups<double>(m) : build_groups<float>(m);
+    if (!st) st = (m->prec == FR_FP64) ? build_groups<double>(m, partner) : build_groups<float>(m, partner);
+    // FP64 hexahedral handles evaluate each interface pair once (split interface phase)
+    m->split_c = (m->prec == FR_FP64) && !m->has_pri;
+    if (!st && m->split_c) st = dalloc(m, &m->d_DF, (size_t)5 * m->nfpt * ts);
     if (!st) st = dalloc(m, (void **)&m->d_partner, partner.size() * sizeof(uint32_t));
     if (!st && cudaMemcpy(m->d_partner, partner.data(), partner.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess)
         st = fail(FR_ECUDA, "partner upload failed");
@@ -618,6 +638,7 @@ extern "C" fr_status fr_destroy(fr_mesh *m)
     for (void **b : bufs) dfree(*b);
     for (Group &g : m->groups) {
         dfree(g.d_geo); dfree((void *&)g.d_eu0); dfree((void *&)g.d_ef0); dfree((void *&)g.d_eph); dfree(g.d_phtab);
+        dfree((void *&)g.d_lpts);
     }
     if (m->h_status) cudaFreeHost(m->h_status);
     for (auto &t : m->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
@@ -733,11 +754,23 @@ static fr_status post_status(fr_mesh *m, cudaStream_t s)
     return FR_OK;
 }
 
+// RK4 stage folded into the fused interface kernel (stage < 0: plain RHS).
+struct RkFold {
+    int stage = -1;
+    double dt = 0;
+    double *U = nullptr, *acc = nullptr;
+    void *us = nullptr;
+};
+
 template <typename T>
-static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s)
+static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, const RkFold &rk = RkFold())
 {
     if (m->form == FR_FUSED) {
-        for (int ph = 0; ph < 3; ph++) {
+        static const int plain[3] = {0, 1, 2}, split[4] = {0, 1, 3, 4};
+        const int *phases = m->split_c ? split : plain;
+        const int nph = m->split_c ? 4 : 3;
+        for (int pi = 0; pi < nph; pi++) {
+            const int ph = phases[pi];
             TimeScope ts(m, ph, s);
             for (const Group &gr : m->groups) {
                 const Block &b = m->blocks[gr.blks[0]];
@@ -747,6 +780,11 @@ static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s)
                     a.geo = reinterpret_cast<const Geo<T> *>(gr.d_geo);
                     a.eu0 = gr.d_eu0; a.ef0 = gr.d_ef0; a.eph = gr.d_eph;
                     a.phtab = reinterpret_cast<const Phys<T> *>(gr.d_phtab);
+                }
+                a.lpts = gr.d_lpts; a.nlpts = gr.nlpts;
+                if ((ph == 2 || ph == 4) && rk.stage >= 0) {
+                    a.rkstage = rk.stage + 1; a.rkdt = rk.dt; a.rkU = rk.U; a.rkacc = rk.acc;
+                    a.rkus = reinterpret_cast<T *>(rk.us);
                 }
                 int lr = b.type == 0 ? hex_fused_phase<T>(b.p, ph, a, s)
                                      : pri_fused_phase<T>(ph, a, reinterpret_cast<const PriOps<T> *>(m->d_priops), s);
@@ -861,6 +899,14 @@ static fr_status rk4_enqueue_step(fr_mesh *m, double *U, double dt, cudaStream_t
         u0 = m->d_rk_us;
     }
     for (int st = 0; st < 4; st++) {
+        if (m->form == FR_FUSED) {
+            // the stage update is folded into the interface kernel: no RHS array, no extra launch
+            RkFold rk;
+            rk.stage = st; rk.dt = dt; rk.U = U; rk.acc = m->d_rk_acc; rk.us = m->d_rk_us;
+            fr_status r = rhs_impl<T>(m, st == 0 ? u0 : m->d_rk_us, m->d_rk_k, s, rk);
+            if (r) return r;
+            continue;
+        }
         fr_status r = rhs_dispatch(m, st == 0 ? u0 : m->d_rk_us, m->d_rk_k, s);
         if (r) return r;
         TimeScope ts(m, 30, s);
@@ -947,7 +993,7 @@ extern "C" fr_status fr_mesh_info(const fr_mesh *m, long long *info)
 {
     if (!m || !info) return fail(FR_EINVAL, "null argument");
     info[0] = m->ne; info[1] = m->nU; info[2] = m->nfpt; info[3] = m->npair; info[4] = (long long)m->inst.size();
-    info[5] = m->form == FR_FUSED ? 3 * (long long)m->groups.size() : 13;
+    info[5] = m->form == FR_FUSED ? (m->split_c ? 4 : 3) * (long long)m->groups.size() : 13;
     info[6] = m->bytes;
     return FR_OK;
 }

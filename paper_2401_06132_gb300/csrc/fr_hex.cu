@@ -95,6 +95,43 @@ __global__ void __launch_bounds__(256) k_disu(HexArgs<T> a)
     }
 }
 
+// Fused phase A: the same disu over blocks of EB elements. The block's solution is staged in shared
+// memory with coalesced loads (each element's 5 x n^3 values are contiguous), then every thread
+// writes one flux-point value; consecutive threads write consecutive flux points of one variable.
+template <typename T, int P, int EB, int NT>
+__global__ void __launch_bounds__(NT) k_disu_blk(HexArgs<T> a)
+{
+    constexpr int N = P + 1, NU = N * N * N, NF = 6 * N * N;
+    __shared__ T s_u[EB * FR_NV * NU];
+    const HexOps<T> &op = OPS<T>(P - 2);
+    for (long long e0 = (long long)blockIdx.x * EB; e0 < a.ne; e0 += (long long)gridDim.x * EB) {
+        const int nb = (int)((a.ne - e0) < EB ? (a.ne - e0) : EB);
+        if (a.eu0 == nullptr) {
+            const T *src = a.U + a.u0 + e0 * FR_NV * NU;
+            for (int i = threadIdx.x; i < nb * FR_NV * NU; i += NT) s_u[i] = src[i];
+        } else {
+            for (int i = threadIdx.x; i < nb * FR_NV * NU; i += NT) {
+                const int el = i / (FR_NV * NU), r = i % (FR_NV * NU);
+                s_u[i] = a.U[a.eu0[e0 + el] + r];
+            }
+        }
+        __syncthreads();
+        for (int it = threadIdx.x; it < FR_NV * nb * NF; it += NT) {
+            const int alpha = it / (nb * NF), r = it % (nb * NF), el = r / NF, sp = r % NF;
+            const int f = sp / (N * N), loc = sp % (N * N);
+            int base, stride;
+            face_line<N>(f, loc, base, stride);
+            const T *u = s_u + (el * FR_NV + alpha) * NU + base;
+            const T *l = (f & 1) ? op.lR : op.lL;
+            T v = T(0);
+#pragma unroll
+            for (int i = 0; i < N; i++) v += l[i] * u[i * stride];
+            a.UF[alpha * a.nfpt + elem_f0(a, e0 + el, NF) + sp] = v;
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Fused phase B: the per-element volume group
 // ---------------------------------------------------------------------------------------------
@@ -217,6 +254,8 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
     T *s_w = s_c + 5 * NF;
     T *s_t1 = s_w + 20 * NQ;
     T *s_t2 = s_t1 + S::T1;
+    __shared__ short s_list[NF];
+    __shared__ int s_cnt;
     const HexOps<T> &op = OPS<T>(P - 2);
 
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
@@ -255,17 +294,40 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
             }
         }
         __syncthreads();
-        // 4. gradcoru: q = J^-T q~ (per point, all three components)
+        // 4. gradcoru: q = J^-T q~ (per point, all three components; diagonal J^-1 is common)
+        const bool diagJ = g.Ji[1] == T(0) && g.Ji[2] == T(0) && g.Ji[3] == T(0) && g.Ji[5] == T(0) &&
+                           g.Ji[6] == T(0) && g.Ji[7] == T(0);
         for (int it = threadIdx.x; it < 5 * NU; it += NT) {
             const int alpha = it / NU, z = it % NU;
             T *q = s_q + alpha * 3 * NU + z;
-            const T q0 = q[0], q1 = q[NU], q2 = q[2 * NU];
+            if (diagJ) {
+                q[0] *= g.Ji[0]; q[NU] *= g.Ji[4]; q[2 * NU] *= g.Ji[8];
+            } else {
+                const T q0 = q[0], q1 = q[NU], q2 = q[2 * NU];
 #pragma unroll
-            for (int k = 0; k < 3; k++) q[k * NU] = g.Ji[k] * q0 + g.Ji[3 + k] * q1 + g.Ji[6 + k] * q2;
+                for (int k = 0; k < 3; k++) q[k * NU] = g.Ji[k] * q0 + g.Ji[3 + k] * q1 + g.Ji[6 + k] * q2;
+            }
+        }
+        // 5. gradcoru_fpts + the viscous part of comm_flux: own-normal n.f^v at own flux points.
+        //    The LDG flux weighs the two sides by 1/2 + beta (L) and 1/2 - beta (R); a side whose
+        //    weight is exactly zero (beta = +-1/2) is not evaluated. The needed points are compacted
+        //    so that whole warps do the work.
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+        for (int s = threadIdx.x; s < NF; s += NT) {
+            const bool isL = (a.partner[gf0 + s] & FR_LFLAG) != 0;
+            const T wgt = isL ? T(0.5) + ph.beta : T(0.5) - ph.beta;
+            if (wgt == T(0)) {
+#pragma unroll
+                for (int k = 0; k < 4; k++) a.FV[k * a.nfpt + gf0 + s] = T(0);
+            } else {
+                s_list[atomicAdd(&s_cnt, 1)] = (short)s;
+            }
         }
         __syncthreads();
-        // 5. gradcoru_fpts + the viscous part of comm_flux: own-normal n.f^v at own flux points
-        for (int s = threadIdx.x; s < NF; s += NT) {
+        const int nlist = s_cnt;
+        for (int li = threadIdx.x; li < nlist; li += NT) {
+            const int s = s_list[li];
             const int f = s / (N * N), loc = s % (N * N);
             int base, stride;
             face_line<N>(f, loc, base, stride);
@@ -307,11 +369,21 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
                 for (int d = 0; d < 3; d++) gq[alpha][d] = s_w[(5 + alpha * 3 + d) * NQ + q];
             }
             ok &= total_flux(ph, u, gq, f);
+            if (diagJ) {
+                const T s0 = g.det * g.Ji[0], s1 = g.det * g.Ji[4], s2 = g.det * g.Ji[8];
 #pragma unroll
-            for (int alpha = 0; alpha < 5; alpha++)
+                for (int alpha = 0; alpha < 5; alpha++) {
+                    s_w[(alpha * 3 + 0) * NQ + q] = s0 * f[0][alpha];
+                    s_w[(alpha * 3 + 1) * NQ + q] = s1 * f[1][alpha];
+                    s_w[(alpha * 3 + 2) * NQ + q] = s2 * f[2][alpha];
+                }
+            } else {
 #pragma unroll
-                for (int d = 0; d < 3; d++)
-                    s_w[(alpha * 3 + d) * NQ + q] = g.det * (g.Ji[3 * d] * f[0][alpha] + g.Ji[3 * d + 1] * f[1][alpha] + g.Ji[3 * d + 2] * f[2][alpha]);
+                for (int alpha = 0; alpha < 5; alpha++)
+#pragma unroll
+                    for (int d = 0; d < 3; d++)
+                        s_w[(alpha * 3 + d) * NQ + q] = g.det * (g.Ji[3 * d] * f[0][alpha] + g.Ji[3 * d + 1] * f[1][alpha] + g.Ji[3 * d + 2] * f[2][alpha]);
+            }
         }
         flag_status(a.status, ok);
         __syncthreads();
@@ -380,7 +452,74 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
             v += op.liftL[i] * D[0 * N * N + j + N * k] + op.liftR[i] * D[1 * N * N + j + N * k];
             v += op.liftL[j] * D[2 * N * N + i + N * k] + op.liftR[j] * D[3 * N * N + i + N * k];
             v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
-            R[it] = v * idet;
+            if (a.rkstage == 0) R[it] = v * idet;
+            else rk_fold(a, elem_u0(a, e, NU) + it, v * idet);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Split interface phase: C1 common flux once per pair, C2 lift
+// ---------------------------------------------------------------------------------------------
+template <typename T, int P>
+__global__ void __launch_bounds__(128) k_pair_flux(HexArgs<T> a)
+{
+    constexpr int N = P + 1, NF = 6 * N * N;
+    bool ok = true;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < a.nlpts; it += (long long)gridDim.x * blockDim.x) {
+        const uint32_t code = a.lpts[it];
+        const long long e = code >> 8;
+        const int s = code & 255, f = s / (N * N);
+        const long long gl = elem_f0(a, e, NF) + s;
+        const long long gr = a.partner[gl] & ~FR_LFLAG;
+        const Phys<T> ph = elem_phys(a, e);
+        T uL[5], uR[5], fvL[4], fvR[4];
+#pragma unroll
+        for (int k = 0; k < 5; k++) { uL[k] = a.UF[k * a.nfpt + gl]; uR[k] = a.UF[k * a.nfpt + gr]; }
+#pragma unroll
+        for (int k = 0; k < 4; k++) { fvL[k] = a.FV[k * a.nfpt + gl]; fvR[k] = a.FV[k * a.nfpt + gr]; }
+        T n[3], mag;
+        face_normal(a.geo[e], f, n, mag);
+        T F[5];
+        ok &= common_flux(ph, uL, uR, fvL, fvR, n, F);
+#pragma unroll
+        for (int k = 0; k < 5; k++) a.DF[k * a.nfpt + gl] = F[k];
+    }
+    flag_status(a.status, ok);
+}
+
+template <typename T, int P, int NT>
+__global__ void __launch_bounds__(NT) k_lift(HexArgs<T> a)
+{
+    constexpr int N = P + 1, NU = N * N * N, NF = 6 * N * N;
+    __shared__ T s_d[5 * NF];
+    const HexOps<T> &op = OPS<T>(P - 2);
+    for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
+        const Geo<T> g = a.geo[e];
+        const long long gf0 = elem_f0(a, e, NF);
+        for (int s = threadIdx.x; s < NF; s += NT) {
+            const uint32_t pc = a.partner[gf0 + s];
+            const bool isL = (pc & FR_LFLAG) != 0;
+            const long long src = isL ? gf0 + s : (long long)(pc & ~FR_LFLAG);
+            T n[3], mag;
+            face_normal(g, s / (N * N), n, mag);
+            const T sc = isL ? mag : -mag;
+#pragma unroll
+            for (int k = 0; k < 5; k++) s_d[k * NF + s] = sc * a.DF[k * a.nfpt + src];
+        }
+        __syncthreads();
+        T *R = a.R + elem_u0(a, e, NU);
+        const T idet = T(-1) / g.det;
+        for (int it = threadIdx.x; it < 5 * NU; it += NT) {
+            const int alpha = it / NU, z = it % NU, i = z % N, j = (z / N) % N, k = z / (N * N);
+            const T *D = s_d + alpha * NF;
+            T v = R[it];
+            v += op.liftL[i] * D[0 * N * N + j + N * k] + op.liftR[i] * D[1 * N * N + j + N * k];
+            v += op.liftL[j] * D[2 * N * N + i + N * k] + op.liftR[j] * D[3 * N * N + i + N * k];
+            v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
+            if (a.rkstage == 0) R[it] = v * idet;
+            else rk_fold(a, elem_u0(a, e, NU) + it, v * idet);
         }
         __syncthreads();
     }
@@ -649,7 +788,10 @@ static int fused_phase(int phase, const HexArgs<T> &a, cudaStream_t s)
     constexpr int N = P + 1, NF = 6 * N * N;
     if (a.ne == 0) return 0;
     if (phase == 0) {
-        k_disu<T, P><<<grid_for(a.ne * 5 * NF, 256), 256, 0, s>>>(a);
+        constexpr int EB = 8;
+        long long g = (a.ne + EB - 1) / EB;
+        if (g > 152LL * 16) g = 152LL * 16;
+        k_disu_blk<T, P, EB, 256><<<(int)g, 256, 0, s>>>(a);
     } else if (phase == 1) {
         constexpr int NT = 128;
         const size_t smem = HexSmem<T, P>::SIZE * sizeof(T);
@@ -659,8 +801,12 @@ static int fused_phase(int phase, const HexArgs<T> &a, cudaStream_t s)
             attr = true;
         }
         k_fused_B<T, P, NT><<<grid_elems(a.ne, 8), NT, smem, s>>>(a);
-    } else {
+    } else if (phase == 2) {
         k_fused_C<T, P, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
+    } else if (phase == 3) {
+        if (a.nlpts > 0) k_pair_flux<T, P><<<grid_for(a.nlpts, 128), 128, 0, s>>>(a);
+    } else {
+        k_lift<T, P, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
     }
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }

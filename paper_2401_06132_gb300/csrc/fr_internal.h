@@ -138,7 +138,36 @@ struct HexArgs {
     const long long *ef0;
     const int *eph;
     const Phys<T> *phtab;
+    // RK4 stage fused into the interface kernel: rkstage = 0 writes R; rkstage = s + 1 folds the
+    // value k = R(u_s) of stage s in directly: acc = (s ? acc : 0) + b_s k and us = U + c_{s+1} dt k
+    // for s < 3; U += dt (acc + b_3 k) for s = 3.
+    // Split interface phase (FP64): C1 evaluates each pair once from its L point (list lpts, entries
+    // element_in_launch * 256 + local flux point) into DF; C2 lifts per element.
+    const uint32_t *lpts;
+    long long nlpts;
+    int rkstage;
+    double rkdt;
+    double *rkU;
+    double *rkacc;
+    T *rkus;
 };
+
+#ifdef __CUDACC__
+template <typename T>
+__device__ __forceinline__ void rk_fold(const HexArgs<T> &a, long long i, T val)
+{
+    const double kv = (double)val;
+    const int st = a.rkstage - 1;
+    if (st == 3) {
+        a.rkU[i] += a.rkdt * (a.rkacc[i] + (1.0 / 6.0) * kv);
+    } else {
+        const double b = st == 0 ? 1.0 / 6.0 : 1.0 / 3.0;
+        const double c = st == 2 ? 1.0 : 0.5;
+        a.rkacc[i] = (st == 0 ? 0.0 : a.rkacc[i]) + b * kv;
+        a.rkus[i] = (T)(a.rkU[i] + c * a.rkdt * kv);
+    }
+}
+#endif
 
 #ifdef __CUDACC__
 template <typename T>
@@ -158,7 +187,8 @@ __device__ __forceinline__ Phys<T> elem_phys(const HexArgs<T> &a, long long e)
 }
 #endif
 
-// Launchers (fr_hex.cu). phase: 0 = A (face solution), 1 = B (volume group), 2 = C (interfaces).
+// Launchers (fr_hex.cu). phase: 0 = A (face solution), 1 = B (volume group), 2 = C (interfaces),
+// 3 = C1 (common flux once per pair, into DF), 4 = C2 (lift and scale from DF).
 template <typename T> int hex_fused_phase(int p, int phase, const HexArgs<T> &a, cudaStream_t s);
 // kernel: 1..13 in the paper's order (disu .. negdivconf)
 template <typename T> int hex_unfused_kernel(int p, int kernel, const HexArgs<T> &a, cudaStream_t s);

@@ -297,7 +297,8 @@ __global__ void __launch_bounds__(NTH) k_pri_C(HexArgs<T> a, const PriOps<T> *go
             for (int f = 0; f < 3; f++)
 #pragma unroll
                 for (int b = 0; b < NZ; b++) v += op.Lf[f][t][b] * D[20 + 16 * f + b + 4 * k];
-            R[it] = v * idet;
+            if (a.rkstage == 0) R[it] = v * idet;
+            else rk_fold(a, elem_u0(a, e, NU) + it, v * idet);
         }
         __syncthreads();
     }

@@ -1,0 +1,70 @@
+"""Run one Taylor-Green configuration through the library and report timings.
+
+    python -m paper_2401_06132_gb300.run_case --n 48 --p 3 --prec fp32 --form fused --rhs 4 --rk4 2
+
+Used as the command under Nsight Compute captures of single kernels, and as a quick check of a
+configuration. Every evaluation goes through the C ABI (libfrgb300.so).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=16, help="elements per box edge")
+    ap.add_argument("--p", type=int, default=3)
+    ap.add_argument("--mesh", default="hex", choices=["hex", "sheared", "mixed"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--form", default="fused", choices=["fused", "unfused"])
+    ap.add_argument("--rhs", type=int, default=3, help="RHS evaluations")
+    ap.add_argument("--rk4", type=int, default=0, help="RK4 steps after the RHS evaluations")
+    ap.add_argument("--mach", type=float, default=0.1)
+    args = ap.parse_args(argv)
+
+    import numpy as np
+    import torch
+
+    from paper_2401_06132_gb300 import fr, workloads as W
+
+    mesh = {"hex": W.box_hex_mesh, "sheared": W.sheared_box_mesh, "mixed": W.mixed_box_mesh}[args.mesh](args.n)
+    p0 = W.tgv_p0(mach=args.mach)
+    m = fr.FRMesh(mesh, fr.make_params(p=args.p, prec=args.prec, p_ref=p0))
+    m.set_form(args.form)
+    blocks = []
+    if mesh["hex_v"].shape[0]:
+        blocks.append((mesh["hex_v"].shape[0], (args.p + 1) ** 3))
+    if mesh["pri_v"].shape[0]:
+        blocks.append((mesh["pri_v"].shape[0], 40))
+    U0 = W.tgv_state(m.sol_coords(), blocks, mach=args.mach, perturb=1e-3)
+    U = torch.from_numpy(U0.astype(np.float64 if args.prec == "fp64" else np.float32)).cuda()
+    R = torch.empty_like(U)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(args.rhs):
+        m.rhs(U, R)
+    ev[1].record()
+    torch.cuda.synchronize()
+    m.sync_status()
+    out = {"dof": int(U0.size), "rhs_ms": ev[0].elapsed_time(ev[1]) / max(1, args.rhs)}
+    if args.rk4:
+        Um = torch.from_numpy(U0).cuda()
+        ev[0].record()
+        m.rk4_step(Um, 2e-4, args.rk4)
+        ev[1].record()
+        torch.cuda.synchronize()
+        m.sync_status()
+        out["rk4_ms"] = ev[0].elapsed_time(ev[1]) / args.rk4
+    out["gdof_rhs_per_s"] = out["dof"] / (out["rhs_ms"] * 1e-3) / 1e9
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
