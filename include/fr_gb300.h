@@ -61,8 +61,9 @@ typedef enum {
 typedef enum {
     FR_FP64 = 0,          /* all arithmetic in FP64 */
     FR_FP32 = 1,          /* FP32 state, operators and fluxes */
-    FR_MIXED_BF16 = 2,    /* FP32 state; prism triangle contractions as split bf16 hi+lo products */
-    FR_MIXED_FP16 = 3     /* as FR_MIXED_BF16 with fp16 splits */
+    FR_MIXED_BF16 = 2,    /* FP32 state; prism triangle contractions as split bf16 hi+lo products
+                           * (not built in this version: FR_EUNSUPPORTED) */
+    FR_MIXED_FP16 = 3     /* as FR_MIXED_BF16 with fp16 splits (not built: FR_EUNSUPPORTED) */
 } fr_precision;
 
 typedef enum {
@@ -87,6 +88,13 @@ typedef struct {
                            * by rounding: a constant flux has zero divergence and its common flux
                            * equals its own normal flux. It keeps the O(1/(gamma M^2)) pressure out of
                            * the rounding of the momentum divergence. */
+    double rho_ref;       /* reference density. With p_ref > 0 and rho_ref > 0 the FP32 form works on
+                           * deviations from the reference state (rho_ref, 0, 0, 0, p_ref/(gamma-1)),
+                           * evolves the reduced energy E - H0 rho (H0 = gamma p_ref/((gamma-1) rho_ref))
+                           * in FP32 and the mass equation in FP64, then returns R_E = R_(E-H0 rho) +
+                           * H0 R_rho. All of it is exact in exact arithmetic; it removes the
+                           * O(1/M^2) cancellations of low-Mach flows from the FP32 rounding. Hex-only
+                           * handles, fused form; ignored in FP64. */
 } fr_params;
 
 /* Host description of one mesh instance (copied by fr_mesh_create). */

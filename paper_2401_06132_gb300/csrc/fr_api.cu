@@ -57,6 +57,7 @@ struct Group {
     int *d_eph = nullptr;
     void *d_phtab = nullptr;        // Phys<T> per instance
     uint32_t *d_lpts = nullptr;     // L flux points of the group (element_in_group * 256 + local)
+    void *d_geo64 = nullptr;        // Geo<double> per element in group order (low-Mach form)
     long long nlpts = 0;
 };
 
@@ -74,6 +75,9 @@ struct fr_mesh {
     void *d_priops = nullptr;            // PriOps<T> on the device
     std::vector<Group> groups;
     bool split_c = false;              // interface phase as pair flux (C1) + lift (C2)
+    bool lowmach = false;              // FP32 low-Mach form (deviations, reduced energy, FP64 mass)
+    void *d_geo64 = nullptr;           // FP64 geometry for the low-Mach form
+    double *d_MF = nullptr, *d_RL = nullptr;
     std::vector<double> geo_host;        // per element Ji[9], det (FP64)
     // device
     void *d_geo = nullptr;               // Geo<T>[ne]
@@ -420,6 +424,8 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
     if (!inst || !prm || n_inst <= 0) return fail(FR_EINVAL, "null descriptor or n_inst <= 0");
     m->prec = prm[0].prec;
     if (m->prec < FR_FP64 || m->prec > FR_MIXED_FP16) return fail(FR_EINVAL, "unknown precision %d", m->prec);
+    if (m->prec == FR_MIXED_BF16 || m->prec == FR_MIXED_FP16)
+        return fail(FR_EUNSUPPORTED, "the split bf16/fp16 tensor-core forms are not built in this version");
     long long elem = 0, u = 0, f = 0;
     std::vector<int> bfirst;
     for (int ii = 0; ii < n_inst; ii++) {
@@ -429,7 +435,8 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
         if (P.prec != m->prec) return fail(FR_EINVAL, "all instances must share one precision");
         int m1 = P.nq1d > 0 ? P.nq1d : P.p + 2;
         if (P.p < 3 || P.p > 4 || m1 != P.p + 2) return fail(FR_EUNSUPPORTED, "instance %d: order %d with %d quadrature points", ii, P.p, m1);
-        if (!(P.gamma > 1.0) || !(P.Pr > 0.0) || P.mu < 0.0 || P.tau < 0.0 || !(P.p_ref == P.p_ref))
+        if (!(P.gamma > 1.0) || !(P.Pr > 0.0) || P.mu < 0.0 || P.tau < 0.0 || !(P.p_ref == P.p_ref) ||
+            !(P.rho_ref >= 0.0))
             return fail(FR_EINVAL, "instance %d: bad physical parameters", ii);
         if (P.rusanov_mode != 0) return fail(FR_EUNSUPPORTED, "rusanov_mode %d", P.rusanov_mode);
         if (d->n_hex < 0 || d->n_pri < 0 || d->n_hex + d->n_pri == 0 || d->n_verts <= 0 || !d->verts)
@@ -532,6 +539,11 @@ static Phys<T> phys_of(const fr_params &P)
     Phys<T> ph;
     ph.gamma = (T)P.gamma; ph.gm1 = (T)(P.gamma - 1.0); ph.mu = (T)P.mu;
     ph.beta = (T)P.beta; ph.tau = (T)P.tau; ph.heat = (T)(P.mu * P.gamma / P.Pr); ph.pref = (T)P.p_ref;
+    ph.dev = 0;
+    ph.rref = (T)P.rho_ref; ph.eref = (T)(P.p_ref / (P.gamma - 1.0));
+    ph.rrefd = P.rho_ref;
+    ph.H0d = P.rho_ref > 0 ? P.gamma * P.p_ref / ((P.gamma - 1.0) * P.rho_ref) : 0.0;
+    ph.H0 = (T)ph.H0d;
     return ph;
 }
 
@@ -547,7 +559,10 @@ static fr_status build_groups(fr_mesh *m, const std::vector<uint32_t> &partner)
         g->ne += B.ne;
     }
     std::vector<Phys<T>> tab;
-    for (const InstanceHost &I : m->inst) tab.push_back(phys_of<T>(I.prm));
+    for (const InstanceHost &I : m->inst) {
+        tab.push_back(phys_of<T>(I.prm));
+        tab.back().dev = m->lowmach ? 1 : 0;
+    }
     for (Group &g : m->groups) {
         // L points for the split interface phase
         std::vector<uint32_t> lp;
@@ -564,6 +579,22 @@ static fr_status build_groups(fr_mesh *m, const std::vector<uint32_t> &partner)
         if (sl) return sl;
         CU(cudaMemcpy(g.d_lpts, lp.data(), lp.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
         if (g.blks.size() < 2) continue;
+        if (m->lowmach) {
+            std::vector<Geo<double>> g64;
+            for (int bi : g.blks) {
+                const Block &B = m->blocks[bi];
+                for (long long e = 0; e < B.ne; e++) {
+                    Geo<double> x;
+                    const double *src = &m->geo_host[(size_t)(B.elem0 + e) * 10];
+                    for (int k = 0; k < 9; k++) x.Ji[k] = src[k];
+                    x.det = src[9];
+                    g64.push_back(x);
+                }
+            }
+            fr_status sg = dalloc(m, &g.d_geo64, g64.size() * sizeof(Geo<double>));
+            if (sg) return sg;
+            CU(cudaMemcpy(g.d_geo64, g64.data(), g64.size() * sizeof(Geo<double>), cudaMemcpyHostToDevice));
+        }
         std::vector<Geo<T>> geo;
         std::vector<long long> eu0, ef0;
         std::vector<int> eph;
@@ -610,6 +641,23 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
     size_t ts = tsize(m->prec);
     st = (m->prec == FR_FP64) ? upload_geo<double>(m) : upload_geo<float>(m);
     if (!st) st = (m->prec == FR_FP64) ? upload_priops<double>(m) : upload_priops<float>(m);
+    if (!st && m->prec != FR_FP64 && !m->has_pri) {
+        bool all = true;
+        for (const InstanceHost &I : m->inst) all = all && I.prm.p_ref > 0 && I.prm.rho_ref > 0;
+        m->lowmach = all;
+    }
+    if (!st && m->lowmach) {
+        std::vector<Geo<double>> g64((size_t)m->ne);
+        for (long long e = 0; e < m->ne; e++) {
+            for (int k = 0; k < 9; k++) g64[e].Ji[k] = m->geo_host[(size_t)e * 10 + k];
+            g64[e].det = m->geo_host[(size_t)e * 10 + 9];
+        }
+        st = dalloc(m, &m->d_geo64, g64.size() * sizeof(Geo<double>));
+        if (!st && cudaMemcpy(m->d_geo64, g64.data(), g64.size() * sizeof(Geo<double>), cudaMemcpyHostToDevice) != cudaSuccess)
+            st = fail(FR_ECUDA, "geometry upload failed");
+        if (!st) st = dalloc(m, (void **)&m->d_MF, (size_t)m->nfpt * sizeof(double));
+        if (!st) st = dalloc(m, (void **)&m->d_RL, (size_t)(m->nU / FR_NV) * sizeof(double));
+    }
     if (!st) st = (m->prec == FR_FP64) ? build_groups<double>(m, partner) : build_groups<float>(m, partner);
     // FP64 hexahedral handles evaluate each interface pair once (split interface phase)
     m->split_c = (m->prec == FR_FP64) && !m->has_pri;
@@ -632,13 +680,14 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
 extern "C" fr_status fr_destroy(fr_mesh *m)
 {
     if (!m) return FR_OK;
-    void **bufs[] = {&m->d_priops, &m->d_geo, (void **)&m->d_partner, &m->d_UF, &m->d_FV, &m->d_CF, &m->d_QF, &m->d_DF, &m->d_Qu,
+    void **bufs[] = {&m->d_geo64, (void **)&m->d_MF, (void **)&m->d_RL, &m->d_priops, &m->d_geo, (void **)&m->d_partner, &m->d_UF, &m->d_FV, &m->d_CF, &m->d_QF, &m->d_DF, &m->d_Qu,
                      &m->d_UQ, &m->d_QQ, &m->d_Rt, &m->d_rk_k, &m->d_rk_us, (void **)&m->d_rk_acc, &m->d_io_U,
                      &m->d_io_R, (void **)&m->d_wsum, (void **)&m->d_status, &m->d_Qsnap};
     for (void **b : bufs) dfree(*b);
     for (Group &g : m->groups) {
         dfree(g.d_geo); dfree((void *&)g.d_eu0); dfree((void *&)g.d_ef0); dfree((void *&)g.d_eph); dfree(g.d_phtab);
         dfree((void *&)g.d_lpts);
+        dfree(g.d_geo64);
     }
     if (m->h_status) cudaFreeHost(m->h_status);
     for (auto &t : m->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
@@ -705,6 +754,10 @@ static HexArgs<T> make_args(fr_mesh *m, const Block &b, const void *U, void *R)
     a.geo = reinterpret_cast<const Geo<T> *>(m->d_geo) + b.elem0;
     a.partner = m->d_partner;
     a.ph = phys_of<T>(I.prm);
+    a.ph.dev = m->lowmach ? 1 : 0;
+    a.geo64 = m->d_geo64 ? reinterpret_cast<const Geo<double> *>(m->d_geo64) + b.elem0 : nullptr;
+    a.MF = m->d_MF;
+    a.RL = m->d_RL;
     a.U = reinterpret_cast<const T *>(U); a.R = reinterpret_cast<T *>(R);
     a.UF = reinterpret_cast<T *>(m->d_UF); a.FV = reinterpret_cast<T *>(m->d_FV);
     a.CF = reinterpret_cast<T *>(m->d_CF); a.QF = reinterpret_cast<T *>(m->d_QF); a.DF = reinterpret_cast<T *>(m->d_DF);
@@ -779,6 +832,7 @@ static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, co
                     a.ne = gr.ne; a.u0 = 0; a.f0 = 0;
                     a.geo = reinterpret_cast<const Geo<T> *>(gr.d_geo);
                     a.eu0 = gr.d_eu0; a.ef0 = gr.d_ef0; a.eph = gr.d_eph;
+                    if (m->lowmach) a.geo64 = reinterpret_cast<const Geo<double> *>(gr.d_geo64);
                     a.phtab = reinterpret_cast<const Phys<T> *>(gr.d_phtab);
                 }
                 a.lpts = gr.d_lpts; a.nlpts = gr.nlpts;
@@ -796,6 +850,7 @@ static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, co
         if (st) return st;
         const Block &b = m->blocks[0];
         HexArgs<T> a = make_args<T>(m, b, U, R);
+        a.ph.dev = 0;   // the unfused form is the plain one-kernel-per-stage form
         for (int k = 1; k <= 13; k++) {
             int lr;
             {

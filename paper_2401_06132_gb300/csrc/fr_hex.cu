@@ -14,6 +14,8 @@
 // tangential axes in increasing axis order; flux point sigma = face * n^2 + local.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "fr_internal.h"
 #include "fr_physics.cuh"
 
@@ -106,14 +108,17 @@ __global__ void __launch_bounds__(NT) k_disu_blk(HexArgs<T> a)
     const HexOps<T> &op = OPS<T>(P - 2);
     for (long long e0 = (long long)blockIdx.x * EB; e0 < a.ne; e0 += (long long)gridDim.x * EB) {
         const int nb = (int)((a.ne - e0) < EB ? (a.ne - e0) : EB);
-        if (a.eu0 == nullptr) {
-            const T *src = a.U + a.u0 + e0 * FR_NV * NU;
-            for (int i = threadIdx.x; i < nb * FR_NV * NU; i += NT) s_u[i] = src[i];
-        } else {
-            for (int i = threadIdx.x; i < nb * FR_NV * NU; i += NT) {
-                const int el = i / (FR_NV * NU), r = i % (FR_NV * NU);
-                s_u[i] = a.U[a.eu0[e0 + el] + r];
+        for (int i = threadIdx.x; i < nb * FR_NV * NU; i += NT) {
+            const int el = i / (FR_NV * NU), r = i % (FR_NV * NU);
+            T v = a.eu0 == nullptr ? a.U[a.u0 + e0 * FR_NV * NU + i] : a.U[a.eu0[e0 + el] + r];
+            if constexpr (std::is_same<T, float>::value) {
+                const Phys<T> ph = elem_phys(a, e0 + el);
+                if (ph.dev) {   // deviations from the reference state (exact in FP32)
+                    if (r < NU) v -= ph.rref;
+                    else if (r >= 4 * NU) v -= ph.eref;
+                }
             }
+            s_u[i] = v;
         }
         __syncthreads();
         for (int it = threadIdx.x; it < FR_NV * nb * NF; it += NT) {
@@ -127,6 +132,30 @@ __global__ void __launch_bounds__(NT) k_disu_blk(HexArgs<T> a)
 #pragma unroll
             for (int i = 0; i < N; i++) v += l[i] * u[i * stride];
             a.UF[alpha * a.nfpt + elem_f0(a, e0 + el, NF) + sp] = v;
+        }
+        if constexpr (std::is_same<T, float>::value) {
+            // low-Mach form: own-normal mass flux n.(rho v) at every flux point, in FP64
+            if (elem_phys(a, e0).dev) {
+                const HexOps<double> &o64 = OPS<double>(P - 2);
+                for (int it = threadIdx.x; it < nb * NF; it += NT) {
+                    const int el = it / NF, sp = it % NF, f = sp / (N * N);
+                    int base, stride;
+                    face_line<N>(f, sp % (N * N), base, stride);
+                    const double *l = (f & 1) ? o64.lR : o64.lL;
+                    double mv[3];
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        const T *u = s_u + (el * FR_NV + 1 + k) * NU + base;
+                        double v = 0.0;
+#pragma unroll
+                        for (int i = 0; i < N; i++) v += l[i] * (double)u[i * stride];
+                        mv[k] = v;
+                    }
+                    double n[3], mag;
+                    face_normal(a.geo64[e0 + el], f, n, mag);
+                    a.MF[elem_f0(a, e0 + el, NF) + sp] = n[0] * mv[0] + n[1] * mv[1] + n[2] * mv[2];
+                }
+            }
         }
         __syncthreads();
     }
@@ -256,6 +285,7 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
     T *s_t2 = s_t1 + S::T1;
     __shared__ short s_list[NF];
     __shared__ int s_cnt;
+    __shared__ double s_m64[std::is_same<T, float>::value ? 3 * NU : 1];
     const HexOps<T> &op = OPS<T>(P - 2);
 
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
@@ -263,8 +293,16 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
         const Phys<T> ph = elem_phys(a, e);
         const T *U = a.U + elem_u0(a, e, NU);
         const long long gf0 = elem_f0(a, e, NF);
-        // 1. load the element's solution
-        for (int it = threadIdx.x; it < 5 * NU; it += NT) s_u[it] = U[it];
+        // 1. load the element's solution (deviations from the reference state in the low-Mach form)
+        bool dev = false;
+        if constexpr (std::is_same<T, float>::value) dev = ph.dev != 0;
+        for (int it = threadIdx.x; it < 5 * NU; it += NT) {
+            T v = U[it];
+            if constexpr (std::is_same<T, float>::value) {
+                if (dev) v -= (it < NU) ? ph.rref : (it >= 4 * NU ? ph.eref : T(0));
+            }
+            s_u[it] = v;
+        }
         // 2. con_u: common solution at own flux points, C = (1/2 - beta) uL + (1/2 + beta) uR
         for (int it = threadIdx.x; it < 5 * NF; it += NT) {
             const int alpha = it / NF, s = it % NF;
@@ -349,10 +387,40 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
             }
             T n[3], mag;
             face_normal(g, f, n, mag);
+            if constexpr (std::is_same<T, float>::value) {
+                if (dev) { uf[0] += ph.rref; uf[4] += ph.eref; }
+            }
             T fvn[4];
             viscous_normal_flux(ph, uf, qf, n, fvn);
 #pragma unroll
             for (int k = 0; k < 4; k++) a.FV[k * a.nfpt + gf0 + s] = fvn[k];
+        }
+        if constexpr (std::is_same<T, float>::value) {
+            // low-Mach form: volume part of R~_rho in FP64 (the mass flux rho v is a polynomial of
+            // the solution space, so its L2 projection is itself: no quadrature points needed)
+            if (dev) {
+                const HexOps<double> &o64 = OPS<double>(P - 2);
+                const Geo<double> g64 = a.geo64[e];
+                for (int it = threadIdx.x; it < NU; it += NT) {
+                    const double m0 = s_u[NU + it], m1 = s_u[2 * NU + it], m2 = s_u[3 * NU + it];
+#pragma unroll
+                    for (int d = 0; d < 3; d++)
+                        s_m64[d * NU + it] = g64.det * (g64.Ji[3 * d] * m0 + g64.Ji[3 * d + 1] * m1 + g64.Ji[3 * d + 2] * m2);
+                }
+                __syncthreads();
+                const long long pbase = elem_u0(a, e, NU) / FR_NV;
+                for (int z = threadIdx.x; z < NU; z += NT) {
+                    const int i = z % N, j = (z / N) % N, k = z / (N * N);
+                    double v = 0.0;
+#pragma unroll
+                    for (int b = 0; b < N; b++) {
+                        v += o64.Dh[i][b] * s_m64[b + N * j + N * N * k];
+                        v += o64.Dh[j][b] * s_m64[NU + i + N * b + N * N * k];
+                        v += o64.Dh[k][b] * s_m64[2 * NU + i + N * j + N * N * b];
+                    }
+                    a.RL[pbase + z] = v;
+                }
+            }
         }
         // 6. uqpts + gradcoru_qpts: 20 fields to quadrature points, 5 at a time
         interp_5<T, P, NT>(op, s_u, s_t1, s_t2, s_w);
@@ -368,7 +436,12 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
 #pragma unroll
                 for (int d = 0; d < 3; d++) gq[alpha][d] = s_w[(5 + alpha * 3 + d) * NQ + q];
             }
-            ok &= total_flux(ph, u, gq, f);
+            if constexpr (std::is_same<T, float>::value) {
+                if (dev) ok &= total_flux_dev(ph, u, gq, f);
+                else ok &= total_flux(ph, u, gq, f);
+            } else {
+                ok &= total_flux(ph, u, gq, f);
+            }
             if (diagJ) {
                 const T s0 = g.det * g.Ji[0], s1 = g.det * g.Ji[4], s2 = g.det * g.Ji[8];
 #pragma unroll
@@ -416,10 +489,13 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
 {
     constexpr int N = P + 1, NU = N * N * N, NF = 6 * N * N;
     __shared__ T s_d[5 * NF];
+    __shared__ double s_d64[std::is_same<T, float>::value ? NF : 1];
     const HexOps<T> &op = OPS<T>(P - 2);
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
         const Geo<T> g = a.geo[e];
         const Phys<T> ph = elem_phys(a, e);
+        bool dev = false;
+        if constexpr (std::is_same<T, float>::value) dev = ph.dev != 0;
         const long long gf0 = elem_f0(a, e, NF);
         bool ok = true;
         for (int s = threadIdx.x; s < NF; s += NT) {
@@ -436,7 +512,24 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
             face_normal(g, f, n, mag);
             T nL[3] = {isL ? n[0] : -n[0], isL ? n[1] : -n[1], isL ? n[2] : -n[2]};
             T F[5];
-            ok &= isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
+            if constexpr (std::is_same<T, float>::value) {
+                if (dev) {
+                    float sw;
+                    ok &= isL ? common_flux_dev(ph, uo, up, fvo, fvp, nL, F, sw) : common_flux_dev(ph, up, uo, fvp, fvo, nL, F, sw);
+                    // FP64 mass flux: 1/2 (mL - mR) + (s/2 + tau)(rho_L - rho_R), mX = own-normal n.(rho v)
+                    const double mo = a.MF[og], mp = a.MF[pg];
+                    const double mL = isL ? mo : mp, mR = isL ? mp : mo;
+                    const double rL = isL ? uo[0] : up[0], rR = isL ? up[0] : uo[0];
+                    const double Fr = 0.5 * (mL - mR) + (0.5 * (double)sw + (double)ph.tau) * (rL - rR);
+                    double n64[3], mag64;
+                    face_normal(a.geo64[e], f, n64, mag64);
+                    s_d64[s] = isL ? mag64 * Fr : -mag64 * Fr;
+                } else {
+                    ok &= isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
+                }
+            } else {
+                ok &= isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
+            }
             const T sc = isL ? mag : -mag;
 #pragma unroll
             for (int k = 0; k < 5; k++) s_d[k * NF + s] = sc * F[k];
@@ -445,15 +538,47 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
         __syncthreads();
         T *R = a.R + elem_u0(a, e, NU);
         const T idet = T(-1) / g.det;
-        for (int it = threadIdx.x; it < 5 * NU; it += NT) {
-            const int alpha = it / NU, z = it % NU, i = z % N, j = (z / N) % N, k = z / (N * N);
-            const T *D = s_d + alpha * NF;
-            T v = R[it];
-            v += op.liftL[i] * D[0 * N * N + j + N * k] + op.liftR[i] * D[1 * N * N + j + N * k];
-            v += op.liftL[j] * D[2 * N * N + i + N * k] + op.liftR[j] * D[3 * N * N + i + N * k];
-            v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
-            if (a.rkstage == 0) R[it] = v * idet;
-            else rk_fold(a, elem_u0(a, e, NU) + it, v * idet);
+        if (!dev) {
+            for (int it = threadIdx.x; it < 5 * NU; it += NT) {
+                const int alpha = it / NU, z = it % NU, i = z % N, j = (z / N) % N, k = z / (N * N);
+                const T *D = s_d + alpha * NF;
+                T v = R[it];
+                v += op.liftL[i] * D[0 * N * N + j + N * k] + op.liftR[i] * D[1 * N * N + j + N * k];
+                v += op.liftL[j] * D[2 * N * N + i + N * k] + op.liftR[j] * D[3 * N * N + i + N * k];
+                v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
+                if (a.rkstage == 0) R[it] = v * idet;
+                else rk_fold(a, elem_u0(a, e, NU) + it, v * idet);
+            }
+        } else if constexpr (std::is_same<T, float>::value) {
+            // low-Mach form: R_rho in FP64, R_E = R_(E - H0 rho) + H0 R_rho
+            const HexOps<double> &o64 = OPS<double>(P - 2);
+            const double idet64 = -1.0 / a.geo64[e].det;
+            const long long pbase = elem_u0(a, e, NU) / FR_NV;
+            for (int z = threadIdx.x; z < NU; z += NT) {
+                const int i = z % N, j = (z / N) % N, k = z / (N * N);
+                double r = a.RL[pbase + z];
+                r += o64.liftL[i] * s_d64[0 * N * N + j + N * k] + o64.liftR[i] * s_d64[1 * N * N + j + N * k];
+                r += o64.liftL[j] * s_d64[2 * N * N + i + N * k] + o64.liftR[j] * s_d64[3 * N * N + i + N * k];
+                r += o64.liftL[k] * s_d64[4 * N * N + i + N * j] + o64.liftR[k] * s_d64[5 * N * N + i + N * j];
+                const double Rrho = r * idet64;
+                float out[5];
+                out[0] = (float)Rrho;
+#pragma unroll
+                for (int alpha = 1; alpha < 5; alpha++) {
+                    const T *D = s_d + alpha * NF;
+                    T v = R[alpha * NU + z];
+                    v += op.liftL[i] * D[0 * N * N + j + N * k] + op.liftR[i] * D[1 * N * N + j + N * k];
+                    v += op.liftL[j] * D[2 * N * N + i + N * k] + op.liftR[j] * D[3 * N * N + i + N * k];
+                    v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
+                    out[alpha] = v * idet;
+                }
+                out[4] = (float)((double)out[4] + ph.H0d * Rrho);
+#pragma unroll
+                for (int alpha = 0; alpha < 5; alpha++) {
+                    if (a.rkstage == 0) R[alpha * NU + z] = out[alpha];
+                    else rk_fold(a, elem_u0(a, e, NU) + alpha * NU + z, out[alpha]);
+                }
+            }
         }
         __syncthreads();
     }

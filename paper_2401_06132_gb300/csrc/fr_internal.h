@@ -88,6 +88,10 @@ struct Phys {
     T gamma, gm1, mu, beta, tau;
     T heat;       // mu gamma / ((gamma - 1) Pr)
     T pref;       // reference pressure removed from the momentum flux
+    // low-Mach FP32 form: deviations from (rref, 0, 0, 0, eref), reduced energy E - H0 rho
+    T rref, eref, H0;
+    double H0d, rrefd;
+    int dev;
 };
 
 // Geometry of one affine element: inverse Jacobian (row-major dxi_i/dx_j) and its determinant.
@@ -141,6 +145,11 @@ struct HexArgs {
     // RK4 stage fused into the interface kernel: rkstage = 0 writes R; rkstage = s + 1 folds the
     // value k = R(u_s) of stage s in directly: acc = (s ? acc : 0) + b_s k and us = U + c_{s+1} dt k
     // for s < 3; U += dt (acc + b_3 k) for s = 3.
+    // Low-Mach FP32 form (ph.dev): FP64 geometry, own-normal mass flux n.(rho v) at flux points,
+    // and the volume part of R~_rho per solution point, all in FP64
+    const Geo<double> *geo64;
+    double *MF;
+    double *RL;
     // Split interface phase (FP64): C1 evaluates each pair once from its L point (list lpts, entries
     // element_in_launch * 256 + local flux point) into DF; C2 lifts per element.
     const uint32_t *lpts;

@@ -107,3 +107,74 @@ __device__ __forceinline__ void flag_status(int *status, bool ok)
 {
     if (!ok) atomicOr(status, 1);
 }
+
+// -------------------------------------------------------------------------------------------------
+// Low-Mach FP32 form. The state is carried as deviations w = (rho - rref, rho v, E - eref) from a
+// reference state at rest with (gamma - 1) eref = pref, and the energy equation is replaced by the
+// reduced energy E - H0 rho (H0 = (eref + pref)/rref), whose flux is
+//   v (E + p) - H0 rho v - f^v_E = v (E' + p' - H0 rho') - f^v_E,   p' = p - pref,
+// a difference of O(1) terms instead of O(1/(gamma M^2)) ones. The mass equation is carried in FP64
+// by the callers, and R_E = R_(E - H0 rho) + H0 R_rho. All of this is exact in exact arithmetic.
+// -------------------------------------------------------------------------------------------------
+
+// Fluxes f[d][a] of (unused, rho v, E - H0 rho) from the deviations w and the physical gradient g
+// (gradients of deviations equal gradients of the conserved variables).
+__device__ __forceinline__ bool total_flux_dev(const Phys<float> &ph, const float *w, const float (*g)[3], float (*f)[5])
+{
+    const float rho = ph.rref + w[0], ir = 1.0f / rho;
+    const float v[3] = {w[1] * ir, w[2] * ir, w[3] * ir};
+    const float pd = ph.gm1 * (w[4] - 0.5f * (w[1] * v[0] + w[2] * v[1] + w[3] * v[2]));
+    const float er = (ph.eref + w[4]) * ir;
+    float dv[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int d = 0; d < 3; d++) dv[i][d] = (g[1 + i][d] - v[i] * g[0][d]) * ir;
+    const float div = dv[0][0] + dv[1][1] + dv[2][2];
+    const float hred = w[4] + pd - ph.H0 * w[0];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        float tau[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) tau[i] = ph.mu * (dv[i][d] + dv[d][i]) - (i == d ? (2.0f / 3.0f) * ph.mu * div : 0.0f);
+        const float phi = ph.heat * ((g[4][d] - er * g[0][d]) * ir - (v[0] * dv[0][d] + v[1] * dv[1][d] + v[2] * dv[2][d]));
+        f[d][0] = 0.0f;
+        f[d][1] = w[1] * v[d] + (d == 0 ? pd : 0.0f) - tau[0];
+        f[d][2] = w[2] * v[d] + (d == 1 ? pd : 0.0f) - tau[1];
+        f[d][3] = w[3] * v[d] + (d == 2 ? pd : 0.0f) - tau[2];
+        f[d][4] = v[d] * hred - (v[0] * tau[0] + v[1] * tau[1] + v[2] * tau[2] + phi);
+    }
+    return rho > 0.0f && ph.pref + pd > 0.0f && isfinite(pd) && isfinite(f[0][4] + f[1][4] + f[2][4]);
+}
+
+// Common normal flux of (rho v, E - H0 rho) (F[1..4]) from deviation states, with the same Rusanov
+// and LDG rules as common_flux; returns the Rusanov wave speed in s for the FP64 mass flux.
+__device__ __forceinline__ bool common_flux_dev(const Phys<float> &ph, const float *wL, const float *wR,
+                                                const float *fvL, const float *fvR, const float *n, float *F, float &s)
+{
+    const float rL = ph.rref + wL[0], rR = ph.rref + wR[0];
+    const float irL = 1.0f / rL, irR = 1.0f / rR;
+    const float vnL = (wL[1] * n[0] + wL[2] * n[1] + wL[3] * n[2]) * irL;
+    const float vnR = (wR[1] * n[0] + wR[2] * n[1] + wR[3] * n[2]) * irR;
+    const float pdL = ph.gm1 * (wL[4] - 0.5f * irL * (wL[1] * wL[1] + wL[2] * wL[2] + wL[3] * wL[3]));
+    const float pdR = ph.gm1 * (wR[4] - 0.5f * irR * (wR[1] * wR[1] + wR[2] * wR[2] + wR[3] * wR[3]));
+    const float pL = ph.pref + pdL, pR = ph.pref + pdR;
+    const float cL = sqrtf(ph.gamma * pL * irL), cR = sqrtf(ph.gamma * pR * irR);
+    s = fmaxf(fabsf(vnL) + cL, fabsf(vnR) + cR);
+    float fnL[5], fnR[5], du[5];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        fnL[1 + i] = wL[1 + i] * vnL + pdL * n[i];
+        fnR[1 + i] = wR[1 + i] * vnR + pdR * n[i];
+        du[1 + i] = wL[1 + i] - wR[1 + i];
+    }
+    fnL[4] = vnL * (wL[4] + pdL - ph.H0 * wL[0]);
+    fnR[4] = vnR * (wR[4] + pdR - ph.H0 * wR[0]);
+    du[4] = (wL[4] - wR[4]) - ph.H0 * (wL[0] - wR[0]);
+    const float wl = 0.5f + ph.beta, wr = 0.5f - ph.beta;
+    F[0] = 0.0f;
+#pragma unroll
+    for (int a = 1; a < 5; a++)
+        F[a] = 0.5f * (fnL[a] + fnR[a]) + 0.5f * s * du[a] - (wl * fvL[a - 1] - wr * fvR[a - 1]) + ph.tau * du[a];
+    return pL > 0.0f && pR > 0.0f && rL > 0.0f && rR > 0.0f && isfinite(s);
+}

@@ -23,6 +23,7 @@ def main(argv=None):
     ap.add_argument("--p", type=int, default=3)
     ap.add_argument("--mesh", default="hex", choices=["hex", "sheared", "mixed"])
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--lowmach", type=int, default=1, help="FP32 low-Mach form (rho_ref = 1)")
     ap.add_argument("--form", default="fused", choices=["fused", "unfused"])
     ap.add_argument("--rhs", type=int, default=3, help="RHS evaluations")
     ap.add_argument("--rk4", type=int, default=0, help="RK4 steps after the RHS evaluations")
@@ -36,7 +37,7 @@ def main(argv=None):
 
     mesh = {"hex": W.box_hex_mesh, "sheared": W.sheared_box_mesh, "mixed": W.mixed_box_mesh}[args.mesh](args.n)
     p0 = W.tgv_p0(mach=args.mach)
-    m = fr.FRMesh(mesh, fr.make_params(p=args.p, prec=args.prec, p_ref=p0))
+    m = fr.FRMesh(mesh, fr.make_params(p=args.p, prec=args.prec, p_ref=p0, rho_ref=1.0 if args.lowmach else 0.0))
     m.set_form(args.form)
     blocks = []
     if mesh["hex_v"].shape[0]:

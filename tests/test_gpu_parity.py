@@ -197,27 +197,62 @@ def test_full_size_48cubed_fp64_parity(form):
     assert err.max() <= 1e-12, err
 
 
-@pytest.mark.parametrize("p", [3, 4])
-def test_fp32_form_error_vs_oracle(p):
-    """FP32 state, operators and fluxes against the oracle on the FP32-rounded input. The measured
-    per-variable error is reported; the bound is the one stated in the design notes."""
-    N = 4
+def _fp32_errors(N, p, lowmach, mesh_fn=W.box_hex_mesh, perturb=1e-3):
     nu = (p + 1) ** 3
-    mesh = W.box_hex_mesh(N)
+    mesh = mesh_fn(N)
     p0 = W.tgv_p0()
     o = O.Oracle(mesh, p, p + 2, threads=NCPU, p_ref=p0)
-    U = W.tgv_state(o.sol_coords(), [(N ** 3, nu)], perturb=1e-3).astype(np.float32)
+    U = W.tgv_state(o.sol_coords(), [(N ** 3, nu)], perturb=perturb).astype(np.float32)
     Ro = o.rhs(U.astype(np.float64))
-    m = fr.FRMesh(mesh, fr.make_params(p=p, prec="fp32", p_ref=p0))
+    m = fr.FRMesh(mesh, fr.make_params(p=p, prec="fp32", p_ref=p0, rho_ref=1.0 if lowmach else 0.0))
     Ud = torch.from_numpy(U).cuda()
     Rd = torch.empty_like(Ud)
     m.rhs(Ud, Rd)
     m.sync_status()
     R = Rd.cpu().numpy().astype(np.float64)
-    err = rel_linf(R, Ro, nu)
-    glob = np.abs(R - Ro).max() / np.abs(Ro).max()
-    print(f"fp32 p={p}: per-variable {err}, global {glob:.3e}")
-    assert glob <= 1e-4 and err.max() <= 5e-3, (err, glob)
+    return rel_linf(R, Ro, nu), np.abs(R - Ro).max() / np.abs(Ro).max()
+
+
+@pytest.mark.parametrize("N,p,meshname", [(4, 3, "box"), (4, 4, "box"), (3, 3, "sheared"), (16, 3, "box")])
+def test_fp32_lowmach_form_within_2e5(N, p, meshname):
+    """FP32 form with the low-Mach reformulation (deviations from the reference state, reduced energy
+    in FP32, mass equation in FP64) against the oracle run on the FP32-rounded input promoted to
+    FP64: relative L-inf per conserved variable <= 2e-5."""
+    fn = W.box_hex_mesh if meshname == "box" else W.sheared_box_mesh
+    err, glob = _fp32_errors(N, p, True, fn)
+    print(f"fp32 low-Mach N={N} p={p} {meshname}: per-variable {err}, global {glob:.3e}")
+    assert err.max() <= 2e-5, err
+
+
+@pytest.mark.parametrize("p", [3, 4])
+def test_fp32_plain_form_error(p):
+    """Plain FP32 (no reference state): the O(1/(gamma M^2)) pressure and enthalpy in FP32 rounding
+    leave errors of order 1e-4 at M = 0.1; reported, and bounded at 1e-3 per variable."""
+    err, glob = _fp32_errors(4, p, False)
+    print(f"fp32 plain p={p}: per-variable {err}, global {glob:.3e}")
+    assert err.max() <= 1e-3, err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_ke_dissipation_after_100_rk4_steps(prec):
+    """8^3 hex p=3 TGV, 100 RK4 steps at dt = 1e-3 on the GPU (FP64 master state; FP32 compute for
+    the reduced-precision form) against the oracle's trajectory: the kinetic-energy dissipation rate
+    eps = -dE_k/dt at the final state agrees to 1e-3 relative (FP64: to 1e-9)."""
+    mesh = W.box_hex_mesh(8)
+    p0 = W.tgv_p0()
+    o = O.Oracle(mesh, 3, 5, threads=NCPU, p_ref=p0)
+    U = W.tgv_state(o.sol_coords(), [(512, 64)])
+    Uo = o.rk4(U, 1e-3, 100)
+    eps_o = o.diagnostics(Uo, o.rhs(Uo))["eps"]
+    m = fr.FRMesh(mesh, fr.make_params(p=3, prec=prec, p_ref=p0, rho_ref=1.0))
+    Ud = torch.from_numpy(U).cuda()
+    m.rk4_step(Ud, 1e-3, 100)
+    m.sync_status()
+    Ug = Ud.cpu().numpy()
+    eps_g = o.diagnostics(Ug, o.rhs(Ug))["eps"]
+    rel = abs(eps_g / eps_o - 1.0)
+    print(f"{prec}: eps oracle {eps_o:.9e} gpu {eps_g:.9e} rel {rel:.2e}")
+    assert rel <= (1e-9 if prec == "fp64" else 1e-3), rel
 
 
 def _rel_linf_blocks(R, Ro, blocks):
