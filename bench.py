@@ -184,6 +184,9 @@ def time_rk4(m, U, steps, warmup, torch):
 
 
 def _time_steps(m, U, steps, warmup, torch):
+    Uc = U if m.prec == 0 else U.float()
+    m.autotune(Uc, torch.empty_like(Uc))
+    del Uc
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         for _ in range(warmup):
@@ -267,6 +270,7 @@ def run_ours(args, rank, world):
     U = torch.from_numpy(U0).cuda()
 
     # --- headline: FP64 fused, RK4 steps, timed with events, barrier + max over ranks -----------
+    tuned = m.autotune(U, torch.empty_like(U))      # launch shape of the volume kernel
     for _ in range(args.warmup):
         m.rk4_step(U, DT, 1)
     torch.cuda.synchronize()
@@ -328,6 +332,9 @@ def run_ours(args, rank, world):
     torch.cuda.empty_cache()
     m32 = fr.FRMesh(mesh, fr.make_params(p=P, prec="fp32", p_ref=p0, rho_ref=1.0))
     U = torch.from_numpy(U0).cuda()
+    U32 = U.float()
+    m32.autotune(U32, torch.empty_like(U32))
+    del U32
     # FP32 fused: low-Mach form (<= 2e-5 relative RHS error against the FP64 oracle)
     forms["fused_fp32"] = dof * RHS_PER_STEP / (time_rk4(m32, U, ksteps, 2, torch) * 1e-3) / 1e9
     m32.set_form("unfused")   # plain FP32, one kernel per paper kernel
@@ -359,7 +366,8 @@ def run_ours(args, rank, world):
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": workload_name(), "elements": info["elements"], "dof": dof, "rhs_per_step": RHS_PER_STEP,
-                   "form": "fused", "l2": "inputs larger than L2 (283 MB FP64 state, 129 MB L2)",
+                   "form": "fused", "volume_kernel_threads": tuned,
+                   "l2": "inputs larger than L2 (283 MB FP64 state, 129 MB L2)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"kernel": "fused B (volume group)", "bound": "alu", "achieved": achieved, "peak": peak_fp64,
                      "unit": "TFLOP/s", "frac": achieved / peak_fp64, "traffic": None,

@@ -139,6 +139,13 @@ fr_status fr_rk4_step(fr_mesh *m, void *U_dev, double dt, int nsteps, void *stre
  * synchronises the stream. */
 fr_status fr_rk4_step_host(fr_mesh *m, void *U_host, double dt, int nsteps, void *stream);
 
+/* Autotuner: times every launch shape of the volume kernel (64, 128 or 256 threads per element) of
+ * each hexahedral group (one element type and order) on the given device state U_dev (R_dev is
+ * scratch output) and keeps the fastest for later calls. chosen[i] (n_chosen entries, may be NULL)
+ * receives the shape index 0, 1, 2 of group i. Results of later calls do not depend on the choice:
+ * every shape evaluates each output with the same operations. Synchronises the stream. */
+fr_status fr_autotune(fr_mesh *m, const void *U_dev, void *R_dev, int *chosen, int n_chosen, void *stream);
+
 /* Blocks until the stream's work on this handle has finished and returns the latched device
  * status (FR_OK or FR_ENONPHYS), clearing it. */
 fr_status fr_sync_status(fr_mesh *m, void *stream);

@@ -57,7 +57,10 @@ struct Group {
     int *d_eph = nullptr;
     void *d_phtab = nullptr;        // Phys<T> per instance
     uint32_t *d_lpts = nullptr;     // L flux points of the group (element_in_group * 256 + local)
+    int variant = 1;                // volume-kernel launch shape (autotuned: 0, 1, 2 = 64, 128, 256 threads)
     void *d_geo64 = nullptr;        // Geo<double> per element in group order (low-Mach form)
+    void *d_fnrm = nullptr;         // face normal table in group order
+    double *d_fnrm64 = nullptr;
     long long nlpts = 0;
 };
 
@@ -78,6 +81,9 @@ struct fr_mesh {
     bool lowmach = false;              // FP32 low-Mach form (deviations, reduced energy, FP64 mass)
     void *d_geo64 = nullptr;           // FP64 geometry for the low-Mach form
     double *d_MF = nullptr, *d_RL = nullptr;
+    std::vector<double> fnrm_host;     // [elem][6][4] unit normal and |n_s| per face
+    void *d_fnrm = nullptr;            // same in the compute precision
+    double *d_fnrm64 = nullptr;        // FP64 copy (low-Mach form)
     std::vector<double> geo_host;        // per element Ji[9], det (FP64)
     // device
     void *d_geo = nullptr;               // Geo<T>[ne]
@@ -547,9 +553,62 @@ static Phys<T> phys_of(const fr_params &P)
     return ph;
 }
 
+// Unit outward normal and |n_s| (n_s = detJ J^-T n~) of every face of every element, in FP64.
+static void build_face_normals(fr_mesh *m)
+{
+    const double r2 = 1.0 / std::sqrt(2.0);
+    const double pri_n[5][3] = {{0, 0, -1}, {0, 0, 1}, {0, -1, 0}, {r2, r2, 0}, {-1, 0, 0}};
+    m->fnrm_host.assign((size_t)m->ne * 24, 0.0);
+    for (const Block &B : m->blocks)
+        for (long long e = 0; e < B.ne; e++) {
+            const long long ge = B.elem0 + e;
+            const double *Ji = &m->geo_host[(size_t)ge * 10], det = m->geo_host[(size_t)ge * 10 + 9];
+            const int nfaces = B.type == 0 ? 6 : 5;
+            for (int f = 0; f < nfaces; f++) {
+                double nr[3] = {0, 0, 0};
+                if (B.type == 0) nr[f / 2] = (f & 1) ? 1.0 : -1.0;
+                else for (int d = 0; d < 3; d++) nr[d] = pri_n[f][d];
+                double ns[3];
+                for (int k = 0; k < 3; k++) ns[k] = det * (Ji[k] * nr[0] + Ji[3 + k] * nr[1] + Ji[6 + k] * nr[2]);
+                const double mag = std::sqrt(ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]);
+                double *o = &m->fnrm_host[((size_t)ge * 6 + f) * 4];
+                for (int k = 0; k < 3; k++) o[k] = ns[k] / mag;
+                o[3] = mag;
+            }
+        }
+}
+
+template <typename T>
+static fr_status upload_face_normals(fr_mesh *m, const std::vector<long long> &order, void **dT, double **d64)
+{
+    std::vector<T> t(order.size() * 24);
+    std::vector<double> t64(order.size() * 24);
+    for (size_t i = 0; i < order.size(); i++)
+        for (int k = 0; k < 24; k++) {
+            t64[i * 24 + k] = m->fnrm_host[(size_t)order[i] * 24 + k];
+            t[i * 24 + k] = (T)t64[i * 24 + k];
+        }
+    fr_status st = dalloc(m, dT, t.size() * sizeof(T));
+    if (st) return st;
+    CU(cudaMemcpy(*dT, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice));
+    if (m->lowmach) {
+        st = dalloc(m, (void **)d64, t64.size() * sizeof(double));
+        if (st) return st;
+        CU(cudaMemcpy(*d64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    return FR_OK;
+}
+
 template <typename T>
 static fr_status build_groups(fr_mesh *m, const std::vector<uint32_t> &partner)
 {
+    {
+        build_face_normals(m);
+        std::vector<long long> all((size_t)m->ne);
+        for (long long e = 0; e < m->ne; e++) all[e] = e;
+        fr_status st = upload_face_normals<T>(m, all, &m->d_fnrm, &m->d_fnrm64);
+        if (st) return st;
+    }
     for (size_t b = 0; b < m->blocks.size(); b++) {
         const Block &B = m->blocks[b];
         Group *g = nullptr;
@@ -579,6 +638,13 @@ static fr_status build_groups(fr_mesh *m, const std::vector<uint32_t> &partner)
         if (sl) return sl;
         CU(cudaMemcpy(g.d_lpts, lp.data(), lp.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
         if (g.blks.size() < 2) continue;
+        {
+            std::vector<long long> order;
+            for (int bi : g.blks)
+                for (long long e = 0; e < m->blocks[bi].ne; e++) order.push_back(m->blocks[bi].elem0 + e);
+            fr_status sn = upload_face_normals<T>(m, order, &g.d_fnrm, &g.d_fnrm64);
+            if (sn) return sn;
+        }
         if (m->lowmach) {
             std::vector<Geo<double>> g64;
             for (int bi : g.blks) {
@@ -680,7 +746,7 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
 extern "C" fr_status fr_destroy(fr_mesh *m)
 {
     if (!m) return FR_OK;
-    void **bufs[] = {&m->d_geo64, (void **)&m->d_MF, (void **)&m->d_RL, &m->d_priops, &m->d_geo, (void **)&m->d_partner, &m->d_UF, &m->d_FV, &m->d_CF, &m->d_QF, &m->d_DF, &m->d_Qu,
+    void **bufs[] = {&m->d_fnrm, (void **)&m->d_fnrm64, &m->d_geo64, (void **)&m->d_MF, (void **)&m->d_RL, &m->d_priops, &m->d_geo, (void **)&m->d_partner, &m->d_UF, &m->d_FV, &m->d_CF, &m->d_QF, &m->d_DF, &m->d_Qu,
                      &m->d_UQ, &m->d_QQ, &m->d_Rt, &m->d_rk_k, &m->d_rk_us, (void **)&m->d_rk_acc, &m->d_io_U,
                      &m->d_io_R, (void **)&m->d_wsum, (void **)&m->d_status, &m->d_Qsnap};
     for (void **b : bufs) dfree(*b);
@@ -688,6 +754,8 @@ extern "C" fr_status fr_destroy(fr_mesh *m)
         dfree(g.d_geo); dfree((void *&)g.d_eu0); dfree((void *&)g.d_ef0); dfree((void *&)g.d_eph); dfree(g.d_phtab);
         dfree((void *&)g.d_lpts);
         dfree(g.d_geo64);
+        dfree(g.d_fnrm);
+        dfree((void *&)g.d_fnrm64);
     }
     if (m->h_status) cudaFreeHost(m->h_status);
     for (auto &t : m->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
@@ -758,6 +826,8 @@ static HexArgs<T> make_args(fr_mesh *m, const Block &b, const void *U, void *R)
     a.geo64 = m->d_geo64 ? reinterpret_cast<const Geo<double> *>(m->d_geo64) + b.elem0 : nullptr;
     a.MF = m->d_MF;
     a.RL = m->d_RL;
+    a.fnrm = m->d_fnrm ? reinterpret_cast<const T *>(m->d_fnrm) + b.elem0 * 24 : nullptr;
+    a.fnrm64 = m->d_fnrm64 ? m->d_fnrm64 + b.elem0 * 24 : nullptr;
     a.U = reinterpret_cast<const T *>(U); a.R = reinterpret_cast<T *>(R);
     a.UF = reinterpret_cast<T *>(m->d_UF); a.FV = reinterpret_cast<T *>(m->d_FV);
     a.CF = reinterpret_cast<T *>(m->d_CF); a.QF = reinterpret_cast<T *>(m->d_QF); a.DF = reinterpret_cast<T *>(m->d_DF);
@@ -833,6 +903,8 @@ static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, co
                     a.geo = reinterpret_cast<const Geo<T> *>(gr.d_geo);
                     a.eu0 = gr.d_eu0; a.ef0 = gr.d_ef0; a.eph = gr.d_eph;
                     if (m->lowmach) a.geo64 = reinterpret_cast<const Geo<double> *>(gr.d_geo64);
+                    a.fnrm = reinterpret_cast<const T *>(gr.d_fnrm);
+                    a.fnrm64 = gr.d_fnrm64;
                     a.phtab = reinterpret_cast<const Phys<T> *>(gr.d_phtab);
                 }
                 a.lpts = gr.d_lpts; a.nlpts = gr.nlpts;
@@ -840,7 +912,7 @@ static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, co
                     a.rkstage = rk.stage + 1; a.rkdt = rk.dt; a.rkU = rk.U; a.rkacc = rk.acc;
                     a.rkus = reinterpret_cast<T *>(rk.us);
                 }
-                int lr = b.type == 0 ? hex_fused_phase<T>(b.p, ph, a, s)
+                int lr = b.type == 0 ? hex_fused_phase<T>(b.p, ph, a, s, gr.variant)
                                      : pri_fused_phase<T>(ph, a, reinterpret_cast<const PriOps<T> *>(m->d_priops), s);
                 if (lr) return fail(FR_ECUDA, "fused phase %d launch: %s", ph, cudaGetErrorString(cudaGetLastError()));
             }
@@ -872,6 +944,80 @@ static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, co
 static fr_status rhs_dispatch(fr_mesh *m, const void *U, void *R, cudaStream_t s)
 {
     return m->prec == FR_FP64 ? rhs_impl<double>(m, U, R, s) : rhs_impl<float>(m, U, R, s);
+}
+
+// Times every launch shape of the volume kernel of each hexahedral group on the caller's state and
+// keeps the fastest. Every shape computes each output with the same operations, so results do not
+// depend on the choice.
+template <typename T>
+static fr_status autotune_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, int *chosen)
+{
+    // face solution of the current state first (the volume kernel reads it)
+    for (const Group &gr : m->groups) {
+        const Block &b = m->blocks[gr.blks[0]];
+        HexArgs<T> a = make_args<T>(m, b, U, R);
+        if (gr.blks.size() > 1) {
+            a.ne = gr.ne; a.u0 = 0; a.f0 = 0;
+            a.geo = reinterpret_cast<const Geo<T> *>(gr.d_geo);
+            a.eu0 = gr.d_eu0; a.ef0 = gr.d_ef0; a.eph = gr.d_eph;
+            a.phtab = reinterpret_cast<const Phys<T> *>(gr.d_phtab);
+            if (m->lowmach) a.geo64 = reinterpret_cast<const Geo<double> *>(gr.d_geo64);
+            a.fnrm = reinterpret_cast<const T *>(gr.d_fnrm);
+            a.fnrm64 = gr.d_fnrm64;
+        }
+        int lr = b.type == 0 ? hex_fused_phase<T>(b.p, 0, a, s, gr.variant)
+                             : pri_fused_phase<T>(0, a, reinterpret_cast<const PriOps<T> *>(m->d_priops), s);
+        if (lr) return fail(FR_ECUDA, "autotune: face phase launch failed");
+    }
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    int gi = 0;
+    for (Group &gr : m->groups) {
+        const Block &b = m->blocks[gr.blks[0]];
+        if (b.type != 0) { chosen[gi++] = gr.variant; continue; }
+        HexArgs<T> a = make_args<T>(m, b, U, R);
+        if (gr.blks.size() > 1) {
+            a.ne = gr.ne; a.u0 = 0; a.f0 = 0;
+            a.geo = reinterpret_cast<const Geo<T> *>(gr.d_geo);
+            a.eu0 = gr.d_eu0; a.ef0 = gr.d_ef0; a.eph = gr.d_eph;
+            a.phtab = reinterpret_cast<const Phys<T> *>(gr.d_phtab);
+            if (m->lowmach) a.geo64 = reinterpret_cast<const Geo<double> *>(gr.d_geo64);
+            a.fnrm = reinterpret_cast<const T *>(gr.d_fnrm);
+            a.fnrm64 = gr.d_fnrm64;
+        }
+        float best = 1e30f;
+        int bestv = gr.variant;
+        for (int v = 0; v < 3; v++) {
+            if (hex_fused_phase<T>(b.p, 1, a, s, v)) return fail(FR_ECUDA, "autotune: volume launch failed");  // warm-up
+            CU(cudaEventRecord(e0, s));
+            for (int r = 0; r < 2; r++) hex_fused_phase<T>(b.p, 1, a, s, v);
+            CU(cudaEventRecord(e1, s));
+            CU(cudaEventSynchronize(e1));
+            float ms = 0;
+            CU(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) { best = ms; bestv = v; }
+        }
+        gr.variant = bestv;
+        chosen[gi++] = bestv;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CU(cudaPeekAtLastError());
+    if (m->graph) { cudaGraphExecDestroy(m->graph); m->graph = nullptr; }   // recapture with the new shapes
+    return FR_OK;
+}
+
+extern "C" fr_status fr_autotune(fr_mesh *m, const void *U_dev, void *R_dev, int *chosen, int n_chosen, void *stream)
+{
+    if (!m || !U_dev || !R_dev) return fail(FR_EINVAL, "null argument");
+    std::vector<int> tmp(m->groups.size(), 0);
+    fr_status st = m->prec == FR_FP64 ? autotune_impl<double>(m, U_dev, R_dev, (cudaStream_t)stream, tmp.data())
+                                      : autotune_impl<float>(m, U_dev, R_dev, (cudaStream_t)stream, tmp.data());
+    if (st) return st;
+    if (chosen)
+        for (int i = 0; i < n_chosen && i < (int)tmp.size(); i++) chosen[i] = tmp[i];
+    return check_status(m);
 }
 
 extern "C" fr_status fr_rhs(fr_mesh *m, const void *U_dev, void *R_dev, void *stream)

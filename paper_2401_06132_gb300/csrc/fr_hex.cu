@@ -60,6 +60,24 @@ __device__ __forceinline__ void face_normal(const Geo<T> &g, int f, T *n, T &mag
     for (int k = 0; k < 3; k++) n[k] = ns[k] * im;
 }
 
+// Unit normal and |n_s| of face f of element e from the per-element face table.
+template <typename T, typename V>
+__device__ __forceinline__ void face_nrm(const V *tab, long long e, int f, V *n, V &mag)
+{
+    const V *t = tab + (e * 6 + f) * 4;
+    n[0] = t[0]; n[1] = t[1]; n[2] = t[2]; mag = t[3];
+}
+
+// Same line in a padded shared-memory layout (x-line stride XS, plane stride PS).
+template <int N, int XS, int PS>
+__device__ __forceinline__ void face_line_p(int f, int local, int &base, int &stride)
+{
+    const int d = f >> 1, a = local % N, b = local / N;
+    if (d == 0) { base = XS * a + PS * b; stride = 1; }
+    else if (d == 1) { base = a + PS * b; stride = XS; }
+    else { base = a + XS * b; stride = PS; }
+}
+
 template <int N>
 __device__ __forceinline__ void face_line(int f, int local, int &base, int &stride)
 {
@@ -142,17 +160,18 @@ __global__ void __launch_bounds__(NT) k_disu_blk(HexArgs<T> a)
                     int base, stride;
                     face_line<N>(f, sp % (N * N), base, stride);
                     const double *l = (f & 1) ? o64.lR : o64.lL;
-                    double mv[3];
+                    double n[3], mag;
+                    face_nrm<T, double>(a.fnrm64, e0 + el, f, n, mag);
+                    double mv[3] = {0.0, 0.0, 0.0};
 #pragma unroll
                     for (int k = 0; k < 3; k++) {
+                        if (n[k] == 0.0) continue;   // axis-aligned faces need one component
                         const T *u = s_u + (el * FR_NV + 1 + k) * NU + base;
                         double v = 0.0;
 #pragma unroll
                         for (int i = 0; i < N; i++) v += l[i] * (double)u[i * stride];
                         mv[k] = v;
                     }
-                    double n[3], mag;
-                    face_normal(a.geo64[e0 + el], f, n, mag);
                     a.MF[elem_f0(a, e0 + el, NF) + sp] = n[0] * mv[0] + n[1] * mv[1] + n[2] * mv[2];
                 }
             }
@@ -167,20 +186,23 @@ __global__ void __launch_bounds__(NT) k_disu_blk(HexArgs<T> a)
 template <typename T, int P>
 struct HexSmem {
     static constexpr int N = P + 1, M = P + 2, NU = N * N * N, NF = 6 * N * N, NQ = M * M * M;
+    // solution-point fields are padded so that x-lines of even length do not start on the same banks
+    static constexpr int XS = (N % 2 == 0) ? N + 1 : N, PS = XS * N, FS = PS * N;
     static constexpr int T1 = 5 * M * N * N, T2 = 5 * M * M * N;
-    static constexpr int SIZE = 5 * NU + 15 * NU + 5 * NF + 20 * NQ + T1 + T2;
+    static constexpr int SIZE = 5 * FS + 15 * FS + 5 * NF + 20 * NQ + T1 + T2;
 };
 
 // Sum-factorised interpolation of 5 fields (src, stride NU) to quadrature points (dst, stride NQ).
-template <typename T, int P, int NT>
+template <typename T, int P, int NT, int XS = P + 1, int PS = (P + 1) * (P + 1), int FS = (P + 1) * (P + 1) * (P + 1)>
 __device__ __forceinline__ void interp_5(const HexOps<T> &op, const T *src, T *t1, T *t2, T *dst)
 {
-    constexpr int N = P + 1, M = P + 2, NU = N * N * N, NQ = M * M * M;
+    constexpr int N = P + 1, M = P + 2, NQ = M * M * M;
     for (int it = threadIdx.x; it < 5 * N * N; it += NT) {  // x: (fc, j, k)
         const int fc = it / (N * N), jk = it % (N * N);
+        const int sb = fc * FS + XS * (jk % N) + PS * (jk / N);
         T u[N];
 #pragma unroll
-        for (int i = 0; i < N; i++) u[i] = src[fc * NU + i + N * jk];
+        for (int i = 0; i < N; i++) u[i] = src[sb + i];
 #pragma unroll
         for (int q = 0; q < M; q++) {
             T v = T(0);
@@ -222,10 +244,10 @@ __device__ __forceinline__ void interp_5(const HexOps<T> &op, const T *src, T *t
 
 // Sum-factorised L2 projection of 5 fields from quadrature points (src, stride NQ) to solution
 // points (dst, stride NU).
-template <typename T, int P, int NT>
+template <typename T, int P, int NT, int XS = P + 1, int PS = (P + 1) * (P + 1), int FS = (P + 1) * (P + 1) * (P + 1)>
 __device__ __forceinline__ void project_5(const HexOps<T> &op, const T *src, T *t1, T *t2, T *dst)
 {
-    constexpr int N = P + 1, M = P + 2, NU = N * N * N, NQ = M * M * M;
+    constexpr int N = P + 1, M = P + 2, NQ = M * M * M;
     for (int it = threadIdx.x; it < 5 * M * M; it += NT) {  // z: (fc, qa, qb) -> k
         const int fc = it / (M * M), ab = it % (M * M);
         T u[M];
@@ -259,12 +281,13 @@ __device__ __forceinline__ void project_5(const HexOps<T> &op, const T *src, T *
         T u[M];
 #pragma unroll
         for (int q = 0; q < M; q++) u[q] = t1[fc * M * N * N + q + M * jk];
+        const int db = fc * FS + XS * (jk % N) + PS * (jk / N);
 #pragma unroll
         for (int i = 0; i < N; i++) {
             T v = T(0);
 #pragma unroll
             for (int q = 0; q < M; q++) v += op.Pj[i][q] * u[q];
-            dst[fc * NU + i + N * jk] = v;
+            dst[db + i] = v;
         }
     }
     __syncthreads();
@@ -275,11 +298,12 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
 {
     using S = HexSmem<T, P>;
     constexpr int N = S::N, M = S::M, NU = S::NU, NF = S::NF, NQ = S::NQ;
+    constexpr int XS = S::XS, PS = S::PS, FS = S::FS;
     (void)M;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s_u = reinterpret_cast<T *>(smem_raw);
-    T *s_q = s_u + 5 * NU;
-    T *s_c = s_q + 15 * NU;
+    T *s_q = s_u + 5 * FS;
+    T *s_c = s_q + 15 * FS;
     T *s_w = s_c + 5 * NF;
     T *s_t1 = s_w + 20 * NQ;
     T *s_t2 = s_t1 + S::T1;
@@ -301,7 +325,8 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
             if constexpr (std::is_same<T, float>::value) {
                 if (dev) v -= (it < NU) ? ph.rref : (it >= 4 * NU ? ph.eref : T(0));
             }
-            s_u[it] = v;
+            const int alpha = it / NU, z = it % NU;
+            s_u[alpha * FS + z % N + XS * ((z / N) % N) + PS * (z / (N * N))] = v;
         }
         // 2. con_u: common solution at own flux points, C = (1/2 - beta) uL + (1/2 + beta) uR
         for (int it = threadIdx.x; it < 5 * NF; it += NT) {
@@ -318,17 +343,17 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
         for (int it = threadIdx.x; it < 15 * N * N; it += NT) {
             const int alpha = it / (3 * N * N), r = it % (3 * N * N), d = r / (N * N), loc = r % (N * N);
             int base, stride;
-            face_line<N>(2 * d, loc, base, stride);
+            face_line_p<N, XS, PS>(2 * d, loc, base, stride);
             T u[N];
 #pragma unroll
-            for (int i = 0; i < N; i++) u[i] = s_u[alpha * NU + base + i * stride];
+            for (int i = 0; i < N; i++) u[i] = s_u[alpha * FS + base + i * stride];
             const T cL = s_c[alpha * NF + (2 * d) * N * N + loc], cR = s_c[alpha * NF + (2 * d + 1) * N * N + loc];
 #pragma unroll
             for (int i = 0; i < N; i++) {
                 T v = op.liftR[i] * cR - op.liftL[i] * cL;
 #pragma unroll
                 for (int j = 0; j < N; j++) v += op.Dh[i][j] * u[j];
-                s_q[(alpha * 3 + d) * NU + base + i * stride] = v;
+                s_q[(alpha * 3 + d) * FS + base + i * stride] = v;
             }
         }
         __syncthreads();
@@ -337,13 +362,13 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
                            g.Ji[6] == T(0) && g.Ji[7] == T(0);
         for (int it = threadIdx.x; it < 5 * NU; it += NT) {
             const int alpha = it / NU, z = it % NU;
-            T *q = s_q + alpha * 3 * NU + z;
+            T *q = s_q + alpha * 3 * FS + z % N + XS * ((z / N) % N) + PS * (z / (N * N));
             if (diagJ) {
-                q[0] *= g.Ji[0]; q[NU] *= g.Ji[4]; q[2 * NU] *= g.Ji[8];
+                q[0] *= g.Ji[0]; q[FS] *= g.Ji[4]; q[2 * FS] *= g.Ji[8];
             } else {
-                const T q0 = q[0], q1 = q[NU], q2 = q[2 * NU];
+                const T q0 = q[0], q1 = q[FS], q2 = q[2 * FS];
 #pragma unroll
-                for (int k = 0; k < 3; k++) q[k * NU] = g.Ji[k] * q0 + g.Ji[3 + k] * q1 + g.Ji[6 + k] * q2;
+                for (int k = 0; k < 3; k++) q[k * FS] = g.Ji[k] * q0 + g.Ji[3 + k] * q1 + g.Ji[6 + k] * q2;
             }
         }
         // 5. gradcoru_fpts + the viscous part of comm_flux: own-normal n.f^v at own flux points.
@@ -368,25 +393,25 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
             const int s = s_list[li];
             const int f = s / (N * N), loc = s % (N * N);
             int base, stride;
-            face_line<N>(f, loc, base, stride);
+            face_line_p<N, XS, PS>(f, loc, base, stride);
             const T *l = (f & 1) ? op.lR : op.lL;
             T uf[5], qf[5][3];
 #pragma unroll
             for (int alpha = 0; alpha < 5; alpha++) {
                 T v = T(0);
 #pragma unroll
-                for (int i = 0; i < N; i++) v += l[i] * s_u[alpha * NU + base + i * stride];
+                for (int i = 0; i < N; i++) v += l[i] * s_u[alpha * FS + base + i * stride];
                 uf[alpha] = v;
 #pragma unroll
                 for (int d = 0; d < 3; d++) {
                     T w = T(0);
 #pragma unroll
-                    for (int i = 0; i < N; i++) w += l[i] * s_q[(alpha * 3 + d) * NU + base + i * stride];
+                    for (int i = 0; i < N; i++) w += l[i] * s_q[(alpha * 3 + d) * FS + base + i * stride];
                     qf[alpha][d] = w;
                 }
             }
             T n[3], mag;
-            face_normal(g, f, n, mag);
+            face_nrm<T, T>(a.fnrm, e, f, n, mag);
             if constexpr (std::is_same<T, float>::value) {
                 if (dev) { uf[0] += ph.rref; uf[4] += ph.eref; }
             }
@@ -402,10 +427,17 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
                 const HexOps<double> &o64 = OPS<double>(P - 2);
                 const Geo<double> g64 = a.geo64[e];
                 for (int it = threadIdx.x; it < NU; it += NT) {
-                    const double m0 = s_u[NU + it], m1 = s_u[2 * NU + it], m2 = s_u[3 * NU + it];
+                    const int pz = it % N + XS * ((it / N) % N) + PS * (it / (N * N));
+                    const double m0 = s_u[FS + pz], m1 = s_u[2 * FS + pz], m2 = s_u[3 * FS + pz];
+                    if (diagJ) {
+                        s_m64[it] = g64.det * g64.Ji[0] * m0;
+                        s_m64[NU + it] = g64.det * g64.Ji[4] * m1;
+                        s_m64[2 * NU + it] = g64.det * g64.Ji[8] * m2;
+                    } else {
 #pragma unroll
-                    for (int d = 0; d < 3; d++)
-                        s_m64[d * NU + it] = g64.det * (g64.Ji[3 * d] * m0 + g64.Ji[3 * d + 1] * m1 + g64.Ji[3 * d + 2] * m2);
+                        for (int d = 0; d < 3; d++)
+                            s_m64[d * NU + it] = g64.det * (g64.Ji[3 * d] * m0 + g64.Ji[3 * d + 1] * m1 + g64.Ji[3 * d + 2] * m2);
+                    }
                 }
                 __syncthreads();
                 const long long pbase = elem_u0(a, e, NU) / FR_NV;
@@ -423,9 +455,9 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
             }
         }
         // 6. uqpts + gradcoru_qpts: 20 fields to quadrature points, 5 at a time
-        interp_5<T, P, NT>(op, s_u, s_t1, s_t2, s_w);
+        interp_5<T, P, NT, XS, PS, FS>(op, s_u, s_t1, s_t2, s_w);
 #pragma unroll 1
-        for (int c = 0; c < 3; c++) interp_5<T, P, NT>(op, s_q + 5 * c * NU, s_t1, s_t2, s_w + (5 + 5 * c) * NQ);
+        for (int c = 0; c < 3; c++) interp_5<T, P, NT, XS, PS, FS>(op, s_q + 5 * c * FS, s_t1, s_t2, s_w + (5 + 5 * c) * NQ);
         // 7. tdisf: transformed flux at each quadrature point, in place
         bool ok = true;
         for (int q = threadIdx.x; q < NQ; q += NT) {
@@ -462,18 +494,18 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
         __syncthreads();
         // 8. tdivtpcorf, first factor: projection of the 15 transformed-flux fields (into s_q)
 #pragma unroll 1
-        for (int c = 0; c < 3; c++) project_5<T, P, NT>(op, s_w + 5 * c * NQ, s_t1, s_t2, s_q + 5 * c * NU);
+        for (int c = 0; c < 3; c++) project_5<T, P, NT, XS, PS, FS>(op, s_w + 5 * c * NQ, s_t1, s_t2, s_q + 5 * c * FS);
         // 9. tdivtpcorf, second factor: R~ = sum_d Dh_d F~_d, written to R (finished in phase C)
         T *R = a.R + elem_u0(a, e, NU);
         for (int it = threadIdx.x; it < 5 * NU; it += NT) {
             const int alpha = it / NU, z = it % NU, i = z % N, j = (z / N) % N, k = z / (N * N);
-            const T *F = s_q + alpha * 3 * NU;
+            const T *F = s_q + alpha * 3 * FS;
             T v = T(0);
 #pragma unroll
             for (int b = 0; b < N; b++) {
-                v += op.Dh[i][b] * F[b + N * j + N * N * k];
-                v += op.Dh[j][b] * F[NU + i + N * b + N * N * k];
-                v += op.Dh[k][b] * F[2 * NU + i + N * j + N * N * b];
+                v += op.Dh[i][b] * F[b + XS * j + PS * k];
+                v += op.Dh[j][b] * F[FS + i + XS * b + PS * k];
+                v += op.Dh[k][b] * F[2 * FS + i + XS * j + PS * b];
             }
             R[it] = v;
         }
@@ -509,7 +541,7 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
 #pragma unroll
             for (int k = 0; k < 4; k++) { fvo[k] = a.FV[k * a.nfpt + og]; fvp[k] = a.FV[k * a.nfpt + pg]; }
             T n[3], mag;
-            face_normal(g, f, n, mag);
+            face_nrm<T, T>(a.fnrm, e, f, n, mag);
             T nL[3] = {isL ? n[0] : -n[0], isL ? n[1] : -n[1], isL ? n[2] : -n[2]};
             T F[5];
             if constexpr (std::is_same<T, float>::value) {
@@ -521,8 +553,7 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
                     const double mL = isL ? mo : mp, mR = isL ? mp : mo;
                     const double rL = isL ? uo[0] : up[0], rR = isL ? up[0] : uo[0];
                     const double Fr = 0.5 * (mL - mR) + (0.5 * (double)sw + (double)ph.tau) * (rL - rR);
-                    double n64[3], mag64;
-                    face_normal(a.geo64[e], f, n64, mag64);
+                    const double mag64 = a.fnrm64[(e * 6 + f) * 4 + 3];
                     s_d64[s] = isL ? mag64 * Fr : -mag64 * Fr;
                 } else {
                     ok &= isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
@@ -605,7 +636,7 @@ __global__ void __launch_bounds__(128) k_pair_flux(HexArgs<T> a)
 #pragma unroll
         for (int k = 0; k < 4; k++) { fvL[k] = a.FV[k * a.nfpt + gl]; fvR[k] = a.FV[k * a.nfpt + gr]; }
         T n[3], mag;
-        face_normal(a.geo[e], f, n, mag);
+        face_nrm<T, T>(a.fnrm, e, f, n, mag);
         T F[5];
         ok &= common_flux(ph, uL, uR, fvL, fvR, n, F);
 #pragma unroll
@@ -627,8 +658,7 @@ __global__ void __launch_bounds__(NT) k_lift(HexArgs<T> a)
             const uint32_t pc = a.partner[gf0 + s];
             const bool isL = (pc & FR_LFLAG) != 0;
             const long long src = isL ? gf0 + s : (long long)(pc & ~FR_LFLAG);
-            T n[3], mag;
-            face_normal(g, s / (N * N), n, mag);
+            const T mag = a.fnrm[(e * 6 + s / (N * N)) * 4 + 3];
             const T sc = isL ? mag : -mag;
 #pragma unroll
             for (int k = 0; k < 5; k++) s_d[k * NF + s] = sc * a.DF[k * a.nfpt + src];
@@ -907,8 +937,20 @@ static int grid_elems(long long ne, int per_sm)
     return (int)(g < 1 ? 1 : g);
 }
 
+template <typename T, int P, int NT>
+static void launch_B(const HexArgs<T> &a, cudaStream_t s)
+{
+    const size_t smem = HexSmem<T, P>::SIZE * sizeof(T);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_fused_B<T, P, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    k_fused_B<T, P, NT><<<grid_elems(a.ne, 8), NT, smem, s>>>(a);
+}
+
 template <typename T, int P>
-static int fused_phase(int phase, const HexArgs<T> &a, cudaStream_t s)
+static int fused_phase(int phase, const HexArgs<T> &a, cudaStream_t s, int variant)
 {
     constexpr int N = P + 1, NF = 6 * N * N;
     if (a.ne == 0) return 0;
@@ -918,14 +960,10 @@ static int fused_phase(int phase, const HexArgs<T> &a, cudaStream_t s)
         if (g > 152LL * 16) g = 152LL * 16;
         k_disu_blk<T, P, EB, 256><<<(int)g, 256, 0, s>>>(a);
     } else if (phase == 1) {
-        constexpr int NT = 128;
-        const size_t smem = HexSmem<T, P>::SIZE * sizeof(T);
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_fused_B<T, P, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr = true;
-        }
-        k_fused_B<T, P, NT><<<grid_elems(a.ne, 8), NT, smem, s>>>(a);
+        // launch shape chosen by the autotuner: 64, 128 or 256 threads per element
+        if (variant == 0) launch_B<T, P, 64>(a, s);
+        else if (variant == 2) launch_B<T, P, 256>(a, s);
+        else launch_B<T, P, 128>(a, s);
     } else if (phase == 2) {
         k_fused_C<T, P, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
     } else if (phase == 3) {
@@ -961,11 +999,11 @@ static int unfused_kernel(int k, const HexArgs<T> &a, cudaStream_t s)
 }
 
 template <typename T>
-int hex_fused_phase(int p, int phase, const HexArgs<T> &a, cudaStream_t s)
+int hex_fused_phase(int p, int phase, const HexArgs<T> &a, cudaStream_t s, int variant)
 {
     switch (p) {
-    case 3: return fused_phase<T, 3>(phase, a, s);
-    case 4: return fused_phase<T, 4>(phase, a, s);
+    case 3: return fused_phase<T, 3>(phase, a, s, variant);
+    case 4: return fused_phase<T, 4>(phase, a, s, variant);
     default: return -3;
     }
 }
@@ -980,7 +1018,7 @@ int hex_unfused_kernel(int p, int k, const HexArgs<T> &a, cudaStream_t s)
     }
 }
 
-template int hex_fused_phase<double>(int, int, const HexArgs<double> &, cudaStream_t);
-template int hex_fused_phase<float>(int, int, const HexArgs<float> &, cudaStream_t);
+template int hex_fused_phase<double>(int, int, const HexArgs<double> &, cudaStream_t, int);
+template int hex_fused_phase<float>(int, int, const HexArgs<float> &, cudaStream_t, int);
 template int hex_unfused_kernel<double>(int, int, const HexArgs<double> &, cudaStream_t);
 template int hex_unfused_kernel<float>(int, int, const HexArgs<float> &, cudaStream_t);

@@ -150,6 +150,9 @@ struct HexArgs {
     const Geo<double> *geo64;
     double *MF;
     double *RL;
+    // Per element and face (6 slots; prisms use 5): unit outward normal and |n_s|, n_s = detJ J^-T n~
+    const T *fnrm;            // [elem][6][4] in the compute precision
+    const double *fnrm64;     // [elem][6][4] in FP64 (low-Mach mass channel)
     // Split interface phase (FP64): C1 evaluates each pair once from its L point (list lpts, entries
     // element_in_launch * 256 + local flux point) into DF; C2 lifts per element.
     const uint32_t *lpts;
@@ -198,7 +201,8 @@ __device__ __forceinline__ Phys<T> elem_phys(const HexArgs<T> &a, long long e)
 
 // Launchers (fr_hex.cu). phase: 0 = A (face solution), 1 = B (volume group), 2 = C (interfaces),
 // 3 = C1 (common flux once per pair, into DF), 4 = C2 (lift and scale from DF).
-template <typename T> int hex_fused_phase(int p, int phase, const HexArgs<T> &a, cudaStream_t s);
+// variant: launch shape of the volume kernel (0, 1, 2 = 64, 128, 256 threads per element)
+template <typename T> int hex_fused_phase(int p, int phase, const HexArgs<T> &a, cudaStream_t s, int variant = 1);
 // kernel: 1..13 in the paper's order (disu .. negdivconf)
 template <typename T> int hex_unfused_kernel(int p, int kernel, const HexArgs<T> &a, cudaStream_t s);
 int hex_upload_ops(int p, int m, const frb::Hex1D &h);

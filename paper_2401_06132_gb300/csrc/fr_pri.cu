@@ -207,8 +207,8 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
 #pragma unroll
                 for (int d = 0; d < 3; d++) qf[alpha][d] = face_value(op, s_q + (alpha * 3 + d) * NU, s);
             }
-            T n[3], mag;
-            pri_normal(g, face_of(s), n, mag);
+            const T *nt = a.fnrm + (e * 6 + face_of(s)) * 4;
+            T n[3] = {nt[0], nt[1], nt[2]};
             T fvn[4];
             viscous_normal_flux(ph, uf, qf, n, fvn);
 #pragma unroll
@@ -276,8 +276,9 @@ __global__ void __launch_bounds__(NTH) k_pri_C(HexArgs<T> a, const PriOps<T> *go
             for (int k = 0; k < 5; k++) { uo[k] = a.UF[k * a.nfpt + og]; up[k] = a.UF[k * a.nfpt + pg]; }
 #pragma unroll
             for (int k = 0; k < 4; k++) { fvo[k] = a.FV[k * a.nfpt + og]; fvp[k] = a.FV[k * a.nfpt + pg]; }
-            T n[3], mag;
-            pri_normal(g, face_of(s), n, mag);
+            const T *nt = a.fnrm + (e * 6 + face_of(s)) * 4;
+            T n[3] = {nt[0], nt[1], nt[2]};
+            const T mag = nt[3];
             T nL[3] = {isL ? n[0] : -n[0], isL ? n[1] : -n[1], isL ? n[2] : -n[2]};
             T F[5];
             ok &= isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);

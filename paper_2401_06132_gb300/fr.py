@@ -69,6 +69,7 @@ def lib():
             "fr_last_error": ([], C.c_char_p),
             "fr_set_timing": ([vp, C.c_int], C.c_int),
             "fr_set_graph": ([vp, C.c_int], C.c_int),
+            "fr_autotune": ([vp, vp, vp, C.POINTER(C.c_int), C.c_int, vp], C.c_int),
             "fr_kernel_times": ([vp, C.POINTER(C.c_double), llp, C.c_int], C.c_int),
             "fr_probe_fma": ([dp, vp], C.c_int),
         }
@@ -203,6 +204,15 @@ class FRMesh:
             o = out[8 * i:8 * i + 8]
             res.append(dict(volume=o[0], Ek=o[1], eps=o[2], sums=o[3:8].copy()))
         return res
+
+    def autotune(self, U, R, stream=None):
+        """Pick the fastest volume-kernel launch shape per group on this state; returns the choices."""
+        self._check_tensor(U)
+        self._check_tensor(R)
+        out = (C.c_int * 16)(*([-1] * 16))
+        _check(lib().fr_autotune(self.h, C.c_void_p(U.data_ptr()), C.c_void_p(R.data_ptr()), out, 16,
+                                 _stream_ptr(stream)))
+        return [(64, 128, 256)[v] for v in out if v >= 0]
 
     def set_graph(self, on: bool):
         _check(lib().fr_set_graph(self.h, int(on)))

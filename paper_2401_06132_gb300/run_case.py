@@ -28,6 +28,7 @@ def main(argv=None):
     ap.add_argument("--rhs", type=int, default=3, help="RHS evaluations")
     ap.add_argument("--rk4", type=int, default=0, help="RK4 steps after the RHS evaluations")
     ap.add_argument("--mach", type=float, default=0.1)
+    ap.add_argument("--autotune", type=int, default=0, help="run the launch-shape autotuner first")
     args = ap.parse_args(argv)
 
     import numpy as np
@@ -47,6 +48,7 @@ def main(argv=None):
     U0 = W.tgv_state(m.sol_coords(), blocks, mach=args.mach, perturb=1e-3)
     U = torch.from_numpy(U0.astype(np.float64 if args.prec == "fp64" else np.float32)).cuda()
     R = torch.empty_like(U)
+    tuned = m.autotune(U, R) if args.autotune else None
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     ev[0].record()
     for _ in range(args.rhs):
@@ -54,7 +56,7 @@ def main(argv=None):
     ev[1].record()
     torch.cuda.synchronize()
     m.sync_status()
-    out = {"dof": int(U0.size), "rhs_ms": ev[0].elapsed_time(ev[1]) / max(1, args.rhs)}
+    out = {"dof": int(U0.size), "rhs_ms": ev[0].elapsed_time(ev[1]) / max(1, args.rhs), "volume_threads": tuned}
     if args.rk4:
         Um = torch.from_numpy(U0).cuda()
         ev[0].record()

@@ -348,3 +348,22 @@ def test_rk4_graph_replay_equals_eager_launches():
         torch.cuda.synchronize()
         res.append(Ud.cpu().numpy())
     assert np.array_equal(res[0], res[1])
+
+
+def test_autotuner_choice_does_not_change_results():
+    """Every launch shape of the volume kernel computes each output with the same operations: the
+    RHS after autotuning is bitwise the RHS before it (FP64 and FP32 low-Mach forms)."""
+    for prec in ("fp64", "fp32"):
+        mesh = W.box_hex_mesh(6)
+        o = O.Oracle(mesh, 3, 5)
+        U = W.tgv_state(o.sol_coords(), [(216, 64)], perturb=1e-2)
+        m = fr.FRMesh(mesh, fr.make_params(p=3, prec=prec, p_ref=W.tgv_p0(), rho_ref=1.0))
+        Ud = torch.from_numpy(U.astype(np.float64 if prec == "fp64" else np.float32)).cuda()
+        R0 = torch.empty_like(Ud)
+        m.rhs(Ud, R0)
+        picks = m.autotune(Ud, torch.empty_like(Ud))
+        assert len(picks) == 1 and picks[0] in (64, 128, 256)
+        R1 = torch.empty_like(Ud)
+        m.rhs(Ud, R1)
+        m.sync_status()
+        assert torch.equal(R0, R1)
