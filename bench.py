@@ -289,12 +289,11 @@ def run_ours(args, rank, world):
     ms_step = e0.elapsed_time(e1) / args.steps
     kt = m.kernel_times()
     m.sync_status()
+    from paper_2401_06132_gb300 import replicas
+    ms_step = replicas.max_over_ranks(ms_step, device="cuda")    # slowest replica
     if world > 1:
-        t = torch.tensor([ms_step], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
         torch.distributed.barrier()
-    value = dof * RHS_PER_STEP * world / (ms_step * 1e-3) / 1e9
+    value = replicas.replica_throughput(dof, RHS_PER_STEP, ms_step, world)
     # fused form: the RK4 stage update is folded into the last interface kernel of each RHS
     launches_per_step = RHS_PER_STEP * info["launches_per_rhs"]
 
