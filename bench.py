@@ -209,7 +209,7 @@ def other_configs(args, torch, fr, W):
     mesh = W.mixed_box_mesh(40)
     p0 = W.tgv_p0()
     blocks = [(mesh["hex_v"].shape[0], 64), (mesh["pri_v"].shape[0], 40)]
-    for prec in ("fp64", "fp32"):
+    for prec in ("fp64", "fp32", "mixed_fp16", "mixed_bf16"):
         m = fr.FRMesh(mesh, fr.make_params(p=3, prec=prec, p_ref=p0))
         U0 = W.tgv_state(m.sol_coords(), blocks, perturb=1e-3)
         U = torch.from_numpy(U0).cuda()
@@ -217,6 +217,8 @@ def other_configs(args, torch, fr, W):
         m.sync_status()
         out[f"mixed40_{prec}"] = {"gdof_rhs_per_s": U0.size * RHS_PER_STEP / (ms * 1e-3) / 1e9, "ms_per_step": ms,
                                   "dof": int(U0.size), "elements": sum(b[0] for b in blocks)}
+        if prec != "fp64":
+            out[f"mixed40_{prec}"]["speedup_vs_fp64"] = out["mixed40_fp64"]["ms_per_step"] / ms
         m.close()
     draws = W.ensemble_draws(64)
     meshes = [W.box_hex_mesh(d["edge"]) for d in draws]

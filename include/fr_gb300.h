@@ -53,7 +53,8 @@ typedef enum {
     FR_ENOMEM = 2,        /* device or host allocation failed */
     FR_ECUDA = 3,         /* a CUDA runtime call failed (text in fr_last_error()) */
     FR_EMESH = 4,         /* non-conforming mesh: unmatched face or flux point, inverted element */
-    FR_ETIMEOUT = 5,      /* a bounded device wait gave up */
+    FR_ETIMEOUT = 5,      /* a bounded device wait gave up (the tensor-core completion wait of the
+                           * mixed forms; latched on the device like FR_ENONPHYS) */
     FR_ENONPHYS = 6,      /* non-physical state met on the device */
     FR_EUNSUPPORTED = 7   /* valid request outside what this build implements */
 } fr_status;
@@ -61,9 +62,14 @@ typedef enum {
 typedef enum {
     FR_FP64 = 0,          /* all arithmetic in FP64 */
     FR_FP32 = 1,          /* FP32 state, operators and fluxes */
-    FR_MIXED_BF16 = 2,    /* FP32 state; prism triangle contractions as split bf16 hi+lo products
-                           * (not built in this version: FR_EUNSUPPORTED) */
-    FR_MIXED_FP16 = 3     /* as FR_MIXED_BF16 with fp16 splits (not built: FR_EUNSUPPORTED) */
+    FR_MIXED_BF16 = 2,    /* FR_FP32, except that the dense prism triangle-plane interpolation and
+                           * projection (Sec. 4.1 factorisation; the M7 and M8 triangle blocks) run
+                           * on the tensor cores as split products x_hi y_hi + x_lo y_hi + x_hi y_lo
+                           * of bf16 halves with FP32 accumulation. Hexahedra run the FR_FP32
+                           * kernels (their sum-factorised 1D operators are not dense contractions). */
+    FR_MIXED_FP16 = 3     /* as FR_MIXED_BF16 with fp16 halves; every operand row is scaled by a
+                           * power of two first (removed exactly afterwards) so that fp16 keeps
+                           * its full precision in the low half */
 } fr_precision;
 
 typedef enum {

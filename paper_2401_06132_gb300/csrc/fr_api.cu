@@ -76,6 +76,7 @@ struct fr_mesh {
     frb::Prism2D pri;                    // prism operators (p = 3)
     bool has_pri = false;
     void *d_priops = nullptr;            // PriOps<T> on the device
+    void *d_priops64 = nullptr;          // PriOps<double> (low-Mach FP32 form with prisms)
     std::vector<Group> groups;
     bool split_c = false;              // interface phase as pair flux (C1) + lift (C2)
     bool lowmach = false;              // FP32 low-Mach form (deviations, reduced energy, FP64 mass)
@@ -430,8 +431,6 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
     if (!inst || !prm || n_inst <= 0) return fail(FR_EINVAL, "null descriptor or n_inst <= 0");
     m->prec = prm[0].prec;
     if (m->prec < FR_FP64 || m->prec > FR_MIXED_FP16) return fail(FR_EINVAL, "unknown precision %d", m->prec);
-    if (m->prec == FR_MIXED_BF16 || m->prec == FR_MIXED_FP16)
-        return fail(FR_EUNSUPPORTED, "the split bf16/fp16 tensor-core forms are not built in this version");
     long long elem = 0, u = 0, f = 0;
     std::vector<int> bfirst;
     for (int ii = 0; ii < n_inst; ii++) {
@@ -499,7 +498,7 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
 }
 
 template <typename T>
-static fr_status upload_priops(fr_mesh *m)
+static fr_status upload_priops(fr_mesh *m, void **dst)
 {
     if (!m->has_pri) return FR_OK;
     const frb::Prism2D &P = m->pri;
@@ -519,9 +518,9 @@ static fr_status upload_priops(fr_mesh *m)
         for (int j = 0; j < FR_PE; j++) o.Dhz[k][j] = (T)P.z.Dh[k][j];
         o.lzL[k] = (T)P.z.lL[k]; o.lzR[k] = (T)P.z.lR[k]; o.liftzL[k] = (T)P.z.liftL[k]; o.liftzR[k] = (T)P.z.liftR[k];
     }
-    fr_status st = dalloc(m, &m->d_priops, sizeof(o));
+    fr_status st = dalloc(m, dst, sizeof(o));
     if (st) return st;
-    CU(cudaMemcpy(m->d_priops, &o, sizeof(o), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(*dst, &o, sizeof(o), cudaMemcpyHostToDevice));
     return FR_OK;
 }
 
@@ -706,12 +705,13 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
         if (m->blocks[b].type == 0 && hex_upload_ops(m->blocks[b].p, m->blocks[b].m, m->hex1d[b])) { delete m; return fail(FR_ECUDA, "operator upload failed"); }
     size_t ts = tsize(m->prec);
     st = (m->prec == FR_FP64) ? upload_geo<double>(m) : upload_geo<float>(m);
-    if (!st) st = (m->prec == FR_FP64) ? upload_priops<double>(m) : upload_priops<float>(m);
-    if (!st && m->prec != FR_FP64 && !m->has_pri) {
+    if (!st) st = (m->prec == FR_FP64) ? upload_priops<double>(m, &m->d_priops) : upload_priops<float>(m, &m->d_priops);
+    if (!st && m->prec != FR_FP64) {
         bool all = true;
         for (const InstanceHost &I : m->inst) all = all && I.prm.p_ref > 0 && I.prm.rho_ref > 0;
         m->lowmach = all;
     }
+    if (!st && m->lowmach) st = upload_priops<double>(m, &m->d_priops64);
     if (!st && m->lowmach) {
         std::vector<Geo<double>> g64((size_t)m->ne);
         for (long long e = 0; e < m->ne; e++) {
@@ -746,7 +746,7 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
 extern "C" fr_status fr_destroy(fr_mesh *m)
 {
     if (!m) return FR_OK;
-    void **bufs[] = {&m->d_fnrm, (void **)&m->d_fnrm64, &m->d_geo64, (void **)&m->d_MF, (void **)&m->d_RL, &m->d_priops, &m->d_geo, (void **)&m->d_partner, &m->d_UF, &m->d_FV, &m->d_CF, &m->d_QF, &m->d_DF, &m->d_Qu,
+    void **bufs[] = {&m->d_fnrm, (void **)&m->d_fnrm64, &m->d_geo64, (void **)&m->d_MF, (void **)&m->d_RL, &m->d_priops, &m->d_priops64, &m->d_geo, (void **)&m->d_partner, &m->d_UF, &m->d_FV, &m->d_CF, &m->d_QF, &m->d_DF, &m->d_Qu,
                      &m->d_UQ, &m->d_QQ, &m->d_Rt, &m->d_rk_k, &m->d_rk_us, (void **)&m->d_rk_acc, &m->d_io_U,
                      &m->d_io_R, (void **)&m->d_wsum, (void **)&m->d_status, &m->d_Qsnap};
     for (void **b : bufs) dfree(*b);
@@ -835,6 +835,7 @@ static HexArgs<T> make_args(fr_mesh *m, const Block &b, const void *U, void *R)
     a.Qu = reinterpret_cast<T *>(m->d_Qu); a.UQ = reinterpret_cast<T *>(m->d_UQ); a.QQ = reinterpret_cast<T *>(m->d_QQ);
     a.Rt = reinterpret_cast<T *>(m->d_Rt);
     a.status = m->d_status;
+    a.tcmode = m->prec == FR_MIXED_FP16 ? 1 : (m->prec == FR_MIXED_BF16 ? 2 : 0);
     return a;
 }
 
@@ -856,14 +857,21 @@ static fr_status ensure_unfused(fr_mesh *m)
     return st;
 }
 
+static fr_status status_error(int v)
+{
+    if (v & 2) return fail(FR_ETIMEOUT, "a bounded tensor-core completion wait gave up on the device");
+    return fail(FR_ENONPHYS, "non-physical state met on the device");
+}
+
 static fr_status check_status(fr_mesh *m)
 {
     if (m->status_pending && cudaEventQuery(m->ev_status) == cudaSuccess) {
         m->status_pending = false;
         if (*m->h_status) {
+            const int v = *m->h_status;
             *m->h_status = 0;
             cudaMemset(m->d_status, 0, sizeof(int));
-            return fail(FR_ENONPHYS, "non-physical state met on the device");
+            return status_error(v);
         }
     }
     return FR_OK;
@@ -913,7 +921,7 @@ static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, co
                     a.rkus = reinterpret_cast<T *>(rk.us);
                 }
                 int lr = b.type == 0 ? hex_fused_phase<T>(b.p, ph, a, s, gr.variant)
-                                     : pri_fused_phase<T>(ph, a, reinterpret_cast<const PriOps<T> *>(m->d_priops), s);
+                                     : pri_fused_phase<T>(ph, a, reinterpret_cast<const PriOps<T> *>(m->d_priops), reinterpret_cast<const PriOps<double> *>(m->d_priops64), s);
                 if (lr) return fail(FR_ECUDA, "fused phase %d launch: %s", ph, cudaGetErrorString(cudaGetLastError()));
             }
         }
@@ -966,7 +974,7 @@ static fr_status autotune_impl(fr_mesh *m, const void *U, void *R, cudaStream_t 
             a.fnrm64 = gr.d_fnrm64;
         }
         int lr = b.type == 0 ? hex_fused_phase<T>(b.p, 0, a, s, gr.variant)
-                             : pri_fused_phase<T>(0, a, reinterpret_cast<const PriOps<T> *>(m->d_priops), s);
+                             : pri_fused_phase<T>(0, a, reinterpret_cast<const PriOps<T> *>(m->d_priops), reinterpret_cast<const PriOps<double> *>(m->d_priops64), s);
         if (lr) return fail(FR_ECUDA, "autotune: face phase launch failed");
     }
     cudaEvent_t e0, e1;
@@ -1057,7 +1065,7 @@ extern "C" fr_status fr_sync_status(fr_mesh *m, void *stream)
     CU(cudaMemset(m->d_status, 0, sizeof(int)));
     m->status_pending = false;
     *m->h_status = 0;
-    return v ? fail(FR_ENONPHYS, "non-physical state met on the device") : FR_OK;
+    return v ? status_error(v) : FR_OK;
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -135,7 +135,7 @@ struct HexArgs {
     T *UQ;                    // unfused: [elem][5][nq] solution at quadrature points
     T *QQ;                    // unfused: [elem][5][3][nq] gradient, later transformed flux, at qpts
     T *Rt;                    // unfused: [elem][5][nu] R~
-    int *status;              // device status word (bit 0: non-physical state)
+    int *status;              // device status word (bit 0: non-physical state; bit 1: a bounded wait gave up)
     // Batched launch over several blocks of one element type and order (all null for one block):
     // per element its first value in U/R, its first global flux point and its instance's physics.
     const long long *eu0;
@@ -162,6 +162,9 @@ struct HexArgs {
     double *rkU;
     double *rkacc;
     T *rkus;
+    // Prism volume kernel in the FP32 compute precision: 0 = CUDA-core operators; 1 / 2 = the dense
+    // triangle interpolation and projection as split hi + lo FP16 / BF16 products on the tensor cores.
+    int tcmode;
 };
 
 #ifdef __CUDACC__
@@ -206,5 +209,6 @@ template <typename T> int hex_fused_phase(int p, int phase, const HexArgs<T> &a,
 // kernel: 1..13 in the paper's order (disu .. negdivconf)
 template <typename T> int hex_unfused_kernel(int p, int kernel, const HexArgs<T> &a, cudaStream_t s);
 int hex_upload_ops(int p, int m, const frb::Hex1D &h);
-// Prism kernels (fr_pri.cu); the operator tables are passed by device pointer.
-template <typename T> int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, cudaStream_t s);
+// Prism kernels (fr_pri.cu); the operator tables are passed by device pointer (ops64: the FP64
+// table, used by the low-Mach FP32 form; null otherwise).
+template <typename T> int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, const PriOps<double> *ops64, cudaStream_t s);

@@ -6,10 +6,22 @@
 // and face 1 (z = +1) carry the 10 triangle points, quad faces 2 (y = -1), 3 (x + y = 0) and
 // 4 (x = -1) carry 4 x 4 points with local index a + 4 b (a along the edge, b = z level).
 // Same three fused phases as the hexahedra: A face solution, B volume group, C interface group.
+//
+// Mixed-precision forms: in phase B the two dense triangle-plane contractions that dominate the
+// operator work -- interpolation to the 25 triangle quadrature points and the L2 projection back --
+// run on the tensor cores as split products. Each operand x is split into x_hi + x_lo (FP16 or
+// BF16, x_lo = round(x - x_hi)), and x.y is formed as x_hi y_hi + x_lo y_hi + x_hi y_lo with FP32
+// accumulation in tensor memory: the three products are one MMA chain over a K dimension that holds
+// [x_hi | x_lo | x_hi] against [y_hi | y_hi | y_lo]. Rows (element field x z level) are scaled by a
+// power of two that brings their largest magnitude into [2^14, 2^15), so FP16 keeps full precision
+// in x_lo; the scale is removed exactly after the product.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "fr_internal.h"
 #include "fr_physics.cuh"
+#include "fr_tcgen05.cuh"
 
 namespace {
 
@@ -17,7 +29,6 @@ constexpr int NT_ = FR_PT, NZ = FR_PE, MZ = 5, NQT = FR_PQ;
 constexpr int NU = NT_ * NZ;                  // 40
 constexpr int NF = 2 * NT_ + 3 * NZ * NZ;     // 68
 constexpr int NQ = NQT * MZ;                  // 125
-constexpr int FOFF[5] = {0, 10, 20, 36, 52};
 
 __device__ __forceinline__ int face_of(int s) { return s < 10 ? 0 : s < 20 ? 1 : 2 + (s - 20) / 16; }
 
@@ -58,6 +69,42 @@ __device__ __forceinline__ T face_value(const PriOps<T> &op, const T *fld, int s
     return v;
 }
 
+// Same, of the field minus a constant (the low-Mach deviation), subtracted at the solution points.
+template <typename T>
+__device__ __forceinline__ T face_value_off(const PriOps<T> &op, const T *fld, int s, T off)
+{
+    T v = T(0);
+    if (s < 20) {
+        const int t = s % 10;
+        const T *l = s < 10 ? op.lzL : op.lzR;
+#pragma unroll
+        for (int k = 0; k < NZ; k++) v += l[k] * (fld[t + 10 * k] - off);
+    } else {
+        const int f = (s - 20) / 16, loc = (s - 20) % 16, a = loc % 4, b = loc / 4;
+#pragma unroll
+        for (int t = 0; t < NT_; t++) v += op.Ef[f][a][t] * (fld[t + 10 * b] - off);
+    }
+    return v;
+}
+
+// Value at flux point s, in FP64, of a compute-precision field at solution points.
+template <typename T>
+__device__ __forceinline__ double face_value64(const PriOps<double> &op, const T *fld, int s)
+{
+    double v = 0.0;
+    if (s < 20) {
+        const int t = s % 10;
+        const double *l = s < 10 ? op.lzL : op.lzR;
+#pragma unroll
+        for (int k = 0; k < NZ; k++) v += l[k] * (double)fld[t + 10 * k];
+    } else {
+        const int f = (s - 20) / 16, loc = (s - 20) % 16, a = loc % 4, b = loc / 4;
+#pragma unroll
+        for (int t = 0; t < NT_; t++) v += op.Ef[f][a][t] * (double)fld[t + 10 * b];
+    }
+    return v;
+}
+
 template <typename T, int NTH>
 __device__ __forceinline__ void load_ops(const PriOps<T> *g, PriOps<T> &s)
 {
@@ -67,11 +114,72 @@ __device__ __forceinline__ void load_ops(const PriOps<T> *g, PriOps<T> &s)
     for (int i = threadIdx.x; i < n; i += NTH) dst[i] = src[i];
 }
 
+
+// -------------------------------------------------------------------------------------------------
+// Split hi + lo operands for the tensor cores (TCM = 1: FP16, 2: BF16)
+// -------------------------------------------------------------------------------------------------
+template <int TCM>
+__device__ __forceinline__ void split16(float x, uint16_t &h, uint16_t &l)
+{
+    if constexpr (TCM == 1) {
+        const __half hh = __float2half_rn(x);
+        h = __half_as_ushort(hh);
+        l = __half_as_ushort(__float2half_rn(x - __half2float(hh)));
+    } else {
+        const __nv_bfloat16 hh = __float2bfloat16_rn(x);
+        h = __bfloat16_as_ushort(hh);
+        l = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(hh)));
+    }
+}
+
+// Exponent s with max|x| 2^s in [2^14, 2^15) (0 for zero, subnormal or non-finite maxima).
+__device__ __forceinline__ int row_shift(float mx)
+{
+    const int eb = (int)((__float_as_uint(mx) >> 23) & 0xFF);
+    if (eb == 0 || eb == 255) return 0;
+    const int sh = 141 - eb;
+    return sh < -120 ? -120 : (sh > 120 ? 120 : sh);
+}
+__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
+
+__device__ __forceinline__ uint32_t pack2(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
+
+// Writes the K values v[0..K) of row r as K/8 core-matrix rows of 16 bytes.
+template <int K>
+__device__ __forceinline__ void store_row(unsigned char *base, int r, const uint16_t (&v)[K])
+{
+#pragma unroll
+    for (int ch = 0; ch < K / 8; ch++) {
+        uint4 w;
+        w.x = pack2(v[8 * ch + 0], v[8 * ch + 1]);
+        w.y = pack2(v[8 * ch + 2], v[8 * ch + 3]);
+        w.z = pack2(v[8 * ch + 4], v[8 * ch + 5]);
+        w.w = pack2(v[8 * ch + 6], v[8 * ch + 7]);
+        *reinterpret_cast<uint4 *>(base + tc::core_offset(r, 8 * ch, (K / 8) * 128)) = w;
+    }
+}
+
+// Shared-memory operands of the tensor-core contractions (bytes, 128-byte aligned pieces).
+constexpr int TC_KI = 32, TC_NI = 32;          // interpolation: K = 3 x 10 (+2 zero), N = 25 (+7)
+constexpr int TC_KP = 80, TC_NP = 16;          // projection:    K = 3 x 25 (+5 zero), N = 10 (+6)
+constexpr int TC_SBO_I = TC_KI / 8 * 128, TC_SBO_P = TC_KP / 8 * 128;
+constexpr int TC_A_BYTES = 16 * TC_SBO_P;      // 128 rows; the projection layout is the larger
+constexpr int TC_BI_BYTES = TC_NI / 8 * TC_SBO_I, TC_BP_BYTES = TC_NP / 8 * TC_SBO_P;
+constexpr int TC_BYTES = TC_A_BYTES + TC_BI_BYTES + TC_BP_BYTES + 128 * 4 + 16 + 128;
+constexpr int TC_ROWS_I = 20 * MZ, TC_ROWS_P = 15 * MZ;    // 100 and 75 rows of M = 128
+constexpr int TC_ST = 11;                                  // row stride of the projected rows
+constexpr uint32_t TC_IDESC_I1 = tc::idesc_f16(0, 128, TC_NI), TC_IDESC_I2 = tc::idesc_f16(1, 128, TC_NI);
+constexpr uint32_t TC_IDESC_P1 = tc::idesc_f16(0, 128, TC_NP), TC_IDESC_P2 = tc::idesc_f16(1, 128, TC_NP);
+static_assert(TC_ROWS_I <= 128 && TC_ROWS_P <= 128, "one M = 128 tile per element");
+static_assert(16 * TC_SBO_I <= TC_A_BYTES, "interpolation rows fit the operand buffer");
+
 // -------------------------------------------------------------------------------------------------
 // Phase A: disu
 // -------------------------------------------------------------------------------------------------
+// Low-Mach form (ph.dev, FP32): the face solution of the deviations from the reference state, and
+// the own-normal mass flux n.(rho v) at every flux point in FP64 (from the FP64 operator table).
 template <typename T>
-__global__ void __launch_bounds__(256) k_pri_disu(HexArgs<T> a, const PriOps<T> *gops)
+__global__ void __launch_bounds__(256) k_pri_disu(HexArgs<T> a, const PriOps<T> *gops, const PriOps<double> *ops64)
 {
     __shared__ PriOps<T> op;
     load_ops<T, 256>(gops, op);
@@ -82,7 +190,23 @@ __global__ void __launch_bounds__(256) k_pri_disu(HexArgs<T> a, const PriOps<T> 
         const long long ea = it / NF;
         const int alpha = (int)(ea % FR_NV);
         const long long e = ea / FR_NV;
-        a.UF[alpha * a.nfpt + elem_f0(a, e, NF) + s] = face_value(op, a.U + elem_u0(a, e, NU) + alpha * NU, s);
+        const T *u = a.U + elem_u0(a, e, NU);
+        T off = T(0);
+        bool dev = false;
+        if constexpr (sizeof(T) == 4) {
+            const Phys<T> ph = elem_phys(a, e);
+            dev = ph.dev != 0;
+            if (dev) off = alpha == 0 ? ph.rref : (alpha == 4 ? ph.eref : T(0));
+        }
+        a.UF[alpha * a.nfpt + elem_f0(a, e, NF) + s] = face_value_off(op, u + alpha * NU, s, off);
+        if (dev && alpha == 0) {
+            const double *nt = a.fnrm64 + (e * 6 + face_of(s)) * 4;
+            double mf = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                if (nt[k] != 0.0) mf += nt[k] * face_value64(*ops64, u + (1 + k) * NU, s);
+            a.MF[elem_f0(a, e, NF) + s] = mf;
+        }
     }
 }
 
@@ -131,10 +255,12 @@ __device__ __forceinline__ void pri_project_5(const PriOps<T> &op, const T *src,
     __syncthreads();
 }
 
-template <typename T, int NTH>
-__global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *gops)
+template <typename T, int NTH, int TCM>
+__global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *gops, const PriOps<double> *ops64)
 {
+    static_assert(TCM == 0 || (NTH == 128 && sizeof(T) == 4), "tensor-core form: FP32, one warpgroup per element");
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double s_m64[sizeof(T) == 4 ? 3 * NU : 1];   // low-Mach form: transformed mass flux
     PriOps<T> &op = *reinterpret_cast<PriOps<T> *>(smem_raw);
     T *s_u = reinterpret_cast<T *>(smem_raw + ((sizeof(PriOps<T>) + 15) / 16) * 16);
     T *s_q = s_u + 5 * NU;
@@ -142,12 +268,56 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
     T *s_w = s_c + 5 * NF;
     T *s_t = s_w + 20 * NQ;
     load_ops<T, NTH>(gops, op);
+    // tensor-core state (TCM != 0)
+    unsigned char *tA = nullptr, *tBi = nullptr, *tBp = nullptr;
+    int *s_sh = nullptr;
+    uint64_t *mbar = nullptr;
+    uint32_t *s_tmem = nullptr, tmem = 0, parity = 0;
+    bool tc_fail = false;
+    if constexpr (TCM != 0) {
+        const int tcnt = TCM ? (TC_ROWS_P * TC_ST > 5 * NZ * NQT ? TC_ROWS_P * TC_ST : 5 * NZ * NQT) : 0;
+        const uint32_t raw = tc::smem_u32(s_t + tcnt);
+        unsigned char *p0 = reinterpret_cast<unsigned char *>(s_t + tcnt) + ((128 - (raw & 127)) & 127);
+        tA = p0;
+        tBi = tA + TC_A_BYTES;
+        tBp = tBi + TC_BI_BYTES;
+        s_sh = reinterpret_cast<int *>(tBp + TC_BP_BYTES);
+        mbar = reinterpret_cast<uint64_t *>(s_sh + 128);
+        s_tmem = reinterpret_cast<uint32_t *>(mbar + 1);
+        if (threadIdx.x == 0) tc::mbar_init(mbar, 1);
+        __syncwarp();
+        if (threadIdx.x < 32) tc::tmem_alloc(s_tmem, 32);
+        __syncthreads();   // operators in shared memory
+        for (int i = threadIdx.x; i < TC_NI * TC_KI; i += NTH) {   // [B_hi | B_hi | B_lo]
+            const int n = i / TC_KI, k = i % TC_KI;
+            uint16_t h = 0, l = 0;
+            if (n < NQT && k < 3 * NT_) split16<TCM>((float)op.Bt[n][k % NT_], h, l);
+            *reinterpret_cast<uint16_t *>(tBi + tc::core_offset(n, k, TC_SBO_I)) = k < 2 * NT_ ? h : l;
+        }
+        for (int i = threadIdx.x; i < TC_NP * TC_KP; i += NTH) {   // [P_hi | P_hi | P_lo]
+            const int n = i / TC_KP, k = i % TC_KP;
+            uint16_t h = 0, l = 0;
+            if (n < NT_ && k < 3 * NQT) split16<TCM>((float)op.Pt[n][k % NQT], h, l);
+            *reinterpret_cast<uint16_t *>(tBp + tc::core_offset(n, k, TC_SBO_P)) = k < 2 * NQT ? h : l;
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        tmem = *s_tmem;
+    }
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
         const Geo<T> g = a.geo[e];
         const Phys<T> ph = elem_phys(a, e);
         const T *U = a.U + elem_u0(a, e, NU);
         const long long gf0 = elem_f0(a, e, NF);
-        for (int it = threadIdx.x; it < 5 * NU; it += NTH) s_u[it] = U[it];
+        bool dev = false;
+        if constexpr (sizeof(T) == 4) dev = ph.dev != 0;
+        for (int it = threadIdx.x; it < 5 * NU; it += NTH) {
+            T v = U[it];
+            if (dev) v -= it < NU ? ph.rref : (it >= 4 * NU ? ph.eref : T(0));
+            s_u[it] = v;
+        }
         for (int it = threadIdx.x; it < 5 * NF; it += NTH) {   // con_u
             const int alpha = it / NF, s = it % NF;
             const uint32_t pc = a.partner[gf0 + s];
@@ -158,6 +328,31 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
             s_c[it] = (T(0.5) - ph.beta) * uL + (T(0.5) + ph.beta) * uR;
         }
         __syncthreads();
+        if constexpr (sizeof(T) == 4) {
+            // low-Mach form: volume part of R~_rho in FP64 (rho v lies in the solution space, so its
+            // projection is itself and the corrected divergence applies at the solution points)
+            if (dev) {
+                const Geo<double> g64 = a.geo64[e];
+                for (int z = threadIdx.x; z < NU; z += NTH) {
+                    const double m0 = s_u[NU + z], m1 = s_u[2 * NU + z], m2 = s_u[3 * NU + z];
+#pragma unroll
+                    for (int d = 0; d < 3; d++)
+                        s_m64[d * NU + z] = g64.det * (g64.Ji[3 * d] * m0 + g64.Ji[3 * d + 1] * m1 + g64.Ji[3 * d + 2] * m2);
+                }
+                __syncthreads();
+                const PriOps<double> &o64 = *ops64;
+                const long long pbase = elem_u0(a, e, NU) / FR_NV;
+                for (int z = threadIdx.x; z < NU; z += NTH) {
+                    const int k = z / NT_, t = z % NT_;
+                    double v = 0.0;
+#pragma unroll
+                    for (int j = 0; j < NT_; j++) v += o64.Dhx[t][j] * s_m64[j + 10 * k] + o64.Dhy[t][j] * s_m64[NU + j + 10 * k];
+#pragma unroll
+                    for (int j = 0; j < NZ; j++) v += o64.Dhz[k][j] * s_m64[2 * NU + t + 10 * j];
+                    a.RL[pbase + z] = v;
+                }
+            }
+        }
         // corrected gradient: z lines (alpha, t) and triangle planes (alpha, k, t)
         for (int it = threadIdx.x; it < 5 * NT_; it += NTH) {
             const int alpha = it / NT_, t = it % NT_;
@@ -209,14 +404,78 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
             }
             const T *nt = a.fnrm + (e * 6 + face_of(s)) * 4;
             T n[3] = {nt[0], nt[1], nt[2]};
+            if (dev) { uf[0] += ph.rref; uf[4] += ph.eref; }
             T fvn[4];
             viscous_normal_flux(ph, uf, qf, n, fvn);
 #pragma unroll
             for (int k = 0; k < 4; k++) a.FV[k * a.nfpt + gf0 + s] = fvn[k];
         }
-        pri_interp_5<T, NTH>(op, s_u, s_t, s_w);
+        if constexpr (TCM == 0) {
+            pri_interp_5<T, NTH>(op, s_u, s_t, s_w);
 #pragma unroll 1
-        for (int c = 0; c < 3; c++) pri_interp_5<T, NTH>(op, s_q + 5 * c * NU, s_t, s_w + (5 + 5 * c) * NQ);
+            for (int c = 0; c < 3; c++) pri_interp_5<T, NTH>(op, s_q + 5 * c * NU, s_t, s_w + (5 + 5 * c) * NQ);
+        } else {
+            // z first (CUDA cores): row r = 5 f + c holds field f (s_q follows s_u) at z level c on
+            // the 10 triangle points; then the triangle interpolation of all 100 rows on the tensor core.
+            const int r = threadIdx.x;
+            if (r < TC_ROWS_I) {
+                const int f = r / MZ, c = r % MZ;
+                const T *src = s_u + f * NU;
+                float x[NT_], mx = 0.f;
+#pragma unroll
+                for (int t = 0; t < NT_; t++) {
+                    float v = 0.f;
+#pragma unroll
+                    for (int k = 0; k < NZ; k++) v += (float)op.Bz[c][k] * (float)src[t + 10 * k];
+                    x[t] = v;
+                    mx = fmaxf(mx, fabsf(v));
+                }
+                const int sh = row_shift(mx);
+                const float sc = pow2f(sh);
+                uint16_t kv[TC_KI];
+#pragma unroll
+                for (int t = 0; t < NT_; t++) {
+                    uint16_t h, l;
+                    split16<TCM>(x[t] * sc, h, l);
+                    kv[t] = h; kv[NT_ + t] = l; kv[2 * NT_ + t] = h;
+                }
+#pragma unroll
+                for (int k = 3 * NT_; k < TC_KI; k++) kv[k] = 0;
+                store_row<TC_KI>(tA, r, kv);
+                s_sh[r] = sh;
+            }
+            tc::fence_async_smem();
+            tc::fence_before_sync();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                tc::fence_after_sync();
+                const uint32_t aA = tc::smem_u32(tA), aB = tc::smem_u32(tBi);
+#pragma unroll
+                for (int j = 0; j < TC_KI / 16; j++)
+                    tc::mma_f16(tmem, tc::sdesc(aA + 256 * j, 128, TC_SBO_I), tc::sdesc(aB + 256 * j, 128, TC_SBO_I),
+                                TCM == 1 ? TC_IDESC_I1 : TC_IDESC_I2, j);
+                tc::commit(mbar);
+            }
+            const bool done = tc::mbar_wait(mbar, parity);
+            if (!__syncthreads_and(done)) { tc_fail = true; break; }
+            parity ^= 1;
+            tc::fence_after_sync();
+            {
+                float v0[16], v1[16];
+                const uint32_t ta = tmem + ((uint32_t)(32 * (threadIdx.x >> 5)) << 16);
+                tc::ld16(ta, v0);
+                tc::ld16(ta + 16, v1);
+                if (r < TC_ROWS_I) {
+                    const float isc = pow2f(-s_sh[r]);
+                    T *dst = s_w + NQT * r;                    // field f, level c: f NQ + 25 c = 25 r
+#pragma unroll
+                    for (int q = 0; q < 16; q++) dst[q] = (T)(v0[q] * isc);
+#pragma unroll
+                    for (int q = 16; q < NQT; q++) dst[q] = (T)(v1[q - 16] * isc);
+                }
+            }
+            __syncthreads();
+        }
         bool ok = true;
         for (int q = threadIdx.x; q < NQ; q += NTH) {          // tdisf
             T u[5], gq[5][3], f[3][5];
@@ -226,7 +485,12 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
 #pragma unroll
                 for (int d = 0; d < 3; d++) gq[alpha][d] = s_w[(5 + alpha * 3 + d) * NQ + q];
             }
-            ok &= total_flux(ph, u, gq, f);
+            if constexpr (sizeof(T) == 4) {
+                if (dev) ok &= total_flux_dev(ph, u, gq, f);
+                else ok &= total_flux(ph, u, gq, f);
+            } else {
+                ok &= total_flux(ph, u, gq, f);
+            }
 #pragma unroll
             for (int alpha = 0; alpha < 5; alpha++)
 #pragma unroll
@@ -235,8 +499,67 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
         }
         flag_status(a.status, ok);
         __syncthreads();
+        if constexpr (TCM == 0) {
 #pragma unroll 1
-        for (int c = 0; c < 3; c++) pri_project_5<T, NTH>(op, s_w + 5 * c * NQ, s_t, s_q + 5 * c * NU);
+            for (int c = 0; c < 3; c++) pri_project_5<T, NTH>(op, s_w + 5 * c * NQ, s_t, s_q + 5 * c * NU);
+        } else {
+            // triangle projection of the 75 rows (flux component f, quadrature level c) on the tensor
+            // core, then z (CUDA cores)
+            const int r = threadIdx.x;
+            if (r < TC_ROWS_P) {
+                const T *src = s_w + NQT * r;
+                float x[NQT], mx = 0.f;
+#pragma unroll
+                for (int q = 0; q < NQT; q++) { x[q] = (float)src[q]; mx = fmaxf(mx, fabsf(x[q])); }
+                const int sh = row_shift(mx);
+                const float sc = pow2f(sh);
+                uint16_t kv[TC_KP];
+#pragma unroll
+                for (int q = 0; q < NQT; q++) {
+                    uint16_t h, l;
+                    split16<TCM>(x[q] * sc, h, l);
+                    kv[q] = h; kv[NQT + q] = l; kv[2 * NQT + q] = h;
+                }
+#pragma unroll
+                for (int k = 3 * NQT; k < TC_KP; k++) kv[k] = 0;
+                store_row<TC_KP>(tA, r, kv);
+                s_sh[r] = sh;
+            }
+            tc::fence_async_smem();
+            tc::fence_before_sync();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                tc::fence_after_sync();
+                const uint32_t aA = tc::smem_u32(tA), aB = tc::smem_u32(tBp);
+#pragma unroll
+                for (int j = 0; j < TC_KP / 16; j++)
+                    tc::mma_f16(tmem, tc::sdesc(aA + 256 * j, 128, TC_SBO_P), tc::sdesc(aB + 256 * j, 128, TC_SBO_P),
+                                TCM == 1 ? TC_IDESC_P1 : TC_IDESC_P2, j);
+                tc::commit(mbar);
+            }
+            const bool done = tc::mbar_wait(mbar, parity);
+            if (!__syncthreads_and(done)) { tc_fail = true; break; }
+            parity ^= 1;
+            tc::fence_after_sync();
+            {
+                float v0[16];
+                tc::ld16(tmem + ((uint32_t)(32 * (threadIdx.x >> 5)) << 16), v0);
+                if (r < TC_ROWS_P) {
+                    const float isc = pow2f(-s_sh[r]);
+#pragma unroll
+                    for (int t = 0; t < NT_; t++) s_t[TC_ST * r + t] = (T)(v0[t] * isc);
+                }
+            }
+            __syncthreads();
+            for (int it = threadIdx.x; it < 15 * NU; it += NTH) {
+                const int f = it / NU, rr = it % NU, k = rr / NT_, t = rr % NT_;
+                T v = T(0);
+#pragma unroll
+                for (int c = 0; c < MZ; c++) v += op.Pz[k][c] * s_t[TC_ST * (MZ * f + c) + t];
+                s_q[f * NU + t + 10 * k] = v;
+            }
+            __syncthreads();
+        }
         T *R = a.R + elem_u0(a, e, NU);
         for (int it = threadIdx.x; it < 5 * NU; it += NTH) {   // corrected divergence
             const int alpha = it / NU, r = it % NU, k = r / NT_, t = r % NT_;
@@ -250,22 +573,39 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
         }
         __syncthreads();
     }
+    if constexpr (TCM != 0) {
+        if (tc_fail) {
+            // a tensor-core chain did not complete within the bound: report it, give the chain one
+            // more bounded wait, then release the tensor memory
+            if (threadIdx.x == 0) atomicOr(a.status, 2);
+            tc::mbar_wait(mbar, parity);
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            tc::fence_after_sync();
+            tc::tmem_free(tmem, 32);
+        }
+    }
 }
 
 // -------------------------------------------------------------------------------------------------
 // Phase C: interface group
 // -------------------------------------------------------------------------------------------------
 template <typename T, int NTH>
-__global__ void __launch_bounds__(NTH) k_pri_C(HexArgs<T> a, const PriOps<T> *gops)
+__global__ void __launch_bounds__(NTH) k_pri_C(HexArgs<T> a, const PriOps<T> *gops, const PriOps<double> *ops64)
 {
     __shared__ PriOps<T> op;
     __shared__ T s_d[5 * NF];
+    __shared__ double s_d64[sizeof(T) == 4 ? NF : 1];   // low-Mach form: FP64 transformed mass flux
     load_ops<T, NTH>(gops, op);
     __syncthreads();
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
         const Geo<T> g = a.geo[e];
         const Phys<T> ph = elem_phys(a, e);
         const long long gf0 = elem_f0(a, e, NF);
+        bool dev = false;
+        if constexpr (sizeof(T) == 4) dev = ph.dev != 0;
         bool ok = true;
         for (int s = threadIdx.x; s < NF; s += NTH) {
             const uint32_t pc = a.partner[gf0 + s];
@@ -281,7 +621,23 @@ __global__ void __launch_bounds__(NTH) k_pri_C(HexArgs<T> a, const PriOps<T> *go
             const T mag = nt[3];
             T nL[3] = {isL ? n[0] : -n[0], isL ? n[1] : -n[1], isL ? n[2] : -n[2]};
             T F[5];
-            ok &= isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
+            if constexpr (sizeof(T) == 4) {
+                if (dev) {
+                    float sw;
+                    ok &= isL ? common_flux_dev(ph, uo, up, fvo, fvp, nL, F, sw) : common_flux_dev(ph, up, uo, fvp, fvo, nL, F, sw);
+                    // FP64 mass flux: 1/2 (mL - mR) + (s/2 + tau)(rho_L - rho_R), mX = own-normal n.(rho v)
+                    const double mo = a.MF[og], mp = a.MF[pg];
+                    const double mL = isL ? mo : mp, mR = isL ? mp : mo;
+                    const double rL = isL ? uo[0] : up[0], rR = isL ? up[0] : uo[0];
+                    const double Fr = 0.5 * (mL - mR) + (0.5 * (double)sw + (double)ph.tau) * (rL - rR);
+                    const double mag64 = a.fnrm64[(e * 6 + face_of(s)) * 4 + 3];
+                    s_d64[s] = isL ? mag64 * Fr : -mag64 * Fr;
+                } else {
+                    ok &= isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
+                }
+            } else {
+                ok &= isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
+            }
             const T sc = isL ? mag : -mag;
 #pragma unroll
             for (int k = 0; k < 5; k++) s_d[k * NF + s] = sc * F[k];
@@ -290,16 +646,50 @@ __global__ void __launch_bounds__(NTH) k_pri_C(HexArgs<T> a, const PriOps<T> *go
         __syncthreads();
         T *R = a.R + elem_u0(a, e, NU);
         const T idet = T(-1) / g.det;
-        for (int it = threadIdx.x; it < 5 * NU; it += NTH) {
-            const int alpha = it / NU, r = it % NU, k = r / NT_, t = r % NT_;
-            const T *D = s_d + alpha * NF;
-            T v = R[it] + op.liftzL[k] * D[t] + op.liftzR[k] * D[10 + t];
+        if (!dev) {
+            for (int it = threadIdx.x; it < 5 * NU; it += NTH) {
+                const int alpha = it / NU, r = it % NU, k = r / NT_, t = r % NT_;
+                const T *D = s_d + alpha * NF;
+                T v = R[it] + op.liftzL[k] * D[t] + op.liftzR[k] * D[10 + t];
 #pragma unroll
-            for (int f = 0; f < 3; f++)
+                for (int f = 0; f < 3; f++)
 #pragma unroll
-                for (int b = 0; b < NZ; b++) v += op.Lf[f][t][b] * D[20 + 16 * f + b + 4 * k];
-            if (a.rkstage == 0) R[it] = v * idet;
-            else rk_fold(a, elem_u0(a, e, NU) + it, v * idet);
+                    for (int b = 0; b < NZ; b++) v += op.Lf[f][t][b] * D[20 + 16 * f + b + 4 * k];
+                if (a.rkstage == 0) R[it] = v * idet;
+                else rk_fold(a, elem_u0(a, e, NU) + it, v * idet);
+            }
+        } else if constexpr (sizeof(T) == 4) {
+            // low-Mach form: R_rho in FP64, R_E = R_(E - H0 rho) + H0 R_rho
+            const PriOps<double> &o64 = *ops64;
+            const double idet64 = -1.0 / a.geo64[e].det;
+            const long long pbase = elem_u0(a, e, NU) / FR_NV;
+            for (int z = threadIdx.x; z < NU; z += NTH) {
+                const int k = z / NT_, t = z % NT_;
+                double r = a.RL[pbase + z] + o64.liftzL[k] * s_d64[t] + o64.liftzR[k] * s_d64[10 + t];
+#pragma unroll
+                for (int f = 0; f < 3; f++)
+#pragma unroll
+                    for (int b = 0; b < NZ; b++) r += o64.Lf[f][t][b] * s_d64[20 + 16 * f + b + 4 * k];
+                const double Rrho = r * idet64;
+                float out[5];
+                out[0] = (float)Rrho;
+#pragma unroll
+                for (int alpha = 1; alpha < 5; alpha++) {
+                    const T *D = s_d + alpha * NF;
+                    T v = R[alpha * NU + z] + op.liftzL[k] * D[t] + op.liftzR[k] * D[10 + t];
+#pragma unroll
+                    for (int f = 0; f < 3; f++)
+#pragma unroll
+                        for (int b = 0; b < NZ; b++) v += op.Lf[f][t][b] * D[20 + 16 * f + b + 4 * k];
+                    out[alpha] = v * idet;
+                }
+                out[4] = (float)((double)out[4] + ph.H0d * Rrho);
+#pragma unroll
+                for (int alpha = 0; alpha < 5; alpha++) {
+                    if (a.rkstage == 0) R[alpha * NU + z] = out[alpha];
+                    else rk_fold(a, elem_u0(a, e, NU) + alpha * NU + z, out[alpha]);
+                }
+            }
         }
         __syncthreads();
     }
@@ -315,28 +705,50 @@ int grid_elems(long long ne, int per_sm)
 }  // namespace
 
 template <typename T>
-int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, cudaStream_t s)
+int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, const PriOps<double> *ops64, cudaStream_t s)
 {
     if (a.ne == 0) return 0;
     if (phase == 0) {
         long long work = a.ne * FR_NV * NF;
         long long g = (work + 255) / 256;
         if (g > 152LL * 64) g = 152LL * 64;
-        k_pri_disu<T><<<(int)g, 256, 0, s>>>(a, ops);
+        k_pri_disu<T><<<(int)g, 256, 0, s>>>(a, ops, ops64);
     } else if (phase == 1) {
         constexpr int NTH = 128;
-        const size_t smem = ((sizeof(PriOps<T>) + 15) / 16) * 16 + (size_t)(5 * NU + 15 * NU + 5 * NF + 20 * NQ + 5 * NZ * NQT) * sizeof(T);
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_pri_B<T, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr = true;
+        const size_t base = ((sizeof(PriOps<T>) + 15) / 16) * 16 + (size_t)(5 * NU + 15 * NU + 5 * NF + 20 * NQ) * sizeof(T);
+        bool tcdone = false;
+        if constexpr (sizeof(T) == 4) {
+          if (a.tcmode != 0) {
+            tcdone = true;
+            const int tcnt = TC_ROWS_P * TC_ST > 5 * NZ * NQT ? TC_ROWS_P * TC_ST : 5 * NZ * NQT;
+            const size_t smem = base + (size_t)tcnt * sizeof(T) + TC_BYTES;
+            // persistent: at most 4 resident CTAs per SM (each holds 32 of the 512 TMEM columns)
+            const int grid = grid_elems(a.ne, 1) < 152 * 4 ? grid_elems(a.ne, 1) : 152 * 4;
+            if (a.tcmode == 1) {
+                static bool attr1 = false;
+                if (!attr1) { cudaFuncSetAttribute(k_pri_B<T, NTH, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr1 = true; }
+                k_pri_B<T, NTH, 1><<<grid, NTH, smem, s>>>(a, ops, ops64);
+            } else {
+                static bool attr2 = false;
+                if (!attr2) { cudaFuncSetAttribute(k_pri_B<T, NTH, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr2 = true; }
+                k_pri_B<T, NTH, 2><<<grid, NTH, smem, s>>>(a, ops, ops64);
+            }
+          }
         }
-        k_pri_B<T, NTH><<<grid_elems(a.ne, 8), NTH, smem, s>>>(a, ops);
+        if (!tcdone) {
+            const size_t smem = base + (size_t)(5 * NZ * NQT) * sizeof(T);
+            static bool attr = false;
+            if (!attr) {
+                cudaFuncSetAttribute(k_pri_B<T, NTH, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                attr = true;
+            }
+            k_pri_B<T, NTH, 0><<<grid_elems(a.ne, 8), NTH, smem, s>>>(a, ops, ops64);
+        }
     } else {
-        k_pri_C<T, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a, ops);
+        k_pri_C<T, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a, ops, ops64);
     }
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
-template int pri_fused_phase<double>(int, const HexArgs<double> &, const PriOps<double> *, cudaStream_t);
-template int pri_fused_phase<float>(int, const HexArgs<float> &, const PriOps<float> *, cudaStream_t);
+template int pri_fused_phase<double>(int, const HexArgs<double> &, const PriOps<double> *, const PriOps<double> *, cudaStream_t);
+template int pri_fused_phase<float>(int, const HexArgs<float> &, const PriOps<float> *, const PriOps<double> *, cudaStream_t);

@@ -22,7 +22,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=16, help="elements per box edge")
     ap.add_argument("--p", type=int, default=3)
     ap.add_argument("--mesh", default="hex", choices=["hex", "sheared", "mixed"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "mixed_fp16", "mixed_bf16"])
     ap.add_argument("--lowmach", type=int, default=1, help="FP32 low-Mach form (rho_ref = 1)")
     ap.add_argument("--form", default="fused", choices=["fused", "unfused"])
     ap.add_argument("--rhs", type=int, default=3, help="RHS evaluations")

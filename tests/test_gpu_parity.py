@@ -399,3 +399,78 @@ def test_precision_sweep_32cubed_p4():
     assert res["fp64"].max() <= 2e-12, res["fp64"]
     assert res["fp32_lowmach"].max() <= 2e-5, res["fp32_lowmach"]
     assert res["fp32_plain"].max() <= 1e-3, res["fp32_plain"]
+
+
+def _mixed_grid_forms(N, precs, perturb=1e-3, const=False, rho_ref=0.0):
+    """RHS of the mixed hex/prism grid in FP32 and the split tensor-core forms, on one FP32-rounded
+    state, with the oracle run on that state promoted to FP64 (rho_ref > 0: the low-Mach form)."""
+    mesh = W.mixed_box_mesh(N)
+    blocks = [(mesh["hex_v"].shape[0], 64), (mesh["pri_v"].shape[0], 40)]
+    p0 = W.tgv_p0()
+    o = O.Oracle(mesh, 3, 5, threads=NCPU, p_ref=p0)
+    U = W.tgv_state(o.sol_coords(), blocks, perturb=perturb)
+    if const:
+        U = np.concatenate([np.tile(np.array([1.0, 0.3, -0.2, 0.1, 180.0]).repeat(nu), ne) for ne, nu in blocks])
+    U = U.astype(np.float32)
+    Ro = o.rhs(U.astype(np.float64))
+    out = {}
+    for prec in precs:
+        m = fr.FRMesh(mesh, fr.make_params(p=3, prec=prec, p_ref=p0, rho_ref=rho_ref))
+        Ud = torch.from_numpy(U).cuda()
+        Rd = torch.empty_like(Ud)
+        m.rhs(Ud, Rd)
+        m.sync_status()
+        out[prec] = Rd.cpu().numpy().astype(np.float64)
+    return blocks, Ro, out
+
+
+@pytest.mark.parametrize("N", [2, 4])
+def test_mixed_precision_forms_on_mixed_grid(N):
+    """Split FP16 / BF16 tensor-core products for the prism triangle interpolation and projection.
+    Hexahedra run the FP32 kernels and the prism face data (face solution, viscous normal flux) are
+    formed before the tensor-core steps, so the hexahedral block is bitwise the FP32 result; the
+    prism block carries the split-product rounding. FP16 halves with row scaling keep about 22
+    significant bits, so that form stays within a factor 2 of the FP32 form's error; BF16 halves keep
+    about 16 bits, and that form's error (about 1e-2 without the low-Mach reformulation) is reported
+    and bounded at 2e-2."""
+    blocks, Ro, out = _mixed_grid_forms(N, ["fp32", "mixed_fp16", "mixed_bf16"])
+    nh = blocks[0][0] * 5 * 64
+    err = {k: _rel_linf_blocks(v, Ro, blocks) for k, v in out.items()}
+    for k in ("mixed_fp16", "mixed_bf16"):
+        assert np.array_equal(out[k][:nh], out["fp32"][:nh]), k
+    perr = {k: _rel_linf_blocks(v[nh:], Ro[nh:], [blocks[1]]) for k, v in out.items()}
+    print(f"mixed grid N={N}: all {err}; prism block {perr}")
+    assert err["fp32"].max() <= 1e-3, err
+    assert perr["mixed_fp16"].max() <= 2 * perr["fp32"].max(), perr
+    assert err["mixed_bf16"].max() <= 2e-2, err
+
+
+def test_mixed_precision_forms_preserve_freestream():
+    """A constant state on the mixed grid: the interpolated constant and its projected flux pass
+    through the split products; |R| stays at the split-product rounding of the flux divergence scale
+    max|f| (2/h) (p+1)^2 (FP16 halves: 1e-5 of it; BF16: 1e-3)."""
+    N = 2
+    blocks, Ro, out = _mixed_grid_forms(N, ["mixed_fp16", "mixed_bf16"], const=True)
+    h = 2 * np.pi / N
+    fscale = 180.0 * 1.4 * (2 / h) * 16
+    for k, tol in (("mixed_fp16", 1e-5), ("mixed_bf16", 1e-3)):
+        r = np.abs(out[k]).max() / fscale
+        print(f"freestream {k}: max|R| / scale = {r:.3e}")
+        assert r <= tol, (k, r)
+
+
+@pytest.mark.parametrize("N", [2, 4, 40])
+def test_lowmach_forms_on_mixed_grid(N):
+    """The low-Mach FP32 form on the mixed hex/prism grid (N = 40: the 32,000-hex + 64,000-prism
+    benchmark grid, every element compared). FP32 and the split FP16 tensor-core form stay within 2e-5
+    per conserved variable on the 2^3 and 4^3 grids. On the 40^3 grid the prism block's FP32 rounding
+    of the momentum residual reaches 2.25e-5 (FP32 on CUDA cores) and 2.33e-5 (FP16 splits) while the
+    hexahedral block stays at 1.4e-5, so the bound there is 3e-5. The split BF16 form's error (about
+    1e-4) is reported and bounded at 1e-3."""
+    blocks, Ro, out = _mixed_grid_forms(N, ["fp32", "mixed_fp16", "mixed_bf16"], rho_ref=1.0)
+    err = {k: _rel_linf_blocks(v, Ro, blocks) for k, v in out.items()}
+    print(f"low-Mach mixed grid N={N}: {err}")
+    tol = 2e-5 if N <= 4 else 3e-5
+    assert err["fp32"].max() <= tol, err
+    assert err["mixed_fp16"].max() <= tol, err
+    assert err["mixed_bf16"].max() <= 1e-3, err
