@@ -210,7 +210,8 @@ def other_configs(args, torch, fr, W):
     p0 = W.tgv_p0()
     blocks = [(mesh["hex_v"].shape[0], 64), (mesh["pri_v"].shape[0], 40)]
     for prec in ("fp64", "fp32", "mixed_fp16", "mixed_bf16"):
-        m = fr.FRMesh(mesh, fr.make_params(p=3, prec=prec, p_ref=p0))
+        # reduced precisions in the low-Mach form (rho_ref = 1; FP64 ignores it)
+        m = fr.FRMesh(mesh, fr.make_params(p=3, prec=prec, p_ref=p0, rho_ref=1.0))
         U0 = W.tgv_state(m.sol_coords(), blocks, perturb=1e-3)
         U = torch.from_numpy(U0).cuda()
         ms = _time_steps(m, U, steps, 2, torch)
@@ -242,6 +243,8 @@ def other_configs(args, torch, fr, W):
         out[f"ensemble64_{prec}"] = {"gdof_rhs_per_s": U0.size * RHS_PER_STEP / (ms * 1e-3) / 1e9, "ms_per_step": ms,
                                      "dof": int(U0.size), "elements": int(info["elements"]),
                                      "launches_per_rhs": int(info["launches_per_rhs"])}
+        if prec != "fp64":
+            out[f"ensemble64_{prec}"]["speedup_vs_fp64"] = out["ensemble64_fp64"]["ms_per_step"] / ms
         m.close()
         del U
         torch.cuda.empty_cache()
@@ -322,7 +325,7 @@ def run_ours(args, rank, world):
     rhs_ms = ms_step / RHS_PER_STEP
     hbm_frac = compulsory / (rhs_ms * 1e-3) / 1e9 / hbm_peak
 
-    # --- other forms (same workload): FP64 unfused, FP32 fused / unfused ---------------------
+    # --- other forms (same workload): FP64 unfused, FP32 fused / unfused, mixed fused -----------
     forms = {"fused_fp64": value / world}
     ksteps = max(2, min(args.steps, 5))
     m.set_form("unfused")
@@ -342,6 +345,14 @@ def run_ours(args, rank, world):
     forms["unfused_fp32"] = dof * RHS_PER_STEP / (time_rk4(m32, U, ksteps, 1, torch) * 1e-3) / 1e9
     m32.close()
     del m32
+    # mixed forms with the hexahedral x-y plane contractions moved to the tensor cores as split
+    # FP16 / BF16 products (low-Mach form); without that switch a hex-only grid runs the FP32 kernels
+    for prec in ("mixed_fp16", "mixed_bf16"):
+        mm = fr.FRMesh(mesh, fr.make_params(p=P, prec=prec, p_ref=p0, rho_ref=1.0))
+        mm.set_hex_tensor_cores(True)
+        forms[f"fused_{prec}_hex_tensor_cores"] = dof * RHS_PER_STEP / (time_rk4(mm, U, ksteps, 2, torch) * 1e-3) / 1e9
+        mm.close()
+        del mm
     torch.cuda.empty_cache()
 
     # --- the other workloads: mixed hex/prism grid and the batched ensemble -----------------------

@@ -205,6 +205,14 @@ fr_status fr_set_debug(fr_mesh *m, int flags);
  * use plain launches. */
 fr_status fr_set_graph(fr_mesh *m, int on);
 
+/* Mixed forms only: on = 1 also moves the x-y factor of the hexahedral interpolation and
+ * projection (the dense Kronecker blocks B (x) B and Pj (x) Pj of the Sec. 4 factorisation) to the
+ * split-product tensor-core path used for the prisms. Default 0: the hexahedra keep the FP32 1D
+ * sweeps on the CUDA cores, which are faster on GB300 (the dense block costs more multiply-adds and
+ * shared memory than the sweeps save). Results then differ from FR_FP32 at the split-product
+ * rounding only. Takes effect at the next launch (and recaptures the RK4 graph). */
+fr_status fr_set_hex_tensor_cores(fr_mesh *m, int on);
+
 /* Per-kernel timing (on = 1): CUDA events are recorded on the launching stream around every later
  * launch. fr_kernel_times waits for them and returns, per kernel id, the summed milliseconds and the
  * launch count, then clears the record. Ids: 0, 1, 2 fused phases (face solution, volume group,

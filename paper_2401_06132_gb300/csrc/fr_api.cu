@@ -115,6 +115,7 @@ struct fr_mesh {
     double graph_dt = 0;
     cudaStream_t graph_stream = nullptr;
     int graph_form = -1;
+    int hex_tc = 0;                      // mixed forms: hexahedral plane contractions on the tensor cores
 };
 
 // Kernel ids for timing: 0..2 fused phases A, B, C; 10+k unfused kernel k (1..13); 30 RK4 update.
@@ -780,6 +781,13 @@ extern "C" fr_status fr_set_graph(fr_mesh *m, int on)
     return FR_OK;
 }
 
+extern "C" fr_status fr_set_hex_tensor_cores(fr_mesh *m, int on)
+{
+    if (!m) return fail(FR_EINVAL, "null handle");
+    m->hex_tc = on != 0;
+    return FR_OK;
+}
+
 extern "C" fr_status fr_set_timing(fr_mesh *m, int on)
 {
     if (!m) return fail(FR_EINVAL, "null handle");
@@ -836,6 +844,7 @@ static HexArgs<T> make_args(fr_mesh *m, const Block &b, const void *U, void *R)
     a.Rt = reinterpret_cast<T *>(m->d_Rt);
     a.status = m->d_status;
     a.tcmode = m->prec == FR_MIXED_FP16 ? 1 : (m->prec == FR_MIXED_BF16 ? 2 : 0);
+    if (b.type == 0 && !m->hex_tc) a.tcmode = 0;
     return a;
 }
 
@@ -1139,7 +1148,8 @@ static fr_status rk4_impl(fr_mesh *m, double *U, double dt, int nsteps, cudaStre
         return FR_OK;
     }
     int done = 0;
-    if (!m->graph || m->graph_U != U || m->graph_dt != dt || m->graph_stream != s || m->graph_form != m->form) {
+    const int gform = m->form + 2 * m->hex_tc;
+    if (!m->graph || m->graph_U != U || m->graph_dt != dt || m->graph_stream != s || m->graph_form != gform) {
         if (m->graph) { cudaGraphExecDestroy(m->graph); m->graph = nullptr; }
         // one eager step first: lazy workspace allocation and first-launch kernel attributes happen
         // outside the capture
@@ -1156,7 +1166,7 @@ static fr_status rk4_impl(fr_mesh *m, double *U, double dt, int nsteps, cudaStre
         ce = cudaGraphInstantiate(&m->graph, g, 0);
         cudaGraphDestroy(g);
         if (ce != cudaSuccess) { m->graph = nullptr; return fail(FR_ECUDA, "RK4 graph instantiate: %s", cudaGetErrorString(ce)); }
-        m->graph_U = U; m->graph_dt = dt; m->graph_stream = s; m->graph_form = m->form;
+        m->graph_U = U; m->graph_dt = dt; m->graph_stream = s; m->graph_form = gform;
     }
     for (int step = done; step < nsteps; step++) CU(cudaGraphLaunch(m->graph, s));
     return FR_OK;

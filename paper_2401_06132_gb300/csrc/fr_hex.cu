@@ -18,6 +18,7 @@
 
 #include "fr_internal.h"
 #include "fr_physics.cuh"
+#include "fr_tcgen05.cuh"
 
 __constant__ HexOps<double> c_hex64[3];  // slot p - 2
 __constant__ HexOps<float> c_hex32[3];
@@ -192,6 +193,69 @@ struct HexSmem {
     static constexpr int SIZE = 5 * FS + 15 * FS + 5 * NF + 20 * NQ + T1 + T2;
 };
 
+// Mixed forms (tcmode 1 = FP16, 2 = BF16 halves): the x-y factor of the interpolation, B (x) B
+// (M^2 x N^2), and of the projection, Pj (x) Pj (N^2 x M^2), are applied as dense blocks on the
+// tensor cores to all 20 (15) fields and all z quadrature levels of an element in one M = 128 MMA
+// chain each, as split products [x_hi | x_lo | x_hi] . [y_hi | y_hi | y_lo]; the z factor stays on
+// the CUDA cores. The dense block takes N M / (N + M) times the multiply-adds of two 1D sweeps (and
+// three for the split), paid on a unit with about 30 times the FP32 rate of the CUDA cores.
+template <int P>
+struct HexTc {
+    static constexpr int N = P + 1, M = P + 2, N2 = N * N, M2 = M * M;
+    static constexpr int RI = 20 * M, RP = 15 * M;                 // rows: field x z quadrature level
+    static constexpr int KI = (3 * N2 + 15) / 16 * 16, KP = (3 * M2 + 15) / 16 * 16;
+    static constexpr int NI = (M2 + 15) / 16 * 16, NP = (N2 + 15) / 16 * 16;
+    static constexpr int SBO_I = KI / 8 * 128, SBO_P = KP / 8 * 128;
+    static constexpr int A_I = (RI + 7) / 8 * SBO_I, A_P = (RP + 7) / 8 * SBO_P;
+    static constexpr int A_BYTES = ((A_I > A_P ? A_I : A_P) + 127) / 128 * 128;
+    static constexpr int BI_BYTES = NI / 8 * SBO_I, BP_BYTES = NP / 8 * SBO_P;
+    static constexpr int ST = N2 | 1;                               // odd row stride of staged rows
+    static constexpr int TT = (RI > RP ? RI : RP) * ST;             // staged rows (floats)
+    static constexpr int COLS = NI > 32 ? 64 : 32;                  // tensor-memory columns
+    static constexpr int HEAD = 128 + A_BYTES + BI_BYTES + BP_BYTES;  // before the kernel's arrays
+    static_assert(RI <= 128 && RP <= 128, "one M = 128 tile per element");
+};
+
+// Writes row r of an operand as [hi | lo | hi | 0 ...] (L values per segment, K values in all)
+// from packed pairs hl[i] = hi | lo << 16.
+template <int K, int L>
+__device__ __forceinline__ void store_split_row(unsigned char *base, int r, const uint32_t (&hl)[L])
+{
+    auto val = [&](int k) -> uint32_t {
+        if (k < L) return hl[k] & 0xFFFFu;
+        if (k < 2 * L) return hl[k - L] >> 16;
+        if (k < 3 * L) return hl[k - 2 * L] & 0xFFFFu;
+        return 0u;
+    };
+#pragma unroll
+    for (int ch = 0; ch < K / 8; ch++) {
+        uint4 w;
+        w.x = val(8 * ch + 0) | (val(8 * ch + 1) << 16);
+        w.y = val(8 * ch + 2) | (val(8 * ch + 3) << 16);
+        w.z = val(8 * ch + 4) | (val(8 * ch + 5) << 16);
+        w.w = val(8 * ch + 6) | (val(8 * ch + 7) << 16);
+        *reinterpret_cast<uint4 *>(base + tc::core_offset(r, 8 * ch, K / 8 * 128)) = w;
+    }
+}
+
+// Splits the L values x of one operand row (scaled by 2^sh) into packed hi/lo pairs.
+template <int TCM, int L>
+__device__ __forceinline__ int split_row(const float (&x)[L], uint32_t (&hl)[L])
+{
+    float mx = 0.f;
+#pragma unroll
+    for (int i = 0; i < L; i++) mx = fmaxf(mx, fabsf(x[i]));
+    const int sh = tc::row_shift(mx);
+    const float sc = tc::pow2f(sh);
+#pragma unroll
+    for (int i = 0; i < L; i++) {
+        uint16_t h, l;
+        tc::split16<TCM>(x[i] * sc, h, l);
+        hl[i] = (uint32_t)h | ((uint32_t)l << 16);
+    }
+    return sh;
+}
+
 // Sum-factorised interpolation of 5 fields (src, stride NU) to quadrature points (dst, stride NQ).
 template <typename T, int P, int NT, int XS = P + 1, int PS = (P + 1) * (P + 1), int FS = (P + 1) * (P + 1) * (P + 1)>
 __device__ __forceinline__ void interp_5(const HexOps<T> &op, const T *src, T *t1, T *t2, T *dst)
@@ -293,15 +357,28 @@ __device__ __forceinline__ void project_5(const HexOps<T> &op, const T *src, T *
     __syncthreads();
 }
 
-template <typename T, int P, int NT>
+template <typename T, int P, int NT, int TCM = 0>
 __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
 {
     using S = HexSmem<T, P>;
+    using TC = HexTc<P>;
+    static_assert(TCM == 0 || (NT == 128 && std::is_same<T, float>::value), "tensor-core form: FP32, one warpgroup");
     constexpr int N = S::N, M = S::M, NU = S::NU, NF = S::NF, NQ = S::NQ;
     constexpr int XS = S::XS, PS = S::PS, FS = S::FS;
     (void)M;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *s_u = reinterpret_cast<T *>(smem_raw);
+    // tensor-core form: operand tiles first (the MMA reads 128 rows of A; rows past the element's
+    // last run on into the following buffers and only feed unread accumulator lanes)
+    unsigned char *tA = nullptr, *tBi = nullptr, *tBp = nullptr;
+    unsigned char *arr = smem_raw;
+    if constexpr (TCM != 0) {
+        const uint32_t raw = tc::smem_u32(smem_raw);
+        tA = smem_raw + ((128 - (raw & 127)) & 127);
+        tBi = tA + TC::A_BYTES;
+        tBp = tBi + TC::BI_BYTES;
+        arr = smem_raw + TC::HEAD;
+    }
+    T *s_u = reinterpret_cast<T *>(arr);
     T *s_q = s_u + 5 * FS;
     T *s_c = s_q + 15 * FS;
     T *s_w = s_c + 5 * NF;
@@ -310,7 +387,40 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
     __shared__ short s_list[NF];
     __shared__ int s_cnt;
     __shared__ double s_m64[std::is_same<T, float>::value ? 3 * NU : 1];
+    __shared__ int s_sh[TCM ? 128 : 1];
+    __shared__ uint64_t s_mbar[1];
+    __shared__ uint32_t s_tmem[1];
     const HexOps<T> &op = OPS<T>(P - 2);
+    uint32_t tmem = 0, parity = 0;
+    bool tc_fail = false;
+    if constexpr (TCM != 0) {
+        tc::setup(s_mbar, s_tmem, TC::COLS);
+        // operator blocks [hi | hi | lo] from the FP64 1D operators
+        const HexOps<double> &o64 = OPS<double>(P - 2);
+        for (int i = threadIdx.x; i < TC::NI * TC::KI; i += NT) {
+            const int n = i / TC::KI, k = i % TC::KI;
+            uint16_t h = 0, l = 0;
+            if (n < TC::M2 && k < 3 * TC::N2) {
+                const int kk = k % TC::N2;
+                tc::split16<TCM>((float)(o64.B[n % M][kk % N] * o64.B[n / M][kk / N]), h, l);
+            }
+            *reinterpret_cast<uint16_t *>(tBi + tc::core_offset(n, k, TC::SBO_I)) = k < 2 * TC::N2 ? h : l;
+        }
+        for (int i = threadIdx.x; i < TC::NP * TC::KP; i += NT) {
+            const int n = i / TC::KP, k = i % TC::KP;
+            uint16_t h = 0, l = 0;
+            if (n < TC::N2 && k < 3 * TC::M2) {
+                const int kk = k % TC::M2;
+                tc::split16<TCM>((float)(o64.Pj[n % N][kk % M] * o64.Pj[n / N][kk / M]), h, l);
+            }
+            *reinterpret_cast<uint16_t *>(tBp + tc::core_offset(n, k, TC::SBO_P)) = k < 2 * TC::M2 ? h : l;
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        tmem = s_tmem[0];
+    }
 
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
         const Geo<T> g = a.geo[e];
@@ -455,9 +565,55 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
             }
         }
         // 6. uqpts + gradcoru_qpts: 20 fields to quadrature points, 5 at a time
-        interp_5<T, P, NT, XS, PS, FS>(op, s_u, s_t1, s_t2, s_w);
+        if constexpr (TCM == 0) {
+            interp_5<T, P, NT, XS, PS, FS>(op, s_u, s_t1, s_t2, s_w);
 #pragma unroll 1
-        for (int c = 0; c < 3; c++) interp_5<T, P, NT, XS, PS, FS>(op, s_q + 5 * c * FS, s_t1, s_t2, s_w + (5 + 5 * c) * NQ);
+            for (int c = 0; c < 3; c++) interp_5<T, P, NT, XS, PS, FS>(op, s_q + 5 * c * FS, s_t1, s_t2, s_w + (5 + 5 * c) * NQ);
+        } else {
+            // z factor on the CUDA cores: row r = f M + c holds field f (s_q follows s_u) at z
+            // quadrature level c on the N^2 in-plane points
+            T *s_tt = s_t1;
+            for (int it = threadIdx.x; it < TC::RI * TC::N2; it += NT) {
+                const int r = it / TC::N2, n = it % TC::N2, f = r / M, c = r % M;
+                const T *src = s_u + f * FS + n % N + XS * (n / N);
+                T v = T(0);
+#pragma unroll
+                for (int k = 0; k < N; k++) v += op.B[c][k] * src[PS * k];
+                s_tt[r * TC::ST + n] = v;
+            }
+            __syncthreads();
+            if (threadIdx.x < TC::RI) {
+                const int r = threadIdx.x;
+                float x[TC::N2];
+                uint32_t hl[TC::N2];
+#pragma unroll
+                for (int n = 0; n < TC::N2; n++) x[n] = s_tt[r * TC::ST + n];
+                s_sh[r] = split_row<TCM, TC::N2>(x, hl);
+                store_split_row<TC::KI, TC::N2>(tA, r, hl);
+            }
+            if (!tc::mma_chain<TC::KI / 16>(tmem, tA, TC::SBO_I, tBi, TC::SBO_I, tc::idesc_f16(TCM - 1, 128, TC::NI), s_mbar, parity)) {
+                tc_fail = true;
+                break;
+            }
+            {
+                const int r = threadIdx.x;
+                const uint32_t ta = tmem + ((uint32_t)(32 * (threadIdx.x >> 5)) << 16);
+                float v[TC::NI];
+#pragma unroll
+                for (int cb = 0; cb < TC::NI / 16; cb++) {
+                    float w[16];
+                    tc::ld16(ta + 16 * cb, w);
+#pragma unroll
+                    for (int q = 0; q < 16; q++) v[16 * cb + q] = w[q];
+                }
+                if (r < TC::RI) {
+                    const float isc = tc::pow2f(-s_sh[r]);
+#pragma unroll
+                    for (int q = 0; q < TC::M2; q++) s_w[TC::M2 * r + q] = v[q] * isc;   // f NQ + M^2 c = M^2 r
+                }
+            }
+            __syncthreads();
+        }
         // 7. tdisf: transformed flux at each quadrature point, in place
         bool ok = true;
         for (int q = threadIdx.x; q < NQ; q += NT) {
@@ -493,8 +649,53 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
         flag_status(a.status, ok);
         __syncthreads();
         // 8. tdivtpcorf, first factor: projection of the 15 transformed-flux fields (into s_q)
+        if constexpr (TCM == 0) {
 #pragma unroll 1
-        for (int c = 0; c < 3; c++) project_5<T, P, NT, XS, PS, FS>(op, s_w + 5 * c * NQ, s_t1, s_t2, s_q + 5 * c * FS);
+            for (int c = 0; c < 3; c++) project_5<T, P, NT, XS, PS, FS>(op, s_w + 5 * c * NQ, s_t1, s_t2, s_q + 5 * c * FS);
+        } else {
+            // x-y factor on the tensor cores: row r = f M + c holds flux component f at quadrature
+            // level c on the M^2 in-plane points; then the z factor on the CUDA cores
+            T *s_tt = s_t1;
+            if (threadIdx.x < TC::RP) {
+                const int r = threadIdx.x;
+                float x[TC::M2];
+                uint32_t hl[TC::M2];
+#pragma unroll
+                for (int q = 0; q < TC::M2; q++) x[q] = s_w[TC::M2 * r + q];
+                s_sh[r] = split_row<TCM, TC::M2>(x, hl);
+                store_split_row<TC::KP, TC::M2>(tA, r, hl);
+            }
+            if (!tc::mma_chain<TC::KP / 16>(tmem, tA, TC::SBO_P, tBp, TC::SBO_P, tc::idesc_f16(TCM - 1, 128, TC::NP), s_mbar, parity)) {
+                tc_fail = true;
+                break;
+            }
+            {
+                const int r = threadIdx.x;
+                const uint32_t ta = tmem + ((uint32_t)(32 * (threadIdx.x >> 5)) << 16);
+                float v[TC::NP];
+#pragma unroll
+                for (int cb = 0; cb < TC::NP / 16; cb++) {
+                    float w[16];
+                    tc::ld16(ta + 16 * cb, w);
+#pragma unroll
+                    for (int q = 0; q < 16; q++) v[16 * cb + q] = w[q];
+                }
+                if (r < TC::RP) {
+                    const float isc = tc::pow2f(-s_sh[r]);
+#pragma unroll
+                    for (int n = 0; n < TC::N2; n++) s_tt[r * TC::ST + n] = v[n] * isc;
+                }
+            }
+            __syncthreads();
+            for (int it = threadIdx.x; it < 15 * NU; it += NT) {
+                const int f = it / NU, z = it % NU, n = z % TC::N2, k = z / TC::N2;
+                T v = T(0);
+#pragma unroll
+                for (int c = 0; c < M; c++) v += op.Pj[k][c] * s_tt[(f * M + c) * TC::ST + n];
+                s_q[f * FS + n % N + XS * (n / N) + PS * k] = v;
+            }
+            __syncthreads();
+        }
         // 9. tdivtpcorf, second factor: R~ = sum_d Dh_d F~_d, written to R (finished in phase C)
         T *R = a.R + elem_u0(a, e, NU);
         for (int it = threadIdx.x; it < 5 * NU; it += NT) {
@@ -510,6 +711,11 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
             R[it] = v;
         }
         __syncthreads();
+    }
+    if constexpr (TCM != 0) {
+        // a chain that did not complete within the bound is reported; the tensor memory is released
+        if (tc_fail && threadIdx.x == 0) atomicOr(a.status, 2);
+        tc::teardown(s_mbar, parity, tc_fail, tmem, TC::COLS);
     }
 }
 
@@ -949,10 +1155,40 @@ static void launch_B(const HexArgs<T> &a, cudaStream_t s)
     k_fused_B<T, P, NT><<<grid_elems(a.ne, 8), NT, smem, s>>>(a);
 }
 
+// Tensor-core form of the volume kernel (FP32, 128 threads, persistent: at most as many CTAs as
+// fit on the SMs, each holding its tensor-memory columns for its lifetime).
+template <int P, int TCM>
+static int launch_B_tc(const HexArgs<float> &a, cudaStream_t s)
+{
+    using TC = HexTc<P>;
+    static_assert(16 * (TC::SBO_I > TC::SBO_P ? TC::SBO_I : TC::SBO_P) <=
+                      TC::A_BYTES + TC::BI_BYTES + TC::BP_BYTES + HexSmem<float, P>::SIZE * (int)sizeof(float),
+                  "the 128 rows an MMA reads stay inside the CTA's shared memory");
+    const size_t tt = (size_t)(TC::TT > HexSmem<float, P>::T1 + HexSmem<float, P>::T2 ? TC::TT - HexSmem<float, P>::T1 - HexSmem<float, P>::T2 : 0);
+    const size_t smem = TC::HEAD + (HexSmem<float, P>::SIZE + tt) * sizeof(float);
+    static int occ = -1;
+    if (occ < 0) {
+        // resident CTAs per SM from the kernel's shared memory and registers (232,448 B of shared
+        // memory and 64K registers per SM, 1 KB reserved per CTA); each CTA holds COLS of the 512
+        // tensor-memory columns, which bounds the count too
+        cudaFuncSetAttribute(k_fused_B<float, P, 128, TCM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncAttributes fa{};
+        if (cudaFuncGetAttributes(&fa, k_fused_B<float, P, 128, TCM>) != cudaSuccess) return -1;
+        const int by_smem = (int)(232448 / (smem + fa.sharedSizeBytes + 1024));
+        const int by_regs = 65536 / (((fa.numRegs + 7) / 8 * 8) * 128);
+        int o = by_smem < by_regs ? by_smem : by_regs;
+        if (o > 512 / TC::COLS) o = 512 / TC::COLS;
+        if (o < 1) return -4;
+        occ = o;
+    }
+    long long g = a.ne < 152LL * occ ? a.ne : 152LL * occ;
+    k_fused_B<float, P, 128, TCM><<<(int)g, 128, smem, s>>>(a);
+    return 0;
+}
+
 template <typename T, int P>
 static int fused_phase(int phase, const HexArgs<T> &a, cudaStream_t s, int variant)
 {
-    constexpr int N = P + 1, NF = 6 * N * N;
     if (a.ne == 0) return 0;
     if (phase == 0) {
         constexpr int EB = 8;
@@ -960,6 +1196,13 @@ static int fused_phase(int phase, const HexArgs<T> &a, cudaStream_t s, int varia
         if (g > 152LL * 16) g = 152LL * 16;
         k_disu_blk<T, P, EB, 256><<<(int)g, 256, 0, s>>>(a);
     } else if (phase == 1) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (a.tcmode != 0) {
+                const int r = a.tcmode == 1 ? launch_B_tc<P, 1>(a, s) : launch_B_tc<P, 2>(a, s);
+                if (r) return r;
+                return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+            }
+        }
         // launch shape chosen by the autotuner: 64, 128 or 256 threads per element
         if (variant == 0) launch_B<T, P, 64>(a, s);
         else if (variant == 2) launch_B<T, P, 256>(a, s);

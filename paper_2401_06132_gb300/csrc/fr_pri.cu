@@ -15,8 +15,6 @@
 // [x_hi | x_lo | x_hi] against [y_hi | y_hi | y_lo]. Rows (element field x z level) are scaled by a
 // power of two that brings their largest magnitude into [2^14, 2^15), so FP16 keeps full precision
 // in x_lo; the scale is removed exactly after the product.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "fr_internal.h"
@@ -114,50 +112,6 @@ __device__ __forceinline__ void load_ops(const PriOps<T> *g, PriOps<T> &s)
     for (int i = threadIdx.x; i < n; i += NTH) dst[i] = src[i];
 }
 
-
-// -------------------------------------------------------------------------------------------------
-// Split hi + lo operands for the tensor cores (TCM = 1: FP16, 2: BF16)
-// -------------------------------------------------------------------------------------------------
-template <int TCM>
-__device__ __forceinline__ void split16(float x, uint16_t &h, uint16_t &l)
-{
-    if constexpr (TCM == 1) {
-        const __half hh = __float2half_rn(x);
-        h = __half_as_ushort(hh);
-        l = __half_as_ushort(__float2half_rn(x - __half2float(hh)));
-    } else {
-        const __nv_bfloat16 hh = __float2bfloat16_rn(x);
-        h = __bfloat16_as_ushort(hh);
-        l = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(hh)));
-    }
-}
-
-// Exponent s with max|x| 2^s in [2^14, 2^15) (0 for zero, subnormal or non-finite maxima).
-__device__ __forceinline__ int row_shift(float mx)
-{
-    const int eb = (int)((__float_as_uint(mx) >> 23) & 0xFF);
-    if (eb == 0 || eb == 255) return 0;
-    const int sh = 141 - eb;
-    return sh < -120 ? -120 : (sh > 120 ? 120 : sh);
-}
-__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
-
-__device__ __forceinline__ uint32_t pack2(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
-
-// Writes the K values v[0..K) of row r as K/8 core-matrix rows of 16 bytes.
-template <int K>
-__device__ __forceinline__ void store_row(unsigned char *base, int r, const uint16_t (&v)[K])
-{
-#pragma unroll
-    for (int ch = 0; ch < K / 8; ch++) {
-        uint4 w;
-        w.x = pack2(v[8 * ch + 0], v[8 * ch + 1]);
-        w.y = pack2(v[8 * ch + 2], v[8 * ch + 3]);
-        w.z = pack2(v[8 * ch + 4], v[8 * ch + 5]);
-        w.w = pack2(v[8 * ch + 6], v[8 * ch + 7]);
-        *reinterpret_cast<uint4 *>(base + tc::core_offset(r, 8 * ch, (K / 8) * 128)) = w;
-    }
-}
 
 // Shared-memory operands of the tensor-core contractions (bytes, 128-byte aligned pieces).
 constexpr int TC_KI = 32, TC_NI = 32;          // interpolation: K = 3 x 10 (+2 zero), N = 25 (+7)
@@ -284,20 +238,18 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
         s_sh = reinterpret_cast<int *>(tBp + TC_BP_BYTES);
         mbar = reinterpret_cast<uint64_t *>(s_sh + 128);
         s_tmem = reinterpret_cast<uint32_t *>(mbar + 1);
-        if (threadIdx.x == 0) tc::mbar_init(mbar, 1);
-        __syncwarp();
-        if (threadIdx.x < 32) tc::tmem_alloc(s_tmem, 32);
+        tc::setup(mbar, s_tmem, 32);
         __syncthreads();   // operators in shared memory
         for (int i = threadIdx.x; i < TC_NI * TC_KI; i += NTH) {   // [B_hi | B_hi | B_lo]
             const int n = i / TC_KI, k = i % TC_KI;
             uint16_t h = 0, l = 0;
-            if (n < NQT && k < 3 * NT_) split16<TCM>((float)op.Bt[n][k % NT_], h, l);
+            if (n < NQT && k < 3 * NT_) tc::split16<TCM>((float)op.Bt[n][k % NT_], h, l);
             *reinterpret_cast<uint16_t *>(tBi + tc::core_offset(n, k, TC_SBO_I)) = k < 2 * NT_ ? h : l;
         }
         for (int i = threadIdx.x; i < TC_NP * TC_KP; i += NTH) {   // [P_hi | P_hi | P_lo]
             const int n = i / TC_KP, k = i % TC_KP;
             uint16_t h = 0, l = 0;
-            if (n < NT_ && k < 3 * NQT) split16<TCM>((float)op.Pt[n][k % NQT], h, l);
+            if (n < NT_ && k < 3 * NQT) tc::split16<TCM>((float)op.Pt[n][k % NQT], h, l);
             *reinterpret_cast<uint16_t *>(tBp + tc::core_offset(n, k, TC_SBO_P)) = k < 2 * NQT ? h : l;
         }
         tc::fence_async_smem();
@@ -430,43 +382,31 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
                     x[t] = v;
                     mx = fmaxf(mx, fabsf(v));
                 }
-                const int sh = row_shift(mx);
-                const float sc = pow2f(sh);
+                const int sh = tc::row_shift(mx);
+                const float sc = tc::pow2f(sh);
                 uint16_t kv[TC_KI];
 #pragma unroll
                 for (int t = 0; t < NT_; t++) {
                     uint16_t h, l;
-                    split16<TCM>(x[t] * sc, h, l);
+                    tc::split16<TCM>(x[t] * sc, h, l);
                     kv[t] = h; kv[NT_ + t] = l; kv[2 * NT_ + t] = h;
                 }
 #pragma unroll
                 for (int k = 3 * NT_; k < TC_KI; k++) kv[k] = 0;
-                store_row<TC_KI>(tA, r, kv);
+                tc::store_row<TC_KI>(tA, r, kv);
                 s_sh[r] = sh;
             }
-            tc::fence_async_smem();
-            tc::fence_before_sync();
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                tc::fence_after_sync();
-                const uint32_t aA = tc::smem_u32(tA), aB = tc::smem_u32(tBi);
-#pragma unroll
-                for (int j = 0; j < TC_KI / 16; j++)
-                    tc::mma_f16(tmem, tc::sdesc(aA + 256 * j, 128, TC_SBO_I), tc::sdesc(aB + 256 * j, 128, TC_SBO_I),
-                                TCM == 1 ? TC_IDESC_I1 : TC_IDESC_I2, j);
-                tc::commit(mbar);
+            if (!tc::mma_chain<TC_KI / 16>(tmem, tA, TC_SBO_I, tBi, TC_SBO_I, TCM == 1 ? TC_IDESC_I1 : TC_IDESC_I2, mbar, parity)) {
+                tc_fail = true;
+                break;
             }
-            const bool done = tc::mbar_wait(mbar, parity);
-            if (!__syncthreads_and(done)) { tc_fail = true; break; }
-            parity ^= 1;
-            tc::fence_after_sync();
             {
                 float v0[16], v1[16];
                 const uint32_t ta = tmem + ((uint32_t)(32 * (threadIdx.x >> 5)) << 16);
                 tc::ld16(ta, v0);
                 tc::ld16(ta + 16, v1);
                 if (r < TC_ROWS_I) {
-                    const float isc = pow2f(-s_sh[r]);
+                    const float isc = tc::pow2f(-s_sh[r]);
                     T *dst = s_w + NQT * r;                    // field f, level c: f NQ + 25 c = 25 r
 #pragma unroll
                     for (int q = 0; q < 16; q++) dst[q] = (T)(v0[q] * isc);
@@ -511,41 +451,29 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
                 float x[NQT], mx = 0.f;
 #pragma unroll
                 for (int q = 0; q < NQT; q++) { x[q] = (float)src[q]; mx = fmaxf(mx, fabsf(x[q])); }
-                const int sh = row_shift(mx);
-                const float sc = pow2f(sh);
+                const int sh = tc::row_shift(mx);
+                const float sc = tc::pow2f(sh);
                 uint16_t kv[TC_KP];
 #pragma unroll
                 for (int q = 0; q < NQT; q++) {
                     uint16_t h, l;
-                    split16<TCM>(x[q] * sc, h, l);
+                    tc::split16<TCM>(x[q] * sc, h, l);
                     kv[q] = h; kv[NQT + q] = l; kv[2 * NQT + q] = h;
                 }
 #pragma unroll
                 for (int k = 3 * NQT; k < TC_KP; k++) kv[k] = 0;
-                store_row<TC_KP>(tA, r, kv);
+                tc::store_row<TC_KP>(tA, r, kv);
                 s_sh[r] = sh;
             }
-            tc::fence_async_smem();
-            tc::fence_before_sync();
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                tc::fence_after_sync();
-                const uint32_t aA = tc::smem_u32(tA), aB = tc::smem_u32(tBp);
-#pragma unroll
-                for (int j = 0; j < TC_KP / 16; j++)
-                    tc::mma_f16(tmem, tc::sdesc(aA + 256 * j, 128, TC_SBO_P), tc::sdesc(aB + 256 * j, 128, TC_SBO_P),
-                                TCM == 1 ? TC_IDESC_P1 : TC_IDESC_P2, j);
-                tc::commit(mbar);
+            if (!tc::mma_chain<TC_KP / 16>(tmem, tA, TC_SBO_P, tBp, TC_SBO_P, TCM == 1 ? TC_IDESC_P1 : TC_IDESC_P2, mbar, parity)) {
+                tc_fail = true;
+                break;
             }
-            const bool done = tc::mbar_wait(mbar, parity);
-            if (!__syncthreads_and(done)) { tc_fail = true; break; }
-            parity ^= 1;
-            tc::fence_after_sync();
             {
                 float v0[16];
                 tc::ld16(tmem + ((uint32_t)(32 * (threadIdx.x >> 5)) << 16), v0);
                 if (r < TC_ROWS_P) {
-                    const float isc = pow2f(-s_sh[r]);
+                    const float isc = tc::pow2f(-s_sh[r]);
 #pragma unroll
                     for (int t = 0; t < NT_; t++) s_t[TC_ST * r + t] = (T)(v0[t] * isc);
                 }
@@ -574,18 +502,9 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
         __syncthreads();
     }
     if constexpr (TCM != 0) {
-        if (tc_fail) {
-            // a tensor-core chain did not complete within the bound: report it, give the chain one
-            // more bounded wait, then release the tensor memory
-            if (threadIdx.x == 0) atomicOr(a.status, 2);
-            tc::mbar_wait(mbar, parity);
-        }
-        tc::fence_before_sync();
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            tc::fence_after_sync();
-            tc::tmem_free(tmem, 32);
-        }
+        // a chain that did not complete within the bound is reported; the tensor memory is released
+        if (tc_fail && threadIdx.x == 0) atomicOr(a.status, 2);
+        tc::teardown(mbar, parity, tc_fail, tmem, 32);
     }
 }
 

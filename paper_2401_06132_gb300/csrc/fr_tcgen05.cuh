@@ -9,6 +9,9 @@
 // with lbo = 128 (core matrices adjacent along K) and sbo = (K / 8) * 128.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <cstdint>
 
 namespace tc {
@@ -117,6 +120,94 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16])
         : "memory");
 #pragma unroll
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// Split hi + lo operands (TCM = 1: FP16, 2: BF16): x_hi = round(x), x_lo = round(x - x_hi).
+template <int TCM>
+__device__ __forceinline__ void split16(float x, uint16_t &h, uint16_t &l)
+{
+    if constexpr (TCM == 1) {
+        const __half hh = __float2half_rn(x);
+        h = __half_as_ushort(hh);
+        l = __half_as_ushort(__float2half_rn(x - __half2float(hh)));
+    } else {
+        const __nv_bfloat16 hh = __float2bfloat16_rn(x);
+        h = __bfloat16_as_ushort(hh);
+        l = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(hh)));
+    }
+}
+
+// Exponent s with max|x| 2^s in [2^14, 2^15) (0 for zero, subnormal or non-finite maxima).
+__device__ __forceinline__ int row_shift(float mx)
+{
+    const int eb = (int)((__float_as_uint(mx) >> 23) & 0xFF);
+    if (eb == 0 || eb == 255) return 0;
+    const int sh = 141 - eb;
+    return sh < -120 ? -120 : (sh > 120 ? 120 : sh);
+}
+__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
+
+__device__ __forceinline__ uint32_t pack2(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
+
+// Writes the K values v[0..K) of row r as K/8 core-matrix rows of 16 bytes.
+template <int K>
+__device__ __forceinline__ void store_row(unsigned char *base, int r, const uint16_t (&v)[K])
+{
+#pragma unroll
+    for (int ch = 0; ch < K / 8; ch++) {
+        uint4 w;
+        w.x = pack2(v[8 * ch + 0], v[8 * ch + 1]);
+        w.y = pack2(v[8 * ch + 2], v[8 * ch + 3]);
+        w.z = pack2(v[8 * ch + 4], v[8 * ch + 5]);
+        w.w = pack2(v[8 * ch + 6], v[8 * ch + 7]);
+        *reinterpret_cast<uint4 *>(base + core_offset(r, 8 * ch, (K / 8) * 128)) = w;
+    }
+}
+
+// One MMA chain D = A B^T over KSTEPS slices of K = 16 (M = 128 rows of A, N rows of B, both K-major
+// with lbo = 128), issued by thread 0 after every thread's operand stores are made visible to the
+// tensor core; then every thread waits (bounded) for completion. Returns false, uniformly across
+// the CTA, if the wait gave up; the phase parity advances only on success.
+template <int KSTEPS>
+__device__ __forceinline__ bool mma_chain(uint32_t tmem, const unsigned char *A, int sbo_a, const unsigned char *B, int sbo_b,
+                                          uint32_t idesc, uint64_t *mbar, uint32_t &parity)
+{
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        fence_after_sync();
+        const uint32_t aA = smem_u32(A), aB = smem_u32(B);
+#pragma unroll
+        for (int j = 0; j < KSTEPS; j++)
+            mma_f16(tmem, sdesc(aA + 256 * j, 128, sbo_a), sdesc(aB + 256 * j, 128, sbo_b), idesc, j);
+        commit(mbar);
+    }
+    const bool done = mbar_wait(mbar, parity);
+    if (!__syncthreads_and(done)) return false;
+    parity ^= 1;
+    fence_after_sync();
+    return true;
+}
+
+// Per-CTA setup: mbarrier (thread 0) and tensor-memory columns (warp 0). Call with every thread.
+__device__ __forceinline__ void setup(uint64_t *mbar, uint32_t *s_tmem, uint32_t ncols)
+{
+    if (threadIdx.x == 0) mbar_init(mbar, 1);
+    __syncwarp();
+    if (threadIdx.x < 32) tmem_alloc(s_tmem, ncols);
+}
+
+// Per-CTA teardown; `failed`: a chain gave up, so its completion gets one more bounded wait first.
+__device__ __forceinline__ void teardown(uint64_t *mbar, uint32_t parity, bool failed, uint32_t tmem, uint32_t ncols)
+{
+    if (failed) mbar_wait(mbar, parity);
+    fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        fence_after_sync();
+        tmem_free(tmem, ncols);
+    }
 }
 
 }  // namespace tc

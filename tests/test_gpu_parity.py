@@ -197,14 +197,15 @@ def test_full_size_48cubed_fp64_parity(form):
     assert err.max() <= 1e-12, err
 
 
-def _fp32_errors(N, p, lowmach, mesh_fn=W.box_hex_mesh, perturb=1e-3):
+def _fp32_errors(N, p, lowmach, mesh_fn=W.box_hex_mesh, perturb=1e-3, prec="fp32", hex_tc=False):
     nu = (p + 1) ** 3
     mesh = mesh_fn(N)
     p0 = W.tgv_p0()
     o = O.Oracle(mesh, p, p + 2, threads=NCPU, p_ref=p0)
     U = W.tgv_state(o.sol_coords(), [(N ** 3, nu)], perturb=perturb).astype(np.float32)
     Ro = o.rhs(U.astype(np.float64))
-    m = fr.FRMesh(mesh, fr.make_params(p=p, prec="fp32", p_ref=p0, rho_ref=1.0 if lowmach else 0.0))
+    m = fr.FRMesh(mesh, fr.make_params(p=p, prec=prec, p_ref=p0, rho_ref=1.0 if lowmach else 0.0))
+    m.set_hex_tensor_cores(hex_tc)
     Ud = torch.from_numpy(U).cuda()
     Rd = torch.empty_like(Ud)
     m.rhs(Ud, Rd)
@@ -222,6 +223,19 @@ def test_fp32_lowmach_form_within_2e5(N, p, meshname):
     err, glob = _fp32_errors(N, p, True, fn)
     print(f"fp32 low-Mach N={N} p={p} {meshname}: per-variable {err}, global {glob:.3e}")
     assert err.max() <= 2e-5, err
+
+
+@pytest.mark.parametrize("N,p,meshname", [(4, 3, "box"), (4, 4, "box"), (3, 3, "sheared"), (3, 4, "sheared"), (16, 3, "box")])
+def test_mixed_forms_on_hexahedra(N, p, meshname):
+    """Split FP16 / BF16 tensor-core x-y plane contractions in the hexahedral volume kernel (low-Mach
+    form, switched on with fr_set_hex_tensor_cores): FP16 halves within 2e-5 per conserved variable,
+    like FP32; BF16 halves reported and bounded at 1e-3."""
+    fn = W.box_hex_mesh if meshname == "box" else W.sheared_box_mesh
+    e16, _ = _fp32_errors(N, p, True, fn, prec="mixed_fp16", hex_tc=True)
+    e8, _ = _fp32_errors(N, p, True, fn, prec="mixed_bf16", hex_tc=True)
+    print(f"hex N={N} p={p} {meshname}: fp16 splits {e16}, bf16 splits {e8}")
+    assert e16.max() <= 2e-5, e16
+    assert e8.max() <= 1e-3, e8
 
 
 @pytest.mark.parametrize("p", [3, 4])
@@ -371,8 +385,9 @@ def test_autotuner_choice_does_not_change_results():
 
 def test_precision_sweep_32cubed_p4():
     """The precision-sweep workload: 32^3 hex p=4 with 6^3 quadrature, every element compared. The
-    FP32 low-Mach form matches the oracle to 2e-5 per variable; the plain FP32 form's error is
-    reported. FP64 is held to 2e-12 here (1e-12 for the p=3 workloads): at p=4 the larger operators
+    FP32 low-Mach form and its split FP16 tensor-core form (x-y plane contractions of the hexahedra on
+    the tensor cores) match the oracle to 2e-5 per variable; the plain FP32 form's error and the split
+    BF16 form's are reported (bounded at 1e-3). FP64 is held to 2e-12 here (1e-12 for the p=3 workloads): at p=4 the larger operators
     put both FP64 codes' rounding near 1e-12 of the small residual R_rho of this nearly
     incompressible flow; the oracle alone moves by 2.5e-13 in momentum under an exact identity
     (p_ref = p0 against 0.9 p0) at this size."""
@@ -387,8 +402,11 @@ def test_precision_sweep_32cubed_p4():
     Ro32 = o.rhs(U32.astype(np.float64))
     res = {}
     for name, prec, rho_ref, Uin, ref in (("fp64", "fp64", 1.0, U, Ro), ("fp32_lowmach", "fp32", 1.0, U32, Ro32),
-                                          ("fp32_plain", "fp32", 0.0, U32, Ro32)):
+                                          ("fp32_plain", "fp32", 0.0, U32, Ro32),
+                                          ("mixed_fp16", "mixed_fp16", 1.0, U32, Ro32),
+                                          ("mixed_bf16", "mixed_bf16", 1.0, U32, Ro32)):
         m = fr.FRMesh(mesh, fr.make_params(p=p, prec=prec, p_ref=p0, rho_ref=rho_ref))
+        m.set_hex_tensor_cores(True)   # the split products on the hexahedra themselves
         Ud = torch.from_numpy(Uin).cuda()
         Rd = torch.empty_like(Ud)
         m.rhs(Ud, Rd)
@@ -399,6 +417,8 @@ def test_precision_sweep_32cubed_p4():
     assert res["fp64"].max() <= 2e-12, res["fp64"]
     assert res["fp32_lowmach"].max() <= 2e-5, res["fp32_lowmach"]
     assert res["fp32_plain"].max() <= 1e-3, res["fp32_plain"]
+    assert res["mixed_fp16"].max() <= 2e-5, res["mixed_fp16"]
+    assert res["mixed_bf16"].max() <= 1e-3, res["mixed_bf16"]
 
 
 def _mixed_grid_forms(N, precs, perturb=1e-3, const=False, rho_ref=0.0):
