@@ -37,6 +37,13 @@ def workload_name(n=N_EDGE, p=P, m=MQ):
     return f"TGV {n}^3 hex p={p} ({p + 1}^3 GL solution pts), {m}^3 GL flux anti-aliasing, RK4 step = 4 RHS"
 
 
+# FP64 peak of the chip from its unit counts and clock: 152 SMs x 2 FP64 FMA/clock x 2 FLOP x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + written) per element of one FP64 volume-kernel launch, from one Nsight Compute
+# capture of that kernel on the 32^3 p = 3 box (389.2 MB / 32,768 elements); the kernel touches each
+# element's inputs and outputs once, so a launch's traffic scales with its element count
+VOLUME_FP64_DRAM_BYTES_PER_ELEMENT = 389.2e6 / 32768
+
 # ---------------------------------------------------------------------------------------------
 # FLOP model of the fused volume kernel (phase B), FMA = 2 FLOP; counted from its arithmetic
 # ---------------------------------------------------------------------------------------------
@@ -313,7 +320,8 @@ def run_ours(args, rank, world):
     b_avg = b_ms / max(1, b_n)
     flops_b = phase_b_flops_per_element() * info["elements"]
     probe = fr.probe_fma()
-    peak_fp64 = probe["fp64_gflops"] / 1e3
+    # FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA per clock x 2 FLOP x 2.07 GHz
+    peak_fp64 = FP64_PEAK_TFLOPS
     achieved = flops_b / (b_avg * 1e-3) / 1e12
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else open(os.devnull) as f:
         try:
@@ -382,8 +390,12 @@ def run_ours(args, rank, world):
                    "l2": "inputs larger than L2 (283 MB FP64 state, 129 MB L2)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"kernel": "fused B (volume group)", "bound": "alu", "achieved": achieved, "peak": peak_fp64,
-                     "unit": "TFLOP/s", "frac": achieved / peak_fp64, "traffic": None,
-                     "peak_source": "FP64 FMA probe (fr_probe_fma), measured in this run",
+                     "unit": "TFLOP/s", "frac": achieved / peak_fp64,
+                     "traffic": VOLUME_FP64_DRAM_BYTES_PER_ELEMENT * info["elements"],
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clock x 2 FLOP x 2.07 GHz",
+                     "traffic_source": "ncu dram bytes of one volume-kernel launch on the 32^3 box, scaled by elements",
+                     "probe_fp64_tflops": probe["fp64_gflops"] / 1e3,
+                     "frac_of_probe": achieved / (probe["fp64_gflops"] / 1e3),
                      "flops_per_launch": flops_b, "avg_launch_ms": b_avg},
         "hbm_roofline": {"compulsory_bytes_per_rhs": compulsory, "peak_gbs": hbm_peak,
                          "frac": hbm_frac, "note": "compulsory bytes (U read + R written) / RHS time / measured copy peak"},
