@@ -49,7 +49,7 @@ struct InstanceHost {
 
 // Blocks of one element type and order, launched together (one launch per phase).
 struct Group {
-    int type = 0, p = 0;
+    int type = 0, p = 0, m = 0;
     std::vector<int> blks;
     long long ne = 0;
     void *d_geo = nullptr;          // Geo<T> per element in group order (multi-block groups)
@@ -440,7 +440,12 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
         if (!d) return fail(FR_EINVAL, "instance %d: null descriptor", ii);
         if (P.prec != m->prec) return fail(FR_EINVAL, "all instances must share one precision");
         int m1 = P.nq1d > 0 ? P.nq1d : P.p + 2;
-        if (P.p < 3 || P.p > 4 || m1 != P.p + 2) return fail(FR_EUNSUPPORTED, "instance %d: order %d with %d quadrature points", ii, P.p, m1);
+        // m1 = p + 2: flux anti-aliasing on (p + 2)^3 GL points; m1 = p + 1: the quadrature points are
+        // the solution points, i.e. the collocation form without anti-aliasing (hexahedra only)
+        if (P.p < 3 || P.p > 4 || (m1 != P.p + 2 && m1 != P.p + 1))
+            return fail(FR_EUNSUPPORTED, "instance %d: order %d with %d quadrature points", ii, P.p, m1);
+        if (m1 == P.p + 1 && d && d->n_pri > 0)
+            return fail(FR_EUNSUPPORTED, "instance %d: prisms are built with flux anti-aliasing only", ii);
         if (!(P.gamma > 1.0) || !(P.Pr > 0.0) || P.mu < 0.0 || P.tau < 0.0 || !(P.p_ref == P.p_ref) ||
             !(P.rho_ref >= 0.0))
             return fail(FR_EINVAL, "instance %d: bad physical parameters", ii);
@@ -464,7 +469,9 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
             B.inst = ii; B.type = type; B.p = P.p; B.m = m1;
             frb::Hex1D h;
             if (type == 0) {
-                if (frb::hex1d(P.p, m1, h)) return fail(FR_EUNSUPPORTED, "hex operators for p=%d m=%d", P.p, m1);
+                // the device tables hold the p + 2 point operators (the collocation form uses none of
+                // the quadrature-point ones)
+                if (frb::hex1d(P.p, P.p + 2, h)) return fail(FR_EUNSUPPORTED, "hex operators for p=%d", P.p);
                 B.nu = (P.p + 1) * (P.p + 1) * (P.p + 1); B.nf = 6 * (P.p + 1) * (P.p + 1);
             } else {
                 if (!m->has_pri) {
@@ -612,8 +619,8 @@ static fr_status build_groups(fr_mesh *m, const std::vector<uint32_t> &partner)
     for (size_t b = 0; b < m->blocks.size(); b++) {
         const Block &B = m->blocks[b];
         Group *g = nullptr;
-        for (Group &x : m->groups) if (x.type == B.type && x.p == B.p) g = &x;
-        if (!g) { m->groups.push_back(Group()); g = &m->groups.back(); g->type = B.type; g->p = B.p; }
+        for (Group &x : m->groups) if (x.type == B.type && x.p == B.p && x.m == B.m) g = &x;
+        if (!g) { m->groups.push_back(Group()); g = &m->groups.back(); g->type = B.type; g->p = B.p; g->m = B.m; }
         g->blks.push_back((int)b);
         g->ne += B.ne;
     }
@@ -703,7 +710,7 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
     cudaError_t ce = cudaGetDevice(&m->dev);
     if (ce != cudaSuccess) { delete m; return fail(FR_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(ce)); }
     for (size_t b = 0; b < m->blocks.size(); b++)
-        if (m->blocks[b].type == 0 && hex_upload_ops(m->blocks[b].p, m->blocks[b].m, m->hex1d[b])) { delete m; return fail(FR_ECUDA, "operator upload failed"); }
+        if (m->blocks[b].type == 0 && hex_upload_ops(m->blocks[b].p, m->blocks[b].p + 2, m->hex1d[b])) { delete m; return fail(FR_ECUDA, "operator upload failed"); }
     size_t ts = tsize(m->prec);
     st = (m->prec == FR_FP64) ? upload_geo<double>(m) : upload_geo<float>(m);
     if (!st) st = (m->prec == FR_FP64) ? upload_priops<double>(m, &m->d_priops) : upload_priops<float>(m, &m->d_priops);
@@ -845,6 +852,8 @@ static HexArgs<T> make_args(fr_mesh *m, const Block &b, const void *U, void *R)
     a.status = m->d_status;
     a.tcmode = m->prec == FR_MIXED_FP16 ? 1 : (m->prec == FR_MIXED_BF16 ? 2 : 0);
     if (b.type == 0 && !m->hex_tc) a.tcmode = 0;
+    a.aa_off = b.m == b.p + 1;
+    if (a.aa_off) a.tcmode = 0;
     return a;
 }
 
@@ -852,6 +861,8 @@ static fr_status ensure_unfused(fr_mesh *m)
 {
     if (m->blocks.size() != 1 || m->blocks[0].type != 0)
         return fail(FR_EUNSUPPORTED, "the unfused form runs single-instance hexahedral meshes");
+    if (m->blocks[0].m != m->blocks[0].p + 2)
+        return fail(FR_EUNSUPPORTED, "the unfused form runs the anti-aliased discretisation only");
     const Block &b = m->blocks[0];
     size_t ts = tsize(m->prec);
     long long nq = (long long)b.m * b.m * b.m;

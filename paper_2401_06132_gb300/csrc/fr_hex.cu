@@ -189,7 +189,11 @@ struct HexSmem {
     static constexpr int N = P + 1, M = P + 2, NU = N * N * N, NF = 6 * N * N, NQ = M * M * M;
     // solution-point fields are padded so that x-lines of even length do not start on the same banks
     static constexpr int XS = (N % 2 == 0) ? N + 1 : N, PS = XS * N, FS = PS * N;
-    static constexpr int T1 = 5 * M * N * N, T2 = 5 * M * M * N;
+    // FP32 sweeps all 20 (15) fields per pass with one staging buffer (the first sweep's output
+    // goes to the quadrature-point buffer); FP64, bound by its FMA pipe rather than by barriers,
+    // keeps five fields per pass and the smaller footprint (more resident CTAs)
+    static constexpr bool WIDE = sizeof(T) == 4;
+    static constexpr int T1 = WIDE ? 0 : 5 * M * N * N, T2 = WIDE ? 20 * M * M * N : 5 * M * M * N;
     static constexpr int SIZE = 5 * FS + 15 * FS + 5 * NF + 20 * NQ + T1 + T2;
 };
 
@@ -306,6 +310,112 @@ __device__ __forceinline__ void interp_5(const HexOps<T> &op, const T *src, T *t
     __syncthreads();
 }
 
+// Sum-factorised interpolation of all 20 fields at once (src: fields at stride FS, padded layout)
+// to the quadrature points (dst, stride NQ), x then y then z; the x sweep is staged in dst itself,
+// the y sweep in tmp (20 M^2 N values). Three barriers instead of twelve.
+template <typename T, int P, int NT, int XS, int PS, int FS>
+__device__ __forceinline__ void interp_all(const HexOps<T> &op, const T *src, T *tmp, T *dst)
+{
+    constexpr int N = P + 1, M = P + 2, NQ = M * M * M, NF_ = 20;
+    T *xs = dst;   // [f][qa + M (j + N k)]
+    for (int it = threadIdx.x; it < NF_ * N * N; it += NT) {
+        const int f = it / (N * N), jk = it % (N * N);
+        const int sb = f * FS + XS * (jk % N) + PS * (jk / N);
+        T u[N];
+#pragma unroll
+        for (int i = 0; i < N; i++) u[i] = src[sb + i];
+#pragma unroll
+        for (int q = 0; q < M; q++) {
+            T v = T(0);
+#pragma unroll
+            for (int i = 0; i < N; i++) v += op.B[q][i] * u[i];
+            xs[f * M * N * N + q + M * jk] = v;
+        }
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < NF_ * M * N; it += NT) {   // (f, qa, k)
+        const int f = it / (M * N), r = it % (M * N), qa = r % M, k = r / M;
+        T u[N];
+#pragma unroll
+        for (int j = 0; j < N; j++) u[j] = xs[f * M * N * N + qa + M * j + M * N * k];
+#pragma unroll
+        for (int q = 0; q < M; q++) {
+            T v = T(0);
+#pragma unroll
+            for (int j = 0; j < N; j++) v += op.B[q][j] * u[j];
+            tmp[f * M * M * N + qa + M * q + M * M * k] = v;
+        }
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < NF_ * M * M; it += NT) {   // (f, qa, qb)
+        const int f = it / (M * M), ab = it % (M * M);
+        T u[N];
+#pragma unroll
+        for (int k = 0; k < N; k++) u[k] = tmp[f * M * M * N + ab + M * M * k];
+#pragma unroll
+        for (int q = 0; q < M; q++) {
+            T v = T(0);
+#pragma unroll
+            for (int k = 0; k < N; k++) v += op.B[q][k] * u[k];
+            dst[f * NQ + ab + M * M * q] = v;
+        }
+    }
+    __syncthreads();
+}
+
+// Sum-factorised L2 projection of all 15 fields at once from the quadrature points (src, stride
+// NQ) to the solution points (dst, padded layout, stride FS), z then y then x; the z sweep is staged
+// in tmp (15 M^2 N values), the y sweep in src itself.
+template <typename T, int P, int NT, int XS, int PS, int FS>
+__device__ __forceinline__ void project_all(const HexOps<T> &op, T *src, T *tmp, T *dst)
+{
+    constexpr int N = P + 1, M = P + 2, NQ = M * M * M, NF_ = 15;
+    for (int it = threadIdx.x; it < NF_ * M * M; it += NT) {   // (f, qa, qb) -> k
+        const int f = it / (M * M), ab = it % (M * M);
+        T u[M];
+#pragma unroll
+        for (int c = 0; c < M; c++) u[c] = src[f * NQ + ab + M * M * c];
+#pragma unroll
+        for (int k = 0; k < N; k++) {
+            T v = T(0);
+#pragma unroll
+            for (int c = 0; c < M; c++) v += op.Pj[k][c] * u[c];
+            tmp[f * M * M * N + ab + M * M * k] = v;
+        }
+    }
+    __syncthreads();
+    T *ys = src;   // [f][qa + M (j + N k)]
+    for (int it = threadIdx.x; it < NF_ * M * N; it += NT) {   // (f, qa, k) -> j
+        const int f = it / (M * N), r = it % (M * N), qa = r % M, k = r / M;
+        T u[M];
+#pragma unroll
+        for (int b = 0; b < M; b++) u[b] = tmp[f * M * M * N + qa + M * b + M * M * k];
+#pragma unroll
+        for (int j = 0; j < N; j++) {
+            T v = T(0);
+#pragma unroll
+            for (int b = 0; b < M; b++) v += op.Pj[j][b] * u[b];
+            ys[f * M * N * N + qa + M * j + M * N * k] = v;
+        }
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < NF_ * N * N; it += NT) {   // (f, j, k) -> i
+        const int f = it / (N * N), jk = it % (N * N);
+        T u[M];
+#pragma unroll
+        for (int q = 0; q < M; q++) u[q] = ys[f * M * N * N + q + M * jk];
+        const int db = f * FS + XS * (jk % N) + PS * (jk / N);
+#pragma unroll
+        for (int i = 0; i < N; i++) {
+            T v = T(0);
+#pragma unroll
+            for (int q = 0; q < M; q++) v += op.Pj[i][q] * u[q];
+            dst[db + i] = v;
+        }
+    }
+    __syncthreads();
+}
+
 // Sum-factorised L2 projection of 5 fields from quadrature points (src, stride NQ) to solution
 // points (dst, stride NU).
 template <typename T, int P, int NT, int XS = P + 1, int PS = (P + 1) * (P + 1), int FS = (P + 1) * (P + 1) * (P + 1)>
@@ -357,9 +467,10 @@ __device__ __forceinline__ void project_5(const HexOps<T> &op, const T *src, T *
     __syncthreads();
 }
 
-template <typename T, int P, int NT, int TCM = 0>
+template <typename T, int P, int NT, int TCM = 0, bool AA = true>
 __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
 {
+    static_assert(AA || TCM == 0, "the collocation form has no interpolation or projection");
     using S = HexSmem<T, P>;
     using TC = HexTc<P>;
     static_assert(TCM == 0 || (NT == 128 && std::is_same<T, float>::value), "tensor-core form: FP32, one warpgroup");
@@ -565,7 +676,11 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
             }
         }
         // 6. uqpts + gradcoru_qpts: 20 fields to quadrature points, 5 at a time
-        if constexpr (TCM == 0) {
+        if constexpr (!AA) {
+            // collocation form: the flux is evaluated at the solution points (step 7b below)
+        } else if constexpr (TCM == 0 && S::WIDE) {
+            interp_all<T, P, NT, XS, PS, FS>(op, s_u, s_t2, s_w);   // s_q follows s_u
+        } else if constexpr (TCM == 0) {
             interp_5<T, P, NT, XS, PS, FS>(op, s_u, s_t1, s_t2, s_w);
 #pragma unroll 1
             for (int c = 0; c < 3; c++) interp_5<T, P, NT, XS, PS, FS>(op, s_q + 5 * c * FS, s_t1, s_t2, s_w + (5 + 5 * c) * NQ);
@@ -616,7 +731,35 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
         }
         // 7. tdisf: transformed flux at each quadrature point, in place
         bool ok = true;
-        for (int q = threadIdx.x; q < NQ; q += NT) {
+        if constexpr (!AA) {
+            // 7b. collocation form: flux at the solution points from s_u and the gradient in s_q,
+            //     written over the gradient (the projection is the identity) once every thread is
+            //     done reading the gradient at the flux points
+            __syncthreads();
+            for (int z = threadIdx.x; z < NU; z += NT) {
+                const int pz = z % N + XS * ((z / N) % N) + PS * (z / (N * N));
+                T u[5], gq[5][3], f[3][5];
+#pragma unroll
+                for (int alpha = 0; alpha < 5; alpha++) {
+                    u[alpha] = s_u[alpha * FS + pz];
+#pragma unroll
+                    for (int d = 0; d < 3; d++) gq[alpha][d] = s_q[(alpha * 3 + d) * FS + pz];
+                }
+                if constexpr (std::is_same<T, float>::value) {
+                    if (dev) ok &= total_flux_dev(ph, u, gq, f);
+                    else ok &= total_flux(ph, u, gq, f);
+                } else {
+                    ok &= total_flux(ph, u, gq, f);
+                }
+#pragma unroll
+                for (int alpha = 0; alpha < 5; alpha++)
+#pragma unroll
+                    for (int d = 0; d < 3; d++)
+                        s_q[(alpha * 3 + d) * FS + pz] =
+                            g.det * (g.Ji[3 * d] * f[0][alpha] + g.Ji[3 * d + 1] * f[1][alpha] + g.Ji[3 * d + 2] * f[2][alpha]);
+            }
+        }
+        for (int q = threadIdx.x; AA && q < NQ; q += NT) {
             T u[5], gq[5][3], f[3][5];
 #pragma unroll
             for (int alpha = 0; alpha < 5; alpha++) {
@@ -649,7 +792,11 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
         flag_status(a.status, ok);
         __syncthreads();
         // 8. tdivtpcorf, first factor: projection of the 15 transformed-flux fields (into s_q)
-        if constexpr (TCM == 0) {
+        if constexpr (!AA) {
+            // collocation form: the flux already sits at the solution points
+        } else if constexpr (TCM == 0 && S::WIDE) {
+            project_all<T, P, NT, XS, PS, FS>(op, s_w, s_t2, s_q);
+        } else if constexpr (TCM == 0) {
 #pragma unroll 1
             for (int c = 0; c < 3; c++) project_5<T, P, NT, XS, PS, FS>(op, s_w + 5 * c * NQ, s_t1, s_t2, s_q + 5 * c * FS);
         } else {
@@ -1143,16 +1290,18 @@ static int grid_elems(long long ne, int per_sm)
     return (int)(g < 1 ? 1 : g);
 }
 
-template <typename T, int P, int NT>
+template <typename T, int P, int NT, bool AA = true>
 static void launch_B(const HexArgs<T> &a, cudaStream_t s)
 {
-    const size_t smem = HexSmem<T, P>::SIZE * sizeof(T);
+    using S = HexSmem<T, P>;
+    // the collocation form needs no quadrature-point buffers
+    const size_t smem = (AA ? S::SIZE : 20 * S::FS + 5 * S::NF) * sizeof(T);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_fused_B<T, P, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_fused_B<T, P, NT, 0, AA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    k_fused_B<T, P, NT><<<grid_elems(a.ne, 8), NT, smem, s>>>(a);
+    k_fused_B<T, P, NT, 0, AA><<<grid_elems(a.ne, 8), NT, smem, s>>>(a);
 }
 
 // Tensor-core form of the volume kernel (FP32, 128 threads, persistent: at most as many CTAs as
@@ -1204,6 +1353,12 @@ static int fused_phase(int phase, const HexArgs<T> &a, cudaStream_t s, int varia
             }
         }
         // launch shape chosen by the autotuner: 64, 128 or 256 threads per element
+        if (a.aa_off) {
+            if (variant == 0) launch_B<T, P, 64, false>(a, s);
+            else if (variant == 2) launch_B<T, P, 256, false>(a, s);
+            else launch_B<T, P, 128, false>(a, s);
+            return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+        }
         if (variant == 0) launch_B<T, P, 64>(a, s);
         else if (variant == 2) launch_B<T, P, 256>(a, s);
         else launch_B<T, P, 128>(a, s);

@@ -165,6 +165,9 @@ struct HexArgs {
     // Prism volume kernel in the FP32 compute precision: 0 = CUDA-core operators; 1 / 2 = the dense
     // triangle interpolation and projection as split hi + lo FP16 / BF16 products on the tensor cores.
     int tcmode;
+    // Hexahedral volume kernel without anti-aliasing: the flux is evaluated at the solution points
+    // (quadrature points = solution points, so interpolation and projection are the identity).
+    int aa_off;
 };
 
 #ifdef __CUDACC__

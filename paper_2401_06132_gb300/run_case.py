@@ -21,6 +21,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=16, help="elements per box edge")
     ap.add_argument("--p", type=int, default=3)
+    ap.add_argument("--nq", type=int, default=0, help="1D quadrature points (0: p + 2; p + 1: no anti-aliasing)")
     ap.add_argument("--mesh", default="hex", choices=["hex", "sheared", "mixed"])
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "mixed_fp16", "mixed_bf16"])
     ap.add_argument("--lowmach", type=int, default=1, help="FP32 low-Mach form (rho_ref = 1)")
@@ -38,7 +39,7 @@ def main(argv=None):
 
     mesh = {"hex": W.box_hex_mesh, "sheared": W.sheared_box_mesh, "mixed": W.mixed_box_mesh}[args.mesh](args.n)
     p0 = W.tgv_p0(mach=args.mach)
-    m = fr.FRMesh(mesh, fr.make_params(p=args.p, prec=args.prec, p_ref=p0, rho_ref=1.0 if args.lowmach else 0.0))
+    m = fr.FRMesh(mesh, fr.make_params(p=args.p, nq1d=args.nq, prec=args.prec, p_ref=p0, rho_ref=1.0 if args.lowmach else 0.0))
     m.set_form(args.form)
     blocks = []
     if mesh["hex_v"].shape[0]:

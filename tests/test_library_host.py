@@ -73,6 +73,10 @@ def test_host_validation_rejects_bad_meshes_before_any_device_work(lib):
     with pytest.raises(fr.FRError) as e:
         _create(W.box_hex_mesh(1), gamma=0.9)
     assert e.value.status == fr.FR_EINVAL
+    # the collocation form (nq1d = p + 1) is built for hexahedra only
+    with pytest.raises(fr.FRError) as e:
+        _create(W.mixed_box_mesh(2), p=3, nq1d=4)
+    assert e.value.status == fr.FR_EUNSUPPORTED and "anti-aliasing" in str(e.value)
 
 
 def test_splitmix64_reference_vectors():

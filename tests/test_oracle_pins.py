@@ -377,13 +377,14 @@ def test_ke_dissipation_rate_converges_to_closed_form():
     assert errs[0] < 1e-3 and errs[1] < 2e-6 and errs[1] < errs[0] / 100
 
 
-@pytest.mark.parametrize("meshfn", [W.box_hex_mesh, W.sheared_box_mesh])
-def test_rhs_converges_to_analytic_navier_stokes(meshfn):
+@pytest.mark.parametrize("meshfn,m", [(W.box_hex_mesh, 5), (W.sheared_box_mesh, 5), (W.box_hex_mesh, 4)])
+def test_rhs_converges_to_analytic_navier_stokes(meshfn, m):
     """Consistency on a compressible periodic field (div v != 0, non-uniform rho, M = 0.3): the
     inviscid RHS (mu = 0) converges to the exact -div f^e at order >= p - 0.5, and the viscous part
     R(mu) - R(0) (stress incl. the -2/3 mu div v term, viscous work and heat flux, Re = 10)
     converges to the exact -div(-f^v) at order >= p - 1.5 (second-derivative terms under LDG).
-    On the sheared mesh this also pins the metric terms (a transposed J^-1 fails)."""
+    On the sheared mesh this also pins the metric terms (a transposed J^-1 fails). m = 4 is the
+    collocation form (no anti-aliasing), which converges at the same orders on this smooth field."""
     from tests.analytic_ns import rhs_function, state_function
     mach, mu = 0.3, 0.1
     state = state_function("wave", 1.4, mach)
@@ -392,8 +393,8 @@ def test_rhs_converges_to_analytic_navier_stokes(meshfn):
     e_inv, e_vis = [], []
     for N in (8, 16):
         mesh = meshfn(N)
-        o0 = O.Oracle(mesh, 3, 5, mu=0.0, threads=os.cpu_count())
-        o1 = O.Oracle(mesh, 3, 5, mu=mu, threads=os.cpu_count())
+        o0 = O.Oracle(mesh, 3, m, mu=0.0, threads=os.cpu_count())
+        o1 = O.Oracle(mesh, 3, m, mu=mu, threads=os.cpu_count())
         x = o0.sol_coords()
         U = W.to_layout(state(x), [(N ** 3, 64)])
         r0 = o0.rhs(U).reshape(N ** 3, 5, 64).transpose(1, 0, 2).reshape(5, -1)
@@ -516,3 +517,22 @@ def test_reference_pressure_is_an_identity(name):
         rel = np.abs(a - b).max(axis=(0, 2)) / np.abs(a).max(axis=(0, 2))
         assert rel.max() < 5e-12, rel
         off += n
+
+
+@pytest.mark.parametrize("p", [3, 4])
+def test_collocation_form_is_identity_quadrature(p):
+    """Without anti-aliasing the flux is evaluated at the solution points: with m = p + 1 GL points
+    the quadrature points are the solution points, so M7 (interpolation) and M8 (the L2 projection,
+    exact because the n-point GL rule integrates degree 2p products) are the identity, and the RHS
+    is the collocation form. Pinned against that definition (identity operators, quadrature points
+    at the solution points) and freestream preservation."""
+    mesh = W.box_hex_mesh(2)
+    o = O.Oracle(mesh, p, p + 1)
+    nu = (p + 1) ** 3
+    np.testing.assert_allclose(o.op(0, "M7"), np.eye(nu), atol=1e-14)
+    np.testing.assert_allclose(o.op(0, "M8"), np.eye(nu), atol=1e-13)
+    np.testing.assert_allclose(o.op(0, "xq"), o.op(0, "xu"), atol=1e-15)
+    # freestream and conservation hold in the collocation form too
+    U = np.tile(np.array([1.1, 0.2, -0.3, 0.1, 180.0]).repeat(nu), 8)
+    R = o.rhs(U)
+    assert np.abs(R).max() <= 1e-13 * 180.0 * (2 / np.pi) * (p + 1) ** 2
