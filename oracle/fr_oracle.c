@@ -22,7 +22,10 @@
  *   G3  the LDG penalty tau(uL-uR) is dissipative in the total flux f = fe - fv.
  *   G4  M7 is Nq x Nu and M8 is Nu x Nq (the index definitions, not the printed dims).
  *   G5  the gradient is of the physical solution u (equivalent for affine elements).
- *   R2  hex flux points: n x n Gauss-Legendre (GL) points per face.
+ *   R2  hex flux points: n x n Gauss-Legendre (GL) points per face. With surface-flux
+ *       anti-aliasing (Sec. 2.2.1: the flux points at the interfaces are replaced by quadrature
+ *       points) they are the m x m GL points of the face quadrature instead; every flux-point
+ *       operator (M0, M3, M6, M2) then follows from the same definitions.
  *   R3  correction functions are the DG-equivalent ones: lift = M^-1 E with the exact mass
  *       matrix M and E = int_face l_zeta l^face_sigma dS (reference measure).
  *   R4  Rusanov: F = 1/2 n.(fe_L + fe_R) + 1/2 s (uL - uR), s = max(|vL.n|+cL, |vR.n|+cR).
@@ -263,6 +266,8 @@ typedef struct {
     double *Wu;             /* [nu] int l_zeta over the reference element */
     tri_basis tb;           /* prism only */
     double g1[16], g1w[16]; /* 1D GL solution nodes */
+    int nfn;                /* 1D nodes of the hex face point grids: n, or m with surface-flux AA */
+    double fg[32];          /* their coordinates */
 } etype_t;
 
 /* Modal orthonormal basis and its reference gradient at a point. */
@@ -330,8 +335,8 @@ static void face_map(const etype_t *et, int f, double s, double t, double *X)
 static double face_nodal(const etype_t *et, int f, int j, double s, double t, const double *TVinv)
 {
     if (et->faces[f].kind == 0) {
-        int n1 = et->n1;
-        return lagrange1d(n1, et->g1, j % n1, s) * lagrange1d(n1, et->g1, j / n1, t);
+        int k = et->nfn;
+        return lagrange1d(k, et->fg, j % k, s) * lagrange1d(k, et->fg, j / k, t);
     }
     int nt = et->tb.nt;
     double phi[64];
@@ -341,7 +346,7 @@ static double face_nodal(const etype_t *et, int f, int j, double s, double t, co
     return v;
 }
 
-static int etype_init(etype_t *et, int type, int p, int m, int tri_k)
+static int etype_init(etype_t *et, int type, int p, int m, int tri_k, int surf)
 {
     memset(et, 0, sizeof(*et));
     et->type = type; et->p = p; et->n1 = p + 1; et->m1 = m;
@@ -349,13 +354,16 @@ static int etype_init(etype_t *et, int type, int p, int m, int tri_k)
     or_gauss_legendre(n1, et->g1, et->g1w);
     double gq[32], gqw[32];
     or_gauss_legendre(m, gq, gqw);
+    if (surf && type != ET_HEX) return -1;   /* surface-flux AA: hexahedra only */
+    et->nfn = surf ? m : n1;
+    for (int i = 0; i < et->nfn; i++) et->fg[i] = surf ? gq[i] : et->g1[i];
     double txy[2 * 64];
     int nt = 0;
     if (type == ET_HEX) {
         et->nu = n1 * n1 * n1; et->nmodes = et->nu; et->nfaces = 6;
         et->nq = m * m * m;
         for (int f = 0; f < 6; f++) {
-            et->faces[f].kind = 0; et->faces[f].npts = n1 * n1; et->faces[f].dS = 1.0;
+            et->faces[f].kind = 0; et->faces[f].npts = et->nfn * et->nfn; et->faces[f].dS = 1.0;
             memset(et->faces[f].nref, 0, sizeof(double) * 3);
             et->faces[f].nref[f / 2] = (f % 2) ? 1.0 : -1.0;
         }
@@ -407,7 +415,7 @@ static int etype_init(etype_t *et, int type, int p, int m, int tri_k)
         for (int f = 0; f < et->nfaces; f++) {
             for (int j = 0; j < et->faces[f].npts; j++, s++) {
                 double ps, pt;
-                if (et->faces[f].kind == 0) { ps = et->g1[j % n1]; pt = et->g1[j / n1]; }
+                if (et->faces[f].kind == 0) { ps = et->fg[j % et->nfn]; pt = et->fg[j / et->nfn]; }
                 else { ps = txy[2 * j]; pt = txy[2 * j + 1]; }
                 et->fparam[2 * s] = ps; et->fparam[2 * s + 1] = pt;
                 face_map(et, f, ps, pt, et->xf + 3 * s);
@@ -671,9 +679,23 @@ static int facekey_cmp(const void *a, const void *b)
     return ((const or_facekey *)a)->face - ((const or_facekey *)b)->face;
 }
 
+void *or_create2(int p, int m, int tri_k, int surf, double gamma, double Pr, double mu, double beta, double tau,
+                 double p_ref, int n_hex, int n_pri, int n_verts, const double *verts, const int *hex_v,
+                 const int *pri_v, const double *period, int *err);
+
 void *or_create(int p, int m, int tri_k, double gamma, double Pr, double mu, double beta, double tau, double p_ref,
                 int n_hex, int n_pri, int n_verts, const double *verts, const int *hex_v, const int *pri_v,
                 const double *period, int *err)
+{
+    return or_create2(p, m, tri_k, 0, gamma, Pr, mu, beta, tau, p_ref, n_hex, n_pri, n_verts, verts, hex_v, pri_v,
+                      period, err);
+}
+
+/* As or_create; surf = 1 selects surface-flux anti-aliasing (hexahedra only): the flux points of
+ * every face are its m x m GL quadrature points. */
+void *or_create2(int p, int m, int tri_k, int surf, double gamma, double Pr, double mu, double beta, double tau,
+                 double p_ref, int n_hex, int n_pri, int n_verts, const double *verts, const int *hex_v,
+                 const int *pri_v, const double *period, int *err)
 {
     *err = OR_OK;
     if (p < 1 || m < 1 || n_hex < 0 || n_pri < 0 || n_hex + n_pri == 0) { *err = OR_EINVAL; return NULL; }
@@ -682,8 +704,8 @@ void *or_create(int p, int m, int tri_k, double gamma, double Pr, double mu, dou
     o->n_hex = n_hex; o->n_pri = n_pri; o->ne = n_hex + n_pri;
     for (int d = 0; d < 3; d++) o->period[d] = period ? period[d] : 0.0;
     o->nthreads = 1;
-    if (n_hex > 0) { if (etype_init(&o->et[ET_HEX], ET_HEX, p, m, tri_k)) { *err = OR_EUNSUPPORTED; free(o); return NULL; } o->has[ET_HEX] = 1; }
-    if (n_pri > 0) { if (etype_init(&o->et[ET_PRI], ET_PRI, p, m, tri_k)) { *err = OR_EUNSUPPORTED; or_destroy(o); return NULL; } o->has[ET_PRI] = 1; }
+    if (n_hex > 0) { if (etype_init(&o->et[ET_HEX], ET_HEX, p, m, tri_k, surf)) { *err = OR_EUNSUPPORTED; free(o); return NULL; } o->has[ET_HEX] = 1; }
+    if (n_pri > 0) { if (etype_init(&o->et[ET_PRI], ET_PRI, p, m, tri_k, surf)) { *err = OR_EUNSUPPORTED; or_destroy(o); return NULL; } o->has[ET_PRI] = 1; }
     int ne = o->ne;
     o->x0 = (double *)malloc(3 * ne * sizeof(double));
     o->J = (double *)malloc(9 * ne * sizeof(double));

@@ -38,6 +38,10 @@ def lib():
         L.or_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
                                 C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, dp, C.POINTER(C.c_int),
                                 C.POINTER(C.c_int), dp, C.POINTER(C.c_int)]
+        L.or_create2.restype = C.c_void_p
+        L.or_create2.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                                 C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, dp, C.POINTER(C.c_int),
+                                 C.POINTER(C.c_int), dp, C.POINTER(C.c_int)]
         L.or_destroy.argtypes = [C.c_void_p]
         L.or_set_threads.argtypes = [C.c_void_p, C.c_int]
         for fn in ("or_num_values", "or_num_fvalues", "or_num_pairs"):
@@ -101,16 +105,16 @@ class Oracle:
     """One mesh instance with its physical parameters (FP64)."""
 
     def __init__(self, mesh, p, m, gamma=1.4, Pr=0.71, mu=1.0 / 1600, beta=0.5, tau=0.1, tri_k=5,
-                 threads=None, p_ref=0.0):
+                 threads=None, p_ref=0.0, surf=False):
         L = lib()
         verts = np.ascontiguousarray(mesh["verts"], dtype=np.float64)
         hex_v = np.ascontiguousarray(mesh.get("hex_v", np.zeros((0, 8))), dtype=np.int32)
         pri_v = np.ascontiguousarray(mesh.get("pri_v", np.zeros((0, 6))), dtype=np.int32)
         period = np.ascontiguousarray(mesh.get("period", (0.0, 0.0, 0.0)), dtype=np.float64)
         err = C.c_int(0)
-        self.h = L.or_create(p, m, tri_k, gamma, Pr, mu, beta, tau, p_ref, hex_v.shape[0], pri_v.shape[0],
-                             verts.shape[0], _dp(verts), hex_v.ctypes.data_as(C.POINTER(C.c_int)),
-                             pri_v.ctypes.data_as(C.POINTER(C.c_int)), _dp(period), C.byref(err))
+        self.h = L.or_create2(p, m, tri_k, int(bool(surf)), gamma, Pr, mu, beta, tau, p_ref, hex_v.shape[0],
+                              pri_v.shape[0], verts.shape[0], _dp(verts), hex_v.ctypes.data_as(C.POINTER(C.c_int)),
+                              pri_v.ctypes.data_as(C.POINTER(C.c_int)), _dp(period), C.byref(err))
         if not self.h:
             raise RuntimeError(f"oracle mesh creation failed with status {err.value}")
         self.n_hex, self.n_pri = hex_v.shape[0], pri_v.shape[0]

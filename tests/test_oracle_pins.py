@@ -377,14 +377,16 @@ def test_ke_dissipation_rate_converges_to_closed_form():
     assert errs[0] < 1e-3 and errs[1] < 2e-6 and errs[1] < errs[0] / 100
 
 
-@pytest.mark.parametrize("meshfn,m", [(W.box_hex_mesh, 5), (W.sheared_box_mesh, 5), (W.box_hex_mesh, 4)])
-def test_rhs_converges_to_analytic_navier_stokes(meshfn, m):
+@pytest.mark.parametrize("meshfn,m,surf", [(W.box_hex_mesh, 5, False), (W.sheared_box_mesh, 5, False),
+                                           (W.box_hex_mesh, 4, False), (W.sheared_box_mesh, 5, True)])
+def test_rhs_converges_to_analytic_navier_stokes(meshfn, m, surf):
     """Consistency on a compressible periodic field (div v != 0, non-uniform rho, M = 0.3): the
     inviscid RHS (mu = 0) converges to the exact -div f^e at order >= p - 0.5, and the viscous part
     R(mu) - R(0) (stress incl. the -2/3 mu div v term, viscous work and heat flux, Re = 10)
     converges to the exact -div(-f^v) at order >= p - 1.5 (second-derivative terms under LDG).
     On the sheared mesh this also pins the metric terms (a transposed J^-1 fails). m = 4 is the
-    collocation form (no anti-aliasing), which converges at the same orders on this smooth field."""
+    collocation form (no anti-aliasing), which converges at the same orders on this smooth field;
+    surf = True adds surface-flux anti-aliasing (full anti-aliasing)."""
     from tests.analytic_ns import rhs_function, state_function
     mach, mu = 0.3, 0.1
     state = state_function("wave", 1.4, mach)
@@ -393,8 +395,8 @@ def test_rhs_converges_to_analytic_navier_stokes(meshfn, m):
     e_inv, e_vis = [], []
     for N in (8, 16):
         mesh = meshfn(N)
-        o0 = O.Oracle(mesh, 3, m, mu=0.0, threads=os.cpu_count())
-        o1 = O.Oracle(mesh, 3, m, mu=mu, threads=os.cpu_count())
+        o0 = O.Oracle(mesh, 3, m, mu=0.0, threads=os.cpu_count(), surf=surf)
+        o1 = O.Oracle(mesh, 3, m, mu=mu, threads=os.cpu_count(), surf=surf)
         x = o0.sol_coords()
         U = W.to_layout(state(x), [(N ** 3, 64)])
         r0 = o0.rhs(U).reshape(N ** 3, 5, 64).transpose(1, 0, 2).reshape(5, -1)
@@ -536,3 +538,69 @@ def test_collocation_form_is_identity_quadrature(p):
     U = np.tile(np.array([1.1, 0.2, -0.3, 0.1, 180.0]).repeat(nu), 8)
     R = o.rhs(U)
     assert np.abs(R).max() <= 1e-13 * 180.0 * (2 / np.pi) * (p + 1) ** 2
+
+
+# --- surface-flux anti-aliasing (hexahedra): flux points replaced by the m x m face quadrature
+@pytest.mark.parametrize("p", [3, 4])
+def test_surface_aa_lift_is_the_dg_lift_of_the_projected_face_data(p):
+    """With the face quadrature points as flux points, the DG lift M3' = M^-1 E' (reading R3) must
+    equal the n x n flux-point lift applied after the face L2 projection from the m x m GL points
+    to the n x n GL points: M3'[z][q] = sum_s M3[z][s] P(s, q), P = Pj (x) Pj with
+    Pj[i][a] = w_a l_i(x_a) / w_i. Both sides come from different constructions (face quadrature
+    of Lagrange products vs. 1D GL weights), so a wrong node set, weight or face mapping fails."""
+    mesh = W.box_hex_mesh(1)
+    o = O.Oracle(mesh, p, p + 2)
+    os_ = O.Oracle(mesh, p, p + 2, surf=True)
+    n, m = p + 1, p + 2
+    M3 = o.op(0, "lift")
+    M3s = os_.op(0, "lift")
+    assert M3s.shape == (n ** 3, 6 * m * m)
+    x, w = O.gauss_legendre(n)
+    xq, wq = O.gauss_legendre(m)
+    L = np.array([[np.prod([(xa - x[j]) / (x[i] - x[j]) for j in range(n) if j != i]) for xa in xq] for i in range(n)])
+    Pj = L * wq[None, :] / w[:, None]
+    P2 = np.kron(Pj, Pj)    # [(i + n j)][(a + m b)] on one face
+    for f in range(6):
+        np.testing.assert_allclose(M3s[:, f * m * m:(f + 1) * m * m], M3[:, f * n * n:(f + 1) * n * n] @ P2, atol=1e-13)
+
+
+@pytest.mark.parametrize("name", ["hex1_self_periodic", "hex3", "sheared3"])
+def test_surface_aa_freestream_and_conservation(name):
+    """Checks (a) and (e) with surface-flux anti-aliasing: a constant state gives a zero RHS, and the
+    quadrature-weighted RHS of a perturbed TGV sums to zero."""
+    mesh = MESHES[name]()
+    o = O.Oracle(mesh, 3, 5, surf=True)
+    blocks = _layout(o, mesh)
+    U = np.concatenate([np.tile(np.repeat(FREESTREAM, npt), ne) for ne, npt in blocks])
+    N = round(mesh["verts"].shape[0] ** (1.0 / 3.0)) - 1
+    assert np.abs(o.rhs(U)).max() < 1e-13 * 1.1 * (2.0 / (2 * np.pi / N)) * 16
+    U = _tgv(o, mesh, perturb=1e-2)
+    d = o.diagnostics(U, o.rhs(U))
+    assert np.all(np.abs(d["sums"]) <= 1e-12 * d["abs_sums"])
+
+
+def test_surface_aa_leaves_the_corrected_gradient_unchanged():
+    """The common solution is linear in the two traces, and the traces are polynomials of degree p
+    that the m x m face points interpolate and the face projection recovers exactly; so moving the
+    interface terms to the face quadrature points leaves the corrected gradient unchanged (to
+    rounding) and changes only the common flux. On the perturbed TGV the RHS does change (the
+    interface quadrature of the nonlinear flux), while the common solution at the face quadrature
+    points is the n x n common solution interpolated there."""
+    mesh = W.sheared_box_mesh(3)
+    o = O.Oracle(mesh, 3, 5)
+    os_ = O.Oracle(mesh, 3, 5, surf=True)
+    U = _tgv(o, mesh, perturb=1e-2)
+    a, b = o.rhs_stages(U), os_.rhs_stages(U)
+    scale = np.abs(a["qu"]).max()
+    np.testing.assert_allclose(b["qu"], a["qu"], atol=1e-12 * scale)
+    n, m = 4, 5
+    x, w = O.gauss_legendre(n)
+    xq, _ = O.gauss_legendre(m)
+    B = np.array([[np.prod([(xa - x[j]) / (x[i] - x[j]) for j in range(n) if j != i]) for i in range(n)] for xa in xq])
+    B2 = np.kron(B, B)      # [(a + m b)][(i + n j)]
+    ne = 27
+    cf = a["cf"].reshape(ne, 5, 6, n * n)
+    cfs = b["cf"].reshape(ne, 5, 6, m * m)
+    np.testing.assert_allclose(cfs, np.einsum("qs,evfs->evfq", B2, cf), atol=1e-12 * np.abs(cf).max())
+    dR = np.abs(a["R"] - b["R"]).max() / np.abs(a["R"]).max()
+    assert 1e-9 < dR < 1e-1, dR
