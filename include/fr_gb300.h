@@ -84,8 +84,10 @@ typedef struct {
     double mu;            /* dynamic viscosity (constant) */
     double beta;          /* LDG switch (Sec. 2.1 common solution and viscous flux) */
     double tau;           /* LDG penalty */
-    int p;                /* solution order; hex p in {2,3,4}, prism p = 3 */
-    int nq1d;             /* Gauss-Legendre quadrature points per line (0 = p + 2) */
+    int p;                /* solution order; hex p in {3,4}, prism p = 3 */
+    int nq1d;             /* Gauss-Legendre quadrature points per line: 0 or p + 2 = flux anti-aliasing
+                           * (Sec. 2.2.1); p + 1 = no anti-aliasing, the flux is evaluated at the
+                           * solution points (the collocation form; hexahedra, fused form only) */
     int tri_strength;     /* prism triangle quadrature strength (0 = 8); collapsed k x k rule, k = strength/2 + 1 */
     int prec;             /* fr_precision */
     int rusanov_mode;     /* 0: wave speed max(|vL.n|+cL, |vR.n|+cR) (the only mode implemented) */
@@ -99,8 +101,13 @@ typedef struct {
                            * evolves the reduced energy E - H0 rho (H0 = gamma p_ref/((gamma-1) rho_ref))
                            * in FP32 and the mass equation in FP64, then returns R_E = R_(E-H0 rho) +
                            * H0 R_rho. All of it is exact in exact arithmetic; it removes the
-                           * O(1/M^2) cancellations of low-Mach flows from the FP32 rounding. Hex-only
-                           * handles, fused form; ignored in FP64. */
+                           * O(1/M^2) cancellations of low-Mach flows from the FP32 rounding. Fused
+                           * form, hexahedra and prisms; ignored in FP64. */
+    int surface_aa;       /* 1: surface-flux anti-aliasing as well (Sec. 2.2.1: the interface flux points
+                           * are replaced by the m x m Gauss-Legendre points of each face, m = nq1d; the
+                           * common flux is evaluated there and lifted through the face L2 projection).
+                           * Single-instance hexahedral meshes, FP64 or FP32 without the low-Mach form,
+                           * fused form. 0: flux points are the n x n solution-point traces. */
 } fr_params;
 
 /* Host description of one mesh instance (copied by fr_mesh_create). */

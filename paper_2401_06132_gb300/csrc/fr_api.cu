@@ -116,6 +116,12 @@ struct fr_mesh {
     cudaStream_t graph_stream = nullptr;
     int graph_form = -1;
     int hex_tc = 0;                      // mixed forms: hexahedral plane contractions on the tensor cores
+    // surface-flux anti-aliasing: face quadrature points (m x m per hex face) as interface points
+    bool surf = false;
+    long long nqf = 0;                   // face quadrature points of the handle
+    std::vector<uint32_t> qpartner_host;
+    uint32_t *d_qpartner = nullptr;
+    void *d_UFQ = nullptr, *d_FVQ = nullptr;
 };
 
 // Kernel ids for timing: 0..2 fused phases A, B, C; 10+k unfused kernel k (1..13); 30 RK4 update.
@@ -171,6 +177,25 @@ static void hex_ref_fpts(const frb::Hex1D &h, std::vector<double> &xf)
                 X[d] = (f & 1) ? 1.0 : -1.0;
                 X[t1] = h.x[a];
                 X[t2] = h.x[b];
+            }
+    }
+}
+
+// Reference face quadrature points of a hexahedron: m x m GL points per face, same ordering as
+// the flux points (local index a + m b over the face's two tangential directions).
+static void hex_ref_qpts(int mq, std::vector<double> &xq)
+{
+    double x[FR_MAXM], w[FR_MAXM];
+    frb::gauss_legendre(mq, x, w);
+    xq.assign((size_t)6 * mq * mq * 3, 0.0);
+    for (int f = 0; f < 6; f++) {
+        int d = f / 2, t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+        for (int b = 0; b < mq; b++)
+            for (int a = 0; a < mq; a++) {
+                double *X = &xq[((size_t)f * mq * mq + a + mq * b) * 3];
+                X[d] = (f & 1) ? 1.0 : -1.0;
+                X[t1] = x[a];
+                X[t2] = x[b];
             }
     }
 }
@@ -381,6 +406,35 @@ static fr_status match_instance(fr_mesh *m, int ii, int b0, int b1, const fr_mes
             partner[gb] = (uint32_t)ga | (aL ? 0u : FR_LFLAG);
         }
         m->npair += n2;
+        if (m->surf) {
+            // the same face pair on the m x m face quadrature points (single hexahedral block)
+            const int mq = BA.m, q2 = mq * mq;
+            static thread_local std::vector<double> refq;
+            if ((int)refq.size() != 6 * q2 * 3) hex_ref_qpts(mq, refq);
+            std::vector<double> qa(q2 * 3), qb(q2 * 3);
+            for (int t = 0; t < q2; t++) {
+                affine_point(JA, &refq[((size_t)A.face * q2 + t) * 3], &qa[t * 3]);
+                affine_point(JB, &refq[((size_t)Bf.face * q2 + t) * 3], &qb[t * 3]);
+            }
+            auto qkey = std::make_tuple(-1, A.face, -1, Bf.face);
+            std::vector<int> &qperm = perm_cache[qkey];
+            bool qok = (int)qperm.size() == q2;
+            for (int t = 0; qok && t < q2; t++) qok = pdist2(&qa[t * 3], &qb[qperm[t] * 3], d->period) < tol2;
+            if (!qok) {
+                qperm.assign(q2, -1);
+                for (int t = 0; t < q2; t++) {
+                    for (int u = 0; u < q2; u++)
+                        if (pdist2(&qa[t * 3], &qb[u * 3], d->period) < tol2) { qperm[t] = u; break; }
+                    if (qperm[t] < 0) return fail(FR_EMESH, "face quadrature point of element %lld face %d has no partner", A.elem, A.face);
+                }
+            }
+            for (int t = 0; t < q2; t++) {
+                long long ga = A.le * 6 * q2 + (long long)A.face * q2 + t;
+                long long gb = Bf.le * 6 * q2 + (long long)Bf.face * q2 + qperm[t];
+                m->qpartner_host[ga] = (uint32_t)gb | (aL ? FR_LFLAG : 0u);
+                m->qpartner_host[gb] = (uint32_t)ga | (aL ? 0u : FR_LFLAG);
+            }
+        }
     }
     return FR_OK;
 }
@@ -446,6 +500,13 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
             return fail(FR_EUNSUPPORTED, "instance %d: order %d with %d quadrature points", ii, P.p, m1);
         if (m1 == P.p + 1 && d && d->n_pri > 0)
             return fail(FR_EUNSUPPORTED, "instance %d: prisms are built with flux anti-aliasing only", ii);
+        if (P.surface_aa) {
+            if (n_inst != 1 || !d || d->n_pri > 0 || m1 != P.p + 2)
+                return fail(FR_EUNSUPPORTED, "surface-flux anti-aliasing runs single-instance hexahedral meshes with m = p + 2");
+            if (P.prec != FR_FP64 && P.p_ref > 0 && P.rho_ref > 0)
+                return fail(FR_EUNSUPPORTED, "surface-flux anti-aliasing runs without the low-Mach form");
+            m->surf = true;
+        }
         if (!(P.gamma > 1.0) || !(P.Pr > 0.0) || P.mu < 0.0 || P.tau < 0.0 || !(P.p_ref == P.p_ref) ||
             !(P.rho_ref >= 0.0))
             return fail(FR_EINVAL, "instance %d: bad physical parameters", ii);
@@ -498,6 +559,12 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
     bfirst.push_back((int)m->blocks.size());
     if (f >= (long long)FR_LFLAG) return fail(FR_EUNSUPPORTED, "more than 2^31 flux points");
     partner.assign((size_t)f, 0xffffffffu);
+    if (m->surf) {
+        const Block &B = m->blocks[0];
+        m->nqf = B.ne * 6LL * B.m * B.m;
+        if (m->nqf >= (long long)FR_LFLAG) return fail(FR_EUNSUPPORTED, "more than 2^31 face quadrature points");
+        m->qpartner_host.assign((size_t)m->nqf, 0xffffffffu);
+    }
     for (int ii = 0; ii < n_inst; ii++) {
         fr_status st = match_instance(m, ii, bfirst[ii], bfirst[ii + 1], inst[ii], partner);
         if (st != FR_OK) return st;
@@ -734,7 +801,15 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
     }
     if (!st) st = (m->prec == FR_FP64) ? build_groups<double>(m, partner) : build_groups<float>(m, partner);
     // FP64 hexahedral handles evaluate each interface pair once (split interface phase)
-    m->split_c = (m->prec == FR_FP64) && !m->has_pri;
+    m->split_c = (m->prec == FR_FP64) && !m->has_pri && !m->surf;
+    if (!st && m->surf) {
+        st = dalloc(m, (void **)&m->d_qpartner, m->qpartner_host.size() * sizeof(uint32_t));
+        if (!st && cudaMemcpy(m->d_qpartner, m->qpartner_host.data(), m->qpartner_host.size() * sizeof(uint32_t),
+                              cudaMemcpyHostToDevice) != cudaSuccess)
+            st = fail(FR_ECUDA, "face quadrature partner upload failed");
+        if (!st) st = dalloc(m, &m->d_UFQ, (size_t)5 * m->nqf * ts);
+        if (!st) st = dalloc(m, &m->d_FVQ, (size_t)4 * m->nqf * ts);
+    }
     if (!st && m->split_c) st = dalloc(m, &m->d_DF, (size_t)5 * m->nfpt * ts);
     if (!st) st = dalloc(m, (void **)&m->d_partner, partner.size() * sizeof(uint32_t));
     if (!st && cudaMemcpy(m->d_partner, partner.data(), partner.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -756,7 +831,8 @@ extern "C" fr_status fr_destroy(fr_mesh *m)
     if (!m) return FR_OK;
     void **bufs[] = {&m->d_fnrm, (void **)&m->d_fnrm64, &m->d_geo64, (void **)&m->d_MF, (void **)&m->d_RL, &m->d_priops, &m->d_priops64, &m->d_geo, (void **)&m->d_partner, &m->d_UF, &m->d_FV, &m->d_CF, &m->d_QF, &m->d_DF, &m->d_Qu,
                      &m->d_UQ, &m->d_QQ, &m->d_Rt, &m->d_rk_k, &m->d_rk_us, (void **)&m->d_rk_acc, &m->d_io_U,
-                     &m->d_io_R, (void **)&m->d_wsum, (void **)&m->d_status, &m->d_Qsnap};
+                     &m->d_io_R, (void **)&m->d_wsum, (void **)&m->d_status, &m->d_Qsnap, (void **)&m->d_qpartner,
+                     &m->d_UFQ, &m->d_FVQ};
     for (void **b : bufs) dfree(*b);
     for (Group &g : m->groups) {
         dfree(g.d_geo); dfree((void *&)g.d_eu0); dfree((void *&)g.d_ef0); dfree((void *&)g.d_eph); dfree(g.d_phtab);
@@ -854,6 +930,14 @@ static HexArgs<T> make_args(fr_mesh *m, const Block &b, const void *U, void *R)
     if (b.type == 0 && !m->hex_tc) a.tcmode = 0;
     a.aa_off = b.m == b.p + 1;
     if (a.aa_off) a.tcmode = 0;
+    if (m->surf) {
+        a.surf = 1;
+        a.qpartner = m->d_qpartner;
+        a.UFQ = reinterpret_cast<T *>(m->d_UFQ);
+        a.FVQ = reinterpret_cast<T *>(m->d_FVQ);
+        a.nqf = m->nqf;
+        a.tcmode = 0;
+    }
     return a;
 }
 
@@ -861,8 +945,8 @@ static fr_status ensure_unfused(fr_mesh *m)
 {
     if (m->blocks.size() != 1 || m->blocks[0].type != 0)
         return fail(FR_EUNSUPPORTED, "the unfused form runs single-instance hexahedral meshes");
-    if (m->blocks[0].m != m->blocks[0].p + 2)
-        return fail(FR_EUNSUPPORTED, "the unfused form runs the anti-aliased discretisation only");
+    if (m->blocks[0].m != m->blocks[0].p + 2 || m->surf)
+        return fail(FR_EUNSUPPORTED, "the unfused form runs the flux-anti-aliased discretisation only");
     const Block &b = m->blocks[0];
     size_t ts = tsize(m->prec);
     long long nq = (long long)b.m * b.m * b.m;

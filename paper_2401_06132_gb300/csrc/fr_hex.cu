@@ -467,10 +467,11 @@ __device__ __forceinline__ void project_5(const HexOps<T> &op, const T *src, T *
     __syncthreads();
 }
 
-template <typename T, int P, int NT, int TCM = 0, bool AA = true>
+template <typename T, int P, int NT, int TCM = 0, bool AA = true, bool SURF = false>
 __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
 {
     static_assert(AA || TCM == 0, "the collocation form has no interpolation or projection");
+    static_assert(!SURF || (AA && TCM == 0), "surface-flux anti-aliasing runs with flux anti-aliasing on the CUDA cores");
     using S = HexSmem<T, P>;
     using TC = HexTc<P>;
     static_assert(TCM == 0 || (NT == 128 && std::is_same<T, float>::value), "tensor-core form: FP32, one warpgroup");
@@ -596,6 +597,65 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
         //    The LDG flux weighs the two sides by 1/2 + beta (L) and 1/2 - beta (R); a side whose
         //    weight is exactly zero (beta = +-1/2) is not evaluated. The needed points are compacted
         //    so that whole warps do the work.
+        if constexpr (SURF) {
+            // surface-flux anti-aliasing: the face solution and the own-normal viscous flux at the
+            // m x m quadrature points of each face, interpolated in-plane from the n x n traces
+            T *tr = s_w;   // [face][field 0..19][n^2] (free until step 6; s_q follows s_u)
+            __syncthreads();   // the physical gradient (step 4) is complete
+            for (int it = threadIdx.x; it < 6 * 20 * N * N; it += NT) {
+                const int f = it / (20 * N * N), r = it % (20 * N * N), fld = r / (N * N), loc = r % (N * N);
+                int base, stride;
+                face_line_p<N, XS, PS>(f, loc, base, stride);
+                const T *l = (f & 1) ? op.lR : op.lL;
+                const T *src = s_u + fld * FS + base;
+                T v = T(0);
+#pragma unroll
+                for (int i = 0; i < N; i++) v += l[i] * src[i * stride];
+                tr[it] = v;
+            }
+            __syncthreads();
+            for (int it = threadIdx.x; it < 6 * M * M; it += NT) {
+                const int f = it / (M * M), t = it % (M * M), qa = t % M, qb = t / M;
+                const long long gq = e * 6LL * M * M + it;
+                const bool isL = (a.qpartner[gq] & FR_LFLAG) != 0;
+                const T wgt = isL ? T(0.5) + ph.beta : T(0.5) - ph.beta;
+                const T *tf = tr + f * 20 * N * N;
+                T w2[N * N];
+#pragma unroll
+                for (int k = 0; k < N; k++)
+#pragma unroll
+                    for (int j = 0; j < N; j++) w2[j + N * k] = op.B[qa][j] * op.B[qb][k];
+                T uf[5];
+#pragma unroll
+                for (int alpha = 0; alpha < 5; alpha++) {
+                    T v = T(0);
+#pragma unroll
+                    for (int q = 0; q < N * N; q++) v += w2[q] * tf[alpha * N * N + q];
+                    uf[alpha] = v;
+                    a.UFQ[alpha * a.nqf + gq] = v;
+                }
+                if (wgt == T(0)) {
+#pragma unroll
+                    for (int k = 0; k < 4; k++) a.FVQ[k * a.nqf + gq] = T(0);
+                    continue;
+                }
+                T qf[5][3];
+#pragma unroll
+                for (int c = 0; c < 15; c++) {
+                    T v = T(0);
+#pragma unroll
+                    for (int q = 0; q < N * N; q++) v += w2[q] * tf[(5 + c) * N * N + q];
+                    qf[c / 3][c % 3] = v;
+                }
+                T n[3], mag;
+                face_nrm<T, T>(a.fnrm, e, f, n, mag);
+                T fvn[4];
+                viscous_normal_flux(ph, uf, qf, n, fvn);
+#pragma unroll
+                for (int k = 0; k < 4; k++) a.FVQ[k * a.nqf + gq] = fvn[k];
+            }
+            __syncthreads();
+        } else {
         if (threadIdx.x == 0) s_cnt = 0;
         __syncthreads();
         for (int s = threadIdx.x; s < NF; s += NT) {
@@ -641,6 +701,7 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
 #pragma unroll
             for (int k = 0; k < 4; k++) a.FV[k * a.nfpt + gf0 + s] = fvn[k];
         }
+        }   // surface-flux anti-aliasing or not
         if constexpr (std::is_same<T, float>::value) {
             // low-Mach form: volume part of R~_rho in FP64 (the mass flux rho v is a polynomial of
             // the solution space, so its L2 projection is itself: no quadrature points needed)
@@ -969,6 +1030,75 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
 }
 
 // ---------------------------------------------------------------------------------------------
+// Interface phase with surface-flux anti-aliasing: the common flux at the m x m quadrature points
+// of each own face (the pair's L/R roles, as k_fused_C), its L2 projection to the n x n face points
+// (Pj (x) Pj, which makes the DG lift of the quadrature-point data the n x n lift of the projected
+// data), then the lift and scaling of k_fused_C.
+// ---------------------------------------------------------------------------------------------
+template <typename T, int P, int NT>
+__global__ void __launch_bounds__(NT) k_surf_C(HexArgs<T> a)
+{
+    constexpr int N = P + 1, M = P + 2, NU = N * N * N, NF = 6 * N * N, NQF = 6 * M * M;
+    __shared__ T s_dq[5 * NQF];
+    __shared__ T s_d[5 * NF];
+    const HexOps<T> &op = OPS<T>(P - 2);
+    for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
+        const Geo<T> g = a.geo[e];
+        const Phys<T> ph = elem_phys(a, e);
+        bool ok = true;
+        for (int s = threadIdx.x; s < NQF; s += NT) {
+            const int f = s / (M * M);
+            const long long og = e * NQF + s;
+            const uint32_t pc = a.qpartner[og];
+            const bool isL = (pc & FR_LFLAG) != 0;
+            const long long pg = pc & ~FR_LFLAG;
+            T uo[5], up[5], fvo[4], fvp[4];
+#pragma unroll
+            for (int k = 0; k < 5; k++) { uo[k] = a.UFQ[k * a.nqf + og]; up[k] = a.UFQ[k * a.nqf + pg]; }
+#pragma unroll
+            for (int k = 0; k < 4; k++) { fvo[k] = a.FVQ[k * a.nqf + og]; fvp[k] = a.FVQ[k * a.nqf + pg]; }
+            T n[3], mag;
+            face_nrm<T, T>(a.fnrm, e, f, n, mag);
+            T nL[3] = {isL ? n[0] : -n[0], isL ? n[1] : -n[1], isL ? n[2] : -n[2]};
+            T F[5];
+            ok &= isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
+            const T sc = isL ? mag : -mag;
+#pragma unroll
+            for (int k = 0; k < 5; k++) s_dq[k * NQF + s] = sc * F[k];
+        }
+        flag_status(a.status, ok);
+        __syncthreads();
+        for (int it = threadIdx.x; it < 5 * NF; it += NT) {   // (alpha, face, i + N j)
+            const int alpha = it / NF, r = it % NF, f = r / (N * N), loc = r % (N * N), i = loc % N, j = loc / N;
+            const T *D = s_dq + alpha * NQF + f * M * M;
+            T v = T(0);
+#pragma unroll
+            for (int b = 0; b < M; b++) {
+                T w = T(0);
+#pragma unroll
+                for (int qa = 0; qa < M; qa++) w += op.Pj[i][qa] * D[qa + M * b];
+                v += op.Pj[j][b] * w;
+            }
+            s_d[it] = v;
+        }
+        __syncthreads();
+        T *R = a.R + elem_u0(a, e, NU);
+        const T idet = T(-1) / g.det;
+        for (int it = threadIdx.x; it < 5 * NU; it += NT) {
+            const int alpha = it / NU, z = it % NU, i = z % N, j = (z / N) % N, k = z / (N * N);
+            const T *D = s_d + alpha * NF;
+            T v = R[it];
+            v += op.liftL[i] * D[0 * N * N + j + N * k] + op.liftR[i] * D[1 * N * N + j + N * k];
+            v += op.liftL[j] * D[2 * N * N + i + N * k] + op.liftR[j] * D[3 * N * N + i + N * k];
+            v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
+            if (a.rkstage == 0) R[it] = v * idet;
+            else rk_fold(a, elem_u0(a, e, NU) + it, v * idet);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
 // Split interface phase: C1 common flux once per pair, C2 lift
 // ---------------------------------------------------------------------------------------------
 template <typename T, int P>
@@ -1290,7 +1420,7 @@ static int grid_elems(long long ne, int per_sm)
     return (int)(g < 1 ? 1 : g);
 }
 
-template <typename T, int P, int NT, bool AA = true>
+template <typename T, int P, int NT, bool AA = true, bool SURF = false>
 static void launch_B(const HexArgs<T> &a, cudaStream_t s)
 {
     using S = HexSmem<T, P>;
@@ -1298,10 +1428,10 @@ static void launch_B(const HexArgs<T> &a, cudaStream_t s)
     const size_t smem = (AA ? S::SIZE : 20 * S::FS + 5 * S::NF) * sizeof(T);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_fused_B<T, P, NT, 0, AA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_fused_B<T, P, NT, 0, AA, SURF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    k_fused_B<T, P, NT, 0, AA><<<grid_elems(a.ne, 8), NT, smem, s>>>(a);
+    k_fused_B<T, P, NT, 0, AA, SURF><<<grid_elems(a.ne, 8), NT, smem, s>>>(a);
 }
 
 // Tensor-core form of the volume kernel (FP32, 128 threads, persistent: at most as many CTAs as
@@ -1353,6 +1483,12 @@ static int fused_phase(int phase, const HexArgs<T> &a, cudaStream_t s, int varia
             }
         }
         // launch shape chosen by the autotuner: 64, 128 or 256 threads per element
+        if (a.surf) {
+            if (variant == 0) launch_B<T, P, 64, true, true>(a, s);
+            else if (variant == 2) launch_B<T, P, 256, true, true>(a, s);
+            else launch_B<T, P, 128, true, true>(a, s);
+            return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+        }
         if (a.aa_off) {
             if (variant == 0) launch_B<T, P, 64, false>(a, s);
             else if (variant == 2) launch_B<T, P, 256, false>(a, s);
@@ -1363,7 +1499,8 @@ static int fused_phase(int phase, const HexArgs<T> &a, cudaStream_t s, int varia
         else if (variant == 2) launch_B<T, P, 256>(a, s);
         else launch_B<T, P, 128>(a, s);
     } else if (phase == 2) {
-        k_fused_C<T, P, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
+        if (a.surf) k_surf_C<T, P, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
+        else k_fused_C<T, P, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
     } else if (phase == 3) {
         if (a.nlpts > 0) k_pair_flux<T, P><<<grid_for(a.nlpts, 128), 128, 0, s>>>(a);
     } else {

@@ -168,6 +168,14 @@ struct HexArgs {
     // Hexahedral volume kernel without anti-aliasing: the flux is evaluated at the solution points
     // (quadrature points = solution points, so interpolation and projection are the identity).
     int aa_off;
+    // Surface-flux anti-aliasing (single hexahedral block): m x m quadrature points per face, element
+    // e's at e * 6 m^2 + face * m^2 + a + m b; partner codes as for flux points; the face solution
+    // and own-normal viscous flux there, var-major over the nqf points.
+    int surf;
+    const uint32_t *qpartner;
+    T *UFQ;
+    T *FVQ;
+    long long nqf;
 };
 
 #ifdef __CUDACC__

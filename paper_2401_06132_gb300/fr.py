@@ -30,7 +30,8 @@ class FRError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("Pr", C.c_double), ("mu", C.c_double), ("beta", C.c_double),
                 ("tau", C.c_double), ("p", C.c_int), ("nq1d", C.c_int), ("tri_strength", C.c_int),
-                ("prec", C.c_int), ("rusanov_mode", C.c_int), ("p_ref", C.c_double), ("rho_ref", C.c_double)]
+                ("prec", C.c_int), ("rusanov_mode", C.c_int), ("p_ref", C.c_double), ("rho_ref", C.c_double),
+                ("surface_aa", C.c_int)]
 
 
 class MeshDesc(C.Structure):
@@ -93,8 +94,9 @@ def _stream_ptr(stream):
 
 
 def make_params(p=3, gamma=1.4, Pr=0.71, mu=1.0 / 1600, beta=0.5, tau=0.1, prec="fp64", nq1d=0, tri_strength=0,
-                p_ref=0.0, rho_ref=0.0):
-    return Params(gamma, Pr, mu, beta, tau, p, nq1d, tri_strength, PRECISIONS[prec], 0, p_ref, rho_ref)
+                p_ref=0.0, rho_ref=0.0, surface_aa=False):
+    return Params(gamma, Pr, mu, beta, tau, p, nq1d, tri_strength, PRECISIONS[prec], 0, p_ref, rho_ref,
+                  int(bool(surface_aa)))
 
 
 class FRMesh:

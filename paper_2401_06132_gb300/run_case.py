@@ -30,6 +30,8 @@ def main(argv=None):
     ap.add_argument("--rk4", type=int, default=0, help="RK4 steps after the RHS evaluations")
     ap.add_argument("--mach", type=float, default=0.1)
     ap.add_argument("--autotune", type=int, default=0, help="run the launch-shape autotuner first")
+    ap.add_argument("--hex-tc", type=int, default=0, help="mixed forms: hexahedral plane contractions on the tensor cores")
+    ap.add_argument("--surf", type=int, default=0, help="surface-flux anti-aliasing as well (full anti-aliasing)")
     args = ap.parse_args(argv)
 
     import numpy as np
@@ -39,8 +41,10 @@ def main(argv=None):
 
     mesh = {"hex": W.box_hex_mesh, "sheared": W.sheared_box_mesh, "mixed": W.mixed_box_mesh}[args.mesh](args.n)
     p0 = W.tgv_p0(mach=args.mach)
-    m = fr.FRMesh(mesh, fr.make_params(p=args.p, nq1d=args.nq, prec=args.prec, p_ref=p0, rho_ref=1.0 if args.lowmach else 0.0))
+    m = fr.FRMesh(mesh, fr.make_params(p=args.p, nq1d=args.nq, prec=args.prec, p_ref=p0,
+                                       rho_ref=1.0 if args.lowmach else 0.0, surface_aa=bool(args.surf)))
     m.set_form(args.form)
+    m.set_hex_tensor_cores(bool(args.hex_tc))
     blocks = []
     if mesh["hex_v"].shape[0]:
         blocks.append((mesh["hex_v"].shape[0], (args.p + 1) ** 3))
