@@ -76,7 +76,7 @@ struct fr_mesh {
     frb::Prism2D pri;                    // prism operators (p = 3)
     bool has_pri = false;
     void *d_priops = nullptr;            // PriOps<T> on the device
-    void *d_priops64 = nullptr;          // PriOps<double> (low-Mach FP32 form with prisms)
+    void *d_priops64 = nullptr;          // PriOpsFF (low-Mach FP32 form with prisms)
     std::vector<Group> groups;
     bool split_c = false;              // interface phase as pair flux (C1) + lift (C2)
     bool lowmach = false;              // FP32 low-Mach form (deviations, reduced energy, FP64 mass)
@@ -84,7 +84,7 @@ struct fr_mesh {
     double *d_MF = nullptr, *d_RL = nullptr;
     std::vector<double> fnrm_host;     // [elem][6][4] unit normal and |n_s| per face
     void *d_fnrm = nullptr;            // same in the compute precision
-    double *d_fnrm64 = nullptr;        // FP64 copy (low-Mach form)
+    double *d_fnrm64 = nullptr;        // float-float copy (low-Mach form; 8 bytes per entry)
     std::vector<double> geo_host;        // per element Ji[9], det (FP64)
     // device
     void *d_geo = nullptr;               // Geo<T>[ne]
@@ -573,11 +573,9 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
 }
 
 template <typename T>
-static fr_status upload_priops(fr_mesh *m, void **dst)
+static void fill_priops(const frb::Prism2D &P, PriOps<T> &o)
 {
-    if (!m->has_pri) return FR_OK;
-    const frb::Prism2D &P = m->pri;
-    PriOps<T> o{};
+    o = PriOps<T>{};
     for (int q = 0; q < FR_PQ; q++)
         for (int t = 0; t < FR_PT; t++) { o.Bt[q][t] = (T)P.Bt[q][t]; o.Pt[t][q] = (T)P.Pt[t][q]; }
     for (int t = 0; t < FR_PT; t++)
@@ -593,6 +591,14 @@ static fr_status upload_priops(fr_mesh *m, void **dst)
         for (int j = 0; j < FR_PE; j++) o.Dhz[k][j] = (T)P.z.Dh[k][j];
         o.lzL[k] = (T)P.z.lL[k]; o.lzR[k] = (T)P.z.lR[k]; o.liftzL[k] = (T)P.z.liftL[k]; o.liftzR[k] = (T)P.z.liftR[k];
     }
+}
+
+template <typename T>
+static fr_status upload_priops(fr_mesh *m, void **dst)
+{
+    if (!m->has_pri) return FR_OK;
+    PriOps<T> o;
+    fill_priops<T>(m->pri, o);
     fr_status st = dalloc(m, dst, sizeof(o));
     if (st) return st;
     CU(cudaMemcpy(*dst, &o, sizeof(o), cudaMemcpyHostToDevice));
@@ -656,19 +662,20 @@ template <typename T>
 static fr_status upload_face_normals(fr_mesh *m, const std::vector<long long> &order, void **dT, double **d64)
 {
     std::vector<T> t(order.size() * 24);
-    std::vector<double> t64(order.size() * 24);
+    std::vector<ff> t64(order.size() * 24);   // float-float copy for the low-Mach mass channel
     for (size_t i = 0; i < order.size(); i++)
         for (int k = 0; k < 24; k++) {
-            t64[i * 24 + k] = m->fnrm_host[(size_t)order[i] * 24 + k];
-            t[i * 24 + k] = (T)t64[i * 24 + k];
+            const double v = m->fnrm_host[(size_t)order[i] * 24 + k];
+            t64[i * 24 + k] = ff_from_double(v);
+            t[i * 24 + k] = (T)v;
         }
     fr_status st = dalloc(m, dT, t.size() * sizeof(T));
     if (st) return st;
     CU(cudaMemcpy(*dT, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice));
     if (m->lowmach) {
-        st = dalloc(m, (void **)d64, t64.size() * sizeof(double));
+        st = dalloc(m, (void **)d64, t64.size() * sizeof(ff));
         if (st) return st;
-        CU(cudaMemcpy(*d64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(*d64, t64.data(), t64.size() * sizeof(ff), cudaMemcpyHostToDevice));
     }
     return FR_OK;
 }
@@ -786,7 +793,21 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
         for (const InstanceHost &I : m->inst) all = all && I.prm.p_ref > 0 && I.prm.rho_ref > 0;
         m->lowmach = all;
     }
-    if (!st && m->lowmach) st = upload_priops<double>(m, &m->d_priops64);
+    if (!st && m->lowmach && m->has_pri) {
+        // float-float prism operators for the mass channel: hi = float(op), lo = float(op - hi)
+        PriOps<double> o64;
+        fill_priops<double>(m->pri, o64);
+        PriOpsFF pff{};
+        fill_priops<float>(m->pri, pff.hi);
+        const double *src = reinterpret_cast<const double *>(&o64);
+        const float *h = reinterpret_cast<const float *>(&pff.hi);
+        float *l = reinterpret_cast<float *>(&pff.lo);
+        static_assert(sizeof(PriOps<double>) == 2 * sizeof(PriOps<float>), "same member layout in both precisions");
+        for (size_t i = 0; i < sizeof(PriOps<float>) / sizeof(float); i++) l[i] = (float)(src[i] - (double)h[i]);
+        st = dalloc(m, &m->d_priops64, sizeof(pff));
+        if (!st && cudaMemcpy(m->d_priops64, &pff, sizeof(pff), cudaMemcpyHostToDevice) != cudaSuccess)
+            st = fail(FR_ECUDA, "prism operator upload failed");
+    }
     if (!st && m->lowmach) {
         std::vector<Geo<double>> g64((size_t)m->ne);
         for (long long e = 0; e < m->ne; e++) {
@@ -796,8 +817,8 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
         st = dalloc(m, &m->d_geo64, g64.size() * sizeof(Geo<double>));
         if (!st && cudaMemcpy(m->d_geo64, g64.data(), g64.size() * sizeof(Geo<double>), cudaMemcpyHostToDevice) != cudaSuccess)
             st = fail(FR_ECUDA, "geometry upload failed");
-        if (!st) st = dalloc(m, (void **)&m->d_MF, (size_t)m->nfpt * sizeof(double));
-        if (!st) st = dalloc(m, (void **)&m->d_RL, (size_t)(m->nU / FR_NV) * sizeof(double));
+        if (!st) st = dalloc(m, (void **)&m->d_MF, (size_t)m->nfpt * sizeof(ff));
+        if (!st) st = dalloc(m, (void **)&m->d_RL, (size_t)(m->nU / FR_NV) * sizeof(ff));
     }
     if (!st) st = (m->prec == FR_FP64) ? build_groups<double>(m, partner) : build_groups<float>(m, partner);
     // FP64 hexahedral handles evaluate each interface pair once (split interface phase)
@@ -915,10 +936,10 @@ static HexArgs<T> make_args(fr_mesh *m, const Block &b, const void *U, void *R)
     a.ph = phys_of<T>(I.prm);
     a.ph.dev = m->lowmach ? 1 : 0;
     a.geo64 = m->d_geo64 ? reinterpret_cast<const Geo<double> *>(m->d_geo64) + b.elem0 : nullptr;
-    a.MF = m->d_MF;
-    a.RL = m->d_RL;
+    a.MF = reinterpret_cast<ff *>(m->d_MF);
+    a.RL = reinterpret_cast<ff *>(m->d_RL);
     a.fnrm = m->d_fnrm ? reinterpret_cast<const T *>(m->d_fnrm) + b.elem0 * 24 : nullptr;
-    a.fnrm64 = m->d_fnrm64 ? m->d_fnrm64 + b.elem0 * 24 : nullptr;
+    a.fnrm64 = m->d_fnrm64 ? reinterpret_cast<const ff *>(m->d_fnrm64) + b.elem0 * 24 : nullptr;
     a.U = reinterpret_cast<const T *>(U); a.R = reinterpret_cast<T *>(R);
     a.UF = reinterpret_cast<T *>(m->d_UF); a.FV = reinterpret_cast<T *>(m->d_FV);
     a.CF = reinterpret_cast<T *>(m->d_CF); a.QF = reinterpret_cast<T *>(m->d_QF); a.DF = reinterpret_cast<T *>(m->d_DF);
@@ -1016,7 +1037,7 @@ static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, co
                     a.eu0 = gr.d_eu0; a.ef0 = gr.d_ef0; a.eph = gr.d_eph;
                     if (m->lowmach) a.geo64 = reinterpret_cast<const Geo<double> *>(gr.d_geo64);
                     a.fnrm = reinterpret_cast<const T *>(gr.d_fnrm);
-                    a.fnrm64 = gr.d_fnrm64;
+                    a.fnrm64 = reinterpret_cast<const ff *>(gr.d_fnrm64);
                     a.phtab = reinterpret_cast<const Phys<T> *>(gr.d_phtab);
                 }
                 a.lpts = gr.d_lpts; a.nlpts = gr.nlpts;
@@ -1025,7 +1046,7 @@ static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, co
                     a.rkus = reinterpret_cast<T *>(rk.us);
                 }
                 int lr = b.type == 0 ? hex_fused_phase<T>(b.p, ph, a, s, gr.variant)
-                                     : pri_fused_phase<T>(ph, a, reinterpret_cast<const PriOps<T> *>(m->d_priops), reinterpret_cast<const PriOps<double> *>(m->d_priops64), s);
+                                     : pri_fused_phase<T>(ph, a, reinterpret_cast<const PriOps<T> *>(m->d_priops), reinterpret_cast<const PriOpsFF *>(m->d_priops64), s);
                 if (lr) return fail(FR_ECUDA, "fused phase %d launch: %s", ph, cudaGetErrorString(cudaGetLastError()));
             }
         }
@@ -1075,10 +1096,10 @@ static fr_status autotune_impl(fr_mesh *m, const void *U, void *R, cudaStream_t 
             a.phtab = reinterpret_cast<const Phys<T> *>(gr.d_phtab);
             if (m->lowmach) a.geo64 = reinterpret_cast<const Geo<double> *>(gr.d_geo64);
             a.fnrm = reinterpret_cast<const T *>(gr.d_fnrm);
-            a.fnrm64 = gr.d_fnrm64;
+            a.fnrm64 = reinterpret_cast<const ff *>(gr.d_fnrm64);
         }
         int lr = b.type == 0 ? hex_fused_phase<T>(b.p, 0, a, s, gr.variant)
-                             : pri_fused_phase<T>(0, a, reinterpret_cast<const PriOps<T> *>(m->d_priops), reinterpret_cast<const PriOps<double> *>(m->d_priops64), s);
+                             : pri_fused_phase<T>(0, a, reinterpret_cast<const PriOps<T> *>(m->d_priops), reinterpret_cast<const PriOpsFF *>(m->d_priops64), s);
         if (lr) return fail(FR_ECUDA, "autotune: face phase launch failed");
     }
     cudaEvent_t e0, e1;
@@ -1096,7 +1117,7 @@ static fr_status autotune_impl(fr_mesh *m, const void *U, void *R, cudaStream_t 
             a.phtab = reinterpret_cast<const Phys<T> *>(gr.d_phtab);
             if (m->lowmach) a.geo64 = reinterpret_cast<const Geo<double> *>(gr.d_geo64);
             a.fnrm = reinterpret_cast<const T *>(gr.d_fnrm);
-            a.fnrm64 = gr.d_fnrm64;
+            a.fnrm64 = reinterpret_cast<const ff *>(gr.d_fnrm64);
         }
         float best = 1e30f;
         int bestv = gr.variant;

@@ -1,0 +1,74 @@
+// fr_ff.cuh -- float-float ("double-single") arithmetic for the FP64 mass channel of the low-Mach
+// FP32 form. A value is the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi)/2), about 48
+// significant bits. Built from the error-free transformations of the floating-point literature:
+// Knuth's TwoSum (exact sum of two floats), Dekker's FastTwoSum (the same when |a| >= |b|), and the
+// exact product of two floats with one fused multiply-add (Ogita, Rump and Oishi, "Accurate sum and
+// dot product", SIAM J. Sci. Comput. 26, 2005). GB300 issues FP32 about 70 times faster than FP64,
+// so these few FP32 operations per step cost less than one FP64 operation.
+#pragma once
+
+struct ff {
+    float hi, lo;
+};
+
+__host__ __device__ inline ff ff_from_double(double d)
+{
+    const float h = (float)d;
+    return ff{h, (float)(d - (double)h)};
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ ff ff_of(float a) { return ff{a, 0.0f}; }
+
+// Knuth's TwoSum: s + e = a + b exactly.
+__device__ __forceinline__ ff two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return ff{s, e};
+}
+
+// Dekker's FastTwoSum (|a| >= |b| or a = 0): s + e = a + b exactly.
+__device__ __forceinline__ ff fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// p + e = a b exactly (one fused multiply-add).
+__device__ __forceinline__ ff two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return ff{p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    ff s = two_sum(a.hi, b.hi);
+    const float t = __fadd_rn(__fadd_rn(a.lo, b.lo), s.lo);
+    return fast_two_sum(s.hi, t);
+}
+
+__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+
+// a * f for a float f
+__device__ __forceinline__ ff ff_mul_f(ff a, float f)
+{
+    ff p = two_prod(a.hi, f);
+    return fast_two_sum(p.hi, __fmaf_rn(a.lo, f, p.lo));
+}
+
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    ff p = two_prod(a.hi, b.hi);
+    const float t = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+    return fast_two_sum(p.hi, t);
+}
+
+// acc + a * b
+__device__ __forceinline__ ff ff_fma(ff a, ff b, ff acc) { return ff_add(acc, ff_mul(a, b)); }
+__device__ __forceinline__ ff ff_fma_f(ff a, float f, ff acc) { return ff_add(acc, ff_mul_f(a, f)); }
+#endif

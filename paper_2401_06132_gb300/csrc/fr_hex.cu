@@ -23,6 +23,13 @@
 __constant__ HexOps<double> c_hex64[3];  // slot p - 2
 __constant__ HexOps<float> c_hex32[3];
 
+// Float-float copies of the operators of the low-Mach form's mass channel.
+struct HexOpsFF {
+    ff lL[FR_MAXN], lR[FR_MAXN], liftL[FR_MAXN], liftR[FR_MAXN];
+    ff Dh[FR_MAXN][FR_MAXN];
+};
+__constant__ HexOpsFF c_hexff[3];
+
 template <typename T> __device__ __forceinline__ const HexOps<T> &OPS(int slot);
 template <> __device__ __forceinline__ const HexOps<double> &OPS<double>(int slot) { return c_hex64[slot]; }
 template <> __device__ __forceinline__ const HexOps<float> &OPS<float>(int slot) { return c_hex32[slot]; }
@@ -41,8 +48,15 @@ int hex_upload_ops(int p, int m, const frb::Hex1D &h)
         f.lL[i] = (float)h.lL[i]; f.lR[i] = (float)h.lR[i]; f.liftL[i] = (float)h.liftL[i];
         f.liftR[i] = (float)h.liftR[i]; f.w[i] = (float)h.w[i];
     }
+    HexOpsFF x{};
+    for (int i = 0; i < FR_MAXN; i++) {
+        x.lL[i] = ff_from_double(h.lL[i]); x.lR[i] = ff_from_double(h.lR[i]);
+        x.liftL[i] = ff_from_double(h.liftL[i]); x.liftR[i] = ff_from_double(h.liftR[i]);
+        for (int j = 0; j < FR_MAXN; j++) x.Dh[i][j] = ff_from_double(h.Dh[i][j]);
+    }
     if (cudaMemcpyToSymbol(c_hex64, &d, sizeof(d), (p - 2) * sizeof(d)) != cudaSuccess) return -2;
     if (cudaMemcpyToSymbol(c_hex32, &f, sizeof(f), (p - 2) * sizeof(f)) != cudaSuccess) return -2;
+    if (cudaMemcpyToSymbol(c_hexff, &x, sizeof(x), (p - 2) * sizeof(x)) != cudaSuccess) return -2;
     return 0;
 }
 
@@ -153,27 +167,27 @@ __global__ void __launch_bounds__(NT) k_disu_blk(HexArgs<T> a)
             a.UF[alpha * a.nfpt + elem_f0(a, e0 + el, NF) + sp] = v;
         }
         if constexpr (std::is_same<T, float>::value) {
-            // low-Mach form: own-normal mass flux n.(rho v) at every flux point, in FP64
+            // low-Mach form: own-normal mass flux n.(rho v) at every flux point, in float-float
             if (elem_phys(a, e0).dev) {
-                const HexOps<double> &o64 = OPS<double>(P - 2);
+                const HexOpsFF &off = c_hexff[P - 2];
                 for (int it = threadIdx.x; it < nb * NF; it += NT) {
                     const int el = it / NF, sp = it % NF, f = sp / (N * N);
                     int base, stride;
                     face_line<N>(f, sp % (N * N), base, stride);
-                    const double *l = (f & 1) ? o64.lR : o64.lL;
-                    double n[3], mag;
-                    face_nrm<T, double>(a.fnrm64, e0 + el, f, n, mag);
-                    double mv[3] = {0.0, 0.0, 0.0};
+                    const ff *l = (f & 1) ? off.lR : off.lL;
+                    const ff *nt = a.fnrm64 + ((e0 + el) * 6 + f) * 4;
+                    ff mf = ff_of(0.0f);
 #pragma unroll
                     for (int k = 0; k < 3; k++) {
-                        if (n[k] == 0.0) continue;   // axis-aligned faces need one component
+                        const ff nk = nt[k];
+                        if (nk.hi == 0.0f) continue;   // axis-aligned faces need one component
                         const T *u = s_u + (el * FR_NV + 1 + k) * NU + base;
-                        double v = 0.0;
+                        ff v = ff_of(0.0f);
 #pragma unroll
-                        for (int i = 0; i < N; i++) v += l[i] * (double)u[i * stride];
-                        mv[k] = v;
+                        for (int i = 0; i < N; i++) v = ff_fma_f(l[i], u[i * stride], v);
+                        mf = ff_fma(nk, v, mf);
                     }
-                    a.MF[elem_f0(a, e0 + el, NF) + sp] = n[0] * mv[0] + n[1] * mv[1] + n[2] * mv[2];
+                    a.MF[elem_f0(a, e0 + el, NF) + sp] = mf;
                 }
             }
         }
@@ -703,34 +717,38 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
         }
         }   // surface-flux anti-aliasing or not
         if constexpr (std::is_same<T, float>::value) {
-            // low-Mach form: volume part of R~_rho in FP64 (the mass flux rho v is a polynomial of
-            // the solution space, so its L2 projection is itself: no quadrature points needed)
+            // low-Mach form: volume part of R~_rho in float-float (the mass flux rho v is a
+            // polynomial of the solution space, so its L2 projection is itself: no quadrature points)
             if (dev) {
-                const HexOps<double> &o64 = OPS<double>(P - 2);
+                const HexOpsFF &off = c_hexff[P - 2];
                 const Geo<double> g64 = a.geo64[e];
+                ff cm[9];   // det J^-1, per element
+#pragma unroll
+                for (int k = 0; k < 9; k++) cm[k] = ff_from_double(g64.det * g64.Ji[k]);
+                ff *s_mf = reinterpret_cast<ff *>(s_m64);
                 for (int it = threadIdx.x; it < NU; it += NT) {
                     const int pz = it % N + XS * ((it / N) % N) + PS * (it / (N * N));
-                    const double m0 = s_u[FS + pz], m1 = s_u[2 * FS + pz], m2 = s_u[3 * FS + pz];
+                    const float m0 = s_u[FS + pz], m1 = s_u[2 * FS + pz], m2 = s_u[3 * FS + pz];
                     if (diagJ) {
-                        s_m64[it] = g64.det * g64.Ji[0] * m0;
-                        s_m64[NU + it] = g64.det * g64.Ji[4] * m1;
-                        s_m64[2 * NU + it] = g64.det * g64.Ji[8] * m2;
+                        s_mf[it] = ff_mul_f(cm[0], m0);
+                        s_mf[NU + it] = ff_mul_f(cm[4], m1);
+                        s_mf[2 * NU + it] = ff_mul_f(cm[8], m2);
                     } else {
 #pragma unroll
                         for (int d = 0; d < 3; d++)
-                            s_m64[d * NU + it] = g64.det * (g64.Ji[3 * d] * m0 + g64.Ji[3 * d + 1] * m1 + g64.Ji[3 * d + 2] * m2);
+                            s_mf[d * NU + it] = ff_add(ff_add(ff_mul_f(cm[3 * d], m0), ff_mul_f(cm[3 * d + 1], m1)), ff_mul_f(cm[3 * d + 2], m2));
                     }
                 }
                 __syncthreads();
                 const long long pbase = elem_u0(a, e, NU) / FR_NV;
                 for (int z = threadIdx.x; z < NU; z += NT) {
                     const int i = z % N, j = (z / N) % N, k = z / (N * N);
-                    double v = 0.0;
+                    ff v = ff_of(0.0f);
 #pragma unroll
                     for (int b = 0; b < N; b++) {
-                        v += o64.Dh[i][b] * s_m64[b + N * j + N * N * k];
-                        v += o64.Dh[j][b] * s_m64[NU + i + N * b + N * N * k];
-                        v += o64.Dh[k][b] * s_m64[2 * NU + i + N * j + N * N * b];
+                        v = ff_fma(off.Dh[i][b], s_mf[b + N * j + N * N * k], v);
+                        v = ff_fma(off.Dh[j][b], s_mf[NU + i + N * b + N * N * k], v);
+                        v = ff_fma(off.Dh[k][b], s_mf[2 * NU + i + N * j + N * N * b], v);
                     }
                     a.RL[pbase + z] = v;
                 }
@@ -935,7 +953,7 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
 {
     constexpr int N = P + 1, NU = N * N * N, NF = 6 * N * N;
     __shared__ T s_d[5 * NF];
-    __shared__ double s_d64[std::is_same<T, float>::value ? NF : 1];
+    __shared__ ff s_dff[std::is_same<T, float>::value ? NF : 1];   // low-Mach form: transformed mass flux
     const HexOps<T> &op = OPS<T>(P - 2);
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
         const Geo<T> g = a.geo[e];
@@ -962,13 +980,14 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
                 if (dev) {
                     float sw;
                     ok &= isL ? common_flux_dev(ph, uo, up, fvo, fvp, nL, F, sw) : common_flux_dev(ph, up, uo, fvp, fvo, nL, F, sw);
-                    // FP64 mass flux: 1/2 (mL - mR) + (s/2 + tau)(rho_L - rho_R), mX = own-normal n.(rho v)
-                    const double mo = a.MF[og], mp = a.MF[pg];
-                    const double mL = isL ? mo : mp, mR = isL ? mp : mo;
-                    const double rL = isL ? uo[0] : up[0], rR = isL ? up[0] : uo[0];
-                    const double Fr = 0.5 * (mL - mR) + (0.5 * (double)sw + (double)ph.tau) * (rL - rR);
-                    const double mag64 = a.fnrm64[(e * 6 + f) * 4 + 3];
-                    s_d64[s] = isL ? mag64 * Fr : -mag64 * Fr;
+                    // mass flux in float-float: 1/2 (mL - mR) + (s/2 + tau)(rho_L - rho_R),
+                    // mX = own-normal n.(rho v)
+                    const ff mo = a.MF[og], mp = a.MF[pg];
+                    const ff mL = isL ? mo : mp, mR = isL ? mp : mo;
+                    const float rL = isL ? uo[0] : up[0], rR = isL ? up[0] : uo[0];
+                    const ff Fr = ff_add(ff_mul_f(ff_sub(mL, mR), 0.5f), ff_mul_f(two_sum(rL, -rR), 0.5f * sw + ph.tau));
+                    const ff mag = a.fnrm64[(e * 6 + f) * 4 + 3];
+                    s_dff[s] = isL ? ff_mul(mag, Fr) : ff_neg(ff_mul(mag, Fr));
                 } else {
                     ok &= isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
                 }
@@ -995,19 +1014,23 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
                 else rk_fold(a, elem_u0(a, e, NU) + it, v * idet);
             }
         } else if constexpr (std::is_same<T, float>::value) {
-            // low-Mach form: R_rho in FP64, R_E = R_(E - H0 rho) + H0 R_rho
-            const HexOps<double> &o64 = OPS<double>(P - 2);
-            const double idet64 = -1.0 / a.geo64[e].det;
+            // low-Mach form: R_rho in float-float, R_E = R_(E - H0 rho) + H0 R_rho
+            const HexOpsFF &off = c_hexff[P - 2];
+            const ff idet64 = ff_from_double(-1.0 / a.geo64[e].det);
+            const ff H0 = ff_from_double(ph.H0d);
             const long long pbase = elem_u0(a, e, NU) / FR_NV;
             for (int z = threadIdx.x; z < NU; z += NT) {
                 const int i = z % N, j = (z / N) % N, k = z / (N * N);
-                double r = a.RL[pbase + z];
-                r += o64.liftL[i] * s_d64[0 * N * N + j + N * k] + o64.liftR[i] * s_d64[1 * N * N + j + N * k];
-                r += o64.liftL[j] * s_d64[2 * N * N + i + N * k] + o64.liftR[j] * s_d64[3 * N * N + i + N * k];
-                r += o64.liftL[k] * s_d64[4 * N * N + i + N * j] + o64.liftR[k] * s_d64[5 * N * N + i + N * j];
-                const double Rrho = r * idet64;
+                ff r = a.RL[pbase + z];
+                r = ff_fma(off.liftL[i], s_dff[0 * N * N + j + N * k], r);
+                r = ff_fma(off.liftR[i], s_dff[1 * N * N + j + N * k], r);
+                r = ff_fma(off.liftL[j], s_dff[2 * N * N + i + N * k], r);
+                r = ff_fma(off.liftR[j], s_dff[3 * N * N + i + N * k], r);
+                r = ff_fma(off.liftL[k], s_dff[4 * N * N + i + N * j], r);
+                r = ff_fma(off.liftR[k], s_dff[5 * N * N + i + N * j], r);
+                const ff Rrho = ff_mul(r, idet64);
                 float out[5];
-                out[0] = (float)Rrho;
+                out[0] = Rrho.hi + Rrho.lo;
 #pragma unroll
                 for (int alpha = 1; alpha < 5; alpha++) {
                     const T *D = s_d + alpha * NF;
@@ -1017,7 +1040,8 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
                     v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
                     out[alpha] = v * idet;
                 }
-                out[4] = (float)((double)out[4] + ph.H0d * Rrho);
+                const ff e4 = ff_fma(H0, Rrho, ff_of(out[4]));
+                out[4] = e4.hi + e4.lo;
 #pragma unroll
                 for (int alpha = 0; alpha < 5; alpha++) {
                     if (a.rkstage == 0) R[alpha * NU + z] = out[alpha];

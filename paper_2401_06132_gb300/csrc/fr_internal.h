@@ -5,6 +5,7 @@
 #include <cstdint>
 
 #include "../../include/fr_gb300.h"
+#include "fr_ff.cuh"
 
 #define FR_NV 5
 #define FR_MAXN 6          // max 1D solution points (p <= 5)
@@ -82,6 +83,11 @@ struct PriOps {
     T lzL[FR_PE], lzR[FR_PE], liftzL[FR_PE], liftzR[FR_PE];
 };
 
+// Prism operators as float-float pairs: value = hi + lo (the low-Mach mass channel).
+struct PriOpsFF {
+    PriOps<float> hi, lo;
+};
+
 // Physical constants of an instance, in the compute precision.
 template <typename T>
 struct Phys {
@@ -148,11 +154,11 @@ struct HexArgs {
     // Low-Mach FP32 form (ph.dev): FP64 geometry, own-normal mass flux n.(rho v) at flux points,
     // and the volume part of R~_rho per solution point, all in FP64
     const Geo<double> *geo64;
-    double *MF;
-    double *RL;
+    ff *MF;                   // float-float (about 48 bits; FP64 rates are 1/70 of FP32 on this chip)
+    ff *RL;
     // Per element and face (6 slots; prisms use 5): unit outward normal and |n_s|, n_s = detJ J^-T n~
     const T *fnrm;            // [elem][6][4] in the compute precision
-    const double *fnrm64;     // [elem][6][4] in FP64 (low-Mach mass channel)
+    const ff *fnrm64;         // [elem][6][4] in float-float (low-Mach mass channel)
     // Split interface phase (FP64): C1 evaluates each pair once from its L point (list lpts, entries
     // element_in_launch * 256 + local flux point) into DF; C2 lifts per element.
     const uint32_t *lpts;
@@ -220,6 +226,6 @@ template <typename T> int hex_fused_phase(int p, int phase, const HexArgs<T> &a,
 // kernel: 1..13 in the paper's order (disu .. negdivconf)
 template <typename T> int hex_unfused_kernel(int p, int kernel, const HexArgs<T> &a, cudaStream_t s);
 int hex_upload_ops(int p, int m, const frb::Hex1D &h);
-// Prism kernels (fr_pri.cu); the operator tables are passed by device pointer (ops64: the FP64
-// table, used by the low-Mach FP32 form; null otherwise).
-template <typename T> int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, const PriOps<double> *ops64, cudaStream_t s);
+// Prism kernels (fr_pri.cu); the operator tables are passed by device pointer (opsff: the
+// float-float table of the low-Mach FP32 form's mass channel; null otherwise).
+template <typename T> int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, const PriOpsFF *opsff, cudaStream_t s);

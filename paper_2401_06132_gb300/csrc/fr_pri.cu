@@ -85,20 +85,26 @@ __device__ __forceinline__ T face_value_off(const PriOps<T> &op, const T *fld, i
     return v;
 }
 
-// Value at flux point s, in FP64, of a compute-precision field at solution points.
-template <typename T>
-__device__ __forceinline__ double face_value64(const PriOps<double> &op, const T *fld, int s)
+// Value at flux point s, in float-float, of an FP32 field at solution points.
+__device__ __forceinline__ ff ffop(const PriOpsFF &o, const float &hi)
 {
-    double v = 0.0;
+    // the lo part sits at the same offset in the second table
+    const float *h = &hi;
+    return ff{hi, *(reinterpret_cast<const float *>(&o.lo) + (h - reinterpret_cast<const float *>(&o.hi)))};
+}
+
+__device__ __forceinline__ ff face_value_ff(const PriOpsFF &o, const float *fld, int s)
+{
+    ff v = ff_of(0.0f);
     if (s < 20) {
         const int t = s % 10;
-        const double *l = s < 10 ? op.lzL : op.lzR;
+        const float *l = s < 10 ? o.hi.lzL : o.hi.lzR;
 #pragma unroll
-        for (int k = 0; k < NZ; k++) v += l[k] * (double)fld[t + 10 * k];
+        for (int k = 0; k < NZ; k++) v = ff_fma_f(ffop(o, l[k]), fld[t + 10 * k], v);
     } else {
         const int f = (s - 20) / 16, loc = (s - 20) % 16, a = loc % 4, b = loc / 4;
 #pragma unroll
-        for (int t = 0; t < NT_; t++) v += op.Ef[f][a][t] * (double)fld[t + 10 * b];
+        for (int t = 0; t < NT_; t++) v = ff_fma_f(ffop(o, o.hi.Ef[f][a][t]), fld[t + 10 * b], v);
     }
     return v;
 }
@@ -133,7 +139,7 @@ static_assert(16 * TC_SBO_I <= TC_A_BYTES, "interpolation rows fit the operand b
 // Low-Mach form (ph.dev, FP32): the face solution of the deviations from the reference state, and
 // the own-normal mass flux n.(rho v) at every flux point in FP64 (from the FP64 operator table).
 template <typename T>
-__global__ void __launch_bounds__(256) k_pri_disu(HexArgs<T> a, const PriOps<T> *gops, const PriOps<double> *ops64)
+__global__ void __launch_bounds__(256) k_pri_disu(HexArgs<T> a, const PriOps<T> *gops, const PriOpsFF *opsff)
 {
     __shared__ PriOps<T> op;
     load_ops<T, 256>(gops, op);
@@ -153,13 +159,15 @@ __global__ void __launch_bounds__(256) k_pri_disu(HexArgs<T> a, const PriOps<T> 
             if (dev) off = alpha == 0 ? ph.rref : (alpha == 4 ? ph.eref : T(0));
         }
         a.UF[alpha * a.nfpt + elem_f0(a, e, NF) + s] = face_value_off(op, u + alpha * NU, s, off);
-        if (dev && alpha == 0) {
-            const double *nt = a.fnrm64 + (e * 6 + face_of(s)) * 4;
-            double mf = 0.0;
+        if constexpr (sizeof(T) == 4) {
+            if (dev && alpha == 0) {
+                const ff *nt = a.fnrm64 + (e * 6 + face_of(s)) * 4;
+                ff mf = ff_of(0.0f);
 #pragma unroll
-            for (int k = 0; k < 3; k++)
-                if (nt[k] != 0.0) mf += nt[k] * face_value64(*ops64, u + (1 + k) * NU, s);
-            a.MF[elem_f0(a, e, NF) + s] = mf;
+                for (int k = 0; k < 3; k++)
+                    if (nt[k].hi != 0.0f) mf = ff_fma(nt[k], face_value_ff(*opsff, u + (1 + k) * NU, s), mf);
+                a.MF[elem_f0(a, e, NF) + s] = mf;
+            }
         }
     }
 }
@@ -210,11 +218,11 @@ __device__ __forceinline__ void pri_project_5(const PriOps<T> &op, const T *src,
 }
 
 template <typename T, int NTH, int TCM>
-__global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *gops, const PriOps<double> *ops64)
+__global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *gops, const PriOpsFF *opsff)
 {
     static_assert(TCM == 0 || (NTH == 128 && sizeof(T) == 4), "tensor-core form: FP32, one warpgroup per element");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double s_m64[sizeof(T) == 4 ? 3 * NU : 1];   // low-Mach form: transformed mass flux
+    __shared__ ff s_mf[sizeof(T) == 4 ? 3 * NU : 1];   // low-Mach form: transformed mass flux
     PriOps<T> &op = *reinterpret_cast<PriOps<T> *>(smem_raw);
     T *s_u = reinterpret_cast<T *>(smem_raw + ((sizeof(PriOps<T>) + 15) / 16) * 16);
     T *s_q = s_u + 5 * NU;
@@ -285,22 +293,28 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
             // projection is itself and the corrected divergence applies at the solution points)
             if (dev) {
                 const Geo<double> g64 = a.geo64[e];
+                ff cm[9];   // det J^-1, per element
+#pragma unroll
+                for (int k = 0; k < 9; k++) cm[k] = ff_from_double(g64.det * g64.Ji[k]);
                 for (int z = threadIdx.x; z < NU; z += NTH) {
-                    const double m0 = s_u[NU + z], m1 = s_u[2 * NU + z], m2 = s_u[3 * NU + z];
+                    const float m0 = s_u[NU + z], m1 = s_u[2 * NU + z], m2 = s_u[3 * NU + z];
 #pragma unroll
                     for (int d = 0; d < 3; d++)
-                        s_m64[d * NU + z] = g64.det * (g64.Ji[3 * d] * m0 + g64.Ji[3 * d + 1] * m1 + g64.Ji[3 * d + 2] * m2);
+                        s_mf[d * NU + z] = ff_add(ff_add(ff_mul_f(cm[3 * d], m0), ff_mul_f(cm[3 * d + 1], m1)), ff_mul_f(cm[3 * d + 2], m2));
                 }
                 __syncthreads();
-                const PriOps<double> &o64 = *ops64;
+                const PriOpsFF &o = *opsff;
                 const long long pbase = elem_u0(a, e, NU) / FR_NV;
                 for (int z = threadIdx.x; z < NU; z += NTH) {
                     const int k = z / NT_, t = z % NT_;
-                    double v = 0.0;
+                    ff v = ff_of(0.0f);
 #pragma unroll
-                    for (int j = 0; j < NT_; j++) v += o64.Dhx[t][j] * s_m64[j + 10 * k] + o64.Dhy[t][j] * s_m64[NU + j + 10 * k];
+                    for (int j = 0; j < NT_; j++) {
+                        v = ff_fma(ffop(o, o.hi.Dhx[t][j]), s_mf[j + 10 * k], v);
+                        v = ff_fma(ffop(o, o.hi.Dhy[t][j]), s_mf[NU + j + 10 * k], v);
+                    }
 #pragma unroll
-                    for (int j = 0; j < NZ; j++) v += o64.Dhz[k][j] * s_m64[2 * NU + t + 10 * j];
+                    for (int j = 0; j < NZ; j++) v = ff_fma(ffop(o, o.hi.Dhz[k][j]), s_mf[2 * NU + t + 10 * j], v);
                     a.RL[pbase + z] = v;
                 }
             }
@@ -512,11 +526,11 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
 // Phase C: interface group
 // -------------------------------------------------------------------------------------------------
 template <typename T, int NTH>
-__global__ void __launch_bounds__(NTH) k_pri_C(HexArgs<T> a, const PriOps<T> *gops, const PriOps<double> *ops64)
+__global__ void __launch_bounds__(NTH) k_pri_C(HexArgs<T> a, const PriOps<T> *gops, const PriOpsFF *opsff)
 {
     __shared__ PriOps<T> op;
     __shared__ T s_d[5 * NF];
-    __shared__ double s_d64[sizeof(T) == 4 ? NF : 1];   // low-Mach form: FP64 transformed mass flux
+    __shared__ ff s_dff[sizeof(T) == 4 ? NF : 1];   // low-Mach form: transformed mass flux (float-float)
     load_ops<T, NTH>(gops, op);
     __syncthreads();
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
@@ -544,13 +558,14 @@ __global__ void __launch_bounds__(NTH) k_pri_C(HexArgs<T> a, const PriOps<T> *go
                 if (dev) {
                     float sw;
                     ok &= isL ? common_flux_dev(ph, uo, up, fvo, fvp, nL, F, sw) : common_flux_dev(ph, up, uo, fvp, fvo, nL, F, sw);
-                    // FP64 mass flux: 1/2 (mL - mR) + (s/2 + tau)(rho_L - rho_R), mX = own-normal n.(rho v)
-                    const double mo = a.MF[og], mp = a.MF[pg];
-                    const double mL = isL ? mo : mp, mR = isL ? mp : mo;
-                    const double rL = isL ? uo[0] : up[0], rR = isL ? up[0] : uo[0];
-                    const double Fr = 0.5 * (mL - mR) + (0.5 * (double)sw + (double)ph.tau) * (rL - rR);
-                    const double mag64 = a.fnrm64[(e * 6 + face_of(s)) * 4 + 3];
-                    s_d64[s] = isL ? mag64 * Fr : -mag64 * Fr;
+                    // mass flux in float-float: 1/2 (mL - mR) + (s/2 + tau)(rho_L - rho_R),
+                    // mX = own-normal n.(rho v)
+                    const ff mo = a.MF[og], mp = a.MF[pg];
+                    const ff mL = isL ? mo : mp, mR = isL ? mp : mo;
+                    const float rL = isL ? uo[0] : up[0], rR = isL ? up[0] : uo[0];
+                    const ff Fr = ff_add(ff_mul_f(ff_sub(mL, mR), 0.5f), ff_mul_f(two_sum(rL, -rR), 0.5f * sw + ph.tau));
+                    const ff magf = a.fnrm64[(e * 6 + face_of(s)) * 4 + 3];
+                    s_dff[s] = isL ? ff_mul(magf, Fr) : ff_neg(ff_mul(magf, Fr));
                 } else {
                     ok &= isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
                 }
@@ -578,20 +593,23 @@ __global__ void __launch_bounds__(NTH) k_pri_C(HexArgs<T> a, const PriOps<T> *go
                 else rk_fold(a, elem_u0(a, e, NU) + it, v * idet);
             }
         } else if constexpr (sizeof(T) == 4) {
-            // low-Mach form: R_rho in FP64, R_E = R_(E - H0 rho) + H0 R_rho
-            const PriOps<double> &o64 = *ops64;
-            const double idet64 = -1.0 / a.geo64[e].det;
+            // low-Mach form: R_rho in float-float, R_E = R_(E - H0 rho) + H0 R_rho
+            const PriOpsFF &o = *opsff;
+            const ff idet64 = ff_from_double(-1.0 / a.geo64[e].det);
+            const ff H0 = ff_from_double(ph.H0d);
             const long long pbase = elem_u0(a, e, NU) / FR_NV;
             for (int z = threadIdx.x; z < NU; z += NTH) {
                 const int k = z / NT_, t = z % NT_;
-                double r = a.RL[pbase + z] + o64.liftzL[k] * s_d64[t] + o64.liftzR[k] * s_d64[10 + t];
+                ff r = a.RL[pbase + z];
+                r = ff_fma(ffop(o, o.hi.liftzL[k]), s_dff[t], r);
+                r = ff_fma(ffop(o, o.hi.liftzR[k]), s_dff[10 + t], r);
 #pragma unroll
                 for (int f = 0; f < 3; f++)
 #pragma unroll
-                    for (int b = 0; b < NZ; b++) r += o64.Lf[f][t][b] * s_d64[20 + 16 * f + b + 4 * k];
-                const double Rrho = r * idet64;
+                    for (int b = 0; b < NZ; b++) r = ff_fma(ffop(o, o.hi.Lf[f][t][b]), s_dff[20 + 16 * f + b + 4 * k], r);
+                const ff Rrho = ff_mul(r, idet64);
                 float out[5];
-                out[0] = (float)Rrho;
+                out[0] = Rrho.hi + Rrho.lo;
 #pragma unroll
                 for (int alpha = 1; alpha < 5; alpha++) {
                     const T *D = s_d + alpha * NF;
@@ -602,7 +620,8 @@ __global__ void __launch_bounds__(NTH) k_pri_C(HexArgs<T> a, const PriOps<T> *go
                         for (int b = 0; b < NZ; b++) v += op.Lf[f][t][b] * D[20 + 16 * f + b + 4 * k];
                     out[alpha] = v * idet;
                 }
-                out[4] = (float)((double)out[4] + ph.H0d * Rrho);
+                const ff e4 = ff_fma(H0, Rrho, ff_of(out[4]));
+                out[4] = e4.hi + e4.lo;
 #pragma unroll
                 for (int alpha = 0; alpha < 5; alpha++) {
                     if (a.rkstage == 0) R[alpha * NU + z] = out[alpha];
@@ -624,7 +643,7 @@ int grid_elems(long long ne, int per_sm)
 }  // namespace
 
 template <typename T>
-int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, const PriOps<double> *ops64, cudaStream_t s)
+int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, const PriOpsFF *ops64, cudaStream_t s)
 {
     if (a.ne == 0) return 0;
     if (phase == 0) {
@@ -669,5 +688,5 @@ int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, const 
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
-template int pri_fused_phase<double>(int, const HexArgs<double> &, const PriOps<double> *, const PriOps<double> *, cudaStream_t);
-template int pri_fused_phase<float>(int, const HexArgs<float> &, const PriOps<float> *, const PriOps<double> *, cudaStream_t);
+template int pri_fused_phase<double>(int, const HexArgs<double> &, const PriOps<double> *, const PriOpsFF *, cudaStream_t);
+template int pri_fused_phase<float>(int, const HexArgs<float> &, const PriOps<float> *, const PriOpsFF *, cudaStream_t);
