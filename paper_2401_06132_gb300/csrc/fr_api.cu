@@ -120,8 +120,9 @@ struct fr_mesh {
     bool surf = false;
     long long nqf = 0;                   // face quadrature points of the handle
     std::vector<uint32_t> qpartner_host;
-    uint32_t *d_qpartner = nullptr;
-    void *d_UFQ = nullptr, *d_FVQ = nullptr;
+    uint32_t *d_qpartner = nullptr, *d_qlpts = nullptr;
+    long long nqlpts = 0;
+    void *d_UFQ = nullptr, *d_FVQ = nullptr, *d_DQ = nullptr;
 };
 
 // Kernel ids for timing: 0..2 fused phases A, B, C; 10+k unfused kernel k (1..13); 30 RK4 update.
@@ -822,7 +823,17 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
     }
     if (!st) st = (m->prec == FR_FP64) ? build_groups<double>(m, partner) : build_groups<float>(m, partner);
     // FP64 hexahedral handles evaluate each interface pair once (split interface phase)
-    m->split_c = (m->prec == FR_FP64) && !m->has_pri && !m->surf;
+    m->split_c = ((m->prec == FR_FP64) && !m->has_pri) || m->surf;
+    if (!st && m->surf) {
+        std::vector<uint32_t> ql;
+        for (long long q = 0; q < m->nqf; q++)
+            if (m->qpartner_host[(size_t)q] & FR_LFLAG) ql.push_back((uint32_t)q);
+        m->nqlpts = (long long)ql.size();
+        st = dalloc(m, (void **)&m->d_qlpts, ql.size() * sizeof(uint32_t));
+        if (!st && cudaMemcpy(m->d_qlpts, ql.data(), ql.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+            st = fail(FR_ECUDA, "face quadrature list upload failed");
+        if (!st) st = dalloc(m, &m->d_DQ, (size_t)5 * m->nqf * ts);
+    }
     if (!st && m->surf) {
         st = dalloc(m, (void **)&m->d_qpartner, m->qpartner_host.size() * sizeof(uint32_t));
         if (!st && cudaMemcpy(m->d_qpartner, m->qpartner_host.data(), m->qpartner_host.size() * sizeof(uint32_t),
@@ -853,7 +864,7 @@ extern "C" fr_status fr_destroy(fr_mesh *m)
     void **bufs[] = {&m->d_fnrm, (void **)&m->d_fnrm64, &m->d_geo64, (void **)&m->d_MF, (void **)&m->d_RL, &m->d_priops, &m->d_priops64, &m->d_geo, (void **)&m->d_partner, &m->d_UF, &m->d_FV, &m->d_CF, &m->d_QF, &m->d_DF, &m->d_Qu,
                      &m->d_UQ, &m->d_QQ, &m->d_Rt, &m->d_rk_k, &m->d_rk_us, (void **)&m->d_rk_acc, &m->d_io_U,
                      &m->d_io_R, (void **)&m->d_wsum, (void **)&m->d_status, &m->d_Qsnap, (void **)&m->d_qpartner,
-                     &m->d_UFQ, &m->d_FVQ};
+                     &m->d_UFQ, &m->d_FVQ, (void **)&m->d_qlpts, &m->d_DQ};
     for (void **b : bufs) dfree(*b);
     for (Group &g : m->groups) {
         dfree(g.d_geo); dfree((void *&)g.d_eu0); dfree((void *&)g.d_ef0); dfree((void *&)g.d_eph); dfree(g.d_phtab);
@@ -956,7 +967,10 @@ static HexArgs<T> make_args(fr_mesh *m, const Block &b, const void *U, void *R)
         a.qpartner = m->d_qpartner;
         a.UFQ = reinterpret_cast<T *>(m->d_UFQ);
         a.FVQ = reinterpret_cast<T *>(m->d_FVQ);
+        a.DQ = reinterpret_cast<T *>(m->d_DQ);
+        a.qlpts = m->d_qlpts;
         a.nqf = m->nqf;
+        a.nqlpts = m->nqlpts;
         a.tcmode = 0;
     }
     return a;

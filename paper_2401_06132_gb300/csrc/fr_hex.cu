@@ -614,7 +614,11 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
         if constexpr (SURF) {
             // surface-flux anti-aliasing: the face solution and the own-normal viscous flux at the
             // m x m quadrature points of each face, interpolated in-plane from the n x n traces
-            T *tr = s_w;   // [face][field 0..19][n^2] (free until step 6; s_q follows s_u)
+            // (along the first face direction into s_t1, then per point along the second). A face
+            // is wholly the L or the R side of its pair; only L faces need the gradient (LDG weight
+            // 1/2 + beta; the R side's weight 1/2 - beta is zero at beta = 1/2, checked per point).
+            T *tr = s_w;    // [face][field 0..19][n^2] traces (free until step 6; s_q follows s_u)
+            T *ti = s_t1;   // [face][field][qa][k] = sum_j B[qa][j] tr[j + n k]
             __syncthreads();   // the physical gradient (step 4) is complete
             for (int it = threadIdx.x; it < 6 * 20 * N * N; it += NT) {
                 const int f = it / (20 * N * N), r = it % (20 * N * N), fld = r / (N * N), loc = r % (N * N);
@@ -628,23 +632,29 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
                 tr[it] = v;
             }
             __syncthreads();
+            for (int it = threadIdx.x; it < 6 * 20 * M * N; it += NT) {
+                const int f = it / (20 * M * N), r = it % (20 * M * N), fld = r / (M * N), qk = r % (M * N);
+                const int qa = qk % M, k = qk / M;
+                if (fld >= 5 && !(a.qpartner[e * 6LL * M * M + f * M * M] & FR_LFLAG)) continue;   // R face
+                const T *t = tr + (f * 20 + fld) * N * N + N * k;
+                T v = T(0);
+#pragma unroll
+                for (int j = 0; j < N; j++) v += op.B[qa][j] * t[j];
+                ti[it] = v;
+            }
+            __syncthreads();
             for (int it = threadIdx.x; it < 6 * M * M; it += NT) {
                 const int f = it / (M * M), t = it % (M * M), qa = t % M, qb = t / M;
                 const long long gq = e * 6LL * M * M + it;
                 const bool isL = (a.qpartner[gq] & FR_LFLAG) != 0;
                 const T wgt = isL ? T(0.5) + ph.beta : T(0.5) - ph.beta;
-                const T *tf = tr + f * 20 * N * N;
-                T w2[N * N];
-#pragma unroll
-                for (int k = 0; k < N; k++)
-#pragma unroll
-                    for (int j = 0; j < N; j++) w2[j + N * k] = op.B[qa][j] * op.B[qb][k];
+                const T *tf = ti + f * 20 * M * N + qa;
                 T uf[5];
 #pragma unroll
                 for (int alpha = 0; alpha < 5; alpha++) {
                     T v = T(0);
 #pragma unroll
-                    for (int q = 0; q < N * N; q++) v += w2[q] * tf[alpha * N * N + q];
+                    for (int k = 0; k < N; k++) v += op.B[qb][k] * tf[alpha * M * N + M * k];
                     uf[alpha] = v;
                     a.UFQ[alpha * a.nqf + gq] = v;
                 }
@@ -653,12 +663,36 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
                     for (int k = 0; k < 4; k++) a.FVQ[k * a.nqf + gq] = T(0);
                     continue;
                 }
+                if (!isL) {
+                    // an R face needs its gradient only if beta != 1/2: evaluate it from the traces
+                    const T *tr_f = tr + f * 20 * N * N;
+                    T qf[5][3];
+#pragma unroll
+                    for (int c = 0; c < 15; c++) {
+                        T v = T(0);
+#pragma unroll
+                        for (int k = 0; k < N; k++) {
+                            T w = T(0);
+#pragma unroll
+                            for (int j = 0; j < N; j++) w += op.B[qa][j] * tr_f[(5 + c) * N * N + j + N * k];
+                            v += op.B[qb][k] * w;
+                        }
+                        qf[c / 3][c % 3] = v;
+                    }
+                    T n[3], mag;
+                    face_nrm<T, T>(a.fnrm, e, f, n, mag);
+                    T fvn[4];
+                    viscous_normal_flux(ph, uf, qf, n, fvn);
+#pragma unroll
+                    for (int k = 0; k < 4; k++) a.FVQ[k * a.nqf + gq] = fvn[k];
+                    continue;
+                }
                 T qf[5][3];
 #pragma unroll
                 for (int c = 0; c < 15; c++) {
                     T v = T(0);
 #pragma unroll
-                    for (int q = 0; q < N * N; q++) v += w2[q] * tf[(5 + c) * N * N + q];
+                    for (int k = 0; k < N; k++) v += op.B[qb][k] * tf[(5 + c) * M * N + M * k];
                     qf[c / 3][c % 3] = v;
                 }
                 T n[3], mag;
@@ -1054,55 +1088,72 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
 }
 
 // ---------------------------------------------------------------------------------------------
-// Interface phase with surface-flux anti-aliasing: the common flux at the m x m quadrature points
-// of each own face (the pair's L/R roles, as k_fused_C), its L2 projection to the n x n face points
-// (Pj (x) Pj, which makes the DG lift of the quadrature-point data the n x n lift of the projected
-// data), then the lift and scaling of k_fused_C.
+// Interface phase with surface-flux anti-aliasing, split like C1/C2: the common flux once per
+// pair of face quadrature points, from its L point (list qlpts), written to both sides' slots of DQ
+// with each side's |n_s| (k_surf_pair); then per element the face L2 projection of DQ to the n x n
+// face points (Pj (x) Pj, which makes the DG lift of the quadrature-point data the n x n lift of the
+// projected data), the lift and the scaling (k_surf_lift).
 // ---------------------------------------------------------------------------------------------
+template <typename T, int P>
+__global__ void __launch_bounds__(128) k_surf_pair(HexArgs<T> a)
+{
+    constexpr int M = P + 2, NQF = 6 * M * M;
+    bool ok = true;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < a.nqlpts; it += (long long)gridDim.x * blockDim.x) {
+        const long long gl = a.qlpts[it];
+        const long long gr = a.qpartner[gl] & ~FR_LFLAG;
+        const long long eL = gl / NQF, eR = gr / NQF;
+        const int fL = (int)(gl % NQF) / (M * M), fR = (int)(gr % NQF) / (M * M);
+        const Phys<T> ph = elem_phys(a, eL);
+        T uL[5], uR[5], fvL[4], fvR[4];
+#pragma unroll
+        for (int k = 0; k < 5; k++) { uL[k] = a.UFQ[k * a.nqf + gl]; uR[k] = a.UFQ[k * a.nqf + gr]; }
+#pragma unroll
+        for (int k = 0; k < 4; k++) { fvL[k] = a.FVQ[k * a.nqf + gl]; fvR[k] = a.FVQ[k * a.nqf + gr]; }
+        T n[3], magL, nR[3], magR;
+        face_nrm<T, T>(a.fnrm, eL, fL, n, magL);
+        face_nrm<T, T>(a.fnrm, eR, fR, nR, magR);
+        T F[5];
+        ok &= common_flux(ph, uL, uR, fvL, fvR, n, F);
+#pragma unroll
+        for (int k = 0; k < 5; k++) {
+            a.DQ[k * a.nqf + gl] = magL * F[k];
+            a.DQ[k * a.nqf + gr] = -magR * F[k];
+        }
+    }
+    flag_status(a.status, ok);
+}
+
 template <typename T, int P, int NT>
-__global__ void __launch_bounds__(NT) k_surf_C(HexArgs<T> a)
+__global__ void __launch_bounds__(NT) k_surf_lift(HexArgs<T> a)
 {
     constexpr int N = P + 1, M = P + 2, NU = N * N * N, NF = 6 * N * N, NQF = 6 * M * M;
     __shared__ T s_dq[5 * NQF];
+    __shared__ T s_t[5 * 6 * N * M];
     __shared__ T s_d[5 * NF];
     const HexOps<T> &op = OPS<T>(P - 2);
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
         const Geo<T> g = a.geo[e];
-        const Phys<T> ph = elem_phys(a, e);
-        bool ok = true;
-        for (int s = threadIdx.x; s < NQF; s += NT) {
-            const int f = s / (M * M);
-            const long long og = e * NQF + s;
-            const uint32_t pc = a.qpartner[og];
-            const bool isL = (pc & FR_LFLAG) != 0;
-            const long long pg = pc & ~FR_LFLAG;
-            T uo[5], up[5], fvo[4], fvp[4];
-#pragma unroll
-            for (int k = 0; k < 5; k++) { uo[k] = a.UFQ[k * a.nqf + og]; up[k] = a.UFQ[k * a.nqf + pg]; }
-#pragma unroll
-            for (int k = 0; k < 4; k++) { fvo[k] = a.FVQ[k * a.nqf + og]; fvp[k] = a.FVQ[k * a.nqf + pg]; }
-            T n[3], mag;
-            face_nrm<T, T>(a.fnrm, e, f, n, mag);
-            T nL[3] = {isL ? n[0] : -n[0], isL ? n[1] : -n[1], isL ? n[2] : -n[2]};
-            T F[5];
-            ok &= isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
-            const T sc = isL ? mag : -mag;
-#pragma unroll
-            for (int k = 0; k < 5; k++) s_dq[k * NQF + s] = sc * F[k];
+        for (int it = threadIdx.x; it < 5 * NQF; it += NT) {
+            const int alpha = it / NQF, s = it % NQF;
+            s_dq[it] = a.DQ[alpha * a.nqf + e * NQF + s];
         }
-        flag_status(a.status, ok);
         __syncthreads();
-        for (int it = threadIdx.x; it < 5 * NF; it += NT) {   // (alpha, face, i + N j)
-            const int alpha = it / NF, r = it % NF, f = r / (N * N), loc = r % (N * N), i = loc % N, j = loc / N;
-            const T *D = s_dq + alpha * NQF + f * M * M;
+        for (int it = threadIdx.x; it < 5 * 6 * N * M; it += NT) {   // (alpha, face, i, b): along a
+            const int af = it / (N * M), r = it % (N * M), i = r % N, b = r / N;
+            const T *D = s_dq + af * M * M + M * b;
             T v = T(0);
 #pragma unroll
-            for (int b = 0; b < M; b++) {
-                T w = T(0);
+            for (int qa = 0; qa < M; qa++) v += op.Pj[i][qa] * D[qa];
+            s_t[it] = v;
+        }
+        __syncthreads();
+        for (int it = threadIdx.x; it < 5 * NF; it += NT) {   // (alpha, face, i + N j): along b
+            const int af = it / (N * N), loc = it % (N * N), i = loc % N, j = loc / N;
+            const T *t = s_t + af * N * M + i;
+            T v = T(0);
 #pragma unroll
-                for (int qa = 0; qa < M; qa++) w += op.Pj[i][qa] * D[qa + M * b];
-                v += op.Pj[j][b] * w;
-            }
+            for (int b = 0; b < M; b++) v += op.Pj[j][b] * t[N * b];
             s_d[it] = v;
         }
         __syncthreads();
@@ -1448,8 +1499,11 @@ template <typename T, int P, int NT, bool AA = true, bool SURF = false>
 static void launch_B(const HexArgs<T> &a, cudaStream_t s)
 {
     using S = HexSmem<T, P>;
-    // the collocation form needs no quadrature-point buffers
-    const size_t smem = (AA ? S::SIZE : 20 * S::FS + 5 * S::NF) * sizeof(T);
+    // the collocation form needs no quadrature-point buffers; surface-flux anti-aliasing stages its
+    // in-plane interpolation (6 faces x 20 fields x m x n values) where the sweep buffers start
+    constexpr int TI = 6 * 20 * S::M * S::N;
+    constexpr int TAIL = S::T1 + S::T2 > TI ? S::T1 + S::T2 : TI;
+    const size_t smem = (!AA ? 20 * S::FS + 5 * S::NF : (SURF ? S::SIZE - S::T1 - S::T2 + TAIL : S::SIZE)) * sizeof(T);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_fused_B<T, P, NT, 0, AA, SURF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1523,12 +1577,13 @@ static int fused_phase(int phase, const HexArgs<T> &a, cudaStream_t s, int varia
         else if (variant == 2) launch_B<T, P, 256>(a, s);
         else launch_B<T, P, 128>(a, s);
     } else if (phase == 2) {
-        if (a.surf) k_surf_C<T, P, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
-        else k_fused_C<T, P, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
+        k_fused_C<T, P, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
     } else if (phase == 3) {
-        if (a.nlpts > 0) k_pair_flux<T, P><<<grid_for(a.nlpts, 128), 128, 0, s>>>(a);
+        if (a.surf) { if (a.nqlpts > 0) k_surf_pair<T, P><<<grid_for(a.nqlpts, 128), 128, 0, s>>>(a); }
+        else if (a.nlpts > 0) k_pair_flux<T, P><<<grid_for(a.nlpts, 128), 128, 0, s>>>(a);
     } else {
-        k_lift<T, P, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
+        if (a.surf) k_surf_lift<T, P, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
+        else k_lift<T, P, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
     }
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }

@@ -181,7 +181,9 @@ struct HexArgs {
     const uint32_t *qpartner;
     T *UFQ;
     T *FVQ;
-    long long nqf;
+    T *DQ;                    // [5][nqf] transformed common flux per side
+    const uint32_t *qlpts;    // L quadrature points (one per pair)
+    long long nqf, nqlpts;
 };
 
 #ifdef __CUDACC__

@@ -32,6 +32,7 @@ def main(argv=None):
     ap.add_argument("--autotune", type=int, default=0, help="run the launch-shape autotuner first")
     ap.add_argument("--hex-tc", type=int, default=0, help="mixed forms: hexahedral plane contractions on the tensor cores")
     ap.add_argument("--surf", type=int, default=0, help="surface-flux anti-aliasing as well (full anti-aliasing)")
+    ap.add_argument("--timing", type=int, default=0, help="per-kernel times (CUDA events) of one more RHS")
     args = ap.parse_args(argv)
 
     import numpy as np
@@ -62,6 +63,12 @@ def main(argv=None):
     torch.cuda.synchronize()
     m.sync_status()
     out = {"dof": int(U0.size), "rhs_ms": ev[0].elapsed_time(ev[1]) / max(1, args.rhs), "volume_threads": tuned}
+    if args.timing:
+        m.set_timing(True)
+        m.rhs(U, R)
+        torch.cuda.synchronize()
+        out["kernel_ms"] = {str(k): round(v[0] / max(1, v[1]), 4) for k, v in m.kernel_times().items()}
+        m.set_timing(False)
     if args.rk4:
         Um = torch.from_numpy(U0).cuda()
         ev[0].record()
