@@ -52,10 +52,12 @@ POINT_FLUX_FLOPS = 150    # total flux f^e - f^v at one quadrature point
 TRANSFORM_FLOPS = 15      # detJ J^-1 f with a diagonal metric: 15 products (90 with a full 3 x 3)
 
 
-def phase_b_flops_per_element(p=P, m=MQ, one_sided=True, diagonal_metric=True):
+def phase_b_flops_per_element(p=P, m=MQ, one_sided=True, diagonal_metric=True, divergence_in_projection=True):
     """FLOPs of the volume kernel per element. With beta = +-1/2 the LDG viscous flux needs only the
     weighted side, i.e. half of the flux points on average (one_sided); axis-aligned elements apply
-    the metric as 3 products instead of 3 x 3 (diagonal_metric)."""
+    the metric as 3 products instead of 3 x 3 (diagonal_metric); the corrected divergence rides on
+    the projection's sweeps (Dh Pj in place of Pj along each flux component's own direction), so it
+    costs no separate sweep (divergence_in_projection)."""
     n = p + 1
     nu, nf, nq = n ** 3, 6 * n * n, m ** 3
     con_u = 5 * nf * 3
@@ -65,7 +67,7 @@ def phase_b_flops_per_element(p=P, m=MQ, one_sided=True, diagonal_metric=True):
     interp = 20 * 2 * (n ** 3 * m + n * n * m * m + n * m ** 3)
     tdisf = nq * (POINT_FLUX_FLOPS + TRANSFORM_FLOPS)
     proj = 15 * 2 * (m ** 3 * n + m * m * n * n + m * n ** 3)
-    div = 5 * nu * 3 * n * 2
+    div = 0 if divergence_in_projection else 5 * nu * 3 * n * 2
     return con_u + grad + jt + face + interp + tdisf + proj + div
 
 
@@ -209,7 +211,7 @@ def _time_steps(m, U, steps, warmup, torch):
 
 def other_configs(args, torch, fr, W):
     """Mixed hex/prism TGV (40^3 box: 32,000 hexes + 64,000 prisms, p = 3), the 48^3 TGV without
-    anti-aliasing, and the batched ensemble
+    anti-aliasing and with full (flux + surface-flux) anti-aliasing, and the batched ensemble
     of 64 TGV instances (edges in {8,...,24}, p in {3,4}, M in [0.05,0.2], Re in [400,3200] from
     SplitMix64(20240111)), each timed over RK4 steps on a side stream (CUDA-graph replay)."""
     out = {}
@@ -240,6 +242,17 @@ def other_configs(args, torch, fr, W):
         m.sync_status()
         out[f"aa_off48_{prec}"] = {"gdof_rhs_per_s": U0.size * RHS_PER_STEP / (ms * 1e-3) / 1e9, "ms_per_step": ms,
                                    "dof": int(U0.size), "elements": N_EDGE ** 3}
+        m.close()
+        del U
+    # ... and with full anti-aliasing (flux + surface flux), FP64 and plain FP32
+    for prec in ("fp64", "fp32"):
+        m = fr.FRMesh(mesh48, fr.make_params(p=P, prec=prec, p_ref=p0, surface_aa=True))
+        U0 = W.tgv_state(m.sol_coords(), [(N_EDGE ** 3, (P + 1) ** 3)], perturb=1e-3)
+        U = torch.from_numpy(U0).cuda()
+        ms = _time_steps(m, U, steps, 2, torch)
+        m.sync_status()
+        out[f"aa_full48_{prec}"] = {"gdof_rhs_per_s": U0.size * RHS_PER_STEP / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+                                    "dof": int(U0.size), "elements": N_EDGE ** 3}
         m.close()
         del U
     draws = W.ensemble_draws(64)

@@ -43,6 +43,11 @@ int hex_upload_ops(int p, int m, const frb::Hex1D &h)
         for (int i = 0; i < FR_MAXN; i++) { d.B[a][i] = h.B[a][i]; f.B[a][i] = (float)h.B[a][i]; }
     for (int i = 0; i < FR_MAXN; i++) {
         for (int a = 0; a < FR_MAXM; a++) { d.Pj[i][a] = h.Pj[i][a]; f.Pj[i][a] = (float)h.Pj[i][a]; }
+        for (int a = 0; a < FR_MAXM; a++) {
+            double v = 0.0;
+            for (int b = 0; b < FR_MAXN; b++) v += h.Dh[i][b] * h.Pj[b][a];
+            d.DP[i][a] = v; f.DP[i][a] = (float)v;
+        }
         for (int j = 0; j < FR_MAXN; j++) { d.Dh[i][j] = h.Dh[i][j]; f.Dh[i][j] = (float)h.Dh[i][j]; }
         d.lL[i] = h.lL[i]; d.lR[i] = h.lR[i]; d.liftL[i] = h.liftL[i]; d.liftR[i] = h.liftR[i]; d.w[i] = h.w[i];
         f.lL[i] = (float)h.lL[i]; f.lR[i] = (float)h.lR[i]; f.liftL[i] = (float)h.liftL[i];
@@ -428,6 +433,73 @@ __device__ __forceinline__ void project_all(const HexOps<T> &op, T *src, T *tmp,
         }
     }
     __syncthreads();
+}
+
+// tdivtpcorf with the corrected divergence folded into the projection: the projection of the
+// flux component along direction d uses Dh Pj instead of Pj along d, and the last (x) sweep sums
+// the three components, so R~[alpha] = sum_d Dh_d (Pj x Pj x Pj) F~[alpha][d] lands in R directly.
+// src: the 15 transformed-flux fields at the quadrature points (field alpha 3 + d, stride NQ);
+// every sweep stages its output where its input has been consumed. FP64: one direction (5 fields)
+// per pass through tmp (5 M^2 N values); FP32 (ALL): all 15 fields per pass (tmp 15 M^2 N).
+template <typename T, int P, int NT, bool ALL>
+__device__ __forceinline__ void project_div(const HexOps<T> &op, T *src, T *tmp, T *R)
+{
+    constexpr int N = P + 1, M = P + 2, NQ = M * M * M, NU = N * N * N;
+    constexpr int NG = ALL ? 3 : 1;   // directions per pass
+#pragma unroll 1
+    for (int d0 = 0; d0 < 3; d0 += NG) {
+        for (int it = threadIdx.x; it < 5 * NG * M * M; it += NT) {   // z: (direction, alpha, qa qb) -> k
+            const int g = it / (5 * M * M), r = it % (5 * M * M), alpha = r / (M * M), ab = r % (M * M);
+            const int d = d0 + g;
+            const T(*Z)[FR_MAXM] = d == 2 ? op.DP : op.Pj;
+            T u[M];
+#pragma unroll
+            for (int c = 0; c < M; c++) u[c] = src[(alpha * 3 + d) * NQ + ab + M * M * c];
+#pragma unroll
+            for (int k = 0; k < N; k++) {
+                T v = T(0);
+#pragma unroll
+                for (int c = 0; c < M; c++) v += Z[k][c] * u[c];
+                tmp[(g * 5 + alpha) * M * M * N + ab + M * M * k] = v;
+            }
+        }
+        __syncthreads();
+        for (int it = threadIdx.x; it < 5 * NG * M * N; it += NT) {   // y: (direction, alpha, qa, k) -> j
+            const int g = it / (5 * M * N), r = it % (5 * M * N), alpha = r / (M * N), r2 = r % (M * N);
+            const int qa = r2 % M, k = r2 / M, d = d0 + g;
+            const T(*Y)[FR_MAXM] = d == 1 ? op.DP : op.Pj;
+            T u[M];
+#pragma unroll
+            for (int b = 0; b < M; b++) u[b] = tmp[(g * 5 + alpha) * M * M * N + qa + M * b + M * M * k];
+#pragma unroll
+            for (int j = 0; j < N; j++) {
+                T v = T(0);
+#pragma unroll
+                for (int b = 0; b < M; b++) v += Y[j][b] * u[b];
+                src[(alpha * 3 + d) * NQ + qa + M * j + M * N * k] = v;   // over the consumed input
+            }
+        }
+        __syncthreads();
+    }
+    for (int it = threadIdx.x; it < 5 * N * N; it += NT) {   // x: (alpha, j, k), sum over d -> i
+        const int alpha = it / (N * N), jk = it % (N * N);
+        T v[N];
+#pragma unroll
+        for (int i = 0; i < N; i++) v[i] = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const T(*X)[FR_MAXM] = d == 0 ? op.DP : op.Pj;
+            T u[M];
+#pragma unroll
+            for (int q = 0; q < M; q++) u[q] = src[(alpha * 3 + d) * NQ + q + M * jk];
+#pragma unroll
+            for (int i = 0; i < N; i++)
+#pragma unroll
+                for (int q = 0; q < M; q++) v[i] += X[i][q] * u[q];
+        }
+#pragma unroll
+        for (int i = 0; i < N; i++) R[alpha * NU + i + N * jk] = v[i];
+    }
 }
 
 // Sum-factorised L2 projection of 5 fields from quadrature points (src, stride NQ) to solution
@@ -904,14 +976,13 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
         }
         flag_status(a.status, ok);
         __syncthreads();
-        // 8. tdivtpcorf, first factor: projection of the 15 transformed-flux fields (into s_q)
+        // 8. tdivtpcorf, first factor: projection of the 15 transformed-flux fields (into s_q);
+        //    on the CUDA-core paths the corrected divergence (step 9) is folded into it
+        T *R = a.R + elem_u0(a, e, NU);
         if constexpr (!AA) {
             // collocation form: the flux already sits at the solution points
-        } else if constexpr (TCM == 0 && S::WIDE) {
-            project_all<T, P, NT, XS, PS, FS>(op, s_w, s_t2, s_q);
         } else if constexpr (TCM == 0) {
-#pragma unroll 1
-            for (int c = 0; c < 3; c++) project_5<T, P, NT, XS, PS, FS>(op, s_w + 5 * c * NQ, s_t1, s_t2, s_q + 5 * c * FS);
+            project_div<T, P, NT, S::WIDE>(op, s_w, s_t2, R);
         } else {
             // x-y factor on the tensor cores: row r = f M + c holds flux component f at quadrature
             // level c on the M^2 in-plane points; then the z factor on the CUDA cores
@@ -957,8 +1028,7 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
             __syncthreads();
         }
         // 9. tdivtpcorf, second factor: R~ = sum_d Dh_d F~_d, written to R (finished in phase C)
-        T *R = a.R + elem_u0(a, e, NU);
-        for (int it = threadIdx.x; it < 5 * NU; it += NT) {
+        for (int it = threadIdx.x; (!AA || TCM != 0) && it < 5 * NU; it += NT) {
             const int alpha = it / NU, z = it % NU, i = z % N, j = (z / N) % N, k = z / (N * N);
             const T *F = s_q + alpha * 3 * FS;
             T v = T(0);

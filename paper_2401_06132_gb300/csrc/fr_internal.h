@@ -64,6 +64,7 @@ template <typename T>
 struct HexOps {
     T B[FR_MAXM][FR_MAXN];
     T Pj[FR_MAXN][FR_MAXM];
+    T DP[FR_MAXN][FR_MAXM];   // Dh Pj: projection followed by the corrected derivative
     T Dh[FR_MAXN][FR_MAXN];
     T lL[FR_MAXN], lR[FR_MAXN];
     T liftL[FR_MAXN], liftR[FR_MAXN];
