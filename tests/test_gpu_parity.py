@@ -247,10 +247,11 @@ def test_fp32_plain_form_error(p):
     assert err.max() <= 1e-3, err
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed_fp16", "mixed_bf16"])
 def test_ke_dissipation_after_100_rk4_steps(prec):
     """8^3 hex p=3 TGV, 100 RK4 steps at dt = 1e-3 on the GPU (FP64 master state; FP32 compute for
-    the reduced-precision form) against the oracle's trajectory: the kinetic-energy dissipation rate
+    the reduced-precision forms, the mixed forms with the split tensor-core products on the
+    hexahedra) against the oracle's trajectory: the kinetic-energy dissipation rate
     eps = -dE_k/dt at the final state agrees to 1e-3 relative (FP64: to 1e-9)."""
     mesh = W.box_hex_mesh(8)
     p0 = W.tgv_p0()
@@ -259,6 +260,7 @@ def test_ke_dissipation_after_100_rk4_steps(prec):
     Uo = o.rk4(U, 1e-3, 100)
     eps_o = o.diagnostics(Uo, o.rhs(Uo))["eps"]
     m = fr.FRMesh(mesh, fr.make_params(p=3, prec=prec, p_ref=p0, rho_ref=1.0))
+    m.set_hex_tensor_cores(True)
     Ud = torch.from_numpy(U).cuda()
     m.rk4_step(Ud, 1e-3, 100)
     m.sync_status()
@@ -582,3 +584,36 @@ def test_full_anti_aliasing_rk4_matches_oracle():
     d = np.abs(Ud.cpu().numpy() - Uo).max() / np.abs(Uo).max()
     print(f"full AA RK4: {d:.3e}")
     assert d <= 1e-13, d
+
+
+def test_precision_sweep_ke_dissipation_32cubed_p4():
+    """The precision sweep's trajectory part: 32^3 hex p=4 with 6^3 quadrature, 100 RK4 steps at
+    dt = 2e-4 from the perturbed TGV in every form. The FP64 trajectory (itself pinned to the oracle
+    by the RHS and RK4 parity tests) is the reference at this size, where 400 oracle RHS evaluations
+    would take minutes; each reduced-precision form's kinetic-energy dissipation rate at the final
+    state, evaluated by the FP64 RHS, agrees with it to 1e-3 relative."""
+    N, p = 32, 4
+    mesh = W.box_hex_mesh(N)
+    p0 = W.tgv_p0()
+    m64 = fr.FRMesh(mesh, fr.make_params(p=p, p_ref=p0))
+    U0 = W.tgv_state(m64.sol_coords(), [(N ** 3, (p + 1) ** 3)], perturb=1e-3)
+
+    def final_eps(prec, rho_ref, hex_tc):
+        m = fr.FRMesh(mesh, fr.make_params(p=p, prec=prec, p_ref=p0, rho_ref=rho_ref))
+        m.set_hex_tensor_cores(hex_tc)
+        Ud = torch.from_numpy(U0).cuda()
+        m.rk4_step(Ud, 2e-4, 100)
+        m.sync_status()
+        Rd = torch.empty_like(Ud)
+        m64.rhs(Ud, Rd)
+        m64.sync_status()
+        return m64.diagnostics(Ud, Rd)[0]["eps"]
+
+    ref = final_eps("fp64", 0.0, False)
+    res = {}
+    for name, prec, rr, tc in (("fp32_lowmach", "fp32", 1.0, False), ("fp32_plain", "fp32", 0.0, False),
+                               ("mixed_fp16", "mixed_fp16", 1.0, True), ("mixed_bf16", "mixed_bf16", 1.0, True)):
+        res[name] = abs(final_eps(prec, rr, tc) / ref - 1.0)
+    print(f"precision sweep 32^3 p=4, eps after 100 steps: fp64 {ref:.9e}; relative errors {res}")
+    for k, v in res.items():
+        assert v <= 1e-3, (k, v)
