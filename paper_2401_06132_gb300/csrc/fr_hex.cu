@@ -591,6 +591,17 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
     const HexOps<T> &op = OPS<T>(P - 2);
     uint32_t tmem = 0, parity = 0;
     bool tc_fail = false;
+    // The next element's state is fetched by the bulk-copy engine while this element computes: the
+    // copy goes into s_c (free from the gradient step on) and lands on s_ubar. Needs the tile to be
+    // a whole number of 16-byte units (p = 3) and 16-byte aligned in memory (checked per element).
+    constexpr bool TMA_U = (5 * NU * sizeof(T)) % 16 == 0 && 5 * NF >= 5 * NU;
+    __shared__ uint64_t s_ubar;
+    bool pending = false;
+    uint32_t uparity = 0;
+    if constexpr (TMA_U) {
+        if (threadIdx.x == 0) tc::mbar_init(&s_ubar, 1);
+        __syncthreads();
+    }
     if constexpr (TCM != 0) {
         tc::setup(s_mbar, s_tmem, TC::COLS);
         // operator blocks [hi | hi | lo] from the FP64 1D operators
@@ -628,14 +639,31 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
         // 1. load the element's solution (deviations from the reference state in the low-Mach form)
         bool dev = false;
         if constexpr (std::is_same<T, float>::value) dev = ph.dev != 0;
+        const T *usrc = U;
+        if constexpr (TMA_U) {
+            if (pending) {
+                const bool landed = tc::mbar_wait(&s_ubar, uparity);
+                uparity ^= 1;
+                pending = false;
+                if (__syncthreads_and(landed)) {
+                    usrc = s_c;
+                } else {
+                    // the copy did not land within the bound: report it, give it one more bounded
+                    // wait, and read the state from global memory
+                    if (threadIdx.x == 0) atomicOr(a.status, 2);
+                    tc::mbar_wait(&s_ubar, uparity ^ 1);
+                }
+            }
+        }
         for (int it = threadIdx.x; it < 5 * NU; it += NT) {
-            T v = U[it];
+            T v = usrc[it];
             if constexpr (std::is_same<T, float>::value) {
                 if (dev) v -= (it < NU) ? ph.rref : (it >= 4 * NU ? ph.eref : T(0));
             }
             const int alpha = it / NU, z = it % NU;
             s_u[alpha * FS + z % N + XS * ((z / N) % N) + PS * (z / (N * N))] = v;
         }
+        if constexpr (TMA_U) __syncthreads();   // s_c is overwritten next
         // 2. con_u: common solution at own flux points, C = (1/2 - beta) uL + (1/2 + beta) uR
         for (int it = threadIdx.x; it < 5 * NF; it += NT) {
             const int alpha = it / NF, s = it % NF;
@@ -664,7 +692,19 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
                 s_q[(alpha * 3 + d) * FS + base + i * stride] = v;
             }
         }
+        if constexpr (TMA_U) tc::fence_async_smem();   // s_c's reads before the copy that overwrites it
         __syncthreads();
+        if constexpr (TMA_U) {
+            // prefetch the next element's state into s_c
+            const long long en = e + gridDim.x;
+            if (en < a.ne) {
+                const T *Un = a.U + elem_u0(a, en, NU);
+                if ((reinterpret_cast<uintptr_t>(Un) & 15) == 0) {
+                    if (threadIdx.x == 0) tc::bulk_g2s(s_c, Un, 5 * NU * sizeof(T), &s_ubar);
+                    pending = true;
+                }
+            }
+        }
         // 4. gradcoru: q = J^-T q~ (per point, all three components; diagonal J^-1 is common)
         const bool diagJ = g.Ji[1] == T(0) && g.Ji[2] == T(0) && g.Ji[3] == T(0) && g.Ji[5] == T(0) &&
                            g.Ji[6] == T(0) && g.Ji[7] == T(0);

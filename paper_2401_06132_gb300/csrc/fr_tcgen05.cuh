@@ -1,6 +1,7 @@
-// fr_tcgen05.cuh -- inline-PTX wrappers for the fifth-generation tensor cores of sm_100a/sm_103a:
-// tensor-memory (TMEM) allocation, shared-memory matrix descriptors, kind::f16 MMA issue by one
-// thread, completion through an mbarrier (bounded wait), and TMEM loads back to registers.
+// fr_tcgen05.cuh -- inline-PTX wrappers for the Blackwell asynchronous units of sm_100a/sm_103a:
+// the fifth-generation tensor cores (tensor-memory allocation, shared-memory matrix descriptors,
+// kind::f16 MMA issue by one thread, completion through an mbarrier, TMEM loads back to registers)
+// and the bulk-copy (TMA) engine (global -> shared copies that complete on an mbarrier).
 //
 // Operand layout used throughout: K-major, no swizzle. A matrix of R rows x K 16-bit values is
 // stored as core matrices of 8 rows x 8 values (16 bytes per row, 128 contiguous bytes per core
@@ -104,6 +105,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint3
         if (i > 64) __nanosleep(32);
     }
     return false;
+}
+
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) from global memory into
+// this CTA's shared memory, completing on *mbar, whose phase also takes one arrival from this call.
+// Issued by one thread.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *mbar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+                 : "memory");
 }
 
 // 16 consecutive FP32 columns of this thread's TMEM lane (lane = 32 * (warp % 4) + lane id),
