@@ -382,59 +382,6 @@ __device__ __forceinline__ void interp_all(const HexOps<T> &op, const T *src, T 
     __syncthreads();
 }
 
-// Sum-factorised L2 projection of all 15 fields at once from the quadrature points (src, stride
-// NQ) to the solution points (dst, padded layout, stride FS), z then y then x; the z sweep is staged
-// in tmp (15 M^2 N values), the y sweep in src itself.
-template <typename T, int P, int NT, int XS, int PS, int FS>
-__device__ __forceinline__ void project_all(const HexOps<T> &op, T *src, T *tmp, T *dst)
-{
-    constexpr int N = P + 1, M = P + 2, NQ = M * M * M, NF_ = 15;
-    for (int it = threadIdx.x; it < NF_ * M * M; it += NT) {   // (f, qa, qb) -> k
-        const int f = it / (M * M), ab = it % (M * M);
-        T u[M];
-#pragma unroll
-        for (int c = 0; c < M; c++) u[c] = src[f * NQ + ab + M * M * c];
-#pragma unroll
-        for (int k = 0; k < N; k++) {
-            T v = T(0);
-#pragma unroll
-            for (int c = 0; c < M; c++) v += op.Pj[k][c] * u[c];
-            tmp[f * M * M * N + ab + M * M * k] = v;
-        }
-    }
-    __syncthreads();
-    T *ys = src;   // [f][qa + M (j + N k)]
-    for (int it = threadIdx.x; it < NF_ * M * N; it += NT) {   // (f, qa, k) -> j
-        const int f = it / (M * N), r = it % (M * N), qa = r % M, k = r / M;
-        T u[M];
-#pragma unroll
-        for (int b = 0; b < M; b++) u[b] = tmp[f * M * M * N + qa + M * b + M * M * k];
-#pragma unroll
-        for (int j = 0; j < N; j++) {
-            T v = T(0);
-#pragma unroll
-            for (int b = 0; b < M; b++) v += op.Pj[j][b] * u[b];
-            ys[f * M * N * N + qa + M * j + M * N * k] = v;
-        }
-    }
-    __syncthreads();
-    for (int it = threadIdx.x; it < NF_ * N * N; it += NT) {   // (f, j, k) -> i
-        const int f = it / (N * N), jk = it % (N * N);
-        T u[M];
-#pragma unroll
-        for (int q = 0; q < M; q++) u[q] = ys[f * M * N * N + q + M * jk];
-        const int db = f * FS + XS * (jk % N) + PS * (jk / N);
-#pragma unroll
-        for (int i = 0; i < N; i++) {
-            T v = T(0);
-#pragma unroll
-            for (int q = 0; q < M; q++) v += op.Pj[i][q] * u[q];
-            dst[db + i] = v;
-        }
-    }
-    __syncthreads();
-}
-
 // tdivtpcorf with the corrected divergence folded into the projection: the projection of the
 // flux component along direction d uses Dh Pj instead of Pj along d, and the last (x) sweep sums
 // the three components, so R~[alpha] = sum_d Dh_d (Pj x Pj x Pj) F~[alpha][d] lands in R directly.
