@@ -1247,8 +1247,11 @@ static fr_status rk4_enqueue_step(fr_mesh *m, double *U, double dt, cudaStream_t
         u0 = m->d_rk_us;
     }
     for (int st = 0; st < 4; st++) {
-        if (m->form == FR_FUSED) {
-            // the stage update is folded into the interface kernel: no RHS array, no extra launch
+        if (m->form == FR_FUSED && m->prec == FR_FP64) {
+            // FP64: the stage update is folded into the interface kernel (no RHS array, no extra
+            // launch). The reduced precisions write R and run the update as its own streaming
+            // kernel: their latency-bound interface kernels would stall on the FP64 master-state
+            // and accumulator traffic, which the element-wise kernel moves near the HBM peak.
             RkFold rk;
             rk.stage = st; rk.dt = dt; rk.U = U; rk.acc = m->d_rk_acc; rk.us = m->d_rk_us;
             fr_status r = rhs_impl<T>(m, st == 0 ? u0 : m->d_rk_us, m->d_rk_k, s, rk);
