@@ -217,12 +217,58 @@ __device__ __forceinline__ void pri_project_5(const PriOps<T> &op, const T *src,
     __syncthreads();
 }
 
+// All 20 fields at once (FP32): triangle plane then z; tmp holds 20 x 4 x 25 values.
+template <typename T, int NTH>
+__device__ __forceinline__ void pri_interp_all(const PriOps<T> &op, const T *src, T *tmp, T *dst)
+{
+    for (int it = threadIdx.x; it < 20 * NZ * NQT; it += NTH) {   // triangle plane: (f, k, q)
+        const int f = it / (NZ * NQT), r = it % (NZ * NQT), k = r / NQT, q = r % NQT;
+        T v = T(0);
+#pragma unroll
+        for (int t = 0; t < NT_; t++) v += op.Bt[q][t] * src[f * NU + t + 10 * k];
+        tmp[it] = v;
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < 20 * MZ * NQT; it += NTH) {   // z: (f, c, q)
+        const int f = it / (MZ * NQT), r = it % (MZ * NQT), c = r / NQT, q = r % NQT;
+        T v = T(0);
+#pragma unroll
+        for (int k = 0; k < NZ; k++) v += op.Bz[c][k] * tmp[f * NZ * NQT + q + NQT * k];
+        dst[f * NQ + q + NQT * c] = v;
+    }
+    __syncthreads();
+}
+
+// All 15 flux fields at once (FP32): z then the triangle plane.
+template <typename T, int NTH>
+__device__ __forceinline__ void pri_project_all(const PriOps<T> &op, const T *src, T *tmp, T *dst)
+{
+    for (int it = threadIdx.x; it < 15 * NZ * NQT; it += NTH) {   // z: (f, k, q)
+        const int f = it / (NZ * NQT), r = it % (NZ * NQT), k = r / NQT, q = r % NQT;
+        T v = T(0);
+#pragma unroll
+        for (int c = 0; c < MZ; c++) v += op.Pz[k][c] * src[f * NQ + q + NQT * c];
+        tmp[it] = v;
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < 15 * NU; it += NTH) {          // triangle plane: (f, k, t)
+        const int f = it / NU, r = it % NU, k = r / NT_, t = r % NT_;
+        T v = T(0);
+#pragma unroll
+        for (int q = 0; q < NQT; q++) v += op.Pt[t][q] * tmp[f * NZ * NQT + q + NQT * k];
+        dst[f * NU + t + 10 * k] = v;
+    }
+    __syncthreads();
+}
+
 template <typename T, int NTH, int TCM>
 __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *gops, const PriOpsFF *opsff)
 {
     static_assert(TCM == 0 || (NTH == 128 && sizeof(T) == 4), "tensor-core form: FP32, one warpgroup per element");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ ff s_mf[sizeof(T) == 4 ? 3 * NU : 1];   // low-Mach form: transformed mass flux
+    __shared__ short s_plist[NF];                         // flux points that need the viscous flux
+    __shared__ int s_pcnt;
     PriOps<T> &op = *reinterpret_cast<PriOps<T> *>(smem_raw);
     T *s_u = reinterpret_cast<T *>(smem_raw + ((sizeof(PriOps<T>) + 15) / 16) * 16);
     T *s_q = s_u + 5 * NU;
@@ -278,6 +324,7 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
             if (dev) v -= it < NU ? ph.rref : (it >= 4 * NU ? ph.eref : T(0));
             s_u[it] = v;
         }
+        if (threadIdx.x == 0) s_pcnt = 0;
         for (int it = threadIdx.x; it < 5 * NF; it += NTH) {   // con_u
             const int alpha = it / NF, s = it % NF;
             const uint32_t pc = a.partner[gf0 + s];
@@ -360,7 +407,22 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
             for (int k = 0; k < 3; k++) q[k * NU] = g.Ji[k] * q0 + g.Ji[3 + k] * q1 + g.Ji[6 + k] * q2;
         }
         __syncthreads();
-        for (int s = threadIdx.x; s < NF; s += NTH) {          // viscous normal flux at own flux points
+        // viscous normal flux at own flux points, on the side whose LDG weight 1/2 +- beta is not
+        // zero (the other side's is never used); the points are compacted so whole warps work
+        for (int s = threadIdx.x; s < NF; s += NTH) {
+            const bool isL = (a.partner[gf0 + s] & FR_LFLAG) != 0;
+            const T wgt = isL ? T(0.5) + ph.beta : T(0.5) - ph.beta;
+            if (wgt == T(0)) {
+#pragma unroll
+                for (int k = 0; k < 4; k++) a.FV[k * a.nfpt + gf0 + s] = T(0);
+            } else {
+                s_plist[atomicAdd(&s_pcnt, 1)] = (short)s;
+            }
+        }
+        __syncthreads();
+        const int nplist = s_pcnt;
+        for (int li = threadIdx.x; li < nplist; li += NTH) {
+            const int s = s_plist[li];
             T uf[5], qf[5][3];
 #pragma unroll
             for (int alpha = 0; alpha < 5; alpha++) {
@@ -376,7 +438,9 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
 #pragma unroll
             for (int k = 0; k < 4; k++) a.FV[k * a.nfpt + gf0 + s] = fvn[k];
         }
-        if constexpr (TCM == 0) {
+        if constexpr (TCM == 0 && sizeof(T) == 4) {
+            pri_interp_all<T, NTH>(op, s_u, s_t, s_w);   // s_q follows s_u
+        } else if constexpr (TCM == 0) {
             pri_interp_5<T, NTH>(op, s_u, s_t, s_w);
 #pragma unroll 1
             for (int c = 0; c < 3; c++) pri_interp_5<T, NTH>(op, s_q + 5 * c * NU, s_t, s_w + (5 + 5 * c) * NQ);
@@ -453,7 +517,9 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
         }
         flag_status(a.status, ok);
         __syncthreads();
-        if constexpr (TCM == 0) {
+        if constexpr (TCM == 0 && sizeof(T) == 4) {
+            pri_project_all<T, NTH>(op, s_w, s_t, s_q);
+        } else if constexpr (TCM == 0) {
 #pragma unroll 1
             for (int c = 0; c < 3; c++) pri_project_5<T, NTH>(op, s_w + 5 * c * NQ, s_t, s_q + 5 * c * NU);
         } else {
@@ -674,7 +740,8 @@ int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, const 
           }
         }
         if (!tcdone) {
-            const size_t smem = base + (size_t)(5 * NZ * NQT) * sizeof(T);
+            // FP32 interpolates all 20 fields per pass (staging 20 x 4 x 25 values)
+            const size_t smem = base + (size_t)((sizeof(T) == 4 ? 20 : 5) * NZ * NQT) * sizeof(T);
             static bool attr = false;
             if (!attr) {
                 cudaFuncSetAttribute(k_pri_B<T, NTH, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
