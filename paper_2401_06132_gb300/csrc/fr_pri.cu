@@ -123,15 +123,21 @@ __device__ __forceinline__ void load_ops(const PriOps<T> *g, PriOps<T> &s)
 constexpr int TC_KI = 32, TC_NI = 32;          // interpolation: K = 3 x 10 (+2 zero), N = 25 (+7)
 constexpr int TC_KP = 80, TC_NP = 16;          // projection:    K = 3 x 25 (+5 zero), N = 10 (+6)
 constexpr int TC_SBO_I = TC_KI / 8 * 128, TC_SBO_P = TC_KP / 8 * 128;
-constexpr int TC_A_BYTES = 16 * TC_SBO_P;      // 128 rows; the projection layout is the larger
-constexpr int TC_BI_BYTES = TC_NI / 8 * TC_SBO_I, TC_BP_BYTES = TC_NP / 8 * TC_SBO_P;
-constexpr int TC_BYTES = TC_A_BYTES + TC_BI_BYTES + TC_BP_BYTES + 128 * 4 + 16 + 128;
 constexpr int TC_ROWS_I = 20 * MZ, TC_ROWS_P = 15 * MZ;    // 100 and 75 rows of M = 128
+// The A tile holds the rows an element writes (the projection layout is the larger); the MMA reads
+// all 128 rows, and the ones past the element's last run on into the buffers that follow the tile
+// (the operator tiles and the kernel's arrays), feeding accumulator lanes that are never read.
+constexpr int TC_A_I = (TC_ROWS_I + 7) / 8 * TC_SBO_I, TC_A_P = (TC_ROWS_P + 7) / 8 * TC_SBO_P;
+constexpr int TC_A_BYTES = ((TC_A_I > TC_A_P ? TC_A_I : TC_A_P) + 127) / 128 * 128;
+constexpr int TC_BI_BYTES = TC_NI / 8 * TC_SBO_I, TC_BP_BYTES = TC_NP / 8 * TC_SBO_P;
+constexpr int TC_HEAD = TC_A_BYTES + TC_BI_BYTES + TC_BP_BYTES + 128 * 4 + 16;   // tiles, row shifts, barrier, TMEM slot
+constexpr int TC_BYTES = TC_HEAD + 128;                                         // + alignment slack
 constexpr int TC_ST = 11;                                  // row stride of the projected rows
 constexpr uint32_t TC_IDESC_I1 = tc::idesc_f16(0, 128, TC_NI), TC_IDESC_I2 = tc::idesc_f16(1, 128, TC_NI);
 constexpr uint32_t TC_IDESC_P1 = tc::idesc_f16(0, 128, TC_NP), TC_IDESC_P2 = tc::idesc_f16(1, 128, TC_NP);
 static_assert(TC_ROWS_I <= 128 && TC_ROWS_P <= 128, "one M = 128 tile per element");
-static_assert(16 * TC_SBO_I <= TC_A_BYTES, "interpolation rows fit the operand buffer");
+static_assert(16 * TC_SBO_P <= TC_HEAD + (5 * NU + 15 * NU + 5 * NF + 20 * NQ) * 4,
+              "the 128 rows an MMA reads stay inside the CTA's shared memory");
 
 // -------------------------------------------------------------------------------------------------
 // Phase A: disu
@@ -270,28 +276,31 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
     __shared__ short s_plist[NF];                         // flux points that need the viscous flux
     __shared__ int s_pcnt;
     PriOps<T> &op = *reinterpret_cast<PriOps<T> *>(smem_raw);
-    T *s_u = reinterpret_cast<T *>(smem_raw + ((sizeof(PriOps<T>) + 15) / 16) * 16);
-    T *s_q = s_u + 5 * NU;
-    T *s_c = s_q + 15 * NU;
-    T *s_w = s_c + 5 * NF;
-    T *s_t = s_w + 20 * NQ;
-    load_ops<T, NTH>(gops, op);
-    // tensor-core state (TCM != 0)
+    unsigned char *arr = smem_raw + ((sizeof(PriOps<T>) + 15) / 16) * 16;
+    // tensor-core state (TCM != 0): the tiles come first, so that the MMA's rows past an element's
+    // last run on into the arrays below
     unsigned char *tA = nullptr, *tBi = nullptr, *tBp = nullptr;
     int *s_sh = nullptr;
     uint64_t *mbar = nullptr;
     uint32_t *s_tmem = nullptr, tmem = 0, parity = 0;
     bool tc_fail = false;
     if constexpr (TCM != 0) {
-        const int tcnt = TCM ? (TC_ROWS_P * TC_ST > 5 * NZ * NQT ? TC_ROWS_P * TC_ST : 5 * NZ * NQT) : 0;
-        const uint32_t raw = tc::smem_u32(s_t + tcnt);
-        unsigned char *p0 = reinterpret_cast<unsigned char *>(s_t + tcnt) + ((128 - (raw & 127)) & 127);
-        tA = p0;
+        const uint32_t raw = tc::smem_u32(arr);
+        tA = arr + ((128 - (raw & 127)) & 127);
         tBi = tA + TC_A_BYTES;
         tBp = tBi + TC_BI_BYTES;
         s_sh = reinterpret_cast<int *>(tBp + TC_BP_BYTES);
         mbar = reinterpret_cast<uint64_t *>(s_sh + 128);
         s_tmem = reinterpret_cast<uint32_t *>(mbar + 1);
+        arr = tA + TC_HEAD;
+    }
+    T *s_u = reinterpret_cast<T *>(arr);
+    T *s_q = s_u + 5 * NU;
+    T *s_c = s_q + 15 * NU;
+    T *s_w = s_c + 5 * NF;
+    T *s_t = s_w + 20 * NQ;
+    load_ops<T, NTH>(gops, op);
+    if constexpr (TCM != 0) {
         tc::setup(mbar, s_tmem, 32);
         __syncthreads();   // operators in shared memory
         for (int i = threadIdx.x; i < TC_NI * TC_KI; i += NTH) {   // [B_hi | B_hi | B_lo]
@@ -726,17 +735,24 @@ int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, const 
             tcdone = true;
             const int tcnt = TC_ROWS_P * TC_ST > 5 * NZ * NQT ? TC_ROWS_P * TC_ST : 5 * NZ * NQT;
             const size_t smem = base + (size_t)tcnt * sizeof(T) + TC_BYTES;
-            // persistent: at most 4 resident CTAs per SM (each holds 32 of the 512 TMEM columns)
-            const int grid = grid_elems(a.ne, 1) < 152 * 4 ? grid_elems(a.ne, 1) : 152 * 4;
-            if (a.tcmode == 1) {
-                static bool attr1 = false;
-                if (!attr1) { cudaFuncSetAttribute(k_pri_B<T, NTH, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr1 = true; }
-                k_pri_B<T, NTH, 1><<<grid, NTH, smem, s>>>(a, ops, ops64);
-            } else {
-                static bool attr2 = false;
-                if (!attr2) { cudaFuncSetAttribute(k_pri_B<T, NTH, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr2 = true; }
-                k_pri_B<T, NTH, 2><<<grid, NTH, smem, s>>>(a, ops, ops64);
+            // persistent: as many CTAs as fit on the SMs (shared memory, registers, and the 512
+            // tensor-memory columns at 32 per CTA)
+            auto kern = a.tcmode == 1 ? k_pri_B<T, NTH, 1> : k_pri_B<T, NTH, 2>;
+            static int occ[3] = {-1, -1, -1};
+            int &o = occ[a.tcmode];
+            if (o < 0) {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                cudaFuncAttributes fa{};
+                if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return -1;
+                const int by_smem = (int)(232448 / (smem + fa.sharedSizeBytes + 1024));
+                const int by_regs = 65536 / (((fa.numRegs + 7) / 8 * 8) * NTH);
+                int v = by_smem < by_regs ? by_smem : by_regs;
+                if (v > 512 / 32) v = 512 / 32;
+                if (v < 1) return -4;
+                o = v;
             }
+            const long long g = a.ne < 152LL * o ? a.ne : 152LL * o;
+            kern<<<(int)g, NTH, smem, s>>>(a, ops, ops64);
           }
         }
         if (!tcdone) {
