@@ -3,8 +3,8 @@
  *
  * A plain, slow, FP64 reference ("the oracle") for one right-hand-side (RHS) evaluation of the
  * flux-reconstruction (FR) discretisation of the compressible Navier-Stokes equations with flux
- * anti-aliasing (over-integration of the flux at element quadrature points), on affine hexahedra
- * and prisms, plus the classical RK4 step around it.
+ * anti-aliasing (over-integration of the flux at element quadrature points), on affine hexahedra,
+ * prisms and tetrahedra, plus the classical RK4 step around it.
  *
  * Only the test-suite, the package smoke check and the CPU-baseline leg of the benchmark may load
  * the library built from this file. It shares no code with the GPU library.
@@ -30,14 +30,24 @@
  *       matrix M and E = int_face l_zeta l^face_sigma dS (reference measure).
  *   R4  Rusanov: F = 1/2 n.(fe_L + fe_R) + 1/2 s (uL - uR), s = max(|vL.n|+cL, |vR.n|+cR).
  *   R5  the L side of a flux-point pair is the element with the smaller global index (hexes
- *       before prisms); a self-pair takes the smaller local face number as L.
+ *       before prisms before tetrahedra); a self-pair takes the smaller local face number as L.
  *   R6  transformed common flux D = |n_s| F with n_s = detJ J^-T n~; each side uses its own |n_s|.
  *   R7  prism solution points: the paper's Williams-Shunn triangle points x GL points in z.
  *   R8  prism quadrature: collapsed (Duffy) k x k GL triangle rule x m GL points in z.
- *   R11 orthonormal bases: normalised Legendre on lines; Gram-Schmidt of monomials on triangles.
+ *   R11 orthonormal bases: normalised Legendre on lines; Gram-Schmidt of monomials on triangles
+ *       and tetrahedra.
+ *   T1  tetrahedra (Sec. 1 lists them among the supported types, with dense operators; the paper
+ *       prints no point set for them): solution points are the order-p equispaced lattice shrunk by
+ *       4/5 towards the centroid; each triangular face carries the printed Williams-Shunn triangle
+ *       points (so p = 2, 3). With the DG-equivalent lift and the L2 projection of the flux, the RHS
+ *       as a polynomial does not depend on the solution points, only its rounding does.
+ *   T2  tetrahedron quadrature: collapsed m x m x m rule (GL in a, Gauss rules of the weights
+ *       (1-b) and (1-c)^2 in b and c), exact to total degree 2m-1 -- with m = p + 2 the same
+ *       degree 2p+3 that m GL points give per direction on the hexahedron.
  *
- * Parity pins: see tests/test_oracle_*.py. Parity for the prism element and for the R4/R5
- * readings is unpinned beyond invariants (freestream, conservation, polynomial exactness).
+ * Parity pins: see tests/test_oracle_*.py. Parity for the prism and tetrahedron elements and for
+ * the R4/R5 readings is pinned by invariants and identities (freestream, conservation, polynomial
+ * exactness, integration by parts, grid convergence), not by printed values.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -130,6 +140,8 @@ static double lagrange1d(int n, const double *xs, int a, double x)
     return v;
 }
 
+static double ipow(double x, int k) { double v = 1.0; for (int i = 0; i < k; i++) v *= x; return v; }
+
 /* Collapsed (Duffy) k x k rule on the reference triangle (-1,-1),(1,-1),(-1,1):
  * x = (1+a)(1-b)/2 - 1, y = b, weight w_a w_b (1-b)/2, exact for total degree 2k-2.
  * Point index ia + k*ib. */
@@ -145,6 +157,109 @@ void or_tri_rule(int k, double *xy, double *w)
             xy[2 * q + 1] = b;
             w[q] = gw[ia] * gw[ib] * 0.5 * (1.0 - b);
         }
+}
+
+/* n-point Gauss rule for the weight (1-x)^alpha on [-1,1] (reading T2 uses alpha = 0, 1, 2).
+ * The nodes are the roots of the degree-n polynomial orthogonal under that weight: it is built by
+ * Gram-Schmidt of the Legendre polynomials P_0..P_n with inner products from a 40-point GL rule
+ * (exact for these integrands), its n roots are bracketed on a fine grid and bisected; the weights
+ * are those of the interpolatory rule on the nodes, w_j = int (1-x)^alpha l_j(x) dx. Returns 0, or
+ * -1 if the n roots were not all found. Nodes in increasing order. */
+int or_gauss_jacobi(int n, int alpha, double *x, double *w)
+{
+    enum { NG = 40 };
+    double g[NG], gw[NG], wt[NG], P[64], dP[64];
+    if (n < 1 || n > 16) return -1;
+    or_gauss_legendre(NG, g, gw);
+    for (int q = 0; q < NG; q++) wt[q] = gw[q] * ipow(1.0 - g[q], alpha);
+    /* c[k][r]: polynomial k = sum_r c[k][r] P_r, orthogonal under the weight */
+    double c[17][17], val[17][NG];
+    memset(c, 0, sizeof c);
+    for (int k = 0; k <= n; k++) {
+        c[k][k] = 1.0;
+        for (int q = 0; q < NG; q++) { legendre_all(k, g[q], P, dP); val[k][q] = P[k]; }
+        for (int pass = 0; pass < 2; pass++)
+            for (int j = 0; j < k; j++) {
+                double ip = 0, nj = 0;
+                for (int q = 0; q < NG; q++) { ip += wt[q] * val[k][q] * val[j][q]; nj += wt[q] * val[j][q] * val[j][q]; }
+                double f = ip / nj;
+                for (int r = 0; r <= n; r++) c[k][r] -= f * c[j][r];
+                for (int q = 0; q < NG; q++) val[k][q] -= f * val[j][q];
+            }
+    }
+    /* the roots of polynomial n */
+    const int NS = 20000;
+    int found = 0;
+    double xa = -1.0, fa;
+    legendre_all(n, xa, P, dP);
+    fa = 0; for (int r = 0; r <= n; r++) fa += c[n][r] * P[r];
+    for (int i = 1; i <= NS && found < n; i++) {
+        double xb = -1.0 + 2.0 * i / NS, fb = 0;
+        legendre_all(n, xb, P, dP);
+        for (int r = 0; r <= n; r++) fb += c[n][r] * P[r];
+        if ((fa < 0) != (fb < 0)) {
+            double lo = xa, hi = xb, flo = fa;
+            for (int it = 0; it < 200 && hi - lo > 0; it++) {
+                double mid = 0.5 * (lo + hi), fm = 0;
+                if (mid <= lo || mid >= hi) break;
+                legendre_all(n, mid, P, dP);
+                for (int r = 0; r <= n; r++) fm += c[n][r] * P[r];
+                if ((fm < 0) == (flo < 0)) { lo = mid; flo = fm; } else hi = mid;
+            }
+            x[found++] = 0.5 * (lo + hi);
+        }
+        xa = xb; fa = fb;
+    }
+    if (found != n) return -1;
+    for (int j = 0; j < n; j++) {
+        double v = 0;
+        for (int q = 0; q < NG; q++) v += wt[q] * lagrange1d(n, x, j, g[q]);
+        w[j] = v;
+    }
+    return 0;
+}
+
+/* Collapsed (Duffy) k x k x k rule on the reference tetrahedron (-1,-1,-1), (1,-1,-1), (-1,1,-1),
+ * (-1,-1,1) (reading T2): for a, b, c in [-1,1], x = (1+a)(1-b)(1-c)/4 - 1, y = (1+b)(1-c)/2 - 1,
+ * z = c, with Jacobian (1-b)(1-c)^2/8; a takes the k-point GL rule, b and c the k-point Gauss rules
+ * of the weights (1-b) and (1-c)^2. A polynomial of total degree d in (x,y,z) is of degree <= d in
+ * each of a, b, c, so the rule is exact for d <= 2k-1. Point index ia + k ib + k^2 ic. */
+int or_tet_rule(int k, double *xyz, double *w)
+{
+    double ga[32], wa[32], gb[32], wb[32], gc[32], wc[32];
+    if (k < 1 || k > 16) return -1;
+    or_gauss_legendre(k, ga, wa);
+    if (or_gauss_jacobi(k, 1, gb, wb) || or_gauss_jacobi(k, 2, gc, wc)) return -1;
+    for (int ic = 0; ic < k; ic++)
+        for (int ib = 0; ib < k; ib++)
+            for (int ia = 0; ia < k; ia++) {
+                int q = ia + k * ib + k * k * ic;
+                double a = ga[ia], b = gb[ib], c = gc[ic];
+                xyz[3 * q + 0] = 0.25 * (1.0 + a) * (1.0 - b) * (1.0 - c) - 1.0;
+                xyz[3 * q + 1] = 0.5 * (1.0 + b) * (1.0 - c) - 1.0;
+                xyz[3 * q + 2] = c;
+                w[q] = wa[ia] * wb[ib] * wc[ic] / 8.0;
+            }
+    return 0;
+}
+
+/* Tetrahedron solution points (reading T1): the equispaced lattice of order p, (a, b, c)/p with
+ * a + b + c <= p, mapped onto the reference tetrahedron and shrunk by the factor 4/5 towards its
+ * centroid (-1/2, -1/2, -1/2), so that every point is interior. The set keeps the tetrahedron's
+ * symmetries and is unisolvent for P_p (an affine image of the lattice). Index order: a fastest,
+ * then b, then c. Returns the count (p+1)(p+2)(p+3)/6. */
+int or_tet_solution_points(int p, double *xyz)
+{
+    const double s = 0.8;
+    int k = 0;
+    for (int c = 0; c <= p; c++)
+        for (int b = 0; b <= p - c; b++)
+            for (int a = 0; a <= p - b - c; a++) {
+                double X[3] = {-1.0 + 2.0 * a / p, -1.0 + 2.0 * b / p, -1.0 + 2.0 * c / p};
+                for (int d = 0; d < 3; d++) xyz[3 * k + d] = -0.5 + s * (X[d] + 0.5);
+                k++;
+            }
+    return k;
 }
 
 /* Williams-Shunn triangle solution points as printed in the paper's prism figures
@@ -178,7 +293,6 @@ typedef struct {
     double *c;          /* [nt][nt] coefficients: phi_t = sum_k c[t][k] x^mi[k] y^mj[k] */
 } tri_basis;
 
-static double ipow(double x, int k) { double v = 1.0; for (int i = 0; i < k; i++) v *= x; return v; }
 
 static void tri_basis_eval(const tri_basis *tb, double x, double y, double *phi, double *dphx, double *dphy)
 {
@@ -235,11 +349,80 @@ static void tri_basis_init(tri_basis *tb, int p)
 
 static void tri_basis_free(tri_basis *tb) { free(tb->mi); free(tb->mj); free(tb->c); }
 
+/* Orthonormal basis of P_p on the reference tetrahedron (volume 4/3): Gram-Schmidt (modified, two
+ * passes) of the monomials x^i y^j z^l, i+j+l <= p in graded order, under the collapsed rule with
+ * p + 2 points per direction (strength 2p+3 >= 2p). */
+typedef struct {
+    int p, nt;
+    int *e;             /* [nt][3] monomial exponents */
+    double *c;          /* [nt][nt] coefficients: phi_t = sum_k c[t][k] x^e[k][0] y^e[k][1] z^e[k][2] */
+} tet_basis;
+
+static void tet_basis_eval(const tet_basis *tb, const double *X, double *phi, double *dphi /* [3][nt] or NULL */)
+{
+    int nt = tb->nt;
+    for (int t = 0; t < nt; t++) {
+        double v = 0, g[3] = {0, 0, 0};
+        for (int k = 0; k < nt; k++) {
+            const int *e = tb->e + 3 * k;
+            double ck = tb->c[t * nt + k];
+            v += ck * ipow(X[0], e[0]) * ipow(X[1], e[1]) * ipow(X[2], e[2]);
+            for (int d = 0; d < 3; d++) {
+                if (e[d] == 0) continue;
+                double m = ck * e[d];
+                for (int dd = 0; dd < 3; dd++) m *= ipow(X[dd], dd == d ? e[dd] - 1 : e[dd]);
+                g[d] += m;
+            }
+        }
+        phi[t] = v;
+        if (dphi) for (int d = 0; d < 3; d++) dphi[d * nt + t] = g[d];
+    }
+}
+
+static int tet_basis_init(tet_basis *tb, int p)
+{
+    int nt = (p + 1) * (p + 2) * (p + 3) / 6;
+    tb->p = p; tb->nt = nt;
+    tb->e = (int *)malloc(3 * nt * sizeof(int));
+    tb->c = (double *)calloc((size_t)nt * nt, sizeof(double));
+    int k = 0;
+    for (int d = 0; d <= p; d++)
+        for (int i = d; i >= 0; i--)
+            for (int j = d - i; j >= 0; j--) { tb->e[3 * k] = i; tb->e[3 * k + 1] = j; tb->e[3 * k + 2] = d - i - j; k++; }
+    int kq = p + 2, nq = kq * kq * kq;
+    double *xyz = (double *)malloc(3 * nq * sizeof(double)), *w = (double *)malloc(nq * sizeof(double));
+    if (or_tet_rule(kq, xyz, w)) { free(xyz); free(w); return -1; }
+    double *val = (double *)malloc((size_t)nt * nq * sizeof(double));
+    for (int t = 0; t < nt; t++) {
+        double *ct = tb->c + t * nt;
+        const int *e = tb->e + 3 * t;
+        ct[t] = 1.0;
+        for (int q = 0; q < nq; q++)
+            val[t * nq + q] = ipow(xyz[3 * q], e[0]) * ipow(xyz[3 * q + 1], e[1]) * ipow(xyz[3 * q + 2], e[2]);
+        for (int pass = 0; pass < 2; pass++)
+            for (int s = 0; s < t; s++) {
+                double ip = 0;
+                for (int q = 0; q < nq; q++) ip += w[q] * val[t * nq + q] * val[s * nq + q];
+                for (int kk = 0; kk < nt; kk++) ct[kk] -= ip * tb->c[s * nt + kk];
+                for (int q = 0; q < nq; q++) val[t * nq + q] -= ip * val[s * nq + q];
+            }
+        double nrm = 0;
+        for (int q = 0; q < nq; q++) nrm += w[q] * val[t * nq + q] * val[t * nq + q];
+        nrm = sqrt(nrm);
+        for (int kk = 0; kk < nt; kk++) ct[kk] /= nrm;
+        for (int q = 0; q < nq; q++) val[t * nq + q] /= nrm;
+    }
+    free(xyz); free(w); free(val);
+    return 0;
+}
+
+static void tet_basis_free(tet_basis *tb) { free(tb->e); free(tb->c); }
+
 /* ---------------------------------------------------------------------------------------------
  * Element types and their dense operators
  * ------------------------------------------------------------------------------------------- */
 
-enum { ET_HEX = 0, ET_PRI = 1 };
+enum { ET_HEX = 0, ET_PRI = 1, ET_TET = 2, ET_COUNT = 3 };
 
 typedef struct {
     int kind;           /* 0 = quad, 1 = triangle */
@@ -264,7 +447,8 @@ typedef struct {
     double *Agrad;          /* [3][nu][nu] M4 - M6 M0 (per direction) */
     double *Adiv;           /* [nu][3][nu] M1 - M3 M2 */
     double *Wu;             /* [nu] int l_zeta over the reference element */
-    tri_basis tb;           /* prism only */
+    tri_basis tb;           /* prism and tetrahedron (their triangle faces) */
+    tet_basis teb;          /* tetrahedron only */
     double g1[16], g1w[16]; /* 1D GL solution nodes */
     int nfn;                /* 1D nodes of the hex face point grids: n, or m with surface-flux AA */
     double fg[32];          /* their coordinates */
@@ -295,6 +479,8 @@ static void modal_eval(const etype_t *et, const double *X, double *psi, double *
                         dpsi[2 * et->nmodes + nu] = Px[a] * Py[b] * dPz[c];
                     }
                 }
+    } else if (et->type == ET_TET) {
+        tet_basis_eval(&et->teb, X, psi, dpsi);
     } else {
         int nt = et->tb.nt;
         double phi[64], phx[64], phy[64];
@@ -319,6 +505,13 @@ static void face_map(const etype_t *et, int f, double s, double t, double *X)
         int d = f / 2; double side = (f % 2) ? 1.0 : -1.0;
         int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
         X[d] = side; X[t1] = s; X[t2] = t;
+    } else if (et->type == ET_TET) {
+        switch (f) {
+        case 0: X[0] = s; X[1] = t; X[2] = -1.0; break;        /* z = -1 */
+        case 1: X[0] = s; X[1] = -1.0; X[2] = t; break;        /* y = -1 */
+        case 2: X[0] = -1.0; X[1] = s; X[2] = t; break;        /* x = -1 */
+        default: X[0] = -1.0 - s - t; X[1] = s; X[2] = t; break; /* x + y + z = -1 */
+        }
     } else {
         switch (f) {
         case 0: X[0] = s; X[1] = t; X[2] = -1.0; break;   /* triangle z = -1 */
@@ -367,6 +560,19 @@ static int etype_init(etype_t *et, int type, int p, int m, int tri_k, int surf)
             memset(et->faces[f].nref, 0, sizeof(double) * 3);
             et->faces[f].nref[f / 2] = (f % 2) ? 1.0 : -1.0;
         }
+    } else if (type == ET_TET) {
+        /* reading T1: p = 2, 3 (the faces carry the printed triangle points) */
+        nt = or_tri_solution_points(p, txy);
+        if (nt < 0) return -1;
+        tri_basis_init(&et->tb, p);
+        if (tet_basis_init(&et->teb, p)) return -1;
+        et->nu = (p + 1) * (p + 2) * (p + 3) / 6; et->nmodes = et->nu; et->nfaces = 4;
+        et->nq = m * m * m;
+        double r3 = 1.0 / sqrt(3.0);
+        face_info fi[4] = {
+            {1, nt, {0, 0, -1}, 1.0}, {1, nt, {0, -1, 0}, 1.0}, {1, nt, {-1, 0, 0}, 1.0},
+            {1, nt, {r3, r3, r3}, sqrt(3.0)}};
+        for (int f = 0; f < 4; f++) et->faces[f] = fi[f];
     } else {
         nt = or_tri_solution_points(p, txy);
         if (nt < 0) return -1;
@@ -402,6 +608,8 @@ static int etype_init(etype_t *et, int type, int p, int m, int tri_k, int surf)
                     int z = i + n1 * j + n1 * n1 * k;
                     et->xu[3 * z] = et->g1[i]; et->xu[3 * z + 1] = et->g1[j]; et->xu[3 * z + 2] = et->g1[k];
                 }
+    } else if (type == ET_TET) {
+        or_tet_solution_points(p, et->xu);
     } else {
         for (int k = 0; k < n1; k++)
             for (int t = 0; t < nt; t++) {
@@ -433,6 +641,9 @@ static int etype_init(etype_t *et, int type, int p, int m, int tri_k, int surf)
                     et->xq[3 * q] = gq[a]; et->xq[3 * q + 1] = gq[b]; et->xq[3 * q + 2] = gq[c];
                     et->wq[q] = gqw[a] * gqw[b] * gqw[c];
                 }
+    } else if (type == ET_TET) {
+        /* reading T2: collapsed Gauss rules, m points per direction */
+        if (or_tet_rule(m, et->xq, et->wq)) return -1;
     } else {
         int nt2 = tri_k * tri_k;
         double *txq = (double *)malloc(2 * nt2 * sizeof(double)), *twq = (double *)malloc(nt2 * sizeof(double));
@@ -511,7 +722,7 @@ static int etype_init(etype_t *et, int type, int p, int m, int tri_k, int surf)
     /* Lift (reading R3): Minv = V V^T in the orthonormal basis; E by face quadrature. */
     {
         double *TVinv = NULL;
-        if (type == ET_PRI) {
+        if (type != ET_HEX) {
             TVinv = (double *)malloc(nt * nt * sizeof(double));
             double phi[64];
             for (int a = 0; a < nt; a++) {
@@ -589,7 +800,8 @@ static void etype_free(etype_t *et)
     free(et->fpt_face); free(et->xu); free(et->xf); free(et->xq); free(et->wq); free(et->fparam);
     free(et->nref); free(et->M0); free(et->Dm); free(et->M3); free(et->M7); free(et->M8);
     free(et->Agrad); free(et->Adiv); free(et->Wu);
-    if (et->type == ET_PRI) tri_basis_free(&et->tb);
+    if (et->type != ET_HEX) tri_basis_free(&et->tb);
+    if (et->type == ET_TET) tet_basis_free(&et->teb);
 }
 
 /* ---------------------------------------------------------------------------------------------
@@ -603,9 +815,9 @@ typedef struct {
 
 typedef struct {
     phys_params ph;
-    etype_t et[2];
-    int has[2];
-    int n_hex, n_pri, ne;
+    etype_t et[ET_COUNT];
+    int has[ET_COUNT];
+    int n_hex, n_pri, n_tet, ne;
     double period[3];
     double *x0;     /* [ne][3] reference origin: x = x0 + J (xi + 1) */
     double *J;      /* [ne][9] row-major dx_i/dxi_j */
@@ -623,7 +835,9 @@ typedef struct {
     int nthreads;
 } oracle_t;
 
-static const etype_t *ET(const oracle_t *o, int e) { return &o->et[e < o->n_hex ? ET_HEX : ET_PRI]; }
+/* Element order: hexahedra, then prisms, then tetrahedra. */
+static int etype_of(const oracle_t *o, int e) { return e < o->n_hex ? ET_HEX : (e < o->n_hex + o->n_pri ? ET_PRI : ET_TET); }
+static const etype_t *ET(const oracle_t *o, int e) { return &o->et[etype_of(o, e)]; }
 
 static double pdist(const oracle_t *o, const double *a, const double *b)
 {
@@ -679,16 +893,16 @@ static int facekey_cmp(const void *a, const void *b)
     return ((const or_facekey *)a)->face - ((const or_facekey *)b)->face;
 }
 
-void *or_create2(int p, int m, int tri_k, int surf, double gamma, double Pr, double mu, double beta, double tau,
-                 double p_ref, int n_hex, int n_pri, int n_verts, const double *verts, const int *hex_v,
-                 const int *pri_v, const double *period, int *err);
+void *or_create3(int p, int m, int tri_k, int surf, double gamma, double Pr, double mu, double beta, double tau,
+                 double p_ref, int n_hex, int n_pri, int n_tet, int n_verts, const double *verts, const int *hex_v,
+                 const int *pri_v, const int *tet_v, const double *period, int *err);
 
 void *or_create(int p, int m, int tri_k, double gamma, double Pr, double mu, double beta, double tau, double p_ref,
                 int n_hex, int n_pri, int n_verts, const double *verts, const int *hex_v, const int *pri_v,
                 const double *period, int *err)
 {
-    return or_create2(p, m, tri_k, 0, gamma, Pr, mu, beta, tau, p_ref, n_hex, n_pri, n_verts, verts, hex_v, pri_v,
-                      period, err);
+    return or_create3(p, m, tri_k, 0, gamma, Pr, mu, beta, tau, p_ref, n_hex, n_pri, 0, n_verts, verts, hex_v, pri_v,
+                      NULL, period, err);
 }
 
 /* As or_create; surf = 1 selects surface-flux anti-aliasing (hexahedra only): the flux points of
@@ -697,15 +911,28 @@ void *or_create2(int p, int m, int tri_k, int surf, double gamma, double Pr, dou
                  double p_ref, int n_hex, int n_pri, int n_verts, const double *verts, const int *hex_v,
                  const int *pri_v, const double *period, int *err)
 {
+    return or_create3(p, m, tri_k, surf, gamma, Pr, mu, beta, tau, p_ref, n_hex, n_pri, 0, n_verts, verts, hex_v,
+                      pri_v, NULL, period, err);
+}
+
+/* As or_create2, with n_tet tetrahedra (4 vertices each, tet_v) after the prisms. */
+void *or_create3(int p, int m, int tri_k, int surf, double gamma, double Pr, double mu, double beta, double tau,
+                 double p_ref, int n_hex, int n_pri, int n_tet, int n_verts, const double *verts, const int *hex_v,
+                 const int *pri_v, const int *tet_v, const double *period, int *err)
+{
     *err = OR_OK;
-    if (p < 1 || m < 1 || n_hex < 0 || n_pri < 0 || n_hex + n_pri == 0) { *err = OR_EINVAL; return NULL; }
+    if (p < 1 || m < 1 || n_hex < 0 || n_pri < 0 || n_tet < 0 || n_hex + n_pri + n_tet == 0) { *err = OR_EINVAL; return NULL; }
     oracle_t *o = (oracle_t *)calloc(1, sizeof(oracle_t));
     o->ph.gamma = gamma; o->ph.Pr = Pr; o->ph.mu = mu; o->ph.beta = beta; o->ph.tau = tau; o->ph.p_ref = p_ref;
-    o->n_hex = n_hex; o->n_pri = n_pri; o->ne = n_hex + n_pri;
+    o->n_hex = n_hex; o->n_pri = n_pri; o->n_tet = n_tet; o->ne = n_hex + n_pri + n_tet;
     for (int d = 0; d < 3; d++) o->period[d] = period ? period[d] : 0.0;
     o->nthreads = 1;
-    if (n_hex > 0) { if (etype_init(&o->et[ET_HEX], ET_HEX, p, m, tri_k, surf)) { *err = OR_EUNSUPPORTED; free(o); return NULL; } o->has[ET_HEX] = 1; }
-    if (n_pri > 0) { if (etype_init(&o->et[ET_PRI], ET_PRI, p, m, tri_k, surf)) { *err = OR_EUNSUPPORTED; or_destroy(o); return NULL; } o->has[ET_PRI] = 1; }
+    const int counts[ET_COUNT] = {n_hex, n_pri, n_tet};
+    for (int t = 0; t < ET_COUNT; t++) {
+        if (counts[t] == 0) continue;
+        if (etype_init(&o->et[t], t, p, m, tri_k, surf)) { *err = OR_EUNSUPPORTED; or_destroy(o); return NULL; }
+        o->has[t] = 1;
+    }
     int ne = o->ne;
     o->x0 = (double *)malloc(3 * ne * sizeof(double));
     o->J = (double *)malloc(9 * ne * sizeof(double));
@@ -721,9 +948,10 @@ void *or_create2(int p, int m, int tri_k, int surf, double gamma, double Pr, dou
         uo += (long)NV * et->nu; fo += (long)NV * et->nf; fb += et->nf;
         /* affine map from vertices; reject non-affine or inverted elements */
         const double *v[8];
-        int nv = (e < n_hex) ? 8 : 6;
+        const int typ = etype_of(o, e);
+        int nv = typ == ET_HEX ? 8 : (typ == ET_PRI ? 6 : 4);
         for (int k = 0; k < nv; k++) {
-            int vi = (e < n_hex) ? hex_v[8 * e + k] : pri_v[6 * (e - n_hex) + k];
+            int vi = typ == ET_HEX ? hex_v[8 * e + k] : (typ == ET_PRI ? pri_v[6 * (e - n_hex) + k] : tet_v[4 * (e - n_hex - n_pri) + k]);
             if (vi < 0 || vi >= n_verts) { *err = OR_EMESH; or_destroy(o); return NULL; }
             v[k] = verts + 3 * vi;
         }
@@ -775,6 +1003,12 @@ void *or_create2(int p, int m, int tri_k, int surf, double gamma, double Pr, dou
                 /* the physical face centroid is the affine image of the reference face centre */
                 double Xc[3], c[3];
                 if (et->type == ET_HEX) { Xc[0] = Xc[1] = Xc[2] = 0.0; Xc[f / 2] = (f % 2) ? 1.0 : -1.0; }
+                else if (et->type == ET_TET) {
+                    /* centroid of the face's three reference vertices */
+                    double t3 = -1.0 / 3.0;
+                    Xc[0] = Xc[1] = Xc[2] = t3;
+                    if (f < 3) Xc[2 - f] = -1.0;
+                }
                 else if (f < 2) { Xc[0] = Xc[1] = -1.0 / 3.0; Xc[2] = f ? 1.0 : -1.0; }
                 else if (f == 2) { Xc[0] = 0.0; Xc[1] = -1.0; Xc[2] = 0.0; }
                 else if (f == 3) { Xc[0] = 0.0; Xc[1] = 0.0; Xc[2] = 0.0; }
@@ -881,7 +1115,7 @@ void or_destroy(void *h)
 {
     oracle_t *o = (oracle_t *)h;
     if (!o) return;
-    for (int t = 0; t < 2; t++) if (o->has[t]) etype_free(&o->et[t]);
+    for (int t = 0; t < ET_COUNT; t++) if (o->has[t]) etype_free(&o->et[t]);
     free(o->x0); free(o->J); free(o->Jinv); free(o->detJ); free(o->uoff); free(o->foff);
     free(o->fpt_base); free(o->fpt_elem); free(o->pairL); free(o->pairR);
     free(o->UF); free(o->CF); free(o->DF); free(o->QF); free(o->Q); free(o->Rt);
@@ -1283,7 +1517,7 @@ void or_diagnostics(void *h, const double *U, const double *R, double *out)
 int or_etype_dims(void *h, int t, int *dims)
 {
     oracle_t *o = (oracle_t *)h;
-    if (t < 0 || t > 1 || !o->has[t]) return -1;
+    if (t < 0 || t >= ET_COUNT || !o->has[t]) return -1;
     const etype_t *et = &o->et[t];
     dims[0] = et->nu; dims[1] = et->nf; dims[2] = et->nq; dims[3] = et->nfaces;
     return 0;
@@ -1295,7 +1529,7 @@ int or_etype_dims(void *h, int t, int *dims)
 int or_get_operator(void *h, int t, int which, double *out)
 {
     oracle_t *o = (oracle_t *)h;
-    if (t < 0 || t > 1 || !o->has[t]) return -1;
+    if (t < 0 || t >= ET_COUNT || !o->has[t]) return -1;
     const etype_t *et = &o->et[t];
     int nu = et->nu, nf = et->nf, nq = et->nq;
     switch (which) {

@@ -168,3 +168,39 @@ def sheared_box_mesh(N: int, length: float = 2 * math.pi, origin: float = -math.
     hex_v = np.stack([vid(ex + (c & 1), ey + ((c >> 1) & 1), ez + ((c >> 2) & 1)) for c in range(8)], axis=1)
     return dict(verts=verts, hex_v=hex_v.astype(np.int32), pri_v=np.zeros((0, 6), np.int32),
                 period=(length, length, length))
+
+
+# Kuhn split of the unit cube into six tetrahedra, one per axis permutation: each walks from corner
+# (0,0,0) to (1,1,1) along the axes in the permutation's order. Corners in tensor order a + 2b + 4c.
+_KUHN_PERMS = ((0, 1, 2), (1, 2, 0), (2, 0, 1), (1, 0, 2), (0, 2, 1), (2, 1, 0))
+
+
+def _kuhn_tets():
+    out = []
+    for k, perm in enumerate(_KUHN_PERMS):
+        c0 = 0
+        c1 = c0 | (1 << perm[0])
+        c2 = c1 | (1 << perm[1])
+        c3 = 7
+        # the last three permutations are odd: swap two vertices to keep a positive orientation
+        out.append((c0, c1, c2, c3) if k < 3 else (c0, c2, c1, c3))
+    return out
+
+
+def box_tet_mesh(N: int, length: float = 2 * math.pi, origin: float = -math.pi, shear: bool = False):
+    """N^3 periodic box of cells, each split into six tetrahedra (Kuhn split, which every cell shares,
+    so the faces of neighbouring cells match, also across the periods). Tetrahedron vertex order:
+    v0..v3 map to the reference corners (-1,-1,-1), (1,-1,-1), (-1,1,-1), (-1,-1,1). With
+    ``shear`` the vertex grid is sheared as in ``sheared_box_mesh``."""
+    h = length / N
+    i, j, k = np.meshgrid(np.arange(N + 1), np.arange(N + 1), np.arange(N + 1), indexing="ij")
+    i, j, k = i.ravel(order="F"), j.ravel(order="F"), k.ravel(order="F")
+    sx = (j + k) * (h / N) if shear else 0.0
+    verts = np.stack([origin + i * h + sx, origin + j * h, origin + k * h], axis=1)
+    vid = lambda a, b, c: a + (N + 1) * (b + (N + 1) * c)  # noqa: E731
+    e = np.arange(N ** 3)
+    ex, ey, ez = e % N, (e // N) % N, e // (N * N)
+    corner = np.stack([vid(ex + (c & 1), ey + ((c >> 1) & 1), ez + ((c >> 2) & 1)) for c in range(8)], axis=1)
+    tets = np.stack([corner[:, list(t)] for t in _kuhn_tets()], axis=1).reshape(-1, 4)
+    return dict(verts=verts, hex_v=np.zeros((0, 8), np.int32), pri_v=np.zeros((0, 6), np.int32),
+                tet_v=tets.astype(np.int32), period=(length, length, length))

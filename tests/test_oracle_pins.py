@@ -31,6 +31,8 @@ def _layout(o, mesh):
         blocks.append((mesh["hex_v"].shape[0], o.dims(0)[0]))
     if mesh["pri_v"].shape[0]:
         blocks.append((mesh["pri_v"].shape[0], o.dims(1)[0]))
+    if mesh.get("tet_v", np.zeros((0, 4))).shape[0]:
+        blocks.append((mesh["tet_v"].shape[0], o.dims(2)[0]))
     return blocks
 
 
@@ -55,13 +57,18 @@ def _eval_poly3_grad(coef, pts, d):
 
 
 def _random_space_poly(rng, p, etype):
-    """Random polynomial in the element's solution space: Q_p (hex) or P_p(tri) x P_p(z) (prism)."""
+    """Random polynomial in the element's solution space: Q_p (hex), P_p(tri) x P_p(z) (prism) or
+    P_p (tetrahedron)."""
     c = rng.standard_normal((p + 1, p + 1, p + 1))
     if etype == 1:
         for a in range(p + 1):
             for b in range(p + 1):
                 if a + b > p:
                     c[a, b, :] = 0
+    if etype == 2:
+        for (a, b, cc), _ in np.ndenumerate(c):
+            if a + b + cc > p:
+                c[a, b, cc] = 0
     return c
 
 
@@ -135,6 +142,65 @@ def test_triangle_basis_orthonormal_and_complete(p):
             assert np.abs(proj - m).max() < 1e-12
 
 
+def _jacobi_moment(alpha, k):
+    """int_{-1}^{1} (1-x)^alpha x^k dx by the binomial expansion of (1-x)^alpha."""
+    return sum(math.comb(alpha, j) * (-1) ** j * (2.0 / (j + k + 1) if (j + k) % 2 == 0 else 0.0)
+               for j in range(alpha + 1))
+
+
+@pytest.mark.parametrize("alpha", [0, 1, 2])
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6, 7])
+def test_gauss_jacobi_rule_exactness(alpha, n):
+    """Reading T2's 1D rules: the n-point Gauss rule of the weight (1-x)^alpha integrates x^k
+    exactly for k <= 2n-1 (closed-form moments) and not for k = 2n; alpha = 0 is Gauss-Legendre."""
+    x, w = O.gauss_jacobi(n, alpha)
+    assert np.all(np.diff(x) > 0) and np.all(np.abs(x) < 1) and np.all(w > 0)
+    for k in range(2 * n):
+        assert abs((w * x ** k).sum() - _jacobi_moment(alpha, k)) < 1e-14
+    assert abs((w * x ** (2 * n)).sum() - _jacobi_moment(alpha, 2 * n)) > 1e-8
+    if alpha == 0:
+        np.testing.assert_allclose(x, O.gauss_legendre(n)[0], atol=1e-15)
+
+
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
+def test_collapsed_tetrahedron_rule_strength(k):
+    """Reading T2: the k^3 collapsed rule integrates lambda1^a lambda2^b lambda3^c exactly for
+    a+b+c <= 2k-1, with lambda_i = (x_i+1)/2 and the Dirichlet integral
+    int_T lambda1^a lambda2^b lambda3^c dV = 8 a! b! c! / (a+b+c+3)! (8 = the map's Jacobian);
+    it fails at degree 2k (catches a wrong Jacobian weight or a wrong Gauss-Jacobi exponent)."""
+    xyz, w = O.tet_rule(k)
+    lam = (xyz + 1) / 2
+    assert np.all(lam > 0) and np.all(lam.sum(axis=1) < 1) and np.all(w > 0)
+    f = math.factorial
+    for a in range(2 * k):
+        for b in range(2 * k - a):
+            for c in range(2 * k - a - b):
+                exact = 8.0 * f(a) * f(b) * f(c) / f(a + b + c + 3)
+                got = (w * lam[:, 0] ** a * lam[:, 1] ** b * lam[:, 2] ** c).sum()
+                assert abs(got - exact) < 1e-14
+    worst = max(abs((w * lam[:, 0] ** a * lam[:, 2] ** (2 * k - a)).sum()
+                    - 8.0 * f(a) * f(2 * k - a) / f(2 * k + 3)) for a in range(2 * k + 1))
+    assert worst > 1e-10
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_tetrahedron_points_symmetric_interior_unisolvent(p):
+    """Reading T1: (p+1)(p+2)(p+3)/6 interior points, invariant under the 24 symmetries of the
+    tetrahedron (permutations of the barycentric coordinates), unisolvent for P_p."""
+    import itertools
+    x = O.tet_solution_points(p)
+    assert x.shape[0] == (p + 1) * (p + 2) * (p + 3) // 6
+    lam = np.concatenate([(x + 1) / 2, 1 - ((x + 1) / 2).sum(axis=1, keepdims=True)], axis=1)
+    assert lam.min() > 0.04
+    for perm in itertools.permutations(range(4)):
+        img = lam[:, list(perm)]
+        d = np.abs(img[:, None, :] - lam[None, :, :]).max(axis=2).min(axis=1)
+        assert d.max() < 1e-15
+    V = np.stack([x[:, 0] ** a * x[:, 1] ** b * x[:, 2] ** c for a in range(p + 1) for b in range(p + 1 - a)
+                  for c in range(p + 1 - a - b)], axis=1)
+    assert np.linalg.cond(V) < 1e4
+
+
 # ----------------------------------------------------------------------------------------------
 # Element operators: exactness, projection, lift, sum factorisation
 # ----------------------------------------------------------------------------------------------
@@ -143,10 +209,13 @@ def _oracle_for(etype, p, m=None):
     m = m or p + 2
     if etype == 0:
         return O.Oracle(W.box_hex_mesh(1), p, m)
+    if etype == 2:
+        return O.Oracle(W.box_tet_mesh(1), p, m)
     return O.Oracle(W.mixed_box_mesh(2), p, m)
 
 
-CASES = [(0, 2), (0, 3), (0, 4), (1, 2), (1, 3)]
+CASES = [(0, 2), (0, 3), (0, 4), (1, 2), (1, 3), (2, 2), (2, 3)]
+VOLUME = {0: 8.0, 1: 4.0, 2: 4.0 / 3.0}
 
 
 @pytest.mark.parametrize("etype,p", CASES)
@@ -176,8 +245,7 @@ def test_volume_quadrature_and_projection(etype, p):
     residual is orthogonal to the space)."""
     o = _oracle_for(etype, p)
     xq, wq, M7, M8 = o.op(etype, "xq"), o.op(etype, "wq"), o.op(etype, "M7"), o.op(etype, "M8")
-    vol = 8.0 if etype == 0 else 4.0
-    assert abs(wq.sum() - vol) < 1e-13
+    assert abs(wq.sum() - VOLUME[etype]) < 1e-13
     np.testing.assert_allclose(M8 @ M7, np.eye(M7.shape[1]), atol=1e-13)
     rng = np.random.default_rng(3)
     g = np.cos(1.3 * xq[:, 0] + 0.7 * xq[:, 1] - 0.4 * xq[:, 2]) + xq[:, 2] ** (p + 1)
@@ -236,6 +304,18 @@ def test_lift_is_dg_lift(etype, p):
                 S, T = np.meshgrid(gx, gx, indexing="ij")
                 pts = np.zeros((S.size, 3)); pts[:, d] = n[d]; pts[:, tang[0]] = S.ravel(); pts[:, tang[1]] = T.ravel()
                 wts = np.outer(gw, gw).ravel()
+            elif etype == 2:
+                # triangle faces of the tetrahedron, parametrised by the reference triangle (s, t)
+                s_, t_ = txy[:, 0], txy[:, 1]
+                one = np.ones_like(s_)
+                if n[2] < -0.5:
+                    pts = np.stack([s_, t_, -one], 1); wts = tw
+                elif n[1] < -0.5:
+                    pts = np.stack([s_, -one, t_], 1); wts = tw
+                elif n[0] < -0.5:
+                    pts = np.stack([-one, s_, t_], 1); wts = tw
+                else:
+                    pts = np.stack([-1 - s_ - t_, s_, t_], 1); wts = tw * math.sqrt(3.0)
             elif abs(n[2]) > 0.5:
                 pts = np.zeros((txy.shape[0], 3)); pts[:, :2] = txy; pts[:, 2] = n[2]; wts = tw
             else:
@@ -298,11 +378,37 @@ def test_dense_equals_sum_factorised(p, m):
         assert np.abs(M0[s] - row).max() < 1e-14
 
 
+@pytest.mark.parametrize("etype,p", CASES)
+def test_corrected_derivatives_integrate_by_parts(etype, p):
+    """Green's identity on every element type: with a zero common value the corrected gradient
+    operator M4 - M6 M0 satisfies int v (Agrad_d u) dV = -int u (d_d v) dV, and the corrected
+    divergence M1 - M3 M2 satisfies int v (Adiv F) dV = -sum_d int F_d (d_d v) dV, for u, v, F_d in
+    the solution space. This pins the lift, the reference normals and the face measure of every
+    face at once (a slanted face's sqrt 2 or sqrt 3, a flipped normal or a transposed lift fail)."""
+    o = _oracle_for(etype, p)
+    xu, wq, M7, D = o.op(etype, "xu"), o.op(etype, "wq"), o.op(etype, "M7"), o.op(etype, "D")
+    Ag, Ad = o.op(etype, "Agrad"), o.op(etype, "Adiv")
+    rng = np.random.default_rng(5)
+    ip = lambda a, b: (wq * (M7 @ a) * (M7 @ b)).sum()  # noqa: E731
+    for _ in range(2):
+        u = _eval_poly3(_random_space_poly(rng, p, etype), xu)
+        v = _eval_poly3(_random_space_poly(rng, p, etype), xu)
+        F = [_eval_poly3(_random_space_poly(rng, p, etype), xu) for _ in range(3)]
+        for d in range(3):
+            lhs, rhs = ip(v, Ag[d] @ u), -ip(u, D[d] @ v)
+            assert abs(lhs - rhs) < 1e-11 * max(1.0, abs(rhs))
+        lhs = ip(v, np.einsum("zdk,dk->z", Ad, np.array(F)))
+        rhs = -sum(ip(F[d], D[d] @ v) for d in range(3))
+        assert abs(lhs - rhs) < 1e-11 * max(1.0, abs(rhs))
+
+
 def test_operator_identities():
     """The rewrites of Eqs. (Qsubs) and (subs): tgradpcoru's M4 - M6 M0 and tdivtpcorf's M1 - M3 M2
     applied to a field equal the two-step forms."""
     o = _oracle_for(1, 3)
-    for t in (0, 1):
+    for t in (0, 1, 2):
+        if t == 2:
+            o = _oracle_for(2, 3)
         D, M0, lift, nref = o.op(t, "D"), o.op(t, "M0"), o.op(t, "lift"), o.op(t, "nref")
         Ag, Ad = o.op(t, "Agrad"), o.op(t, "Adiv")
         u = np.random.default_rng(0).standard_normal(D.shape[1])
@@ -326,6 +432,8 @@ MESHES = {
     "sheared3": lambda: W.sheared_box_mesh(3),
     "mixed2": lambda: W.mixed_box_mesh(2),
     "mixed4": lambda: W.mixed_box_mesh(4),
+    "tet2": lambda: W.box_tet_mesh(2),
+    "tetshear2": lambda: W.box_tet_mesh(2, shear=True),
 }
 
 
@@ -336,7 +444,7 @@ def test_freestream_preservation(name, p):
     self-periodic, sheared and mixed hex/prism meshes. Rounding in the divergence grows with the
     operator norm, so the bound is relative to the RHS scale max|f| (2/h) (p+1)^2."""
     mesh = MESHES[name]()
-    if mesh["pri_v"].shape[0] and p != 3:
+    if (mesh["pri_v"].shape[0] or mesh.get("tet_v", np.zeros((0, 4))).shape[0]) and p != 3:
         pytest.skip("printed triangle points exist for p=2,3 only")
     o = O.Oracle(mesh, p, p + 2)
     blocks = _layout(o, mesh)
@@ -352,7 +460,7 @@ def _tgv(o, mesh, perturb=0.0, mach=0.1):
     return W.tgv_state(o.sol_coords(), _layout(o, mesh), mach=mach, perturb=perturb)
 
 
-@pytest.mark.parametrize("name", ["hex1_self_periodic", "hex3", "sheared3", "mixed4"])
+@pytest.mark.parametrize("name", ["hex1_self_periodic", "hex3", "sheared3", "mixed4", "tetshear2"])
 def test_discrete_conservation(name):
     """Check (e): the quadrature-weighted RHS sums to zero to 1e-12 relative, per variable."""
     mesh = MESHES[name]()
@@ -410,6 +518,37 @@ def test_rhs_converges_to_analytic_navier_stokes(meshfn, m, surf):
     assert np.all(e_inv[1] < 1e-2), e_inv
     assert np.all(np.log2(e_vis[0] / e_vis[1]) > 1.5), e_vis
     assert np.all(e_vis[1] < 0.1), e_vis
+
+
+def test_tetrahedra_rhs_converges_to_analytic_navier_stokes():
+    """Consistency of the tetrahedral discretisation (readings T1, T2) on the sheared Kuhn mesh,
+    whose elements have full, non-diagonal Jacobians: on the compressible wave field of the hex test
+    the inviscid RHS converges at order >= p - 0.5 and the viscous part at order >= p - 1.5 between
+    8^3 and 16^3 cells (3,072 and 24,576 tetrahedra)."""
+    from tests.analytic_ns import rhs_function, state_function
+    mach, mu = 0.3, 0.1
+    state = state_function("wave", 1.4, mach)
+    ex_inv = rhs_function("wave", 1.4, mach, 0.0, 0.71)
+    ex_vis = rhs_function("wave", 1.4, mach, mu, 0.71)
+    e_inv, e_vis = [], []
+    for N in (8, 16):
+        mesh = W.box_tet_mesh(N, shear=True)
+        ne = mesh["tet_v"].shape[0]
+        o0 = O.Oracle(mesh, 3, 5, mu=0.0, threads=os.cpu_count())
+        o1 = O.Oracle(mesh, 3, 5, mu=mu, threads=os.cpu_count())
+        x = o0.sol_coords()
+        U = W.to_layout(state(x), [(ne, 20)])
+        r0 = o0.rhs(U).reshape(ne, 5, 20).transpose(1, 0, 2).reshape(5, -1)
+        r1 = o1.rhs(U).reshape(ne, 5, 20).transpose(1, 0, 2).reshape(5, -1)
+        x0, x1 = ex_inv(x), ex_vis(x)
+        e_inv.append(np.abs(r0 - x0).max(axis=1) / np.abs(x0).max(axis=1))
+        dv, dx = (r1 - r0)[1:], (x1 - x0)[1:]
+        e_vis.append(np.abs(dv - dx).max(axis=1) / np.abs(dx).max(axis=1))
+    e_inv, e_vis = np.array(e_inv), np.array(e_vis)
+    assert np.all(np.log2(e_inv[0] / e_inv[1]) > 2.5), e_inv
+    assert np.all(e_inv[1] < 0.05), e_inv
+    assert np.all(np.log2(e_vis[0] / e_vis[1]) > 1.5), e_vis
+    assert np.all(e_vis[1] < 0.5), e_vis
 
 
 def test_penalty_term_is_dissipative_energy_identity():
