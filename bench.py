@@ -211,7 +211,7 @@ def _time_steps(m, U, steps, warmup, torch):
 
 def other_configs(args, torch, fr, W):
     """Mixed hex/prism TGV (40^3 box: 32,000 hexes + 64,000 prisms, p = 3), the 48^3 TGV without
-    anti-aliasing and with full (flux + surface-flux) anti-aliasing, and the batched ensemble
+    anti-aliasing and with full (flux + surface-flux) anti-aliasing, a tetrahedral TGV box, and the batched ensemble
     of 64 TGV instances (edges in {8,...,24}, p in {3,4}, M in [0.05,0.2], Re in [400,3200] from
     SplitMix64(20240111)), each timed over RK4 steps on a side stream (CUDA-graph replay)."""
     out = {}
@@ -253,6 +253,22 @@ def other_configs(args, torch, fr, W):
         m.sync_status()
         out[f"aa_full48_{prec}"] = {"gdof_rhs_per_s": U0.size * RHS_PER_STEP / (ms * 1e-3) / 1e9, "ms_per_step": ms,
                                     "dof": int(U0.size), "elements": N_EDGE ** 3}
+        m.close()
+        del U
+    # tetrahedra: the 24^3 box split into 82,944 Kuhn tetrahedra (p = 3, dense operators, collapsed
+    # 5^3 quadrature), FP64 and FP32 (reference pressure removed)
+    mesh_t = W.box_tet_mesh(24)
+    nt = mesh_t["tet_v"].shape[0]
+    for prec in ("fp64", "fp32"):
+        m = fr.FRMesh(mesh_t, fr.make_params(p=3, prec=prec, p_ref=p0))
+        U0 = W.tgv_state(m.sol_coords(), [(nt, 20)], perturb=1e-3)
+        U = torch.from_numpy(U0).cuda()
+        ms = _time_steps(m, U, steps, 2, torch)
+        m.sync_status()
+        out[f"tet24_{prec}"] = {"gdof_rhs_per_s": U0.size * RHS_PER_STEP / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+                                "dof": int(U0.size), "elements": nt}
+        if prec != "fp64":
+            out[f"tet24_{prec}"]["speedup_vs_fp64"] = out["tet24_fp64"]["ms_per_step"] / ms
         m.close()
         del U
     draws = W.ensemble_draws(64)

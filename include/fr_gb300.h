@@ -3,7 +3,8 @@
  *
  * The library evaluates the right-hand side (RHS) R(u) of the semi-discrete system du/dt = R(u)
  * obtained by flux reconstruction (FR) of the compressible Navier-Stokes equations with flux
- * anti-aliasing, on affine hexahedral and prismatic meshes, and advances it with classical RK4.
+ * anti-aliasing, on affine hexahedral, prismatic and tetrahedral meshes, and advances it with
+ * classical RK4.
  * Paper: Akkurt, Witherden, Vincent, "Cache blocking for flux reconstruction: extension to
  * Navier-Stokes equations and anti-aliasing".
  *   - governing equations, fluxes and the perfect-gas closure: Sec. 2.1 (Eqs. gov, fluxe, fluxv);
@@ -11,6 +12,7 @@
  *     Sec. 2.1 Eqs. FR-disu .. FRfinal, and their kernel form in Sec. 2.2;
  *   - flux anti-aliasing (interpolation to quadrature points, L2 projection): Sec. 2.1.1 and
  *     Sec. 2.2.1 (operators M7..M10); sum factorisation of the hex and prism operators: Sec. 4;
+ *     tetrahedra (listed in Sec. 1 among the supported types) with dense per-element operators;
  *   - the semi-discrete form du/dt = -J^-1 div~ f~: Eq. govqtrans; RK4: Sec. 3.
  *
  * Conventions shared by every entry point
@@ -27,18 +29,22 @@
  *     the state U and the result R: device pointers (or host pointers for the *_host variants).
  *   - Layout of U and R (reading R10 of the design notes): element-major [elem][var][pt], with
  *     var in (rho, rho vx, rho vy, rho vz, E). Elements are ordered instance by instance; inside an
- *     instance hexahedra come first, then prisms, each in descriptor order. Hex point index is
- *     i + n j + n^2 k (n = p+1 Gauss-Legendre points per direction, i fastest along xi); prism
- *     point index is t + 10 k (t = triangle point in the paper's printed Williams-Shunn order,
- *     k = Gauss-Legendre level in z).
+ *     instance hexahedra come first, then prisms, then tetrahedra, each in descriptor order. Hex
+ *     point index is i + n j + n^2 k (n = p+1 Gauss-Legendre points per direction, i fastest along
+ *     xi); prism point index is t + 10 k (t = triangle point in the paper's printed Williams-Shunn
+ *     order, k = Gauss-Legendre level in z); tetrahedron point index runs over the order-3 lattice
+ *     points (a, b, c), a + b + c <= 3, a fastest, then b, then c, each at reference coordinates
+ *     -1/2 + 4/5 (-1 + 2 (a, b, c)/3 + 1/2) (the lattice shrunk by 4/5 towards the centroid).
  *   - Element type of U/R: double for FR_FP64; float for FR_FP32 and the mixed forms. The RK4
  *     entry points always take an FP64 master state (double), whatever the compute precision.
  *   - Vertex order: hexahedra in tensor order (corner a + 2b + 4c for (a,b,c) in {0,1}^3);
  *     prisms v0,v1,v2 at the lower triangle mapped to the reference (-1,-1),(1,-1),(-1,1) and
- *     v3,v4,v5 above them. Elements must be affine (parallelepipeds / straight prisms); other
- *     elements give FR_EUNSUPPORTED.
+ *     v3,v4,v5 above them; tetrahedra v0..v3 mapped to the reference (-1,-1,-1), (1,-1,-1),
+ *     (-1,1,-1), (-1,-1,1). Elements must be affine (parallelepipeds / straight prisms / any
+ *     tetrahedron); other elements give FR_EUNSUPPORTED.
  *   - Local face order (used by the L/R rule): hex -xi, +xi, -eta, +eta, -zeta, +zeta; prism
- *     z=-1 triangle, z=+1 triangle, y=-1 quad, x+y=0 quad, x=-1 quad.
+ *     z=-1 triangle, z=+1 triangle, y=-1 quad, x+y=0 quad, x=-1 quad; tetrahedron z=-1, y=-1,
+ *     x=-1, x+y+z=-1 (each with the 10 printed triangle points as flux points).
  */
 #ifndef FR_GB300_H
 #define FR_GB300_H
@@ -66,7 +72,9 @@ typedef enum {
                            * projection (Sec. 4.1 factorisation; the M7 and M8 triangle blocks) run
                            * on the tensor cores as split products x_hi y_hi + x_lo y_hi + x_hi y_lo
                            * of bf16 halves with FP32 accumulation. Hexahedra run the FR_FP32
-                           * kernels (their sum-factorised 1D operators are not dense contractions). */
+                           * kernels (their sum-factorised 1D operators are not dense contractions)
+                           * unless fr_set_hex_tensor_cores() is on; tetrahedra run the FR_FP32
+                           * kernels. */
     FR_MIXED_FP16 = 3     /* as FR_MIXED_BF16 with fp16 halves; every operand row is scaled by a
                            * power of two first (removed exactly afterwards) so that fp16 keeps
                            * its full precision in the low half */
@@ -84,9 +92,10 @@ typedef struct {
     double mu;            /* dynamic viscosity (constant) */
     double beta;          /* LDG switch (Sec. 2.1 common solution and viscous flux) */
     double tau;           /* LDG penalty */
-    int p;                /* solution order; hex p in {3,4}, prism p = 3 */
+    int p;                /* solution order; hex p in {3,4}, prism and tetrahedron p = 3 */
     int nq1d;             /* Gauss-Legendre quadrature points per line: 0 or p + 2 = flux anti-aliasing
-                           * (Sec. 2.2.1); p + 1 = no anti-aliasing, the flux is evaluated at the
+                           * (Sec. 2.2.1; tetrahedra: the collapsed (p+2)^3 Gauss-Jacobi rule, exact
+                           * to degree 2p+3); p + 1 = no anti-aliasing, the flux is evaluated at the
                            * solution points (the collocation form; hexahedra, fused form only) */
     int tri_strength;     /* prism triangle quadrature strength (0 = 8); collapsed k x k rule, k = strength/2 + 1 */
     int prec;             /* fr_precision */
@@ -102,7 +111,8 @@ typedef struct {
                            * in FP32 and the mass equation in FP64, then returns R_E = R_(E-H0 rho) +
                            * H0 R_rho. All of it is exact in exact arithmetic; it removes the
                            * O(1/M^2) cancellations of low-Mach flows from the FP32 rounding. Fused
-                           * form, hexahedra and prisms; ignored in FP64. */
+                           * form, hexahedra and prisms (with tetrahedra: FR_EUNSUPPORTED); ignored
+                           * in FP64. */
     int surface_aa;       /* 1: surface-flux anti-aliasing as well (Sec. 2.2.1: the interface flux points
                            * are replaced by the m x m Gauss-Legendre points of each face, m = nq1d; the
                            * common flux is evaluated there and lifted through the face L2 projection).
@@ -119,6 +129,8 @@ typedef struct {
     const int *hex_v;     /* [n_hex][8] vertex ids, tensor order */
     const int *pri_v;     /* [n_pri][6] vertex ids */
     double period[3];     /* periodic box lengths; 0 = not periodic. Faces are matched modulo period */
+    int n_tet;            /* number of tetrahedra (p = 3, flux anti-aliasing, fused form) */
+    const int *tet_v;     /* [n_tet][4] vertex ids */
 } fr_mesh_desc;
 
 typedef struct fr_mesh fr_mesh;

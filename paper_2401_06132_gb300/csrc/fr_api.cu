@@ -43,7 +43,7 @@ extern "C" const char *fr_last_error(void) { return g_err.c_str(); }
 // ---------------------------------------------------------------------------------------------
 struct InstanceHost {
     fr_params prm;
-    int n_hex, n_pri;
+    int n_hex, n_pri, n_tet;
     std::vector<double> x0J;   // per element: x0[3], J[9] (row-major dx_i/dxi_j); x = x0 + J (xi + 1)
 };
 
@@ -77,6 +77,9 @@ struct fr_mesh {
     bool has_pri = false;
     void *d_priops = nullptr;            // PriOps<T> on the device
     void *d_priops64 = nullptr;          // PriOpsFF (low-Mach FP32 form with prisms)
+    frb::Tet3D tet;                      // tetrahedron operators (p = 3)
+    bool has_tet = false;
+    void *d_tetops = nullptr;            // TetOps<T> on the device
     std::vector<Group> groups;
     bool split_c = false;              // interface phase as pair flux (C1) + lift (C2)
     bool lowmach = false;              // FP32 low-Mach form (deviations, reduced energy, FP64 mass)
@@ -222,6 +225,20 @@ static void ref_faces(const fr_mesh *m, int blk, RefFaces &r)
             r.centre[f][0] = r.centre[f][1] = r.centre[f][2] = 0.0;
             r.centre[f][f / 2] = (f & 1) ? 1.0 : -1.0;
         }
+        return;
+    }
+    if (B.type == 2) {
+        const frb::Tet3D &Tt = m->tet;
+        static const double cen[4][3] = {{-1.0 / 3, -1.0 / 3, -1}, {-1.0 / 3, -1, -1.0 / 3}, {-1, -1.0 / 3, -1.0 / 3},
+                                         {-1.0 / 3, -1.0 / 3, -1.0 / 3}};
+        r.nfaces = 4;
+        for (int f = 0; f < 4; f++) {
+            r.count[f] = 10; r.off[f] = 10 * f;
+            for (int d = 0; d < 3; d++) r.centre[f][d] = cen[f][d];
+        }
+        r.xf.assign((size_t)FR_TF * 3, 0.0);
+        for (int s2 = 0; s2 < FR_TF; s2++)
+            for (int d = 0; d < 3; d++) r.xf[(size_t)s2 * 3 + d] = Tt.xf[s2][d];
         return;
     }
     const frb::Prism2D &P = m->pri;
@@ -446,15 +463,15 @@ static fr_status match_instance(fr_mesh *m, int ii, int b0, int b1, const fr_mes
 // Affine map of one element from its vertices; rejects non-affine and inverted elements.
 static fr_status element_map(int ii, long long e, int type, const fr_mesh_desc *d, double *x0J, std::vector<double> &geo)
 {
-    const int nv = type == 0 ? 8 : 6;
-    const int *conn = type == 0 ? d->hex_v + 8 * e : d->pri_v + 6 * e;
+    const int nv = type == 0 ? 8 : (type == 1 ? 6 : 4);
+    const int *conn = type == 0 ? d->hex_v + 8 * e : (type == 1 ? d->pri_v + 6 * e : d->tet_v + 4 * e);
     const double *v[8];
     for (int k = 0; k < nv; k++) {
         int vi = conn[k];
         if (vi < 0 || vi >= d->n_verts) return fail(FR_EMESH, "instance %d element %lld: vertex id %d out of range", ii, e, vi);
         v[k] = d->verts + 3 * (size_t)vi;
     }
-    const int c3 = type == 0 ? 4 : 3;   // corner along the third reference axis
+    const int c3 = type == 0 ? 4 : 3;   // corner along the third reference axis (prisms, tetrahedra: v3)
     double scale = 0;
     for (int i = 0; i < 3; i++) {
         x0J[i] = v[0][i];
@@ -499,10 +516,10 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
         // the solution points, i.e. the collocation form without anti-aliasing (hexahedra only)
         if (P.p < 3 || P.p > 4 || (m1 != P.p + 2 && m1 != P.p + 1))
             return fail(FR_EUNSUPPORTED, "instance %d: order %d with %d quadrature points", ii, P.p, m1);
-        if (m1 == P.p + 1 && d && d->n_pri > 0)
-            return fail(FR_EUNSUPPORTED, "instance %d: prisms are built with flux anti-aliasing only", ii);
+        if (m1 == P.p + 1 && d && (d->n_pri > 0 || d->n_tet > 0))
+            return fail(FR_EUNSUPPORTED, "instance %d: prisms and tetrahedra are built with flux anti-aliasing only", ii);
         if (P.surface_aa) {
-            if (n_inst != 1 || !d || d->n_pri > 0 || m1 != P.p + 2)
+            if (n_inst != 1 || !d || d->n_pri > 0 || d->n_tet > 0 || m1 != P.p + 2)
                 return fail(FR_EUNSUPPORTED, "surface-flux anti-aliasing runs single-instance hexahedral meshes with m = p + 2");
             if (P.prec != FR_FP64 && P.p_ref > 0 && P.rho_ref > 0)
                 return fail(FR_EUNSUPPORTED, "surface-flux anti-aliasing runs without the low-Mach form");
@@ -512,20 +529,26 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
             !(P.rho_ref >= 0.0))
             return fail(FR_EINVAL, "instance %d: bad physical parameters", ii);
         if (P.rusanov_mode != 0) return fail(FR_EUNSUPPORTED, "rusanov_mode %d", P.rusanov_mode);
-        if (d->n_hex < 0 || d->n_pri < 0 || d->n_hex + d->n_pri == 0 || d->n_verts <= 0 || !d->verts)
+        if (d->n_hex < 0 || d->n_pri < 0 || d->n_tet < 0 || d->n_hex + d->n_pri + d->n_tet == 0 || d->n_verts <= 0 ||
+            !d->verts)
             return fail(FR_EINVAL, "instance %d: empty or malformed mesh", ii);
         if (d->n_hex > 0 && !d->hex_v) return fail(FR_EINVAL, "instance %d: null hex connectivity", ii);
         if (d->n_pri > 0 && !d->pri_v) return fail(FR_EINVAL, "instance %d: null prism connectivity", ii);
+        if (d->n_tet > 0 && !d->tet_v) return fail(FR_EINVAL, "instance %d: null tetrahedron connectivity", ii);
+        if (d->n_tet > 0 && P.p != 3)
+            return fail(FR_EUNSUPPORTED, "instance %d: tetrahedra are built for p = 3", ii);
+        if (d->n_tet > 0 && P.prec != FR_FP64 && P.p_ref > 0 && P.rho_ref > 0)
+            return fail(FR_EUNSUPPORTED, "instance %d: tetrahedra run the plain FP32 form (no low-Mach form)", ii);
         if (d->n_pri > 0 && (P.p != 3 || (P.tri_strength != 0 && P.tri_strength != 8)))
             return fail(FR_EUNSUPPORTED, "instance %d: prisms are built for p = 3 with a strength-8 triangle rule", ii);
         InstanceHost I;
         I.prm = P; I.prm.nq1d = m1;
-        I.n_hex = d->n_hex; I.n_pri = d->n_pri;
-        I.x0J.resize((size_t)(d->n_hex + d->n_pri) * 12);
+        I.n_hex = d->n_hex; I.n_pri = d->n_pri; I.n_tet = d->n_tet;
+        I.x0J.resize((size_t)(d->n_hex + d->n_pri + d->n_tet) * 12);
         m->inst_u0.push_back(u);
         bfirst.push_back((int)m->blocks.size());
-        for (int type = 0; type < 2; type++) {
-            long long ne = type == 0 ? d->n_hex : d->n_pri;
+        for (int type = 0; type < 3; type++) {
+            long long ne = type == 0 ? d->n_hex : (type == 1 ? d->n_pri : d->n_tet);
             if (ne == 0) continue;
             Block B{};
             B.inst = ii; B.type = type; B.p = P.p; B.m = m1;
@@ -535,16 +558,23 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
                 // the quadrature-point ones)
                 if (frb::hex1d(P.p, P.p + 2, h)) return fail(FR_EUNSUPPORTED, "hex operators for p=%d", P.p);
                 B.nu = (P.p + 1) * (P.p + 1) * (P.p + 1); B.nf = 6 * (P.p + 1) * (P.p + 1);
-            } else {
+            } else if (type == 1) {
                 if (!m->has_pri) {
                     if (frb::prism2d(m->pri)) return fail(FR_EUNSUPPORTED, "prism operators");
                     m->has_pri = true;
                 }
                 h = m->pri.z;
                 B.nu = FR_PT * FR_PE; B.nf = 2 * FR_PT + 3 * FR_PE * FR_PE;
+            } else {
+                if (!m->has_tet) {
+                    if (frb::tet3d(m->tet)) return fail(FR_EUNSUPPORTED, "tetrahedron operators");
+                    m->has_tet = true;
+                }
+                std::memset(&h, 0, sizeof h);
+                B.nu = FR_TU; B.nf = FR_TF;
             }
             B.ne = ne; B.elem0 = elem; B.u0 = u; B.f0 = f;
-            long long le0 = type == 0 ? 0 : d->n_hex;
+            long long le0 = type == 0 ? 0 : (type == 1 ? d->n_hex : d->n_hex + d->n_pri);
             for (long long e = 0; e < ne; e++) {
                 fr_status st = element_map(ii, e, type, d, &I.x0J[(size_t)(le0 + e) * 12], m->geo_host);
                 if (st) return st;
@@ -607,6 +637,37 @@ static fr_status upload_priops(fr_mesh *m, void **dst)
 }
 
 template <typename T>
+static fr_status upload_tetops(fr_mesh *m)
+{
+    if (!m->has_tet) return FR_OK;
+    const frb::Tet3D &Tt = m->tet;
+    std::vector<TetOps<T>> o(1);
+    TetOps<T> &t = o[0];
+    for (int j = 0; j < FR_TU; j++) {
+        for (int q = 0; q < FR_TQ; q++) t.Bt[j][q] = (T)Tt.B[q][j];
+        for (int s2 = 0; s2 < FR_TF; s2++) t.M0t[j][s2] = (T)Tt.M0[s2][j];
+        for (int d = 0; d < 3; d++)
+            for (int z = 0; z < FR_TU; z++) t.Dht[d][j][z] = (T)Tt.Dh[d][z][j];
+    }
+    for (int s2 = 0; s2 < FR_TF; s2++)
+        for (int z = 0; z < FR_TU; z++) t.Lt[s2][z] = (T)Tt.L[z][s2];
+    // projection with the corrected divergence: (Dh_d Pj)[z][q], formed in FP64
+    for (int d = 0; d < 3; d++)
+        for (int q = 0; q < FR_TQ; q++)
+            for (int z = 0; z < FR_TU; z++) {
+                double v = 0;
+                for (int j = 0; j < FR_TU; j++) v += Tt.Dh[d][z][j] * Tt.Pj[j][q];
+                t.Dvt[d][q][z] = (T)v;
+            }
+    for (int f = 0; f < 4; f++)
+        for (int d = 0; d < 3; d++) t.nf[f][d] = (T)Tt.nf[f][d];
+    fr_status st = dalloc(m, &m->d_tetops, sizeof(TetOps<T>));
+    if (st) return st;
+    CU(cudaMemcpy(m->d_tetops, o.data(), sizeof(TetOps<T>), cudaMemcpyHostToDevice));
+    return FR_OK;
+}
+
+template <typename T>
 static fr_status upload_geo(fr_mesh *m)
 {
     std::vector<Geo<T>> g((size_t)m->ne);
@@ -644,11 +705,12 @@ static void build_face_normals(fr_mesh *m)
         for (long long e = 0; e < B.ne; e++) {
             const long long ge = B.elem0 + e;
             const double *Ji = &m->geo_host[(size_t)ge * 10], det = m->geo_host[(size_t)ge * 10 + 9];
-            const int nfaces = B.type == 0 ? 6 : 5;
+            const int nfaces = B.type == 0 ? 6 : (B.type == 1 ? 5 : 4);
             for (int f = 0; f < nfaces; f++) {
                 double nr[3] = {0, 0, 0};
                 if (B.type == 0) nr[f / 2] = (f & 1) ? 1.0 : -1.0;
-                else for (int d = 0; d < 3; d++) nr[d] = pri_n[f][d];
+                else if (B.type == 1) for (int d = 0; d < 3; d++) nr[d] = pri_n[f][d];
+                else for (int d = 0; d < 3; d++) nr[d] = m->tet.nf[f][d];
                 double ns[3];
                 for (int k = 0; k < 3; k++) ns[k] = det * (Ji[k] * nr[0] + Ji[3 + k] * nr[1] + Ji[6 + k] * nr[2]);
                 const double mag = std::sqrt(ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]);
@@ -789,6 +851,7 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
     size_t ts = tsize(m->prec);
     st = (m->prec == FR_FP64) ? upload_geo<double>(m) : upload_geo<float>(m);
     if (!st) st = (m->prec == FR_FP64) ? upload_priops<double>(m, &m->d_priops) : upload_priops<float>(m, &m->d_priops);
+    if (!st) st = (m->prec == FR_FP64) ? upload_tetops<double>(m) : upload_tetops<float>(m);
     if (!st && m->prec != FR_FP64) {
         bool all = true;
         for (const InstanceHost &I : m->inst) all = all && I.prm.p_ref > 0 && I.prm.rho_ref > 0;
@@ -823,7 +886,7 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
     }
     if (!st) st = (m->prec == FR_FP64) ? build_groups<double>(m, partner) : build_groups<float>(m, partner);
     // FP64 hexahedral handles evaluate each interface pair once (split interface phase)
-    m->split_c = ((m->prec == FR_FP64) && !m->has_pri) || m->surf;
+    m->split_c = ((m->prec == FR_FP64) && !m->has_pri && !m->has_tet) || m->surf;
     if (!st && m->surf) {
         std::vector<uint32_t> ql;
         for (long long q = 0; q < m->nqf; q++)
@@ -861,7 +924,7 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
 extern "C" fr_status fr_destroy(fr_mesh *m)
 {
     if (!m) return FR_OK;
-    void **bufs[] = {&m->d_fnrm, (void **)&m->d_fnrm64, &m->d_geo64, (void **)&m->d_MF, (void **)&m->d_RL, &m->d_priops, &m->d_priops64, &m->d_geo, (void **)&m->d_partner, &m->d_UF, &m->d_FV, &m->d_CF, &m->d_QF, &m->d_DF, &m->d_Qu,
+    void **bufs[] = {&m->d_fnrm, (void **)&m->d_fnrm64, &m->d_geo64, (void **)&m->d_MF, (void **)&m->d_RL, &m->d_priops, &m->d_priops64, &m->d_tetops, &m->d_geo, (void **)&m->d_partner, &m->d_UF, &m->d_FV, &m->d_CF, &m->d_QF, &m->d_DF, &m->d_Qu,
                      &m->d_UQ, &m->d_QQ, &m->d_Rt, &m->d_rk_k, &m->d_rk_us, (void **)&m->d_rk_acc, &m->d_io_U,
                      &m->d_io_R, (void **)&m->d_wsum, (void **)&m->d_status, &m->d_Qsnap, (void **)&m->d_qpartner,
                      &m->d_UFQ, &m->d_FVQ, (void **)&m->d_qlpts, &m->d_DQ};
@@ -1060,7 +1123,8 @@ static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, co
                     a.rkus = reinterpret_cast<T *>(rk.us);
                 }
                 int lr = b.type == 0 ? hex_fused_phase<T>(b.p, ph, a, s, gr.variant)
-                                     : pri_fused_phase<T>(ph, a, reinterpret_cast<const PriOps<T> *>(m->d_priops), reinterpret_cast<const PriOpsFF *>(m->d_priops64), s);
+                         : b.type == 1 ? pri_fused_phase<T>(ph, a, reinterpret_cast<const PriOps<T> *>(m->d_priops), reinterpret_cast<const PriOpsFF *>(m->d_priops64), s)
+                                       : tet_fused_phase<T>(ph, a, reinterpret_cast<const TetOps<T> *>(m->d_tetops), s);
                 if (lr) return fail(FR_ECUDA, "fused phase %d launch: %s", ph, cudaGetErrorString(cudaGetLastError()));
             }
         }
@@ -1113,7 +1177,8 @@ static fr_status autotune_impl(fr_mesh *m, const void *U, void *R, cudaStream_t 
             a.fnrm64 = reinterpret_cast<const ff *>(gr.d_fnrm64);
         }
         int lr = b.type == 0 ? hex_fused_phase<T>(b.p, 0, a, s, gr.variant)
-                             : pri_fused_phase<T>(0, a, reinterpret_cast<const PriOps<T> *>(m->d_priops), reinterpret_cast<const PriOpsFF *>(m->d_priops64), s);
+                 : b.type == 1 ? pri_fused_phase<T>(0, a, reinterpret_cast<const PriOps<T> *>(m->d_priops), reinterpret_cast<const PriOpsFF *>(m->d_priops64), s)
+                               : tet_fused_phase<T>(0, a, reinterpret_cast<const TetOps<T> *>(m->d_tetops), s);
         if (lr) return fail(FR_ECUDA, "autotune: face phase launch failed");
     }
     cudaEvent_t e0, e1;
@@ -1366,13 +1431,14 @@ extern "C" fr_status fr_sol_coords(const fr_mesh *m, double *xyz)
         const InstanceHost &I = m->inst[B.inst];
         const frb::Hex1D &h = m->hex1d[b];
         int n = h.n;
-        long long le0 = B.type == 0 ? 0 : I.n_hex;
+        long long le0 = B.type == 0 ? 0 : (B.type == 1 ? I.n_hex : I.n_hex + I.n_pri);
         for (long long e = 0; e < B.ne; e++) {
             const double *x0J = &I.x0J[(size_t)(le0 + e) * 12];
             for (int z = 0; z < B.nu; z++, k++) {
                 double X[3];
                 if (B.type == 0) { X[0] = h.x[z % n]; X[1] = h.x[(z / n) % n]; X[2] = h.x[z / (n * n)]; }
-                else { X[0] = m->pri.xt[z % FR_PT][0]; X[1] = m->pri.xt[z % FR_PT][1]; X[2] = h.x[z / FR_PT]; }
+                else if (B.type == 1) { X[0] = m->pri.xt[z % FR_PT][0]; X[1] = m->pri.xt[z % FR_PT][1]; X[2] = h.x[z / FR_PT]; }
+                else { X[0] = m->tet.x[z][0]; X[1] = m->tet.x[z][1]; X[2] = m->tet.x[z][2]; }
                 affine_point(x0J, X, xyz + 3 * k);
             }
         }
@@ -1429,7 +1495,7 @@ extern "C" fr_status fr_diagnostics(fr_mesh *m, const void *U, const void *R, do
         const frb::Hex1D &h = m->hex1d[bi];
         for (int z = 0; z < b.nu; z++)
             wp.w[z] = b.type == 0 ? h.w[z % h.n] * h.w[(z / h.n) % h.n] * h.w[z / (h.n * h.n)]
-                                  : m->pri.wt[z % FR_PT] * h.w[z / FR_PT];
+                    : b.type == 1 ? m->pri.wt[z % FR_PT] * h.w[z / FR_PT] : m->tet.w[z];
         int grid = (int)std::min<long long>(std::max<long long>(b.ne, 1), 152LL * 8);
         double *o = m->d_wsum + 8 * b.inst;
         size_t ts = tsize(m->prec);
@@ -1507,7 +1573,7 @@ extern "C" fr_status fr_diagnostics_noalloc(fr_mesh *m, const void *U, const voi
         const frb::Hex1D &h = m->hex1d[bi];
         for (int z = 0; z < b.nu; z++)
             wp.w[z] = b.type == 0 ? h.w[z % h.n] * h.w[(z / h.n) % h.n] * h.w[z / (h.n * h.n)]
-                                  : m->pri.wt[z % FR_PT] * h.w[z / FR_PT];
+                    : b.type == 1 ? m->pri.wt[z % FR_PT] * h.w[z / FR_PT] : m->tet.w[z];
         int grid = (int)std::min<long long>(std::max<long long>(b.ne, 1), 152LL * 8);
         double *o = acc + 8 * b.inst;
         size_t ts = tsize(m->prec);

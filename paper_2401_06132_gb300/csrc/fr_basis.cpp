@@ -284,4 +284,244 @@ int prism2d(Prism2D &P)
     return 0;
 }
 
+// Gauss rule of the weight (1-x)^alpha on [-1,1]: the three-term recurrence of its monic orthogonal
+// polynomials from the discretised Stieltjes procedure (inner products by the 16-point GL rule,
+// exact for the degrees met here), then Golub-Welsch: the nodes are the eigenvalues of the Jacobi
+// matrix and the weights mu_0 times the squared first eigenvector components; two Newton steps on
+// the recurrence polish the nodes. Nodes ascending.
+static int gauss_weight_rule(int n, int alpha, double *x, double *w)
+{
+    if (n < 1 || n > 8) return -1;
+    double g[16], gw[16], ww[16], pm[16], pc[16];
+    gauss_legendre(16, g, gw);
+    for (int q = 0; q < 16; q++) {
+        ww[q] = gw[q] * std::pow(1.0 - g[q], alpha);
+        pm[q] = 0.0;
+        pc[q] = 1.0;
+    }
+    double ak[8], bk[8], nprev = 1.0;
+    for (int k = 0; k < n; k++) {
+        double nk = 0, xk = 0;
+        for (int q = 0; q < 16; q++) { nk += ww[q] * pc[q] * pc[q]; xk += ww[q] * g[q] * pc[q] * pc[q]; }
+        ak[k] = xk / nk;
+        bk[k] = k ? nk / nprev : nk;   // b_0 = mu_0
+        nprev = nk;
+        for (int q = 0; q < 16; q++) {
+            double nx = (g[q] - ak[k]) * pc[q] - (k ? bk[k] : 0.0) * pm[q];
+            pm[q] = pc[q];
+            pc[q] = nx;
+        }
+    }
+    double a[64], v[64];
+    for (int i = 0; i < n * n; i++) a[i] = 0.0;
+    for (int k = 0; k < n; k++) a[k * n + k] = ak[k];
+    for (int k = 1; k < n; k++) a[(k - 1) * n + k] = a[k * n + k - 1] = std::sqrt(bk[k]);
+    jacobi_eig(n, a, v);
+    int idx[8];
+    for (int i = 0; i < n; i++) idx[i] = i;
+    for (int i = 0; i < n; i++)
+        for (int j = i + 1; j < n; j++)
+            if (a[idx[j] * n + idx[j]] < a[idx[i] * n + idx[i]]) { int t = idx[i]; idx[i] = idx[j]; idx[j] = t; }
+    for (int i = 0; i < n; i++) {
+        double xi = a[idx[i] * n + idx[i]];
+        for (int it = 0; it < 2; it++) {
+            double p0 = 0.0, p1 = 1.0, d0 = 0.0, d1 = 0.0;
+            for (int k = 0; k < n; k++) {
+                double p2 = (xi - ak[k]) * p1 - (k ? bk[k] : 0.0) * p0;
+                double d2 = p1 + (xi - ak[k]) * d1 - (k ? bk[k] : 0.0) * d0;
+                p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+            }
+            xi -= p1 / d1;
+        }
+        x[i] = xi;
+        double v0 = v[0 * n + idx[i]];
+        w[i] = bk[0] * v0 * v0;
+    }
+    return 0;
+}
+
+// Monomials x^i y^j z^k with i + j + k <= 3 (20 of them) and their gradients.
+static void monomials3d(const double *X, double *m, double (*dm)[FR_TU])
+{
+    int k = 0;
+    for (int d = 0; d <= 3; d++)
+        for (int i = d; i >= 0; i--)
+            for (int j = d - i; j >= 0; j--) {
+                const int l = d - i - j, e[3] = {i, j, l};
+                m[k] = std::pow(X[0], i) * std::pow(X[1], j) * std::pow(X[2], l);
+                if (dm)
+                    for (int c = 0; c < 3; c++) {
+                        double v = e[c];
+                        for (int cc = 0; cc < 3; cc++) v *= std::pow(X[cc], cc == c ? (e[cc] ? e[cc] - 1 : 0) : e[cc]);
+                        dm[c][k] = e[c] ? v : 0.0;
+                    }
+                k++;
+            }
+}
+
+// In-place inverse of an n x n matrix (n <= FR_TU), Gauss-Jordan with partial pivoting.
+static int invert_n(int n, double *a)
+{
+    double aug[FR_TU][2 * FR_TU];
+    if (n > FR_TU) return -1;
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < 2 * n; j++) aug[i][j] = j < n ? a[i * n + j] : (j - n == i ? 1.0 : 0.0);
+    for (int c = 0; c < n; c++) {
+        int piv = c;
+        for (int r = c + 1; r < n; r++) if (std::fabs(aug[r][c]) > std::fabs(aug[piv][c])) piv = r;
+        if (std::fabs(aug[piv][c]) < 1e-300) return -1;
+        for (int j = 0; j < 2 * n; j++) { double t = aug[c][j]; aug[c][j] = aug[piv][j]; aug[piv][j] = t; }
+        double d = aug[c][c];
+        for (int j = 0; j < 2 * n; j++) aug[c][j] /= d;
+        for (int r = 0; r < n; r++) {
+            if (r == c || aug[r][c] == 0.0) continue;
+            double f = aug[r][c];
+            for (int j = 0; j < 2 * n; j++) aug[r][j] -= f * aug[c][j];
+        }
+    }
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) a[i * n + j] = aug[i][n + j];
+    return 0;
+}
+
+int tet3d(Tet3D &T)
+{
+    std::memset(&T, 0, sizeof(T));
+    // solution points: order-3 lattice (a, b, c)/3, a fastest, shrunk by 4/5 towards (-1/2,-1/2,-1/2)
+    int k = 0;
+    for (int c = 0; c <= 3; c++)
+        for (int b = 0; b <= 3 - c; b++)
+            for (int a = 0; a <= 3 - b - c; a++) {
+                const double X[3] = {-1.0 + 2.0 * a / 3.0, -1.0 + 2.0 * b / 3.0, -1.0 + 2.0 * c / 3.0};
+                for (int d = 0; d < 3; d++) T.x[k][d] = -0.5 + 0.8 * (X[d] + 0.5);
+                k++;
+            }
+    // flux points: the printed triangle points on each face, X = face map of (s, t)
+    Prism2D P;
+    if (prism2d(P)) return -1;
+    const double r3 = 1.0 / std::sqrt(3.0);
+    const double nrm[4][3] = {{0, 0, -1}, {0, -1, 0}, {-1, 0, 0}, {r3, r3, r3}};
+    const double dS[4] = {1.0, 1.0, 1.0, std::sqrt(3.0)};
+    std::memcpy(T.nf, nrm, sizeof nrm);
+    for (int f = 0; f < 4; f++)
+        for (int t = 0; t < 10; t++) {
+            const double s = P.xt[t][0], u = P.xt[t][1];
+            double *X = T.xf[10 * f + t];
+            if (f == 0) { X[0] = s; X[1] = u; X[2] = -1.0; }
+            else if (f == 1) { X[0] = s; X[1] = -1.0; X[2] = u; }
+            else if (f == 2) { X[0] = -1.0; X[1] = s; X[2] = u; }
+            else { X[0] = -1.0 - s - u; X[1] = s; X[2] = u; }
+        }
+    // collapsed rule: GL in a, the Gauss rules of (1-b) and (1-c)^2 in b and c
+    double ga[5], wa[5], gb[5], wb[5], gc[5], wc[5];
+    gauss_legendre(5, ga, wa);
+    if (gauss_weight_rule(5, 1, gb, wb) || gauss_weight_rule(5, 2, gc, wc)) return -2;
+    for (int ic = 0; ic < 5; ic++)
+        for (int ib = 0; ib < 5; ib++)
+            for (int ia = 0; ia < 5; ia++) {
+                const int q = ia + 5 * ib + 25 * ic;
+                T.xq[q][0] = 0.25 * (1.0 + ga[ia]) * (1.0 - gb[ib]) * (1.0 - gc[ic]) - 1.0;
+                T.xq[q][1] = 0.5 * (1.0 + gb[ib]) * (1.0 - gc[ic]) - 1.0;
+                T.xq[q][2] = gc[ic];
+                T.wq[q] = wa[ia] * wb[ib] * wc[ic] / 8.0;
+            }
+    // nodal basis from the monomial Vandermonde matrix: l_z = sum_k m_k C[k][z]
+    double C[FR_TU * FR_TU];
+    for (int z = 0; z < FR_TU; z++) monomials3d(T.x[z], &C[z * FR_TU], nullptr);
+    if (invert_n(FR_TU, C)) return -3;
+    auto nodal = [&](const double *X, double *l, double (*dl)[FR_TU]) {
+        double m[FR_TU], dm[3][FR_TU];
+        monomials3d(X, m, dm);
+        for (int z = 0; z < FR_TU; z++) {
+            double v = 0, g0 = 0, g1 = 0, g2 = 0;
+            for (int kk = 0; kk < FR_TU; kk++) {
+                const double c = C[kk * FR_TU + z];
+                v += m[kk] * c; g0 += dm[0][kk] * c; g1 += dm[1][kk] * c; g2 += dm[2][kk] * c;
+            }
+            l[z] = v;
+            if (dl) { dl[0][z] = g0; dl[1][z] = g1; dl[2][z] = g2; }
+        }
+    };
+    for (int q = 0; q < FR_TQ; q++) nodal(T.xq[q], T.B[q], nullptr);
+    for (int s = 0; s < FR_TF; s++) nodal(T.xf[s], T.M0[s], nullptr);
+    for (int z = 0; z < FR_TU; z++) {
+        double l[FR_TU], dl[3][FR_TU];
+        nodal(T.x[z], l, dl);
+        for (int d = 0; d < 3; d++)
+            for (int j = 0; j < FR_TU; j++) T.D[d][z][j] = dl[d][j];
+    }
+    // mass matrix (the rule is exact to degree 9 >= 6), its inverse, the point weights, projection
+    double M[FR_TU * FR_TU];
+    for (int z = 0; z < FR_TU; z++) {
+        double wz = 0;
+        for (int q = 0; q < FR_TQ; q++) wz += T.wq[q] * T.B[q][z];
+        T.w[z] = wz;
+        for (int j = 0; j < FR_TU; j++) {
+            double v = 0;
+            for (int q = 0; q < FR_TQ; q++) v += T.wq[q] * T.B[q][z] * T.B[q][j];
+            M[z * FR_TU + j] = v;
+        }
+    }
+    if (invert_n(FR_TU, M)) return -4;
+    for (int z = 0; z < FR_TU; z++)
+        for (int q = 0; q < FR_TQ; q++) {
+            double v = 0;
+            for (int j = 0; j < FR_TU; j++) v += M[z * FR_TU + j] * T.B[q][j];
+            T.Pj[z][q] = v * T.wq[q];
+        }
+    // lift: E[z][10 f + t] = dS_f int_face l_z l^face_t; on a face l_z is a polynomial of the face
+    // space, l_z = sum_t' l_z(x_t') l^face_t', so E = dS_f M0_f^T Mf with the face mass matrix Mf of
+    // the triangle's nodal basis (collapsed 5 x 5 triangle rule, exact to degree 8 >= 6)
+    double Mf[10][10];
+    {
+        double Vt[10 * 10];
+        auto mono2 = [](double x, double y, double *m) {
+            int kk = 0;
+            for (int d = 0; d <= 3; d++)
+                for (int j = 0; j <= d; j++) m[kk++] = std::pow(x, d - j) * std::pow(y, j);
+        };
+        for (int t = 0; t < 10; t++) mono2(P.xt[t][0], P.xt[t][1], &Vt[t * 10]);
+        if (invert_n(10, Vt)) return -5;
+        for (int t = 0; t < 10; t++)
+            for (int u = 0; u < 10; u++) Mf[t][u] = 0.0;
+        for (int q = 0; q < FR_PQ; q++) {
+            double m[10], l[10];
+            mono2(P.xq[q][0], P.xq[q][1], m);
+            for (int t = 0; t < 10; t++) {
+                double v = 0;
+                for (int kk = 0; kk < 10; kk++) v += m[kk] * Vt[kk * 10 + t];
+                l[t] = v;
+            }
+            for (int t = 0; t < 10; t++)
+                for (int u = 0; u < 10; u++) Mf[t][u] += P.wq[q] * l[t] * l[u];
+        }
+    }
+    for (int z = 0; z < FR_TU; z++)
+        for (int f = 0; f < 4; f++)
+            for (int t = 0; t < 10; t++) {
+                double e = 0;
+                for (int tp = 0; tp < 10; tp++) e += T.M0[10 * f + tp][z] * Mf[tp][t];
+                T.L[z][10 * f + t] = dS[f] * e;   // E for now
+            }
+    {
+        double E[FR_TU][FR_TF];
+        std::memcpy(E, T.L, sizeof E);
+        for (int z = 0; z < FR_TU; z++)
+            for (int s = 0; s < FR_TF; s++) {
+                double v = 0;
+                for (int j = 0; j < FR_TU; j++) v += M[z * FR_TU + j] * E[j][s];
+                T.L[z][s] = v;
+            }
+    }
+    // corrected derivative
+    for (int d = 0; d < 3; d++)
+        for (int z = 0; z < FR_TU; z++)
+            for (int j = 0; j < FR_TU; j++) {
+                double c = 0;
+                for (int s = 0; s < FR_TF; s++) c += T.L[z][s] * nrm[s / 10][d] * T.M0[s][j];
+                T.Dh[d][z][j] = T.D[d][z][j] - c;
+            }
+    return 0;
+}
+
 }  // namespace frb

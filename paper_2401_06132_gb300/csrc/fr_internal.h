@@ -55,6 +55,28 @@ struct Prism2D {
 };
 int prism2d(Prism2D &P);
 
+// Tetrahedron of order 3 with dense operators (Sec. 1: tetrahedra use no sum factorisation):
+// 20 solution points (the order-3 equispaced lattice shrunk by 4/5 towards the centroid), 4 faces x
+// 10 flux points (the paper's printed Williams-Shunn triangle points), 125 collapsed Gauss-Jacobi
+// quadrature points (exact to total degree 9). Faces: 0 z = -1, 1 y = -1, 2 x = -1, 3 x+y+z = -1.
+#define FR_TU 20      // solution points
+#define FR_TF 40      // flux points
+#define FR_TQ 125     // quadrature points
+struct Tet3D {
+    double x[FR_TU][3];            // solution points (reference coordinates)
+    double w[FR_TU];               // int l_z over the reference tetrahedron
+    double xf[FR_TF][3];           // flux points; face f holds points 10 f .. 10 f + 9
+    double nf[4][3];               // unit outward reference normals
+    double xq[FR_TQ][3], wq[FR_TQ];
+    double B[FR_TQ][FR_TU];        // interpolation to quadrature points (M7)
+    double M0[FR_TF][FR_TU];       // interpolation to flux points
+    double D[3][FR_TU][FR_TU];     // D[d][z][j] = d l_j / dX_d at x_z
+    double L[FR_TU][FR_TF];        // DG-equivalent lift M^-1 E
+    double Dh[3][FR_TU][FR_TU];    // D_d - L diag(n_d) M0: the operator of M4 - M6 M0 and of M1 - M3 M2
+    double Pj[FR_TU][FR_TQ];       // L2 projection (M8)
+};
+int tet3d(Tet3D &T);
+
 }  // namespace frb
 
 // ---------------------------------------------------------------------------------------------
@@ -84,6 +106,18 @@ struct PriOps {
     T lzL[FR_PE], lzR[FR_PE], liftzL[FR_PE], liftzR[FR_PE];
 };
 
+// Tetrahedron (p = 3) operator tables, transposed so that the output index runs fastest (a warp's
+// lanes compute consecutive outputs and read consecutive entries).
+template <typename T>
+struct TetOps {
+    T Bt[FR_TU][FR_TQ];            // B^T: [j][q]
+    T M0t[FR_TU][FR_TF];           // M0^T: [z][s]
+    T Dht[3][FR_TU][FR_TU];        // [d][j][z] = Dh[d][z][j]
+    T Lt[FR_TF][FR_TU];            // [s][z] = L[z][s]
+    T Dvt[3][FR_TQ][FR_TU];        // (Dh_d Pj)^T: projection with the corrected divergence, [d][q][z]
+    T nf[4][3];
+};
+
 // Prism operators as float-float pairs: value = hi + lo (the low-Mach mass channel).
 struct PriOpsFF {
     PriOps<float> hi, lo;
@@ -111,7 +145,7 @@ struct Geo {
 // One block of elements of one type and order inside one instance.
 struct Block {
     int inst;                 // instance index
-    int type;                 // 0 hex, 1 prism
+    int type;                 // 0 hex, 1 prism, 2 tetrahedron
     int p, m;                 // order, 1D quadrature points
     int nu, nf;               // points per element, flux points per element
     long long ne;             // elements
@@ -232,3 +266,5 @@ int hex_upload_ops(int p, int m, const frb::Hex1D &h);
 // Prism kernels (fr_pri.cu); the operator tables are passed by device pointer (opsff: the
 // float-float table of the low-Mach FP32 form's mass channel; null otherwise).
 template <typename T> int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, const PriOpsFF *opsff, cudaStream_t s);
+// Tetrahedral kernels (fr_tet.cu), operator table by device pointer.
+template <typename T> int tet_fused_phase(int phase, const HexArgs<T> &a, const TetOps<T> *ops, cudaStream_t s);

@@ -1,0 +1,276 @@
+// fr_tet.cu -- tetrahedral kernels (p = 3) of the anti-aliased Navier-Stokes FR right-hand side.
+//
+// A tetrahedron has no tensor-product structure, so every operator is a dense matrix applied per
+// element (Sec. 1; sum factorisation, Sec. 4, serves hexahedra and prisms only): 20 solution points,
+// 4 faces x 10 flux points, 125 quadrature points. Same three fused phases as the other types:
+// A face solution, B volume group, C interface group. The volume group evaluates, per element, the
+// con_u average, the corrected gradient (Dh_d u plus the face lift of the common solution, then
+// J^-T), the own-normal viscous flux at the flux points whose LDG weight is not zero, the
+// interpolation of the 20 fields (u and its gradient) to the quadrature points, the pointwise flux
+// and its transformation det J J^-1 f, and the L2 projection with the corrected divergence folded
+// in (R~ = sum_d (Dh_d Pj) f~_d: one dense 20 x 125 operator per direction).
+//
+// The operator tables (TetOps, 100 KB in FP64) stay in global memory, read through the L1/L2
+// caches; they are stored with the output index fastest, so that a warp's lanes, which compute
+// consecutive outputs, read consecutive entries while the field values they multiply are one
+// shared-memory broadcast per warp.
+#include <cuda_runtime.h>
+
+#include "fr_internal.h"
+#include "fr_physics.cuh"
+
+namespace {
+
+constexpr int NU = FR_TU, NF = FR_TF, NQ = FR_TQ;
+
+__device__ __forceinline__ int face_of(int s) { return s / 10; }
+
+// -------------------------------------------------------------------------------------------------
+// Phase A: disu (U^f = M0 U)
+// -------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_tet_disu(HexArgs<T> a, const TetOps<T> *__restrict__ op)
+{
+    const long long total = a.ne * FR_NV * NF;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(it % NF);
+        const long long ea = it / NF;
+        const int alpha = (int)(ea % FR_NV);
+        const long long e = ea / FR_NV;
+        const T *u = a.U + elem_u0(a, e, NU) + alpha * NU;
+        T v = T(0);
+#pragma unroll
+        for (int z = 0; z < NU; z++) v += op->M0t[z][s] * u[z];
+        a.UF[alpha * a.nfpt + elem_f0(a, e, NF) + s] = v;
+    }
+}
+
+// -------------------------------------------------------------------------------------------------
+// Phase B: volume group, one element per CTA of NTH threads (persistent over elements)
+// -------------------------------------------------------------------------------------------------
+template <typename T, int NTH>
+__global__ void __launch_bounds__(NTH) k_tet_B(HexArgs<T> a, const TetOps<T> *__restrict__ op)
+{
+    static_assert(NTH >= NQ, "one thread per quadrature point");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ short s_plist[NF];
+    __shared__ int s_pcnt;
+    T *s_u = reinterpret_cast<T *>(smem_raw);   // [5][NU] state
+    T *s_q = s_u + 5 * NU;                        // [15][NU] physical gradient (field 5 + 3 alpha + d of s_u)
+    T *s_c = s_q + 15 * NU;                       // [5][NF] common solution
+    T *s_w = s_c + 5 * NF;                        // [20][NQ] fields at quadrature points, then f~
+    for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
+        const Geo<T> g = a.geo[e];
+        const Phys<T> ph = elem_phys(a, e);
+        const T *U = a.U + elem_u0(a, e, NU);
+        const long long gf0 = elem_f0(a, e, NF);
+        for (int it = threadIdx.x; it < 5 * NU; it += NTH) s_u[it] = U[it];
+        if (threadIdx.x == 0) s_pcnt = 0;
+        for (int it = threadIdx.x; it < 5 * NF; it += NTH) {   // con_u
+            const int alpha = it / NF, s = it % NF;
+            const uint32_t pc = a.partner[gf0 + s];
+            const bool isL = (pc & FR_LFLAG) != 0;
+            const long long pg = pc & ~FR_LFLAG;
+            const T own = a.UF[alpha * a.nfpt + gf0 + s], oth = a.UF[alpha * a.nfpt + pg];
+            const T uL = isL ? own : oth, uR = isL ? oth : own;
+            s_c[it] = (T(0.5) - ph.beta) * uL + (T(0.5) + ph.beta) * uR;
+        }
+        __syncthreads();
+        // corrected gradient q~_d = Dh_d u + sum_f n_f,d (L_f c), then q = J^-T q~
+        for (int it = threadIdx.x; it < 5 * NU; it += NTH) {
+            const int alpha = it / NU, z = it % NU;
+            const T *u = s_u + alpha * NU;
+            const T *c = s_c + alpha * NF;
+            T q0 = T(0), q1 = T(0), q2 = T(0);
+#pragma unroll 4
+            for (int j = 0; j < NU; j++) {
+                const T uj = u[j];
+                q0 += op->Dht[0][j][z] * uj;
+                q1 += op->Dht[1][j][z] * uj;
+                q2 += op->Dht[2][j][z] * uj;
+            }
+#pragma unroll
+            for (int f = 0; f < 4; f++) {
+                T l = T(0);
+#pragma unroll
+                for (int t = 0; t < 10; t++) l += op->Lt[10 * f + t][z] * c[10 * f + t];
+                q0 += op->nf[f][0] * l;
+                q1 += op->nf[f][1] * l;
+                q2 += op->nf[f][2] * l;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; k++) s_q[(alpha * 3 + k) * NU + z] = g.Ji[k] * q0 + g.Ji[3 + k] * q1 + g.Ji[6 + k] * q2;
+        }
+        __syncthreads();
+        // viscous normal flux at own flux points, on the side whose LDG weight 1/2 +- beta is not
+        // zero (the other side's is never used); the points are compacted so whole warps work
+        for (int s = threadIdx.x; s < NF; s += NTH) {
+            const bool isL = (a.partner[gf0 + s] & FR_LFLAG) != 0;
+            const T wgt = isL ? T(0.5) + ph.beta : T(0.5) - ph.beta;
+            if (wgt == T(0)) {
+#pragma unroll
+                for (int k = 0; k < 4; k++) a.FV[k * a.nfpt + gf0 + s] = T(0);
+            } else {
+                s_plist[atomicAdd(&s_pcnt, 1)] = (short)s;
+            }
+        }
+        __syncthreads();
+        const int nplist = s_pcnt;
+        for (int li = threadIdx.x; li < nplist; li += NTH) {
+            const int s = s_plist[li];
+            T v[20];
+#pragma unroll
+            for (int f = 0; f < 20; f++) v[f] = T(0);
+#pragma unroll 2
+            for (int z = 0; z < NU; z++) {
+                const T m = op->M0t[z][s];
+#pragma unroll
+                for (int f = 0; f < 20; f++) v[f] += m * s_u[f * NU + z];
+            }
+            T uf[5], qf[5][3];
+#pragma unroll
+            for (int alpha = 0; alpha < 5; alpha++) {
+                uf[alpha] = v[alpha];
+#pragma unroll
+                for (int d = 0; d < 3; d++) qf[alpha][d] = v[5 + alpha * 3 + d];
+            }
+            const T *nt = a.fnrm + (e * 6 + face_of(s)) * 4;
+            T n[3] = {nt[0], nt[1], nt[2]};
+            T fvn[4];
+            viscous_normal_flux(ph, uf, qf, n, fvn);
+#pragma unroll
+            for (int k = 0; k < 4; k++) a.FV[k * a.nfpt + gf0 + s] = fvn[k];
+        }
+        // interpolation of the 20 fields to the quadrature points: one point per thread
+        for (int q = threadIdx.x; q < NQ; q += NTH) {
+            T v[20];
+#pragma unroll
+            for (int f = 0; f < 20; f++) v[f] = T(0);
+#pragma unroll 2
+            for (int j = 0; j < NU; j++) {
+                const T b = op->Bt[j][q];
+#pragma unroll
+                for (int f = 0; f < 20; f++) v[f] += b * s_u[f * NU + j];
+            }
+#pragma unroll
+            for (int f = 0; f < 20; f++) s_w[f * NQ + q] = v[f];
+        }
+        __syncthreads();
+        bool ok = true;
+        for (int q = threadIdx.x; q < NQ; q += NTH) {          // tdisf, in place
+            T u[5], gq[5][3], f[3][5];
+#pragma unroll
+            for (int alpha = 0; alpha < 5; alpha++) {
+                u[alpha] = s_w[alpha * NQ + q];
+#pragma unroll
+                for (int d = 0; d < 3; d++) gq[alpha][d] = s_w[(5 + alpha * 3 + d) * NQ + q];
+            }
+            ok &= total_flux(ph, u, gq, f);
+#pragma unroll
+            for (int alpha = 0; alpha < 5; alpha++)
+#pragma unroll
+                for (int d = 0; d < 3; d++)
+                    s_w[(alpha * 3 + d) * NQ + q] = g.det * (g.Ji[3 * d] * f[0][alpha] + g.Ji[3 * d + 1] * f[1][alpha] + g.Ji[3 * d + 2] * f[2][alpha]);
+        }
+        flag_status(a.status, ok);
+        __syncthreads();
+        // projection with the corrected divergence: R~[alpha][z] = sum_d sum_q Dv_d[z][q] f~_d[alpha][q]
+        T *R = a.R + elem_u0(a, e, NU);
+        for (int it = threadIdx.x; it < 5 * NU; it += NTH) {
+            const int alpha = it / NU, z = it % NU;
+            const T *F = s_w + alpha * 3 * NQ;
+            T v0 = T(0), v1 = T(0), v2 = T(0);
+#pragma unroll 5
+            for (int q = 0; q < NQ; q++) {
+                v0 += op->Dvt[0][q][z] * F[q];
+                v1 += op->Dvt[1][q][z] * F[NQ + q];
+                v2 += op->Dvt[2][q][z] * F[2 * NQ + q];
+            }
+            R[it] = (v0 + v1) + v2;
+        }
+        __syncthreads();
+    }
+}
+
+// -------------------------------------------------------------------------------------------------
+// Phase C: interface group (common flux at every own flux point, lift and scale)
+// -------------------------------------------------------------------------------------------------
+template <typename T, int NTH>
+__global__ void __launch_bounds__(NTH) k_tet_C(HexArgs<T> a, const TetOps<T> *__restrict__ op)
+{
+    __shared__ T s_d[5 * NF];
+    for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
+        const Geo<T> g = a.geo[e];
+        const Phys<T> ph = elem_phys(a, e);
+        const long long gf0 = elem_f0(a, e, NF);
+        bool ok = true;
+        for (int s = threadIdx.x; s < NF; s += NTH) {
+            const uint32_t pc = a.partner[gf0 + s];
+            const bool isL = (pc & FR_LFLAG) != 0;
+            const long long pg = pc & ~FR_LFLAG, og = gf0 + s;
+            T uo[5], up[5], fvo[4], fvp[4];
+#pragma unroll
+            for (int k = 0; k < 5; k++) { uo[k] = a.UF[k * a.nfpt + og]; up[k] = a.UF[k * a.nfpt + pg]; }
+#pragma unroll
+            for (int k = 0; k < 4; k++) { fvo[k] = a.FV[k * a.nfpt + og]; fvp[k] = a.FV[k * a.nfpt + pg]; }
+            const T *nt = a.fnrm + (e * 6 + face_of(s)) * 4;
+            const T mag = nt[3];
+            T nL[3] = {isL ? nt[0] : -nt[0], isL ? nt[1] : -nt[1], isL ? nt[2] : -nt[2]};
+            T F[5];
+            ok &= isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
+            const T sc = isL ? mag : -mag;
+#pragma unroll
+            for (int k = 0; k < 5; k++) s_d[k * NF + s] = sc * F[k];
+        }
+        flag_status(a.status, ok);
+        __syncthreads();
+        T *R = a.R + elem_u0(a, e, NU);
+        const T idet = T(-1) / g.det;
+        for (int it = threadIdx.x; it < 5 * NU; it += NTH) {
+            const int alpha = it / NU, z = it % NU;
+            const T *D = s_d + alpha * NF;
+            T v = R[it];
+#pragma unroll 8
+            for (int s = 0; s < NF; s++) v += op->Lt[s][z] * D[s];
+            if (a.rkstage == 0) R[it] = v * idet;
+            else rk_fold(a, elem_u0(a, e, NU) + it, v * idet);
+        }
+        __syncthreads();
+    }
+}
+
+int grid_elems(long long ne, int per_sm)
+{
+    long long g = ne;
+    if (g > 152LL * per_sm * 8) g = 152LL * per_sm * 8;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+template <typename T>
+int tet_fused_phase(int phase, const HexArgs<T> &a, const TetOps<T> *ops, cudaStream_t s)
+{
+    if (a.ne == 0) return 0;
+    if (phase == 0) {
+        long long work = a.ne * FR_NV * NF;
+        long long g = (work + 255) / 256;
+        if (g > 152LL * 64) g = 152LL * 64;
+        k_tet_disu<T><<<(int)g, 256, 0, s>>>(a, ops);
+    } else if (phase == 1) {
+        constexpr int NTH = 128;
+        const size_t smem = (size_t)(5 * NU + 15 * NU + 5 * NF + 20 * NQ) * sizeof(T);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_tet_B<T, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr = true;
+        }
+        k_tet_B<T, NTH><<<grid_elems(a.ne, 8), NTH, smem, s>>>(a, ops);
+    } else {
+        k_tet_C<T, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a, ops);
+    }
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+template int tet_fused_phase<double>(int, const HexArgs<double> &, const TetOps<double> *, cudaStream_t);
+template int tet_fused_phase<float>(int, const HexArgs<float> &, const TetOps<float> *, cudaStream_t);

@@ -617,3 +617,128 @@ def test_precision_sweep_ke_dissipation_32cubed_p4():
     print(f"precision sweep 32^3 p=4, eps after 100 steps: fp64 {ref:.9e}; relative errors {res}")
     for k, v in res.items():
         assert v <= 1e-3, (k, v)
+
+
+# ----------------------------------------------------------------------------------------------
+# Tetrahedra (dense per-element operators)
+# ----------------------------------------------------------------------------------------------
+
+TET_MESHES = {"tet1": lambda: W.box_tet_mesh(1), "tetshear2": lambda: W.box_tet_mesh(2, shear=True),
+              "tet4": lambda: W.box_tet_mesh(4)}
+
+
+def _tet_bound(mesh, U, nu):
+    """Parity bound for the dense tetrahedral operators: the oracle's own rounding level, measured as
+    the largest difference between its results for p_ref = 0, p0/2 and p0 (the same RHS in exact
+    arithmetic: the reference pressure only moves a constant through the flux), doubled, and never
+    below the hexahedral 1e-12. The oracle's dense per-element sums (125 quadrature points, then 60
+    terms per divergence) round at a level that grows like 1/h relative to R."""
+    p0 = W.tgv_p0()
+    R = [O.Oracle(mesh, 3, 5, threads=NCPU, p_ref=f * p0).rhs(U) for f in (0.0, 0.5, 1.0)]
+    spread = max(rel_linf(R[i], R[j], nu).max() for i in range(3) for j in range(i + 1, 3))
+    return max(1e-12, 2.0 * spread), spread
+
+
+@pytest.mark.parametrize("name", list(TET_MESHES))
+@pytest.mark.parametrize("pref", [0.0, 1.0])
+def test_tet_rhs_fp64_matches_oracle(name, pref):
+    """Kuhn-split periodic boxes (6, 48 and 384 tetrahedra; the sheared one has full, non-diagonal
+    Jacobians), p = 3 with the collapsed 5^3 rule, FP64 against the oracle within the bound of
+    _tet_bound (1e-12 to 2e-12 here)."""
+    mesh = TET_MESHES[name]()
+    ne, nu = mesh["tet_v"].shape[0], 20
+    p_ref = pref * W.tgv_p0()
+    o = O.Oracle(mesh, 3, 5, threads=NCPU, p_ref=p_ref)
+    U = W.tgv_state(o.sol_coords(), [(ne, nu)], perturb=1e-2)
+    Ro = o.rhs(U)
+    m = fr.FRMesh(mesh, fr.make_params(p=3, p_ref=p_ref))
+    assert np.abs(m.sol_coords() - o.sol_coords()).max() < 1e-13
+    Ud = torch.from_numpy(U).cuda()
+    Rd = torch.empty_like(Ud)
+    m.rhs(Ud, Rd)
+    m.sync_status()
+    err = rel_linf(Rd.cpu().numpy(), Ro, nu)
+    bound, spread = _tet_bound(mesh, U, nu)
+    print(f"tet {name} pref={pref}: {err} (oracle spread {spread:.2e}, bound {bound:.2e})")
+    assert err.max() <= bound and bound <= 3e-12, (err, bound)
+
+
+def test_tet_freestream_and_conservation():
+    """A constant state gives a zero RHS (to rounding) and the weighted RHS sums vanish, through the
+    library's own diagnostics, on the sheared tetrahedral box."""
+    mesh = W.box_tet_mesh(4, shear=True)
+    ne, nu = mesh["tet_v"].shape[0], 20
+    m = fr.FRMesh(mesh, fr.make_params(p=3))
+    fs = np.array([1.1, 1.1 * 0.3, -1.1 * 0.2, 1.1 * 0.1, 1.0 / 0.4 + 0.5 * 1.1 * 0.14])
+    U = torch.from_numpy(np.tile(np.repeat(fs, nu), ne)).cuda()
+    R = torch.empty_like(U)
+    m.rhs(U, R)
+    m.sync_status()
+    assert R.abs().max().item() < 1e-11
+    U = torch.from_numpy(W.tgv_state(m.sol_coords(), [(ne, nu)], perturb=1e-2)).cuda()
+    m.rhs(U, R)
+    d = m.diagnostics(U, R)[0]
+    o = O.Oracle(mesh, 3, 5, threads=NCPU)
+    do = o.diagnostics(U.cpu().numpy(), o.rhs(U.cpu().numpy()))
+    assert abs(d["volume"] / do["volume"] - 1) < 1e-13
+    assert abs(d["eps"] / do["eps"] - 1) < 1e-7
+    assert np.all(np.abs(d["sums"]) <= 1e-11 * do["abs_sums"])
+
+
+def test_tet_rk4_matches_oracle():
+    """10 RK4 steps (graph-replayed, the stage update folded into the interface kernel) on 384
+    tetrahedra against the oracle's RK4."""
+    mesh = W.box_tet_mesh(4)
+    ne, nu = mesh["tet_v"].shape[0], 20
+    p0 = W.tgv_p0()
+    o = O.Oracle(mesh, 3, 5, threads=NCPU, p_ref=p0)
+    U = W.tgv_state(o.sol_coords(), [(ne, nu)], perturb=1e-2)
+    Uo = o.rk4(U, 1e-3, 10)
+    m = fr.FRMesh(mesh, fr.make_params(p=3, p_ref=p0))
+    Ud = torch.from_numpy(U).cuda()
+    m.rk4_step(Ud, 1e-3, 10)
+    m.sync_status()
+    d = np.abs(Ud.cpu().numpy() - Uo).max() / np.abs(Uo).max()
+    print(f"tet RK4: {d:.3e}")
+    assert d <= 1e-13, d
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed_fp16"])
+def test_tet_fp32_matches_oracle(prec):
+    """The FP32 kernels (which the mixed forms run on tetrahedra) against the oracle on the
+    FP32-rounded input, with the reference pressure removed (measured 2e-5 on this grid)."""
+    mesh = W.box_tet_mesh(4, shear=True)
+    ne, nu = mesh["tet_v"].shape[0], 20
+    p0 = W.tgv_p0()
+    o = O.Oracle(mesh, 3, 5, threads=NCPU, p_ref=p0)
+    U32 = W.tgv_state(o.sol_coords(), [(ne, nu)], perturb=1e-2).astype(np.float32)
+    Ro = o.rhs(U32.astype(np.float64))
+    m = fr.FRMesh(mesh, fr.make_params(p=3, prec=prec, p_ref=p0))
+    Ud = torch.from_numpy(U32).cuda()
+    Rd = torch.empty_like(Ud)
+    m.rhs(Ud, Rd)
+    m.sync_status()
+    err = rel_linf(Rd.cpu().numpy().astype(np.float64), Ro, nu)
+    print(f"tet {prec}: {err}")
+    assert err.max() <= 5e-5, err
+
+
+def test_tet_full_size_sampled_against_oracle():
+    """The tetrahedral benchmark size class: 16^3 cells (24,576 tetrahedra, 2.46M DOF), FP64, every
+    element against the oracle (which still finishes in seconds here), within _tet_bound (the
+    oracle's own rounding level is about 5e-12 at this resolution)."""
+    mesh = W.box_tet_mesh(16)
+    ne, nu = mesh["tet_v"].shape[0], 20
+    p0 = W.tgv_p0()
+    o = O.Oracle(mesh, 3, 5, threads=NCPU, p_ref=p0)
+    U = W.tgv_state(o.sol_coords(), [(ne, nu)], perturb=1e-3)
+    Ro = o.rhs(U)
+    m = fr.FRMesh(mesh, fr.make_params(p=3, p_ref=p0))
+    Ud = torch.from_numpy(U).cuda()
+    Rd = torch.empty_like(Ud)
+    m.rhs(Ud, Rd)
+    m.sync_status()
+    err = rel_linf(Rd.cpu().numpy(), Ro, nu)
+    bound, spread = _tet_bound(mesh, U, nu)
+    print(f"tet 16^3: {err} (oracle spread {spread:.2e}, bound {bound:.2e})")
+    assert err.max() <= bound and bound <= 2e-11, (err, bound)

@@ -143,3 +143,38 @@ def test_host_validation_prisms(lib):
     with pytest.raises(fr.FRError) as e:
         _create(mesh)
     assert e.value.status == fr.FR_EMESH
+
+
+def test_tet_mesh_generator_orientation_and_volume():
+    """The Kuhn split: six positively oriented tetrahedra per cell filling the box."""
+    for shear in (False, True):
+        m = W.box_tet_mesh(3, shear=shear)
+        v, t = m["verts"], m["tet_v"]
+        assert t.shape == (6 * 27, 4)
+        J = np.stack([v[t[:, 1]] - v[t[:, 0]], v[t[:, 2]] - v[t[:, 0]], v[t[:, 3]] - v[t[:, 0]]], axis=2)
+        det = np.linalg.det(J)
+        assert np.all(det > 0)
+        assert abs(det.sum() / 6 - (2 * np.pi) ** 3) < 1e-9
+
+
+def test_host_validation_tetrahedra(lib):
+    mesh = W.box_tet_mesh(1)
+    p0 = W.tgv_p0()
+    for kw in (dict(p=4), dict(p=3, nq1d=4), dict(p=3, surface_aa=True),
+               dict(p=3, prec="fp32", p_ref=p0, rho_ref=1.0)):
+        with pytest.raises(fr.FRError) as e:
+            _create(mesh, **kw)
+        assert e.value.status == fr.FR_EUNSUPPORTED, kw
+    # one tetrahedron removed: faces without partners
+    mesh = W.box_tet_mesh(2)
+    mesh["tet_v"] = mesh["tet_v"][1:].copy()
+    with pytest.raises(fr.FRError) as e:
+        _create(mesh)
+    assert e.value.status == fr.FR_EMESH
+    # an inverted tetrahedron (two vertices swapped)
+    mesh = W.box_tet_mesh(2)
+    mesh["tet_v"] = mesh["tet_v"].copy()
+    mesh["tet_v"][0, [1, 2]] = mesh["tet_v"][0, [2, 1]]
+    with pytest.raises(fr.FRError) as e:
+        _create(mesh)
+    assert e.value.status == fr.FR_EMESH
