@@ -71,6 +71,21 @@ def phase_b_flops_per_element(p=P, m=MQ, one_sided=True, diagonal_metric=True, d
     return con_u + grad + jt + face + interp + tdisf + proj + div
 
 
+def tet_phase_b_flops_per_element():
+    """FLOPs of the tetrahedral volume kernel per element (p = 3: 20 solution points, 40 flux
+    points, 125 quadrature points; dense operators, full metric, one-sided viscous flux, the
+    divergence folded into the projection as one 20 x 375 operator per variable)."""
+    nu, nf, nq = 20, 40, 125
+    con_u = 5 * nf * 3
+    grad = 3 * nu * nu * 5 * 2 + nf * nu * 5 * 2 + 4 * 3 * 5 * nu * 2   # Dh u, face lifts, normals
+    jt = 5 * nu * 15
+    face = (nf // 2) * (20 * nu * 2 + VISC_NORMAL_FLOPS)
+    interp = 20 * nq * nu * 2
+    tdisf = nq * (POINT_FLUX_FLOPS + 90)
+    proj = 5 * nu * 3 * nq * 2
+    return con_u + grad + jt + face + interp + tdisf + proj
+
+
 # ---------------------------------------------------------------------------------------------
 # Clock sampling during the timed region
 # ---------------------------------------------------------------------------------------------
@@ -267,6 +282,21 @@ def other_configs(args, torch, fr, W):
         m.sync_status()
         out[f"tet24_{prec}"] = {"gdof_rhs_per_s": U0.size * RHS_PER_STEP / (ms * 1e-3) / 1e9, "ms_per_step": ms,
                                 "dof": int(U0.size), "elements": nt}
+        # the volume kernel alone (CUDA events around its launches in one RHS)
+        Uc = U if prec == "fp64" else U.float()
+        Rc = torch.empty_like(Uc)
+        m.set_timing(True)
+        m.rhs(Uc, Rc)
+        torch.cuda.synchronize()
+        m.set_timing(False)
+        kt = m.kernel_times()
+        b_ms = kt[1][0] / max(1, kt[1][1])
+        tfl = tet_phase_b_flops_per_element() * nt / (b_ms * 1e-3) / 1e12
+        out[f"tet24_{prec}"].update({"volume_kernel_ms": b_ms, "volume_tflops": tfl,
+                                     "flops_per_element": tet_phase_b_flops_per_element()})
+        if prec == "fp64":
+            out[f"tet24_{prec}"]["volume_frac_of_fp64_peak"] = tfl / FP64_PEAK_TFLOPS
+        del Uc, Rc
         if prec != "fp64":
             out[f"tet24_{prec}"]["speedup_vs_fp64"] = out["tet24_fp64"]["ms_per_step"] / ms
         m.close()
