@@ -3,8 +3,8 @@
  *
  * A plain, slow, FP64 reference ("the oracle") for one right-hand-side (RHS) evaluation of the
  * flux-reconstruction (FR) discretisation of the compressible Navier-Stokes equations with flux
- * anti-aliasing (over-integration of the flux at element quadrature points), on affine hexahedra,
- * prisms and tetrahedra, plus the classical RK4 step around it.
+ * anti-aliasing (over-integration of the flux at element quadrature points), on affine or trilinear
+ * hexahedra, affine prisms and affine tetrahedra, plus the classical RK4 step around it.
  *
  * Only the test-suite, the package smoke check and the CPU-baseline leg of the benchmark may load
  * the library built from this file. It shares no code with the GPU library.
@@ -41,6 +41,10 @@
  *       4/5 towards the centroid; each triangular face carries the printed Williams-Shunn triangle
  *       points (so p = 2, 3). With the DG-equivalent lift and the L2 projection of the flux, the RHS
  *       as a polynomial does not depend on the solution points, only its rounding does.
+ *   C1  curved (non-affine) hexahedra (the metric terms x^(c) of the paper's byte tables vary per
+ *       point): the trilinear map of the 8 vertices; J^-T at each solution point for the gradient,
+ *       det J J^-1 at each quadrature point for the flux, n_s = det J J^-T n~ at each flux point,
+ *       R = -R~ / det J at each solution point. Prisms and tetrahedra stay affine.
  *   T2  tetrahedron quadrature: collapsed m x m x m rule (GL in a, Gauss rules of the weights
  *       (1-b) and (1-c)^2 in b and c), exact to total degree 2m-1 -- with m = p + 2 the same
  *       degree 2p+3 that m GL points give per direction on the hexahedron.
@@ -823,6 +827,8 @@ typedef struct {
     double *J;      /* [ne][9] row-major dx_i/dxi_j */
     double *Jinv;   /* [ne][9] dxi_i/dx_j */
     double *detJ;   /* [ne] */
+    int *curved;    /* [ne] 1: a non-affine (trilinear) hexahedron, metric terms vary per point */
+    double *vx;     /* [ne][8][3] hexahedron vertices (tensor order), for the trilinear map */
     long *uoff, *foff; /* per element offset into [elem][var][pt] solution and flux-point arrays */
     long nU, nF;       /* total solution and flux-point values (times NV) */
     long nfpt;         /* total flux points */
@@ -850,8 +856,45 @@ static double pdist(const oracle_t *o, const double *a, const double *b)
     return sqrt(s);
 }
 
+/* Trilinear map of hexahedron e (corners c = a + 2b + 4c, reference corner (+-1, +-1, +-1)):
+ * x(X) = sum_c N_c(X) v_c with N_c = prod_d (1 + s_cd X_d)/2; its Jacobian dx_i/dX_j. */
+static void trilinear(const oracle_t *o, int e, const double *X, double *x, double *J)
+{
+    const double *v = o->vx + 24 * (size_t)e;
+    if (x) x[0] = x[1] = x[2] = 0.0;
+    if (J) for (int k = 0; k < 9; k++) J[k] = 0.0;
+    for (int c = 0; c < 8; c++) {
+        double sg[3] = {(c & 1) ? 1.0 : -1.0, (c & 2) ? 1.0 : -1.0, (c & 4) ? 1.0 : -1.0};
+        double f[3];
+        for (int d = 0; d < 3; d++) f[d] = 0.5 * (1.0 + sg[d] * X[d]);
+        double N = f[0] * f[1] * f[2];
+        double dN[3] = {0.5 * sg[0] * f[1] * f[2], 0.5 * sg[1] * f[0] * f[2], 0.5 * sg[2] * f[0] * f[1]};
+        for (int i = 0; i < 3; i++) {
+            if (x) x[i] += N * v[3 * c + i];
+            if (J) for (int j = 0; j < 3; j++) J[3 * i + j] += dN[j] * v[3 * c + i];
+        }
+    }
+}
+
+static void inv3(const double *a, double *b, double *det);
+
+/* Inverse Jacobian (row-major dX_i/dx_j) and det J of element e at reference point X: the element
+ * constants for affine elements, the trilinear map's values at X for curved hexahedra. */
+static void point_geom(const oracle_t *o, int e, const double *X, double *Jinv, double *det)
+{
+    if (o->curved[e]) {
+        double J[9];
+        trilinear(o, e, X, NULL, J);
+        inv3(J, Jinv, det);
+        return;
+    }
+    memcpy(Jinv, o->Jinv + 9 * e, 9 * sizeof(double));
+    *det = o->detJ[e];
+}
+
 static void phys_coord(const oracle_t *o, int e, const double *X, double *x)
 {
+    if (o->curved[e]) { trilinear(o, e, X, x, NULL); return; }
     for (int i = 0; i < 3; i++) {
         x[i] = o->x0[3 * e + i];
         for (int j = 0; j < 3; j++) x[i] += o->J[9 * e + 3 * i + j] * (X[j] + 1.0);
@@ -938,6 +981,8 @@ void *or_create3(int p, int m, int tri_k, int surf, double gamma, double Pr, dou
     o->J = (double *)malloc(9 * ne * sizeof(double));
     o->Jinv = (double *)malloc(9 * ne * sizeof(double));
     o->detJ = (double *)malloc(ne * sizeof(double));
+    o->curved = (int *)calloc(ne, sizeof(int));
+    o->vx = (double *)calloc((size_t)24 * ne, sizeof(double));
     o->uoff = (long *)malloc(ne * sizeof(long));
     o->foff = (long *)malloc(ne * sizeof(long));
     o->fpt_base = (long *)malloc(ne * sizeof(long));
@@ -964,7 +1009,11 @@ void *or_create3(int p, int m, int tri_k, int surf, double gamma, double Pr, dou
             o->J[9 * e + 3 * i + 2] = 0.5 * (v[c3][i] - v[0][i]);
             scale += fabs(v[c1][i] - v[0][i]) + fabs(v[c2][i] - v[0][i]) + fabs(v[c3][i] - v[0][i]);
         }
-        /* affinity: every vertex equals the affine image of its reference corner */
+        if (typ == ET_HEX)
+            for (int k = 0; k < 8; k++)
+                for (int i = 0; i < 3; i++) o->vx[24 * (size_t)e + 3 * k + i] = v[k][i];
+        /* affinity: every vertex equals the affine image of its reference corner; a hexahedron that
+         * is not affine is kept as a trilinear (curved) element, other types are rejected */
         for (int k = 0; k < nv; k++) {
             double X[3];
             if (e < n_hex) { X[0] = (k & 1) ? 1 : -1; X[1] = (k & 2) ? 1 : -1; X[2] = (k & 4) ? 1 : -1; }
@@ -974,11 +1023,25 @@ void *or_create3(int p, int m, int tri_k, int surf, double gamma, double Pr, dou
             }
             double x[3];
             phys_coord(o, e, X, x);
-            for (int i = 0; i < 3; i++)
-                if (fabs(x[i] - v[k][i]) > 1e-10 * scale) { *err = OR_EUNSUPPORTED; or_destroy(o); return NULL; }
+            int off = 0;
+            for (int i = 0; i < 3; i++) off |= fabs(x[i] - v[k][i]) > 1e-10 * scale;
+            if (off && typ != ET_HEX) { *err = OR_EUNSUPPORTED; or_destroy(o); return NULL; }
+            if (off) o->curved[e] = 1;
         }
         inv3(o->J + 9 * e, o->Jinv + 9 * e, &o->detJ[e]);
         if (!(o->detJ[e] > 0)) { *err = OR_EMESH; or_destroy(o); return NULL; }
+        if (o->curved[e]) {
+            /* the trilinear map must be invertible at every point the method uses */
+            const etype_t *et = ET(o, e);
+            const double *sets[3] = {et->xu, et->xq, et->xf};
+            const int counts[3] = {et->nu, et->nq, et->nf};
+            for (int t = 0; t < 3; t++)
+                for (int z = 0; z < counts[t]; z++) {
+                    double Ji[9], dj;
+                    point_geom(o, e, sets[t] + 3 * z, Ji, &dj);
+                    if (!(dj > 0)) { *err = OR_EMESH; or_destroy(o); return NULL; }
+                }
+        }
     }
     o->nU = uo; o->nF = fo; o->nfpt = fb;
     o->fpt_elem = (int *)malloc(fb * sizeof(int));
@@ -1117,6 +1180,7 @@ void or_destroy(void *h)
     if (!o) return;
     for (int t = 0; t < ET_COUNT; t++) if (o->has[t]) etype_free(&o->et[t]);
     free(o->x0); free(o->J); free(o->Jinv); free(o->detJ); free(o->uoff); free(o->foff);
+    free(o->curved); free(o->vx);
     free(o->fpt_base); free(o->fpt_elem); free(o->pairL); free(o->pairR);
     free(o->UF); free(o->CF); free(o->DF); free(o->QF); free(o->Q); free(o->Rt);
     free(o);
@@ -1211,13 +1275,16 @@ static void flux_viscous(const phys_params *ph, const double *u, const double q[
     }
 }
 
-/* Physical outward normal scaling of flux point s of element e: n_s = detJ J^-T n~. */
-static void normal_scaled(const oracle_t *o, int e, const double *nref, double *ns)
+/* Physical outward normal scaling at flux point X of element e: n_s = detJ J^-T n~ (the metric at
+ * the flux point itself on curved elements). */
+static void normal_scaled(const oracle_t *o, int e, const double *X, const double *nref, double *ns)
 {
+    double Ji[9], dj;
+    point_geom(o, e, X, Ji, &dj);
     for (int k = 0; k < 3; k++) {
         ns[k] = 0;
-        for (int d = 0; d < 3; d++) ns[k] += o->Jinv[9 * e + 3 * d + k] * nref[d];
-        ns[k] *= o->detJ[e];
+        for (int d = 0; d < 3; d++) ns[k] += Ji[3 * d + k] * nref[d];
+        ns[k] *= dj;
     }
 }
 
@@ -1289,12 +1356,15 @@ static int rhs_impl(oracle_t *o, const double *U, double *R, or_stages *st)
                     for (int s = 0; s < nf; s++) v += et->M3[z * nf + s] * et->nref[3 * s + d] * cf[a * nf + s];
                     qt[d * nu + z] += v;
                 }
-            for (int z = 0; z < nu; z++)
+            for (int z = 0; z < nu; z++) {
+                double Ji[9], dj;
+                point_geom(o, e, et->xu + 3 * z, Ji, &dj);
                 for (int k = 0; k < 3; k++) {
                     double v = 0;
-                    for (int d = 0; d < 3; d++) v += o->Jinv[9 * e + 3 * d + k] * qt[d * nu + z];
+                    for (int d = 0; d < 3; d++) v += Ji[3 * d + k] * qt[d * nu + z];
                     q[(a * 3 + k) * nu + z] = v;
                 }
+            }
         }
         free(qt);
     }
@@ -1348,11 +1418,13 @@ static int rhs_impl(oracle_t *o, const double *U, double *R, or_stages *st)
             }
             flux_inviscid(ph, us, fe, NULL);
             flux_viscous(ph, us, qs, fv);
+            double Ji[9], dj;
+            point_geom(o, e, et->xq + 3 * s, Ji, &dj);
             for (int a = 0; a < NV; a++)
                 for (int d = 0; d < 3; d++) {
                     double v = 0;
-                    for (int k = 0; k < 3; k++) v += o->Jinv[9 * e + 3 * d + k] * (fe[k][a] - fv[k][a]);
-                    fq[(a * 3 + d) * nq + s] = o->detJ[e] * v;
+                    for (int k = 0; k < 3; k++) v += Ji[3 * d + k] * (fe[k][a] - fv[k][a]);
+                    fq[(a * 3 + d) * nq + s] = dj * v;
                 }
         }
         /* 10. tdivtpcorf: R~ = (M1 - M3 M2) M9 F~(q), with M9 = I3 (x) M8 */
@@ -1393,8 +1465,8 @@ static int rhs_impl(oracle_t *o, const double *U, double *R, or_stages *st)
             }
         }
         double nsL[3], nsR[3];
-        normal_scaled(o, eL, tL->nref + 3 * sL, nsL);
-        normal_scaled(o, eR, tR->nref + 3 * sR, nsR);
+        normal_scaled(o, eL, tL->xf + 3 * sL, tL->nref + 3 * sL, nsL);
+        normal_scaled(o, eR, tR->xf + 3 * sR, tR->nref + 3 * sR, nsR);
         double magL = sqrt(nsL[0] * nsL[0] + nsL[1] * nsL[1] + nsL[2] * nsL[2]);
         double magR = sqrt(nsR[0] * nsR[0] + nsR[1] * nsR[1] + nsR[2] * nsR[2]);
         double n[3] = {nsL[0] / magL, nsL[1] / magL, nsL[2] / magL};
@@ -1435,7 +1507,9 @@ static int rhs_impl(oracle_t *o, const double *U, double *R, or_stages *st)
                 double v = 0;
                 for (int s = 0; s < nf; s++) v += et->M3[z * nf + s] * df[a * nf + s];
                 rt[a * nu + z] += v;
-                r[a * nu + z] = -rt[a * nu + z] / o->detJ[e];
+                double Ji[9], dj;
+                point_geom(o, e, et->xu + 3 * z, Ji, &dj);
+                r[a * nu + z] = -rt[a * nu + z] / dj;
             }
     }
 
@@ -1493,7 +1567,9 @@ void or_diagnostics(void *h, const double *U, const double *R, double *out)
         const double *u = U + o->uoff[e];
         const double *r = R ? R + o->uoff[e] : NULL;
         for (int z = 0; z < et->nu; z++) {
-            double w = et->Wu[z] * o->detJ[e];
+            double Ji[9], dj;
+            point_geom(o, e, et->xu + 3 * z, Ji, &dj);
+            double w = et->Wu[z] * dj;
             double rho = u[z], v[3] = {u[et->nu + z] / rho, u[2 * et->nu + z] / rho, u[3 * et->nu + z] / rho};
             double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
             out[0] += w;

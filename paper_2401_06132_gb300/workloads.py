@@ -204,3 +204,23 @@ def box_tet_mesh(N: int, length: float = 2 * math.pi, origin: float = -math.pi, 
     tets = np.stack([corner[:, list(t)] for t in _kuhn_tets()], axis=1).reshape(-1, 4)
     return dict(verts=verts, hex_v=np.zeros((0, 8), np.int32), pri_v=np.zeros((0, 6), np.int32),
                 tet_v=tets.astype(np.int32), period=(length, length, length))
+
+
+def curved_box_mesh(N: int, amp: float = 0.1, length: float = 2 * math.pi, origin: float = -math.pi):
+    """N^3 periodic box of non-affine (trilinear) hexahedra: the uniform vertex grid (X, Y, Z) moved
+    by amp * h * (sin(2 pi Y/L) sin(2 pi Z/L), sin(2 pi Z/L) sin(2 pi X/L), sin(2 pi X/L) sin(2 pi Y/L)),
+    a displacement that is periodic on the grid, so faces still match across the periods. Every
+    element is a general hexahedron with straight edges whose metric terms vary inside it."""
+    h = length / N
+    g = origin + length * np.arange(N + 1) / N
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    X, Y, Z = X.ravel(order="F"), Y.ravel(order="F"), Z.ravel(order="F")
+    w = 2 * math.pi / length
+    sx, sy, sz = np.sin(w * (X - origin)), np.sin(w * (Y - origin)), np.sin(w * (Z - origin))
+    verts = np.stack([X + amp * h * sy * sz, Y + amp * h * sz * sx, Z + amp * h * sx * sy], axis=1)
+    vid = lambda i, j, k: i + (N + 1) * (j + (N + 1) * k)  # noqa: E731
+    e = np.arange(N ** 3)
+    ex, ey, ez = e % N, (e // N) % N, e // (N * N)
+    hex_v = np.stack([vid(ex + (c & 1), ey + ((c >> 1) & 1), ez + ((c >> 2) & 1)) for c in range(8)], axis=1)
+    return dict(verts=verts, hex_v=hex_v.astype(np.int32), pri_v=np.zeros((0, 6), np.int32),
+                period=(length, length, length))

@@ -432,6 +432,7 @@ MESHES = {
     "sheared3": lambda: W.sheared_box_mesh(3),
     "mixed2": lambda: W.mixed_box_mesh(2),
     "mixed4": lambda: W.mixed_box_mesh(4),
+    "curved3": lambda: W.curved_box_mesh(3, amp=0.15),
     "tet2": lambda: W.box_tet_mesh(2),
     "tetshear2": lambda: W.box_tet_mesh(2, shear=True),
 }
@@ -441,7 +442,8 @@ MESHES = {
 @pytest.mark.parametrize("p", [3, 4])
 def test_freestream_preservation(name, p):
     """Check (a): a constant state gives a zero RHS to 1e-13 on affine meshes, including
-    self-periodic, sheared and mixed hex/prism meshes. Rounding in the divergence grows with the
+    self-periodic, sheared and mixed hex/prism meshes, and on trilinear (curved) hexahedra, whose
+    metric terms lie in the solution space for p >= 2 so that the discrete metric identities hold. Rounding in the divergence grows with the
     operator norm, so the bound is relative to the RHS scale max|f| (2/h) (p+1)^2."""
     mesh = MESHES[name]()
     if (mesh["pri_v"].shape[0] or mesh.get("tet_v", np.zeros((0, 4))).shape[0]) and p != 3:
@@ -460,7 +462,7 @@ def _tgv(o, mesh, perturb=0.0, mach=0.1):
     return W.tgv_state(o.sol_coords(), _layout(o, mesh), mach=mach, perturb=perturb)
 
 
-@pytest.mark.parametrize("name", ["hex1_self_periodic", "hex3", "sheared3", "mixed4", "tetshear2"])
+@pytest.mark.parametrize("name", ["hex1_self_periodic", "hex3", "sheared3", "mixed4", "tetshear2", "curved3"])
 def test_discrete_conservation(name):
     """Check (e): the quadrature-weighted RHS sums to zero to 1e-12 relative, per variable."""
     mesh = MESHES[name]()
@@ -486,7 +488,8 @@ def test_ke_dissipation_rate_converges_to_closed_form():
 
 
 @pytest.mark.parametrize("meshfn,m,surf", [(W.box_hex_mesh, 5, False), (W.sheared_box_mesh, 5, False),
-                                           (W.box_hex_mesh, 4, False), (W.sheared_box_mesh, 5, True)])
+                                           (W.box_hex_mesh, 4, False), (W.sheared_box_mesh, 5, True),
+                                           (W.curved_box_mesh, 5, False)])
 def test_rhs_converges_to_analytic_navier_stokes(meshfn, m, surf):
     """Consistency on a compressible periodic field (div v != 0, non-uniform rho, M = 0.3): the
     inviscid RHS (mu = 0) converges to the exact -div f^e at order >= p - 0.5, and the viscous part
@@ -494,7 +497,8 @@ def test_rhs_converges_to_analytic_navier_stokes(meshfn, m, surf):
     converges to the exact -div(-f^v) at order >= p - 1.5 (second-derivative terms under LDG).
     On the sheared mesh this also pins the metric terms (a transposed J^-1 fails). m = 4 is the
     collocation form (no anti-aliasing), which converges at the same orders on this smooth field;
-    surf = True adds surface-flux anti-aliasing (full anti-aliasing)."""
+    surf = True adds surface-flux anti-aliasing (full anti-aliasing). The curved mesh (trilinear
+    hexahedra) pins the per-point metric terms: an element-constant metric fails it."""
     from tests.analytic_ns import rhs_function, state_function
     mach, mu = 0.3, 0.1
     state = state_function("wave", 1.4, mach)
