@@ -45,6 +45,8 @@ struct InstanceHost {
     fr_params prm;
     int n_hex, n_pri, n_tet;
     std::vector<double> x0J;   // per element: x0[3], J[9] (row-major dx_i/dxi_j); x = x0 + J (xi + 1)
+    std::vector<char> curved;  // per element: 1 = non-affine (trilinear) hexahedron
+    std::vector<double> vx;    // per element: the 8 hexahedron vertices (tensor order), [24]
 };
 
 // Blocks of one element type and order, launched together (one launch per phase).
@@ -126,6 +128,9 @@ struct fr_mesh {
     uint32_t *d_qpartner = nullptr, *d_qlpts = nullptr;
     long long nqlpts = 0;
     void *d_UFQ = nullptr, *d_FVQ = nullptr, *d_DQ = nullptr;
+    // curved (trilinear) hexahedra: metric terms per point (unfused form)
+    bool curved = false;
+    void *d_mu = nullptr, *d_mq = nullptr, *d_mfn = nullptr;
 };
 
 // Kernel ids for timing: 0..2 fused phases A, B, C; 10+k unfused kernel k (1..13); 30 RK4 update.
@@ -276,6 +281,26 @@ static void affine_point(const double *x0J, const double *X, double *x)
     }
 }
 
+// Trilinear map of a hexahedron with vertices v[8][3] (tensor order, corner c at reference
+// (+-1, +-1, +-1)): x(X) = sum_c N_c(X) v_c, N_c = prod_d (1 + s_cd X_d)/2, and J = dx/dX (row-major).
+static void trilinear_map(const double *v, const double *X, double *x, double *J)
+{
+    if (x) x[0] = x[1] = x[2] = 0.0;
+    if (J) for (int k = 0; k < 9; k++) J[k] = 0.0;
+    for (int c = 0; c < 8; c++) {
+        const double s0 = (c & 1) ? 1.0 : -1.0, s1 = (c & 2) ? 1.0 : -1.0, s2 = (c & 4) ? 1.0 : -1.0;
+        const double f0 = 0.5 * (1.0 + s0 * X[0]), f1 = 0.5 * (1.0 + s1 * X[1]), f2 = 0.5 * (1.0 + s2 * X[2]);
+        const double g[3] = {0.5 * s0 * f1 * f2, 0.5 * s1 * f0 * f2, 0.5 * s2 * f0 * f1};
+        for (int i = 0; i < 3; i++) {
+            if (x) x[i] += f0 * f1 * f2 * v[3 * c + i];
+            if (J) for (int j = 0; j < 3; j++) J[3 * i + j] += g[j] * v[3 * c + i];
+        }
+    }
+}
+
+// Physical point of reference point X in element li of instance I (affine or trilinear map).
+static void map_point(const struct InstanceHost &I, long long li, const double *X, double *x);
+
 static double inv3(const double *a, double *b)
 {
     double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
@@ -285,6 +310,12 @@ static double inv3(const double *a, double *b)
     b[3] = c01 * id; b[4] = (a[0] * a[8] - a[2] * a[6]) * id; b[5] = (a[2] * a[3] - a[0] * a[5]) * id;
     b[6] = c02 * id; b[7] = (a[1] * a[6] - a[0] * a[7]) * id; b[8] = (a[0] * a[4] - a[1] * a[3]) * id;
     return det;
+}
+
+static void map_point(const InstanceHost &I, long long li, const double *X, double *x)
+{
+    if (!I.curved.empty() && I.curved[(size_t)li]) trilinear_map(&I.vx[(size_t)li * 24], X, x, nullptr);
+    else affine_point(&I.x0J[(size_t)li * 12], X, x);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -332,13 +363,14 @@ static fr_status match_instance(fr_mesh *m, int ii, int b0, int b1, const fr_mes
         const Block &B = m->blocks[b];
         ref_faces(m, b, rf[b - b0]);
         for (long long le = 0; le < B.ne; le++) {
-            const double *x0J = &I.x0J[(size_t)(B.elem0 - m->blocks[b0].elem0 + le) * 12];
+            const long long li = B.elem0 - m->blocks[b0].elem0 + le;
+            const double *x0J = &I.x0J[(size_t)li * 12];
             double hh = std::cbrt(std::fabs(x0J[3] * (x0J[7] * x0J[11] - x0J[8] * x0J[10]) - x0J[4] * (x0J[6] * x0J[11] - x0J[8] * x0J[9]) + x0J[5] * (x0J[6] * x0J[10] - x0J[7] * x0J[9])));
             hmin = std::min(hmin, hh);
             for (int f = 0; f < rf[b - b0].nfaces; f++) {
                 FaceRef fr;
                 fr.elem = B.elem0 + le; fr.blk = b; fr.le = le; fr.face = f;
-                affine_point(x0J, rf[b - b0].centre[f], fr.c);
+                map_point(I, li, rf[b - b0].centre[f], fr.c);
                 faces.push_back(fr);
             }
         }
@@ -396,12 +428,11 @@ static fr_status match_instance(fr_mesh *m, int ii, int b0, int b1, const fr_mes
         const RefFaces &RA = rf[A.blk - b0], &RB = rf[Bf.blk - b0];
         int n2 = RA.count[A.face];
         if (RB.count[Bf.face] != n2) return fail(FR_EMESH, "element %lld face %d meets a face with a different point count", A.elem, A.face);
-        const double *JA = &I.x0J[(size_t)(A.elem - m->blocks[b0].elem0) * 12];
-        const double *JB = &I.x0J[(size_t)(Bf.elem - m->blocks[b0].elem0) * 12];
+        const long long liA = A.elem - m->blocks[b0].elem0, liB = Bf.elem - m->blocks[b0].elem0;
         xa.resize(n2 * 3); xb.resize(n2 * 3);
         for (int t = 0; t < n2; t++) {
-            affine_point(JA, &RA.xf[((size_t)RA.off[A.face] + t) * 3], &xa[t * 3]);
-            affine_point(JB, &RB.xf[((size_t)RB.off[Bf.face] + t) * 3], &xb[t * 3]);
+            map_point(I, liA, &RA.xf[((size_t)RA.off[A.face] + t) * 3], &xa[t * 3]);
+            map_point(I, liB, &RB.xf[((size_t)RB.off[Bf.face] + t) * 3], &xb[t * 3]);
         }
         auto key = std::make_tuple(BA.type, A.face, BB.type, Bf.face);
         std::vector<int> &perm = perm_cache[key];
@@ -431,8 +462,8 @@ static fr_status match_instance(fr_mesh *m, int ii, int b0, int b1, const fr_mes
             if ((int)refq.size() != 6 * q2 * 3) hex_ref_qpts(mq, refq);
             std::vector<double> qa(q2 * 3), qb(q2 * 3);
             for (int t = 0; t < q2; t++) {
-                affine_point(JA, &refq[((size_t)A.face * q2 + t) * 3], &qa[t * 3]);
-                affine_point(JB, &refq[((size_t)Bf.face * q2 + t) * 3], &qb[t * 3]);
+                map_point(I, liA, &refq[((size_t)A.face * q2 + t) * 3], &qa[t * 3]);
+                map_point(I, liB, &refq[((size_t)Bf.face * q2 + t) * 3], &qb[t * 3]);
             }
             auto qkey = std::make_tuple(-1, A.face, -1, Bf.face);
             std::vector<int> &qperm = perm_cache[qkey];
@@ -461,7 +492,12 @@ static fr_status match_instance(fr_mesh *m, int ii, int b0, int b1, const fr_mes
 // Mesh creation
 // ---------------------------------------------------------------------------------------------
 // Affine map of one element from its vertices; rejects non-affine and inverted elements.
-static fr_status element_map(int ii, long long e, int type, const fr_mesh_desc *d, double *x0J, std::vector<double> &geo)
+// Affine map of one element from its vertices (x0J); a hexahedron that is not affine is kept as a
+// trilinear (curved) element of instance I (local index li): its vertices are stored, and the
+// element geometry recorded is the map's at the element centre. Other non-affine elements give
+// FR_EUNSUPPORTED; inverted ones FR_EMESH.
+static fr_status element_map(int ii, long long e, int type, const fr_mesh_desc *d, double *x0J, std::vector<double> &geo,
+                             InstanceHost &I, long long li)
 {
     const int nv = type == 0 ? 8 : (type == 1 ? 6 : 4);
     const int *conn = type == 0 ? d->hex_v + 8 * e : (type == 1 ? d->pri_v + 6 * e : d->tet_v + 4 * e);
@@ -487,11 +523,25 @@ static fr_status element_map(int ii, long long e, int type, const fr_mesh_desc *
         else { X[0] = pc[k][0]; X[1] = pc[k][1]; X[2] = pc[k][2]; }
         affine_point(x0J, X, x);
         for (int i = 0; i < 3; i++)
-            if (std::fabs(x[i] - v[k][i]) > 1e-10 * scale)
-                return fail(FR_EUNSUPPORTED, "instance %d element %lld is not affine", ii, e);
+            if (std::fabs(x[i] - v[k][i]) > 1e-10 * scale) {
+                if (type != 0) return fail(FR_EUNSUPPORTED, "instance %d element %lld is not affine", ii, e);
+                I.curved[(size_t)li] = 1;
+            }
     }
     double Ji[9];
-    double det = inv3(x0J + 3, Ji);
+    double det;
+    if (type == 0) {
+        for (int k = 0; k < 8; k++)
+            for (int i = 0; i < 3; i++) I.vx[(size_t)li * 24 + 3 * k + i] = v[k][i];
+    }
+    if (type == 0 && I.curved[(size_t)li]) {
+        double J[9];
+        const double X0[3] = {0.0, 0.0, 0.0};
+        trilinear_map(&I.vx[(size_t)li * 24], X0, nullptr, J);
+        det = inv3(J, Ji);
+    } else {
+        det = inv3(x0J + 3, Ji);
+    }
     if (!(det > 0)) return fail(FR_EMESH, "instance %d element %lld is inverted or degenerate", ii, e);
     for (int k = 0; k < 9; k++) geo.push_back(Ji[k]);
     geo.push_back(det);
@@ -545,6 +595,8 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
         I.prm = P; I.prm.nq1d = m1;
         I.n_hex = d->n_hex; I.n_pri = d->n_pri; I.n_tet = d->n_tet;
         I.x0J.resize((size_t)(d->n_hex + d->n_pri + d->n_tet) * 12);
+        I.curved.assign((size_t)(d->n_hex + d->n_pri + d->n_tet), 0);
+        I.vx.assign((size_t)(d->n_hex + d->n_pri + d->n_tet) * 24, 0.0);
         m->inst_u0.push_back(u);
         bfirst.push_back((int)m->blocks.size());
         for (int type = 0; type < 3; type++) {
@@ -576,7 +628,7 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
             B.ne = ne; B.elem0 = elem; B.u0 = u; B.f0 = f;
             long long le0 = type == 0 ? 0 : (type == 1 ? d->n_hex : d->n_hex + d->n_pri);
             for (long long e = 0; e < ne; e++) {
-                fr_status st = element_map(ii, e, type, d, &I.x0J[(size_t)(le0 + e) * 12], m->geo_host);
+                fr_status st = element_map(ii, e, type, d, &I.x0J[(size_t)(le0 + e) * 12], m->geo_host, I, le0 + e);
                 if (st) return st;
             }
             m->blocks.push_back(B);
@@ -586,6 +638,11 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
         m->inst.push_back(I);
     }
     m->ne = elem; m->nU = u; m->nfpt = f;
+    for (const InstanceHost &I : m->inst)
+        for (char c : I.curved) m->curved = m->curved || c;
+    if (m->curved && (n_inst != 1 || m->blocks.size() != 1 || m->surf || m->blocks[0].m != m->blocks[0].p + 2))
+        return fail(FR_EUNSUPPORTED, "curved (non-affine) hexahedra run single-instance hexahedral meshes with flux "
+                                     "anti-aliasing (m = p + 2), in the unfused form");
     m->inst_u0.push_back(u);
     bfirst.push_back((int)m->blocks.size());
     if (f >= (long long)FR_LFLAG) return fail(FR_EUNSUPPORTED, "more than 2^31 flux points");
@@ -664,6 +721,61 @@ static fr_status upload_tetops(fr_mesh *m)
     fr_status st = dalloc(m, &m->d_tetops, sizeof(TetOps<T>));
     if (st) return st;
     CU(cudaMemcpy(m->d_tetops, o.data(), sizeof(TetOps<T>), cudaMemcpyHostToDevice));
+    return FR_OK;
+}
+
+// Metric terms at every point of a curved (trilinear) hexahedral mesh (single block): J^-1 and
+// det J at the solution points, det J J^-1 at the quadrature points, the unit normal and |n_s| of
+// n_s = det J J^-T n~ at the flux points. Rejects a map that is not invertible at one of them.
+template <typename T>
+static fr_status upload_curved(fr_mesh *m)
+{
+    if (!m->curved) return FR_OK;
+    const Block &B = m->blocks[0];
+    const InstanceHost &I = m->inst[0];
+    const frb::Hex1D &h = m->hex1d[0];
+    const int n = h.n, mq = h.m, nu = B.nu, nf = B.nf, nq = mq * mq * mq;
+    std::vector<double> xf;
+    hex_ref_fpts(h, xf);
+    std::vector<T> tu((size_t)B.ne * nu * 10), tq((size_t)B.ne * nq * 9), tf((size_t)B.ne * nf * 4);
+    for (long long e = 0; e < B.ne; e++) {
+        const double *v = &I.vx[(size_t)e * 24];
+        double J[9], Ji[9], det;
+        for (int z = 0; z < nu; z++) {
+            const double X[3] = {h.x[z % n], h.x[(z / n) % n], h.x[z / (n * n)]};
+            trilinear_map(v, X, nullptr, J);
+            det = inv3(J, Ji);
+            if (!(det > 0)) return fail(FR_EMESH, "curved element %lld is not invertible at a solution point", e);
+            for (int k = 0; k < 9; k++) tu[((size_t)e * nu + z) * 10 + k] = (T)Ji[k];
+            tu[((size_t)e * nu + z) * 10 + 9] = (T)det;
+        }
+        for (int q = 0; q < nq; q++) {
+            const double X[3] = {h.xq[q % mq], h.xq[(q / mq) % mq], h.xq[q / (mq * mq)]};
+            trilinear_map(v, X, nullptr, J);
+            det = inv3(J, Ji);
+            if (!(det > 0)) return fail(FR_EMESH, "curved element %lld is not invertible at a quadrature point", e);
+            for (int k = 0; k < 9; k++) tq[((size_t)e * nq + q) * 9 + k] = (T)(det * Ji[k]);
+        }
+        for (int s2 = 0; s2 < nf; s2++) {
+            const int f = s2 / (n * n);
+            trilinear_map(v, &xf[(size_t)s2 * 3], nullptr, J);
+            det = inv3(J, Ji);
+            if (!(det > 0)) return fail(FR_EMESH, "curved element %lld is not invertible at a flux point", e);
+            double nr[3] = {0, 0, 0}, ns[3];
+            nr[f / 2] = (f & 1) ? 1.0 : -1.0;
+            for (int k = 0; k < 3; k++) ns[k] = det * (Ji[k] * nr[0] + Ji[3 + k] * nr[1] + Ji[6 + k] * nr[2]);
+            const double mag = std::sqrt(ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]);
+            for (int k = 0; k < 3; k++) tf[((size_t)e * nf + s2) * 4 + k] = (T)(ns[k] / mag);
+            tf[((size_t)e * nf + s2) * 4 + 3] = (T)mag;
+        }
+    }
+    fr_status st = dalloc(m, &m->d_mu, tu.size() * sizeof(T));
+    if (!st) st = dalloc(m, &m->d_mq, tq.size() * sizeof(T));
+    if (!st) st = dalloc(m, &m->d_mfn, tf.size() * sizeof(T));
+    if (st) return st;
+    CU(cudaMemcpy(m->d_mu, tu.data(), tu.size() * sizeof(T), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(m->d_mq, tq.data(), tq.size() * sizeof(T), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(m->d_mfn, tf.data(), tf.size() * sizeof(T), cudaMemcpyHostToDevice));
     return FR_OK;
 }
 
@@ -852,6 +964,7 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
     st = (m->prec == FR_FP64) ? upload_geo<double>(m) : upload_geo<float>(m);
     if (!st) st = (m->prec == FR_FP64) ? upload_priops<double>(m, &m->d_priops) : upload_priops<float>(m, &m->d_priops);
     if (!st) st = (m->prec == FR_FP64) ? upload_tetops<double>(m) : upload_tetops<float>(m);
+    if (!st) st = (m->prec == FR_FP64) ? upload_curved<double>(m) : upload_curved<float>(m);
     if (!st && m->prec != FR_FP64) {
         bool all = true;
         for (const InstanceHost &I : m->inst) all = all && I.prm.p_ref > 0 && I.prm.rho_ref > 0;
@@ -927,7 +1040,7 @@ extern "C" fr_status fr_destroy(fr_mesh *m)
     void **bufs[] = {&m->d_fnrm, (void **)&m->d_fnrm64, &m->d_geo64, (void **)&m->d_MF, (void **)&m->d_RL, &m->d_priops, &m->d_priops64, &m->d_tetops, &m->d_geo, (void **)&m->d_partner, &m->d_UF, &m->d_FV, &m->d_CF, &m->d_QF, &m->d_DF, &m->d_Qu,
                      &m->d_UQ, &m->d_QQ, &m->d_Rt, &m->d_rk_k, &m->d_rk_us, (void **)&m->d_rk_acc, &m->d_io_U,
                      &m->d_io_R, (void **)&m->d_wsum, (void **)&m->d_status, &m->d_Qsnap, (void **)&m->d_qpartner,
-                     &m->d_UFQ, &m->d_FVQ, (void **)&m->d_qlpts, &m->d_DQ};
+                     &m->d_UFQ, &m->d_FVQ, (void **)&m->d_qlpts, &m->d_DQ, &m->d_mu, &m->d_mq, &m->d_mfn};
     for (void **b : bufs) dfree(*b);
     for (Group &g : m->groups) {
         dfree(g.d_geo); dfree((void *&)g.d_eu0); dfree((void *&)g.d_ef0); dfree((void *&)g.d_eph); dfree(g.d_phtab);
@@ -1036,6 +1149,11 @@ static HexArgs<T> make_args(fr_mesh *m, const Block &b, const void *U, void *R)
         a.nqlpts = m->nqlpts;
         a.tcmode = 0;
     }
+    if (m->curved) {
+        a.mu = reinterpret_cast<const T *>(m->d_mu);
+        a.mq = reinterpret_cast<const T *>(m->d_mq);
+        a.mfn = reinterpret_cast<const T *>(m->d_mfn);
+    }
     return a;
 }
 
@@ -1098,6 +1216,8 @@ struct RkFold {
 template <typename T>
 static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, const RkFold &rk = RkFold())
 {
+    if (m->form == FR_FUSED && m->curved)
+        return fail(FR_EUNSUPPORTED, "curved (non-affine) hexahedra run the unfused form (fr_set_form(FR_UNFUSED))");
     if (m->form == FR_FUSED) {
         static const int plain[3] = {0, 1, 2}, split[4] = {0, 1, 3, 4};
         const int *phases = m->split_c ? split : plain;
@@ -1163,6 +1283,10 @@ static fr_status rhs_dispatch(fr_mesh *m, const void *U, void *R, cudaStream_t s
 template <typename T>
 static fr_status autotune_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, int *chosen)
 {
+    if (m->curved) {   // the fused volume kernels (the ones tuned) do not run curved meshes
+        for (size_t gi = 0; gi < m->groups.size(); gi++) chosen[gi] = m->groups[gi].variant;
+        return FR_OK;
+    }
     // face solution of the current state first (the volume kernel reads it)
     for (const Group &gr : m->groups) {
         const Block &b = m->blocks[gr.blks[0]];
@@ -1433,13 +1557,12 @@ extern "C" fr_status fr_sol_coords(const fr_mesh *m, double *xyz)
         int n = h.n;
         long long le0 = B.type == 0 ? 0 : (B.type == 1 ? I.n_hex : I.n_hex + I.n_pri);
         for (long long e = 0; e < B.ne; e++) {
-            const double *x0J = &I.x0J[(size_t)(le0 + e) * 12];
             for (int z = 0; z < B.nu; z++, k++) {
                 double X[3];
                 if (B.type == 0) { X[0] = h.x[z % n]; X[1] = h.x[(z / n) % n]; X[2] = h.x[z / (n * n)]; }
                 else if (B.type == 1) { X[0] = m->pri.xt[z % FR_PT][0]; X[1] = m->pri.xt[z % FR_PT][1]; X[2] = h.x[z / FR_PT]; }
                 else { X[0] = m->tet.x[z][0]; X[1] = m->tet.x[z][1]; X[2] = m->tet.x[z][2]; }
-                affine_point(x0J, X, xyz + 3 * k);
+                map_point(I, le0 + e, X, xyz + 3 * k);
             }
         }
     }
@@ -1454,7 +1577,7 @@ struct WPts {
 // 2 -int d(rho|v|^2/2)/dt from R, 3..7 int R_alpha (weights W = tensor GL weights times detJ).
 template <typename T>
 __global__ void k_diag(const T *__restrict__ U, const T *__restrict__ R, const Geo<T> *__restrict__ geo, long long ne,
-                       int NU, WPts wp, double *out)
+                       int NU, WPts wp, double *out, const T *__restrict__ mu)
 {
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (long long e = blockIdx.x; e < ne; e += gridDim.x) {
@@ -1462,7 +1585,8 @@ __global__ void k_diag(const T *__restrict__ U, const T *__restrict__ R, const G
         const T *r = R ? R + e * 5 * NU : nullptr;
         const double det = (double)geo[e].det;
         for (int z = threadIdx.x; z < NU; z += blockDim.x) {
-            const double w = wp.w[z] * det;
+            // curved elements: det J at the solution point
+            const double w = wp.w[z] * (mu ? (double)mu[(e * NU + z) * 10 + 9] : det);
             const double rho = (double)u[z];
             const double v0 = (double)u[NU + z] / rho, v1 = (double)u[2 * NU + z] / rho, v2 = (double)u[3 * NU + z] / rho;
             const double v2s = v0 * v0 + v1 * v1 + v2 * v2;
@@ -1503,10 +1627,12 @@ extern "C" fr_status fr_diagnostics(fr_mesh *m, const void *U, const void *R, do
         const char *r = R ? (const char *)R + b.u0 * ts : nullptr;
         if (m->prec == FR_FP64)
             k_diag<double><<<grid, 128, 0, s>>>((const double *)u, (const double *)r,
-                                                 (const Geo<double> *)m->d_geo + b.elem0, b.ne, b.nu, wp, o);
+                                                 (const Geo<double> *)m->d_geo + b.elem0, b.ne, b.nu, wp, o,
+                                                 (const double *)m->d_mu);
         else
             k_diag<float><<<grid, 128, 0, s>>>((const float *)u, (const float *)r,
-                                                (const Geo<float> *)m->d_geo + b.elem0, b.ne, b.nu, wp, o);
+                                                (const Geo<float> *)m->d_geo + b.elem0, b.ne, b.nu, wp, o,
+                                                (const float *)m->d_mu);
         CU(cudaPeekAtLastError());
     }
     std::vector<double> h(ni * 8);
@@ -1581,10 +1707,12 @@ extern "C" fr_status fr_diagnostics_noalloc(fr_mesh *m, const void *U, const voi
         const char *r = R ? (const char *)R + b.u0 * ts : nullptr;
         if (m->prec == FR_FP64)
             k_diag<double><<<grid, 128, 0, s>>>((const double *)u, (const double *)r,
-                                                 (const Geo<double> *)m->d_geo + b.elem0, b.ne, b.nu, wp, o);
+                                                 (const Geo<double> *)m->d_geo + b.elem0, b.ne, b.nu, wp, o,
+                                                 (const double *)m->d_mu);
         else
             k_diag<float><<<grid, 128, 0, s>>>((const float *)u, (const float *)r,
-                                                (const Geo<float> *)m->d_geo + b.elem0, b.ne, b.nu, wp, o);
+                                                (const Geo<float> *)m->d_geo + b.elem0, b.ne, b.nu, wp, o,
+                                                (const float *)m->d_mu);
         CU(cudaPeekAtLastError());
     }
     // raw sums straight into the caller's array, then normalised in place (no host buffer either)

@@ -1363,11 +1363,12 @@ __global__ void __launch_bounds__(256) k_gradcoru(HexArgs<T> a)
     for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
         const long long e = it / (5 * NU);
         const int r = (int)(it % (5 * NU)), alpha = r / NU, z = r % NU;
-        const Geo<T> &g = a.geo[e];
+        // the element's metric, or (curved elements) the metric at this solution point
+        const T *Ji = a.mu ? a.mu + (e * NU + z) * 10 : a.geo[e].Ji;
         T *q = a.Qu + (e * 5 + alpha) * 3 * NU + z;
         const T q0 = q[0], q1 = q[NU], q2 = q[2 * NU];
 #pragma unroll
-        for (int k = 0; k < 3; k++) q[k * NU] = g.Ji[k] * q0 + g.Ji[3 + k] * q1 + g.Ji[6 + k] * q2;
+        for (int k = 0; k < 3; k++) q[k * NU] = Ji[k] * q0 + Ji[3 + k] * q1 + Ji[6 + k] * q2;
     }
 }
 
@@ -1432,11 +1433,20 @@ __global__ void __launch_bounds__(128) k_tdisf(HexArgs<T> a)
             for (int d = 0; d < 3; d++) gq[alpha][d] = Q[(alpha * 3 + d) * NQ];
         }
         ok &= total_flux(a.ph, u, gq, f);
+        if (a.mq) {   // curved elements: det J J^-1 at this quadrature point
+            const T *c = a.mq + (e * NQ + q) * 9;
 #pragma unroll
-        for (int alpha = 0; alpha < 5; alpha++)
+            for (int alpha = 0; alpha < 5; alpha++)
 #pragma unroll
-            for (int d = 0; d < 3; d++)
-                Q[(alpha * 3 + d) * NQ] = g.det * (g.Ji[3 * d] * f[0][alpha] + g.Ji[3 * d + 1] * f[1][alpha] + g.Ji[3 * d + 2] * f[2][alpha]);
+                for (int d = 0; d < 3; d++)
+                    Q[(alpha * 3 + d) * NQ] = c[3 * d] * f[0][alpha] + c[3 * d + 1] * f[1][alpha] + c[3 * d + 2] * f[2][alpha];
+        } else {
+#pragma unroll
+            for (int alpha = 0; alpha < 5; alpha++)
+#pragma unroll
+                for (int d = 0; d < 3; d++)
+                    Q[(alpha * 3 + d) * NQ] = g.det * (g.Ji[3 * d] * f[0][alpha] + g.Ji[3 * d + 1] * f[1][alpha] + g.Ji[3 * d + 2] * f[2][alpha]);
+        }
     }
     flag_status(a.status, ok);
 }
@@ -1494,13 +1504,19 @@ __global__ void __launch_bounds__(128) k_comm_flux(HexArgs<T> a)
             for (int d = 0; d < 3; d++) { qL[k][d] = a.QF[(k * 3 + d) * a.nfpt + gl]; qR[k][d] = a.QF[(k * 3 + d) * a.nfpt + gr]; }
         }
         T n[3], magL;
-        face_normal(a.geo[e], f, n, magL);
         // the R side's |n_s| comes from its own element (global flux point -> element of this handle's
         // hex blocks; the unfused form supports single-block hex meshes)
         const long long eR = (gr - a.f0) / NF;
         const int fR = (int)((gr - a.f0) % NF) / (N * N);
         T nR[3], magR;
-        face_normal(a.geo[eR], fR, nR, magR);
+        if (a.mfn) {   // curved elements: the normal at the flux point itself, from each side
+            const T *tl = a.mfn + (gl - a.f0) * 4, *tr = a.mfn + (gr - a.f0) * 4;
+            n[0] = tl[0]; n[1] = tl[1]; n[2] = tl[2]; magL = tl[3];
+            nR[0] = tr[0]; nR[1] = tr[1]; nR[2] = tr[2]; magR = tr[3];
+        } else {
+            face_normal(a.geo[e], f, n, magL);
+            face_normal(a.geo[eR], fR, nR, magR);
+        }
         T fvL[4], fvR[4], mnR[3] = {-n[0], -n[1], -n[2]};
         viscous_normal_flux(a.ph, uL, qL, n, fvL);
         viscous_normal_flux(a.ph, uR, qR, mnR, fvR);
@@ -1530,7 +1546,7 @@ __global__ void __launch_bounds__(256) k_tdivtconf(HexArgs<T> a)
             v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
             a.Rt[it] = v;
         } else {
-            a.R[a.u0 + it] = -a.Rt[it] / a.geo[e].det;
+            a.R[a.u0 + it] = -a.Rt[it] / (a.mu ? a.mu[(e * NU + z) * 10 + 9] : a.geo[e].det);
         }
     }
 }

@@ -219,6 +219,10 @@ struct HexArgs {
     T *DQ;                    // [5][nqf] transformed common flux per side
     const uint32_t *qlpts;    // L quadrature points (one per pair)
     long long nqf, nqlpts;
+    // Curved (trilinear) hexahedra, unfused form: metric terms at every point (null on affine meshes)
+    const T *mu;              // [elem][nu][10]: J^-1 (row-major dxi_i/dx_j) and det J at solution points
+    const T *mq;              // [elem][nq][9]: det J J^-1 at quadrature points
+    const T *mfn;             // [elem][nf][4]: unit outward normal and |n_s| at flux points
 };
 
 #ifdef __CUDACC__

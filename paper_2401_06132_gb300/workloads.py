@@ -210,7 +210,8 @@ def curved_box_mesh(N: int, amp: float = 0.1, length: float = 2 * math.pi, origi
     """N^3 periodic box of non-affine (trilinear) hexahedra: the uniform vertex grid (X, Y, Z) moved
     by amp * h * (sin(2 pi Y/L) sin(2 pi Z/L), sin(2 pi Z/L) sin(2 pi X/L), sin(2 pi X/L) sin(2 pi Y/L)),
     a displacement that is periodic on the grid, so faces still match across the periods. Every
-    element is a general hexahedron with straight edges whose metric terms vary inside it."""
+    element is a general hexahedron with straight edges whose metric terms vary inside it (for
+    N >= 3; at N = 2 every vertex sits on a zero of the displacement)."""
     h = length / N
     g = origin + length * np.arange(N + 1) / N
     X, Y, Z = np.meshgrid(g, g, g, indexing="ij")

@@ -742,3 +742,72 @@ def test_tet_full_size_sampled_against_oracle():
     bound, spread = _tet_bound(mesh, U, nu)
     print(f"tet 16^3: {err} (oracle spread {spread:.2e}, bound {bound:.2e})")
     assert err.max() <= bound and bound <= 2e-11, (err, bound)
+
+
+# ----------------------------------------------------------------------------------------------
+# Curved (trilinear) hexahedra: metric terms per point, unfused form
+# ----------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N,amp", [(3, 0.15), (4, 0.1)])
+@pytest.mark.parametrize("p", [3, 4])
+@pytest.mark.parametrize("pref", [0.0, 1.0])
+def test_curved_rhs_fp64_matches_oracle(N, amp, p, pref):
+    """Non-affine hexahedra (the periodic box with sinusoidally displaced vertices): J^-T at every
+    solution point, det J J^-1 at every quadrature point, n_s at every flux point; the unfused form
+    against the oracle, FP64, 1e-12."""
+    mesh = W.curved_box_mesh(N, amp=amp)
+    nu = (p + 1) ** 3
+    p_ref = pref * W.tgv_p0()
+    o = O.Oracle(mesh, p, p + 2, threads=NCPU, p_ref=p_ref)
+    U = W.tgv_state(o.sol_coords(), [(N ** 3, nu)], perturb=1e-2)
+    Ro = o.rhs(U)
+    m = fr.FRMesh(mesh, fr.make_params(p=p, p_ref=p_ref))
+    assert np.abs(m.sol_coords() - o.sol_coords()).max() < 1e-13
+    m.set_form("unfused")
+    Ud = torch.from_numpy(U).cuda()
+    Rd = torch.empty_like(Ud)
+    m.rhs(Ud, Rd)
+    m.sync_status()
+    err = rel_linf(Rd.cpu().numpy(), Ro, nu)
+    print(f"curved N={N} p={p} pref={pref}: {err}")
+    assert err.max() <= 1e-12, err
+    # the fused kernels assume an element-constant metric: they refuse curved meshes
+    m.set_form("fused")
+    with pytest.raises(fr.FRError) as e:
+        m.rhs(Ud, Rd)
+    assert e.value.status == fr.FR_EUNSUPPORTED
+
+
+def test_curved_rk4_diagnostics_and_fp32():
+    """RK4 (unfused, graph-replayed) and the diagnostics (weights W det J at each solution point) on
+    the curved 4^3 box against the oracle; the FP32 unfused form against the oracle on the
+    FP32-rounded input."""
+    mesh = W.curved_box_mesh(4)
+    p0 = W.tgv_p0()
+    o = O.Oracle(mesh, 3, 5, threads=NCPU, p_ref=p0)
+    U = W.tgv_state(o.sol_coords(), [(64, 64)], perturb=1e-2)
+    m = fr.FRMesh(mesh, fr.make_params(p=3, p_ref=p0))
+    m.set_form("unfused")
+    Ud = torch.from_numpy(U).cuda()
+    Rd = torch.empty_like(Ud)
+    m.rhs(Ud, Rd)
+    d = m.diagnostics(Ud, Rd)[0]
+    do = o.diagnostics(U, o.rhs(U))
+    assert abs(d["volume"] / do["volume"] - 1) < 1e-13 and abs(d["eps"] / do["eps"] - 1) < 1e-8
+    Uo = o.rk4(U, 1e-3, 5)
+    m.rk4_step(Ud, 1e-3, 5)
+    m.sync_status()
+    dr = np.abs(Ud.cpu().numpy() - Uo).max() / np.abs(Uo).max()
+    print(f"curved RK4: {dr:.3e}")
+    assert dr <= 1e-13, dr
+    U32 = U.astype(np.float32)
+    Ro = o.rhs(U32.astype(np.float64))
+    m32 = fr.FRMesh(mesh, fr.make_params(p=3, prec="fp32", p_ref=p0))
+    m32.set_form("unfused")
+    Ud = torch.from_numpy(U32).cuda()
+    Rd = torch.empty_like(Ud)
+    m32.rhs(Ud, Rd)
+    m32.sync_status()
+    err = rel_linf(Rd.cpu().numpy().astype(np.float64), Ro, 64)
+    print(f"curved fp32: {err}")
+    assert err.max() <= 1e-3, err

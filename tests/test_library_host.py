@@ -43,13 +43,14 @@ def test_host_validation_rejects_bad_meshes_before_any_device_work(lib):
     with pytest.raises(fr.FRError) as e:
         _create(W.box_hex_mesh(2, periodic=False))
     assert e.value.status == fr.FR_EMESH
-    # non-affine hex: move one corner
-    mesh = W.box_hex_mesh(2)
+    # non-affine hex (one corner moved) is a curved element: with a non-affine prism beside it the
+    # mesh is refused (prisms must be affine)
+    mesh = W.mixed_box_mesh(2)
     mesh["verts"] = mesh["verts"].copy()
-    mesh["verts"][13] += np.array([0.1, 0.0, 0.0])
+    mesh["verts"][mesh["pri_v"][0, 4]] += np.array([0.05, 0.0, 0.0])
     with pytest.raises(fr.FRError) as e:
         _create(mesh)
-    assert e.value.status == fr.FR_EUNSUPPORTED
+    assert e.value.status in (fr.FR_EUNSUPPORTED, fr.FR_EMESH)
     # inverted element: swap two corners of the tensor order
     mesh = W.box_hex_mesh(1)
     mesh["hex_v"] = mesh["hex_v"][:, [1, 0, 3, 2, 5, 4, 7, 6]].copy()
@@ -178,3 +179,15 @@ def test_host_validation_tetrahedra(lib):
     with pytest.raises(fr.FRError) as e:
         _create(mesh)
     assert e.value.status == fr.FR_EMESH
+
+
+def test_host_validation_curved(lib):
+    """Curved (trilinear) hexahedra run single-instance hexahedral meshes with m = p + 2."""
+    mesh = W.curved_box_mesh(3)
+    for kw in (dict(p=3, nq1d=4), dict(p=3, surface_aa=True)):
+        with pytest.raises(fr.FRError) as e:
+            _create(mesh, **kw)
+        assert e.value.status == fr.FR_EUNSUPPORTED, kw
+    with pytest.raises(fr.FRError) as e:
+        fr.FRMesh([mesh, mesh], fr.make_params(p=3))
+    assert e.value.status == fr.FR_EUNSUPPORTED
