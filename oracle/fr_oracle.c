@@ -41,8 +41,8 @@
  *       4/5 towards the centroid; each triangular face carries the printed Williams-Shunn triangle
  *       points (so p = 2, 3). With the DG-equivalent lift and the L2 projection of the flux, the RHS
  *       as a polynomial does not depend on the solution points, only its rounding does.
- *   C1  curved (non-affine) hexahedra (the metric terms x^(c) of the paper's byte tables vary per
- *       point): the trilinear map of the 8 vertices; J^-T at each solution point for the gradient,
+ *   C1  curved (non-affine) hexahedra (gradcoru reads per-point metric terms J^(u) in the
+ *       appendix's data-movement table): the trilinear map of the 8 vertices; J^-T at each solution point for the gradient,
  *       det J J^-1 at each quadrature point for the flux, n_s = det J J^-T n~ at each flux point,
  *       R = -R~ / det J at each solution point. Prisms and tetrahedra stay affine.
  *   T2  tetrahedron quadrature: collapsed m x m x m rule (GL in a, Gauss rules of the weights
