@@ -710,7 +710,7 @@ static fr_status upload_tetops(fr_mesh *m)
         for (int z = 0; z < FR_TU; z++) t.Lt[s2][z] = (T)Tt.L[z][s2];
     // projection with the corrected divergence: (Dh_d Pj)[z][q], formed in FP64
     for (int d = 0; d < 3; d++)
-        for (int q = 0; q < FR_TQ; q++)
+        for (int q = 0; q < FR_TQ; q++)   // rows FR_TQ .. FR_TQP-1 stay zero
             for (int z = 0; z < FR_TU; z++) {
                 double v = 0;
                 for (int j = 0; j < FR_TU; j++) v += Tt.Dh[d][z][j] * Tt.Pj[j][q];

@@ -62,6 +62,7 @@ int prism2d(Prism2D &P);
 #define FR_TU 20      // solution points
 #define FR_TF 40      // flux points
 #define FR_TQ 125     // quadrature points
+#define FR_TQP 128    // quadrature points padded to whole 16-byte vectors (the pad rows are zero)
 struct Tet3D {
     double x[FR_TU][3];            // solution points (reference coordinates)
     double w[FR_TU];               // int l_z over the reference tetrahedron
@@ -114,7 +115,7 @@ struct TetOps {
     T M0t[FR_TU][FR_TF];           // M0^T: [z][s]
     T Dht[3][FR_TU][FR_TU];        // [d][j][z] = Dh[d][z][j]
     T Lt[FR_TF][FR_TU];            // [s][z] = L[z][s]
-    T Dvt[3][FR_TQ][FR_TU];        // (Dh_d Pj)^T: projection with the corrected divergence, [d][q][z]
+    T Dvt[3][FR_TQP][FR_TU];       // (Dh_d Pj)^T: projection with the corrected divergence, [d][q][z]
     T nf[4][3];
 };
 

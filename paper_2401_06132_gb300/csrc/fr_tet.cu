@@ -21,9 +21,21 @@
 
 namespace {
 
-constexpr int NU = FR_TU, NF = FR_TF, NQ = FR_TQ;
+constexpr int NU = FR_TU, NF = FR_TF, NQ = FR_TQ, NQP = FR_TQP;
 
 __device__ __forceinline__ int face_of(int s) { return s / 10; }
+
+// 16 bytes of T (4 floats or 2 doubles): one vector shared-memory load
+template <typename T>
+struct alignas(16) V16 {
+    static constexpr int n = 16 / sizeof(T);
+    T v[n];
+};
+template <typename T>
+__device__ __forceinline__ V16<T> ld16(const T *p)
+{
+    return *reinterpret_cast<const V16<T> *>(p);
+}
 
 // -------------------------------------------------------------------------------------------------
 // Phase A: disu (U^f = M0 U)
@@ -55,10 +67,17 @@ __global__ void __launch_bounds__(NTH) k_tet_B(HexArgs<T> a, const TetOps<T> *__
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ short s_plist[NF];
     __shared__ int s_pcnt;
+    constexpr int VW = V16<T>::n;
+    constexpr int NCH = 6;                        // quadrature-point chunks of the projection
     T *s_u = reinterpret_cast<T *>(smem_raw);   // [5][NU] state
     T *s_q = s_u + 5 * NU;                        // [15][NU] physical gradient (field 5 + 3 alpha + d of s_u)
     T *s_c = s_q + 15 * NU;                       // [5][NF] common solution
-    T *s_w = s_c + 5 * NF;                        // [20][NQ] fields at quadrature points, then f~
+    T *s_w = s_c + 5 * NF;                        // [20][NQP] fields at quadrature points, then f~
+    T *s_red = s_u;                               // [NCH][5][NU] projection partial sums (s_u, s_q, s_c are dead by then)
+    static_assert(NCH * 5 * NU <= 20 * NU + 5 * NF, "partial sums fit in the state, gradient and common-solution arrays");
+    static_assert(NU % VW == 0 && (NU * sizeof(T)) % 16 == 0 && (NQP * sizeof(T)) % 16 == 0, "16-byte rows");
+    // the pad columns q = NQ .. NQP-1 of s_w meet zero operator rows; they stay zero
+    for (int it = threadIdx.x; it < 20 * (NQP - NQ); it += NTH) s_w[(it / (NQP - NQ)) * NQP + NQ + it % (NQP - NQ)] = T(0);
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
         const Geo<T> g = a.geo[e];
         const Phys<T> ph = elem_phys(a, e);
@@ -121,11 +140,17 @@ __global__ void __launch_bounds__(NTH) k_tet_B(HexArgs<T> a, const TetOps<T> *__
             T v[20];
 #pragma unroll
             for (int f = 0; f < 20; f++) v[f] = T(0);
-#pragma unroll 2
-            for (int z = 0; z < NU; z++) {
-                const T m = op->M0t[z][s];
+#pragma unroll 1
+            for (int z0 = 0; z0 < NU; z0 += VW) {
+                T m[VW];
 #pragma unroll
-                for (int f = 0; f < 20; f++) v[f] += m * s_u[f * NU + z];
+                for (int k = 0; k < VW; k++) m[k] = op->M0t[z0 + k][s];
+#pragma unroll
+                for (int f = 0; f < 20; f++) {
+                    const V16<T> x = ld16(s_u + f * NU + z0);
+#pragma unroll
+                    for (int k = 0; k < VW; k++) v[f] += m[k] * x.v[k];
+                }
             }
             T uf[5], qf[5][3];
 #pragma unroll
@@ -146,14 +171,20 @@ __global__ void __launch_bounds__(NTH) k_tet_B(HexArgs<T> a, const TetOps<T> *__
             T v[20];
 #pragma unroll
             for (int f = 0; f < 20; f++) v[f] = T(0);
-#pragma unroll 2
-            for (int j = 0; j < NU; j++) {
-                const T b = op->Bt[j][q];
+#pragma unroll 1
+            for (int j0 = 0; j0 < NU; j0 += VW) {
+                T b[VW];
 #pragma unroll
-                for (int f = 0; f < 20; f++) v[f] += b * s_u[f * NU + j];
+                for (int k = 0; k < VW; k++) b[k] = op->Bt[j0 + k][q];
+#pragma unroll
+                for (int f = 0; f < 20; f++) {
+                    const V16<T> x = ld16(s_u + f * NU + j0);
+#pragma unroll
+                    for (int k = 0; k < VW; k++) v[f] += b[k] * x.v[k];
+                }
             }
 #pragma unroll
-            for (int f = 0; f < 20; f++) s_w[f * NQ + q] = v[f];
+            for (int f = 0; f < 20; f++) s_w[f * NQP + q] = v[f];
         }
         __syncthreads();
         bool ok = true;
@@ -161,32 +192,56 @@ __global__ void __launch_bounds__(NTH) k_tet_B(HexArgs<T> a, const TetOps<T> *__
             T u[5], gq[5][3], f[3][5];
 #pragma unroll
             for (int alpha = 0; alpha < 5; alpha++) {
-                u[alpha] = s_w[alpha * NQ + q];
+                u[alpha] = s_w[alpha * NQP + q];
 #pragma unroll
-                for (int d = 0; d < 3; d++) gq[alpha][d] = s_w[(5 + alpha * 3 + d) * NQ + q];
+                for (int d = 0; d < 3; d++) gq[alpha][d] = s_w[(5 + alpha * 3 + d) * NQP + q];
             }
             ok &= total_flux(ph, u, gq, f);
 #pragma unroll
             for (int alpha = 0; alpha < 5; alpha++)
 #pragma unroll
                 for (int d = 0; d < 3; d++)
-                    s_w[(alpha * 3 + d) * NQ + q] = g.det * (g.Ji[3 * d] * f[0][alpha] + g.Ji[3 * d + 1] * f[1][alpha] + g.Ji[3 * d + 2] * f[2][alpha]);
+                    s_w[(alpha * 3 + d) * NQP + q] = g.det * (g.Ji[3 * d] * f[0][alpha] + g.Ji[3 * d + 1] * f[1][alpha] + g.Ji[3 * d + 2] * f[2][alpha]);
         }
         flag_status(a.status, ok);
         __syncthreads();
-        // projection with the corrected divergence: R~[alpha][z] = sum_d sum_q Dv_d[z][q] f~_d[alpha][q]
+        // projection with the corrected divergence: R~[alpha][z] = sum_d sum_q Dv_d[z][q] f~_d[alpha][q].
+        // Thread (z, chunk c of the NQP/4 groups of 4 quadrature points) sums all 5 variables over its
+        // chunk (one operator load per 5 FMAs, the flux values as 16-byte broadcasts); the NCH
+        // partial sums are then added in shared memory.
+        if (threadIdx.x < NU * NCH) {
+            const int z = threadIdx.x % NU, c = threadIdx.x / NU;
+            const int gb = c * (NQP / 4) / NCH, ge = (c + 1) * (NQP / 4) / NCH;
+            T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll 1
+            for (int d = 0; d < 3; d++)
+#pragma unroll 1
+                for (int gq4 = gb; gq4 < ge; gq4++) {
+                    const int q0 = 4 * gq4;
+                    T mv[4];
+#pragma unroll
+                    for (int k = 0; k < 4; k++) mv[k] = op->Dvt[d][q0 + k][z];
+#pragma unroll
+                    for (int alpha = 0; alpha < 5; alpha++) {
+                        const T *F = s_w + (alpha * 3 + d) * NQP + q0;
+#pragma unroll
+                        for (int h = 0; h < 4; h += VW) {
+                            const V16<T> x = ld16(F + h);
+#pragma unroll
+                            for (int k = 0; k < VW; k++) acc[alpha] += mv[h + k] * x.v[k];
+                        }
+                    }
+                }
+#pragma unroll
+            for (int alpha = 0; alpha < 5; alpha++) s_red[(c * 5 + alpha) * NU + z] = acc[alpha];
+        }
+        __syncthreads();
         T *R = a.R + elem_u0(a, e, NU);
         for (int it = threadIdx.x; it < 5 * NU; it += NTH) {
-            const int alpha = it / NU, z = it % NU;
-            const T *F = s_w + alpha * 3 * NQ;
-            T v0 = T(0), v1 = T(0), v2 = T(0);
-#pragma unroll 5
-            for (int q = 0; q < NQ; q++) {
-                v0 += op->Dvt[0][q][z] * F[q];
-                v1 += op->Dvt[1][q][z] * F[NQ + q];
-                v2 += op->Dvt[2][q][z] * F[2 * NQ + q];
-            }
-            R[it] = (v0 + v1) + v2;
+            T v = T(0);
+#pragma unroll
+            for (int c = 0; c < NCH; c++) v += s_red[c * 5 * NU + it];
+            R[it] = v;
         }
         __syncthreads();
     }
@@ -259,7 +314,7 @@ int tet_fused_phase(int phase, const HexArgs<T> &a, const TetOps<T> *ops, cudaSt
         k_tet_disu<T><<<(int)g, 256, 0, s>>>(a, ops);
     } else if (phase == 1) {
         constexpr int NTH = 128;
-        const size_t smem = (size_t)(5 * NU + 15 * NU + 5 * NF + 20 * NQ) * sizeof(T);
+        const size_t smem = (size_t)(5 * NU + 15 * NU + 5 * NF + 20 * NQP) * sizeof(T);
         static bool attr = false;
         if (!attr) {
             cudaFuncSetAttribute(k_tet_B<T, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
