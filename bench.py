@@ -227,7 +227,7 @@ def _time_steps(m, U, steps, warmup, torch):
 def other_configs(args, torch, fr, W):
     """Mixed hex/prism TGV (40^3 box: 32,000 hexes + 64,000 prisms, p = 3), the 48^3 TGV without
     anti-aliasing and with full (flux + surface-flux) anti-aliasing, a tetrahedral TGV box, a curved
-    (trilinear) hexahedral TGV box in the unfused form, and the batched ensemble
+    (trilinear) hexahedral TGV box, and the batched ensemble
     of 64 TGV instances (edges in {8,...,24}, p in {3,4}, M in [0.05,0.2], Re in [400,3200] from
     SplitMix64(20240111)), each timed over RK4 steps on a side stream (CUDA-graph replay)."""
     out = {}
@@ -302,17 +302,18 @@ def other_configs(args, torch, fr, W):
             out[f"tet24_{prec}"]["speedup_vs_fp64"] = out["tet24_fp64"]["ms_per_step"] / ms
         m.close()
         del U
-    # curved (trilinear) hexahedra, 48^3 p = 3: metric terms at every point, unfused form
+    # curved (trilinear) hexahedra, 48^3 p = 3: metric terms at every point; fused FP64 and plain
+    # FP32, and the unfused FP64 form
     mesh_c = W.curved_box_mesh(N_EDGE)
-    for prec in ("fp64", "fp32"):
+    for name, prec, form in (("fp64", "fp64", "fused"), ("fp32", "fp32", "fused"), ("unfused_fp64", "fp64", "unfused")):
         m = fr.FRMesh(mesh_c, fr.make_params(p=P, prec=prec, p_ref=p0))
-        m.set_form("unfused")
+        m.set_form(form)
         U0 = W.tgv_state(m.sol_coords(), [(N_EDGE ** 3, (P + 1) ** 3)], perturb=1e-3)
         U = torch.from_numpy(U0).cuda()
         ms = _time_steps(m, U, steps, 2, torch)
         m.sync_status()
-        out[f"curved48_unfused_{prec}"] = {"gdof_rhs_per_s": U0.size * RHS_PER_STEP / (ms * 1e-3) / 1e9,
-                                           "ms_per_step": ms, "dof": int(U0.size), "elements": N_EDGE ** 3}
+        out[f"curved48_{name}"] = {"gdof_rhs_per_s": U0.size * RHS_PER_STEP / (ms * 1e-3) / 1e9,
+                                   "ms_per_step": ms, "dof": int(U0.size), "elements": N_EDGE ** 3}
         m.close()
         del U
         torch.cuda.empty_cache()

@@ -642,7 +642,7 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
         for (char c : I.curved) m->curved = m->curved || c;
     if (m->curved && (n_inst != 1 || m->blocks.size() != 1 || m->surf || m->blocks[0].m != m->blocks[0].p + 2))
         return fail(FR_EUNSUPPORTED, "curved (non-affine) hexahedra run single-instance hexahedral meshes with flux "
-                                     "anti-aliasing (m = p + 2), in the unfused form");
+                                     "anti-aliasing (m = p + 2)");
     m->inst_u0.push_back(u);
     bfirst.push_back((int)m->blocks.size());
     if (f >= (long long)FR_LFLAG) return fail(FR_EUNSUPPORTED, "more than 2^31 flux points");
@@ -1150,6 +1150,7 @@ static HexArgs<T> make_args(fr_mesh *m, const Block &b, const void *U, void *R)
         a.tcmode = 0;
     }
     if (m->curved) {
+        a.tcmode = 0;   // the tensor-core volume kernels keep an element-constant metric
         a.mu = reinterpret_cast<const T *>(m->d_mu);
         a.mq = reinterpret_cast<const T *>(m->d_mq);
         a.mfn = reinterpret_cast<const T *>(m->d_mfn);
@@ -1216,8 +1217,9 @@ struct RkFold {
 template <typename T>
 static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, const RkFold &rk = RkFold())
 {
-    if (m->form == FR_FUSED && m->curved)
-        return fail(FR_EUNSUPPORTED, "curved (non-affine) hexahedra run the unfused form (fr_set_form(FR_UNFUSED))");
+    if (m->form == FR_FUSED && m->curved && m->lowmach)
+        return fail(FR_EUNSUPPORTED, "curved (non-affine) hexahedra: the low-Mach FP32 form is not built for them "
+                                     "(set rho_ref = 0 for the plain FP32 form)");
     if (m->form == FR_FUSED) {
         static const int plain[3] = {0, 1, 2}, split[4] = {0, 1, 3, 4};
         const int *phases = m->split_c ? split : plain;

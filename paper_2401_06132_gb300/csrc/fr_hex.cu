@@ -500,11 +500,13 @@ __device__ __forceinline__ void project_5(const HexOps<T> &op, const T *src, T *
     __syncthreads();
 }
 
-template <typename T, int P, int NT, int TCM = 0, bool AA = true, bool SURF = false>
+template <typename T, int P, int NT, int TCM = 0, bool AA = true, bool SURF = false, bool CURV = false>
 __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
 {
     static_assert(AA || TCM == 0, "the collocation form has no interpolation or projection");
     static_assert(!SURF || (AA && TCM == 0), "surface-flux anti-aliasing runs with flux anti-aliasing on the CUDA cores");
+    // CURV: curved (trilinear) elements of a single block, metric terms per point from a.mu, a.mq, a.mfn
+    static_assert(!CURV || (AA && !SURF && TCM == 0), "curved elements: flux anti-aliasing on the CUDA cores");
     using S = HexSmem<T, P>;
     using TC = HexTc<P>;
     static_assert(TCM == 0 || (NT == 128 && std::is_same<T, float>::value), "tensor-core form: FP32, one warpgroup");
@@ -658,7 +660,12 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
         for (int it = threadIdx.x; it < 5 * NU; it += NT) {
             const int alpha = it / NU, z = it % NU;
             T *q = s_q + alpha * 3 * FS + z % N + XS * ((z / N) % N) + PS * (z / (N * N));
-            if (diagJ) {
+            if constexpr (CURV) {   // J^-T at this solution point
+                const T *Ji = a.mu + (e * NU + z) * 10;
+                const T q0 = q[0], q1 = q[FS], q2 = q[2 * FS];
+#pragma unroll
+                for (int k = 0; k < 3; k++) q[k * FS] = Ji[k] * q0 + Ji[3 + k] * q1 + Ji[6 + k] * q2;
+            } else if (diagJ) {
                 q[0] *= g.Ji[0]; q[FS] *= g.Ji[4]; q[2 * FS] *= g.Ji[8];
             } else {
                 const T q0 = q[0], q1 = q[FS], q2 = q[2 * FS];
@@ -799,7 +806,12 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
                 }
             }
             T n[3], mag;
-            face_nrm<T, T>(a.fnrm, e, f, n, mag);
+            if constexpr (CURV) {   // the normal at this flux point
+                const T *t = a.mfn + (e * NF + s) * 4;
+                n[0] = t[0]; n[1] = t[1]; n[2] = t[2]; mag = t[3];
+            } else {
+                face_nrm<T, T>(a.fnrm, e, f, n, mag);
+            }
             if constexpr (std::is_same<T, float>::value) {
                 if (dev) { uf[0] += ph.rref; uf[4] += ph.eref; }
             }
@@ -945,7 +957,14 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
             } else {
                 ok &= total_flux(ph, u, gq, f);
             }
-            if (diagJ) {
+            if constexpr (CURV) {   // det J J^-1 at this quadrature point
+                const T *c = a.mq + (e * NQ + q) * 9;
+#pragma unroll
+                for (int alpha = 0; alpha < 5; alpha++)
+#pragma unroll
+                    for (int d = 0; d < 3; d++)
+                        s_w[(alpha * 3 + d) * NQ + q] = c[3 * d] * f[0][alpha] + c[3 * d + 1] * f[1][alpha] + c[3 * d + 2] * f[2][alpha];
+            } else if (diagJ) {
                 const T s0 = g.det * g.Ji[0], s1 = g.det * g.Ji[4], s2 = g.det * g.Ji[8];
 #pragma unroll
                 for (int alpha = 0; alpha < 5; alpha++) {
@@ -1064,7 +1083,12 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
 #pragma unroll
             for (int k = 0; k < 4; k++) { fvo[k] = a.FV[k * a.nfpt + og]; fvp[k] = a.FV[k * a.nfpt + pg]; }
             T n[3], mag;
-            face_nrm<T, T>(a.fnrm, e, f, n, mag);
+            if (a.mfn) {   // curved elements: the normal at this flux point
+                const T *t = a.mfn + (e * NF + s) * 4;
+                n[0] = t[0]; n[1] = t[1]; n[2] = t[2]; mag = t[3];
+            } else {
+                face_nrm<T, T>(a.fnrm, e, f, n, mag);
+            }
             T nL[3] = {isL ? n[0] : -n[0], isL ? n[1] : -n[1], isL ? n[2] : -n[2]};
             T F[5];
             if constexpr (std::is_same<T, float>::value) {
@@ -1101,8 +1125,10 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
                 v += op.liftL[i] * D[0 * N * N + j + N * k] + op.liftR[i] * D[1 * N * N + j + N * k];
                 v += op.liftL[j] * D[2 * N * N + i + N * k] + op.liftR[j] * D[3 * N * N + i + N * k];
                 v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
-                if (a.rkstage == 0) R[it] = v * idet;
-                else rk_fold(a, elem_u0(a, e, NU) + it, v * idet);
+                // curved elements: det J at this solution point
+                const T sc = a.mu ? T(-1) / a.mu[(e * NU + z) * 10 + 9] : idet;
+                if (a.rkstage == 0) R[it] = v * sc;
+                else rk_fold(a, elem_u0(a, e, NU) + it, v * sc);
             }
         } else if constexpr (std::is_same<T, float>::value) {
             // low-Mach form: R_rho in float-float, R_E = R_(E - H0 rho) + H0 R_rho
@@ -1251,7 +1277,12 @@ __global__ void __launch_bounds__(128) k_pair_flux(HexArgs<T> a)
 #pragma unroll
         for (int k = 0; k < 4; k++) { fvL[k] = a.FV[k * a.nfpt + gl]; fvR[k] = a.FV[k * a.nfpt + gr]; }
         T n[3], mag;
-        face_nrm<T, T>(a.fnrm, e, f, n, mag);
+        if (a.mfn) {   // curved elements: the normal at this flux point
+            const T *t = a.mfn + (e * NF + s) * 4;
+            n[0] = t[0]; n[1] = t[1]; n[2] = t[2]; mag = t[3];
+        } else {
+            face_nrm<T, T>(a.fnrm, e, f, n, mag);
+        }
         T F[5];
         ok &= common_flux(ph, uL, uR, fvL, fvR, n, F);
 #pragma unroll
@@ -1273,7 +1304,7 @@ __global__ void __launch_bounds__(NT) k_lift(HexArgs<T> a)
             const uint32_t pc = a.partner[gf0 + s];
             const bool isL = (pc & FR_LFLAG) != 0;
             const long long src = isL ? gf0 + s : (long long)(pc & ~FR_LFLAG);
-            const T mag = a.fnrm[(e * 6 + s / (N * N)) * 4 + 3];
+            const T mag = a.mfn ? a.mfn[(e * NF + s) * 4 + 3] : a.fnrm[(e * 6 + s / (N * N)) * 4 + 3];
             const T sc = isL ? mag : -mag;
 #pragma unroll
             for (int k = 0; k < 5; k++) s_d[k * NF + s] = sc * a.DF[k * a.nfpt + src];
@@ -1288,8 +1319,10 @@ __global__ void __launch_bounds__(NT) k_lift(HexArgs<T> a)
             v += op.liftL[i] * D[0 * N * N + j + N * k] + op.liftR[i] * D[1 * N * N + j + N * k];
             v += op.liftL[j] * D[2 * N * N + i + N * k] + op.liftR[j] * D[3 * N * N + i + N * k];
             v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
-            if (a.rkstage == 0) R[it] = v * idet;
-            else rk_fold(a, elem_u0(a, e, NU) + it, v * idet);
+            // curved elements: det J at this solution point
+            const T sc = a.mu ? T(-1) / a.mu[(e * NU + z) * 10 + 9] : idet;
+            if (a.rkstage == 0) R[it] = v * sc;
+            else rk_fold(a, elem_u0(a, e, NU) + it, v * sc);
         }
         __syncthreads();
     }
@@ -1568,7 +1601,7 @@ static int grid_elems(long long ne, int per_sm)
     return (int)(g < 1 ? 1 : g);
 }
 
-template <typename T, int P, int NT, bool AA = true, bool SURF = false>
+template <typename T, int P, int NT, bool AA = true, bool SURF = false, bool CURV = false>
 static void launch_B(const HexArgs<T> &a, cudaStream_t s)
 {
     using S = HexSmem<T, P>;
@@ -1579,10 +1612,10 @@ static void launch_B(const HexArgs<T> &a, cudaStream_t s)
     const size_t smem = (!AA ? 20 * S::FS + 5 * S::NF : (SURF ? S::SIZE - S::T1 - S::T2 + TAIL : S::SIZE)) * sizeof(T);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_fused_B<T, P, NT, 0, AA, SURF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_fused_B<T, P, NT, 0, AA, SURF, CURV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    k_fused_B<T, P, NT, 0, AA, SURF><<<grid_elems(a.ne, 8), NT, smem, s>>>(a);
+    k_fused_B<T, P, NT, 0, AA, SURF, CURV><<<grid_elems(a.ne, 8), NT, smem, s>>>(a);
 }
 
 // Tensor-core form of the volume kernel (FP32, 128 threads, persistent: at most as many CTAs as
@@ -1632,6 +1665,10 @@ static int fused_phase(int phase, const HexArgs<T> &a, cudaStream_t s, int varia
                 if (r) return r;
                 return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
             }
+        }
+        if (a.mu) {   // curved elements: per-point metric terms (one launch shape)
+            launch_B<T, P, 128, true, false, true>(a, s);
+            return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
         }
         // launch shape chosen by the autotuner: 64, 128 or 256 threads per element
         if (a.surf) {

@@ -751,10 +751,11 @@ def test_tet_full_size_sampled_against_oracle():
 @pytest.mark.parametrize("N,amp", [(3, 0.15), (4, 0.1)])
 @pytest.mark.parametrize("p", [3, 4])
 @pytest.mark.parametrize("pref", [0.0, 1.0])
-def test_curved_rhs_fp64_matches_oracle(N, amp, p, pref):
+@pytest.mark.parametrize("form", ["fused", "unfused"])
+def test_curved_rhs_fp64_matches_oracle(N, amp, p, pref, form):
     """Non-affine hexahedra (the periodic box with sinusoidally displaced vertices): J^-T at every
-    solution point, det J J^-1 at every quadrature point, n_s at every flux point; the unfused form
-    against the oracle, FP64, 1e-12."""
+    solution point, det J J^-1 at every quadrature point, n_s at every flux point, det J at every
+    solution point for the final scaling; both forms against the oracle, FP64, 1e-12."""
     mesh = W.curved_box_mesh(N, amp=amp)
     nu = (p + 1) ** 3
     p_ref = pref * W.tgv_p0()
@@ -763,24 +764,19 @@ def test_curved_rhs_fp64_matches_oracle(N, amp, p, pref):
     Ro = o.rhs(U)
     m = fr.FRMesh(mesh, fr.make_params(p=p, p_ref=p_ref))
     assert np.abs(m.sol_coords() - o.sol_coords()).max() < 1e-13
-    m.set_form("unfused")
+    m.set_form(form)
     Ud = torch.from_numpy(U).cuda()
     Rd = torch.empty_like(Ud)
     m.rhs(Ud, Rd)
     m.sync_status()
     err = rel_linf(Rd.cpu().numpy(), Ro, nu)
-    print(f"curved N={N} p={p} pref={pref}: {err}")
+    print(f"curved {form} N={N} p={p} pref={pref}: {err}")
     assert err.max() <= 1e-12, err
-    # the fused kernels assume an element-constant metric: they refuse curved meshes
-    m.set_form("fused")
-    with pytest.raises(fr.FRError) as e:
-        m.rhs(Ud, Rd)
-    assert e.value.status == fr.FR_EUNSUPPORTED
 
 
 def test_curved_rk4_diagnostics_and_fp32():
-    """RK4 (unfused, graph-replayed) and the diagnostics (weights W det J at each solution point) on
-    the curved 4^3 box against the oracle; the FP32 unfused form against the oracle on the
+    """RK4 (both forms) and the diagnostics (weights W det J at each solution point) on the curved
+    4^3 box against the oracle; the plain FP32 form (both forms) against the oracle on the
     FP32-rounded input."""
     mesh = W.curved_box_mesh(4)
     p0 = W.tgv_p0()
@@ -802,12 +798,26 @@ def test_curved_rk4_diagnostics_and_fp32():
     assert dr <= 1e-13, dr
     U32 = U.astype(np.float32)
     Ro = o.rhs(U32.astype(np.float64))
-    m32 = fr.FRMesh(mesh, fr.make_params(p=3, prec="fp32", p_ref=p0))
-    m32.set_form("unfused")
-    Ud = torch.from_numpy(U32).cuda()
-    Rd = torch.empty_like(Ud)
-    m32.rhs(Ud, Rd)
-    m32.sync_status()
-    err = rel_linf(Rd.cpu().numpy().astype(np.float64), Ro, 64)
-    print(f"curved fp32: {err}")
-    assert err.max() <= 1e-3, err
+    for form in ("unfused", "fused"):
+        m32 = fr.FRMesh(mesh, fr.make_params(p=3, prec="fp32", p_ref=p0))
+        m32.set_form(form)
+        Ud = torch.from_numpy(U32).cuda()
+        Rd = torch.empty_like(Ud)
+        m32.rhs(Ud, Rd)
+        m32.sync_status()
+        err = rel_linf(Rd.cpu().numpy().astype(np.float64), Ro, 64)
+        print(f"curved fp32 {form}: {err}")
+        assert err.max() <= 5e-5, err
+    # the low-Mach FP32 form is not built for curved elements
+    m32 = fr.FRMesh(mesh, fr.make_params(p=3, prec="fp32", p_ref=p0, rho_ref=1.0))
+    with pytest.raises(fr.FRError) as e:
+        m32.rhs(Ud, Rd)
+    assert e.value.status == fr.FR_EUNSUPPORTED
+    # the fused RK4 (graph-replayed, stage update folded into the interface kernel)
+    m = fr.FRMesh(mesh, fr.make_params(p=3, p_ref=p0))
+    Ud = torch.from_numpy(U).cuda()
+    m.rk4_step(Ud, 1e-3, 5)
+    m.sync_status()
+    dr = np.abs(Ud.cpu().numpy() - Uo).max() / np.abs(Uo).max()
+    print(f"curved fused RK4: {dr:.3e}")
+    assert dr <= 1e-13, dr
