@@ -1058,7 +1058,7 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
 // ---------------------------------------------------------------------------------------------
 // Fused phase C: comm_flux + tdivtconf + negdivconf per element
 // ---------------------------------------------------------------------------------------------
-template <typename T, int P, int NT>
+template <typename T, int P, int NT, bool CURV = false>
 __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
 {
     constexpr int N = P + 1, NU = N * N * N, NF = 6 * N * N;
@@ -1083,7 +1083,7 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
 #pragma unroll
             for (int k = 0; k < 4; k++) { fvo[k] = a.FV[k * a.nfpt + og]; fvp[k] = a.FV[k * a.nfpt + pg]; }
             T n[3], mag;
-            if (a.mfn) {   // curved elements: the normal at this flux point
+            if constexpr (CURV) {   // curved elements: the normal at this flux point
                 const T *t = a.mfn + (e * NF + s) * 4;
                 n[0] = t[0]; n[1] = t[1]; n[2] = t[2]; mag = t[3];
             } else {
@@ -1126,7 +1126,7 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
                 v += op.liftL[j] * D[2 * N * N + i + N * k] + op.liftR[j] * D[3 * N * N + i + N * k];
                 v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
                 // curved elements: det J at this solution point
-                const T sc = a.mu ? T(-1) / a.mu[(e * NU + z) * 10 + 9] : idet;
+                const T sc = CURV ? T(-1) / a.mu[(e * NU + z) * 10 + 9] : idet;
                 if (a.rkstage == 0) R[it] = v * sc;
                 else rk_fold(a, elem_u0(a, e, NU) + it, v * sc);
             }
@@ -1259,7 +1259,7 @@ __global__ void __launch_bounds__(NT) k_surf_lift(HexArgs<T> a)
 // ---------------------------------------------------------------------------------------------
 // Split interface phase: C1 common flux once per pair, C2 lift
 // ---------------------------------------------------------------------------------------------
-template <typename T, int P>
+template <typename T, int P, bool CURV = false>
 __global__ void __launch_bounds__(128) k_pair_flux(HexArgs<T> a)
 {
     constexpr int N = P + 1, NF = 6 * N * N;
@@ -1277,7 +1277,7 @@ __global__ void __launch_bounds__(128) k_pair_flux(HexArgs<T> a)
 #pragma unroll
         for (int k = 0; k < 4; k++) { fvL[k] = a.FV[k * a.nfpt + gl]; fvR[k] = a.FV[k * a.nfpt + gr]; }
         T n[3], mag;
-        if (a.mfn) {   // curved elements: the normal at this flux point
+        if constexpr (CURV) {   // curved elements: the normal at this flux point
             const T *t = a.mfn + (e * NF + s) * 4;
             n[0] = t[0]; n[1] = t[1]; n[2] = t[2]; mag = t[3];
         } else {
@@ -1291,7 +1291,7 @@ __global__ void __launch_bounds__(128) k_pair_flux(HexArgs<T> a)
     flag_status(a.status, ok);
 }
 
-template <typename T, int P, int NT>
+template <typename T, int P, int NT, bool CURV = false>
 __global__ void __launch_bounds__(NT) k_lift(HexArgs<T> a)
 {
     constexpr int N = P + 1, NU = N * N * N, NF = 6 * N * N;
@@ -1304,7 +1304,7 @@ __global__ void __launch_bounds__(NT) k_lift(HexArgs<T> a)
             const uint32_t pc = a.partner[gf0 + s];
             const bool isL = (pc & FR_LFLAG) != 0;
             const long long src = isL ? gf0 + s : (long long)(pc & ~FR_LFLAG);
-            const T mag = a.mfn ? a.mfn[(e * NF + s) * 4 + 3] : a.fnrm[(e * 6 + s / (N * N)) * 4 + 3];
+            const T mag = CURV ? a.mfn[(e * NF + s) * 4 + 3] : a.fnrm[(e * 6 + s / (N * N)) * 4 + 3];
             const T sc = isL ? mag : -mag;
 #pragma unroll
             for (int k = 0; k < 5; k++) s_d[k * NF + s] = sc * a.DF[k * a.nfpt + src];
@@ -1320,7 +1320,7 @@ __global__ void __launch_bounds__(NT) k_lift(HexArgs<T> a)
             v += op.liftL[j] * D[2 * N * N + i + N * k] + op.liftR[j] * D[3 * N * N + i + N * k];
             v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
             // curved elements: det J at this solution point
-            const T sc = a.mu ? T(-1) / a.mu[(e * NU + z) * 10 + 9] : idet;
+            const T sc = CURV ? T(-1) / a.mu[(e * NU + z) * 10 + 9] : idet;
             if (a.rkstage == 0) R[it] = v * sc;
             else rk_fold(a, elem_u0(a, e, NU) + it, v * sc);
         }
@@ -1687,12 +1687,15 @@ static int fused_phase(int phase, const HexArgs<T> &a, cudaStream_t s, int varia
         else if (variant == 2) launch_B<T, P, 256>(a, s);
         else launch_B<T, P, 128>(a, s);
     } else if (phase == 2) {
-        k_fused_C<T, P, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
+        if (a.mu) k_fused_C<T, P, 128, true><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
+        else k_fused_C<T, P, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
     } else if (phase == 3) {
         if (a.surf) { if (a.nqlpts > 0) k_surf_pair<T, P><<<grid_for(a.nqlpts, 128), 128, 0, s>>>(a); }
+        else if (a.nlpts > 0 && a.mu) k_pair_flux<T, P, true><<<grid_for(a.nlpts, 128), 128, 0, s>>>(a);
         else if (a.nlpts > 0) k_pair_flux<T, P><<<grid_for(a.nlpts, 128), 128, 0, s>>>(a);
     } else {
         if (a.surf) k_surf_lift<T, P, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
+        else if (a.mu) k_lift<T, P, 128, true><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
         else k_lift<T, P, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
     }
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
