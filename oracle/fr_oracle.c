@@ -4,7 +4,7 @@
  * A plain, slow, FP64 reference ("the oracle") for one right-hand-side (RHS) evaluation of the
  * flux-reconstruction (FR) discretisation of the compressible Navier-Stokes equations with flux
  * anti-aliasing (over-integration of the flux at element quadrature points), on affine or trilinear
- * hexahedra, affine prisms and affine tetrahedra, plus the classical RK4 step around it.
+ * hexahedra, affine prisms, tetrahedra and pyramids, plus the classical RK4 step around it.
  *
  * Only the test-suite, the package smoke check and the CPU-baseline leg of the benchmark may load
  * the library built from this file. It shares no code with the GPU library.
@@ -30,7 +30,8 @@
  *       matrix M and E = int_face l_zeta l^face_sigma dS (reference measure).
  *   R4  Rusanov: F = 1/2 n.(fe_L + fe_R) + 1/2 s (uL - uR), s = max(|vL.n|+cL, |vR.n|+cR).
  *   R5  the L side of a flux-point pair is the element with the smaller global index (hexes
- *       before prisms before tetrahedra); a self-pair takes the smaller local face number as L.
+ *       before prisms before tetrahedra before pyramids); a self-pair takes the smaller local face
+ *       number as L.
  *   R6  transformed common flux D = |n_s| F with n_s = detJ J^-T n~; each side uses its own |n_s|.
  *   R7  prism solution points: the paper's Williams-Shunn triangle points x GL points in z.
  *   R8  prism quadrature: collapsed (Duffy) k x k GL triangle rule x m GL points in z.
@@ -45,6 +46,18 @@
  *       appendix's data-movement table): the trilinear map of the 8 vertices; J^-T at each solution point for the gradient,
  *       det J J^-1 at each quadrature point for the flux, n_s = det J J^-T n~ at each flux point,
  *       R = -R~ / det J at each solution point. Prisms and tetrahedra stay affine.
+ *   P1  pyramids (named in Sec. 1; no space or points printed): the rational pyramid space spanned by
+ *       a^i b^j (1-c)^max(i,j) c^k in the collapsed coordinates (Q_p on the base, P_p on the
+ *       triangles, so it conforms with hexahedra and tetrahedra); solution points: the order-p
+ *       pyramid lattice shrunk by 4/5 towards the centroid; flux points: n x n GL points on the base,
+ *       the printed Williams-Shunn triangle points on the four triangles (so p = 2, 3).
+ *   P3  pyramid derivative: the space is not closed under differentiation (d/dx of a b (1-c) is
+ *       2b, outside it), so the derivative operator is the L2 projection of the exact derivative,
+ *       M^-1 int l_zeta d l_nu; with it the DG-equivalent scheme stays conservative (the nodal
+ *       derivative would not integrate to the boundary flux). On the polynomial spaces of the
+ *       other types the projection is the identity, so the nodal derivative is kept there.
+ *   P2  pyramid quadrature: collapsed m^3 rule (GL in a and b, the Gauss rule of (1-c)^2 in c),
+ *       exact to total degree 2m-1.
  *   T2  tetrahedron quadrature: collapsed m x m x m rule (GL in a, Gauss rules of the weights
  *       (1-b) and (1-c)^2 in b and c), exact to total degree 2m-1 -- with m = p + 2 the same
  *       degree 2p+3 that m GL points give per direction on the hexahedron.
@@ -287,6 +300,53 @@ int or_tri_solution_points(int p, double *xy)
     return -1;
 }
 
+/* Collapsed k x k x k rule on the reference pyramid (base [-1,1]^2 at z = -1, apex (0,0,1); reading
+ * P2): x = a(1-c)/2, y = b(1-c)/2, z = c with Jacobian (1-c)^2/4; a and b take the k-point GL rule,
+ * c the k-point Gauss rule of the weight (1-c)^2. A polynomial of total degree d in (x,y,z), and a
+ * product of two functions of the pyramid space of order <= d/2, are polynomials of degree <= d in
+ * each of a, b, c, so the rule is exact for d <= 2k-1. Index ia + k ib + k^2 ic. */
+int or_pyr_rule(int k, double *xyz, double *w)
+{
+    double ga[32], wa[32], gc[32], wc[32];
+    if (k < 1 || k > 16) return -1;
+    or_gauss_legendre(k, ga, wa);
+    if (or_gauss_jacobi(k, 2, gc, wc)) return -1;
+    for (int ic = 0; ic < k; ic++)
+        for (int ib = 0; ib < k; ib++)
+            for (int ia = 0; ia < k; ia++) {
+                int q = ia + k * ib + k * k * ic;
+                double c = gc[ic];
+                xyz[3 * q + 0] = 0.5 * ga[ia] * (1.0 - c);
+                xyz[3 * q + 1] = 0.5 * ga[ib] * (1.0 - c);
+                xyz[3 * q + 2] = c;
+                w[q] = wa[ia] * wa[ib] * wc[ic] / 4.0;
+            }
+    return 0;
+}
+
+/* Pyramid solution points (reading P1): the pyramid lattice of order p -- layer k = 0..p at
+ * z = -1 + 2k/p holds the (p+1-k)^2 points x, y = (1 - k/p)(-1 + 2i/(p-k)) (the apex for k = p) --
+ * shrunk by 4/5 towards the centroid (0, 0, -1/2), so every point is interior. Index order: i
+ * fastest (x), then j (y), then the layer k. Returns the count (p+1)(p+2)(2p+3)/6. */
+int or_pyr_solution_points(int p, double *xyz)
+{
+    const double s = 0.8;
+    int n = 0;
+    for (int k = 0; k <= p; k++) {
+        int m = p - k;
+        double z = -1.0 + 2.0 * k / p, h = 1.0 - (double)k / p;
+        for (int j = 0; j <= m; j++)
+            for (int i = 0; i <= m; i++) {
+                double X[3] = {m ? h * (-1.0 + 2.0 * i / m) : 0.0, m ? h * (-1.0 + 2.0 * j / m) : 0.0, z};
+                xyz[3 * n + 0] = s * X[0];
+                xyz[3 * n + 1] = s * X[1];
+                xyz[3 * n + 2] = -0.5 + s * (X[2] + 0.5);
+                n++;
+            }
+    }
+    return n;
+}
+
 /* ---------------------------------------------------------------------------------------------
  * Orthonormal modal bases (reading R11)
  * ------------------------------------------------------------------------------------------- */
@@ -422,11 +482,101 @@ static int tet_basis_init(tet_basis *tb, int p)
 
 static void tet_basis_free(tet_basis *tb) { free(tb->e); free(tb->c); }
 
+/* Orthonormal basis of the pyramid space of order p (reading P1): the span of the functions
+ * g_ijk = a^i b^j (1-c)^max(i,j) c^k, 0 <= i, j <= p, 0 <= k <= p - max(i,j), in the collapsed
+ * coordinates a = 2x/(1-z), b = 2y/(1-z), c = z -- rational in (x, y, z), with Q_p traces on the
+ * base and P_p traces on the triangular faces; (p+1)(p+2)(2p+3)/6 functions. Gram-Schmidt
+ * (modified, two passes) under the collapsed rule with p + 2 points per direction, exact for the
+ * products (degree <= 2p in each collapsed coordinate). */
+typedef struct {
+    int p, nt;
+    int *e;             /* [nt][3] exponents (i, j, k) */
+    double *c;          /* [nt][nt] coefficients over the generators */
+} pyr_basis;
+
+/* Generator g_ijk and its (x, y, z) gradient at X (interior: z < 1). */
+static void pyr_gen(const int *e, const double *X, double *g, double *dg)
+{
+    const double om = 1.0 - X[2], a = 2.0 * X[0] / om, b = 2.0 * X[1] / om, c = X[2];
+    const int i = e[0], j = e[1], k = e[2], mm = i > j ? i : j;
+    const double ai = ipow(a, i), bj = ipow(b, j), cm = ipow(om, mm), ck = ipow(c, k);
+    *g = ai * bj * cm * ck;
+    if (!dg) return;
+    const double ga = i ? i * ipow(a, i - 1) * bj * cm * ck : 0.0;
+    const double gb = j ? j * ai * ipow(b, j - 1) * cm * ck : 0.0;
+    double gc = 0.0;
+    if (mm) gc -= mm * ai * bj * ipow(om, mm - 1) * ck;
+    if (k) gc += ai * bj * cm * k * ipow(c, k - 1);
+    dg[0] = ga * 2.0 / om;
+    dg[1] = gb * 2.0 / om;
+    dg[2] = (ga * a + gb * b) / om + gc;
+}
+
+static void pyr_basis_eval(const pyr_basis *pb, const double *X, double *phi, double *dphi /* [3][nt] or NULL */)
+{
+    int nt = pb->nt;
+    double g[64], dg[3 * 64];
+    for (int k = 0; k < nt; k++) pyr_gen(pb->e + 3 * k, X, &g[k], dphi ? &dg[3 * k] : NULL);
+    for (int t = 0; t < nt; t++) {
+        double v = 0, d0 = 0, d1 = 0, d2 = 0;
+        for (int k = 0; k < nt; k++) {
+            double ck = pb->c[t * nt + k];
+            v += ck * g[k];
+            if (dphi) { d0 += ck * dg[3 * k]; d1 += ck * dg[3 * k + 1]; d2 += ck * dg[3 * k + 2]; }
+        }
+        phi[t] = v;
+        if (dphi) { dphi[t] = d0; dphi[nt + t] = d1; dphi[2 * nt + t] = d2; }
+    }
+}
+
+static int pyr_basis_init(pyr_basis *pb, int p)
+{
+    int nt = (p + 1) * (p + 2) * (2 * p + 3) / 6;
+    if (nt > 64) return -1;
+    pb->p = p; pb->nt = nt;
+    pb->e = (int *)malloc(3 * nt * sizeof(int));
+    pb->c = (double *)calloc((size_t)nt * nt, sizeof(double));
+    int n = 0;
+    for (int mm = 0; mm <= p; mm++)          /* graded by max(i,j), then k */
+        for (int k = 0; k <= p - mm; k++)
+            for (int j = 0; j <= mm; j++)
+                for (int i = 0; i <= mm; i++) {
+                    if ((i > j ? i : j) != mm) continue;
+                    pb->e[3 * n] = i; pb->e[3 * n + 1] = j; pb->e[3 * n + 2] = k;
+                    n++;
+                }
+    int kq = p + 2, nq = kq * kq * kq;
+    double *xyz = (double *)malloc(3 * nq * sizeof(double)), *w = (double *)malloc(nq * sizeof(double));
+    if (or_pyr_rule(kq, xyz, w)) { free(xyz); free(w); return -1; }
+    double *val = (double *)malloc((size_t)nt * nq * sizeof(double));
+    for (int t = 0; t < nt; t++) {
+        double *ct = pb->c + t * nt;
+        ct[t] = 1.0;
+        for (int q = 0; q < nq; q++) pyr_gen(pb->e + 3 * t, xyz + 3 * q, &val[t * nq + q], NULL);
+        for (int pass = 0; pass < 2; pass++)
+            for (int s2 = 0; s2 < t; s2++) {
+                double ip = 0;
+                for (int q = 0; q < nq; q++) ip += w[q] * val[t * nq + q] * val[s2 * nq + q];
+                for (int kk = 0; kk < nt; kk++) ct[kk] -= ip * pb->c[s2 * nt + kk];
+                for (int q = 0; q < nq; q++) val[t * nq + q] -= ip * val[s2 * nq + q];
+            }
+        double nrm = 0;
+        for (int q = 0; q < nq; q++) nrm += w[q] * val[t * nq + q] * val[t * nq + q];
+        nrm = sqrt(nrm);
+        for (int kk = 0; kk < nt; kk++) ct[kk] /= nrm;
+        for (int q = 0; q < nq; q++) val[t * nq + q] /= nrm;
+    }
+    free(xyz); free(w); free(val);
+    return 0;
+}
+
+static void pyr_basis_free(pyr_basis *pb) { free(pb->e); free(pb->c); }
+
 /* ---------------------------------------------------------------------------------------------
  * Element types and their dense operators
  * ------------------------------------------------------------------------------------------- */
 
-enum { ET_HEX = 0, ET_PRI = 1, ET_TET = 2, ET_COUNT = 3 };
+enum { ET_HEX = 0, ET_PRI = 1, ET_TET = 2, ET_PYR = 3, ET_COUNT = 4 };
 
 typedef struct {
     int kind;           /* 0 = quad, 1 = triangle */
@@ -453,6 +603,7 @@ typedef struct {
     double *Wu;             /* [nu] int l_zeta over the reference element */
     tri_basis tb;           /* prism and tetrahedron (their triangle faces) */
     tet_basis teb;          /* tetrahedron only */
+    pyr_basis pyb;          /* pyramid only */
     double g1[16], g1w[16]; /* 1D GL solution nodes */
     int nfn;                /* 1D nodes of the hex face point grids: n, or m with surface-flux AA */
     double fg[32];          /* their coordinates */
@@ -485,6 +636,8 @@ static void modal_eval(const etype_t *et, const double *X, double *psi, double *
                 }
     } else if (et->type == ET_TET) {
         tet_basis_eval(&et->teb, X, psi, dpsi);
+    } else if (et->type == ET_PYR) {
+        pyr_basis_eval(&et->pyb, X, psi, dpsi);
     } else {
         int nt = et->tb.nt;
         double phi[64], phx[64], phy[64];
@@ -515,6 +668,19 @@ static void face_map(const etype_t *et, int f, double s, double t, double *X)
         case 1: X[0] = s; X[1] = -1.0; X[2] = t; break;        /* y = -1 */
         case 2: X[0] = -1.0; X[1] = s; X[2] = t; break;        /* x = -1 */
         default: X[0] = -1.0 - s - t; X[1] = s; X[2] = t; break; /* x + y + z = -1 */
+        }
+    } else if (et->type == ET_PYR) {
+        /* base (s, t) = (x, y); a triangle of vertices P0, P1, P2 at barycentric
+         * ((-(s+t))/2, (1+s)/2, (1+t)/2) */
+        static const double tri[4][3][3] = {
+            {{-1, -1, -1}, {1, -1, -1}, {0, 0, 1}},    /* y = -(1-z)/2 */
+            {{1, -1, -1}, {1, 1, -1}, {0, 0, 1}},      /* x = (1-z)/2 */
+            {{1, 1, -1}, {-1, 1, -1}, {0, 0, 1}},      /* y = (1-z)/2 */
+            {{-1, 1, -1}, {-1, -1, -1}, {0, 0, 1}}};   /* x = -(1-z)/2 */
+        if (f == 0) { X[0] = s; X[1] = t; X[2] = -1.0; }
+        else {
+            const double l0 = -0.5 * (s + t), l1 = 0.5 * (1.0 + s), l2 = 0.5 * (1.0 + t);
+            for (int d = 0; d < 3; d++) X[d] = l0 * tri[f - 1][0][d] + l1 * tri[f - 1][1][d] + l2 * tri[f - 1][2][d];
         }
     } else {
         switch (f) {
@@ -564,6 +730,19 @@ static int etype_init(etype_t *et, int type, int p, int m, int tri_k, int surf)
             memset(et->faces[f].nref, 0, sizeof(double) * 3);
             et->faces[f].nref[f / 2] = (f % 2) ? 1.0 : -1.0;
         }
+    } else if (type == ET_PYR) {
+        /* reading P1: p = 2, 3 (the triangular faces carry the printed triangle points) */
+        nt = or_tri_solution_points(p, txy);
+        if (nt < 0) return -1;
+        tri_basis_init(&et->tb, p);
+        if (pyr_basis_init(&et->pyb, p)) return -1;
+        et->nu = (p + 1) * (p + 2) * (2 * p + 3) / 6; et->nmodes = et->nu; et->nfaces = 5;
+        et->nq = m * m * m;
+        double r5 = 1.0 / sqrt(5.0), dst = 0.5 * sqrt(5.0);
+        face_info fi[5] = {
+            {0, et->nfn * et->nfn, {0, 0, -1}, 1.0}, {1, nt, {0, -2 * r5, r5}, dst}, {1, nt, {2 * r5, 0, r5}, dst},
+            {1, nt, {0, 2 * r5, r5}, dst}, {1, nt, {-2 * r5, 0, r5}, dst}};
+        for (int f = 0; f < 5; f++) et->faces[f] = fi[f];
     } else if (type == ET_TET) {
         /* reading T1: p = 2, 3 (the faces carry the printed triangle points) */
         nt = or_tri_solution_points(p, txy);
@@ -614,6 +793,8 @@ static int etype_init(etype_t *et, int type, int p, int m, int tri_k, int surf)
                 }
     } else if (type == ET_TET) {
         or_tet_solution_points(p, et->xu);
+    } else if (type == ET_PYR) {
+        or_pyr_solution_points(p, et->xu);
     } else {
         for (int k = 0; k < n1; k++)
             for (int t = 0; t < nt; t++) {
@@ -648,6 +829,9 @@ static int etype_init(etype_t *et, int type, int p, int m, int tri_k, int surf)
     } else if (type == ET_TET) {
         /* reading T2: collapsed Gauss rules, m points per direction */
         if (or_tet_rule(m, et->xq, et->wq)) return -1;
+    } else if (type == ET_PYR) {
+        /* reading P2: collapsed Gauss rules, m points per direction */
+        if (or_pyr_rule(m, et->xq, et->wq)) return -1;
     } else {
         int nt2 = tri_k * tri_k;
         double *txq = (double *)malloc(2 * nt2 * sizeof(double)), *twq = (double *)malloc(nt2 * sizeof(double));
@@ -698,6 +882,41 @@ static int etype_init(etype_t *et, int type, int p, int m, int tri_k, int surf)
                 for (int k = 0; k < nm; k++) v += dpsi[d * nm + k] * Vinv[k * nu + z];
                 et->Dm[(d * nu + zp) * nu + z] = v;
             }
+    }
+    /* Pyramid (reading P3): the rational space is not closed under differentiation, so the
+     * derivative operator is the L2 projection of the exact derivative onto the space,
+     * D_d = M^-1 S_d with S_d[zeta][nu] = int l_zeta d_d l_nu (the collapsed rule is exact for these
+     * products). On the polynomial spaces of the other types this equals the nodal derivative. */
+    if (type == ET_PYR) {
+        double *S = (double *)calloc((size_t)3 * nu * nu, sizeof(double));
+        double *lq = (double *)malloc(nu * sizeof(double)), *dlq = (double *)malloc(3 * nu * sizeof(double));
+        for (int q = 0; q < nq; q++) {
+            modal_eval(et, et->xq + 3 * q, psi, dpsi);
+            for (int z = 0; z < nu; z++) {
+                double v = 0, g[3] = {0, 0, 0};
+                for (int k = 0; k < nm; k++) {
+                    v += psi[k] * Vinv[k * nu + z];
+                    for (int d = 0; d < 3; d++) g[d] += dpsi[d * nm + k] * Vinv[k * nu + z];
+                }
+                lq[z] = v;
+                for (int d = 0; d < 3; d++) dlq[d * nu + z] = g[d];
+            }
+            for (int d = 0; d < 3; d++)
+                for (int z = 0; z < nu; z++)
+                    for (int j = 0; j < nu; j++) S[(d * nu + z) * nu + j] += et->wq[q] * lq[z] * dlq[d * nu + j];
+        }
+        for (int d = 0; d < 3; d++)
+            for (int z = 0; z < nu; z++)
+                for (int j = 0; j < nu; j++) {
+                    double v = 0;
+                    for (int zp = 0; zp < nu; zp++) {
+                        double minv = 0;
+                        for (int k = 0; k < nm; k++) minv += V[z * nm + k] * V[zp * nm + k];
+                        v += minv * S[(d * nu + zp) * nu + j];
+                    }
+                    et->Dm[(d * nu + z) * nu + j] = v;
+                }
+        free(S); free(lq); free(dlq);
     }
     /* M7 (uqpts) and M8 (L2 projection, reading G4 for its shape) */
     double *PQ = (double *)malloc((size_t)nq * nm * sizeof(double));
@@ -806,6 +1025,7 @@ static void etype_free(etype_t *et)
     free(et->Agrad); free(et->Adiv); free(et->Wu);
     if (et->type != ET_HEX) tri_basis_free(&et->tb);
     if (et->type == ET_TET) tet_basis_free(&et->teb);
+    if (et->type == ET_PYR) pyr_basis_free(&et->pyb);
 }
 
 /* ---------------------------------------------------------------------------------------------
@@ -821,7 +1041,7 @@ typedef struct {
     phys_params ph;
     etype_t et[ET_COUNT];
     int has[ET_COUNT];
-    int n_hex, n_pri, n_tet, ne;
+    int n_hex, n_pri, n_tet, n_pyr, ne;
     double period[3];
     double *x0;     /* [ne][3] reference origin: x = x0 + J (xi + 1) */
     double *J;      /* [ne][9] row-major dx_i/dxi_j */
@@ -842,7 +1062,10 @@ typedef struct {
 } oracle_t;
 
 /* Element order: hexahedra, then prisms, then tetrahedra. */
-static int etype_of(const oracle_t *o, int e) { return e < o->n_hex ? ET_HEX : (e < o->n_hex + o->n_pri ? ET_PRI : ET_TET); }
+static int etype_of(const oracle_t *o, int e)
+{
+    return e < o->n_hex ? ET_HEX : (e < o->n_hex + o->n_pri ? ET_PRI : (e < o->n_hex + o->n_pri + o->n_tet ? ET_TET : ET_PYR));
+}
 static const etype_t *ET(const oracle_t *o, int e) { return &o->et[etype_of(o, e)]; }
 
 static double pdist(const oracle_t *o, const double *a, const double *b)
@@ -936,16 +1159,16 @@ static int facekey_cmp(const void *a, const void *b)
     return ((const or_facekey *)a)->face - ((const or_facekey *)b)->face;
 }
 
-void *or_create3(int p, int m, int tri_k, int surf, double gamma, double Pr, double mu, double beta, double tau,
-                 double p_ref, int n_hex, int n_pri, int n_tet, int n_verts, const double *verts, const int *hex_v,
-                 const int *pri_v, const int *tet_v, const double *period, int *err);
+void *or_create4(int p, int m, int tri_k, int surf, double gamma, double Pr, double mu, double beta, double tau,
+                 double p_ref, int n_hex, int n_pri, int n_tet, int n_pyr, int n_verts, const double *verts,
+                 const int *hex_v, const int *pri_v, const int *tet_v, const int *pyr_v, const double *period, int *err);
 
 void *or_create(int p, int m, int tri_k, double gamma, double Pr, double mu, double beta, double tau, double p_ref,
                 int n_hex, int n_pri, int n_verts, const double *verts, const int *hex_v, const int *pri_v,
                 const double *period, int *err)
 {
-    return or_create3(p, m, tri_k, 0, gamma, Pr, mu, beta, tau, p_ref, n_hex, n_pri, 0, n_verts, verts, hex_v, pri_v,
-                      NULL, period, err);
+    return or_create4(p, m, tri_k, 0, gamma, Pr, mu, beta, tau, p_ref, n_hex, n_pri, 0, 0, n_verts, verts, hex_v, pri_v,
+                      NULL, NULL, period, err);
 }
 
 /* As or_create; surf = 1 selects surface-flux anti-aliasing (hexahedra only): the flux points of
@@ -954,8 +1177,8 @@ void *or_create2(int p, int m, int tri_k, int surf, double gamma, double Pr, dou
                  double p_ref, int n_hex, int n_pri, int n_verts, const double *verts, const int *hex_v,
                  const int *pri_v, const double *period, int *err)
 {
-    return or_create3(p, m, tri_k, surf, gamma, Pr, mu, beta, tau, p_ref, n_hex, n_pri, 0, n_verts, verts, hex_v,
-                      pri_v, NULL, period, err);
+    return or_create4(p, m, tri_k, surf, gamma, Pr, mu, beta, tau, p_ref, n_hex, n_pri, 0, 0, n_verts, verts, hex_v,
+                      pri_v, NULL, NULL, period, err);
 }
 
 /* As or_create2, with n_tet tetrahedra (4 vertices each, tet_v) after the prisms. */
@@ -963,14 +1186,28 @@ void *or_create3(int p, int m, int tri_k, int surf, double gamma, double Pr, dou
                  double p_ref, int n_hex, int n_pri, int n_tet, int n_verts, const double *verts, const int *hex_v,
                  const int *pri_v, const int *tet_v, const double *period, int *err)
 {
+    return or_create4(p, m, tri_k, surf, gamma, Pr, mu, beta, tau, p_ref, n_hex, n_pri, n_tet, 0, n_verts, verts,
+                      hex_v, pri_v, tet_v, NULL, period, err);
+}
+
+/* As or_create3, with n_pyr pyramids (5 vertices each, pyr_v: the base corners in tensor order --
+ * reference (-1,-1,-1), (1,-1,-1), (-1,1,-1), (1,1,-1) -- then the apex, reference (0,0,1)) after the
+ * tetrahedra. */
+void *or_create4(int p, int m, int tri_k, int surf, double gamma, double Pr, double mu, double beta, double tau,
+                 double p_ref, int n_hex, int n_pri, int n_tet, int n_pyr, int n_verts, const double *verts,
+                 const int *hex_v, const int *pri_v, const int *tet_v, const int *pyr_v, const double *period, int *err)
+{
     *err = OR_OK;
-    if (p < 1 || m < 1 || n_hex < 0 || n_pri < 0 || n_tet < 0 || n_hex + n_pri + n_tet == 0) { *err = OR_EINVAL; return NULL; }
+    if (p < 1 || m < 1 || n_hex < 0 || n_pri < 0 || n_tet < 0 || n_pyr < 0 || n_hex + n_pri + n_tet + n_pyr == 0) {
+        *err = OR_EINVAL;
+        return NULL;
+    }
     oracle_t *o = (oracle_t *)calloc(1, sizeof(oracle_t));
     o->ph.gamma = gamma; o->ph.Pr = Pr; o->ph.mu = mu; o->ph.beta = beta; o->ph.tau = tau; o->ph.p_ref = p_ref;
-    o->n_hex = n_hex; o->n_pri = n_pri; o->n_tet = n_tet; o->ne = n_hex + n_pri + n_tet;
+    o->n_hex = n_hex; o->n_pri = n_pri; o->n_tet = n_tet; o->n_pyr = n_pyr; o->ne = n_hex + n_pri + n_tet + n_pyr;
     for (int d = 0; d < 3; d++) o->period[d] = period ? period[d] : 0.0;
     o->nthreads = 1;
-    const int counts[ET_COUNT] = {n_hex, n_pri, n_tet};
+    const int counts[ET_COUNT] = {n_hex, n_pri, n_tet, n_pyr};
     for (int t = 0; t < ET_COUNT; t++) {
         if (counts[t] == 0) continue;
         if (etype_init(&o->et[t], t, p, m, tri_k, surf)) { *err = OR_EUNSUPPORTED; or_destroy(o); return NULL; }
@@ -994,9 +1231,12 @@ void *or_create3(int p, int m, int tri_k, int surf, double gamma, double Pr, dou
         /* affine map from vertices; reject non-affine or inverted elements */
         const double *v[8];
         const int typ = etype_of(o, e);
-        int nv = typ == ET_HEX ? 8 : (typ == ET_PRI ? 6 : 4);
+        int nv = typ == ET_HEX ? 8 : (typ == ET_PRI ? 6 : (typ == ET_TET ? 4 : 5));
         for (int k = 0; k < nv; k++) {
-            int vi = typ == ET_HEX ? hex_v[8 * e + k] : (typ == ET_PRI ? pri_v[6 * (e - n_hex) + k] : tet_v[4 * (e - n_hex - n_pri) + k]);
+            int vi = typ == ET_HEX ? hex_v[8 * e + k]
+                     : typ == ET_PRI ? pri_v[6 * (e - n_hex) + k]
+                     : typ == ET_TET ? tet_v[4 * (e - n_hex - n_pri) + k]
+                                     : pyr_v[5 * (e - n_hex - n_pri - n_tet) + k];
             if (vi < 0 || vi >= n_verts) { *err = OR_EMESH; or_destroy(o); return NULL; }
             v[k] = verts + 3 * vi;
         }
@@ -1006,8 +1246,10 @@ void *or_create3(int p, int m, int tri_k, int surf, double gamma, double Pr, dou
             o->x0[3 * e + i] = v[0][i];
             o->J[9 * e + 3 * i + 0] = 0.5 * (v[c1][i] - v[0][i]);
             o->J[9 * e + 3 * i + 1] = 0.5 * (v[c2][i] - v[0][i]);
-            o->J[9 * e + 3 * i + 2] = 0.5 * (v[c3][i] - v[0][i]);
-            scale += fabs(v[c1][i] - v[0][i]) + fabs(v[c2][i] - v[0][i]) + fabs(v[c3][i] - v[0][i]);
+            /* pyramid: the apex (0,0,1) = corner (-1,-1,-1) + (1,1,2) */
+            o->J[9 * e + 3 * i + 2] = typ == ET_PYR ? 0.5 * (v[4][i] - v[0][i]) - 0.25 * (v[c1][i] - v[0][i]) - 0.25 * (v[c2][i] - v[0][i])
+                                                    : 0.5 * (v[c3][i] - v[0][i]);
+            scale += fabs(v[c1][i] - v[0][i]) + fabs(v[c2][i] - v[0][i]) + fabs(v[typ == ET_PYR ? 4 : c3][i] - v[0][i]);
         }
         if (typ == ET_HEX)
             for (int k = 0; k < 8; k++)
@@ -1017,7 +1259,10 @@ void *or_create3(int p, int m, int tri_k, int surf, double gamma, double Pr, dou
         for (int k = 0; k < nv; k++) {
             double X[3];
             if (e < n_hex) { X[0] = (k & 1) ? 1 : -1; X[1] = (k & 2) ? 1 : -1; X[2] = (k & 4) ? 1 : -1; }
-            else {
+            else if (typ == ET_PYR) {
+                static const double pp[5][3] = {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {1, 1, -1}, {0, 0, 1}};
+                X[0] = pp[k][0]; X[1] = pp[k][1]; X[2] = pp[k][2];
+            } else {
                 static const double pc[6][3] = {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}, {1, -1, 1}, {-1, 1, 1}};
                 X[0] = pc[k][0]; X[1] = pc[k][1]; X[2] = pc[k][2];
             }
@@ -1071,6 +1316,11 @@ void *or_create3(int p, int m, int tri_k, int surf, double gamma, double Pr, dou
                     double t3 = -1.0 / 3.0;
                     Xc[0] = Xc[1] = Xc[2] = t3;
                     if (f < 3) Xc[2 - f] = -1.0;
+                }
+                else if (et->type == ET_PYR) {
+                    /* base: its centre; a triangle: the image of the reference triangle's centroid */
+                    if (f == 0) face_map(et, 0, 0.0, 0.0, Xc);
+                    else face_map(et, f, -1.0 / 3.0, -1.0 / 3.0, Xc);
                 }
                 else if (f < 2) { Xc[0] = Xc[1] = -1.0 / 3.0; Xc[2] = f ? 1.0 : -1.0; }
                 else if (f == 2) { Xc[0] = 0.0; Xc[1] = -1.0; Xc[2] = 0.0; }

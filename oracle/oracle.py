@@ -38,6 +38,13 @@ def lib():
         L.or_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
                                 C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, dp, C.POINTER(C.c_int),
                                 C.POINTER(C.c_int), dp, C.POINTER(C.c_int)]
+        L.or_create4.restype = C.c_void_p
+        L.or_create4.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                                 C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, dp,
+                                 C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), dp,
+                                 C.POINTER(C.c_int)]
+        L.or_pyr_rule.argtypes = [C.c_int, dp, dp]
+        L.or_pyr_solution_points.argtypes = [C.c_int, dp]
         L.or_create3.restype = C.c_void_p
         L.or_create3.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
                                  C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, dp, C.POINTER(C.c_int),
@@ -109,6 +116,19 @@ def tet_solution_points(p):
     return xyz
 
 
+def pyr_rule(k):
+    xyz = np.zeros((k ** 3, 3)); w = np.zeros(k ** 3)
+    if lib().or_pyr_rule(k, _dp(xyz), _dp(w)) != 0:
+        raise ValueError("pyramid rule construction failed")
+    return xyz, w
+
+
+def pyr_solution_points(p):
+    xyz = np.zeros(((p + 1) * (p + 2) * (2 * p + 3) // 6, 3))
+    lib().or_pyr_solution_points(p, _dp(xyz))
+    return xyz
+
+
 def tri_solution_points(p):
     xy = np.zeros((64, 2))
     n = lib().or_tri_solution_points(p, _dp(xy))
@@ -139,15 +159,17 @@ class Oracle:
         hex_v = np.ascontiguousarray(mesh.get("hex_v", np.zeros((0, 8))), dtype=np.int32)
         pri_v = np.ascontiguousarray(mesh.get("pri_v", np.zeros((0, 6))), dtype=np.int32)
         tet_v = np.ascontiguousarray(mesh.get("tet_v", np.zeros((0, 4))), dtype=np.int32)
+        pyr_v = np.ascontiguousarray(mesh.get("pyr_v", np.zeros((0, 5))), dtype=np.int32)
         period = np.ascontiguousarray(mesh.get("period", (0.0, 0.0, 0.0)), dtype=np.float64)
         err = C.c_int(0)
         ip = C.POINTER(C.c_int)
-        self.h = L.or_create3(p, m, tri_k, int(bool(surf)), gamma, Pr, mu, beta, tau, p_ref, hex_v.shape[0],
-                              pri_v.shape[0], tet_v.shape[0], verts.shape[0], _dp(verts), hex_v.ctypes.data_as(ip),
-                              pri_v.ctypes.data_as(ip), tet_v.ctypes.data_as(ip), _dp(period), C.byref(err))
+        self.h = L.or_create4(p, m, tri_k, int(bool(surf)), gamma, Pr, mu, beta, tau, p_ref, hex_v.shape[0],
+                              pri_v.shape[0], tet_v.shape[0], pyr_v.shape[0], verts.shape[0], _dp(verts),
+                              hex_v.ctypes.data_as(ip), pri_v.ctypes.data_as(ip), tet_v.ctypes.data_as(ip),
+                              pyr_v.ctypes.data_as(ip), _dp(period), C.byref(err))
         if not self.h:
             raise RuntimeError(f"oracle mesh creation failed with status {err.value}")
-        self.n_hex, self.n_pri, self.n_tet = hex_v.shape[0], pri_v.shape[0], tet_v.shape[0]
+        self.n_hex, self.n_pri, self.n_tet, self.n_pyr = hex_v.shape[0], pri_v.shape[0], tet_v.shape[0], pyr_v.shape[0]
         self.p, self.m = p, m
         self.nU = L.or_num_values(self.h)
         self.nF = L.or_num_fvalues(self.h)

@@ -225,3 +225,53 @@ def curved_box_mesh(N: int, amp: float = 0.1, length: float = 2 * math.pi, origi
     hex_v = np.stack([vid(ex + (c & 1), ey + ((c >> 1) & 1), ez + ((c >> 2) & 1)) for c in range(8)], axis=1)
     return dict(verts=verts, hex_v=hex_v.astype(np.int32), pri_v=np.zeros((0, 6), np.int32),
                 period=(length, length, length))
+
+
+def box_pyr_mesh(N: int, hex_below: int = 0, length: float = 2 * math.pi, origin: float = -math.pi):
+    """N^3 periodic box of cells; cells with x index < hex_below are hexahedra, every other cell is
+    split into six pyramids, one per cell face, with the face as base and the cell centre as apex
+    (its triangular faces meet the neighbouring pyramids of the same cell; its base meets the next
+    cell's face, a hexahedron's or another pyramid's base). Pyramid vertex order: the base corners in
+    tensor order (reference (-1,-1,-1), (1,-1,-1), (-1,1,-1), (1,1,-1)), then the apex (0,0,1)."""
+    g = origin + length * np.arange(N + 1) / N
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    verts = [np.stack([X.ravel(order="F"), Y.ravel(order="F"), Z.ravel(order="F")], axis=1)]
+    nv0 = (N + 1) ** 3
+    vid = lambda i, j, k: i + (N + 1) * (j + (N + 1) * k)  # noqa: E731
+    h = length / N
+    hexes, pyrs, centres = [], [], []
+    for ez in range(N):
+        for ey in range(N):
+            for ex in range(N):
+                c = [vid(ex + (q & 1), ey + ((q >> 1) & 1), ez + ((q >> 2) & 1)) for q in range(8)]
+                if ex < hex_below:
+                    hexes.append(c)
+                    continue
+                ci = nv0 + len(centres)
+                centres.append([origin + (ex + 0.5) * h, origin + (ey + 0.5) * h, origin + (ez + 0.5) * h])
+                for d in range(3):
+                    t1, t2 = [t for t in range(3) if t != d]
+                    for side in (0, 1):
+                        base = []
+                        for b in (0, 1):
+                            for a in (0, 1):
+                                q = (side << d) | (a << t1) | (b << t2)
+                                base.append(c[q])
+                        # orientation: the apex must lie on the +z side of the reference base
+                        if side == 1:
+                            base = [base[0], base[2], base[1], base[3]]
+                        pyrs.append(base + [ci])
+    verts.append(np.array(centres, dtype=np.float64).reshape(-1, 3))
+    verts = np.concatenate(verts)
+    # fix orientation by the sign of the affine map's determinant
+    P = np.array(pyrs, np.int64).reshape(-1, 5)
+    if P.shape[0]:
+        v = verts
+        J0 = 0.5 * (v[P[:, 1]] - v[P[:, 0]])
+        J1 = 0.5 * (v[P[:, 2]] - v[P[:, 0]])
+        J2 = 0.5 * (v[P[:, 4]] - v[P[:, 0]]) - 0.5 * (J0 + J1)
+        det = np.einsum("ij,ij->i", J0, np.cross(J1, J2))
+        neg = det < 0
+        P[neg] = P[neg][:, [0, 2, 1, 3, 4]]
+    return dict(verts=verts, hex_v=np.array(hexes, np.int32).reshape(-1, 8), pri_v=np.zeros((0, 6), np.int32),
+                tet_v=np.zeros((0, 4), np.int32), pyr_v=P.astype(np.int32), period=(length, length, length))

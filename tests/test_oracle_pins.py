@@ -33,6 +33,8 @@ def _layout(o, mesh):
         blocks.append((mesh["pri_v"].shape[0], o.dims(1)[0]))
     if mesh.get("tet_v", np.zeros((0, 4))).shape[0]:
         blocks.append((mesh["tet_v"].shape[0], o.dims(2)[0]))
+    if mesh.get("pyr_v", np.zeros((0, 5))).shape[0]:
+        blocks.append((mesh["pyr_v"].shape[0], o.dims(3)[0]))
     return blocks
 
 
@@ -70,6 +72,27 @@ def _random_space_poly(rng, p, etype):
             if a + b + cc > p:
                 c[a, b, cc] = 0
     return c
+
+
+class _SpaceFn:
+    """A random function of an element's solution space: a polynomial (coefficient array) on
+    hexahedra, prisms and tetrahedra; on pyramids a combination of the rational generators
+    a^i b^j (1-c)^max(i,j) c^k (a = 2x/(1-z), b = 2y/(1-z), c = z), evaluated directly."""
+
+    def __init__(self, rng, p, etype):
+        self.etype = etype
+        if etype == 3:
+            self.terms = [(i, j, k, rng.standard_normal()) for m in range(p + 1) for k in range(p + 1 - m)
+                          for j in range(m + 1) for i in range(m + 1) if max(i, j) == m]
+        else:
+            self.c = _random_space_poly(rng, p, etype)
+
+    def __call__(self, X):
+        if self.etype != 3:
+            return _eval_poly3(self.c, X)
+        om = 1.0 - X[:, 2]
+        a, b, c = 2 * X[:, 0] / om, 2 * X[:, 1] / om, X[:, 2]
+        return sum(v * a ** i * b ** j * om ** max(i, j) * c ** k for i, j, k, v in self.terms)
 
 
 # ----------------------------------------------------------------------------------------------
@@ -201,6 +224,55 @@ def test_tetrahedron_points_symmetric_interior_unisolvent(p):
     assert np.linalg.cond(V) < 1e4
 
 
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
+def test_collapsed_pyramid_rule_strength(k):
+    """Reading P2: the k^3 collapsed pyramid rule integrates x^a y^b z^c exactly for a+b+c <= 2k-1,
+    against int = 4/((a+1)(b+1)) int_{-1}^{1} z^c ((1-z)/2)^(a+b+2) dz for even a, b (zero otherwise),
+    the last integral by the binomial expansion; it fails at degree 2k."""
+    xyz, w = O.pyr_rule(k)
+    assert np.all(w > 0) and np.all(np.abs(xyz[:, :2]) < (1 - xyz[:, 2:3]) / 2) and abs(w.sum() - 8 / 3) < 1e-14
+
+    def exact(a, b, c):
+        if a % 2 or b % 2:
+            return 0.0
+        n = a + b + 2
+        zint = sum(math.comb(n, j) * (-1) ** j * (2.0 / (c + j + 1) if (c + j) % 2 == 0 else 0.0) for j in range(n + 1))
+        return 4.0 / ((a + 1) * (b + 1)) * zint / 2 ** n
+
+    for a in range(2 * k):
+        for b in range(2 * k - a):
+            for c in range(2 * k - a - b):
+                got = (w * xyz[:, 0] ** a * xyz[:, 1] ** b * xyz[:, 2] ** c).sum()
+                assert abs(got - exact(a, b, c)) < 1e-14, (a, b, c)
+    worst = max(abs((w * xyz[:, 2] ** (2 * k)).sum() - exact(0, 0, 2 * k)),
+                abs((w * xyz[:, 0] ** 2 * xyz[:, 2] ** (2 * k - 2)).sum() - exact(2, 0, 2 * k - 2)))
+    assert worst > 1e-12
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_pyramid_points_symmetric_interior_unisolvent(p):
+    """Reading P1: (p+1)(p+2)(2p+3)/6 interior points, invariant under the eight symmetries of the
+    square base, unisolvent for the rational pyramid space (its generators' Vandermonde matrix is
+    well conditioned)."""
+    x = O.pyr_solution_points(p)
+    n = (p + 1) * (p + 2) * (2 * p + 3) // 6
+    assert x.shape[0] == n
+    assert np.all(x[:, 2] > -1) and np.all(x[:, 2] < 1) and np.all(np.abs(x[:, :2]).max(axis=1) < (1 - x[:, 2]) / 2)
+    for sx, sy, swap in [(a, b, c) for a in (1, -1) for b in (1, -1) for c in (0, 1)]:
+        img = x.copy()
+        if swap:
+            img[:, [0, 1]] = img[:, [1, 0]]
+        img[:, 0] *= sx
+        img[:, 1] *= sy
+        d = np.abs(img[:, None, :] - x[None, :, :]).max(axis=2).min(axis=1)
+        assert d.max() < 1e-15
+    om = 1 - x[:, 2]
+    a, b, c = 2 * x[:, 0] / om, 2 * x[:, 1] / om, x[:, 2]
+    V = np.stack([a ** i * b ** j * om ** max(i, j) * c ** k for m in range(p + 1) for k in range(p + 1 - m)
+                  for j in range(m + 1) for i in range(m + 1) if max(i, j) == m], axis=1)
+    assert V.shape == (n, n) and np.linalg.cond(V) < 1e5
+
+
 # ----------------------------------------------------------------------------------------------
 # Element operators: exactness, projection, lift, sum factorisation
 # ----------------------------------------------------------------------------------------------
@@ -211,26 +283,32 @@ def _oracle_for(etype, p, m=None):
         return O.Oracle(W.box_hex_mesh(1), p, m)
     if etype == 2:
         return O.Oracle(W.box_tet_mesh(1), p, m)
+    if etype == 3:
+        return O.Oracle(W.box_pyr_mesh(1), p, m)
     return O.Oracle(W.mixed_box_mesh(2), p, m)
 
 
-CASES = [(0, 2), (0, 3), (0, 4), (1, 2), (1, 3), (2, 2), (2, 3)]
-VOLUME = {0: 8.0, 1: 4.0, 2: 4.0 / 3.0}
+CASES = [(0, 2), (0, 3), (0, 4), (1, 2), (1, 3), (2, 2), (2, 3), (3, 2), (3, 3)]
+VOLUME = {0: 8.0, 1: 4.0, 2: 4.0 / 3.0, 3: 8.0 / 3.0}
 
 
 @pytest.mark.parametrize("etype,p", CASES)
 def test_interpolation_and_derivative_exact_on_space(etype, p):
-    """Check (b): M0 (disu), M7 (uqpts) and the derivative matrices M4 = M1 reproduce every
-    polynomial of the solution space exactly (catches a transposed operator or a wrong point set)."""
+    """Check (b): M0 (disu) and M7 (uqpts) reproduce every function of the solution space exactly,
+    and the derivative matrices M4 = M1 every polynomial of it (on the pyramid, whose rational space
+    is not closed under differentiation, reading P3: the polynomials P_p, where the projected
+    derivative is exact). Catches a transposed operator or a wrong point set."""
     o = _oracle_for(etype, p)
     xu, xf, xq = o.op(etype, "xu"), o.op(etype, "xf"), o.op(etype, "xq")
     M0, M7, D = o.op(etype, "M0"), o.op(etype, "M7"), o.op(etype, "D")
     rng = np.random.default_rng(7)
     for _ in range(3):
-        c = _random_space_poly(rng, p, etype)
+        f = _SpaceFn(rng, p, etype)
+        u = f(xu)
+        assert np.abs(M0 @ u - f(xf)).max() < 1e-12
+        assert np.abs(M7 @ u - f(xq)).max() < 1e-12
+        c = _random_space_poly(rng, p, 2 if etype == 3 else etype)
         u = _eval_poly3(c, xu)
-        assert np.abs(M0 @ u - _eval_poly3(c, xf)).max() < 1e-12
-        assert np.abs(M7 @ u - _eval_poly3(c, xq)).max() < 1e-12
         for d in range(3):
             assert np.abs(D[d] @ u - _eval_poly3_grad(c, xu, d)).max() < 1e-11
     # one degree higher is not reproduced (the space is exactly the stated one)
@@ -251,8 +329,8 @@ def test_volume_quadrature_and_projection(etype, p):
     g = np.cos(1.3 * xq[:, 0] + 0.7 * xq[:, 1] - 0.4 * xq[:, 2]) + xq[:, 2] ** (p + 1)
     r = g - M7 @ (M8 @ g)
     for _ in range(4):
-        c = _random_space_poly(rng, p, etype)
-        assert abs((wq * r * _eval_poly3(c, xq)).sum()) < 1e-13
+        f = _SpaceFn(rng, p, etype)
+        assert abs((wq * r * f(xq)).sum()) < 1e-13
 
 
 def _radau_dg_lift(p, xi):
@@ -293,12 +371,27 @@ def test_lift_is_dg_lift(etype, p):
         sel = face == f
         n = nref[sel][0]
         for _ in range(2):
-            cv = _random_space_poly(rng, p, etype)
-            ch = _random_space_poly(rng, p, etype)
-            h_at_f = np.where(sel, _eval_poly3(ch, xf), 0.0)
-            lhs = (wq * _eval_poly3(cv, xq) * (M7 @ (lift @ h_at_f))).sum()
+            fv = _SpaceFn(rng, p, etype)
+            fh = _SpaceFn(rng, p, etype)
+            h_at_f = np.where(sel, fh(xf), 0.0)
+            lhs = (wq * fv(xq) * (M7 @ (lift @ h_at_f))).sum()
             # face quadrature in the face parameters; X(s,t) built from the face's plane
-            if etype == 0:
+            if etype == 3 and n[2] < -0.5:
+                # pyramid base z = -1: the traces are Q_p
+                S, T = np.meshgrid(gx, gx, indexing="ij")
+                pts = np.stack([S.ravel(), T.ravel(), -np.ones(S.size)], 1)
+                wts = np.outer(gw, gw).ravel()
+            elif etype == 3:
+                # pyramid triangle: the apex and the base edge the outward normal points to
+                e0 = np.array([n[0], n[1]]) / max(abs(n[0]), abs(n[1]))
+                t_ = np.array([-e0[1], e0[0]])
+                P0 = np.array([e0[0] - t_[0], e0[1] - t_[1], -1.0])
+                P1 = np.array([e0[0] + t_[0], e0[1] + t_[1], -1.0])
+                P2 = np.array([0.0, 0.0, 1.0])
+                s_, u_ = txy[:, 0], txy[:, 1]
+                pts = P0 + np.outer((1 + s_) / 2, P1 - P0) + np.outer((1 + u_) / 2, P2 - P0)
+                wts = tw * np.linalg.norm(np.cross(P1 - P0, P2 - P0)) / 4
+            elif etype == 0:
                 d = int(np.argmax(np.abs(n)))
                 tang = [t for t in range(3) if t != d]
                 S, T = np.meshgrid(gx, gx, indexing="ij")
@@ -328,7 +421,7 @@ def test_lift_is_dg_lift(etype, p):
                     pts = np.stack([-np.ones_like(s), s, t], 1)
                 else:
                     pts = np.stack([-s, s, t], 1); wts = wts * math.sqrt(2.0)
-            rhs = (wts * _eval_poly3(cv, pts) * _eval_poly3(ch, pts)).sum()
+            rhs = (wts * fv(pts) * fh(pts)).sum()
             assert abs(lhs - rhs) < 1e-11 * max(1.0, abs(rhs))
 
 
@@ -384,16 +477,18 @@ def test_corrected_derivatives_integrate_by_parts(etype, p):
     operator M4 - M6 M0 satisfies int v (Agrad_d u) dV = -int u (d_d v) dV, and the corrected
     divergence M1 - M3 M2 satisfies int v (Adiv F) dV = -sum_d int F_d (d_d v) dV, for u, v, F_d in
     the solution space. This pins the lift, the reference normals and the face measure of every
-    face at once (a slanted face's sqrt 2 or sqrt 3, a flipped normal or a transposed lift fail)."""
+    face at once (a slanted face's sqrt 2, sqrt 3 or sqrt 5 / 2, a flipped normal or a transposed
+    lift fail) and, on the pyramid, the projected derivative of reading P3 (the nodal derivative of
+    its rational space fails it)."""
     o = _oracle_for(etype, p)
     xu, wq, M7, D = o.op(etype, "xu"), o.op(etype, "wq"), o.op(etype, "M7"), o.op(etype, "D")
     Ag, Ad = o.op(etype, "Agrad"), o.op(etype, "Adiv")
     rng = np.random.default_rng(5)
     ip = lambda a, b: (wq * (M7 @ a) * (M7 @ b)).sum()  # noqa: E731
     for _ in range(2):
-        u = _eval_poly3(_random_space_poly(rng, p, etype), xu)
-        v = _eval_poly3(_random_space_poly(rng, p, etype), xu)
-        F = [_eval_poly3(_random_space_poly(rng, p, etype), xu) for _ in range(3)]
+        u = _SpaceFn(rng, p, etype)(xu)
+        v = _SpaceFn(rng, p, etype)(xu)
+        F = [_SpaceFn(rng, p, etype)(xu) for _ in range(3)]
         for d in range(3):
             lhs, rhs = ip(v, Ag[d] @ u), -ip(u, D[d] @ v)
             assert abs(lhs - rhs) < 1e-11 * max(1.0, abs(rhs))
@@ -433,6 +528,8 @@ MESHES = {
     "mixed2": lambda: W.mixed_box_mesh(2),
     "mixed4": lambda: W.mixed_box_mesh(4),
     "curved3": lambda: W.curved_box_mesh(3, amp=0.15),
+    "pyr2": lambda: W.box_pyr_mesh(2),
+    "hexpyr2": lambda: W.box_pyr_mesh(2, hex_below=1),
     "tet2": lambda: W.box_tet_mesh(2),
     "tetshear2": lambda: W.box_tet_mesh(2, shear=True),
 }
@@ -446,7 +543,8 @@ def test_freestream_preservation(name, p):
     metric terms lie in the solution space for p >= 2 so that the discrete metric identities hold. Rounding in the divergence grows with the
     operator norm, so the bound is relative to the RHS scale max|f| (2/h) (p+1)^2."""
     mesh = MESHES[name]()
-    if (mesh["pri_v"].shape[0] or mesh.get("tet_v", np.zeros((0, 4))).shape[0]) and p != 3:
+    if (mesh["pri_v"].shape[0] or mesh.get("tet_v", np.zeros((0, 4))).shape[0]
+            or mesh.get("pyr_v", np.zeros((0, 5))).shape[0]) and p != 3:
         pytest.skip("printed triangle points exist for p=2,3 only")
     o = O.Oracle(mesh, p, p + 2)
     blocks = _layout(o, mesh)
@@ -462,7 +560,8 @@ def _tgv(o, mesh, perturb=0.0, mach=0.1):
     return W.tgv_state(o.sol_coords(), _layout(o, mesh), mach=mach, perturb=perturb)
 
 
-@pytest.mark.parametrize("name", ["hex1_self_periodic", "hex3", "sheared3", "mixed4", "tetshear2", "curved3"])
+@pytest.mark.parametrize("name", ["hex1_self_periodic", "hex3", "sheared3", "mixed4", "tetshear2", "curved3", "pyr2",
+                                  "hexpyr2"])
 def test_discrete_conservation(name):
     """Check (e): the quadrature-weighted RHS sums to zero to 1e-12 relative, per variable."""
     mesh = MESHES[name]()
@@ -553,6 +652,36 @@ def test_tetrahedra_rhs_converges_to_analytic_navier_stokes():
     assert np.all(e_inv[1] < 0.05), e_inv
     assert np.all(np.log2(e_vis[0] / e_vis[1]) > 1.5), e_vis
     assert np.all(e_vis[1] < 0.5), e_vis
+
+
+def test_pyramids_rhs_converges_to_analytic_navier_stokes():
+    """Consistency of the pyramidal discretisation (readings P1-P3) on the box of cells split into
+    six pyramids each: inviscid order >= p - 0.5 and viscous order >= p - 1.5 between 8^3 and 16^3
+    cells (3,072 and 24,576 pyramids)."""
+    from tests.analytic_ns import rhs_function, state_function
+    mach, mu = 0.3, 0.1
+    state = state_function("wave", 1.4, mach)
+    ex_inv = rhs_function("wave", 1.4, mach, 0.0, 0.71)
+    ex_vis = rhs_function("wave", 1.4, mach, mu, 0.71)
+    e_inv, e_vis = [], []
+    for N in (8, 16):
+        mesh = W.box_pyr_mesh(N)
+        ne = mesh["pyr_v"].shape[0]
+        o0 = O.Oracle(mesh, 3, 5, mu=0.0, threads=os.cpu_count())
+        o1 = O.Oracle(mesh, 3, 5, mu=mu, threads=os.cpu_count())
+        x = o0.sol_coords()
+        U = W.to_layout(state(x), [(ne, 30)])
+        r0 = o0.rhs(U).reshape(ne, 5, 30).transpose(1, 0, 2).reshape(5, -1)
+        r1 = o1.rhs(U).reshape(ne, 5, 30).transpose(1, 0, 2).reshape(5, -1)
+        x0, x1 = ex_inv(x), ex_vis(x)
+        e_inv.append(np.abs(r0 - x0).max(axis=1) / np.abs(x0).max(axis=1))
+        dv, dx = (r1 - r0)[1:], (x1 - x0)[1:]
+        e_vis.append(np.abs(dv - dx).max(axis=1) / np.abs(dx).max(axis=1))
+    e_inv, e_vis = np.array(e_inv), np.array(e_vis)
+    assert np.all(np.log2(e_inv[0] / e_inv[1]) > 2.5), e_inv
+    assert np.all(e_inv[1] < 0.01), e_inv
+    assert np.all(np.log2(e_vis[0] / e_vis[1]) > 1.5), e_vis
+    assert np.all(e_vis[1] < 0.2), e_vis
 
 
 def test_penalty_term_is_dissipative_energy_identity():
