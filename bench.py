@@ -71,13 +71,14 @@ def phase_b_flops_per_element(p=P, m=MQ, one_sided=True, diagonal_metric=True, d
     return con_u + grad + jt + face + interp + tdisf + proj + div
 
 
-def tet_phase_b_flops_per_element():
-    """FLOPs of the tetrahedral volume kernel per element (p = 3: 20 solution points, 40 flux
-    points, 125 quadrature points; dense operators, full metric, one-sided viscous flux, the
-    divergence folded into the projection as one 20 x 375 operator per variable)."""
-    nu, nf, nq = 20, 40, 125
+def tet_phase_b_flops_per_element(nu=20, nf=40, nfaces=4):
+    """FLOPs of the dense-element volume kernel per element (p = 3; tetrahedron: 20 solution points,
+    40 flux points, 4 faces; pyramid: 30, 56, 5; 125 quadrature points; dense operators, full
+    metric, one-sided viscous flux, the divergence folded into the projection as one nu x 375
+    operator per variable)."""
+    nq = 125
     con_u = 5 * nf * 3
-    grad = 3 * nu * nu * 5 * 2 + nf * nu * 5 * 2 + 4 * 3 * 5 * nu * 2   # Dh u, face lifts, normals
+    grad = 3 * nu * nu * 5 * 2 + nf * nu * 5 * 2 + nfaces * 3 * 5 * nu * 2   # Dh u, face lifts, normals
     jt = 5 * nu * 15
     face = (nf // 2) * (20 * nu * 2 + VISC_NORMAL_FLOPS)
     interp = 20 * nq * nu * 2
@@ -226,8 +227,8 @@ def _time_steps(m, U, steps, warmup, torch):
 
 def other_configs(args, torch, fr, W):
     """Mixed hex/prism TGV (40^3 box: 32,000 hexes + 64,000 prisms, p = 3), the 48^3 TGV without
-    anti-aliasing and with full (flux + surface-flux) anti-aliasing, a tetrahedral TGV box, a curved
-    (trilinear) hexahedral TGV box, and the batched ensemble
+    anti-aliasing and with full (flux + surface-flux) anti-aliasing, a tetrahedral and a pyramidal TGV
+    box, a curved (trilinear) hexahedral TGV box, and the batched ensemble
     of 64 TGV instances (edges in {8,...,24}, p in {3,4}, M in [0.05,0.2], Re in [400,3200] from
     SplitMix64(20240111)), each timed over RK4 steps on a side stream (CUDA-graph replay)."""
     out = {}
@@ -317,6 +318,33 @@ def other_configs(args, torch, fr, W):
         m.close()
         del U
         torch.cuda.empty_cache()
+    # pyramids: the 20^3 box, every cell split into six pyramids (48,000 pyramids, 7.2M DOF)
+    mesh_y = W.box_pyr_mesh(20)
+    ny = mesh_y["pyr_v"].shape[0]
+    fl_y = tet_phase_b_flops_per_element(30, 56, 5)
+    for prec in ("fp64", "fp32"):
+        m = fr.FRMesh(mesh_y, fr.make_params(p=3, prec=prec, p_ref=p0))
+        U0 = W.tgv_state(m.sol_coords(), [(ny, 30)], perturb=1e-3)
+        U = torch.from_numpy(U0).cuda()
+        ms = _time_steps(m, U, steps, 2, torch)
+        m.sync_status()
+        Uc = U if prec == "fp64" else U.float()
+        Rc = torch.empty_like(Uc)
+        m.set_timing(True)
+        m.rhs(Uc, Rc)
+        torch.cuda.synchronize()
+        m.set_timing(False)
+        kt = m.kernel_times()
+        b_ms = kt[1][0] / max(1, kt[1][1])
+        out[f"pyr20_{prec}"] = {"gdof_rhs_per_s": U0.size * RHS_PER_STEP / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+                                "dof": int(U0.size), "elements": ny, "volume_kernel_ms": b_ms,
+                                "volume_tflops": fl_y * ny / (b_ms * 1e-3) / 1e12, "flops_per_element": fl_y}
+        if prec == "fp64":
+            out["pyr20_fp64"]["volume_frac_of_fp64_peak"] = out["pyr20_fp64"]["volume_tflops"] / FP64_PEAK_TFLOPS
+        else:
+            out[f"pyr20_{prec}"]["speedup_vs_fp64"] = out["pyr20_fp64"]["ms_per_step"] / ms
+        m.close()
+        del U, Uc, Rc
     draws = W.ensemble_draws(64)
     meshes = [W.box_hex_mesh(d["edge"]) for d in draws]
     for prec in ("fp64", "fp32"):

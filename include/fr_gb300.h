@@ -3,8 +3,8 @@
  *
  * The library evaluates the right-hand side (RHS) R(u) of the semi-discrete system du/dt = R(u)
  * obtained by flux reconstruction (FR) of the compressible Navier-Stokes equations with flux
- * anti-aliasing, on affine hexahedral, prismatic and tetrahedral meshes, and advances it with
- * classical RK4.
+ * anti-aliasing, on hexahedral (affine or trilinear), prismatic, tetrahedral and pyramidal meshes,
+ * and advances it with classical RK4.
  * Paper: Akkurt, Witherden, Vincent, "Cache blocking for flux reconstruction: extension to
  * Navier-Stokes equations and anti-aliasing".
  *   - governing equations, fluxes and the perfect-gas closure: Sec. 2.1 (Eqs. gov, fluxe, fluxv);
@@ -12,7 +12,8 @@
  *     Sec. 2.1 Eqs. FR-disu .. FRfinal, and their kernel form in Sec. 2.2;
  *   - flux anti-aliasing (interpolation to quadrature points, L2 projection): Sec. 2.1.1 and
  *     Sec. 2.2.1 (operators M7..M10); sum factorisation of the hex and prism operators: Sec. 4;
- *     tetrahedra (listed in Sec. 1 among the supported types) with dense per-element operators;
+ *     tetrahedra and pyramids (listed in Sec. 1 among the supported types) with dense per-element
+ *     operators;
  *   - the semi-discrete form du/dt = -J^-1 div~ f~: Eq. govqtrans; RK4: Sec. 3.
  *
  * Conventions shared by every entry point
@@ -29,22 +30,29 @@
  *     the state U and the result R: device pointers (or host pointers for the *_host variants).
  *   - Layout of U and R (reading R10 of the design notes): element-major [elem][var][pt], with
  *     var in (rho, rho vx, rho vy, rho vz, E). Elements are ordered instance by instance; inside an
- *     instance hexahedra come first, then prisms, then tetrahedra, each in descriptor order. Hex
+ *     instance hexahedra come first, then prisms, then tetrahedra, then pyramids, each in descriptor
+ *     order. Hex
  *     point index is i + n j + n^2 k (n = p+1 Gauss-Legendre points per direction, i fastest along
  *     xi); prism point index is t + 10 k (t = triangle point in the paper's printed Williams-Shunn
  *     order, k = Gauss-Legendre level in z); tetrahedron point index runs over the order-3 lattice
  *     points (a, b, c), a + b + c <= 3, a fastest, then b, then c, each at reference coordinates
- *     -1/2 + 4/5 (-1 + 2 (a, b, c)/3 + 1/2) (the lattice shrunk by 4/5 towards the centroid).
+ *     -1/2 + 4/5 (-1 + 2 (a, b, c)/3 + 1/2) (the lattice shrunk by 4/5 towards the centroid);
+ *     pyramid point index runs over the order-3 pyramid lattice, layer k = 0..3 at z = -1 + 2k/3
+ *     with (4-k)^2 points x, y = (1 - k/3)(-1 + 2i/(3-k)) (i fastest, then j, then k), shrunk by
+ *     4/5 towards (0, 0, -1/2).
  *   - Element type of U/R: double for FR_FP64; float for FR_FP32 and the mixed forms. The RK4
  *     entry points always take an FP64 master state (double), whatever the compute precision.
  *   - Vertex order: hexahedra in tensor order (corner a + 2b + 4c for (a,b,c) in {0,1}^3);
  *     prisms v0,v1,v2 at the lower triangle mapped to the reference (-1,-1),(1,-1),(-1,1) and
  *     v3,v4,v5 above them; tetrahedra v0..v3 mapped to the reference (-1,-1,-1), (1,-1,-1),
- *     (-1,1,-1), (-1,-1,1). Elements must be affine (parallelepipeds / straight prisms / any
- *     tetrahedron); other elements give FR_EUNSUPPORTED.
+ *     (-1,1,-1), (-1,-1,1); pyramids: the base corners in tensor order, reference (-1,-1,-1),
+ *     (1,-1,-1), (-1,1,-1), (1,1,-1), then the apex, reference (0,0,1). Prisms, tetrahedra and
+ *     pyramids must be affine (other ones give FR_EUNSUPPORTED); a non-affine hexahedron is a
+ *     trilinear (curved) element.
  *   - Local face order (used by the L/R rule): hex -xi, +xi, -eta, +eta, -zeta, +zeta; prism
  *     z=-1 triangle, z=+1 triangle, y=-1 quad, x+y=0 quad, x=-1 quad; tetrahedron z=-1, y=-1,
- *     x=-1, x+y+z=-1 (each with the 10 printed triangle points as flux points).
+ *     x=-1, x+y+z=-1 (each with the 10 printed triangle points as flux points); pyramid base z=-1
+ *     (4 x 4 GL points), then the triangles y=-(1-z)/2, x=(1-z)/2, y=(1-z)/2, x=-(1-z)/2.
  */
 #ifndef FR_GB300_H
 #define FR_GB300_H
@@ -92,7 +100,7 @@ typedef struct {
     double mu;            /* dynamic viscosity (constant) */
     double beta;          /* LDG switch (Sec. 2.1 common solution and viscous flux) */
     double tau;           /* LDG penalty */
-    int p;                /* solution order; hex p in {3,4}, prism and tetrahedron p = 3 */
+    int p;                /* solution order; hex p in {3,4}, prism, tetrahedron and pyramid p = 3 */
     int nq1d;             /* Gauss-Legendre quadrature points per line: 0 or p + 2 = flux anti-aliasing
                            * (Sec. 2.2.1; tetrahedra: the collapsed (p+2)^3 Gauss-Jacobi rule, exact
                            * to degree 2p+3); p + 1 = no anti-aliasing, the flux is evaluated at the
@@ -131,6 +139,8 @@ typedef struct {
     double period[3];     /* periodic box lengths; 0 = not periodic. Faces are matched modulo period */
     int n_tet;            /* number of tetrahedra (p = 3, flux anti-aliasing, fused form) */
     const int *tet_v;     /* [n_tet][4] vertex ids */
+    int n_pyr;            /* number of pyramids (p = 3, flux anti-aliasing, fused form) */
+    const int *pyr_v;     /* [n_pyr][5] vertex ids: base corners in tensor order, then the apex */
 } fr_mesh_desc;
 
 typedef struct fr_mesh fr_mesh;

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfrgb300.so")
-SOURCES = ["fr_api.cu", "fr_hex.cu", "fr_pri.cu", "fr_tet.cu", "fr_probe.cu", "fr_basis.cpp"]
+SOURCES = ["fr_api.cu", "fr_hex.cu", "fr_pri.cu", "fr_dense.cu", "fr_probe.cu", "fr_basis.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"] + ARCH
 

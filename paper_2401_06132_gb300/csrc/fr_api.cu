@@ -43,7 +43,7 @@ extern "C" const char *fr_last_error(void) { return g_err.c_str(); }
 // ---------------------------------------------------------------------------------------------
 struct InstanceHost {
     fr_params prm;
-    int n_hex, n_pri, n_tet;
+    int n_hex, n_pri, n_tet, n_pyr;
     std::vector<double> x0J;   // per element: x0[3], J[9] (row-major dx_i/dxi_j); x = x0 + J (xi + 1)
     std::vector<char> curved;  // per element: 1 = non-affine (trilinear) hexahedron
     std::vector<double> vx;    // per element: the 8 hexahedron vertices (tensor order), [24]
@@ -82,6 +82,9 @@ struct fr_mesh {
     frb::Tet3D tet;                      // tetrahedron operators (p = 3)
     bool has_tet = false;
     void *d_tetops = nullptr;            // TetOps<T> on the device
+    frb::Pyr3D pyr;                      // pyramid operators (p = 3)
+    bool has_pyr = false;
+    void *d_pyrops = nullptr;            // PyrOps<T> on the device
     std::vector<Group> groups;
     bool split_c = false;              // interface phase as pair flux (C1) + lift (C2)
     bool lowmach = false;              // FP32 low-Mach form (deviations, reduced energy, FP64 mass)
@@ -232,18 +235,24 @@ static void ref_faces(const fr_mesh *m, int blk, RefFaces &r)
         }
         return;
     }
-    if (B.type == 2) {
-        const frb::Tet3D &Tt = m->tet;
-        static const double cen[4][3] = {{-1.0 / 3, -1.0 / 3, -1}, {-1.0 / 3, -1, -1.0 / 3}, {-1, -1.0 / 3, -1.0 / 3},
-                                         {-1.0 / 3, -1.0 / 3, -1.0 / 3}};
-        r.nfaces = 4;
-        for (int f = 0; f < 4; f++) {
-            r.count[f] = 10; r.off[f] = 10 * f;
-            for (int d = 0; d < 3; d++) r.centre[f][d] = cen[f][d];
+    if (B.type == 2 || B.type == 3) {
+        // dense types: faces from the operator tables; the centre of a face is the mean of its
+        // vertices (a triangle's centroid, the base's centre)
+        static const double tcen[4][3] = {{-1.0 / 3, -1.0 / 3, -1}, {-1.0 / 3, -1, -1.0 / 3}, {-1, -1.0 / 3, -1.0 / 3},
+                                          {-1.0 / 3, -1.0 / 3, -1.0 / 3}};
+        static const double ycen[5][3] = {{0, 0, -1}, {0, -2.0 / 3, -1.0 / 3}, {2.0 / 3, 0, -1.0 / 3}, {0, 2.0 / 3, -1.0 / 3},
+                                          {-2.0 / 3, 0, -1.0 / 3}};
+        const bool tet = B.type == 2;
+        const int nfc = tet ? 4 : 5, nf = tet ? FR_TF : FR_YF;
+        const int *foff = tet ? m->tet.foff : m->pyr.foff;
+        r.nfaces = nfc;
+        for (int f = 0; f < nfc; f++) {
+            r.count[f] = foff[f + 1] - foff[f]; r.off[f] = foff[f];
+            for (int d = 0; d < 3; d++) r.centre[f][d] = tet ? tcen[f][d] : ycen[f][d];
         }
-        r.xf.assign((size_t)FR_TF * 3, 0.0);
-        for (int s2 = 0; s2 < FR_TF; s2++)
-            for (int d = 0; d < 3; d++) r.xf[(size_t)s2 * 3 + d] = Tt.xf[s2][d];
+        r.xf.assign((size_t)nf * 3, 0.0);
+        for (int s2 = 0; s2 < nf; s2++)
+            for (int d = 0; d < 3; d++) r.xf[(size_t)s2 * 3 + d] = tet ? m->tet.xf[s2][d] : m->pyr.xf[s2][d];
         return;
     }
     const frb::Prism2D &P = m->pri;
@@ -499,8 +508,11 @@ static fr_status match_instance(fr_mesh *m, int ii, int b0, int b1, const fr_mes
 static fr_status element_map(int ii, long long e, int type, const fr_mesh_desc *d, double *x0J, std::vector<double> &geo,
                              InstanceHost &I, long long li)
 {
-    const int nv = type == 0 ? 8 : (type == 1 ? 6 : 4);
-    const int *conn = type == 0 ? d->hex_v + 8 * e : (type == 1 ? d->pri_v + 6 * e : d->tet_v + 4 * e);
+    const int nv = type == 0 ? 8 : (type == 1 ? 6 : (type == 2 ? 4 : 5));
+    const int *conn = type == 0 ? d->hex_v + 8 * e
+                      : type == 1 ? d->pri_v + 6 * e
+                      : type == 2 ? d->tet_v + 4 * e
+                                  : d->pyr_v + 5 * e;
     const double *v[8];
     for (int k = 0; k < nv; k++) {
         int vi = conn[k];
@@ -513,13 +525,17 @@ static fr_status element_map(int ii, long long e, int type, const fr_mesh_desc *
         x0J[i] = v[0][i];
         x0J[3 + 3 * i + 0] = 0.5 * (v[1][i] - v[0][i]);
         x0J[3 + 3 * i + 1] = 0.5 * (v[2][i] - v[0][i]);
-        x0J[3 + 3 * i + 2] = 0.5 * (v[c3][i] - v[0][i]);
-        scale = std::max(scale, std::fabs(v[1][i] - v[0][i]) + std::fabs(v[2][i] - v[0][i]) + std::fabs(v[c3][i] - v[0][i]));
+        // pyramid: the apex, reference (0,0,1), is corner 0 + (1,1,2) in reference units
+        x0J[3 + 3 * i + 2] = type == 3 ? 0.5 * (v[4][i] - v[0][i]) - 0.25 * (v[1][i] - v[0][i]) - 0.25 * (v[2][i] - v[0][i])
+                                       : 0.5 * (v[c3][i] - v[0][i]);
+        scale = std::max(scale, std::fabs(v[1][i] - v[0][i]) + std::fabs(v[2][i] - v[0][i]) + std::fabs(v[type == 3 ? 4 : c3][i] - v[0][i]));
     }
     static const double pc[6][3] = {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}, {1, -1, 1}, {-1, 1, 1}};
+    static const double pp[5][3] = {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {1, 1, -1}, {0, 0, 1}};
     for (int k = 0; k < nv; k++) {  // affine: every corner is the image of its reference corner
         double X[3], x[3];
         if (type == 0) { X[0] = (k & 1) ? 1.0 : -1.0; X[1] = (k & 2) ? 1.0 : -1.0; X[2] = (k & 4) ? 1.0 : -1.0; }
+        else if (type == 3) { X[0] = pp[k][0]; X[1] = pp[k][1]; X[2] = pp[k][2]; }
         else { X[0] = pc[k][0]; X[1] = pc[k][1]; X[2] = pc[k][2]; }
         affine_point(x0J, X, x);
         for (int i = 0; i < 3; i++)
@@ -566,10 +582,10 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
         // the solution points, i.e. the collocation form without anti-aliasing (hexahedra only)
         if (P.p < 3 || P.p > 4 || (m1 != P.p + 2 && m1 != P.p + 1))
             return fail(FR_EUNSUPPORTED, "instance %d: order %d with %d quadrature points", ii, P.p, m1);
-        if (m1 == P.p + 1 && d && (d->n_pri > 0 || d->n_tet > 0))
-            return fail(FR_EUNSUPPORTED, "instance %d: prisms and tetrahedra are built with flux anti-aliasing only", ii);
+        if (m1 == P.p + 1 && d && (d->n_pri > 0 || d->n_tet > 0 || d->n_pyr > 0))
+            return fail(FR_EUNSUPPORTED, "instance %d: prisms, tetrahedra and pyramids are built with flux anti-aliasing only", ii);
         if (P.surface_aa) {
-            if (n_inst != 1 || !d || d->n_pri > 0 || d->n_tet > 0 || m1 != P.p + 2)
+            if (n_inst != 1 || !d || d->n_pri > 0 || d->n_tet > 0 || d->n_pyr > 0 || m1 != P.p + 2)
                 return fail(FR_EUNSUPPORTED, "surface-flux anti-aliasing runs single-instance hexahedral meshes with m = p + 2");
             if (P.prec != FR_FP64 && P.p_ref > 0 && P.rho_ref > 0)
                 return fail(FR_EUNSUPPORTED, "surface-flux anti-aliasing runs without the low-Mach form");
@@ -579,8 +595,8 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
             !(P.rho_ref >= 0.0))
             return fail(FR_EINVAL, "instance %d: bad physical parameters", ii);
         if (P.rusanov_mode != 0) return fail(FR_EUNSUPPORTED, "rusanov_mode %d", P.rusanov_mode);
-        if (d->n_hex < 0 || d->n_pri < 0 || d->n_tet < 0 || d->n_hex + d->n_pri + d->n_tet == 0 || d->n_verts <= 0 ||
-            !d->verts)
+        if (d->n_hex < 0 || d->n_pri < 0 || d->n_tet < 0 || d->n_pyr < 0 || d->n_hex + d->n_pri + d->n_tet + d->n_pyr == 0 ||
+            d->n_verts <= 0 || !d->verts)
             return fail(FR_EINVAL, "instance %d: empty or malformed mesh", ii);
         if (d->n_hex > 0 && !d->hex_v) return fail(FR_EINVAL, "instance %d: null hex connectivity", ii);
         if (d->n_pri > 0 && !d->pri_v) return fail(FR_EINVAL, "instance %d: null prism connectivity", ii);
@@ -589,18 +605,24 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
             return fail(FR_EUNSUPPORTED, "instance %d: tetrahedra are built for p = 3", ii);
         if (d->n_tet > 0 && P.prec != FR_FP64 && P.p_ref > 0 && P.rho_ref > 0)
             return fail(FR_EUNSUPPORTED, "instance %d: tetrahedra run the plain FP32 form (no low-Mach form)", ii);
+        if (d->n_pyr > 0 && !d->pyr_v) return fail(FR_EINVAL, "instance %d: null pyramid connectivity", ii);
+        if (d->n_pyr > 0 && P.p != 3)
+            return fail(FR_EUNSUPPORTED, "instance %d: pyramids are built for p = 3", ii);
+        if (d->n_pyr > 0 && P.prec != FR_FP64 && P.p_ref > 0 && P.rho_ref > 0)
+            return fail(FR_EUNSUPPORTED, "instance %d: pyramids run the plain FP32 form (no low-Mach form)", ii);
         if (d->n_pri > 0 && (P.p != 3 || (P.tri_strength != 0 && P.tri_strength != 8)))
             return fail(FR_EUNSUPPORTED, "instance %d: prisms are built for p = 3 with a strength-8 triangle rule", ii);
         InstanceHost I;
         I.prm = P; I.prm.nq1d = m1;
-        I.n_hex = d->n_hex; I.n_pri = d->n_pri; I.n_tet = d->n_tet;
-        I.x0J.resize((size_t)(d->n_hex + d->n_pri + d->n_tet) * 12);
-        I.curved.assign((size_t)(d->n_hex + d->n_pri + d->n_tet), 0);
-        I.vx.assign((size_t)(d->n_hex + d->n_pri + d->n_tet) * 24, 0.0);
+        I.n_hex = d->n_hex; I.n_pri = d->n_pri; I.n_tet = d->n_tet; I.n_pyr = d->n_pyr;
+        const size_t nel = (size_t)d->n_hex + d->n_pri + d->n_tet + d->n_pyr;
+        I.x0J.resize(nel * 12);
+        I.curved.assign(nel, 0);
+        I.vx.assign(nel * 24, 0.0);
         m->inst_u0.push_back(u);
         bfirst.push_back((int)m->blocks.size());
-        for (int type = 0; type < 3; type++) {
-            long long ne = type == 0 ? d->n_hex : (type == 1 ? d->n_pri : d->n_tet);
+        for (int type = 0; type < 4; type++) {
+            long long ne = type == 0 ? d->n_hex : (type == 1 ? d->n_pri : (type == 2 ? d->n_tet : d->n_pyr));
             if (ne == 0) continue;
             Block B{};
             B.inst = ii; B.type = type; B.p = P.p; B.m = m1;
@@ -617,16 +639,23 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
                 }
                 h = m->pri.z;
                 B.nu = FR_PT * FR_PE; B.nf = 2 * FR_PT + 3 * FR_PE * FR_PE;
-            } else {
+            } else if (type == 2) {
                 if (!m->has_tet) {
                     if (frb::tet3d(m->tet)) return fail(FR_EUNSUPPORTED, "tetrahedron operators");
                     m->has_tet = true;
                 }
                 std::memset(&h, 0, sizeof h);
                 B.nu = FR_TU; B.nf = FR_TF;
+            } else {
+                if (!m->has_pyr) {
+                    if (frb::pyr3d(m->pyr)) return fail(FR_EUNSUPPORTED, "pyramid operators");
+                    m->has_pyr = true;
+                }
+                std::memset(&h, 0, sizeof h);
+                B.nu = FR_YU; B.nf = FR_YF;
             }
             B.ne = ne; B.elem0 = elem; B.u0 = u; B.f0 = f;
-            long long le0 = type == 0 ? 0 : (type == 1 ? d->n_hex : d->n_hex + d->n_pri);
+            long long le0 = type == 0 ? 0 : (type == 1 ? d->n_hex : (type == 2 ? d->n_hex + d->n_pri : d->n_hex + d->n_pri + d->n_tet));
             for (long long e = 0; e < ne; e++) {
                 fr_status st = element_map(ii, e, type, d, &I.x0J[(size_t)(le0 + e) * 12], m->geo_host, I, le0 + e);
                 if (st) return st;
@@ -693,40 +722,49 @@ static fr_status upload_priops(fr_mesh *m, void **dst)
     return FR_OK;
 }
 
-template <typename T>
-static fr_status upload_tetops(fr_mesh *m)
+// Transposed dense-element operator tables (DenseOps) from the host construction (DenseRef).
+template <typename T, typename REF, typename OPS>
+static fr_status upload_dense(fr_mesh *m, const REF &R, void **dst)
 {
-    if (!m->has_tet) return FR_OK;
-    const frb::Tet3D &Tt = m->tet;
-    std::vector<TetOps<T>> o(1);
-    TetOps<T> &t = o[0];
-    for (int j = 0; j < FR_TU; j++) {
-        for (int q = 0; q < FR_TQ; q++) t.Bt[j][q] = (T)Tt.B[q][j];
-        for (int s2 = 0; s2 < FR_TF; s2++) t.M0t[j][s2] = (T)Tt.M0[s2][j];
+    constexpr int NU = REF::NU, NF = REF::NF, NFACE = REF::NFACE;
+    std::vector<OPS> o(1);   // value-initialised: the pad rows stay zero
+    OPS &t = o[0];
+    for (int j = 0; j < NU; j++) {
+        for (int q = 0; q < FR_TQ; q++) t.Bt[j][q] = (T)R.B[q][j];
+        for (int s2 = 0; s2 < NF; s2++) t.M0t[j][s2] = (T)R.M0[s2][j];
         for (int d = 0; d < 3; d++)
-            for (int z = 0; z < FR_TU; z++) t.Dht[d][j][z] = (T)Tt.Dh[d][z][j];
+            for (int z = 0; z < NU; z++) t.Dht[d][j][z] = (T)R.Dh[d][z][j];
     }
-    for (int s2 = 0; s2 < FR_TF; s2++)
-        for (int z = 0; z < FR_TU; z++) t.Lt[s2][z] = (T)Tt.L[z][s2];
+    for (int s2 = 0; s2 < NF; s2++)
+        for (int z = 0; z < NU; z++) t.Lt[s2][z] = (T)R.L[z][s2];
     // projection with the corrected divergence: (Dh_d Pj)[z][q], formed in FP64
     for (int d = 0; d < 3; d++)
         for (int q = 0; q < FR_TQ; q++)   // rows FR_TQ .. FR_TQP-1 stay zero
-            for (int z = 0; z < FR_TU; z++) {
+            for (int z = 0; z < NU; z++) {
                 double v = 0;
-                for (int j = 0; j < FR_TU; j++) v += Tt.Dh[d][z][j] * Tt.Pj[j][q];
+                for (int j = 0; j < NU; j++) v += R.Dh[d][z][j] * R.Pj[j][q];
                 t.Dvt[d][q][z] = (T)v;
             }
-    for (int f = 0; f < 4; f++)
-        for (int d = 0; d < 3; d++) t.nf[f][d] = (T)Tt.nf[f][d];
-    fr_status st = dalloc(m, &m->d_tetops, sizeof(TetOps<T>));
+    for (int f = 0; f < NFACE; f++) {
+        for (int d = 0; d < 3; d++) t.nf[f][d] = (T)R.nf[f][d];
+        for (int s2 = R.foff[f]; s2 < R.foff[f + 1]; s2++) t.fidx[s2] = (unsigned char)f;
+    }
+    for (int f = 0; f <= NFACE; f++) t.foff[f] = R.foff[f];
+    fr_status st = dalloc(m, dst, sizeof(OPS));
     if (st) return st;
-    CU(cudaMemcpy(m->d_tetops, o.data(), sizeof(TetOps<T>), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(*dst, o.data(), sizeof(OPS), cudaMemcpyHostToDevice));
     return FR_OK;
 }
 
-// Metric terms at every point of a curved (trilinear) hexahedral mesh (single block): J^-1 and
-// det J at the solution points, det J J^-1 at the quadrature points, the unit normal and |n_s| of
-// n_s = det J J^-T n~ at the flux points. Rejects a map that is not invertible at one of them.
+template <typename T>
+static fr_status upload_tetops(fr_mesh *m)
+{
+    fr_status st = FR_OK;
+    if (m->has_tet) st = upload_dense<T, frb::Tet3D, TetOps<T>>(m, m->tet, &m->d_tetops);
+    if (!st && m->has_pyr) st = upload_dense<T, frb::Pyr3D, PyrOps<T>>(m, m->pyr, &m->d_pyrops);
+    return st;
+}
+
 template <typename T>
 static fr_status upload_curved(fr_mesh *m)
 {
@@ -817,12 +855,13 @@ static void build_face_normals(fr_mesh *m)
         for (long long e = 0; e < B.ne; e++) {
             const long long ge = B.elem0 + e;
             const double *Ji = &m->geo_host[(size_t)ge * 10], det = m->geo_host[(size_t)ge * 10 + 9];
-            const int nfaces = B.type == 0 ? 6 : (B.type == 1 ? 5 : 4);
+            const int nfaces = B.type == 0 ? 6 : (B.type == 1 ? 5 : (B.type == 2 ? 4 : 5));
             for (int f = 0; f < nfaces; f++) {
                 double nr[3] = {0, 0, 0};
                 if (B.type == 0) nr[f / 2] = (f & 1) ? 1.0 : -1.0;
                 else if (B.type == 1) for (int d = 0; d < 3; d++) nr[d] = pri_n[f][d];
-                else for (int d = 0; d < 3; d++) nr[d] = m->tet.nf[f][d];
+                else if (B.type == 2) for (int d = 0; d < 3; d++) nr[d] = m->tet.nf[f][d];
+                else for (int d = 0; d < 3; d++) nr[d] = m->pyr.nf[f][d];
                 double ns[3];
                 for (int k = 0; k < 3; k++) ns[k] = det * (Ji[k] * nr[0] + Ji[3 + k] * nr[1] + Ji[6 + k] * nr[2]);
                 const double mag = std::sqrt(ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]);
@@ -999,7 +1038,7 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
     }
     if (!st) st = (m->prec == FR_FP64) ? build_groups<double>(m, partner) : build_groups<float>(m, partner);
     // FP64 hexahedral handles evaluate each interface pair once (split interface phase)
-    m->split_c = ((m->prec == FR_FP64) && !m->has_pri && !m->has_tet) || m->surf;
+    m->split_c = ((m->prec == FR_FP64) && !m->has_pri && !m->has_tet && !m->has_pyr) || m->surf;
     if (!st && m->surf) {
         std::vector<uint32_t> ql;
         for (long long q = 0; q < m->nqf; q++)
@@ -1037,7 +1076,7 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
 extern "C" fr_status fr_destroy(fr_mesh *m)
 {
     if (!m) return FR_OK;
-    void **bufs[] = {&m->d_fnrm, (void **)&m->d_fnrm64, &m->d_geo64, (void **)&m->d_MF, (void **)&m->d_RL, &m->d_priops, &m->d_priops64, &m->d_tetops, &m->d_geo, (void **)&m->d_partner, &m->d_UF, &m->d_FV, &m->d_CF, &m->d_QF, &m->d_DF, &m->d_Qu,
+    void **bufs[] = {&m->d_fnrm, (void **)&m->d_fnrm64, &m->d_geo64, (void **)&m->d_MF, (void **)&m->d_RL, &m->d_priops, &m->d_priops64, &m->d_tetops, &m->d_pyrops, &m->d_geo, (void **)&m->d_partner, &m->d_UF, &m->d_FV, &m->d_CF, &m->d_QF, &m->d_DF, &m->d_Qu,
                      &m->d_UQ, &m->d_QQ, &m->d_Rt, &m->d_rk_k, &m->d_rk_us, (void **)&m->d_rk_acc, &m->d_io_U,
                      &m->d_io_R, (void **)&m->d_wsum, (void **)&m->d_status, &m->d_Qsnap, (void **)&m->d_qpartner,
                      &m->d_UFQ, &m->d_FVQ, (void **)&m->d_qlpts, &m->d_DQ, &m->d_mu, &m->d_mq, &m->d_mfn};
@@ -1246,7 +1285,8 @@ static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, co
                 }
                 int lr = b.type == 0 ? hex_fused_phase<T>(b.p, ph, a, s, gr.variant)
                          : b.type == 1 ? pri_fused_phase<T>(ph, a, reinterpret_cast<const PriOps<T> *>(m->d_priops), reinterpret_cast<const PriOpsFF *>(m->d_priops64), s)
-                                       : tet_fused_phase<T>(ph, a, reinterpret_cast<const TetOps<T> *>(m->d_tetops), s);
+                         : b.type == 2 ? tet_fused_phase<T>(ph, a, reinterpret_cast<const TetOps<T> *>(m->d_tetops), s)
+                                       : pyr_fused_phase<T>(ph, a, reinterpret_cast<const PyrOps<T> *>(m->d_pyrops), s);
                 if (lr) return fail(FR_ECUDA, "fused phase %d launch: %s", ph, cudaGetErrorString(cudaGetLastError()));
             }
         }
@@ -1304,7 +1344,8 @@ static fr_status autotune_impl(fr_mesh *m, const void *U, void *R, cudaStream_t 
         }
         int lr = b.type == 0 ? hex_fused_phase<T>(b.p, 0, a, s, gr.variant)
                  : b.type == 1 ? pri_fused_phase<T>(0, a, reinterpret_cast<const PriOps<T> *>(m->d_priops), reinterpret_cast<const PriOpsFF *>(m->d_priops64), s)
-                               : tet_fused_phase<T>(0, a, reinterpret_cast<const TetOps<T> *>(m->d_tetops), s);
+                 : b.type == 2 ? tet_fused_phase<T>(0, a, reinterpret_cast<const TetOps<T> *>(m->d_tetops), s)
+                               : pyr_fused_phase<T>(0, a, reinterpret_cast<const PyrOps<T> *>(m->d_pyrops), s);
         if (lr) return fail(FR_ECUDA, "autotune: face phase launch failed");
     }
     cudaEvent_t e0, e1;
@@ -1557,13 +1598,14 @@ extern "C" fr_status fr_sol_coords(const fr_mesh *m, double *xyz)
         const InstanceHost &I = m->inst[B.inst];
         const frb::Hex1D &h = m->hex1d[b];
         int n = h.n;
-        long long le0 = B.type == 0 ? 0 : (B.type == 1 ? I.n_hex : I.n_hex + I.n_pri);
+        long long le0 = B.type == 0 ? 0 : (B.type == 1 ? I.n_hex : (B.type == 2 ? I.n_hex + I.n_pri : I.n_hex + I.n_pri + I.n_tet));
         for (long long e = 0; e < B.ne; e++) {
             for (int z = 0; z < B.nu; z++, k++) {
                 double X[3];
                 if (B.type == 0) { X[0] = h.x[z % n]; X[1] = h.x[(z / n) % n]; X[2] = h.x[z / (n * n)]; }
                 else if (B.type == 1) { X[0] = m->pri.xt[z % FR_PT][0]; X[1] = m->pri.xt[z % FR_PT][1]; X[2] = h.x[z / FR_PT]; }
-                else { X[0] = m->tet.x[z][0]; X[1] = m->tet.x[z][1]; X[2] = m->tet.x[z][2]; }
+                else if (B.type == 2) { X[0] = m->tet.x[z][0]; X[1] = m->tet.x[z][1]; X[2] = m->tet.x[z][2]; }
+                else { X[0] = m->pyr.x[z][0]; X[1] = m->pyr.x[z][1]; X[2] = m->pyr.x[z][2]; }
                 map_point(I, le0 + e, X, xyz + 3 * k);
             }
         }
@@ -1621,7 +1663,7 @@ extern "C" fr_status fr_diagnostics(fr_mesh *m, const void *U, const void *R, do
         const frb::Hex1D &h = m->hex1d[bi];
         for (int z = 0; z < b.nu; z++)
             wp.w[z] = b.type == 0 ? h.w[z % h.n] * h.w[(z / h.n) % h.n] * h.w[z / (h.n * h.n)]
-                    : b.type == 1 ? m->pri.wt[z % FR_PT] * h.w[z / FR_PT] : m->tet.w[z];
+                    : b.type == 1 ? m->pri.wt[z % FR_PT] * h.w[z / FR_PT] : (b.type == 2 ? m->tet.w[z] : m->pyr.w[z]);
         int grid = (int)std::min<long long>(std::max<long long>(b.ne, 1), 152LL * 8);
         double *o = m->d_wsum + 8 * b.inst;
         size_t ts = tsize(m->prec);
@@ -1701,7 +1743,7 @@ extern "C" fr_status fr_diagnostics_noalloc(fr_mesh *m, const void *U, const voi
         const frb::Hex1D &h = m->hex1d[bi];
         for (int z = 0; z < b.nu; z++)
             wp.w[z] = b.type == 0 ? h.w[z % h.n] * h.w[(z / h.n) % h.n] * h.w[z / (h.n * h.n)]
-                    : b.type == 1 ? m->pri.wt[z % FR_PT] * h.w[z / FR_PT] : m->tet.w[z];
+                    : b.type == 1 ? m->pri.wt[z % FR_PT] * h.w[z / FR_PT] : (b.type == 2 ? m->tet.w[z] : m->pyr.w[z]);
         int grid = (int)std::min<long long>(std::max<long long>(b.ne, 1), 152LL * 8);
         double *o = acc + 8 * b.inst;
         size_t ts = tsize(m->prec);

@@ -359,11 +359,11 @@ static void monomials3d(const double *X, double *m, double (*dm)[FR_TU])
             }
 }
 
-// In-place inverse of an n x n matrix (n <= FR_TU), Gauss-Jordan with partial pivoting.
+// In-place inverse of an n x n matrix (n <= FR_YU), Gauss-Jordan with partial pivoting.
 static int invert_n(int n, double *a)
 {
-    double aug[FR_TU][2 * FR_TU];
-    if (n > FR_TU) return -1;
+    double aug[FR_YU][2 * FR_YU];
+    if (n > FR_YU) return -1;
     for (int i = 0; i < n; i++)
         for (int j = 0; j < 2 * n; j++) aug[i][j] = j < n ? a[i * n + j] : (j - n == i ? 1.0 : 0.0);
     for (int c = 0; c < n; c++) {
@@ -403,6 +403,7 @@ int tet3d(Tet3D &T)
     const double nrm[4][3] = {{0, 0, -1}, {0, -1, 0}, {-1, 0, 0}, {r3, r3, r3}};
     const double dS[4] = {1.0, 1.0, 1.0, std::sqrt(3.0)};
     std::memcpy(T.nf, nrm, sizeof nrm);
+    for (int f = 0; f <= 4; f++) T.foff[f] = 10 * f;
     for (int f = 0; f < 4; f++)
         for (int t = 0; t < 10; t++) {
             const double s = P.xt[t][0], u = P.xt[t][1];
@@ -520,6 +521,196 @@ int tet3d(Tet3D &T)
                 double c = 0;
                 for (int s = 0; s < FR_TF; s++) c += T.L[z][s] * nrm[s / 10][d] * T.M0[s][j];
                 T.Dh[d][z][j] = T.D[d][z][j] - c;
+            }
+    return 0;
+}
+
+// Generator g_ijk = a^i b^j (1-c)^max(i,j) c^k of the pyramid space (a = 2x/(1-z), b = 2y/(1-z),
+// c = z) and its (x, y, z) gradient; ordered by max(i,j), then k, then j, then i (30 at order 3).
+static void pyr_generators(const double *X, double *g, double (*dg)[FR_YU])
+{
+    const double om = 1.0 - X[2], a = 2.0 * X[0] / om, b = 2.0 * X[1] / om, c = X[2];
+    int n = 0;
+    for (int mm = 0; mm <= 3; mm++)
+        for (int k = 0; k <= 3 - mm; k++)
+            for (int j = 0; j <= mm; j++)
+                for (int i = 0; i <= mm; i++) {
+                    if ((i > j ? i : j) != mm) continue;
+                    const double ai = std::pow(a, i), bj = std::pow(b, j), cm = std::pow(om, mm), ck = std::pow(c, k);
+                    g[n] = ai * bj * cm * ck;
+                    if (dg) {
+                        const double ga = i ? i * std::pow(a, i - 1) * bj * cm * ck : 0.0;
+                        const double gb = j ? j * ai * std::pow(b, j - 1) * cm * ck : 0.0;
+                        double gc = (mm ? -mm * ai * bj * std::pow(om, mm - 1) * ck : 0.0) + (k ? ai * bj * cm * k * std::pow(c, k - 1) : 0.0);
+                        dg[0][n] = 2.0 * ga / om;
+                        dg[1][n] = 2.0 * gb / om;
+                        dg[2][n] = (a * ga + b * gb) / om + gc;
+                    }
+                    n++;
+                }
+}
+
+int pyr3d(Pyr3D &P)
+{
+    std::memset(&P, 0, sizeof(P));
+    constexpr int NU = FR_YU, NF = FR_YF;
+    // solution points: the order-3 pyramid lattice (layer k at z = -1 + 2k/3 holds (4-k)^2 points at
+    // x, y = (1 - k/3)(-1 + 2i/(3-k))), shrunk by 4/5 towards (0, 0, -1/2); i fastest, then j, then k
+    int n = 0;
+    for (int k = 0; k <= 3; k++) {
+        const int m = 3 - k;
+        const double z = -1.0 + 2.0 * k / 3.0, h = 1.0 - k / 3.0;
+        for (int j = 0; j <= m; j++)
+            for (int i = 0; i <= m; i++) {
+                const double x = m ? h * (-1.0 + 2.0 * i / m) : 0.0, y = m ? h * (-1.0 + 2.0 * j / m) : 0.0;
+                P.x[n][0] = 0.8 * x; P.x[n][1] = 0.8 * y; P.x[n][2] = -0.5 + 0.8 * (z + 0.5);
+                n++;
+            }
+    }
+    // faces: the base (4 x 4 GL points, a + 4 b) and four triangles (the printed triangle points)
+    Prism2D Pr;
+    if (prism2d(Pr)) return -1;
+    const double r5 = 1.0 / std::sqrt(5.0);
+    const double nrm[5][3] = {{0, 0, -1}, {0, -2 * r5, r5}, {2 * r5, 0, r5}, {0, 2 * r5, r5}, {-2 * r5, 0, r5}};
+    std::memcpy(P.nf, nrm, sizeof nrm);
+    P.foff[0] = 0;
+    P.foff[1] = 16;
+    for (int f = 2; f <= 5; f++) P.foff[f] = 16 + 10 * (f - 1);
+    static const double tri[4][3][3] = {{{-1, -1, -1}, {1, -1, -1}, {0, 0, 1}},
+                                        {{1, -1, -1}, {1, 1, -1}, {0, 0, 1}},
+                                        {{1, 1, -1}, {-1, 1, -1}, {0, 0, 1}},
+                                        {{-1, 1, -1}, {-1, -1, -1}, {0, 0, 1}}};
+    for (int b = 0; b < 4; b++)
+        for (int a = 0; a < 4; a++) {
+            P.xf[a + 4 * b][0] = Pr.z.x[a]; P.xf[a + 4 * b][1] = Pr.z.x[b]; P.xf[a + 4 * b][2] = -1.0;
+        }
+    for (int f = 0; f < 4; f++)
+        for (int t = 0; t < 10; t++) {
+            const double s = Pr.xt[t][0], u = Pr.xt[t][1];
+            const double l0 = -0.5 * (s + u), l1 = 0.5 * (1.0 + s), l2 = 0.5 * (1.0 + u);
+            for (int d = 0; d < 3; d++) P.xf[16 + 10 * f + t][d] = l0 * tri[f][0][d] + l1 * tri[f][1][d] + l2 * tri[f][2][d];
+        }
+    // collapsed rule: GL in a and b, the Gauss rule of (1-c)^2 in c; x = a(1-c)/2, y = b(1-c)/2
+    double ga[5], wa[5], gc[5], wc[5];
+    gauss_legendre(5, ga, wa);
+    if (gauss_weight_rule(5, 2, gc, wc)) return -2;
+    for (int ic = 0; ic < 5; ic++)
+        for (int ib = 0; ib < 5; ib++)
+            for (int ia = 0; ia < 5; ia++) {
+                const int q = ia + 5 * ib + 25 * ic;
+                P.xq[q][0] = 0.5 * ga[ia] * (1.0 - gc[ic]);
+                P.xq[q][1] = 0.5 * ga[ib] * (1.0 - gc[ic]);
+                P.xq[q][2] = gc[ic];
+                P.wq[q] = wa[ia] * wa[ib] * wc[ic] / 4.0;
+            }
+    // nodal basis from the generators' Vandermonde matrix: l_z = sum_k g_k C[k][z]
+    double C[NU * NU];
+    for (int z = 0; z < NU; z++) pyr_generators(P.x[z], &C[z * NU], nullptr);
+    if (invert_n(NU, C)) return -3;
+    auto nodal = [&](const double *X, double *l, double (*dl)[NU]) {
+        double g[NU], dg[3][NU];
+        pyr_generators(X, g, dl ? dg : nullptr);
+        for (int z = 0; z < NU; z++) {
+            double v = 0, g0 = 0, g1 = 0, g2 = 0;
+            for (int kk = 0; kk < NU; kk++) {
+                const double c = C[kk * NU + z];
+                v += g[kk] * c;
+                if (dl) { g0 += dg[0][kk] * c; g1 += dg[1][kk] * c; g2 += dg[2][kk] * c; }
+            }
+            l[z] = v;
+            if (dl) { dl[0][z] = g0; dl[1][z] = g1; dl[2][z] = g2; }
+        }
+    };
+    static double dq[3][FR_TQ][NU];   // derivatives of the nodal basis at the quadrature points
+    for (int q = 0; q < FR_TQ; q++) {
+        double dl[3][NU];
+        nodal(P.xq[q], P.B[q], dl);
+        for (int d = 0; d < 3; d++)
+            for (int z = 0; z < NU; z++) dq[d][q][z] = dl[d][z];
+    }
+    for (int s = 0; s < NF; s++) nodal(P.xf[s], P.M0[s], nullptr);
+    // mass matrix (the rule is exact for the products), its inverse, point weights, projection
+    double M[NU * NU];
+    for (int z = 0; z < NU; z++) {
+        double wz = 0;
+        for (int q = 0; q < FR_TQ; q++) wz += P.wq[q] * P.B[q][z];
+        P.w[z] = wz;
+        for (int j = 0; j < NU; j++) {
+            double v = 0;
+            for (int q = 0; q < FR_TQ; q++) v += P.wq[q] * P.B[q][z] * P.B[q][j];
+            M[z * NU + j] = v;
+        }
+    }
+    if (invert_n(NU, M)) return -4;
+    for (int z = 0; z < NU; z++)
+        for (int q = 0; q < FR_TQ; q++) {
+            double v = 0;
+            for (int j = 0; j < NU; j++) v += M[z * NU + j] * P.B[q][j];
+            P.Pj[z][q] = v * P.wq[q];
+        }
+    // derivative: the L2 projection of the exact derivative, D_d = Pj (d_d l_j at the quadrature points)
+    for (int d = 0; d < 3; d++)
+        for (int z = 0; z < NU; z++)
+            for (int j = 0; j < NU; j++) {
+                double v = 0;
+                for (int q = 0; q < FR_TQ; q++) v += P.Pj[z][q] * dq[d][q][j];
+                P.D[d][z][j] = v;
+            }
+    // lift: E = M0_f^T W_f on the base (the 4 x 4 GL rule is exact for the Q_3 traces' products)
+    // and dS_f M0_f^T Mf on the triangles (face mass matrix of the triangle's nodal basis,
+    // dS = sqrt(5)/2); L = M^-1 E
+    double Mf[10][10];
+    {
+        double Vt[10 * 10];
+        auto mono2 = [](double x, double y, double *mm) {
+            int kk = 0;
+            for (int d = 0; d <= 3; d++)
+                for (int j = 0; j <= d; j++) mm[kk++] = std::pow(x, d - j) * std::pow(y, j);
+        };
+        for (int t = 0; t < 10; t++) mono2(Pr.xt[t][0], Pr.xt[t][1], &Vt[t * 10]);
+        if (invert_n(10, Vt)) return -5;
+        for (int t = 0; t < 10; t++)
+            for (int u = 0; u < 10; u++) Mf[t][u] = 0.0;
+        for (int q = 0; q < FR_PQ; q++) {
+            double mm[10], l[10];
+            mono2(Pr.xq[q][0], Pr.xq[q][1], mm);
+            for (int t = 0; t < 10; t++) {
+                double v = 0;
+                for (int kk = 0; kk < 10; kk++) v += mm[kk] * Vt[kk * 10 + t];
+                l[t] = v;
+            }
+            for (int t = 0; t < 10; t++)
+                for (int u = 0; u < 10; u++) Mf[t][u] += Pr.wq[q] * l[t] * l[u];
+        }
+    }
+    static double E[NU][NF];
+    const double dst = 0.5 * std::sqrt(5.0);
+    for (int z = 0; z < NU; z++) {
+        for (int b = 0; b < 4; b++)
+            for (int a = 0; a < 4; a++) E[z][a + 4 * b] = P.M0[a + 4 * b][z] * Pr.z.w[a] * Pr.z.w[b];
+        for (int f = 0; f < 4; f++)
+            for (int t = 0; t < 10; t++) {
+                double e = 0;
+                for (int tp = 0; tp < 10; tp++) e += P.M0[16 + 10 * f + tp][z] * Mf[tp][t];
+                E[z][16 + 10 * f + t] = dst * e;
+            }
+    }
+    for (int z = 0; z < NU; z++)
+        for (int s = 0; s < NF; s++) {
+            double v = 0;
+            for (int j = 0; j < NU; j++) v += M[z * NU + j] * E[j][s];
+            P.L[z][s] = v;
+        }
+    // corrected derivative
+    for (int d = 0; d < 3; d++)
+        for (int z = 0; z < NU; z++)
+            for (int j = 0; j < NU; j++) {
+                double c = 0;
+                for (int s = 0; s < NF; s++) {
+                    const int f = s < 16 ? 0 : 1 + (s - 16) / 10;
+                    c += P.L[z][s] * nrm[f][d] * P.M0[s][j];
+                }
+                P.Dh[d][z][j] = P.D[d][z][j] - c;
             }
     return 0;
 }

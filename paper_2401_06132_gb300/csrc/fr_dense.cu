@@ -1,19 +1,21 @@
-// fr_tet.cu -- tetrahedral kernels (p = 3) of the anti-aliased Navier-Stokes FR right-hand side.
+// fr_dense.cu -- kernels of the anti-aliased Navier-Stokes FR right-hand side for element types
+// without tensor-product structure (p = 3): tetrahedra and pyramids.
 //
-// A tetrahedron has no tensor-product structure, so every operator is a dense matrix applied per
-// element (Sec. 1; sum factorisation, Sec. 4, serves hexahedra and prisms only): 20 solution points,
-// 4 faces x 10 flux points, 125 quadrature points. Same three fused phases as the other types:
-// A face solution, B volume group, C interface group. The volume group evaluates, per element, the
-// con_u average, the corrected gradient (Dh_d u plus the face lift of the common solution, then
-// J^-T), the own-normal viscous flux at the flux points whose LDG weight is not zero, the
-// interpolation of the 20 fields (u and its gradient) to the quadrature points, the pointwise flux
-// and its transformation det J J^-1 f, and the L2 projection with the corrected divergence folded
-// in (R~ = sum_d (Dh_d Pj) f~_d: one dense 20 x 125 operator per direction).
+// Sum factorisation (Sec. 4) serves hexahedra and prisms only; for tetrahedra and pyramids (Sec. 1)
+// every operator is a dense matrix applied per element: NU solution points (20 / 30), NF flux points
+// on NFACE faces (4 x 10 / a 16-point base and 4 x 10), 125 quadrature points. Same three fused
+// phases as the other types: A face solution, B volume group, C interface group. The volume group
+// evaluates, per element, the con_u average, the corrected gradient (Dh_d u plus the face lift of the
+// common solution, then J^-T), the own-normal viscous flux at the flux points whose LDG weight is not
+// zero, the interpolation of the 20 fields (u and its gradient) to the quadrature points, the
+// pointwise flux and its transformation det J J^-1 f, and the L2 projection with the corrected
+// divergence folded in (R~ = sum_d (Dh_d Pj) f~_d: one dense NU x 125 operator per direction).
 //
-// The operator tables (TetOps, 100 KB in FP64) stay in global memory, read through the L1/L2
-// caches; they are stored with the output index fastest, so that a warp's lanes, which compute
+// The operator tables (DenseOps: 100 KB / 160 KB in FP64) stay in global memory, read through the
+// L1/L2 caches; they are stored with the output index fastest, so that a warp's lanes, which compute
 // consecutive outputs, read consecutive entries while the field values they multiply are one
-// shared-memory broadcast per warp.
+// shared-memory broadcast per warp (16-byte vector loads along the solution-point index, whose rows
+// are padded to NUS with zero operator rows).
 #include <cuda_runtime.h>
 
 #include "fr_internal.h"
@@ -21,9 +23,7 @@
 
 namespace {
 
-constexpr int NU = FR_TU, NF = FR_TF, NQ = FR_TQ, NQP = FR_TQP;
-
-__device__ __forceinline__ int face_of(int s) { return s / 10; }
+constexpr int NQ = FR_TQ, NQP = FR_TQP;
 
 // 16 bytes of T (4 floats or 2 doubles): one vector shared-memory load
 template <typename T>
@@ -40,9 +40,10 @@ __device__ __forceinline__ V16<T> ld16(const T *p)
 // -------------------------------------------------------------------------------------------------
 // Phase A: disu (U^f = M0 U)
 // -------------------------------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_tet_disu(HexArgs<T> a, const TetOps<T> *__restrict__ op)
+template <typename T, typename OPS>
+__global__ void __launch_bounds__(256) k_dense_disu(HexArgs<T> a, const OPS *__restrict__ op)
 {
+    constexpr int NU = OPS::NU, NF = OPS::NF;
     const long long total = a.ne * FR_NV * NF;
     for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
         const int s = (int)(it % NF);
@@ -60,30 +61,35 @@ __global__ void __launch_bounds__(256) k_tet_disu(HexArgs<T> a, const TetOps<T> 
 // -------------------------------------------------------------------------------------------------
 // Phase B: volume group, one element per CTA of NTH threads (persistent over elements)
 // -------------------------------------------------------------------------------------------------
-template <typename T, int NTH>
-__global__ void __launch_bounds__(NTH) k_tet_B(HexArgs<T> a, const TetOps<T> *__restrict__ op)
+template <typename T, int NTH, typename OPS>
+__global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__restrict__ op)
 {
+    constexpr int NU = OPS::NU, NF = OPS::NF, NFACE = OPS::NFACE, NUS = OPS::NUS;
     static_assert(NTH >= NQ, "one thread per quadrature point");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ short s_plist[NF];
     __shared__ int s_pcnt;
     constexpr int VW = V16<T>::n;
-    constexpr int NCH = 6;                        // quadrature-point chunks of the projection
-    T *s_u = reinterpret_cast<T *>(smem_raw);   // [5][NU] state
-    T *s_q = s_u + 5 * NU;                        // [15][NU] physical gradient (field 5 + 3 alpha + d of s_u)
-    T *s_c = s_q + 15 * NU;                       // [5][NF] common solution
+    constexpr int NCH = NTH / NU;                 // quadrature-point chunks of the projection
+    T *s_u = reinterpret_cast<T *>(smem_raw);   // [5][NUS] state
+    T *s_q = s_u + 5 * NUS;                       // [15][NUS] physical gradient (field 5 + 3 alpha + d of s_u)
+    T *s_c = s_q + 15 * NUS;                      // [5][NF] common solution
     T *s_w = s_c + 5 * NF;                        // [20][NQP] fields at quadrature points, then f~
-    T *s_red = s_u;                               // [NCH][5][NU] projection partial sums (s_u, s_q, s_c are dead by then)
-    static_assert(NCH * 5 * NU <= 20 * NU + 5 * NF, "partial sums fit in the state, gradient and common-solution arrays");
-    static_assert(NU % VW == 0 && (NU * sizeof(T)) % 16 == 0 && (NQP * sizeof(T)) % 16 == 0, "16-byte rows");
-    // the pad columns q = NQ .. NQP-1 of s_w meet zero operator rows; they stay zero
+    T *s_red = s_w + 15 * NQP;                    // [NCH][5][NU] projection partial sums (fields 15-19 are dead by then)
+    static_assert(NCH * 5 * NU <= 5 * NQP, "partial sums fit in the dead quadrature-point rows");
+    static_assert(NUS % VW == 0 && (NUS * sizeof(T)) % 16 == 0 && (NQP * sizeof(T)) % 16 == 0 && (NF * sizeof(T)) % 16 == 0,
+                  "16-byte rows");
+    // pads that meet zero operator rows in the vector loads stay zero: s_w columns NQ.. and the
+    // solution-point columns NU.. of the 20 fields
     for (int it = threadIdx.x; it < 20 * (NQP - NQ); it += NTH) s_w[(it / (NQP - NQ)) * NQP + NQ + it % (NQP - NQ)] = T(0);
+    if constexpr (NUS > NU)
+        for (int it = threadIdx.x; it < 20 * (NUS - NU); it += NTH) s_u[(it / (NUS - NU)) * NUS + NU + it % (NUS - NU)] = T(0);
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
         const Geo<T> g = a.geo[e];
         const Phys<T> ph = elem_phys(a, e);
         const T *U = a.U + elem_u0(a, e, NU);
         const long long gf0 = elem_f0(a, e, NF);
-        for (int it = threadIdx.x; it < 5 * NU; it += NTH) s_u[it] = U[it];
+        for (int it = threadIdx.x; it < 5 * NU; it += NTH) s_u[(it / NU) * NUS + it % NU] = U[it];
         if (threadIdx.x == 0) s_pcnt = 0;
         for (int it = threadIdx.x; it < 5 * NF; it += NTH) {   // con_u
             const int alpha = it / NF, s = it % NF;
@@ -98,7 +104,7 @@ __global__ void __launch_bounds__(NTH) k_tet_B(HexArgs<T> a, const TetOps<T> *__
         // corrected gradient q~_d = Dh_d u + sum_f n_f,d (L_f c), then q = J^-T q~
         for (int it = threadIdx.x; it < 5 * NU; it += NTH) {
             const int alpha = it / NU, z = it % NU;
-            const T *u = s_u + alpha * NU;
+            const T *u = s_u + alpha * NUS;
             const T *c = s_c + alpha * NF;
             T q0 = T(0), q1 = T(0), q2 = T(0);
 #pragma unroll 4
@@ -109,16 +115,15 @@ __global__ void __launch_bounds__(NTH) k_tet_B(HexArgs<T> a, const TetOps<T> *__
                 q2 += op->Dht[2][j][z] * uj;
             }
 #pragma unroll
-            for (int f = 0; f < 4; f++) {
+            for (int f = 0; f < NFACE; f++) {
                 T l = T(0);
-#pragma unroll
-                for (int t = 0; t < 10; t++) l += op->Lt[10 * f + t][z] * c[10 * f + t];
+                for (int s = op->foff[f]; s < op->foff[f + 1]; s++) l += op->Lt[s][z] * c[s];
                 q0 += op->nf[f][0] * l;
                 q1 += op->nf[f][1] * l;
                 q2 += op->nf[f][2] * l;
             }
 #pragma unroll
-            for (int k = 0; k < 3; k++) s_q[(alpha * 3 + k) * NU + z] = g.Ji[k] * q0 + g.Ji[3 + k] * q1 + g.Ji[6 + k] * q2;
+            for (int k = 0; k < 3; k++) s_q[(alpha * 3 + k) * NUS + z] = g.Ji[k] * q0 + g.Ji[3 + k] * q1 + g.Ji[6 + k] * q2;
         }
         __syncthreads();
         // viscous normal flux at own flux points, on the side whose LDG weight 1/2 +- beta is not
@@ -141,13 +146,13 @@ __global__ void __launch_bounds__(NTH) k_tet_B(HexArgs<T> a, const TetOps<T> *__
 #pragma unroll
             for (int f = 0; f < 20; f++) v[f] = T(0);
 #pragma unroll 1
-            for (int z0 = 0; z0 < NU; z0 += VW) {
+            for (int z0 = 0; z0 < NUS; z0 += VW) {
                 T m[VW];
 #pragma unroll
                 for (int k = 0; k < VW; k++) m[k] = op->M0t[z0 + k][s];
 #pragma unroll
                 for (int f = 0; f < 20; f++) {
-                    const V16<T> x = ld16(s_u + f * NU + z0);
+                    const V16<T> x = ld16(s_u + f * NUS + z0);
 #pragma unroll
                     for (int k = 0; k < VW; k++) v[f] += m[k] * x.v[k];
                 }
@@ -159,7 +164,7 @@ __global__ void __launch_bounds__(NTH) k_tet_B(HexArgs<T> a, const TetOps<T> *__
 #pragma unroll
                 for (int d = 0; d < 3; d++) qf[alpha][d] = v[5 + alpha * 3 + d];
             }
-            const T *nt = a.fnrm + (e * 6 + face_of(s)) * 4;
+            const T *nt = a.fnrm + (e * 6 + op->fidx[s]) * 4;
             T n[3] = {nt[0], nt[1], nt[2]};
             T fvn[4];
             viscous_normal_flux(ph, uf, qf, n, fvn);
@@ -172,13 +177,13 @@ __global__ void __launch_bounds__(NTH) k_tet_B(HexArgs<T> a, const TetOps<T> *__
 #pragma unroll
             for (int f = 0; f < 20; f++) v[f] = T(0);
 #pragma unroll 1
-            for (int j0 = 0; j0 < NU; j0 += VW) {
+            for (int j0 = 0; j0 < NUS; j0 += VW) {
                 T b[VW];
 #pragma unroll
                 for (int k = 0; k < VW; k++) b[k] = op->Bt[j0 + k][q];
 #pragma unroll
                 for (int f = 0; f < 20; f++) {
-                    const V16<T> x = ld16(s_u + f * NU + j0);
+                    const V16<T> x = ld16(s_u + f * NUS + j0);
 #pragma unroll
                     for (int k = 0; k < VW; k++) v[f] += b[k] * x.v[k];
                 }
@@ -250,9 +255,10 @@ __global__ void __launch_bounds__(NTH) k_tet_B(HexArgs<T> a, const TetOps<T> *__
 // -------------------------------------------------------------------------------------------------
 // Phase C: interface group (common flux at every own flux point, lift and scale)
 // -------------------------------------------------------------------------------------------------
-template <typename T, int NTH>
-__global__ void __launch_bounds__(NTH) k_tet_C(HexArgs<T> a, const TetOps<T> *__restrict__ op)
+template <typename T, int NTH, typename OPS>
+__global__ void __launch_bounds__(NTH) k_dense_C(HexArgs<T> a, const OPS *__restrict__ op)
 {
+    constexpr int NU = OPS::NU, NF = OPS::NF;
     __shared__ T s_d[5 * NF];
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
         const Geo<T> g = a.geo[e];
@@ -268,7 +274,7 @@ __global__ void __launch_bounds__(NTH) k_tet_C(HexArgs<T> a, const TetOps<T> *__
             for (int k = 0; k < 5; k++) { uo[k] = a.UF[k * a.nfpt + og]; up[k] = a.UF[k * a.nfpt + pg]; }
 #pragma unroll
             for (int k = 0; k < 4; k++) { fvo[k] = a.FV[k * a.nfpt + og]; fvp[k] = a.FV[k * a.nfpt + pg]; }
-            const T *nt = a.fnrm + (e * 6 + face_of(s)) * 4;
+            const T *nt = a.fnrm + (e * 6 + op->fidx[s]) * 4;
             const T mag = nt[3];
             T nL[3] = {isL ? nt[0] : -nt[0], isL ? nt[1] : -nt[1], isL ? nt[2] : -nt[2]};
             T F[5];
@@ -301,31 +307,47 @@ int grid_elems(long long ne, int per_sm)
     return (int)(g < 1 ? 1 : g);
 }
 
-}  // namespace
-
-template <typename T>
-int tet_fused_phase(int phase, const HexArgs<T> &a, const TetOps<T> *ops, cudaStream_t s)
+template <typename T, typename OPS>
+int dense_phase(int phase, const HexArgs<T> &a, const OPS *ops, cudaStream_t s)
 {
+    constexpr int NU = OPS::NU, NF = OPS::NF, NUS = OPS::NUS;
     if (a.ne == 0) return 0;
     if (phase == 0) {
         long long work = a.ne * FR_NV * NF;
         long long g = (work + 255) / 256;
         if (g > 152LL * 64) g = 152LL * 64;
-        k_tet_disu<T><<<(int)g, 256, 0, s>>>(a, ops);
+        k_dense_disu<T, OPS><<<(int)g, 256, 0, s>>>(a, ops);
     } else if (phase == 1) {
         constexpr int NTH = 128;
-        const size_t smem = (size_t)(5 * NU + 15 * NU + 5 * NF + 20 * NQP) * sizeof(T);
+        const size_t smem = (size_t)(20 * NUS + 5 * NF + 20 * NQP) * sizeof(T);
         static bool attr = false;
         if (!attr) {
-            cudaFuncSetAttribute(k_tet_B<T, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_dense_B<T, NTH, OPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             attr = true;
         }
-        k_tet_B<T, NTH><<<grid_elems(a.ne, 8), NTH, smem, s>>>(a, ops);
+        k_dense_B<T, NTH, OPS><<<grid_elems(a.ne, 8), NTH, smem, s>>>(a, ops);
     } else {
-        k_tet_C<T, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a, ops);
+        k_dense_C<T, 128, OPS><<<grid_elems(a.ne, 8), 128, 0, s>>>(a, ops);
     }
+    (void)NU;
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace
+
+template <typename T>
+int tet_fused_phase(int phase, const HexArgs<T> &a, const TetOps<T> *ops, cudaStream_t s)
+{
+    return dense_phase<T, TetOps<T>>(phase, a, ops, s);
+}
+
+template <typename T>
+int pyr_fused_phase(int phase, const HexArgs<T> &a, const PyrOps<T> *ops, cudaStream_t s)
+{
+    return dense_phase<T, PyrOps<T>>(phase, a, ops, s);
 }
 
 template int tet_fused_phase<double>(int, const HexArgs<double> &, const TetOps<double> *, cudaStream_t);
 template int tet_fused_phase<float>(int, const HexArgs<float> &, const TetOps<float> *, cudaStream_t);
+template int pyr_fused_phase<double>(int, const HexArgs<double> &, const PyrOps<double> *, cudaStream_t);
+template int pyr_fused_phase<float>(int, const HexArgs<float> &, const PyrOps<float> *, cudaStream_t);

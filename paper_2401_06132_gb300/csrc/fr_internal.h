@@ -55,28 +55,45 @@ struct Prism2D {
 };
 int prism2d(Prism2D &P);
 
-// Tetrahedron of order 3 with dense operators (Sec. 1: tetrahedra use no sum factorisation):
-// 20 solution points (the order-3 equispaced lattice shrunk by 4/5 towards the centroid), 4 faces x
-// 10 flux points (the paper's printed Williams-Shunn triangle points), 125 collapsed Gauss-Jacobi
-// quadrature points (exact to total degree 9). Faces: 0 z = -1, 1 y = -1, 2 x = -1, 3 x+y+z = -1.
-#define FR_TU 20      // solution points
-#define FR_TF 40      // flux points
+// Element types without tensor-product structure (Sec. 1: tetrahedra and pyramids use no sum
+// factorisation), order 3, with dense per-element operators: NU solution points, NF flux points on
+// NFACE faces (face f holds points foff[f] .. foff[f+1]-1), 125 collapsed Gauss-Jacobi quadrature
+// points (exact to total degree 9).
+//   tetrahedron: 20 solution points (the order-3 equispaced lattice shrunk by 4/5 towards the
+//     centroid), 4 faces x 10 flux points (the paper's printed Williams-Shunn triangle points);
+//     faces 0 z = -1, 1 y = -1, 2 x = -1, 3 x+y+z = -1.
+//   pyramid (base [-1,1]^2 at z = -1, apex (0,0,1)): the rational pyramid space (Q_3 traces on the
+//     base, P_3 on the triangles), 30 solution points (the order-3 pyramid lattice shrunk by 4/5
+//     towards the centroid (0,0,-1/2)), base 4 x 4 GL flux points (a + 4 b) then 4 triangles x 10
+//     Williams-Shunn points; faces 0 base, 1 y = -(1-z)/2, 2 x = (1-z)/2, 3 y = (1-z)/2,
+//     4 x = -(1-z)/2. Its derivative operator is the L2 projection of the exact derivative (the
+//     rational space is not closed under differentiation).
 #define FR_TQ 125     // quadrature points
 #define FR_TQP 128    // quadrature points padded to whole 16-byte vectors (the pad rows are zero)
-struct Tet3D {
-    double x[FR_TU][3];            // solution points (reference coordinates)
-    double w[FR_TU];               // int l_z over the reference tetrahedron
-    double xf[FR_TF][3];           // flux points; face f holds points 10 f .. 10 f + 9
-    double nf[4][3];               // unit outward reference normals
+template <int NU_, int NF_, int NFACE_>
+struct DenseRef {
+    static constexpr int NU = NU_, NF = NF_, NFACE = NFACE_;
+    double x[NU][3];               // solution points (reference coordinates)
+    double w[NU];                  // int l_z over the reference element
+    double xf[NF][3];              // flux points
+    double nf[NFACE][3];           // unit outward reference normals
+    int foff[NFACE + 1];           // first flux point of each face
     double xq[FR_TQ][3], wq[FR_TQ];
-    double B[FR_TQ][FR_TU];        // interpolation to quadrature points (M7)
-    double M0[FR_TF][FR_TU];       // interpolation to flux points
-    double D[3][FR_TU][FR_TU];     // D[d][z][j] = d l_j / dX_d at x_z
-    double L[FR_TU][FR_TF];        // DG-equivalent lift M^-1 E
-    double Dh[3][FR_TU][FR_TU];    // D_d - L diag(n_d) M0: the operator of M4 - M6 M0 and of M1 - M3 M2
-    double Pj[FR_TU][FR_TQ];       // L2 projection (M8)
+    double B[FR_TQ][NU];           // interpolation to quadrature points (M7)
+    double M0[NF][NU];             // interpolation to flux points
+    double D[3][NU][NU];           // D[d][z][j]: derivative of l_j at x_z (projected on the pyramid)
+    double L[NU][NF];              // DG-equivalent lift M^-1 E
+    double Dh[3][NU][NU];          // D_d - L diag(n_d) M0: the operator of M4 - M6 M0 and of M1 - M3 M2
+    double Pj[NU][FR_TQ];          // L2 projection (M8)
 };
+using Tet3D = DenseRef<20, 40, 4>;
+using Pyr3D = DenseRef<30, 56, 5>;
+#define FR_TU 20      // tetrahedron solution points
+#define FR_TF 40      // tetrahedron flux points
+#define FR_YU 30      // pyramid solution points
+#define FR_YF 56      // pyramid flux points
 int tet3d(Tet3D &T);
+int pyr3d(Pyr3D &P);
 
 }  // namespace frb
 
@@ -107,17 +124,23 @@ struct PriOps {
     T lzL[FR_PE], lzR[FR_PE], liftzL[FR_PE], liftzR[FR_PE];
 };
 
-// Tetrahedron (p = 3) operator tables, transposed so that the output index runs fastest (a warp's
-// lanes compute consecutive outputs and read consecutive entries).
-template <typename T>
-struct TetOps {
-    T Bt[FR_TU][FR_TQ];            // B^T: [j][q]
-    T M0t[FR_TU][FR_TF];           // M0^T: [z][s]
-    T Dht[3][FR_TU][FR_TU];        // [d][j][z] = Dh[d][z][j]
-    T Lt[FR_TF][FR_TU];            // [s][z] = L[z][s]
-    T Dvt[3][FR_TQP][FR_TU];       // (Dh_d Pj)^T: projection with the corrected divergence, [d][q][z]
-    T nf[4][3];
+// Dense-element (p = 3) operator tables, transposed so that the output index runs fastest (a warp's
+// lanes compute consecutive outputs and read consecutive entries). Rows of the solution-point index
+// are padded to NUS (a multiple of 4) for 16-byte vector loads; the pad rows are zero.
+template <typename T, int NU_, int NF_, int NFACE_>
+struct DenseOps {
+    static constexpr int NU = NU_, NF = NF_, NFACE = NFACE_, NUS = (NU_ + 3) / 4 * 4;
+    T Bt[NUS][FR_TQ];              // B^T: [j][q]
+    T M0t[NUS][NF];                // M0^T: [z][s]
+    T Dht[3][NU][NU];              // [d][j][z] = Dh[d][z][j]
+    T Lt[NF][NU];                  // [s][z] = L[z][s]
+    T Dvt[3][FR_TQP][NU];          // (Dh_d Pj)^T: projection with the corrected divergence, [d][q][z]
+    T nf[NFACE][3];
+    int foff[NFACE + 1];
+    unsigned char fidx[NF];        // face of each flux point
 };
+template <typename T> using TetOps = DenseOps<T, 20, 40, 4>;
+template <typename T> using PyrOps = DenseOps<T, 30, 56, 5>;
 
 // Prism operators as float-float pairs: value = hi + lo (the low-Mach mass channel).
 struct PriOpsFF {
@@ -146,7 +169,7 @@ struct Geo {
 // One block of elements of one type and order inside one instance.
 struct Block {
     int inst;                 // instance index
-    int type;                 // 0 hex, 1 prism, 2 tetrahedron
+    int type;                 // 0 hex, 1 prism, 2 tetrahedron, 3 pyramid
     int p, m;                 // order, 1D quadrature points
     int nu, nf;               // points per element, flux points per element
     long long ne;             // elements
@@ -271,5 +294,6 @@ int hex_upload_ops(int p, int m, const frb::Hex1D &h);
 // Prism kernels (fr_pri.cu); the operator tables are passed by device pointer (opsff: the
 // float-float table of the low-Mach FP32 form's mass channel; null otherwise).
 template <typename T> int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, const PriOpsFF *opsff, cudaStream_t s);
-// Tetrahedral kernels (fr_tet.cu), operator table by device pointer.
+// Dense-element kernels (fr_dense.cu): tetrahedra and pyramids, operator table by device pointer.
 template <typename T> int tet_fused_phase(int phase, const HexArgs<T> &a, const TetOps<T> *ops, cudaStream_t s);
+template <typename T> int pyr_fused_phase(int phase, const HexArgs<T> &a, const PyrOps<T> *ops, cudaStream_t s);

@@ -37,7 +37,7 @@ class Params(C.Structure):
 class MeshDesc(C.Structure):
     _fields_ = [("n_hex", C.c_int), ("n_pri", C.c_int), ("n_verts", C.c_int), ("verts", C.POINTER(C.c_double)),
                 ("hex_v", C.POINTER(C.c_int)), ("pri_v", C.POINTER(C.c_int)), ("period", C.c_double * 3),
-                ("n_tet", C.c_int), ("tet_v", C.POINTER(C.c_int))]
+                ("n_tet", C.c_int), ("tet_v", C.POINTER(C.c_int)), ("n_pyr", C.c_int), ("pyr_v", C.POINTER(C.c_int))]
 
 
 _lib = None
@@ -116,11 +116,13 @@ class FRMesh:
             hex_v = np.ascontiguousarray(m.get("hex_v", np.zeros((0, 8))), dtype=np.int32)
             pri_v = np.ascontiguousarray(m.get("pri_v", np.zeros((0, 6))), dtype=np.int32)
             tet_v = np.ascontiguousarray(m.get("tet_v", np.zeros((0, 4))), dtype=np.int32)
-            self._keep += [verts, hex_v, pri_v, tet_v]
+            pyr_v = np.ascontiguousarray(m.get("pyr_v", np.zeros((0, 5))), dtype=np.int32)
+            self._keep += [verts, hex_v, pri_v, tet_v, pyr_v]
             ip = C.POINTER(C.c_int)
             d = MeshDesc(hex_v.shape[0], pri_v.shape[0], verts.shape[0], verts.ctypes.data_as(C.POINTER(C.c_double)),
                          hex_v.ctypes.data_as(ip), pri_v.ctypes.data_as(ip),
-                         (C.c_double * 3)(*m.get("period", (0.0, 0.0, 0.0))), tet_v.shape[0], tet_v.ctypes.data_as(ip))
+                         (C.c_double * 3)(*m.get("period", (0.0, 0.0, 0.0))), tet_v.shape[0], tet_v.ctypes.data_as(ip),
+                         pyr_v.shape[0], pyr_v.ctypes.data_as(ip))
             descs.append(d)
         arr = (C.POINTER(MeshDesc) * len(descs))(*[C.pointer(d) for d in descs])
         self._descs = descs

@@ -22,7 +22,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=16, help="elements per box edge")
     ap.add_argument("--p", type=int, default=3)
     ap.add_argument("--nq", type=int, default=0, help="1D quadrature points (0: p + 2; p + 1: no anti-aliasing)")
-    ap.add_argument("--mesh", default="hex", choices=["hex", "sheared", "mixed", "tet", "tetshear"])
+    ap.add_argument("--mesh", default="hex", choices=["hex", "sheared", "mixed", "tet", "tetshear", "pyr", "hexpyr"])
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "mixed_fp16", "mixed_bf16"])
     ap.add_argument("--lowmach", type=int, default=1, help="FP32 low-Mach form (rho_ref = 1)")
     ap.add_argument("--form", default="fused", choices=["fused", "unfused"])
@@ -41,7 +41,8 @@ def main(argv=None):
     from paper_2401_06132_gb300 import fr, workloads as W
 
     mesh = {"hex": W.box_hex_mesh, "sheared": W.sheared_box_mesh, "mixed": W.mixed_box_mesh, "tet": W.box_tet_mesh,
-            "tetshear": lambda n: W.box_tet_mesh(n, shear=True)}[args.mesh](args.n)
+            "tetshear": lambda n: W.box_tet_mesh(n, shear=True), "pyr": W.box_pyr_mesh,
+            "hexpyr": lambda n: W.box_pyr_mesh(n, hex_below=n // 2)}[args.mesh](args.n)
     p0 = W.tgv_p0(mach=args.mach)
     m = fr.FRMesh(mesh, fr.make_params(p=args.p, nq1d=args.nq, prec=args.prec, p_ref=p0,
                                        rho_ref=1.0 if args.lowmach else 0.0, surface_aa=bool(args.surf)))
@@ -54,6 +55,8 @@ def main(argv=None):
         blocks.append((mesh["pri_v"].shape[0], 40))
     if mesh.get("tet_v") is not None and mesh["tet_v"].shape[0]:
         blocks.append((mesh["tet_v"].shape[0], 20))
+    if mesh.get("pyr_v") is not None and mesh["pyr_v"].shape[0]:
+        blocks.append((mesh["pyr_v"].shape[0], 30))
     U0 = W.tgv_state(m.sol_coords(), blocks, mach=args.mach, perturb=1e-3)
     U = torch.from_numpy(U0.astype(np.float64 if args.prec == "fp64" else np.float32)).cuda()
     R = torch.empty_like(U)

@@ -627,8 +627,8 @@ TET_MESHES = {"tet1": lambda: W.box_tet_mesh(1), "tetshear2": lambda: W.box_tet_
               "tet4": lambda: W.box_tet_mesh(4)}
 
 
-def _tet_bound(mesh, U, nu):
-    """Parity bound for the dense tetrahedral operators: the oracle's own rounding level, measured as
+def _dense_bound(mesh, U, nu):
+    """Parity bound for the dense tetrahedral and pyramidal operators: the oracle's own rounding level, measured as
     the largest difference between its results for p_ref = 0, p0/2 and p0 (the same RHS in exact
     arithmetic: the reference pressure only moves a constant through the flux), doubled, and never
     below the hexahedral 1e-12. The oracle's dense per-element sums (125 quadrature points, then 60
@@ -658,7 +658,7 @@ def test_tet_rhs_fp64_matches_oracle(name, pref):
     m.rhs(Ud, Rd)
     m.sync_status()
     err = rel_linf(Rd.cpu().numpy(), Ro, nu)
-    bound, spread = _tet_bound(mesh, U, nu)
+    bound, spread = _dense_bound(mesh, U, nu)
     print(f"tet {name} pref={pref}: {err} (oracle spread {spread:.2e}, bound {bound:.2e})")
     assert err.max() <= bound and bound <= 3e-12, (err, bound)
 
@@ -739,7 +739,7 @@ def test_tet_full_size_sampled_against_oracle():
     m.rhs(Ud, Rd)
     m.sync_status()
     err = rel_linf(Rd.cpu().numpy(), Ro, nu)
-    bound, spread = _tet_bound(mesh, U, nu)
+    bound, spread = _dense_bound(mesh, U, nu)
     print(f"tet 16^3: {err} (oracle spread {spread:.2e}, bound {bound:.2e})")
     assert err.max() <= bound and bound <= 2e-11, (err, bound)
 
@@ -821,3 +821,113 @@ def test_curved_rk4_diagnostics_and_fp32():
     dr = np.abs(Ud.cpu().numpy() - Uo).max() / np.abs(Uo).max()
     print(f"curved fused RK4: {dr:.3e}")
     assert dr <= 1e-13, dr
+
+
+# ----------------------------------------------------------------------------------------------
+# Pyramids (dense per-element operators, rational pyramid space)
+# ----------------------------------------------------------------------------------------------
+
+PYR_MESHES = {"pyr1": lambda: W.box_pyr_mesh(1), "hexpyr2": lambda: W.box_pyr_mesh(2, hex_below=1),
+              "pyr3": lambda: W.box_pyr_mesh(3)}
+
+
+def _blocks(mesh):
+    out = []
+    if mesh["hex_v"].shape[0]:
+        out.append((mesh["hex_v"].shape[0], 64))
+    if mesh.get("pyr_v") is not None and mesh["pyr_v"].shape[0]:
+        out.append((mesh["pyr_v"].shape[0], 30))
+    return out
+
+
+def _rel_blocks(R, Ro, blocks):
+    err, off = np.zeros(5), 0
+    for ne, nu in blocks:
+        n = ne * 5 * nu
+        err = np.maximum(err, rel_linf(R[off:off + n], Ro[off:off + n], nu))
+        off += n
+    return err
+
+
+@pytest.mark.parametrize("name", list(PYR_MESHES))
+@pytest.mark.parametrize("pref", [0.0, 1.0])
+def test_pyr_rhs_fp64_matches_oracle(name, pref):
+    """Boxes of cells split into six pyramids each (6 self-periodic pyramids; a hexahedron/pyramid
+    mix whose pyramid bases meet hexahedral faces; 162 pyramids), p = 3, FP64 against the oracle
+    within the bound of _dense_bound."""
+    mesh = PYR_MESHES[name]()
+    blocks = _blocks(mesh)
+    p_ref = pref * W.tgv_p0()
+    o = O.Oracle(mesh, 3, 5, threads=NCPU, p_ref=p_ref)
+    U = W.tgv_state(o.sol_coords(), blocks, perturb=1e-2)
+    Ro = o.rhs(U)
+    m = fr.FRMesh(mesh, fr.make_params(p=3, p_ref=p_ref))
+    assert np.abs(m.sol_coords() - o.sol_coords()).max() < 1e-13
+    Ud = torch.from_numpy(U).cuda()
+    Rd = torch.empty_like(Ud)
+    m.rhs(Ud, Rd)
+    m.sync_status()
+    err = _rel_blocks(Rd.cpu().numpy(), Ro, blocks)
+    bound, spread = _dense_bound(mesh, U, blocks[-1][1]) if len(blocks) == 1 else (2e-12, 0.0)
+    print(f"pyr {name} pref={pref}: {err} (oracle spread {spread:.2e}, bound {bound:.2e})")
+    assert err.max() <= bound and bound <= 3e-12, (err, bound)
+
+
+def test_pyr_freestream_conservation_rk4_fp32():
+    """On 162 pyramids: a constant state gives a zero RHS; the weighted RHS sums vanish; 5 RK4 steps
+    (stage update folded into the interface kernel) match the oracle's; the plain FP32 kernels match
+    the oracle on the FP32-rounded input."""
+    mesh = W.box_pyr_mesh(3)
+    ne, nu = mesh["pyr_v"].shape[0], 30
+    p0 = W.tgv_p0()
+    m = fr.FRMesh(mesh, fr.make_params(p=3, p_ref=p0))
+    fs = np.array([1.1, 1.1 * 0.3, -1.1 * 0.2, 1.1 * 0.1, 1.0 / 0.4 + 0.5 * 1.1 * 0.14])
+    U = torch.from_numpy(np.tile(np.repeat(fs, nu), ne)).cuda()
+    R = torch.empty_like(U)
+    m.rhs(U, R)
+    m.sync_status()
+    assert R.abs().max().item() < 1e-11
+    o = O.Oracle(mesh, 3, 5, threads=NCPU, p_ref=p0)
+    U0 = W.tgv_state(o.sol_coords(), [(ne, nu)], perturb=1e-2)
+    U = torch.from_numpy(U0).cuda()
+    m.rhs(U, R)
+    d = m.diagnostics(U, R)[0]
+    do = o.diagnostics(U0, o.rhs(U0))
+    assert abs(d["volume"] / do["volume"] - 1) < 1e-13 and abs(d["eps"] / do["eps"] - 1) < 1e-7
+    assert np.all(np.abs(d["sums"]) <= 1e-11 * do["abs_sums"])
+    Uo = o.rk4(U0, 1e-3, 5)
+    m.rk4_step(U, 1e-3, 5)
+    m.sync_status()
+    dr = np.abs(U.cpu().numpy() - Uo).max() / np.abs(Uo).max()
+    print(f"pyr RK4: {dr:.3e}")
+    assert dr <= 1e-13, dr
+    U32 = U0.astype(np.float32)
+    Ro = o.rhs(U32.astype(np.float64))
+    m32 = fr.FRMesh(mesh, fr.make_params(p=3, prec="fp32", p_ref=p0))
+    Ud = torch.from_numpy(U32).cuda()
+    Rd = torch.empty_like(Ud)
+    m32.rhs(Ud, Rd)
+    m32.sync_status()
+    err = rel_linf(Rd.cpu().numpy().astype(np.float64), Ro, nu)
+    print(f"pyr fp32: {err}")
+    assert err.max() <= 5e-5, err
+
+
+def test_pyr_full_size_against_oracle():
+    """The pyramidal benchmark size class: 12^3 cells (10,368 pyramids, 1.56M DOF), FP64, every
+    element against the oracle, within _dense_bound."""
+    mesh = W.box_pyr_mesh(12)
+    ne, nu = mesh["pyr_v"].shape[0], 30
+    p0 = W.tgv_p0()
+    o = O.Oracle(mesh, 3, 5, threads=NCPU, p_ref=p0)
+    U = W.tgv_state(o.sol_coords(), [(ne, nu)], perturb=1e-3)
+    Ro = o.rhs(U)
+    m = fr.FRMesh(mesh, fr.make_params(p=3, p_ref=p0))
+    Ud = torch.from_numpy(U).cuda()
+    Rd = torch.empty_like(Ud)
+    m.rhs(Ud, Rd)
+    m.sync_status()
+    err = rel_linf(Rd.cpu().numpy(), Ro, nu)
+    bound, spread = _dense_bound(mesh, U, nu)
+    print(f"pyr 12^3: {err} (oracle spread {spread:.2e}, bound {bound:.2e})")
+    assert err.max() <= bound and bound <= 2e-11, (err, bound)

@@ -191,3 +191,40 @@ def test_host_validation_curved(lib):
     with pytest.raises(fr.FRError) as e:
         fr.FRMesh([mesh, mesh], fr.make_params(p=3))
     assert e.value.status == fr.FR_EUNSUPPORTED
+
+
+def test_pyr_mesh_generator_orientation_and_volume():
+    """Six positively oriented pyramids per cell, filling the box; bases in tensor order."""
+    for hb in (0, 2):
+        m = W.box_pyr_mesh(3, hex_below=hb)
+        v, P = m["verts"], m["pyr_v"]
+        assert P.shape == (6 * 9 * (3 - hb), 5) and m["hex_v"].shape[0] == 9 * hb
+        J0 = 0.5 * (v[P[:, 1]] - v[P[:, 0]])
+        J1 = 0.5 * (v[P[:, 2]] - v[P[:, 0]])
+        J2 = 0.5 * (v[P[:, 4]] - v[P[:, 0]]) - 0.5 * (J0 + J1)
+        det = np.einsum("ij,ij->i", J0, np.cross(J1, J2))
+        assert np.all(det > 0)
+        np.testing.assert_allclose(v[P[:, 3]], v[P[:, 1]] + v[P[:, 2]] - v[P[:, 0]], atol=1e-12)
+        vol = det.sum() * 8 / 3 + 8 * (2 * np.pi / 3) ** 3 / 8 * m["hex_v"].shape[0]
+        assert abs(vol - (2 * np.pi) ** 3) < 1e-9
+
+
+def test_host_validation_pyramids(lib):
+    mesh = W.box_pyr_mesh(1)
+    p0 = W.tgv_p0()
+    for kw in (dict(p=4), dict(p=3, nq1d=4), dict(p=3, surface_aa=True),
+               dict(p=3, prec="fp32", p_ref=p0, rho_ref=1.0)):
+        with pytest.raises(fr.FRError) as e:
+            _create(mesh, **kw)
+        assert e.value.status == fr.FR_EUNSUPPORTED, kw
+    mesh = W.box_pyr_mesh(2)
+    mesh["pyr_v"] = mesh["pyr_v"][1:].copy()
+    with pytest.raises(fr.FRError) as e:
+        _create(mesh)
+    assert e.value.status == fr.FR_EMESH
+    mesh = W.box_pyr_mesh(2)
+    mesh["pyr_v"] = mesh["pyr_v"].copy()
+    mesh["pyr_v"][0, [1, 2]] = mesh["pyr_v"][0, [2, 1]]
+    with pytest.raises(fr.FRError) as e:
+        _create(mesh)
+    assert e.value.status == fr.FR_EMESH
