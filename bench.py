@@ -277,7 +277,8 @@ def other_configs(args, torch, fr, W):
     mesh_t = W.box_tet_mesh(24)
     nt = mesh_t["tet_v"].shape[0]
     for prec in ("fp64", "fp32"):
-        m = fr.FRMesh(mesh_t, fr.make_params(p=3, prec=prec, p_ref=p0))
+        # FP32 in the low-Mach form (rho_ref = 1; FP64 ignores it)
+        m = fr.FRMesh(mesh_t, fr.make_params(p=3, prec=prec, p_ref=p0, rho_ref=1.0))
         U0 = W.tgv_state(m.sol_coords(), [(nt, 20)], perturb=1e-3)
         U = torch.from_numpy(U0).cuda()
         ms = _time_steps(m, U, steps, 2, torch)
@@ -323,7 +324,7 @@ def other_configs(args, torch, fr, W):
     ny = mesh_y["pyr_v"].shape[0]
     fl_y = tet_phase_b_flops_per_element(30, 56, 5)
     for prec in ("fp64", "fp32"):
-        m = fr.FRMesh(mesh_y, fr.make_params(p=3, prec=prec, p_ref=p0))
+        m = fr.FRMesh(mesh_y, fr.make_params(p=3, prec=prec, p_ref=p0, rho_ref=1.0))
         U0 = W.tgv_state(m.sol_coords(), [(ny, 30)], perturb=1e-3)
         U = torch.from_numpy(U0).cuda()
         ms = _time_steps(m, U, steps, 2, torch)

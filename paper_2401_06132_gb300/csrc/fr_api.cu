@@ -82,9 +82,11 @@ struct fr_mesh {
     frb::Tet3D tet;                      // tetrahedron operators (p = 3)
     bool has_tet = false;
     void *d_tetops = nullptr;            // TetOps<T> on the device
+    void *d_tetops64 = nullptr;          // DenseOpsFF<TetOps<float>> (low-Mach FP32 form)
     frb::Pyr3D pyr;                      // pyramid operators (p = 3)
     bool has_pyr = false;
     void *d_pyrops = nullptr;            // PyrOps<T> on the device
+    void *d_pyrops64 = nullptr;          // DenseOpsFF<PyrOps<float>> (low-Mach FP32 form)
     std::vector<Group> groups;
     bool split_c = false;              // interface phase as pair flux (C1) + lift (C2)
     bool lowmach = false;              // FP32 low-Mach form (deviations, reduced energy, FP64 mass)
@@ -603,13 +605,10 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
         if (d->n_tet > 0 && !d->tet_v) return fail(FR_EINVAL, "instance %d: null tetrahedron connectivity", ii);
         if (d->n_tet > 0 && P.p != 3)
             return fail(FR_EUNSUPPORTED, "instance %d: tetrahedra are built for p = 3", ii);
-        if (d->n_tet > 0 && P.prec != FR_FP64 && P.p_ref > 0 && P.rho_ref > 0)
-            return fail(FR_EUNSUPPORTED, "instance %d: tetrahedra run the plain FP32 form (no low-Mach form)", ii);
         if (d->n_pyr > 0 && !d->pyr_v) return fail(FR_EINVAL, "instance %d: null pyramid connectivity", ii);
         if (d->n_pyr > 0 && P.p != 3)
             return fail(FR_EUNSUPPORTED, "instance %d: pyramids are built for p = 3", ii);
-        if (d->n_pyr > 0 && P.prec != FR_FP64 && P.p_ref > 0 && P.rho_ref > 0)
-            return fail(FR_EUNSUPPORTED, "instance %d: pyramids run the plain FP32 form (no low-Mach form)", ii);
+
         if (d->n_pri > 0 && (P.p != 3 || (P.tri_strength != 0 && P.tri_strength != 8)))
             return fail(FR_EUNSUPPORTED, "instance %d: prisms are built for p = 3 with a strength-8 triangle rule", ii);
         InstanceHost I;
@@ -745,14 +744,37 @@ static fr_status upload_dense(fr_mesh *m, const REF &R, void **dst)
                 for (int j = 0; j < NU; j++) v += R.Dh[d][z][j] * R.Pj[j][q];
                 t.Dvt[d][q][z] = (T)v;
             }
-    for (int f = 0; f < NFACE; f++) {
+    for (int f = 0; f < NFACE; f++)
         for (int d = 0; d < 3; d++) t.nf[f][d] = (T)R.nf[f][d];
-        for (int s2 = R.foff[f]; s2 < R.foff[f + 1]; s2++) t.fidx[s2] = (unsigned char)f;
+    for (int f = 0; f <= NFACE; f++) {
+        t.foff[f] = R.foff[f];
+        if (R.foff[f] != (f == NFACE ? NF : OPS::F0(f))) return fail(FR_EUNSUPPORTED, "dense-element face layout");
     }
-    for (int f = 0; f <= NFACE; f++) t.foff[f] = R.foff[f];
     fr_status st = dalloc(m, dst, sizeof(OPS));
     if (st) return st;
     CU(cudaMemcpy(*dst, o.data(), sizeof(OPS), cudaMemcpyHostToDevice));
+    return FR_OK;
+}
+
+// Float-float copy of the dense tables the low-Mach form's mass channel reads (M0, Dh, L):
+// hi = float(op), lo = float(op - hi).
+template <typename REF, typename OPSF>
+static fr_status upload_dense_ff(fr_mesh *m, const REF &R, void **dst)
+{
+    constexpr int NU = REF::NU, NF = REF::NF;
+    std::vector<DenseOpsFF<OPSF>> o(1);   // value-initialised
+    OPSF &h = o[0].hi, &l = o[0].lo;
+    auto split = [](double v, float &hi, float &lo) { hi = (float)v; lo = (float)(v - (double)hi); };
+    for (int j = 0; j < NU; j++) {
+        for (int s2 = 0; s2 < NF; s2++) split(R.M0[s2][j], h.M0t[j][s2], l.M0t[j][s2]);
+        for (int d = 0; d < 3; d++)
+            for (int z = 0; z < NU; z++) split(R.Dh[d][z][j], h.Dht[d][j][z], l.Dht[d][j][z]);
+    }
+    for (int s2 = 0; s2 < NF; s2++)
+        for (int z = 0; z < NU; z++) split(R.L[z][s2], h.Lt[s2][z], l.Lt[s2][z]);
+    fr_status st = dalloc(m, dst, sizeof(DenseOpsFF<OPSF>));
+    if (st) return st;
+    CU(cudaMemcpy(*dst, o.data(), sizeof(DenseOpsFF<OPSF>), cudaMemcpyHostToDevice));
     return FR_OK;
 }
 
@@ -1024,6 +1046,8 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
         if (!st && cudaMemcpy(m->d_priops64, &pff, sizeof(pff), cudaMemcpyHostToDevice) != cudaSuccess)
             st = fail(FR_ECUDA, "prism operator upload failed");
     }
+    if (!st && m->lowmach && m->has_tet) st = upload_dense_ff<frb::Tet3D, TetOps<float>>(m, m->tet, &m->d_tetops64);
+    if (!st && m->lowmach && m->has_pyr) st = upload_dense_ff<frb::Pyr3D, PyrOps<float>>(m, m->pyr, &m->d_pyrops64);
     if (!st && m->lowmach) {
         std::vector<Geo<double>> g64((size_t)m->ne);
         for (long long e = 0; e < m->ne; e++) {
@@ -1076,7 +1100,7 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
 extern "C" fr_status fr_destroy(fr_mesh *m)
 {
     if (!m) return FR_OK;
-    void **bufs[] = {&m->d_fnrm, (void **)&m->d_fnrm64, &m->d_geo64, (void **)&m->d_MF, (void **)&m->d_RL, &m->d_priops, &m->d_priops64, &m->d_tetops, &m->d_pyrops, &m->d_geo, (void **)&m->d_partner, &m->d_UF, &m->d_FV, &m->d_CF, &m->d_QF, &m->d_DF, &m->d_Qu,
+    void **bufs[] = {&m->d_fnrm, (void **)&m->d_fnrm64, &m->d_geo64, (void **)&m->d_MF, (void **)&m->d_RL, &m->d_priops, &m->d_priops64, &m->d_tetops, &m->d_pyrops, &m->d_tetops64, &m->d_pyrops64, &m->d_geo, (void **)&m->d_partner, &m->d_UF, &m->d_FV, &m->d_CF, &m->d_QF, &m->d_DF, &m->d_Qu,
                      &m->d_UQ, &m->d_QQ, &m->d_Rt, &m->d_rk_k, &m->d_rk_us, (void **)&m->d_rk_acc, &m->d_io_U,
                      &m->d_io_R, (void **)&m->d_wsum, (void **)&m->d_status, &m->d_Qsnap, (void **)&m->d_qpartner,
                      &m->d_UFQ, &m->d_FVQ, (void **)&m->d_qlpts, &m->d_DQ, &m->d_mu, &m->d_mq, &m->d_mfn};
@@ -1285,8 +1309,8 @@ static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, co
                 }
                 int lr = b.type == 0 ? hex_fused_phase<T>(b.p, ph, a, s, gr.variant)
                          : b.type == 1 ? pri_fused_phase<T>(ph, a, reinterpret_cast<const PriOps<T> *>(m->d_priops), reinterpret_cast<const PriOpsFF *>(m->d_priops64), s)
-                         : b.type == 2 ? tet_fused_phase<T>(ph, a, reinterpret_cast<const TetOps<T> *>(m->d_tetops), s)
-                                       : pyr_fused_phase<T>(ph, a, reinterpret_cast<const PyrOps<T> *>(m->d_pyrops), s);
+                         : b.type == 2 ? tet_fused_phase<T>(ph, a, reinterpret_cast<const TetOps<T> *>(m->d_tetops), reinterpret_cast<const DenseOpsFF<TetOps<float>> *>(m->d_tetops64), s)
+                                       : pyr_fused_phase<T>(ph, a, reinterpret_cast<const PyrOps<T> *>(m->d_pyrops), reinterpret_cast<const DenseOpsFF<PyrOps<float>> *>(m->d_pyrops64), s);
                 if (lr) return fail(FR_ECUDA, "fused phase %d launch: %s", ph, cudaGetErrorString(cudaGetLastError()));
             }
         }
@@ -1344,8 +1368,8 @@ static fr_status autotune_impl(fr_mesh *m, const void *U, void *R, cudaStream_t 
         }
         int lr = b.type == 0 ? hex_fused_phase<T>(b.p, 0, a, s, gr.variant)
                  : b.type == 1 ? pri_fused_phase<T>(0, a, reinterpret_cast<const PriOps<T> *>(m->d_priops), reinterpret_cast<const PriOpsFF *>(m->d_priops64), s)
-                 : b.type == 2 ? tet_fused_phase<T>(0, a, reinterpret_cast<const TetOps<T> *>(m->d_tetops), s)
-                               : pyr_fused_phase<T>(0, a, reinterpret_cast<const PyrOps<T> *>(m->d_pyrops), s);
+                 : b.type == 2 ? tet_fused_phase<T>(0, a, reinterpret_cast<const TetOps<T> *>(m->d_tetops), reinterpret_cast<const DenseOpsFF<TetOps<float>> *>(m->d_tetops64), s)
+                               : pyr_fused_phase<T>(0, a, reinterpret_cast<const PyrOps<T> *>(m->d_pyrops), reinterpret_cast<const DenseOpsFF<PyrOps<float>> *>(m->d_pyrops64), s);
         if (lr) return fail(FR_ECUDA, "autotune: face phase launch failed");
     }
     cudaEvent_t e0, e1;

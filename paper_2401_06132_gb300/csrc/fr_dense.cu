@@ -37,11 +37,24 @@ __device__ __forceinline__ V16<T> ld16(const T *p)
     return *reinterpret_cast<const V16<T> *>(p);
 }
 
+// The float-float table type of an operator table, and one entry of it as a pair (the lo part sits
+// at the same offset in the second table).
+template <typename OPS>
+using FFOf = DenseOpsFF<DenseOps<float, OPS::NU, OPS::NF, OPS::NFACE>>;
+template <typename FF>
+__device__ __forceinline__ ff ffat(const FF &o, const float &hi)
+{
+    const float *h0 = reinterpret_cast<const float *>(&o.hi);
+    return ff{hi, reinterpret_cast<const float *>(&o.lo)[&hi - h0]};
+}
+
 // -------------------------------------------------------------------------------------------------
 // Phase A: disu (U^f = M0 U)
 // -------------------------------------------------------------------------------------------------
+// Low-Mach FP32 form (ph.dev): the face solution of the deviations from the reference state, and the
+// own-normal mass flux n.(rho v) at every flux point in float-float.
 template <typename T, typename OPS>
-__global__ void __launch_bounds__(256) k_dense_disu(HexArgs<T> a, const OPS *__restrict__ op)
+__global__ void __launch_bounds__(256) k_dense_disu(HexArgs<T> a, const OPS *__restrict__ op, const FFOf<OPS> *__restrict__ opsff)
 {
     constexpr int NU = OPS::NU, NF = OPS::NF;
     const long long total = a.ne * FR_NV * NF;
@@ -50,11 +63,33 @@ __global__ void __launch_bounds__(256) k_dense_disu(HexArgs<T> a, const OPS *__r
         const long long ea = it / NF;
         const int alpha = (int)(ea % FR_NV);
         const long long e = ea / FR_NV;
-        const T *u = a.U + elem_u0(a, e, NU) + alpha * NU;
+        const T *ub = a.U + elem_u0(a, e, NU);
+        const T *u = ub + alpha * NU;
+        T off = T(0);
+        bool dev = false;
+        if constexpr (sizeof(T) == 4) {
+            const Phys<T> ph = elem_phys(a, e);
+            dev = ph.dev != 0;
+            if (dev) off = alpha == 0 ? ph.rref : (alpha == 4 ? ph.eref : T(0));
+        }
         T v = T(0);
 #pragma unroll
-        for (int z = 0; z < NU; z++) v += op->M0t[z][s] * u[z];
+        for (int z = 0; z < NU; z++) v += op->M0t[z][s] * (u[z] - off);
         a.UF[alpha * a.nfpt + elem_f0(a, e, NF) + s] = v;
+        if constexpr (sizeof(T) == 4) {
+            if (dev && alpha == 0) {
+                const ff *nt = a.fnrm64 + (e * 6 + OPS::FACE(s)) * 4;
+                ff mf = ff_of(0.0f);
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    if (nt[k].hi == 0.0f) continue;
+                    ff w = ff_of(0.0f);
+                    for (int z = 0; z < NU; z++) w = ff_fma_f(ffat(*opsff, opsff->hi.M0t[z][s]), ub[(1 + k) * NU + z], w);
+                    mf = ff_fma(nt[k], w, mf);
+                }
+                a.MF[elem_f0(a, e, NF) + s] = mf;
+            }
+        }
     }
 }
 
@@ -62,13 +97,14 @@ __global__ void __launch_bounds__(256) k_dense_disu(HexArgs<T> a, const OPS *__r
 // Phase B: volume group, one element per CTA of NTH threads (persistent over elements)
 // -------------------------------------------------------------------------------------------------
 template <typename T, int NTH, typename OPS>
-__global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__restrict__ op)
+__global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__restrict__ op, const FFOf<OPS> *__restrict__ opsff)
 {
     constexpr int NU = OPS::NU, NF = OPS::NF, NFACE = OPS::NFACE, NUS = OPS::NUS;
     static_assert(NTH >= NQ, "one thread per quadrature point");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ short s_plist[NF];
     __shared__ int s_pcnt;
+    __shared__ ff s_mf[sizeof(T) == 4 ? 3 * NU : 1];   // low-Mach form: transformed mass flux
     constexpr int VW = V16<T>::n;
     constexpr int NCH = NTH / NU;                 // quadrature-point chunks of the projection
     T *s_u = reinterpret_cast<T *>(smem_raw);   // [5][NUS] state
@@ -89,7 +125,13 @@ __global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__rest
         const Phys<T> ph = elem_phys(a, e);
         const T *U = a.U + elem_u0(a, e, NU);
         const long long gf0 = elem_f0(a, e, NF);
-        for (int it = threadIdx.x; it < 5 * NU; it += NTH) s_u[(it / NU) * NUS + it % NU] = U[it];
+        bool dev = false;
+        if constexpr (sizeof(T) == 4) dev = ph.dev != 0;
+        for (int it = threadIdx.x; it < 5 * NU; it += NTH) {
+            T v = U[it];
+            if (dev) v -= it < NU ? ph.rref : (it >= 4 * NU ? ph.eref : T(0));
+            s_u[(it / NU) * NUS + it % NU] = v;
+        }
         if (threadIdx.x == 0) s_pcnt = 0;
         for (int it = threadIdx.x; it < 5 * NF; it += NTH) {   // con_u
             const int alpha = it / NF, s = it % NF;
@@ -101,6 +143,33 @@ __global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__rest
             s_c[it] = (T(0.5) - ph.beta) * uL + (T(0.5) + ph.beta) * uR;
         }
         __syncthreads();
+        if constexpr (sizeof(T) == 4) {
+            // low-Mach form: the volume part of R~_rho in float-float (the mass flux rho v lies in the
+            // solution space, so its L2 projection is itself and the corrected divergence Dh applies
+            // at the solution points)
+            if (dev) {
+                const Geo<double> g64 = a.geo64[e];
+                ff cm[9];   // det J^-1
+#pragma unroll
+                for (int k = 0; k < 9; k++) cm[k] = ff_from_double(g64.det * g64.Ji[k]);
+                for (int z = threadIdx.x; z < NU; z += NTH) {
+                    const float m0 = s_u[NUS + z], m1 = s_u[2 * NUS + z], m2 = s_u[3 * NUS + z];
+#pragma unroll
+                    for (int d = 0; d < 3; d++)
+                        s_mf[d * NU + z] = ff_add(ff_add(ff_mul_f(cm[3 * d], m0), ff_mul_f(cm[3 * d + 1], m1)), ff_mul_f(cm[3 * d + 2], m2));
+                }
+                __syncthreads();
+                const FFOf<OPS> &o = *opsff;
+                const long long pbase = elem_u0(a, e, NU) / FR_NV;
+                for (int z = threadIdx.x; z < NU; z += NTH) {
+                    ff v = ff_of(0.0f);
+#pragma unroll
+                    for (int d = 0; d < 3; d++)
+                        for (int j = 0; j < NU; j++) v = ff_fma(ffat(o, o.hi.Dht[d][j][z]), s_mf[d * NU + j], v);
+                    a.RL[pbase + z] = v;
+                }
+            }
+        }
         // corrected gradient q~_d = Dh_d u + sum_f n_f,d (L_f c), then q = J^-T q~
         for (int it = threadIdx.x; it < 5 * NU; it += NTH) {
             const int alpha = it / NU, z = it % NU;
@@ -117,7 +186,8 @@ __global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__rest
 #pragma unroll
             for (int f = 0; f < NFACE; f++) {
                 T l = T(0);
-                for (int s = op->foff[f]; s < op->foff[f + 1]; s++) l += op->Lt[s][z] * c[s];
+#pragma unroll
+                for (int s = OPS::F0(f); s < OPS::F0(f + 1); s++) l += op->Lt[s][z] * c[s];
                 q0 += op->nf[f][0] * l;
                 q1 += op->nf[f][1] * l;
                 q2 += op->nf[f][2] * l;
@@ -164,8 +234,9 @@ __global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__rest
 #pragma unroll
                 for (int d = 0; d < 3; d++) qf[alpha][d] = v[5 + alpha * 3 + d];
             }
-            const T *nt = a.fnrm + (e * 6 + op->fidx[s]) * 4;
+            const T *nt = a.fnrm + (e * 6 + OPS::FACE(s)) * 4;
             T n[3] = {nt[0], nt[1], nt[2]};
+            if (dev) { uf[0] += ph.rref; uf[4] += ph.eref; }
             T fvn[4];
             viscous_normal_flux(ph, uf, qf, n, fvn);
 #pragma unroll
@@ -201,7 +272,12 @@ __global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__rest
 #pragma unroll
                 for (int d = 0; d < 3; d++) gq[alpha][d] = s_w[(5 + alpha * 3 + d) * NQP + q];
             }
-            ok &= total_flux(ph, u, gq, f);
+            if constexpr (sizeof(T) == 4) {
+                if (dev) ok &= total_flux_dev(ph, u, gq, f);
+                else ok &= total_flux(ph, u, gq, f);
+            } else {
+                ok &= total_flux(ph, u, gq, f);
+            }
 #pragma unroll
             for (int alpha = 0; alpha < 5; alpha++)
 #pragma unroll
@@ -256,14 +332,17 @@ __global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__rest
 // Phase C: interface group (common flux at every own flux point, lift and scale)
 // -------------------------------------------------------------------------------------------------
 template <typename T, int NTH, typename OPS>
-__global__ void __launch_bounds__(NTH) k_dense_C(HexArgs<T> a, const OPS *__restrict__ op)
+__global__ void __launch_bounds__(NTH) k_dense_C(HexArgs<T> a, const OPS *__restrict__ op, const FFOf<OPS> *__restrict__ opsff)
 {
     constexpr int NU = OPS::NU, NF = OPS::NF;
     __shared__ T s_d[5 * NF];
+    __shared__ ff s_dff[sizeof(T) == 4 ? NF : 1];   // low-Mach form: transformed mass flux (float-float)
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
         const Geo<T> g = a.geo[e];
         const Phys<T> ph = elem_phys(a, e);
         const long long gf0 = elem_f0(a, e, NF);
+        bool dev = false;
+        if constexpr (sizeof(T) == 4) dev = ph.dev != 0;
         bool ok = true;
         for (int s = threadIdx.x; s < NF; s += NTH) {
             const uint32_t pc = a.partner[gf0 + s];
@@ -274,11 +353,27 @@ __global__ void __launch_bounds__(NTH) k_dense_C(HexArgs<T> a, const OPS *__rest
             for (int k = 0; k < 5; k++) { uo[k] = a.UF[k * a.nfpt + og]; up[k] = a.UF[k * a.nfpt + pg]; }
 #pragma unroll
             for (int k = 0; k < 4; k++) { fvo[k] = a.FV[k * a.nfpt + og]; fvp[k] = a.FV[k * a.nfpt + pg]; }
-            const T *nt = a.fnrm + (e * 6 + op->fidx[s]) * 4;
+            const T *nt = a.fnrm + (e * 6 + OPS::FACE(s)) * 4;
             const T mag = nt[3];
             T nL[3] = {isL ? nt[0] : -nt[0], isL ? nt[1] : -nt[1], isL ? nt[2] : -nt[2]};
             T F[5];
-            ok &= isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
+            if constexpr (sizeof(T) == 4) {
+                if (dev) {
+                    float sw;
+                    ok &= isL ? common_flux_dev(ph, uo, up, fvo, fvp, nL, F, sw) : common_flux_dev(ph, up, uo, fvp, fvo, nL, F, sw);
+                    // mass flux in float-float: 1/2 (mL - mR) + (s/2 + tau)(rho_L - rho_R), mX = own-normal n.(rho v)
+                    const ff mo = a.MF[og], mp = a.MF[pg];
+                    const ff mL = isL ? mo : mp, mR = isL ? mp : mo;
+                    const float rL = isL ? uo[0] : up[0], rR = isL ? up[0] : uo[0];
+                    const ff Fr = ff_add(ff_mul_f(ff_sub(mL, mR), 0.5f), ff_mul_f(two_sum(rL, -rR), 0.5f * sw + ph.tau));
+                    const ff magf = a.fnrm64[(e * 6 + OPS::FACE(s)) * 4 + 3];
+                    s_dff[s] = isL ? ff_mul(magf, Fr) : ff_neg(ff_mul(magf, Fr));
+                } else {
+                    ok &= isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
+                }
+            } else {
+                ok &= isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
+            }
             const T sc = isL ? mag : -mag;
 #pragma unroll
             for (int k = 0; k < 5; k++) s_d[k * NF + s] = sc * F[k];
@@ -287,14 +382,44 @@ __global__ void __launch_bounds__(NTH) k_dense_C(HexArgs<T> a, const OPS *__rest
         __syncthreads();
         T *R = a.R + elem_u0(a, e, NU);
         const T idet = T(-1) / g.det;
-        for (int it = threadIdx.x; it < 5 * NU; it += NTH) {
-            const int alpha = it / NU, z = it % NU;
-            const T *D = s_d + alpha * NF;
-            T v = R[it];
+        if (!dev) {
+            for (int it = threadIdx.x; it < 5 * NU; it += NTH) {
+                const int alpha = it / NU, z = it % NU;
+                const T *D = s_d + alpha * NF;
+                T v = R[it];
 #pragma unroll 8
-            for (int s = 0; s < NF; s++) v += op->Lt[s][z] * D[s];
-            if (a.rkstage == 0) R[it] = v * idet;
-            else rk_fold(a, elem_u0(a, e, NU) + it, v * idet);
+                for (int s = 0; s < NF; s++) v += op->Lt[s][z] * D[s];
+                if (a.rkstage == 0) R[it] = v * idet;
+                else rk_fold(a, elem_u0(a, e, NU) + it, v * idet);
+            }
+        } else if constexpr (sizeof(T) == 4) {
+            // low-Mach form: R_rho in float-float, R_E = R_(E - H0 rho) + H0 R_rho
+            const FFOf<OPS> &o = *opsff;
+            const ff idet64 = ff_from_double(-1.0 / a.geo64[e].det);
+            const ff H0 = ff_from_double(ph.H0d);
+            const long long pbase = elem_u0(a, e, NU) / FR_NV;
+            for (int z = threadIdx.x; z < NU; z += NTH) {
+                ff r = a.RL[pbase + z];
+                for (int s = 0; s < NF; s++) r = ff_fma(ffat(o, o.hi.Lt[s][z]), s_dff[s], r);
+                const ff Rrho = ff_mul(r, idet64);
+                float out[5];
+                out[0] = Rrho.hi + Rrho.lo;
+#pragma unroll
+                for (int alpha = 1; alpha < 5; alpha++) {
+                    const T *D = s_d + alpha * NF;
+                    T v = R[alpha * NU + z];
+#pragma unroll 8
+                    for (int s = 0; s < NF; s++) v += op->Lt[s][z] * D[s];
+                    out[alpha] = v * idet;
+                }
+                const ff e4 = ff_fma(H0, Rrho, ff_of(out[4]));
+                out[4] = e4.hi + e4.lo;
+#pragma unroll
+                for (int alpha = 0; alpha < 5; alpha++) {
+                    if (a.rkstage == 0) R[alpha * NU + z] = out[alpha];
+                    else rk_fold(a, elem_u0(a, e, NU) + alpha * NU + z, out[alpha]);
+                }
+            }
         }
         __syncthreads();
     }
@@ -308,7 +433,7 @@ int grid_elems(long long ne, int per_sm)
 }
 
 template <typename T, typename OPS>
-int dense_phase(int phase, const HexArgs<T> &a, const OPS *ops, cudaStream_t s)
+int dense_phase(int phase, const HexArgs<T> &a, const OPS *ops, const FFOf<OPS> *opsff, cudaStream_t s)
 {
     constexpr int NU = OPS::NU, NF = OPS::NF, NUS = OPS::NUS;
     if (a.ne == 0) return 0;
@@ -316,7 +441,7 @@ int dense_phase(int phase, const HexArgs<T> &a, const OPS *ops, cudaStream_t s)
         long long work = a.ne * FR_NV * NF;
         long long g = (work + 255) / 256;
         if (g > 152LL * 64) g = 152LL * 64;
-        k_dense_disu<T, OPS><<<(int)g, 256, 0, s>>>(a, ops);
+        k_dense_disu<T, OPS><<<(int)g, 256, 0, s>>>(a, ops, opsff);
     } else if (phase == 1) {
         constexpr int NTH = 128;
         const size_t smem = (size_t)(20 * NUS + 5 * NF + 20 * NQP) * sizeof(T);
@@ -325,9 +450,9 @@ int dense_phase(int phase, const HexArgs<T> &a, const OPS *ops, cudaStream_t s)
             cudaFuncSetAttribute(k_dense_B<T, NTH, OPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             attr = true;
         }
-        k_dense_B<T, NTH, OPS><<<grid_elems(a.ne, 8), NTH, smem, s>>>(a, ops);
+        k_dense_B<T, NTH, OPS><<<grid_elems(a.ne, 8), NTH, smem, s>>>(a, ops, opsff);
     } else {
-        k_dense_C<T, 128, OPS><<<grid_elems(a.ne, 8), 128, 0, s>>>(a, ops);
+        k_dense_C<T, 128, OPS><<<grid_elems(a.ne, 8), 128, 0, s>>>(a, ops, opsff);
     }
     (void)NU;
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
@@ -336,18 +461,18 @@ int dense_phase(int phase, const HexArgs<T> &a, const OPS *ops, cudaStream_t s)
 }  // namespace
 
 template <typename T>
-int tet_fused_phase(int phase, const HexArgs<T> &a, const TetOps<T> *ops, cudaStream_t s)
+int tet_fused_phase(int phase, const HexArgs<T> &a, const TetOps<T> *ops, const DenseOpsFF<TetOps<float>> *opsff, cudaStream_t s)
 {
-    return dense_phase<T, TetOps<T>>(phase, a, ops, s);
+    return dense_phase<T, TetOps<T>>(phase, a, ops, opsff, s);
 }
 
 template <typename T>
-int pyr_fused_phase(int phase, const HexArgs<T> &a, const PyrOps<T> *ops, cudaStream_t s)
+int pyr_fused_phase(int phase, const HexArgs<T> &a, const PyrOps<T> *ops, const DenseOpsFF<PyrOps<float>> *opsff, cudaStream_t s)
 {
-    return dense_phase<T, PyrOps<T>>(phase, a, ops, s);
+    return dense_phase<T, PyrOps<T>>(phase, a, ops, opsff, s);
 }
 
-template int tet_fused_phase<double>(int, const HexArgs<double> &, const TetOps<double> *, cudaStream_t);
-template int tet_fused_phase<float>(int, const HexArgs<float> &, const TetOps<float> *, cudaStream_t);
-template int pyr_fused_phase<double>(int, const HexArgs<double> &, const PyrOps<double> *, cudaStream_t);
-template int pyr_fused_phase<float>(int, const HexArgs<float> &, const PyrOps<float> *, cudaStream_t);
+template int tet_fused_phase<double>(int, const HexArgs<double> &, const TetOps<double> *, const DenseOpsFF<TetOps<float>> *, cudaStream_t);
+template int tet_fused_phase<float>(int, const HexArgs<float> &, const TetOps<float> *, const DenseOpsFF<TetOps<float>> *, cudaStream_t);
+template int pyr_fused_phase<double>(int, const HexArgs<double> &, const PyrOps<double> *, const DenseOpsFF<PyrOps<float>> *, cudaStream_t);
+template int pyr_fused_phase<float>(int, const HexArgs<float> &, const PyrOps<float> *, const DenseOpsFF<PyrOps<float>> *, cudaStream_t);

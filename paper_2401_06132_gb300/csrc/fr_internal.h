@@ -130,17 +130,26 @@ struct PriOps {
 template <typename T, int NU_, int NF_, int NFACE_>
 struct DenseOps {
     static constexpr int NU = NU_, NF = NF_, NFACE = NFACE_, NUS = (NU_ + 3) / 4 * 4;
+    // face f holds flux points F0(f) .. F0(f+1)-1: the first face has NF - 10 (NFACE - 1) points
+    // (10 on the tetrahedron, the 16-point base on the pyramid), every other face the 10 triangle points
+    static constexpr int FIRST = NF_ - 10 * (NFACE_ - 1);
+    static constexpr __host__ __device__ int F0(int f) { return f == 0 ? 0 : FIRST + 10 * (f - 1); }
+    static constexpr __host__ __device__ int FACE(int s) { return s < FIRST ? 0 : 1 + (s - FIRST) / 10; }
     T Bt[NUS][FR_TQ];              // B^T: [j][q]
     T M0t[NUS][NF];                // M0^T: [z][s]
     T Dht[3][NU][NU];              // [d][j][z] = Dh[d][z][j]
     T Lt[NF][NU];                  // [s][z] = L[z][s]
     T Dvt[3][FR_TQP][NU];          // (Dh_d Pj)^T: projection with the corrected divergence, [d][q][z]
     T nf[NFACE][3];
-    int foff[NFACE + 1];
-    unsigned char fidx[NF];        // face of each flux point
+    int foff[NFACE + 1];           // F0(f), kept with the table
 };
 template <typename T> using TetOps = DenseOps<T, 20, 40, 4>;
 template <typename T> using PyrOps = DenseOps<T, 30, 56, 5>;
+// The FP32 tables as float-float pairs (value = hi + lo): the low-Mach FP32 form's mass channel.
+template <typename OPS32>
+struct DenseOpsFF {
+    OPS32 hi, lo;
+};
 
 // Prism operators as float-float pairs: value = hi + lo (the low-Mach mass channel).
 struct PriOpsFF {
@@ -295,5 +304,8 @@ int hex_upload_ops(int p, int m, const frb::Hex1D &h);
 // float-float table of the low-Mach FP32 form's mass channel; null otherwise).
 template <typename T> int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, const PriOpsFF *opsff, cudaStream_t s);
 // Dense-element kernels (fr_dense.cu): tetrahedra and pyramids, operator table by device pointer.
-template <typename T> int tet_fused_phase(int phase, const HexArgs<T> &a, const TetOps<T> *ops, cudaStream_t s);
-template <typename T> int pyr_fused_phase(int phase, const HexArgs<T> &a, const PyrOps<T> *ops, cudaStream_t s);
+// (opsff: the float-float FP32 table of the low-Mach form's mass channel; null otherwise).
+template <typename T>
+int tet_fused_phase(int phase, const HexArgs<T> &a, const TetOps<T> *ops, const DenseOpsFF<TetOps<float>> *opsff, cudaStream_t s);
+template <typename T>
+int pyr_fused_phase(int phase, const HexArgs<T> &a, const PyrOps<T> *ops, const DenseOpsFF<PyrOps<float>> *opsff, cudaStream_t s);

@@ -931,3 +931,35 @@ def test_pyr_full_size_against_oracle():
     bound, spread = _dense_bound(mesh, U, nu)
     print(f"pyr 12^3: {err} (oracle spread {spread:.2e}, bound {bound:.2e})")
     assert err.max() <= bound and bound <= 2e-11, (err, bound)
+
+
+
+@pytest.mark.parametrize("name", ["tetshear2", "tet4", "pyr3", "hexpyr2"])
+def test_dense_lowmach_fp32_matches_oracle(name):
+    """The low-Mach FP32 form (deviations from the reference state, reduced energy, mass channel in
+    float-float) on tetrahedra, pyramids and a hexahedron/pyramid mix, against the oracle on the
+    FP32-rounded input: within the FP32 bound of 2e-5."""
+    mesh = {"tetshear2": lambda: W.box_tet_mesh(2, shear=True), "tet4": lambda: W.box_tet_mesh(4),
+            "pyr3": lambda: W.box_pyr_mesh(3), "hexpyr2": lambda: W.box_pyr_mesh(2, hex_below=1)}[name]()
+    blocks = [b for b in ((mesh["hex_v"].shape[0], 64), (mesh.get("tet_v", np.zeros((0, 4))).shape[0], 20),
+                          (mesh.get("pyr_v", np.zeros((0, 5))).shape[0], 30)) if b[0]]
+    p0 = W.tgv_p0()
+    o = O.Oracle(mesh, 3, 5, threads=NCPU, p_ref=p0)
+    U32 = W.tgv_state(o.sol_coords(), blocks, perturb=1e-2).astype(np.float32)
+    Ro = o.rhs(U32.astype(np.float64))
+    m = fr.FRMesh(mesh, fr.make_params(p=3, prec="fp32", p_ref=p0, rho_ref=1.0))
+    Ud = torch.from_numpy(U32).cuda()
+    Rd = torch.empty_like(Ud)
+    m.rhs(Ud, Rd)
+    m.sync_status()
+    err = _rel_blocks(Rd.cpu().numpy().astype(np.float64), Ro, blocks)
+    print(f"dense low-Mach fp32 {name}: {err}")
+    assert err.max() <= 2e-5, err
+    # RK4 in the low-Mach form: FP64 master state, FP32 stages
+    Uo = o.rk4(U32.astype(np.float64), 1e-3, 3)
+    Um = torch.from_numpy(U32.astype(np.float64)).cuda()
+    m.rk4_step(Um, 1e-3, 3)
+    m.sync_status()
+    dr = np.abs(Um.cpu().numpy() - Uo).max() / np.abs(Uo).max()
+    print(f"dense low-Mach fp32 RK4 {name}: {dr:.3e}")
+    assert dr <= 1e-6, dr

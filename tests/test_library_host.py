@@ -160,9 +160,7 @@ def test_tet_mesh_generator_orientation_and_volume():
 
 def test_host_validation_tetrahedra(lib):
     mesh = W.box_tet_mesh(1)
-    p0 = W.tgv_p0()
-    for kw in (dict(p=4), dict(p=3, nq1d=4), dict(p=3, surface_aa=True),
-               dict(p=3, prec="fp32", p_ref=p0, rho_ref=1.0)):
+    for kw in (dict(p=4), dict(p=3, nq1d=4), dict(p=3, surface_aa=True)):
         with pytest.raises(fr.FRError) as e:
             _create(mesh, **kw)
         assert e.value.status == fr.FR_EUNSUPPORTED, kw
@@ -211,9 +209,7 @@ def test_pyr_mesh_generator_orientation_and_volume():
 
 def test_host_validation_pyramids(lib):
     mesh = W.box_pyr_mesh(1)
-    p0 = W.tgv_p0()
-    for kw in (dict(p=4), dict(p=3, nq1d=4), dict(p=3, surface_aa=True),
-               dict(p=3, prec="fp32", p_ref=p0, rho_ref=1.0)):
+    for kw in (dict(p=4), dict(p=3, nq1d=4), dict(p=3, surface_aa=True)):
         with pytest.raises(fr.FRError) as e:
             _create(mesh, **kw)
         assert e.value.status == fr.FR_EUNSUPPORTED, kw
