@@ -116,11 +116,11 @@ typedef struct {
     double rho_ref;       /* reference density. With p_ref > 0 and rho_ref > 0 the FP32 form works on
                            * deviations from the reference state (rho_ref, 0, 0, 0, p_ref/(gamma-1)),
                            * evolves the reduced energy E - H0 rho (H0 = gamma p_ref/((gamma-1) rho_ref))
-                           * in FP32 and the mass equation in FP64, then returns R_E = R_(E-H0 rho) +
-                           * H0 R_rho. All of it is exact in exact arithmetic; it removes the
-                           * O(1/M^2) cancellations of low-Mach flows from the FP32 rounding. Fused
-                           * form, hexahedra and prisms (with tetrahedra: FR_EUNSUPPORTED); ignored
-                           * in FP64. */
+                           * in FP32 and the mass equation in float-float (about 48 bits), then
+                           * returns R_E = R_(E-H0 rho) + H0 R_rho. All of it is exact in exact
+                           * arithmetic; it removes the O(1/M^2) cancellations of low-Mach flows from
+                           * the FP32 rounding. Fused form, every element type (curved hexahedra:
+                           * FR_EUNSUPPORTED at the first RHS call); ignored in FP64. */
     int surface_aa;       /* 1: surface-flux anti-aliasing as well (Sec. 2.2.1: the interface flux points
                            * are replaced by the m x m Gauss-Legendre points of each face, m = nq1d; the
                            * common flux is evaluated there and lifted through the face L2 projection).

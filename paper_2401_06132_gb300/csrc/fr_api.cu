@@ -779,7 +779,7 @@ static fr_status upload_dense_ff(fr_mesh *m, const REF &R, void **dst)
 }
 
 template <typename T>
-static fr_status upload_tetops(fr_mesh *m)
+static fr_status upload_dense_tables(fr_mesh *m)
 {
     fr_status st = FR_OK;
     if (m->has_tet) st = upload_dense<T, frb::Tet3D, TetOps<T>>(m, m->tet, &m->d_tetops);
@@ -1024,7 +1024,7 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
     size_t ts = tsize(m->prec);
     st = (m->prec == FR_FP64) ? upload_geo<double>(m) : upload_geo<float>(m);
     if (!st) st = (m->prec == FR_FP64) ? upload_priops<double>(m, &m->d_priops) : upload_priops<float>(m, &m->d_priops);
-    if (!st) st = (m->prec == FR_FP64) ? upload_tetops<double>(m) : upload_tetops<float>(m);
+    if (!st) st = (m->prec == FR_FP64) ? upload_dense_tables<double>(m) : upload_dense_tables<float>(m);
     if (!st) st = (m->prec == FR_FP64) ? upload_curved<double>(m) : upload_curved<float>(m);
     if (!st && m->prec != FR_FP64) {
         bool all = true;
