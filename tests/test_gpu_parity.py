@@ -963,3 +963,83 @@ def test_dense_lowmach_fp32_matches_oracle(name):
     dr = np.abs(Um.cpu().numpy() - Uo).max() / np.abs(Uo).max()
     print(f"dense low-Mach fp32 RK4 {name}: {dr:.3e}")
     assert dr <= 1e-6, dr
+
+
+def test_heterogeneous_ensemble_matches_per_instance_oracles():
+    """One handle over instances of every element type and order (hexahedra p = 3 and 4, a
+    hexahedron/prism mix, two tetrahedral boxes, a pyramid box and a hexahedron/pyramid mix), each
+    with its own Mach and Reynolds numbers: blocks of one type and order from different instances run
+    in one launch (per-element offsets, per-instance physics). FP64 per instance against its own
+    oracle, and the low-Mach FP32 form within 2e-5."""
+    specs = [(W.box_hex_mesh(2), 4, 0.1, 1600.0), (W.mixed_box_mesh(2), 3, 0.15, 800.0),
+             (W.box_tet_mesh(2), 3, 0.08, 400.0), (W.box_tet_mesh(2, shear=True), 3, 0.12, 3200.0),
+             (W.box_pyr_mesh(2), 3, 0.1, 1000.0), (W.box_pyr_mesh(2, hex_below=1), 3, 0.2, 500.0),
+             (W.box_hex_mesh(3), 3, 0.05, 2000.0)]
+    meshes = [s[0] for s in specs]
+
+    def blocks_of(mesh, p):
+        out = []
+        for key, nu in (("hex_v", (p + 1) ** 3), ("pri_v", 40), ("tet_v", 20), ("pyr_v", 30)):
+            arr = mesh.get(key)
+            if arr is not None and arr.shape[0]:
+                out.append((arr.shape[0], nu))
+        return out
+
+    for prec in ("fp64", "fp32"):
+        params = [fr.make_params(p=p, mu=1.0 / re, prec=prec, p_ref=W.tgv_p0(mach=M), rho_ref=1.0)
+                  for (_, p, M, re) in specs]
+        m = fr.FRMesh(meshes, params)
+        off = m.instance_offsets()
+        xyz = m.sol_coords()
+        parts, refs = [], []
+        for i, (mesh, p, M, re) in enumerate(specs):
+            o = O.Oracle(mesh, p, p + 2, mu=1.0 / re, threads=NCPU, p_ref=W.tgv_p0(mach=M))
+            n = (off[i + 1] - off[i]) // 5
+            assert np.abs(xyz[off[i] // 5: off[i] // 5 + n] - o.sol_coords()).max() < 1e-12
+            U = W.tgv_state(o.sol_coords(), blocks_of(mesh, p), mach=M, perturb=1e-2, dof_offset=off[i])
+            if prec == "fp32":
+                U = U.astype(np.float32).astype(np.float64)
+            parts.append(U)
+            refs.append((o.rhs(U), blocks_of(mesh, p)))
+        U = np.concatenate(parts)
+        Ud = torch.from_numpy(U if prec == "fp64" else U.astype(np.float32)).cuda()
+        Rd = torch.empty_like(Ud)
+        m.rhs(Ud, Rd)
+        m.sync_status()
+        R = Rd.cpu().numpy().astype(np.float64)
+        for i, (Ro, blocks) in enumerate(refs):
+            err = _rel_blocks(R[off[i]:off[i + 1]], Ro, blocks)
+            print(f"ensemble {prec} instance {i}: {err.max():.3e}")
+            assert err.max() <= (3e-12 if prec == "fp64" else 2e-5), (i, err)
+
+
+@pytest.mark.parametrize("kind", ["tet", "pyr"])
+def test_dense_ke_dissipation_reduced_precision(kind):
+    """Kinetic-energy dissipation rate after 50 RK4 steps (dt = 1e-3) on the 6^3-cell tetrahedral /
+    pyramidal box: the low-Mach FP32 trajectory against the FP64 one (itself pinned to the oracle by
+    the RK4 parity tests), 1e-3 relative; the FP64 trajectory's rate against the oracle's, 1e-9."""
+    mesh = W.box_tet_mesh(6) if kind == "tet" else W.box_pyr_mesh(6)
+    key, nu = ("tet_v", 20) if kind == "tet" else ("pyr_v", 30)
+    ne = mesh[key].shape[0]
+    p0 = W.tgv_p0()
+    m64 = fr.FRMesh(mesh, fr.make_params(p=3, p_ref=p0))
+    U0 = W.tgv_state(m64.sol_coords(), [(ne, nu)], perturb=1e-3)
+
+    def eps_after(prec):
+        m = fr.FRMesh(mesh, fr.make_params(p=3, prec=prec, p_ref=p0, rho_ref=1.0))
+        Ud = torch.from_numpy(U0).cuda()
+        m.rk4_step(Ud, 1e-3, 50)
+        m.sync_status()
+        Rd = torch.empty_like(Ud)
+        m64.rhs(Ud, Rd)
+        m64.sync_status()
+        return m64.diagnostics(Ud, Rd)[0]["eps"], Ud.cpu().numpy()
+
+    e64, U64 = eps_after("fp64")
+    e32, _ = eps_after("fp32")
+    o = O.Oracle(mesh, 3, 5, threads=NCPU, p_ref=p0)
+    Uo = o.rk4(U0, 1e-3, 50)
+    eo = o.diagnostics(Uo, o.rhs(Uo))["eps"]
+    print(f"{kind} eps after 50 steps: oracle {eo:.9e} fp64 {e64:.9e} fp32 {e32:.9e}")
+    assert abs(e64 / eo - 1) < 1e-9
+    assert abs(e32 / e64 - 1) < 1e-3
