@@ -34,6 +34,18 @@ template <typename T> __device__ __forceinline__ const HexOps<T> &OPS(int slot);
 template <> __device__ __forceinline__ const HexOps<double> &OPS<double>(int slot) { return c_hex64[slot]; }
 template <> __device__ __forceinline__ const HexOps<float> &OPS<float>(int slot) { return c_hex32[slot]; }
 
+// Even/odd form of the R x C line operator A (row stride ld) in both precisions.
+static void eo_fill(const double *A, int ld, int R, int C, HexEO<double> &d, HexEO<float> &f)
+{
+    for (int r = 0; r < (R + 1) / 2; r++) {
+        for (int c = 0; c < C / 2; c++) {
+            const double e = 0.5 * (A[r * ld + c] + A[r * ld + C - 1 - c]), o = 0.5 * (A[r * ld + c] - A[r * ld + C - 1 - c]);
+            d.e[r][c] = e; d.o[r][c] = o; f.e[r][c] = (float)e; f.o[r][c] = (float)o;
+        }
+        if (C % 2) { d.m[r] = A[r * ld + C / 2]; f.m[r] = (float)A[r * ld + C / 2]; }
+    }
+}
+
 int hex_upload_ops(int p, int m, const frb::Hex1D &h)
 {
     if (p < 2 || p > 4 || m != p + 2) return -1;
@@ -53,6 +65,10 @@ int hex_upload_ops(int p, int m, const frb::Hex1D &h)
         f.lL[i] = (float)h.lL[i]; f.lR[i] = (float)h.lR[i]; f.liftL[i] = (float)h.liftL[i];
         f.liftR[i] = (float)h.liftR[i]; f.w[i] = (float)h.w[i];
     }
+    const int n = p + 1;
+    eo_fill(&h.B[0][0], FR_MAXN, m, n, d.Beo, f.Beo);
+    eo_fill(&h.Pj[0][0], FR_MAXM, n, m, d.Peo, f.Peo);
+    eo_fill(&d.DP[0][0], FR_MAXM, n, m, d.DPeo, f.DPeo);
     HexOpsFF x{};
     for (int i = 0; i < FR_MAXN; i++) {
         x.lL[i] = ff_from_double(h.lL[i]); x.lR[i] = ff_from_double(h.lR[i]);
@@ -96,6 +112,30 @@ __device__ __forceinline__ void face_line_p(int f, int local, int &base, int &st
     if (d == 0) { base = XS * a + PS * b; stride = 1; }
     else if (d == 1) { base = a + PS * b; stride = XS; }
     else { base = a + XS * b; stride = PS; }
+}
+
+// y = A x along one line for an operator in even/odd form (HexEO), S = +1 symmetric, -1 antisymmetric.
+template <typename T, int C, int R, int S>
+__device__ __forceinline__ void line_eo(const HexEO<T> &A, const T (&x)[C], T (&y)[R])
+{
+    constexpr int CH = C / 2, RH = R / 2;
+    T xe[CH], xo[CH];
+#pragma unroll
+    for (int c = 0; c < CH; c++) { xe[c] = x[c] + x[C - 1 - c]; xo[c] = x[c] - x[C - 1 - c]; }
+#pragma unroll
+    for (int r = 0; r < RH; r++) {
+        T E = (C % 2) ? A.m[r] * x[CH] : T(0), O = T(0);
+#pragma unroll
+        for (int c = 0; c < CH; c++) { E += A.e[r][c] * xe[c]; O += A.o[r][c] * xo[c]; }
+        y[r] = E + O;
+        y[R - 1 - r] = S > 0 ? E - O : O - E;
+    }
+    if constexpr (R % 2) {   // middle row: the even part alone (S = +1) or the odd part alone (S = -1)
+        T v = (S > 0 && (C % 2)) ? A.m[RH] * x[CH] : T(0);
+#pragma unroll
+        for (int c = 0; c < CH; c++) v += S > 0 ? A.e[RH][c] * xe[c] : A.o[RH][c] * xo[c];
+        y[RH] = v;
+    }
 }
 
 template <int N>
@@ -287,43 +327,33 @@ __device__ __forceinline__ void interp_5(const HexOps<T> &op, const T *src, T *t
     for (int it = threadIdx.x; it < 5 * N * N; it += NT) {  // x: (fc, j, k)
         const int fc = it / (N * N), jk = it % (N * N);
         const int sb = fc * FS + XS * (jk % N) + PS * (jk / N);
-        T u[N];
+        T u[N], v[M];
 #pragma unroll
         for (int i = 0; i < N; i++) u[i] = src[sb + i];
+        line_eo<T, N, M, 1>(op.Beo, u, v);
 #pragma unroll
-        for (int q = 0; q < M; q++) {
-            T v = T(0);
-#pragma unroll
-            for (int i = 0; i < N; i++) v += op.B[q][i] * u[i];
-            t1[fc * M * N * N + q + M * jk] = v;
-        }
+        for (int q = 0; q < M; q++) t1[fc * M * N * N + q + M * jk] = v[q];
     }
     __syncthreads();
     for (int it = threadIdx.x; it < 5 * M * N; it += NT) {  // y: (fc, qa, k)
         const int fc = it / (M * N), r = it % (M * N), qa = r % M, k = r / M;
-        T u[N];
+        T u[N], v[M];
 #pragma unroll
         for (int j = 0; j < N; j++) u[j] = t1[fc * M * N * N + qa + M * j + M * N * k];
+        line_eo<T, N, M, 1>(op.Beo, u, v);
 #pragma unroll
-        for (int q = 0; q < M; q++) {
-            T v = T(0);
-#pragma unroll
-            for (int j = 0; j < N; j++) v += op.B[q][j] * u[j];
-            t2[fc * M * M * N + qa + M * q + M * M * k] = v;
-        }
+        for (int q = 0; q < M; q++) t2[fc * M * M * N + qa + M * q + M * M * k] = v[q];
     }
     __syncthreads();
     for (int it = threadIdx.x; it < 5 * M * M; it += NT) {  // z: (fc, qa, qb)
         const int fc = it / (M * M), ab = it % (M * M);
-        T u[N];
+        T u[N], v[M];
 #pragma unroll
         for (int k = 0; k < N; k++) u[k] = t2[fc * M * M * N + ab + M * M * k];
+        line_eo<T, N, M, 1>(op.Beo, u, v);
 #pragma unroll
         for (int q = 0; q < M; q++) {
-            T v = T(0);
-#pragma unroll
-            for (int k = 0; k < N; k++) v += op.B[q][k] * u[k];
-            dst[fc * NQ + ab + M * M * q] = v;
+            dst[fc * NQ + ab + M * M * q] = v[q];
         }
     }
     __syncthreads();
@@ -398,32 +428,48 @@ __device__ __forceinline__ void project_div(const HexOps<T> &op, T *src, T *tmp,
         for (int it = threadIdx.x; it < 5 * NG * M * M; it += NT) {   // z: (direction, alpha, qa qb) -> k
             const int g = it / (5 * M * M), r = it % (5 * M * M), alpha = r / (M * M), ab = r % (M * M);
             const int d = d0 + g;
-            const T(*Z)[FR_MAXM] = d == 2 ? op.DP : op.Pj;
             T u[M];
 #pragma unroll
             for (int c = 0; c < M; c++) u[c] = src[(alpha * 3 + d) * NQ + ab + M * M * c];
+            if constexpr (ALL) {
+                const T(*Z)[FR_MAXM] = d == 2 ? op.DP : op.Pj;
 #pragma unroll
-            for (int k = 0; k < N; k++) {
-                T v = T(0);
+                for (int k = 0; k < N; k++) {
+                    T v = T(0);
 #pragma unroll
-                for (int c = 0; c < M; c++) v += Z[k][c] * u[c];
-                tmp[(g * 5 + alpha) * M * M * N + ab + M * M * k] = v;
+                    for (int c = 0; c < M; c++) v += Z[k][c] * u[c];
+                    tmp[(g * 5 + alpha) * M * M * N + ab + M * M * k] = v;
+                }
+            } else {   // one direction per pass: the even/odd forms (DP is antisymmetric, Pj symmetric)
+                T v[N];
+                if (d == 2) line_eo<T, M, N, -1>(op.DPeo, u, v);
+                else line_eo<T, M, N, 1>(op.Peo, u, v);
+#pragma unroll
+                for (int k = 0; k < N; k++) tmp[(g * 5 + alpha) * M * M * N + ab + M * M * k] = v[k];
             }
         }
         __syncthreads();
         for (int it = threadIdx.x; it < 5 * NG * M * N; it += NT) {   // y: (direction, alpha, qa, k) -> j
             const int g = it / (5 * M * N), r = it % (5 * M * N), alpha = r / (M * N), r2 = r % (M * N);
             const int qa = r2 % M, k = r2 / M, d = d0 + g;
-            const T(*Y)[FR_MAXM] = d == 1 ? op.DP : op.Pj;
             T u[M];
 #pragma unroll
             for (int b = 0; b < M; b++) u[b] = tmp[(g * 5 + alpha) * M * M * N + qa + M * b + M * M * k];
+            if constexpr (ALL) {
+                const T(*Y)[FR_MAXM] = d == 1 ? op.DP : op.Pj;
 #pragma unroll
-            for (int j = 0; j < N; j++) {
-                T v = T(0);
+                for (int j = 0; j < N; j++) {
+                    T v = T(0);
 #pragma unroll
-                for (int b = 0; b < M; b++) v += Y[j][b] * u[b];
-                src[(alpha * 3 + d) * NQ + qa + M * j + M * N * k] = v;   // over the consumed input
+                    for (int b = 0; b < M; b++) v += Y[j][b] * u[b];
+                    src[(alpha * 3 + d) * NQ + qa + M * j + M * N * k] = v;   // over the consumed input
+                }
+            } else {
+                T v[N];
+                if (d == 1) line_eo<T, M, N, -1>(op.DPeo, u, v);
+                else line_eo<T, M, N, 1>(op.Peo, u, v);
+#pragma unroll
+                for (int j = 0; j < N; j++) src[(alpha * 3 + d) * NQ + qa + M * j + M * N * k] = v[j];   // over the consumed input
             }
         }
         __syncthreads();
@@ -435,14 +481,22 @@ __device__ __forceinline__ void project_div(const HexOps<T> &op, T *src, T *tmp,
         for (int i = 0; i < N; i++) v[i] = T(0);
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            const T(*X)[FR_MAXM] = d == 0 ? op.DP : op.Pj;
             T u[M];
 #pragma unroll
             for (int q = 0; q < M; q++) u[q] = src[(alpha * 3 + d) * NQ + q + M * jk];
+            if constexpr (ALL) {
+                const T(*X)[FR_MAXM] = d == 0 ? op.DP : op.Pj;
 #pragma unroll
-            for (int i = 0; i < N; i++)
+                for (int i = 0; i < N; i++)
 #pragma unroll
-                for (int q = 0; q < M; q++) v[i] += X[i][q] * u[q];
+                    for (int q = 0; q < M; q++) v[i] += X[i][q] * u[q];
+            } else {
+                T y[N];
+                if (d == 0) line_eo<T, M, N, -1>(op.DPeo, u, y);
+                else line_eo<T, M, N, 1>(op.Peo, u, y);
+#pragma unroll
+                for (int i = 0; i < N; i++) v[i] += y[i];
+            }
         }
 #pragma unroll
         for (int i = 0; i < N; i++) R[alpha * NU + i + N * jk] = v[i];

@@ -100,8 +100,22 @@ int pyr3d(Pyr3D &P);
 // ---------------------------------------------------------------------------------------------
 // Device-side operator tables (constant memory, one slot per hex order p = 2, 3, 4)
 // ---------------------------------------------------------------------------------------------
+// A line operator A (R outputs x C inputs) whose Gauss-Legendre node sets are symmetric about 0, so
+// that A[R-1-r][C-1-c] = S A[r][c] (S = +1 for interpolation and projection, -1 for operators with
+// one derivative), in even/odd form: with x_e[c] = x[c] + x[C-1-c] and x_o[c] = x[c] - x[C-1-c]
+// (c < C/2), E[r] = sum_c e[r][c] x_e[c] (+ m[r] x[C/2] for odd C) and O[r] = sum_c o[r][c] x_o[c]
+// give y[r] = E + O and y[R-1-r] = S (E - O) for r < R/2 (the middle row of odd R is E or O alone):
+// about half the multiply-adds of the plain product.
+template <typename T>
+struct HexEO {
+    T e[FR_MAXM][FR_MAXM];    // (A[r][c] + A[r][C-1-c]) / 2
+    T o[FR_MAXM][FR_MAXM];    // (A[r][c] - A[r][C-1-c]) / 2
+    T m[FR_MAXM];             // A[r][(C-1)/2] (odd C)
+};
+
 template <typename T>
 struct HexOps {
+    HexEO<T> Beo, Peo, DPeo;  // B, Pj and DP in even/odd form
     T B[FR_MAXM][FR_MAXN];
     T Pj[FR_MAXN][FR_MAXM];
     T DP[FR_MAXN][FR_MAXM];   // Dh Pj: projection followed by the corrected derivative
