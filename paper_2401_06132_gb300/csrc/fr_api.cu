@@ -768,7 +768,10 @@ static fr_status upload_dense_ff(fr_mesh *m, const REF &R, void **dst)
     for (int j = 0; j < NU; j++) {
         for (int s2 = 0; s2 < NF; s2++) split(R.M0[s2][j], h.M0t[j][s2], l.M0t[j][s2]);
         for (int d = 0; d < 3; d++)
-            for (int z = 0; z < NU; z++) split(R.Dh[d][z][j], h.Dht[d][j][z], l.Dht[d][j][z]);
+            for (int z = 0; z < NU; z++) {
+                split(R.Dh[d][z][j], h.Dht[d][j][z], l.Dht[d][j][z]);
+                o[0].Dht64[d][j][z] = R.Dh[d][z][j];
+            }
     }
     for (int s2 = 0; s2 < NF; s2++)
         for (int z = 0; z < NU; z++) split(R.L[z][s2], h.Lt[s2][z], l.Lt[s2][z]);

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__rest
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ short s_plist[NF];
     __shared__ int s_pcnt;
-    __shared__ ff s_mf[sizeof(T) == 4 ? 3 * NU : 1];   // low-Mach form: transformed mass flux
+    __shared__ __align__(8) double s_mfb[sizeof(T) == 4 ? 3 * NU : 1];   // low-Mach form: transformed mass flux
     constexpr int VW = V16<T>::n;
     constexpr int NCH = NTH / NU;                 // quadrature-point chunks of the projection
     T *s_u = reinterpret_cast<T *>(smem_raw);   // [5][NUS] state
@@ -148,25 +148,49 @@ __global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__rest
             // solution space, so its L2 projection is itself and the corrected divergence Dh applies
             // at the solution points)
             if (dev) {
+                // The dense product costs 3 NU^2 multiply-adds per element: on the tetrahedron (NU = 20)
+                // the FP64 pipe, idle in this kernel, does them faster than float-float arithmetic on
+                // the busy FP32 pipe; on the pyramid (NU = 30) the FP64 pipe would become the limit,
+                // so it stays in float-float (both about 48 bits or better).
                 const Geo<double> g64 = a.geo64[e];
-                ff cm[9];   // det J^-1
-#pragma unroll
-                for (int k = 0; k < 9; k++) cm[k] = ff_from_double(g64.det * g64.Ji[k]);
-                for (int z = threadIdx.x; z < NU; z += NTH) {
-                    const float m0 = s_u[NUS + z], m1 = s_u[2 * NUS + z], m2 = s_u[3 * NUS + z];
-#pragma unroll
-                    for (int d = 0; d < 3; d++)
-                        s_mf[d * NU + z] = ff_add(ff_add(ff_mul_f(cm[3 * d], m0), ff_mul_f(cm[3 * d + 1], m1)), ff_mul_f(cm[3 * d + 2], m2));
-                }
-                __syncthreads();
                 const FFOf<OPS> &o = *opsff;
                 const long long pbase = elem_u0(a, e, NU) / FR_NV;
-                for (int z = threadIdx.x; z < NU; z += NTH) {
-                    ff v = ff_of(0.0f);
+                if constexpr (NU <= 20) {
+                    double *s_mf = reinterpret_cast<double *>(s_mfb);
+                    for (int z = threadIdx.x; z < NU; z += NTH) {
+                        const double m0 = s_u[NUS + z], m1 = s_u[2 * NUS + z], m2 = s_u[3 * NUS + z];
 #pragma unroll
-                    for (int d = 0; d < 3; d++)
-                        for (int j = 0; j < NU; j++) v = ff_fma(ffat(o, o.hi.Dht[d][j][z]), s_mf[d * NU + j], v);
-                    a.RL[pbase + z] = v;
+                        for (int d = 0; d < 3; d++)
+                            s_mf[d * NU + z] = g64.det * (g64.Ji[3 * d] * m0 + g64.Ji[3 * d + 1] * m1 + g64.Ji[3 * d + 2] * m2);
+                    }
+                    __syncthreads();
+                    for (int z = threadIdx.x; z < NU; z += NTH) {
+                        double v = 0.0;
+#pragma unroll
+                        for (int d = 0; d < 3; d++)
+#pragma unroll 5
+                            for (int j = 0; j < NU; j++) v += o.Dht64[d][j][z] * s_mf[d * NU + j];
+                        a.RL[pbase + z] = ff_from_double(v);
+                    }
+                } else {
+                    ff *s_mf = reinterpret_cast<ff *>(s_mfb);
+                    ff cm[9];   // det J^-1
+#pragma unroll
+                    for (int k = 0; k < 9; k++) cm[k] = ff_from_double(g64.det * g64.Ji[k]);
+                    for (int z = threadIdx.x; z < NU; z += NTH) {
+                        const float m0 = s_u[NUS + z], m1 = s_u[2 * NUS + z], m2 = s_u[3 * NUS + z];
+#pragma unroll
+                        for (int d = 0; d < 3; d++)
+                            s_mf[d * NU + z] = ff_add(ff_add(ff_mul_f(cm[3 * d], m0), ff_mul_f(cm[3 * d + 1], m1)), ff_mul_f(cm[3 * d + 2], m2));
+                    }
+                    __syncthreads();
+                    for (int z = threadIdx.x; z < NU; z += NTH) {
+                        ff v = ff_of(0.0f);
+#pragma unroll
+                        for (int d = 0; d < 3; d++)
+                            for (int j = 0; j < NU; j++) v = ff_fma(ffat(o, o.hi.Dht[d][j][z]), s_mf[d * NU + j], v);
+                        a.RL[pbase + z] = v;
+                    }
                 }
             }
         }

@@ -163,6 +163,7 @@ template <typename T> using PyrOps = DenseOps<T, 30, 56, 5>;
 template <typename OPS32>
 struct DenseOpsFF {
     OPS32 hi, lo;
+    double Dht64[3][OPS32::NU][OPS32::NU];   // Dh in FP64, [d][j][z]: the mass channel's volume term
 };
 
 // Prism operators as float-float pairs: value = hi + lo (the low-Mach mass channel).
