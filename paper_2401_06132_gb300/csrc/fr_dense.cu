@@ -51,45 +51,95 @@ __device__ __forceinline__ ff ffat(const FF &o, const float &hi)
 // -------------------------------------------------------------------------------------------------
 // Phase A: disu (U^f = M0 U)
 // -------------------------------------------------------------------------------------------------
+// EPB elements per CTA iteration, one thread per (element, flux point). The states of the EPB
+// elements are staged in shared memory with coalesced loads; each thread keeps its column of M0 in
+// registers for the whole persistent loop and reads the state with 16-byte broadcast loads.
 // Low-Mach FP32 form (ph.dev): the face solution of the deviations from the reference state, and the
-// own-normal mass flux n.(rho v) at every flux point in float-float.
-template <typename T, typename OPS>
-__global__ void __launch_bounds__(256) k_dense_disu(HexArgs<T> a, const OPS *__restrict__ op, const FFOf<OPS> *__restrict__ opsff)
+// own-normal mass flux n.(rho v) at every flux point in float-float: first m_f = n_f . (rho v) at the
+// solution points per face (the face normal is constant on an affine element), then the compensated
+// dot product (Dot2 of Ogita, Rump and Oishi) of the float-float M0 row with m_f.
+template <typename T, typename OPS, int EPB>
+__global__ void __launch_bounds__(OPS::NF * EPB) k_dense_disu(HexArgs<T> a, const OPS *__restrict__ op, const FFOf<OPS> *__restrict__ opsff)
 {
-    constexpr int NU = OPS::NU, NF = OPS::NF;
-    const long long total = a.ne * FR_NV * NF;
-    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
-        const int s = (int)(it % NF);
-        const long long ea = it / NF;
-        const int alpha = (int)(ea % FR_NV);
-        const long long e = ea / FR_NV;
-        const T *ub = a.U + elem_u0(a, e, NU);
-        const T *u = ub + alpha * NU;
-        T off = T(0);
-        bool dev = false;
-        if constexpr (sizeof(T) == 4) {
-            const Phys<T> ph = elem_phys(a, e);
-            dev = ph.dev != 0;
-            if (dev) off = alpha == 0 ? ph.rref : (alpha == 4 ? ph.eref : T(0));
+    constexpr int NU = OPS::NU, NF = OPS::NF, NUS = OPS::NUS, NFACE = OPS::NFACE, NTH = NF * EPB;
+    constexpr bool F32 = sizeof(T) == 4;
+    constexpr int VN = V16<T>::n;
+    __shared__ __align__(16) T s_u[EPB][FR_NV * NUS];
+    __shared__ __align__(16) ff s_m[F32 ? EPB : 1][F32 ? NFACE * NUS : 1];
+    const int el = threadIdx.x / NF, s = threadIdx.x % NF;
+    T col[NUS];
+#pragma unroll
+    for (int z = 0; z < NUS; z++) col[z] = op->M0t[z][s];   // pad rows are zero
+    if constexpr (NUS > NU) {
+        for (int i = threadIdx.x; i < EPB * FR_NV * (NUS - NU); i += NTH) {
+            const int l = i / (FR_NV * (NUS - NU)), r = i % (FR_NV * (NUS - NU));
+            s_u[l][(r / (NUS - NU)) * NUS + NU + r % (NUS - NU)] = T(0);
         }
-        T v = T(0);
-#pragma unroll
-        for (int z = 0; z < NU; z++) v += op->M0t[z][s] * (u[z] - off);
-        a.UF[alpha * a.nfpt + elem_f0(a, e, NF) + s] = v;
-        if constexpr (sizeof(T) == 4) {
-            if (dev && alpha == 0) {
-                const ff *nt = a.fnrm64 + (e * 6 + OPS::FACE(s)) * 4;
-                ff mf = ff_of(0.0f);
-#pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    if (nt[k].hi == 0.0f) continue;
-                    ff w = ff_of(0.0f);
-                    for (int z = 0; z < NU; z++) w = ff_fma_f(ffat(*opsff, opsff->hi.M0t[z][s]), ub[(1 + k) * NU + z], w);
-                    mf = ff_fma(nt[k], w, mf);
-                }
-                a.MF[elem_f0(a, e, NF) + s] = mf;
+    }
+    const long long ng = (a.ne + EPB - 1) / EPB;
+    for (long long g = blockIdx.x; g < ng; g += gridDim.x) {
+        const long long e0 = g * EPB;
+        const int nel = (int)(a.ne - e0 < EPB ? a.ne - e0 : EPB);
+        for (int i = threadIdx.x; i < nel * FR_NV * NU; i += NTH) {
+            const int l = i / (FR_NV * NU), r = i % (FR_NV * NU), alpha = r / NU;
+            const long long e = e0 + l;
+            T v = a.U[elem_u0(a, e, NU) + r];
+            if constexpr (F32) {
+                const Phys<T> ph = elem_phys(a, e);
+                if (ph.dev) v -= alpha == 0 ? ph.rref : (alpha == 4 ? ph.eref : T(0));
+            }
+            s_u[l][alpha * NUS + r % NU] = v;
+        }
+        if constexpr (F32) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < nel * NFACE * NU; i += NTH) {
+                const int l = i / (NFACE * NU), r = i % (NFACE * NU), f = r / NU, z = r % NU;
+                const long long e = e0 + l;
+                if (!elem_phys(a, e).dev) continue;
+                const ff *nt = a.fnrm64 + (e * 6 + f) * 4;
+                const float *u = s_u[l];
+                ff m = ff_mul_f(nt[0], u[NUS + z]);
+                m = ff_add(m, ff_mul_f(nt[1], u[2 * NUS + z]));
+                s_m[l][f * NUS + z] = ff_add(m, ff_mul_f(nt[2], u[3 * NUS + z]));
             }
         }
+        __syncthreads();
+        if (el < nel) {
+            const long long e = e0 + el;
+            const long long f0 = elem_f0(a, e, NF);
+            const T *u = s_u[el];
+            T v[FR_NV];
+#pragma unroll
+            for (int alpha = 0; alpha < FR_NV; alpha++) v[alpha] = T(0);
+#pragma unroll
+            for (int z = 0; z < NUS; z += VN) {
+#pragma unroll
+                for (int alpha = 0; alpha < FR_NV; alpha++) {
+                    const V16<T> x = ld16(u + alpha * NUS + z);
+#pragma unroll
+                    for (int j = 0; j < VN; j++) v[alpha] += col[z + j] * x.v[j];
+                }
+            }
+#pragma unroll
+            for (int alpha = 0; alpha < FR_NV; alpha++) a.UF[alpha * a.nfpt + f0 + s] = v[alpha];
+            if constexpr (F32) {
+                if (elem_phys(a, e).dev) {
+                    const ff *m = s_m[el] + OPS::FACE(s) * NUS;
+                    float sh = 0.0f, c = 0.0f;
+#pragma unroll
+                    for (int z = 0; z < NU; z++) {
+                        const ff mz = m[z];
+                        const float pr = col[z] * mz.hi;
+                        const float er = __fmaf_rn(opsff->lo.M0t[z][s], mz.hi, __fmaf_rn(col[z], mz.lo, __fmaf_rn(col[z], mz.hi, -pr)));
+                        const ff t = two_sum(sh, pr);
+                        sh = t.hi;
+                        c += t.lo + er;
+                    }
+                    a.MF[f0 + s] = two_sum(sh, c);
+                }
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -355,23 +405,29 @@ __global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__rest
 // -------------------------------------------------------------------------------------------------
 // Phase C: interface group (common flux at every own flux point, lift and scale)
 // -------------------------------------------------------------------------------------------------
-template <typename T, int NTH, typename OPS>
-__global__ void __launch_bounds__(NTH) k_dense_C(HexArgs<T> a, const OPS *__restrict__ op, const FFOf<OPS> *__restrict__ opsff)
+template <typename T, typename OPS, int EPB>
+__global__ void __launch_bounds__(OPS::NF * EPB) k_dense_C(HexArgs<T> a, const OPS *__restrict__ op, const FFOf<OPS> *__restrict__ opsff)
 {
-    constexpr int NU = OPS::NU, NF = OPS::NF;
-    __shared__ T s_d[5 * NF];
-    __shared__ ff s_dff[sizeof(T) == 4 ? NF : 1];   // low-Mach form: transformed mass flux (float-float)
-    for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
-        const Geo<T> g = a.geo[e];
-        const Phys<T> ph = elem_phys(a, e);
-        const long long gf0 = elem_f0(a, e, NF);
-        bool dev = false;
-        if constexpr (sizeof(T) == 4) dev = ph.dev != 0;
+    constexpr int NU = OPS::NU, NF = OPS::NF, NTH = NF * EPB;
+    constexpr bool F32 = sizeof(T) == 4;
+    constexpr int VN = V16<T>::n;
+    static_assert(NF % VN == 0, "flux-point rows are whole 16-byte vectors");
+    __shared__ __align__(16) T s_d[EPB][FR_NV * NF];
+    __shared__ ff s_dff[F32 ? EPB : 1][F32 ? NF : 1];    // low-Mach form: scaled common mass flux (float-float)
+    __shared__ ff s_rr[F32 ? EPB : 1][F32 ? NU : 1];     // low-Mach form: R_rho (float-float)
+    const int el = threadIdx.x / NF, s = threadIdx.x % NF;
+    const long long ng = (a.ne + EPB - 1) / EPB;
+    for (long long g = blockIdx.x; g < ng; g += gridDim.x) {
+        const long long e0 = g * EPB;
+        const int nel = (int)(a.ne - e0 < EPB ? a.ne - e0 : EPB);
         bool ok = true;
-        for (int s = threadIdx.x; s < NF; s += NTH) {
-            const uint32_t pc = a.partner[gf0 + s];
+        if (el < nel) {
+            const long long e = e0 + el;
+            const Phys<T> ph = elem_phys(a, e);
+            const long long og = elem_f0(a, e, NF) + s;
+            const uint32_t pc = a.partner[og];
             const bool isL = (pc & FR_LFLAG) != 0;
-            const long long pg = pc & ~FR_LFLAG, og = gf0 + s;
+            const long long pg = pc & ~FR_LFLAG;
             T uo[5], up[5], fvo[4], fvp[4];
 #pragma unroll
             for (int k = 0; k < 5; k++) { uo[k] = a.UF[k * a.nfpt + og]; up[k] = a.UF[k * a.nfpt + pg]; }
@@ -381,72 +437,93 @@ __global__ void __launch_bounds__(NTH) k_dense_C(HexArgs<T> a, const OPS *__rest
             const T mag = nt[3];
             T nL[3] = {isL ? nt[0] : -nt[0], isL ? nt[1] : -nt[1], isL ? nt[2] : -nt[2]};
             T F[5];
-            if constexpr (sizeof(T) == 4) {
-                if (dev) {
+            bool dev = false;
+            if constexpr (F32) dev = ph.dev != 0;
+            if (dev) {
+                if constexpr (F32) {
                     float sw;
-                    ok &= isL ? common_flux_dev(ph, uo, up, fvo, fvp, nL, F, sw) : common_flux_dev(ph, up, uo, fvp, fvo, nL, F, sw);
+                    ok = isL ? common_flux_dev(ph, uo, up, fvo, fvp, nL, F, sw) : common_flux_dev(ph, up, uo, fvp, fvo, nL, F, sw);
                     // mass flux in float-float: 1/2 (mL - mR) + (s/2 + tau)(rho_L - rho_R), mX = own-normal n.(rho v)
                     const ff mo = a.MF[og], mp = a.MF[pg];
                     const ff mL = isL ? mo : mp, mR = isL ? mp : mo;
                     const float rL = isL ? uo[0] : up[0], rR = isL ? up[0] : uo[0];
                     const ff Fr = ff_add(ff_mul_f(ff_sub(mL, mR), 0.5f), ff_mul_f(two_sum(rL, -rR), 0.5f * sw + ph.tau));
                     const ff magf = a.fnrm64[(e * 6 + OPS::FACE(s)) * 4 + 3];
-                    s_dff[s] = isL ? ff_mul(magf, Fr) : ff_neg(ff_mul(magf, Fr));
-                } else {
-                    ok &= isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
+                    s_dff[el][s] = isL ? ff_mul(magf, Fr) : ff_neg(ff_mul(magf, Fr));
                 }
             } else {
-                ok &= isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
+                ok = isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
             }
             const T sc = isL ? mag : -mag;
 #pragma unroll
-            for (int k = 0; k < 5; k++) s_d[k * NF + s] = sc * F[k];
+            for (int k = 0; k < 5; k++) s_d[el][k * NF + s] = sc * F[k];
         }
         flag_status(a.status, ok);
         __syncthreads();
-        T *R = a.R + elem_u0(a, e, NU);
-        const T idet = T(-1) / g.det;
-        if (!dev) {
-            for (int it = threadIdx.x; it < 5 * NU; it += NTH) {
-                const int alpha = it / NU, z = it % NU;
-                const T *D = s_d + alpha * NF;
-                T v = R[it];
+        // lift and scale: R += L D, R *= -1/det; the mass rows of low-Mach elements in float-float,
+        // then the energy rows, which add H0 R_rho
+        for (int pass = 0; pass < 2; pass++) {
+            const int nrow = pass == 0 ? 4 : 1;
+            for (int i = threadIdx.x; i < nel * nrow * NU; i += NTH) {
+                const int l = i / (nrow * NU), alpha = pass == 0 ? (i / NU) % 4 : 4, z = i % NU;
+                const long long e = e0 + l;
+                const long long ui = elem_u0(a, e, NU) + alpha * NU + z;
+                bool dev = false;
+                if constexpr (F32) dev = elem_phys(a, e).dev != 0;
+                float outf = 0.0f;
+                T out;
+                if (F32 && dev && alpha == 0) {
+                    if constexpr (F32) {
+                        const ff r0 = a.RL[elem_u0(a, e, NU) / FR_NV + z];
+                        float sh = r0.hi, c = r0.lo;
+                        const ff *d = s_dff[l];
 #pragma unroll 8
-                for (int s = 0; s < NF; s++) v += op->Lt[s][z] * D[s];
-                if (a.rkstage == 0) R[it] = v * idet;
-                else rk_fold(a, elem_u0(a, e, NU) + it, v * idet);
-            }
-        } else if constexpr (sizeof(T) == 4) {
-            // low-Mach form: R_rho in float-float, R_E = R_(E - H0 rho) + H0 R_rho
-            const FFOf<OPS> &o = *opsff;
-            const ff idet64 = ff_from_double(-1.0 / a.geo64[e].det);
-            const ff H0 = ff_from_double(ph.H0d);
-            const long long pbase = elem_u0(a, e, NU) / FR_NV;
-            for (int z = threadIdx.x; z < NU; z += NTH) {
-                ff r = a.RL[pbase + z];
-                for (int s = 0; s < NF; s++) r = ff_fma(ffat(o, o.hi.Lt[s][z]), s_dff[s], r);
-                const ff Rrho = ff_mul(r, idet64);
-                float out[5];
-                out[0] = Rrho.hi + Rrho.lo;
+                        for (int s2 = 0; s2 < NF; s2++) {
+                            const float lh = op->Lt[s2][z], ll = opsff->lo.Lt[s2][z];
+                            const ff ds = d[s2];
+                            const float pr = lh * ds.hi;
+                            const float er = __fmaf_rn(ll, ds.hi, __fmaf_rn(lh, ds.lo, __fmaf_rn(lh, ds.hi, -pr)));
+                            const ff t = two_sum(sh, pr);
+                            sh = t.hi;
+                            c += t.lo + er;
+                        }
+                        const ff Rrho = ff_mul(two_sum(sh, c), ff_from_double(-1.0 / a.geo64[e].det));
+                        s_rr[l][z] = Rrho;
+                        outf = Rrho.hi + Rrho.lo;
+                    }
+                    out = (T)outf;
+                } else {
+                    const T *D = s_d[l] + alpha * NF;
+                    T v = a.R[ui];
+#pragma unroll 2
+                    for (int s2 = 0; s2 < NF; s2 += VN) {
+                        const V16<T> x = ld16(D + s2);
 #pragma unroll
-                for (int alpha = 1; alpha < 5; alpha++) {
-                    const T *D = s_d + alpha * NF;
-                    T v = R[alpha * NU + z];
-#pragma unroll 8
-                    for (int s = 0; s < NF; s++) v += op->Lt[s][z] * D[s];
-                    out[alpha] = v * idet;
+                        for (int j = 0; j < VN; j++) v += op->Lt[s2 + j][z] * x.v[j];
+                    }
+                    out = v * (T(-1) / a.geo[e].det);
+                    if constexpr (F32) {
+                        if (dev && alpha == 4) {
+                            const ff e4 = ff_fma(ff_from_double(elem_phys(a, e).H0d), s_rr[l][z], ff_of(out));
+                            out = e4.hi + e4.lo;
+                        }
+                    }
                 }
-                const ff e4 = ff_fma(H0, Rrho, ff_of(out[4]));
-                out[4] = e4.hi + e4.lo;
-#pragma unroll
-                for (int alpha = 0; alpha < 5; alpha++) {
-                    if (a.rkstage == 0) R[alpha * NU + z] = out[alpha];
-                    else rk_fold(a, elem_u0(a, e, NU) + alpha * NU + z, out[alpha]);
-                }
+                if (a.rkstage == 0) a.R[ui] = out;
+                else rk_fold(a, ui, out);
             }
+            if (F32 && pass == 0) __syncthreads();
         }
         __syncthreads();
     }
+}
+
+// persistent grid over groups of epb elements: at most per_sm CTAs per SM, 8 waves
+int grid_groups(long long ne, int epb, int per_sm)
+{
+    long long g = (ne + epb - 1) / epb;
+    if (g > 152LL * per_sm * 8) g = 152LL * per_sm * 8;
+    return (int)(g < 1 ? 1 : g);
 }
 
 int grid_elems(long long ne, int per_sm)
@@ -462,10 +539,7 @@ int dense_phase(int phase, const HexArgs<T> &a, const OPS *ops, const FFOf<OPS> 
     constexpr int NU = OPS::NU, NF = OPS::NF, NUS = OPS::NUS;
     if (a.ne == 0) return 0;
     if (phase == 0) {
-        long long work = a.ne * FR_NV * NF;
-        long long g = (work + 255) / 256;
-        if (g > 152LL * 64) g = 152LL * 64;
-        k_dense_disu<T, OPS><<<(int)g, 256, 0, s>>>(a, ops, opsff);
+        k_dense_disu<T, OPS, 4><<<grid_groups(a.ne, 4, 8), NF * 4, 0, s>>>(a, ops, opsff);
     } else if (phase == 1) {
         constexpr int NTH = 128;
         const size_t smem = (size_t)(20 * NUS + 5 * NF + 20 * NQP) * sizeof(T);
@@ -476,7 +550,7 @@ int dense_phase(int phase, const HexArgs<T> &a, const OPS *ops, const FFOf<OPS> 
         }
         k_dense_B<T, NTH, OPS><<<grid_elems(a.ne, 8), NTH, smem, s>>>(a, ops, opsff);
     } else {
-        k_dense_C<T, 128, OPS><<<grid_elems(a.ne, 8), 128, 0, s>>>(a, ops, opsff);
+        k_dense_C<T, OPS, 4><<<grid_groups(a.ne, 4, 8), NF * 4, 0, s>>>(a, ops, opsff);
     }
     (void)NU;
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
