@@ -273,17 +273,18 @@ def other_configs(args, torch, fr, W):
         m.close()
         del U
     # tetrahedra: the 24^3 box split into 82,944 Kuhn tetrahedra (p = 3, dense operators, collapsed
-    # 5^3 quadrature), FP64 and FP32 (reference pressure removed)
+    # 5^3 quadrature), FP64, FP32 and the mixed FP16 form with the interpolation on the tensor cores
+    # (reduced precisions in the low-Mach form: rho_ref = 1; FP64 ignores it)
     mesh_t = W.box_tet_mesh(24)
     nt = mesh_t["tet_v"].shape[0]
-    for prec in ("fp64", "fp32"):
-        # FP32 in the low-Mach form (rho_ref = 1; FP64 ignores it)
+    for name, prec in (("fp64", "fp64"), ("fp32", "fp32"), ("mixed_fp16_tc", "mixed_fp16")):
         m = fr.FRMesh(mesh_t, fr.make_params(p=3, prec=prec, p_ref=p0, rho_ref=1.0))
+        m.set_dense_tensor_cores(prec == "mixed_fp16")
         U0 = W.tgv_state(m.sol_coords(), [(nt, 20)], perturb=1e-3)
         U = torch.from_numpy(U0).cuda()
         ms = _time_steps(m, U, steps, 2, torch)
         m.sync_status()
-        out[f"tet24_{prec}"] = {"gdof_rhs_per_s": U0.size * RHS_PER_STEP / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+        out[f"tet24_{name}"] = {"gdof_rhs_per_s": U0.size * RHS_PER_STEP / (ms * 1e-3) / 1e9, "ms_per_step": ms,
                                 "dof": int(U0.size), "elements": nt}
         # the volume kernel alone (CUDA events around its launches in one RHS)
         Uc = U if prec == "fp64" else U.float()
@@ -295,13 +296,13 @@ def other_configs(args, torch, fr, W):
         kt = m.kernel_times()
         b_ms = kt[1][0] / max(1, kt[1][1])
         tfl = tet_phase_b_flops_per_element() * nt / (b_ms * 1e-3) / 1e12
-        out[f"tet24_{prec}"].update({"volume_kernel_ms": b_ms, "volume_tflops": tfl,
+        out[f"tet24_{name}"].update({"volume_kernel_ms": b_ms, "volume_tflops": tfl,
                                      "flops_per_element": tet_phase_b_flops_per_element()})
         if prec == "fp64":
-            out[f"tet24_{prec}"]["volume_frac_of_fp64_peak"] = tfl / FP64_PEAK_TFLOPS
+            out[f"tet24_{name}"]["volume_frac_of_fp64_peak"] = tfl / FP64_PEAK_TFLOPS
         del Uc, Rc
         if prec != "fp64":
-            out[f"tet24_{prec}"]["speedup_vs_fp64"] = out["tet24_fp64"]["ms_per_step"] / ms
+            out[f"tet24_{name}"]["speedup_vs_fp64"] = out["tet24_fp64"]["ms_per_step"] / ms
         m.close()
         del U
     # curved (trilinear) hexahedra, 48^3 p = 3: metric terms at every point; fused FP64 and plain

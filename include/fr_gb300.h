@@ -81,8 +81,8 @@ typedef enum {
                            * on the tensor cores as split products x_hi y_hi + x_lo y_hi + x_hi y_lo
                            * of bf16 halves with FP32 accumulation. Hexahedra run the FR_FP32
                            * kernels (their sum-factorised 1D operators are not dense contractions)
-                           * unless fr_set_hex_tensor_cores() is on; tetrahedra run the FR_FP32
-                           * kernels. */
+                           * unless fr_set_hex_tensor_cores() is on; tetrahedra and pyramids run
+                           * the FR_FP32 kernels unless fr_set_dense_tensor_cores() is on. */
     FR_MIXED_FP16 = 3     /* as FR_MIXED_BF16 with fp16 halves; every operand row is scaled by a
                            * power of two first (removed exactly afterwards) so that fp16 keeps
                            * its full precision in the low half */
@@ -241,6 +241,18 @@ fr_status fr_set_graph(fr_mesh *m, int on);
  * shared memory than the sweeps save). Results then differ from FR_FP32 at the split-product
  * rounding only. Takes effect at the next launch (and recaptures the RK4 graph). */
 fr_status fr_set_hex_tensor_cores(fr_mesh *m, int on);
+
+/* Mixed forms only: on = 1 moves the interpolation of the 20 fields (state and corrected gradient)
+ * to the 125 quadrature points of every tetrahedron and pyramid (a dense 125 x NU operator, Sec. 1
+ * element types without the Sec. 4 factorisation) to the split-product tensor-core path: one
+ * M = 128 (quadrature points) x N = 32 (fields) MMA chain per element over K = 3 NU, the operator
+ * split once per CTA. Default 0: the volume kernel of these types is bound by latency at six CTAs
+ * per SM, and the tensor-core tiles add shared memory and a wait per element, so the FP32 products
+ * on the CUDA cores are faster on GB300 (volume kernel 0.65 vs 0.71 ms per launch on the 20^3
+ * Kuhn box, 1.30 vs 1.86 ms on the 20^3 pyramid box). Results
+ * then differ from FR_FP32 at the split-product rounding only. Takes effect at the next launch (and
+ * recaptures the RK4 graph). */
+fr_status fr_set_dense_tensor_cores(fr_mesh *m, int on);
 
 /* Per-kernel timing (on = 1): CUDA events are recorded on the launching stream around every later
  * launch. fr_kernel_times waits for them and returns, per kernel id, the summed milliseconds and the

@@ -126,6 +126,7 @@ struct fr_mesh {
     cudaStream_t graph_stream = nullptr;
     int graph_form = -1;
     int hex_tc = 0;                      // mixed forms: hexahedral plane contractions on the tensor cores
+    int dense_tc = 0;                    // mixed forms: tetrahedral / pyramidal interpolation on the tensor cores
     // surface-flux anti-aliasing: face quadrature points (m x m per hex face) as interface points
     bool surf = false;
     long long nqf = 0;                   // face quadrature points of the handle
@@ -1145,6 +1146,13 @@ extern "C" fr_status fr_set_hex_tensor_cores(fr_mesh *m, int on)
     return FR_OK;
 }
 
+extern "C" fr_status fr_set_dense_tensor_cores(fr_mesh *m, int on)
+{
+    if (!m) return fail(FR_EINVAL, "null handle");
+    m->dense_tc = on != 0;
+    return FR_OK;
+}
+
 extern "C" fr_status fr_set_timing(fr_mesh *m, int on)
 {
     if (!m) return fail(FR_EINVAL, "null handle");
@@ -1202,6 +1210,7 @@ static HexArgs<T> make_args(fr_mesh *m, const Block &b, const void *U, void *R)
     a.status = m->d_status;
     a.tcmode = m->prec == FR_MIXED_FP16 ? 1 : (m->prec == FR_MIXED_BF16 ? 2 : 0);
     if (b.type == 0 && !m->hex_tc) a.tcmode = 0;
+    if ((b.type == 2 || b.type == 3) && !m->dense_tc) a.tcmode = 0;
     a.aa_off = b.m == b.p + 1;
     if (a.aa_off) a.tcmode = 0;
     if (m->surf) {
@@ -1469,27 +1478,57 @@ extern "C" fr_status fr_sync_status(fr_mesh *m, void *stream)
 // ---------------------------------------------------------------------------------------------
 // RK4
 // ---------------------------------------------------------------------------------------------
-template <typename T>
-__global__ void k_rk_cast(const double *__restrict__ U, T *__restrict__ us, long long n)
-{
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) us[i] = (T)U[i];
-}
-
-// After stage s (k = R(u_s)): acc (+)= b_s k; u_{s+1} = U + c_{s+1} dt k; the last stage updates U.
-template <typename T>
-__global__ void k_rk_update(double *__restrict__ U, const T *__restrict__ k, double *__restrict__ acc, T *__restrict__ us,
-                            long long n, double dt, int stage)
+// FP64 unfused form, after stage s (k = R(u_s)): acc (+)= b_s k; u_{s+1} = U + c_{s+1} dt k; the last
+// stage updates U.
+__global__ void k_rk_update64(double *__restrict__ U, const double *__restrict__ k, double *__restrict__ acc,
+                              double *__restrict__ us, long long n, double dt, int stage)
 {
     const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
     const double cnext[4] = {0.5, 0.5, 1.0, 0.0};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const double kv = (double)k[i];
+        const double kv = k[i];
         if (stage == 3) {
             U[i] += dt * (acc[i] + b[3] * kv);
         } else {
             const double a = (stage == 0 ? 0.0 : acc[i]) + b[stage] * kv;
             acc[i] = a;
-            us[i] = (T)(U[i] + cnext[stage] * dt * kv);
+            us[i] = U[i] + cnext[stage] * dt * kv;
+        }
+    }
+}
+
+// Reduced precisions. GB300 runs FP64 arithmetic and FP32<->FP64 conversions on its FP64 pipe, at
+// 1/64 of the FP32 rate, so the stage updates keep FP64 work to the two places that need it: at
+// the start of a step the FP64 master state U is split once into float halves U = hi + lo
+// (|lo| <= ulp(hi)/2); stage states u_{s+1} = hi + (lo + c_{s+1} dt k_s) and the Runge-Kutta sum
+// acc = sum b_s k_s are formed in FP32; the last stage adds the increment dt (acc + b_3 k_3) to U
+// in FP64. The increments carry an FP32 rounding on top of that of k itself; U stays FP64.
+template <typename T>
+__global__ void k_rk_split(const double *__restrict__ U, float *__restrict__ hi, float *__restrict__ lo, T *__restrict__ us,
+                           long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double u = U[i];
+        const float h = (float)u;
+        hi[i] = h;
+        lo[i] = (float)(u - (double)h);
+        us[i] = (T)h;
+    }
+}
+
+// After stage s (k = R(u_s)): acc (+)= b_s k; u_{s+1} = hi + (lo + c_{s+1} dt k); the last stage
+// updates U.
+template <typename T>
+__global__ void k_rk_update(double *__restrict__ U, const T *__restrict__ k, float *__restrict__ acc, const float *__restrict__ hi,
+                            const float *__restrict__ lo, T *__restrict__ us, long long n, double dt, float cdt, float b, int stage)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float kv = (float)k[i];
+        if (stage == 3) {
+            U[i] += dt * (double)(acc[i] + b * kv);
+        } else {
+            acc[i] = (stage == 0 ? 0.0f : acc[i]) + b * kv;
+            us[i] = (T)(hi[i] + (lo[i] + cdt * kv));
         }
     }
 }
@@ -1501,8 +1540,11 @@ static fr_status rk4_enqueue_step(fr_mesh *m, double *U, double dt, cudaStream_t
     const int thr = 256;
     const int grid = (int)std::min<long long>((n + thr - 1) / thr, 152LL * 16);
     const void *u0 = U;
+    // reduced precisions: d_rk_acc holds the FP32 Runge-Kutta sum and the float halves of U
+    float *accf = reinterpret_cast<float *>(m->d_rk_acc);
+    float *uhi = m->prec == FR_FP64 ? nullptr : accf + n, *ulo = m->prec == FR_FP64 ? nullptr : accf + 2 * n;
     if (m->prec != FR_FP64) {
-        k_rk_cast<T><<<grid, thr, 0, s>>>(U, reinterpret_cast<T *>(m->d_rk_us), n);
+        k_rk_split<T><<<grid, thr, 0, s>>>(U, uhi, ulo, reinterpret_cast<T *>(m->d_rk_us), n);
         u0 = m->d_rk_us;
     }
     for (int st = 0; st < 4; st++) {
@@ -1520,8 +1562,15 @@ static fr_status rk4_enqueue_step(fr_mesh *m, double *U, double dt, cudaStream_t
         fr_status r = rhs_dispatch(m, st == 0 ? u0 : m->d_rk_us, m->d_rk_k, s);
         if (r) return r;
         TimeScope ts(m, 30, s);
-        k_rk_update<T><<<grid, thr, 0, s>>>(U, reinterpret_cast<const T *>(m->d_rk_k), m->d_rk_acc,
-                                            reinterpret_cast<T *>(m->d_rk_us), n, dt, st);
+        if constexpr (sizeof(T) == 8) {
+            k_rk_update64<<<grid, thr, 0, s>>>(U, reinterpret_cast<const double *>(m->d_rk_k), m->d_rk_acc,
+                                               reinterpret_cast<double *>(m->d_rk_us), n, dt, st);
+        } else {
+            const double bs[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0}, cnext[4] = {0.5, 0.5, 1.0, 0.0};
+            k_rk_update<T><<<grid, thr, 0, s>>>(U, reinterpret_cast<const T *>(m->d_rk_k), accf, uhi, ulo,
+                                                reinterpret_cast<T *>(m->d_rk_us), n, dt, (float)(cnext[st] * dt),
+                                                (float)bs[st], st);
+        }
     }
     CU(cudaPeekAtLastError());
     return FR_OK;
@@ -1540,7 +1589,7 @@ static fr_status rk4_impl(fr_mesh *m, double *U, double dt, int nsteps, cudaStre
         return FR_OK;
     }
     int done = 0;
-    const int gform = m->form + 2 * m->hex_tc;
+    const int gform = m->form + 2 * m->hex_tc + 4 * m->dense_tc;
     if (!m->graph || m->graph_U != U || m->graph_dt != dt || m->graph_stream != s || m->graph_form != gform) {
         if (m->graph) { cudaGraphExecDestroy(m->graph); m->graph = nullptr; }
         // one eager step first: lazy workspace allocation and first-launch kernel attributes happen
@@ -1572,7 +1621,8 @@ extern "C" fr_status fr_rk4_step(fr_mesh *m, void *U_dev, double dt, int nsteps,
     size_t ts = tsize(m->prec);
     st = dalloc(m, &m->d_rk_k, (size_t)m->nU * ts);
     if (!st) st = dalloc(m, &m->d_rk_us, (size_t)m->nU * ts);
-    if (!st) st = dalloc(m, (void **)&m->d_rk_acc, (size_t)m->nU * sizeof(double));
+    // FP64: the Runge-Kutta sum; reduced precisions: its FP32 form and the float halves of U
+    if (!st) st = dalloc(m, (void **)&m->d_rk_acc, (size_t)m->nU * (m->prec == FR_FP64 ? sizeof(double) : 3 * sizeof(float)));
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
     st = m->prec == FR_FP64 ? rk4_impl<double>(m, (double *)U_dev, dt, nsteps, s) : rk4_impl<float>(m, (double *)U_dev, dt, nsteps, s);

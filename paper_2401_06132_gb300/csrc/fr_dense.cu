@@ -20,10 +20,28 @@
 
 #include "fr_internal.h"
 #include "fr_physics.cuh"
+#include "fr_tcgen05.cuh"
 
 namespace {
 
 constexpr int NQ = FR_TQ, NQP = FR_TQP;
+
+// Tensor-core interpolation of the mixed forms: D[q][f] = sum_j B[q][j] x_f[j] for the 20 fields
+// (state and gradient) of one element, M = 128 quadrature-point rows (125 used), N = 32 field rows
+// (20 used), K = three NU-wide slices [B_hi | B_hi | B_lo] against [x_hi | x_lo | x_hi], zero-padded
+// to a multiple of 16. The operator tile is split once per CTA; each element writes its 20 field
+// rows (scaled by a power of two per row) and reads its quadrature point's 20 values back from
+// tensor memory, one lane per thread.
+template <typename OPS>
+struct DenseTC {
+    static constexpr int KI = (3 * OPS::NU + 15) / 16 * 16;    // 64 (tetrahedron), 96 (pyramid)
+    static constexpr int SBO = KI / 8 * 128;
+    static constexpr int A_BYTES = 16 * SBO;                   // 128 rows
+    static constexpr int B_BYTES = 4 * SBO;                    // 32 rows
+    static constexpr int HEAD = A_BYTES + B_BYTES + 32 * 4 + 16;   // tiles, row shifts, barrier, TMEM slot
+    static constexpr int BYTES = HEAD + 128;                   // + alignment slack
+    static constexpr uint32_t IDESC1 = tc::idesc_f16(0, 128, 32), IDESC2 = tc::idesc_f16(1, 128, 32);
+};
 
 // 16 bytes of T (4 floats or 2 doubles): one vector shared-memory load
 template <typename T>
@@ -146,18 +164,50 @@ __global__ void __launch_bounds__(OPS::NF * EPB) k_dense_disu(HexArgs<T> a, cons
 // -------------------------------------------------------------------------------------------------
 // Phase B: volume group, one element per CTA of NTH threads (persistent over elements)
 // -------------------------------------------------------------------------------------------------
-template <typename T, int NTH, typename OPS>
+template <typename T, int NTH, typename OPS, int TCM>
 __global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__restrict__ op, const FFOf<OPS> *__restrict__ opsff)
 {
     constexpr int NU = OPS::NU, NF = OPS::NF, NFACE = OPS::NFACE, NUS = OPS::NUS;
     static_assert(NTH >= NQ, "one thread per quadrature point");
+    static_assert(TCM == 0 || (NTH == 128 && sizeof(T) == 4), "tensor-core form: FP32, one warpgroup per element");
+    using TC = DenseTC<OPS>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ short s_plist[NF];
     __shared__ int s_pcnt;
     __shared__ __align__(8) double s_mfb[sizeof(T) == 4 ? 3 * NU : 1];   // low-Mach form: transformed mass flux
     constexpr int VW = V16<T>::n;
     constexpr int NCH = NTH / NU;                 // quadrature-point chunks of the projection
-    T *s_u = reinterpret_cast<T *>(smem_raw);   // [5][NUS] state
+    unsigned char *arr = smem_raw;
+    // tensor-core state (TCM != 0): operator tile, field tile, row shifts, barrier, TMEM address
+    unsigned char *tA = nullptr, *tB = nullptr;
+    int *s_sh = nullptr;
+    uint64_t *mbar = nullptr;
+    uint32_t *s_tmem = nullptr, tmem = 0, parity = 0;
+    bool tc_fail = false;
+    if constexpr (TCM != 0) {
+        const uint32_t raw = tc::smem_u32(arr);
+        tA = arr + ((128 - (raw & 127)) & 127);
+        tB = tA + TC::A_BYTES;
+        s_sh = reinterpret_cast<int *>(tB + TC::B_BYTES);
+        mbar = reinterpret_cast<uint64_t *>(s_sh + 32);
+        s_tmem = reinterpret_cast<uint32_t *>(mbar + 1);
+        arr = tA + TC::HEAD;
+        tc::setup(mbar, s_tmem, 32);
+        for (int i = threadIdx.x; i < 128 * TC::KI; i += NTH) {   // [B_hi | B_hi | B_lo], rows q
+            const int n = i / TC::KI, k = i % TC::KI;
+            uint16_t h = 0, l = 0;
+            if (n < NQ && k < 3 * NU) tc::split16<TCM>((float)op->Bt[k % NU][n], h, l);
+            *reinterpret_cast<uint16_t *>(tA + tc::core_offset(n, k, TC::SBO)) = k < 2 * NU ? h : l;
+        }
+        for (int i = threadIdx.x; i < 32 * TC::KI; i += NTH)     // field rows 20..31 and the K pad stay zero
+            *reinterpret_cast<uint16_t *>(tB + tc::core_offset(i / TC::KI, i % TC::KI, TC::SBO)) = 0;
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        tmem = *s_tmem;
+    }
+    T *s_u = reinterpret_cast<T *>(arr);        // [5][NUS] state
     T *s_q = s_u + 5 * NUS;                       // [15][NUS] physical gradient (field 5 + 3 alpha + d of s_u)
     T *s_c = s_q + 15 * NUS;                      // [5][NF] common solution
     T *s_w = s_c + 5 * NF;                        // [20][NQP] fields at quadrature points, then f~
@@ -282,7 +332,55 @@ __global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__rest
                 s_plist[atomicAdd(&s_pcnt, 1)] = (short)s;
             }
         }
+        if constexpr (TCM != 0) {
+            // the 20 field rows (s_q follows s_u) for the tensor-core interpolation, four threads per
+            // row: [x_hi | x_lo | x_hi], scaled by 2^sh so that the row's largest magnitude lies in
+            // [2^14, 2^15); the MMA then runs while the viscous flux below is evaluated
+            if (threadIdx.x < 96) {   // warps 0-2, whole warps in the shuffles
+                const int r = threadIdx.x >> 2, sub = threadIdx.x & 3;
+                const bool row = r < 20;
+                constexpr int NV = (NU + 3) / 4;
+                float x[NV], mx = 0.f;
+#pragma unroll
+                for (int i = 0; i < NV; i++) {
+                    const int j = sub + 4 * i;
+                    x[i] = (row && j < NU) ? (float)s_u[r * NUS + j] : 0.f;
+                    mx = fmaxf(mx, fabsf(x[i]));
+                }
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+                if (row) {
+                    const int sh = tc::row_shift(mx);
+                    const float sc = tc::pow2f(sh);
+#pragma unroll
+                    for (int i = 0; i < NV; i++) {
+                        const int j = sub + 4 * i;
+                        if (j < NU) {
+                            uint16_t h, l;
+                            tc::split16<TCM>(x[i] * sc, h, l);
+                            *reinterpret_cast<uint16_t *>(tB + tc::core_offset(r, j, TC::SBO)) = h;
+                            *reinterpret_cast<uint16_t *>(tB + tc::core_offset(r, NU + j, TC::SBO)) = l;
+                            *reinterpret_cast<uint16_t *>(tB + tc::core_offset(r, 2 * NU + j, TC::SBO)) = h;
+                        }
+                    }
+                    if (sub == 0) s_sh[r] = sh;
+                }
+            }
+            tc::fence_async_smem();
+            tc::fence_before_sync();
+        }
         __syncthreads();
+        if constexpr (TCM != 0) {
+            if (threadIdx.x == 0) {
+                tc::fence_after_sync();
+                const uint32_t aA = tc::smem_u32(tA), aB = tc::smem_u32(tB);
+#pragma unroll
+                for (int j = 0; j < TC::KI / 16; j++)
+                    tc::mma_f16(tmem, tc::sdesc(aA + 256 * j, 128, TC::SBO), tc::sdesc(aB + 256 * j, 128, TC::SBO),
+                                TCM == 1 ? TC::IDESC1 : TC::IDESC2, j);
+                tc::commit(mbar);
+            }
+        }
         const int nplist = s_pcnt;
         for (int li = threadIdx.x; li < nplist; li += NTH) {
             const int s = s_plist[li];
@@ -316,25 +414,47 @@ __global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__rest
 #pragma unroll
             for (int k = 0; k < 4; k++) a.FV[k * a.nfpt + gf0 + s] = fvn[k];
         }
-        // interpolation of the 20 fields to the quadrature points: one point per thread
-        for (int q = threadIdx.x; q < NQ; q += NTH) {
-            T v[20];
-#pragma unroll
-            for (int f = 0; f < 20; f++) v[f] = T(0);
-#pragma unroll 1
-            for (int j0 = 0; j0 < NUS; j0 += VW) {
-                T b[VW];
-#pragma unroll
-                for (int k = 0; k < VW; k++) b[k] = op->Bt[j0 + k][q];
-#pragma unroll
-                for (int f = 0; f < 20; f++) {
-                    const V16<T> x = ld16(s_u + f * NUS + j0);
-#pragma unroll
-                    for (int k = 0; k < VW; k++) v[f] += b[k] * x.v[k];
-                }
+        if constexpr (TCM != 0) {
+            // the interpolation issued above: wait (bounded) and read lane q = this thread
+            const bool done = tc::mbar_wait(mbar, parity);
+            if (!__syncthreads_and(done)) {
+                tc_fail = true;
+                break;
             }
+            parity ^= 1;
+            tc::fence_after_sync();
+            float v0[16], v1[16];
+            const uint32_t ta = tmem + ((uint32_t)(32 * (threadIdx.x >> 5)) << 16);   // lane = quadrature point
+            tc::ld16(ta, v0);
+            tc::ld16(ta + 16, v1);
+            const int q = threadIdx.x;
+            if (q < NQ) {
 #pragma unroll
-            for (int f = 0; f < 20; f++) s_w[f * NQP + q] = v[f];
+                for (int f = 0; f < 16; f++) s_w[f * NQP + q] = v0[f] * tc::pow2f(-s_sh[f]);
+#pragma unroll
+                for (int f = 16; f < 20; f++) s_w[f * NQP + q] = v1[f - 16] * tc::pow2f(-s_sh[f]);
+            }
+        } else {
+            // interpolation of the 20 fields to the quadrature points: one point per thread
+            for (int q = threadIdx.x; q < NQ; q += NTH) {
+                T v[20];
+#pragma unroll
+                for (int f = 0; f < 20; f++) v[f] = T(0);
+#pragma unroll 1
+                for (int j0 = 0; j0 < NUS; j0 += VW) {
+                    T b[VW];
+#pragma unroll
+                    for (int k = 0; k < VW; k++) b[k] = op->Bt[j0 + k][q];
+#pragma unroll
+                    for (int f = 0; f < 20; f++) {
+                        const V16<T> x = ld16(s_u + f * NUS + j0);
+#pragma unroll
+                        for (int k = 0; k < VW; k++) v[f] += b[k] * x.v[k];
+                    }
+                }
+#pragma unroll
+                for (int f = 0; f < 20; f++) s_w[f * NQP + q] = v[f];
+            }
         }
         __syncthreads();
         bool ok = true;
@@ -400,6 +520,11 @@ __global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__rest
         }
         __syncthreads();
     }
+    if constexpr (TCM != 0) {
+        // a chain that did not complete within the bound is reported; the tensor memory is released
+        if (tc_fail && threadIdx.x == 0) atomicOr(a.status, 2);
+        tc::teardown(mbar, parity, tc_fail, tmem, 32);
+    }
 }
 
 // -------------------------------------------------------------------------------------------------
@@ -415,6 +540,7 @@ __global__ void __launch_bounds__(OPS::NF * EPB) k_dense_C(HexArgs<T> a, const O
     __shared__ __align__(16) T s_d[EPB][FR_NV * NF];
     __shared__ ff s_dff[F32 ? EPB : 1][F32 ? NF : 1];    // low-Mach form: scaled common mass flux (float-float)
     __shared__ ff s_rr[F32 ? EPB : 1][F32 ? NU : 1];     // low-Mach form: R_rho (float-float)
+    __shared__ ff s_idet[F32 ? EPB : 1];                 // low-Mach form: -1 / det J (float-float)
     const int el = threadIdx.x / NF, s = threadIdx.x % NF;
     const long long ng = (a.ne + EPB - 1) / EPB;
     for (long long g = blockIdx.x; g < ng; g += gridDim.x) {
@@ -450,6 +576,7 @@ __global__ void __launch_bounds__(OPS::NF * EPB) k_dense_C(HexArgs<T> a, const O
                     const ff Fr = ff_add(ff_mul_f(ff_sub(mL, mR), 0.5f), ff_mul_f(two_sum(rL, -rR), 0.5f * sw + ph.tau));
                     const ff magf = a.fnrm64[(e * 6 + OPS::FACE(s)) * 4 + 3];
                     s_dff[el][s] = isL ? ff_mul(magf, Fr) : ff_neg(ff_mul(magf, Fr));
+                    if (s == 0) s_idet[el] = ff_from_double(-1.0 / a.geo64[e].det);
                 }
             } else {
                 ok = isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
@@ -487,7 +614,7 @@ __global__ void __launch_bounds__(OPS::NF * EPB) k_dense_C(HexArgs<T> a, const O
                             sh = t.hi;
                             c += t.lo + er;
                         }
-                        const ff Rrho = ff_mul(two_sum(sh, c), ff_from_double(-1.0 / a.geo64[e].det));
+                        const ff Rrho = ff_mul(two_sum(sh, c), s_idet[l]);
                         s_rr[l][z] = Rrho;
                         outf = Rrho.hi + Rrho.lo;
                     }
@@ -542,13 +669,40 @@ int dense_phase(int phase, const HexArgs<T> &a, const OPS *ops, const FFOf<OPS> 
         k_dense_disu<T, OPS, 4><<<grid_groups(a.ne, 4, 8), NF * 4, 0, s>>>(a, ops, opsff);
     } else if (phase == 1) {
         constexpr int NTH = 128;
-        const size_t smem = (size_t)(20 * NUS + 5 * NF + 20 * NQP) * sizeof(T);
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_dense_B<T, NTH, OPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr = true;
+        const size_t base = (size_t)(20 * NUS + 5 * NF + 20 * NQP) * sizeof(T);
+        bool tcdone = false;
+        if constexpr (sizeof(T) == 4) {
+            if (a.tcmode != 0) {
+                tcdone = true;
+                const size_t smem = base + DenseTC<OPS>::BYTES;
+                // persistent: as many CTAs as fit on the SMs (shared memory, registers, and the 512
+                // tensor-memory columns at 32 per CTA)
+                auto kern = a.tcmode == 1 ? k_dense_B<T, NTH, OPS, 1> : k_dense_B<T, NTH, OPS, 2>;
+                static int occ[3] = {-1, -1, -1};
+                int &o = occ[a.tcmode];
+                if (o < 0) {
+                    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    cudaFuncAttributes fa{};
+                    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return -1;
+                    const int by_smem = (int)(232448 / (smem + fa.sharedSizeBytes + 1024));
+                    const int by_regs = 65536 / (((fa.numRegs + 7) / 8 * 8) * NTH);
+                    int v = by_smem < by_regs ? by_smem : by_regs;
+                    if (v > 512 / 32) v = 512 / 32;
+                    if (v < 1) return -4;
+                    o = v;
+                }
+                const long long g = a.ne < 152LL * o ? a.ne : 152LL * o;
+                kern<<<(int)g, NTH, smem, s>>>(a, ops, opsff);
+            }
         }
-        k_dense_B<T, NTH, OPS><<<grid_elems(a.ne, 8), NTH, smem, s>>>(a, ops, opsff);
+        if (!tcdone) {
+            static bool attr = false;
+            if (!attr) {
+                cudaFuncSetAttribute(k_dense_B<T, NTH, OPS, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)base);
+                attr = true;
+            }
+            k_dense_B<T, NTH, OPS, 0><<<grid_elems(a.ne, 8), NTH, base, s>>>(a, ops, opsff);
+        }
     } else {
         k_dense_C<T, OPS, 4><<<grid_groups(a.ne, 4, 8), NF * 4, 0, s>>>(a, ops, opsff);
     }

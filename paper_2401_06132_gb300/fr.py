@@ -72,6 +72,7 @@ def lib():
             "fr_set_timing": ([vp, C.c_int], C.c_int),
             "fr_set_graph": ([vp, C.c_int], C.c_int),
             "fr_set_hex_tensor_cores": ([vp, C.c_int], C.c_int),
+            "fr_set_dense_tensor_cores": ([vp, C.c_int], C.c_int),
             "fr_autotune": ([vp, vp, vp, C.POINTER(C.c_int), C.c_int, vp], C.c_int),
             "fr_kernel_times": ([vp, C.POINTER(C.c_double), llp, C.c_int], C.c_int),
             "fr_probe_fma": ([dp, vp], C.c_int),
@@ -227,6 +228,9 @@ class FRMesh:
 
     def set_hex_tensor_cores(self, on: bool):
         _check(lib().fr_set_hex_tensor_cores(self.h, int(on)))
+
+    def set_dense_tensor_cores(self, on: bool):
+        _check(lib().fr_set_dense_tensor_cores(self.h, int(on)))
 
     def set_timing(self, on: bool):
         _check(lib().fr_set_timing(self.h, int(on)))

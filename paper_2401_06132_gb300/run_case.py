@@ -31,6 +31,7 @@ def main(argv=None):
     ap.add_argument("--mach", type=float, default=0.1)
     ap.add_argument("--autotune", type=int, default=0, help="run the launch-shape autotuner first")
     ap.add_argument("--hex-tc", type=int, default=0, help="mixed forms: hexahedral plane contractions on the tensor cores")
+    ap.add_argument("--dense-tc", type=int, default=0, help="mixed forms: tetrahedral / pyramidal interpolation on the tensor cores")
     ap.add_argument("--surf", type=int, default=0, help="surface-flux anti-aliasing as well (full anti-aliasing)")
     ap.add_argument("--timing", type=int, default=0, help="per-kernel times (CUDA events) of one more RHS")
     args = ap.parse_args(argv)
@@ -48,6 +49,7 @@ def main(argv=None):
                                        rho_ref=1.0 if args.lowmach else 0.0, surface_aa=bool(args.surf)))
     m.set_form(args.form)
     m.set_hex_tensor_cores(bool(args.hex_tc))
+    m.set_dense_tensor_cores(bool(args.dense_tc))
     blocks = []
     if mesh["hex_v"].shape[0]:
         blocks.append((mesh["hex_v"].shape[0], (args.p + 1) ** 3))

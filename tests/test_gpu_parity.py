@@ -705,8 +705,9 @@ def test_tet_rk4_matches_oracle():
 
 @pytest.mark.parametrize("prec", ["fp32", "mixed_fp16"])
 def test_tet_fp32_matches_oracle(prec):
-    """The FP32 kernels (which the mixed forms run on tetrahedra) against the oracle on the
-    FP32-rounded input, with the reference pressure removed (measured 2e-5 on this grid)."""
+    """The FP32 kernels, and the mixed FP16 form (the interpolation to the quadrature points as
+    split FP16 products on the tensor cores), against the oracle on the FP32-rounded input, with the
+    reference pressure removed (measured 2e-5 on this grid)."""
     mesh = W.box_tet_mesh(4, shear=True)
     ne, nu = mesh["tet_v"].shape[0], 20
     p0 = W.tgv_p0()
@@ -963,6 +964,43 @@ def test_dense_lowmach_fp32_matches_oracle(name):
     dr = np.abs(Um.cpu().numpy() - Uo).max() / np.abs(Uo).max()
     print(f"dense low-Mach fp32 RK4 {name}: {dr:.3e}")
     assert dr <= 1e-6, dr
+
+
+@pytest.mark.parametrize("name", ["tetshear2", "tet4", "pyr3", "hexpyr2"])
+@pytest.mark.parametrize("lowmach", [True, False])
+def test_dense_mixed_forms_match_oracle(name, lowmach):
+    """The mixed forms on tetrahedra and pyramids with fr_set_dense_tensor_cores on: the interpolation of the 20 fields to the 125
+    quadrature points runs on the tensor cores as split products (K = [B_hi | B_hi | B_lo] against
+    [x_hi | x_lo | x_hi], rows scaled by powers of two), the rest as in the FP32 kernels. Against the
+    oracle on the FP32-rounded input: FP16 halves within 2e-5 in the low-Mach form and within 1e-4
+    in the plain form (the level of the plain FP32 form itself: 1.0-1.4e-4 on hexahedra, 2-6e-5 here),
+    BF16 halves within 1e-3; the low-Mach FP16 form also over three RK4 steps."""
+    mesh = {"tetshear2": lambda: W.box_tet_mesh(2, shear=True), "tet4": lambda: W.box_tet_mesh(4),
+            "pyr3": lambda: W.box_pyr_mesh(3), "hexpyr2": lambda: W.box_pyr_mesh(2, hex_below=1)}[name]()
+    blocks = [b for b in ((mesh["hex_v"].shape[0], 64), (mesh.get("tet_v", np.zeros((0, 4))).shape[0], 20),
+                          (mesh.get("pyr_v", np.zeros((0, 5))).shape[0], 30)) if b[0]]
+    p0 = W.tgv_p0()
+    o = O.Oracle(mesh, 3, 5, threads=NCPU, p_ref=p0)
+    U32 = W.tgv_state(o.sol_coords(), blocks, perturb=1e-2).astype(np.float32)
+    Ro = o.rhs(U32.astype(np.float64))
+    for prec, tol in (("mixed_fp16", 2e-5 if lowmach else 1e-4), ("mixed_bf16", 1e-3)):
+        m = fr.FRMesh(mesh, fr.make_params(p=3, prec=prec, p_ref=p0, rho_ref=1.0 if lowmach else 0.0))
+        m.set_dense_tensor_cores(True)
+        Ud = torch.from_numpy(U32).cuda()
+        Rd = torch.empty_like(Ud)
+        m.rhs(Ud, Rd)
+        m.sync_status()
+        err = _rel_blocks(Rd.cpu().numpy().astype(np.float64), Ro, blocks)
+        print(f"dense {prec} {'low-Mach' if lowmach else 'plain'} {name}: {err}")
+        assert err.max() <= tol, (prec, err)
+        if prec == "mixed_fp16" and lowmach:
+            Uo = o.rk4(U32.astype(np.float64), 1e-3, 3)
+            Um = torch.from_numpy(U32.astype(np.float64)).cuda()
+            m.rk4_step(Um, 1e-3, 3)
+            m.sync_status()
+            dr = np.abs(Um.cpu().numpy() - Uo).max() / np.abs(Uo).max()
+            print(f"dense {prec} low-Mach RK4 {name}: {dr:.3e}")
+            assert dr <= 1e-6, dr
 
 
 def test_heterogeneous_ensemble_matches_per_instance_oracles():
