@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(OPS::NF * EPB) k_dense_disu(HexArgs<T> a, cons
 // Phase B: volume group, one element per CTA of NTH threads (persistent over elements)
 // -------------------------------------------------------------------------------------------------
 template <typename T, int NTH, typename OPS, int TCM>
-__global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__restrict__ op, const FFOf<OPS> *__restrict__ opsff)
+__global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? (TCM == 0 ? 8 : 6) : 0) k_dense_B(HexArgs<T> a, const OPS *__restrict__ op, const FFOf<OPS> *__restrict__ opsff)
 {
     constexpr int NU = OPS::NU, NF = OPS::NF, NFACE = OPS::NFACE, NUS = OPS::NUS;
     static_assert(NTH >= NQ, "one thread per quadrature point");
@@ -175,6 +175,7 @@ __global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__rest
     __shared__ short s_plist[NF];
     __shared__ int s_pcnt;
     __shared__ __align__(8) double s_mfb[sizeof(T) == 4 ? 3 * NU : 1];   // low-Mach form: transformed mass flux
+    __shared__ __align__(8) double s_rlb[sizeof(T) == 4 ? 3 * NU : 1];   // low-Mach form: Dh_d of it, per d
     constexpr int VW = V16<T>::n;
     constexpr int NCH = NTH / NU;                 // quadrature-point chunks of the projection
     unsigned char *arr = smem_raw;
@@ -232,6 +233,34 @@ __global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__rest
             if (dev) v -= it < NU ? ph.rref : (it >= 4 * NU ? ph.eref : T(0));
             s_u[(it / NU) * NUS + it % NU] = v;
         }
+        if constexpr (sizeof(T) == 4) {
+            // low-Mach form: the volume part of R~_rho, sum_d Dh_d (det J J^-1 rho v)_d, in about 48
+            // bits or better (rho v lies in the solution space, so its L2 projection is itself and
+            // the corrected divergence Dh applies at the solution points). First the transformed
+            // mass flux (read from the state in global memory, so that it is ready at the first
+            // barrier); the 3 NU products Dh_d m_d then ride along with the gradient items below.
+            // The dense product costs 3 NU^2 multiply-adds per element: on the tetrahedron (NU = 20)
+            // the FP64 pipe, idle in this kernel, does them faster than float-float arithmetic on
+            // the busy FP32 pipe; on the pyramid (NU = 30) the FP64 pipe would become the limit, so
+            // it stays in float-float.
+            if (dev) {
+                const Geo<double> g64 = a.geo64[e];
+                for (int z = threadIdx.x; z < NU; z += NTH) {
+                    const float m0 = U[NU + z], m1 = U[2 * NU + z], m2 = U[3 * NU + z];
+#pragma unroll
+                    for (int d = 0; d < 3; d++) {
+                        if constexpr (NU <= 20) {
+                            s_mfb[d * NU + z] = g64.det * (g64.Ji[3 * d] * (double)m0 + g64.Ji[3 * d + 1] * (double)m1 + g64.Ji[3 * d + 2] * (double)m2);
+                        } else {
+                            ff *s_mf = reinterpret_cast<ff *>(s_mfb);
+                            const ff c0 = ff_from_double(g64.det * g64.Ji[3 * d]), c1 = ff_from_double(g64.det * g64.Ji[3 * d + 1]),
+                                     c2 = ff_from_double(g64.det * g64.Ji[3 * d + 2]);
+                            s_mf[d * NU + z] = ff_add(ff_add(ff_mul_f(c0, m0), ff_mul_f(c1, m1)), ff_mul_f(c2, m2));
+                        }
+                    }
+                }
+            }
+        }
         if (threadIdx.x == 0) s_pcnt = 0;
         for (int it = threadIdx.x; it < 5 * NF; it += NTH) {   // con_u
             const int alpha = it / NF, s = it % NF;
@@ -243,59 +272,37 @@ __global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__rest
             s_c[it] = (T(0.5) - ph.beta) * uL + (T(0.5) + ph.beta) * uR;
         }
         __syncthreads();
-        if constexpr (sizeof(T) == 4) {
-            // low-Mach form: the volume part of R~_rho in float-float (the mass flux rho v lies in the
-            // solution space, so its L2 projection is itself and the corrected divergence Dh applies
-            // at the solution points)
-            if (dev) {
-                // The dense product costs 3 NU^2 multiply-adds per element: on the tetrahedron (NU = 20)
-                // the FP64 pipe, idle in this kernel, does them faster than float-float arithmetic on
-                // the busy FP32 pipe; on the pyramid (NU = 30) the FP64 pipe would become the limit,
-                // so it stays in float-float (both about 48 bits or better).
-                const Geo<double> g64 = a.geo64[e];
-                const FFOf<OPS> &o = *opsff;
-                const long long pbase = elem_u0(a, e, NU) / FR_NV;
-                if constexpr (NU <= 20) {
-                    double *s_mf = reinterpret_cast<double *>(s_mfb);
-                    for (int z = threadIdx.x; z < NU; z += NTH) {
-                        const double m0 = s_u[NUS + z], m1 = s_u[2 * NUS + z], m2 = s_u[3 * NUS + z];
-#pragma unroll
-                        for (int d = 0; d < 3; d++)
-                            s_mf[d * NU + z] = g64.det * (g64.Ji[3 * d] * m0 + g64.Ji[3 * d + 1] * m1 + g64.Ji[3 * d + 2] * m2);
-                    }
-                    __syncthreads();
-                    for (int z = threadIdx.x; z < NU; z += NTH) {
+        // corrected gradient q~_d = Dh_d u + sum_f n_f,d (L_f c), then q = J^-T q~
+        const int ngrad = 5 * NU + (dev ? 3 * NU : 0);
+        for (int it = threadIdx.x; it < ngrad; it += NTH) {
+            if constexpr (sizeof(T) == 4) {
+                if (it >= 5 * NU) {   // low-Mach mass channel: (Dh_d m_d)[z]
+                    const int d = (it - 5 * NU) / NU, z = (it - 5 * NU) % NU;
+                    const FFOf<OPS> &o = *opsff;
+                    if constexpr (NU <= 20) {
                         double v = 0.0;
-#pragma unroll
-                        for (int d = 0; d < 3; d++)
 #pragma unroll 5
-                            for (int j = 0; j < NU; j++) v += o.Dht64[d][j][z] * s_mf[d * NU + j];
-                        a.RL[pbase + z] = ff_from_double(v);
+                        for (int j = 0; j < NU; j++) v += o.Dht64[d][j][z] * s_mfb[d * NU + j];
+                        s_rlb[d * NU + z] = v;
+                    } else {
+                        // compensated dot product (Dot2) of the float-float operator row and m_d
+                        const ff *m = reinterpret_cast<const ff *>(s_mfb) + d * NU;
+                        float sh = 0.0f, c = 0.0f;
+#pragma unroll 5
+                        for (int j = 0; j < NU; j++) {
+                            const float h = o.hi.Dht[d][j][z], l = o.lo.Dht[d][j][z];
+                            const ff mj = m[j];
+                            const float pr = h * mj.hi;
+                            const float er = __fmaf_rn(l, mj.hi, __fmaf_rn(h, mj.lo, __fmaf_rn(h, mj.hi, -pr)));
+                            const ff t = two_sum(sh, pr);
+                            sh = t.hi;
+                            c += t.lo + er;
+                        }
+                        reinterpret_cast<ff *>(s_rlb)[d * NU + z] = two_sum(sh, c);
                     }
-                } else {
-                    ff *s_mf = reinterpret_cast<ff *>(s_mfb);
-                    ff cm[9];   // det J^-1
-#pragma unroll
-                    for (int k = 0; k < 9; k++) cm[k] = ff_from_double(g64.det * g64.Ji[k]);
-                    for (int z = threadIdx.x; z < NU; z += NTH) {
-                        const float m0 = s_u[NUS + z], m1 = s_u[2 * NUS + z], m2 = s_u[3 * NUS + z];
-#pragma unroll
-                        for (int d = 0; d < 3; d++)
-                            s_mf[d * NU + z] = ff_add(ff_add(ff_mul_f(cm[3 * d], m0), ff_mul_f(cm[3 * d + 1], m1)), ff_mul_f(cm[3 * d + 2], m2));
-                    }
-                    __syncthreads();
-                    for (int z = threadIdx.x; z < NU; z += NTH) {
-                        ff v = ff_of(0.0f);
-#pragma unroll
-                        for (int d = 0; d < 3; d++)
-                            for (int j = 0; j < NU; j++) v = ff_fma(ffat(o, o.hi.Dht[d][j][z]), s_mf[d * NU + j], v);
-                        a.RL[pbase + z] = v;
-                    }
+                    continue;
                 }
             }
-        }
-        // corrected gradient q~_d = Dh_d u + sum_f n_f,d (L_f c), then q = J^-T q~
-        for (int it = threadIdx.x; it < 5 * NU; it += NTH) {
             const int alpha = it / NU, z = it % NU;
             const T *u = s_u + alpha * NUS;
             const T *c = s_c + alpha * NF;
@@ -320,6 +327,19 @@ __global__ void __launch_bounds__(NTH) k_dense_B(HexArgs<T> a, const OPS *__rest
             for (int k = 0; k < 3; k++) s_q[(alpha * 3 + k) * NUS + z] = g.Ji[k] * q0 + g.Ji[3 + k] * q1 + g.Ji[6 + k] * q2;
         }
         __syncthreads();
+        if constexpr (sizeof(T) == 4) {
+            if (dev) {
+                const long long pbase = elem_u0(a, e, NU) / FR_NV;
+                for (int z = threadIdx.x; z < NU; z += NTH) {
+                    if constexpr (NU <= 20) {
+                        a.RL[pbase + z] = ff_from_double(s_rlb[z] + s_rlb[NU + z] + s_rlb[2 * NU + z]);
+                    } else {
+                        const ff *r = reinterpret_cast<const ff *>(s_rlb);
+                        a.RL[pbase + z] = ff_add(ff_add(r[z], r[NU + z]), r[2 * NU + z]);
+                    }
+                }
+            }
+        }
         // viscous normal flux at own flux points, on the side whose LDG weight 1/2 +- beta is not
         // zero (the other side's is never used); the points are compacted so whole warps work
         for (int s = threadIdx.x; s < NF; s += NTH) {
