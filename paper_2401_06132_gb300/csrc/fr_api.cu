@@ -60,7 +60,7 @@ struct Group {
     void *d_phtab = nullptr;        // Phys<T> per instance
     uint32_t *d_lpts = nullptr;     // L flux points of the group (element_in_group * 256 + local)
     int variant = 1;                // volume-kernel launch shape (autotuned: 0, 1, 2 = 64, 128, 256 threads)
-    void *d_geo64 = nullptr;        // Geo<double> per element in group order (low-Mach form)
+    void *d_geo64 = nullptr;        // GeoLM per element in group order (low-Mach form)
     void *d_fnrm = nullptr;         // face normal table in group order
     double *d_fnrm64 = nullptr;
     long long nlpts = 0;
@@ -759,6 +759,17 @@ static fr_status upload_dense(fr_mesh *m, const REF &R, void **dst)
 
 // Float-float copy of the dense tables the low-Mach form's mass channel reads (M0, Dh, L):
 // hi = float(op), lo = float(op - hi).
+// The low-Mach geometry of one element from its FP64 inverse Jacobian and determinant (10 values).
+static GeoLM geo_lm(const double *src)
+{
+    GeoLM x;
+    for (int k = 0; k < 9; k++) x.Ji[k] = src[k];
+    x.det = src[9];
+    for (int k = 0; k < 9; k++) x.cm[k] = ff_from_double(x.det * x.Ji[k]);
+    x.idet = ff_from_double(-1.0 / x.det);
+    return x;
+}
+
 template <typename REF, typename OPSF>
 static fr_status upload_dense_ff(fr_mesh *m, const REF &R, void **dst)
 {
@@ -868,6 +879,7 @@ static Phys<T> phys_of(const fr_params &P)
     ph.rrefd = P.rho_ref;
     ph.H0d = P.rho_ref > 0 ? P.gamma * P.p_ref / ((P.gamma - 1.0) * P.rho_ref) : 0.0;
     ph.H0 = (T)ph.H0d;
+    ph.H0ff = ff_from_double(ph.H0d);
     return ph;
 }
 
@@ -967,20 +979,14 @@ static fr_status build_groups(fr_mesh *m, const std::vector<uint32_t> &partner)
             if (sn) return sn;
         }
         if (m->lowmach) {
-            std::vector<Geo<double>> g64;
+            std::vector<GeoLM> g64;
             for (int bi : g.blks) {
                 const Block &B = m->blocks[bi];
-                for (long long e = 0; e < B.ne; e++) {
-                    Geo<double> x;
-                    const double *src = &m->geo_host[(size_t)(B.elem0 + e) * 10];
-                    for (int k = 0; k < 9; k++) x.Ji[k] = src[k];
-                    x.det = src[9];
-                    g64.push_back(x);
-                }
+                for (long long e = 0; e < B.ne; e++) g64.push_back(geo_lm(&m->geo_host[(size_t)(B.elem0 + e) * 10]));
             }
-            fr_status sg = dalloc(m, &g.d_geo64, g64.size() * sizeof(Geo<double>));
+            fr_status sg = dalloc(m, &g.d_geo64, g64.size() * sizeof(GeoLM));
             if (sg) return sg;
-            CU(cudaMemcpy(g.d_geo64, g64.data(), g64.size() * sizeof(Geo<double>), cudaMemcpyHostToDevice));
+            CU(cudaMemcpy(g.d_geo64, g64.data(), g64.size() * sizeof(GeoLM), cudaMemcpyHostToDevice));
         }
         std::vector<Geo<T>> geo;
         std::vector<long long> eu0, ef0;
@@ -1053,13 +1059,10 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
     if (!st && m->lowmach && m->has_tet) st = upload_dense_ff<frb::Tet3D, TetOps<float>>(m, m->tet, &m->d_tetops64);
     if (!st && m->lowmach && m->has_pyr) st = upload_dense_ff<frb::Pyr3D, PyrOps<float>>(m, m->pyr, &m->d_pyrops64);
     if (!st && m->lowmach) {
-        std::vector<Geo<double>> g64((size_t)m->ne);
-        for (long long e = 0; e < m->ne; e++) {
-            for (int k = 0; k < 9; k++) g64[e].Ji[k] = m->geo_host[(size_t)e * 10 + k];
-            g64[e].det = m->geo_host[(size_t)e * 10 + 9];
-        }
-        st = dalloc(m, &m->d_geo64, g64.size() * sizeof(Geo<double>));
-        if (!st && cudaMemcpy(m->d_geo64, g64.data(), g64.size() * sizeof(Geo<double>), cudaMemcpyHostToDevice) != cudaSuccess)
+        std::vector<GeoLM> g64((size_t)m->ne);
+        for (long long e = 0; e < m->ne; e++) g64[e] = geo_lm(&m->geo_host[(size_t)e * 10]);
+        st = dalloc(m, &m->d_geo64, g64.size() * sizeof(GeoLM));
+        if (!st && cudaMemcpy(m->d_geo64, g64.data(), g64.size() * sizeof(GeoLM), cudaMemcpyHostToDevice) != cudaSuccess)
             st = fail(FR_ECUDA, "geometry upload failed");
         if (!st) st = dalloc(m, (void **)&m->d_MF, (size_t)m->nfpt * sizeof(ff));
         if (!st) st = dalloc(m, (void **)&m->d_RL, (size_t)(m->nU / FR_NV) * sizeof(ff));
@@ -1196,7 +1199,7 @@ static HexArgs<T> make_args(fr_mesh *m, const Block &b, const void *U, void *R)
     a.partner = m->d_partner;
     a.ph = phys_of<T>(I.prm);
     a.ph.dev = m->lowmach ? 1 : 0;
-    a.geo64 = m->d_geo64 ? reinterpret_cast<const Geo<double> *>(m->d_geo64) + b.elem0 : nullptr;
+    a.geo64 = m->d_geo64 ? reinterpret_cast<const GeoLM *>(m->d_geo64) + b.elem0 : nullptr;
     a.MF = reinterpret_cast<ff *>(m->d_MF);
     a.RL = reinterpret_cast<ff *>(m->d_RL);
     a.fnrm = m->d_fnrm ? reinterpret_cast<const T *>(m->d_fnrm) + b.elem0 * 24 : nullptr;
@@ -1309,7 +1312,7 @@ static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, co
                     a.ne = gr.ne; a.u0 = 0; a.f0 = 0;
                     a.geo = reinterpret_cast<const Geo<T> *>(gr.d_geo);
                     a.eu0 = gr.d_eu0; a.ef0 = gr.d_ef0; a.eph = gr.d_eph;
-                    if (m->lowmach) a.geo64 = reinterpret_cast<const Geo<double> *>(gr.d_geo64);
+                    if (m->lowmach) a.geo64 = reinterpret_cast<const GeoLM *>(gr.d_geo64);
                     a.fnrm = reinterpret_cast<const T *>(gr.d_fnrm);
                     a.fnrm64 = reinterpret_cast<const ff *>(gr.d_fnrm64);
                     a.phtab = reinterpret_cast<const Phys<T> *>(gr.d_phtab);
@@ -1374,7 +1377,7 @@ static fr_status autotune_impl(fr_mesh *m, const void *U, void *R, cudaStream_t 
             a.geo = reinterpret_cast<const Geo<T> *>(gr.d_geo);
             a.eu0 = gr.d_eu0; a.ef0 = gr.d_ef0; a.eph = gr.d_eph;
             a.phtab = reinterpret_cast<const Phys<T> *>(gr.d_phtab);
-            if (m->lowmach) a.geo64 = reinterpret_cast<const Geo<double> *>(gr.d_geo64);
+            if (m->lowmach) a.geo64 = reinterpret_cast<const GeoLM *>(gr.d_geo64);
             a.fnrm = reinterpret_cast<const T *>(gr.d_fnrm);
             a.fnrm64 = reinterpret_cast<const ff *>(gr.d_fnrm64);
         }
@@ -1397,7 +1400,7 @@ static fr_status autotune_impl(fr_mesh *m, const void *U, void *R, cudaStream_t 
             a.geo = reinterpret_cast<const Geo<T> *>(gr.d_geo);
             a.eu0 = gr.d_eu0; a.ef0 = gr.d_ef0; a.eph = gr.d_eph;
             a.phtab = reinterpret_cast<const Phys<T> *>(gr.d_phtab);
-            if (m->lowmach) a.geo64 = reinterpret_cast<const Geo<double> *>(gr.d_geo64);
+            if (m->lowmach) a.geo64 = reinterpret_cast<const GeoLM *>(gr.d_geo64);
             a.fnrm = reinterpret_cast<const T *>(gr.d_fnrm);
             a.fnrm64 = reinterpret_cast<const ff *>(gr.d_fnrm64);
         }

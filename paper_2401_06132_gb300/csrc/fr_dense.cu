@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? (TCM == 0 ? 8 : 6) : 0) 
             // the busy FP32 pipe; on the pyramid (NU = 30) the FP64 pipe would become the limit, so
             // it stays in float-float.
             if (dev) {
-                const Geo<double> g64 = a.geo64[e];
+                const GeoLM &g64 = a.geo64[e];
                 for (int z = threadIdx.x; z < NU; z += NTH) {
                     const float m0 = U[NU + z], m1 = U[2 * NU + z], m2 = U[3 * NU + z];
 #pragma unroll
@@ -253,9 +253,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? (TCM == 0 ? 8 : 6) : 0) 
                             s_mfb[d * NU + z] = g64.det * (g64.Ji[3 * d] * (double)m0 + g64.Ji[3 * d + 1] * (double)m1 + g64.Ji[3 * d + 2] * (double)m2);
                         } else {
                             ff *s_mf = reinterpret_cast<ff *>(s_mfb);
-                            const ff c0 = ff_from_double(g64.det * g64.Ji[3 * d]), c1 = ff_from_double(g64.det * g64.Ji[3 * d + 1]),
-                                     c2 = ff_from_double(g64.det * g64.Ji[3 * d + 2]);
-                            s_mf[d * NU + z] = ff_add(ff_add(ff_mul_f(c0, m0), ff_mul_f(c1, m1)), ff_mul_f(c2, m2));
+                            s_mf[d * NU + z] = ff_add(ff_add(ff_mul_f(g64.cm[3 * d], m0), ff_mul_f(g64.cm[3 * d + 1], m1)), ff_mul_f(g64.cm[3 * d + 2], m2));
                         }
                     }
                 }
@@ -596,7 +594,7 @@ __global__ void __launch_bounds__(OPS::NF * EPB) k_dense_C(HexArgs<T> a, const O
                     const ff Fr = ff_add(ff_mul_f(ff_sub(mL, mR), 0.5f), ff_mul_f(two_sum(rL, -rR), 0.5f * sw + ph.tau));
                     const ff magf = a.fnrm64[(e * 6 + OPS::FACE(s)) * 4 + 3];
                     s_dff[el][s] = isL ? ff_mul(magf, Fr) : ff_neg(ff_mul(magf, Fr));
-                    if (s == 0) s_idet[el] = ff_from_double(-1.0 / a.geo64[e].det);
+                    if (s == 0) s_idet[el] = a.geo64[e].idet;
                 }
             } else {
                 ok = isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
@@ -651,7 +649,7 @@ __global__ void __launch_bounds__(OPS::NF * EPB) k_dense_C(HexArgs<T> a, const O
                     out = v * (T(-1) / a.geo[e].det);
                     if constexpr (F32) {
                         if (dev && alpha == 4) {
-                            const ff e4 = ff_fma(ff_from_double(elem_phys(a, e).H0d), s_rr[l][z], ff_of(out));
+                            const ff e4 = ff_fma(elem_phys(a, e).H0ff, s_rr[l][z], ff_of(out));
                             out = e4.hi + e4.lo;
                         }
                     }

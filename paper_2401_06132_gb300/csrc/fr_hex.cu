@@ -880,10 +880,7 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
             // polynomial of the solution space, so its L2 projection is itself: no quadrature points)
             if (dev) {
                 const HexOpsFF &off = c_hexff[P - 2];
-                const Geo<double> g64 = a.geo64[e];
-                ff cm[9];   // det J^-1, per element
-#pragma unroll
-                for (int k = 0; k < 9; k++) cm[k] = ff_from_double(g64.det * g64.Ji[k]);
+                const ff *cm = a.geo64[e].cm;   // det J J^-1, per element
                 ff *s_mf = reinterpret_cast<ff *>(s_m64);
                 for (int it = threadIdx.x; it < NU; it += NT) {
                     const int pz = it % N + XS * ((it / N) % N) + PS * (it / (N * N));
@@ -1187,8 +1184,8 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
         } else if constexpr (std::is_same<T, float>::value) {
             // low-Mach form: R_rho in float-float, R_E = R_(E - H0 rho) + H0 R_rho
             const HexOpsFF &off = c_hexff[P - 2];
-            const ff idet64 = ff_from_double(-1.0 / a.geo64[e].det);
-            const ff H0 = ff_from_double(ph.H0d);
+            const ff idet64 = a.geo64[e].idet;
+            const ff H0 = ph.H0ff;
             const long long pbase = elem_u0(a, e, NU) / FR_NV;
             for (int z = threadIdx.x; z < NU; z += NT) {
                 const int i = z % N, j = (z / N) % N, k = z / (N * N);

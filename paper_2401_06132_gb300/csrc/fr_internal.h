@@ -180,6 +180,7 @@ struct Phys {
     // low-Mach FP32 form: deviations from (rref, 0, 0, 0, eref), reduced energy E - H0 rho
     T rref, eref, H0;
     double H0d, rrefd;
+    ff H0ff;      // H0 as a float-float pair
     int dev;
 };
 
@@ -188,6 +189,15 @@ template <typename T>
 struct Geo {
     T Ji[9];
     T det;
+};
+// The low-Mach form's geometry of one element: the FP64 inverse Jacobian and determinant, and the
+// float-float pairs its mass channel multiplies by, det J J^-1 (row-major) and -1 / det J, formed on
+// the host (FP64 arithmetic and conversions run at 1/64 of the FP32 rate on GB300).
+struct GeoLM {
+    double Ji[9];
+    double det;
+    ff cm[9];
+    ff idet;
 };
 
 // One block of elements of one type and order inside one instance.
@@ -236,7 +246,7 @@ struct HexArgs {
     // for s < 3; U += dt (acc + b_3 k) for s = 3.
     // Low-Mach FP32 form (ph.dev): FP64 geometry, own-normal mass flux n.(rho v) at flux points,
     // and the volume part of R~_rho per solution point, all in FP64
-    const Geo<double> *geo64;
+    const GeoLM *geo64;
     ff *MF;                   // float-float (about 48 bits; FP64 rates are 1/70 of FP32 on this chip)
     ff *RL;
     // Per element and face (6 slots; prisms use 5): unit outward normal and |n_s|, n_s = detJ J^-T n~

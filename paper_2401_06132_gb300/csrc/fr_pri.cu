@@ -348,10 +348,7 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
             // low-Mach form: volume part of R~_rho in FP64 (rho v lies in the solution space, so its
             // projection is itself and the corrected divergence applies at the solution points)
             if (dev) {
-                const Geo<double> g64 = a.geo64[e];
-                ff cm[9];   // det J^-1, per element
-#pragma unroll
-                for (int k = 0; k < 9; k++) cm[k] = ff_from_double(g64.det * g64.Ji[k]);
+                const ff *cm = a.geo64[e].cm;   // det J J^-1, per element
                 for (int z = threadIdx.x; z < NU; z += NTH) {
                     const float m0 = s_u[NU + z], m1 = s_u[2 * NU + z], m2 = s_u[3 * NU + z];
 #pragma unroll
@@ -670,8 +667,8 @@ __global__ void __launch_bounds__(NTH) k_pri_C(HexArgs<T> a, const PriOps<T> *go
         } else if constexpr (sizeof(T) == 4) {
             // low-Mach form: R_rho in float-float, R_E = R_(E - H0 rho) + H0 R_rho
             const PriOpsFF &o = *opsff;
-            const ff idet64 = ff_from_double(-1.0 / a.geo64[e].det);
-            const ff H0 = ff_from_double(ph.H0d);
+            const ff idet64 = a.geo64[e].idet;
+            const ff H0 = ph.H0ff;
             const long long pbase = elem_u0(a, e, NU) / FR_NV;
             for (int z = threadIdx.x; z < NU; z += NTH) {
                 const int k = z / NT_, t = z % NT_;
