@@ -199,27 +199,26 @@ __global__ void __launch_bounds__(NT) k_disu_blk(HexArgs<T> a)
             s_u[i] = v;
         }
         __syncthreads();
-        for (int it = threadIdx.x; it < FR_NV * nb * NF; it += NT) {
-            const int alpha = it / (nb * NF), r = it % (nb * NF), el = r / NF, sp = r % NF;
-            const int f = sp / (N * N), loc = sp % (N * N);
+        // one thread per (element, flux point), all five variables: the face line is located once
+        for (int it = threadIdx.x; it < nb * NF; it += NT) {
+            const int el = it / NF, sp = it % NF, f = sp / (N * N);
             int base, stride;
-            face_line<N>(f, loc, base, stride);
-            const T *u = s_u + (el * FR_NV + alpha) * NU + base;
+            face_line<N>(f, sp % (N * N), base, stride);
             const T *l = (f & 1) ? op.lR : op.lL;
-            T v = T(0);
+            const long long fo = elem_f0(a, e0 + el, NF) + sp;
 #pragma unroll
-            for (int i = 0; i < N; i++) v += l[i] * u[i * stride];
-            a.UF[alpha * a.nfpt + elem_f0(a, e0 + el, NF) + sp] = v;
-        }
-        if constexpr (std::is_same<T, float>::value) {
-            // low-Mach form: own-normal mass flux n.(rho v) at every flux point, in float-float
-            if (elem_phys(a, e0).dev) {
-                const HexOpsFF &off = c_hexff[P - 2];
-                for (int it = threadIdx.x; it < nb * NF; it += NT) {
-                    const int el = it / NF, sp = it % NF, f = sp / (N * N);
-                    int base, stride;
-                    face_line<N>(f, sp % (N * N), base, stride);
-                    const ff *l = (f & 1) ? off.lR : off.lL;
+            for (int alpha = 0; alpha < FR_NV; alpha++) {
+                const T *u = s_u + (el * FR_NV + alpha) * NU + base;
+                T v = T(0);
+#pragma unroll
+                for (int i = 0; i < N; i++) v += l[i] * u[i * stride];
+                a.UF[alpha * a.nfpt + fo] = v;
+            }
+            if constexpr (std::is_same<T, float>::value) {
+                // low-Mach form: own-normal mass flux n.(rho v) at every flux point, in float-float
+                if (elem_phys(a, e0 + el).dev) {
+                    const HexOpsFF &off = c_hexff[P - 2];
+                    const ff *lf = (f & 1) ? off.lR : off.lL;
                     const ff *nt = a.fnrm64 + ((e0 + el) * 6 + f) * 4;
                     ff mf = ff_of(0.0f);
 #pragma unroll
@@ -229,10 +228,10 @@ __global__ void __launch_bounds__(NT) k_disu_blk(HexArgs<T> a)
                         const T *u = s_u + (el * FR_NV + 1 + k) * NU + base;
                         ff v = ff_of(0.0f);
 #pragma unroll
-                        for (int i = 0; i < N; i++) v = ff_fma_f(l[i], u[i * stride], v);
+                        for (int i = 0; i < N; i++) v = ff_fma_f(lf[i], u[i * stride], v);
                         mf = ff_fma(nk, v, mf);
                     }
-                    a.MF[elem_f0(a, e0 + el, NF) + sp] = mf;
+                    a.MF[fo] = mf;
                 }
             }
         }
