@@ -1502,28 +1502,25 @@ __global__ void k_rk_update64(double *__restrict__ U, const double *__restrict__
 
 // Reduced precisions. GB300 runs FP64 arithmetic and FP32<->FP64 conversions on its FP64 pipe, at
 // 1/64 of the FP32 rate, so the stage updates keep FP64 work to the two places that need it: at
-// the start of a step the FP64 master state U is split once into float halves U = hi + lo
-// (|lo| <= ulp(hi)/2); stage states u_{s+1} = hi + (lo + c_{s+1} dt k_s) and the Runge-Kutta sum
-// acc = sum b_s k_s are formed in FP32; the last stage adds the increment dt (acc + b_3 k_3) to U
-// in FP64. The increments carry an FP32 rounding on top of that of k itself; U stays FP64.
+// the start of a step the FP64 master state U is rounded once to FP32, hi = fl32(U); stage states
+// u_{s+1} = hi + c_{s+1} dt k_s and the Runge-Kutta sum acc = sum b_s k_s are formed in FP32; the
+// last stage adds the increment dt (acc + b_3 k_3) to U in FP64. A stage state thus differs from
+// fl32(U + c dt k) by at most about one FP32 rounding (it is an FP32 input of the RHS either way);
+// the increments carry an FP32 rounding on top of that of k itself; U stays FP64.
 template <typename T>
-__global__ void k_rk_split(const double *__restrict__ U, float *__restrict__ hi, float *__restrict__ lo, T *__restrict__ us,
-                           long long n)
+__global__ void k_rk_split(const double *__restrict__ U, float *__restrict__ hi, T *__restrict__ us, long long n)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const double u = U[i];
-        const float h = (float)u;
+        const float h = (float)U[i];
         hi[i] = h;
-        lo[i] = (float)(u - (double)h);
         us[i] = (T)h;
     }
 }
 
-// After stage s (k = R(u_s)): acc (+)= b_s k; u_{s+1} = hi + (lo + c_{s+1} dt k); the last stage
-// updates U.
+// After stage s (k = R(u_s)): acc (+)= b_s k; u_{s+1} = hi + c_{s+1} dt k; the last stage updates U.
 template <typename T>
 __global__ void k_rk_update(double *__restrict__ U, const T *__restrict__ k, float *__restrict__ acc, const float *__restrict__ hi,
-                            const float *__restrict__ lo, T *__restrict__ us, long long n, double dt, float cdt, float b, int stage)
+                            T *__restrict__ us, long long n, double dt, float cdt, float b, int stage)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float kv = (float)k[i];
@@ -1531,7 +1528,7 @@ __global__ void k_rk_update(double *__restrict__ U, const T *__restrict__ k, flo
             U[i] += dt * (double)(acc[i] + b * kv);
         } else {
             acc[i] = (stage == 0 ? 0.0f : acc[i]) + b * kv;
-            us[i] = (T)(hi[i] + (lo[i] + cdt * kv));
+            us[i] = (T)(hi[i] + cdt * kv);
         }
     }
 }
@@ -1543,11 +1540,11 @@ static fr_status rk4_enqueue_step(fr_mesh *m, double *U, double dt, cudaStream_t
     const int thr = 256;
     const int grid = (int)std::min<long long>((n + thr - 1) / thr, 152LL * 16);
     const void *u0 = U;
-    // reduced precisions: d_rk_acc holds the FP32 Runge-Kutta sum and the float halves of U
+    // reduced precisions: d_rk_acc holds the FP32 Runge-Kutta sum and fl32(U)
     float *accf = reinterpret_cast<float *>(m->d_rk_acc);
-    float *uhi = m->prec == FR_FP64 ? nullptr : accf + n, *ulo = m->prec == FR_FP64 ? nullptr : accf + 2 * n;
+    float *uhi = m->prec == FR_FP64 ? nullptr : accf + n;
     if (m->prec != FR_FP64) {
-        k_rk_split<T><<<grid, thr, 0, s>>>(U, uhi, ulo, reinterpret_cast<T *>(m->d_rk_us), n);
+        k_rk_split<T><<<grid, thr, 0, s>>>(U, uhi, reinterpret_cast<T *>(m->d_rk_us), n);
         u0 = m->d_rk_us;
     }
     for (int st = 0; st < 4; st++) {
@@ -1570,7 +1567,7 @@ static fr_status rk4_enqueue_step(fr_mesh *m, double *U, double dt, cudaStream_t
                                                reinterpret_cast<double *>(m->d_rk_us), n, dt, st);
         } else {
             const double bs[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0}, cnext[4] = {0.5, 0.5, 1.0, 0.0};
-            k_rk_update<T><<<grid, thr, 0, s>>>(U, reinterpret_cast<const T *>(m->d_rk_k), accf, uhi, ulo,
+            k_rk_update<T><<<grid, thr, 0, s>>>(U, reinterpret_cast<const T *>(m->d_rk_k), accf, uhi,
                                                 reinterpret_cast<T *>(m->d_rk_us), n, dt, (float)(cnext[st] * dt),
                                                 (float)bs[st], st);
         }
@@ -1624,8 +1621,8 @@ extern "C" fr_status fr_rk4_step(fr_mesh *m, void *U_dev, double dt, int nsteps,
     size_t ts = tsize(m->prec);
     st = dalloc(m, &m->d_rk_k, (size_t)m->nU * ts);
     if (!st) st = dalloc(m, &m->d_rk_us, (size_t)m->nU * ts);
-    // FP64: the Runge-Kutta sum; reduced precisions: its FP32 form and the float halves of U
-    if (!st) st = dalloc(m, (void **)&m->d_rk_acc, (size_t)m->nU * (m->prec == FR_FP64 ? sizeof(double) : 3 * sizeof(float)));
+    // FP64: the Runge-Kutta sum; reduced precisions: its FP32 form and fl32(U) (the same bytes)
+    if (!st) st = dalloc(m, (void **)&m->d_rk_acc, (size_t)m->nU * sizeof(double));
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
     st = m->prec == FR_FP64 ? rk4_impl<double>(m, (double *)U_dev, dt, nsteps, s) : rk4_impl<float>(m, (double *)U_dev, dt, nsteps, s);
