@@ -246,10 +246,10 @@ fr_status fr_set_hex_tensor_cores(fr_mesh *m, int on);
  * to the 125 quadrature points of every tetrahedron and pyramid (a dense 125 x NU operator, Sec. 1
  * element types without the Sec. 4 factorisation) to the split-product tensor-core path: one
  * M = 128 (quadrature points) x N = 32 (fields) MMA chain per element over K = 3 NU, the operator
- * split once per CTA. Default 0: the volume kernel of these types is bound by latency at six CTAs
- * per SM, and the tensor-core tiles add shared memory and a wait per element, so the FP32 products
- * on the CUDA cores are faster on GB300 (volume kernel 0.65 vs 0.71 ms per launch on the 20^3
- * Kuhn box, 1.30 vs 1.86 ms on the 20^3 pyramid box). Results
+ * split once per CTA. Default 0: the volume kernel of these types is bound by latency, and the
+ * tensor-core tiles add shared memory and a wait per element, so the FP32 products
+ * on the CUDA cores are faster on GB300 (volume kernel 1.24 vs 1.47 ms per launch on the 24^3
+ * Kuhn box in the low-Mach form). Results
  * then differ from FR_FP32 at the split-product rounding only. Takes effect at the next launch (and
  * recaptures the RK4 graph). */
 fr_status fr_set_dense_tensor_cores(fr_mesh *m, int on);
