@@ -8,6 +8,31 @@
 // Point physics (Sec. 2.1): total flux f = f^e - f^v, viscous normal flux, Rusanov common flux
 // ---------------------------------------------------------------------------------------------
 
+// rho times the velocity gradient, w[i][d] = rho dv_i/dx_d = d(rho v_i)/dx_d - v_i d(rho)/dx_d; the
+// factor 1/rho is folded into the coefficients that multiply it (mu/rho, heat/rho).
+template <typename T>
+__device__ __forceinline__ void rho_dv(const T *v, const T (*g)[3], T (*w)[3])
+{
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int d = 0; d < 3; d++) w[i][d] = g[1 + i][d] - v[i] * g[0][d];
+}
+
+// The symmetric viscous stress tau[i][d] = mu (dv_i/dx_d + dv_d/dx_i) - 2/3 mu div v delta_id from
+// w = rho dv and mr = mu / rho (six distinct entries).
+template <typename T>
+__device__ __forceinline__ void viscous_stress(const T mr, const T (*w)[3], T (*tau)[3])
+{
+    const T lam = T(-2.0 / 3.0) * mr * (w[0][0] + w[1][1] + w[2][2]);
+    const T m2 = mr + mr;
+#pragma unroll
+    for (int i = 0; i < 3; i++) tau[i][i] = m2 * w[i][i] + lam;
+    tau[0][1] = tau[1][0] = mr * (w[0][1] + w[1][0]);
+    tau[0][2] = tau[2][0] = mr * (w[0][2] + w[2][0]);
+    tau[1][2] = tau[2][1] = mr * (w[1][2] + w[2][1]);
+}
+
 // Physical total flux f[d][alpha] from the state u and its physical gradient g[alpha][d].
 // Returns false for a non-physical state (rho <= 0, p <= 0 or non-finite).
 template <typename T>
@@ -17,26 +42,19 @@ __device__ __forceinline__ bool total_flux(const Phys<T> &ph, const T *u, const 
     const T v[3] = {u[1] * ir, u[2] * ir, u[3] * ir};
     const T E = u[4];
     const T p = ph.gm1 * (E - T(0.5) * (u[1] * v[0] + u[2] * v[1] + u[3] * v[2]));
-    T dv[3][3];  // dv[i][d] = d v_i / d x_d
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int d = 0; d < 3; d++) dv[i][d] = (g[1 + i][d] - v[i] * g[0][d]) * ir;
-    const T div = dv[0][0] + dv[1][1] + dv[2][2];
-    const T er = E * ir;
-    const T pm = p - ph.pref;
+    T w[3][3], tau[3][3];
+    rho_dv(v, g, w);
+    viscous_stress(ph.mu * ir, w, tau);
+    const T er = E * ir, hr = ph.heat * ir, pm = p - ph.pref, ep = E + p;
 #pragma unroll
     for (int d = 0; d < 3; d++) {
-        T tau[3];
-#pragma unroll
-        for (int i = 0; i < 3; i++) tau[i] = ph.mu * (dv[i][d] + dv[d][i]) - (i == d ? T(2.0 / 3.0) * ph.mu * div : T(0));
         // heat flux mu gamma/Pr [d(E/rho) - v.dv] = mu gamma/((gamma-1)Pr) d(p/rho)
-        const T phi = ph.heat * ((g[4][d] - er * g[0][d]) * ir - (v[0] * dv[0][d] + v[1] * dv[1][d] + v[2] * dv[2][d]));
+        const T phi = hr * ((g[4][d] - er * g[0][d]) - (v[0] * w[0][d] + v[1] * w[1][d] + v[2] * w[2][d]));
         f[d][0] = u[1 + d];
-        f[d][1] = u[1] * v[d] + (d == 0 ? pm : T(0)) - tau[0];
-        f[d][2] = u[2] * v[d] + (d == 1 ? pm : T(0)) - tau[1];
-        f[d][3] = u[3] * v[d] + (d == 2 ? pm : T(0)) - tau[2];
-        f[d][4] = v[d] * (E + p) - (v[0] * tau[0] + v[1] * tau[1] + v[2] * tau[2] + phi);
+        f[d][1] = u[1] * v[d] + (d == 0 ? pm : T(0)) - tau[0][d];
+        f[d][2] = u[2] * v[d] + (d == 1 ? pm : T(0)) - tau[1][d];
+        f[d][3] = u[3] * v[d] + (d == 2 ? pm : T(0)) - tau[2][d];
+        f[d][4] = v[d] * ep - (v[0] * tau[0][d] + v[1] * tau[1][d] + v[2] * tau[2][d] + phi);
     }
     return rho > T(0) && p > T(0) && isfinite(p) && isfinite(f[0][4] + f[1][4] + f[2][4]);
 }
@@ -47,27 +65,17 @@ __device__ __forceinline__ void viscous_normal_flux(const Phys<T> &ph, const T *
 {
     const T rho = u[0], ir = T(1) / rho;
     const T v[3] = {u[1] * ir, u[2] * ir, u[3] * ir};
-    T dv[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int d = 0; d < 3; d++) dv[i][d] = (g[1 + i][d] - v[i] * g[0][d]) * ir;
-    const T div = dv[0][0] + dv[1][1] + dv[2][2];
+    T w[3][3], tau[3][3];
+    rho_dv(v, g, w);
+    viscous_stress(ph.mu * ir, w, tau);
     const T er = u[4] * ir;
-    T acc[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
-        T tau[3];
+    for (int i = 0; i < 3; i++) fvn[i] = n[0] * tau[i][0] + n[1] * tau[i][1] + n[2] * tau[i][2];
+    // n . (tau v + phi) = v . (tau n) + n . phi
+    T nphi = T(0);
 #pragma unroll
-        for (int i = 0; i < 3; i++) tau[i] = ph.mu * (dv[i][d] + dv[d][i]) - (i == d ? T(2.0 / 3.0) * ph.mu * div : T(0));
-        const T phi = ph.heat * ((g[4][d] - er * g[0][d]) * ir - (v[0] * dv[0][d] + v[1] * dv[1][d] + v[2] * dv[2][d]));
-        acc[0] += n[d] * tau[0];
-        acc[1] += n[d] * tau[1];
-        acc[2] += n[d] * tau[2];
-        acc[3] += n[d] * (v[0] * tau[0] + v[1] * tau[1] + v[2] * tau[2] + phi);
-    }
-#pragma unroll
-    for (int a = 0; a < 4; a++) fvn[a] = acc[a];
+    for (int d = 0; d < 3; d++) nphi += n[d] * ((g[4][d] - er * g[0][d]) - (v[0] * w[0][d] + v[1] * w[1][d] + v[2] * w[2][d]));
+    fvn[3] = v[0] * fvn[0] + v[1] * fvn[1] + v[2] * fvn[2] + ph.heat * ir * nphi;
 }
 
 // Common physical normal flux along nL (Rusanov inviscid part, LDG viscous part and penalty):
@@ -124,25 +132,19 @@ __device__ __forceinline__ bool total_flux_dev(const Phys<float> &ph, const floa
     const float rho = ph.rref + w[0], ir = 1.0f / rho;
     const float v[3] = {w[1] * ir, w[2] * ir, w[3] * ir};
     const float pd = ph.gm1 * (w[4] - 0.5f * (w[1] * v[0] + w[2] * v[1] + w[3] * v[2]));
-    const float er = (ph.eref + w[4]) * ir;
-    float dv[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int d = 0; d < 3; d++) dv[i][d] = (g[1 + i][d] - v[i] * g[0][d]) * ir;
-    const float div = dv[0][0] + dv[1][1] + dv[2][2];
+    const float er = (ph.eref + w[4]) * ir, hr = ph.heat * ir;
+    float rw[3][3], tau[3][3];
+    rho_dv(v, g, rw);
+    viscous_stress(ph.mu * ir, rw, tau);
     const float hred = w[4] + pd - ph.H0 * w[0];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
-        float tau[3];
-#pragma unroll
-        for (int i = 0; i < 3; i++) tau[i] = ph.mu * (dv[i][d] + dv[d][i]) - (i == d ? (2.0f / 3.0f) * ph.mu * div : 0.0f);
-        const float phi = ph.heat * ((g[4][d] - er * g[0][d]) * ir - (v[0] * dv[0][d] + v[1] * dv[1][d] + v[2] * dv[2][d]));
+        const float phi = hr * ((g[4][d] - er * g[0][d]) - (v[0] * rw[0][d] + v[1] * rw[1][d] + v[2] * rw[2][d]));
         f[d][0] = 0.0f;
-        f[d][1] = w[1] * v[d] + (d == 0 ? pd : 0.0f) - tau[0];
-        f[d][2] = w[2] * v[d] + (d == 1 ? pd : 0.0f) - tau[1];
-        f[d][3] = w[3] * v[d] + (d == 2 ? pd : 0.0f) - tau[2];
-        f[d][4] = v[d] * hred - (v[0] * tau[0] + v[1] * tau[1] + v[2] * tau[2] + phi);
+        f[d][1] = w[1] * v[d] + (d == 0 ? pd : 0.0f) - tau[0][d];
+        f[d][2] = w[2] * v[d] + (d == 1 ? pd : 0.0f) - tau[1][d];
+        f[d][3] = w[3] * v[d] + (d == 2 ? pd : 0.0f) - tau[2][d];
+        f[d][4] = v[d] * hred - (v[0] * tau[0][d] + v[1] * tau[1][d] + v[2] * tau[2][d] + phi);
     }
     return rho > 0.0f && ph.pref + pd > 0.0f && isfinite(pd) && isfinite(f[0][4] + f[1][4] + f[2][4]);
 }
