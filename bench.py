@@ -40,9 +40,9 @@ def workload_name(n=N_EDGE, p=P, m=MQ):
 # FP64 peak of the chip from its unit counts and clock: 152 SMs x 2 FP64 FMA/clock x 2 FLOP x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + written) per element of one FP64 volume-kernel launch, from one Nsight Compute
-# capture of that kernel on the 32^3 p = 3 box (385.7 MB / 32,768 elements); the kernel touches each
+# capture of that kernel on the 32^3 p = 3 box (385.2 MB / 32,768 elements); the kernel touches each
 # element's inputs and outputs once, so a launch's traffic scales with its element count
-VOLUME_FP64_DRAM_BYTES_PER_ELEMENT = 385.74e6 / 32768
+VOLUME_FP64_DRAM_BYTES_PER_ELEMENT = 385.17e6 / 32768
 
 # ---------------------------------------------------------------------------------------------
 # FLOP model of the fused volume kernel (phase B), FMA = 2 FLOP; counted from its arithmetic
