@@ -861,6 +861,7 @@ static fr_status upload_geo(fr_mesh *m)
     for (long long e = 0; e < m->ne; e++) {
         for (int k = 0; k < 9; k++) g[e].Ji[k] = (T)m->geo_host[(size_t)e * 10 + k];
         g[e].det = (T)m->geo_host[(size_t)e * 10 + 9];
+        g[e].nidet = T(-1) / g[e].det;
     }
     fr_status st = dalloc(m, &m->d_geo, g.size() * sizeof(Geo<T>));
     if (st) return st;
@@ -998,6 +999,7 @@ static fr_status build_groups(fr_mesh *m, const std::vector<uint32_t> &partner)
                 const double *src = &m->geo_host[(size_t)(B.elem0 + e) * 10];
                 for (int k = 0; k < 9; k++) x.Ji[k] = (T)src[k];
                 x.det = (T)src[9];
+                x.nidet = T(-1) / x.det;
                 geo.push_back(x);
                 eu0.push_back(B.u0 + e * FR_NV * B.nu);
                 ef0.push_back(B.f0 + e * B.nf);

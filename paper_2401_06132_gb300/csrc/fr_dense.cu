@@ -646,7 +646,7 @@ __global__ void __launch_bounds__(OPS::NF * EPB) k_dense_C(HexArgs<T> a, const O
 #pragma unroll
                         for (int j = 0; j < VN; j++) v += op->Lt[s2 + j][z] * x.v[j];
                     }
-                    out = v * (T(-1) / a.geo[e].det);
+                    out = v * a.geo[e].nidet;
                     if constexpr (F32) {
                         if (dev && alpha == 4) {
                             const ff e4 = ff_fma(elem_phys(a, e).H0ff, s_rr[l][z], ff_of(out));

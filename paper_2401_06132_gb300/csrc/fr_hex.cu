@@ -1166,7 +1166,7 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
         flag_status(a.status, ok);
         __syncthreads();
         T *R = a.R + elem_u0(a, e, NU);
-        const T idet = T(-1) / g.det;
+        const T idet = g.nidet;
         if (!dev) {
             for (int it = threadIdx.x; it < 5 * NU; it += NT) {
                 const int alpha = it / NU, z = it % NU, i = z % N, j = (z / N) % N, k = z / (N * N);
@@ -1291,7 +1291,7 @@ __global__ void __launch_bounds__(NT) k_surf_lift(HexArgs<T> a)
         }
         __syncthreads();
         T *R = a.R + elem_u0(a, e, NU);
-        const T idet = T(-1) / g.det;
+        const T idet = g.nidet;
         for (int it = threadIdx.x; it < 5 * NU; it += NT) {
             const int alpha = it / NU, z = it % NU, i = z % N, j = (z / N) % N, k = z / (N * N);
             const T *D = s_d + alpha * NF;
@@ -1361,7 +1361,7 @@ __global__ void __launch_bounds__(NT) k_lift(HexArgs<T> a)
         }
         __syncthreads();
         T *R = a.R + elem_u0(a, e, NU);
-        const T idet = T(-1) / g.det;
+        const T idet = g.nidet;
         for (int it = threadIdx.x; it < 5 * NU; it += NT) {
             const int alpha = it / NU, z = it % NU, i = z % N, j = (z / N) % N, k = z / (N * N);
             const T *D = s_d + alpha * NF;

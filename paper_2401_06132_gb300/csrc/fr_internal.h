@@ -189,6 +189,7 @@ template <typename T>
 struct Geo {
     T Ji[9];
     T det;
+    T nidet;      // -1 / det, formed on the host (a division per thread and element costs FP64-pipe slots)
 };
 // The low-Mach form's geometry of one element: the FP64 inverse Jacobian and determinant, and the
 // float-float pairs its mass channel multiplies by, det J J^-1 (row-major) and -1 / det J, formed on

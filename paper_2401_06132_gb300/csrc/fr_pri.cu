@@ -651,7 +651,7 @@ __global__ void __launch_bounds__(NTH) k_pri_C(HexArgs<T> a, const PriOps<T> *go
         flag_status(a.status, ok);
         __syncthreads();
         T *R = a.R + elem_u0(a, e, NU);
-        const T idet = T(-1) / g.det;
+        const T idet = g.nidet;
         if (!dev) {
             for (int it = threadIdx.x; it < 5 * NU; it += NTH) {
                 const int alpha = it / NU, r = it % NU, k = r / NT_, t = r % NT_;
