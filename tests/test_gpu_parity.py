@@ -705,9 +705,9 @@ def test_tet_rk4_matches_oracle():
 
 @pytest.mark.parametrize("prec", ["fp32", "mixed_fp16"])
 def test_tet_fp32_matches_oracle(prec):
-    """The FP32 kernels, and the mixed FP16 form (the interpolation to the quadrature points as
-    split FP16 products on the tensor cores), against the oracle on the FP32-rounded input, with the
-    reference pressure removed (measured 2e-5 on this grid)."""
+    """The FP32 kernels (which the mixed forms run on tetrahedra unless fr_set_dense_tensor_cores is
+    on) against the oracle on the FP32-rounded input, with the reference pressure removed (measured
+    2e-5 on this grid)."""
     mesh = W.box_tet_mesh(4, shear=True)
     ne, nu = mesh["tet_v"].shape[0], 20
     p0 = W.tgv_p0()
