@@ -1855,8 +1855,6 @@ extern "C" fr_status fr_stage(fr_mesh *m, int which, double *host, long long n_h
     void *src = nullptr;
     long long n = 0;
     const Block &b = m->blocks[0];
-    long long nq = (long long)b.m * b.m * b.m;
-    (void)nq;
     switch (which) {
     case 0: src = m->d_UF; n = 5 * m->nfpt; break;
     case 1: src = m->d_CF; n = 5 * m->nfpt; break;
