@@ -34,6 +34,16 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, n), n
 
 
+def test_setters_reject_a_null_handle(lib):
+    """The switches of a handle (form, graphs, tensor-core paths, timing, debug) check the handle on
+    the host and return FR_EINVAL for a null one, with no device work."""
+    for name in ("fr_set_form", "fr_set_graph", "fr_set_hex_tensor_cores", "fr_set_dense_tensor_cores",
+                 "fr_set_timing"):
+        f = getattr(lib, name)
+        f.restype = C.c_int
+        assert f(C.c_void_p(None), C.c_int(1)) == fr.FR_EINVAL, name
+
+
 def _create(mesh, **kw):
     return fr.FRMesh(mesh, fr.make_params(**kw))
 
