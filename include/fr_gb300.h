@@ -167,7 +167,9 @@ fr_status fr_rhs(fr_mesh *m, const void *U_dev, void *R_dev, void *stream);
 fr_status fr_rhs_host(fr_mesh *m, const void *U_host, void *R_host, void *stream);
 
 /* nsteps classical RK4 steps of size dt, in place, on the FP64 master state U_dev (double, device,
- * boundary layout). Stage states are formed in the compute precision; stage accumulation stays FP64. */
+ * boundary layout). FR_FP64: stage states and the Runge-Kutta sum in FP64. Reduced precisions: the
+ * stage states fl32(U) + c dt k and the Runge-Kutta sum are formed in FP32 (they are FP32 RHS inputs
+ * and values either way), and the increment dt sum b_s k_s is added to U in FP64. */
 fr_status fr_rk4_step(fr_mesh *m, void *U_dev, double dt, int nsteps, void *stream);
 
 /* As fr_rk4_step on a host FP64 state: copies U host->device, advances nsteps, copies it back and
