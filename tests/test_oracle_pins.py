@@ -744,6 +744,21 @@ def test_rk4_damps_interface_jumps():
     assert np.all(np.diff(ek[1:]) < 0)
 
 
+def test_rk4_is_fourth_order_in_time():
+    """The oracle's time integrator (Sec. 3, classical RK4): on the 2^3 box, p = 3, a TGV state
+    advanced to T = 0.08 with 8, 16 and 32 steps against 256 steps; halving dt divides the error by
+    about 2^4 = 16 (measured 17.5 and 16.8). A wrong stage weight or stage time drops the order to
+    three or less (ratio <= 8)."""
+    mesh = W.box_hex_mesh(2)
+    o = O.Oracle(mesh, 3, 5, threads=os.cpu_count())
+    U0 = _tgv(o, mesh, perturb=1e-3)
+    T = 0.08
+    ref = o.rk4(U0, T / 256, 256)
+    err = [np.abs(o.rk4(U0, T / n, n) - ref).max() / np.abs(ref).max() for n in (8, 16, 32)]
+    r1, r2 = err[0] / err[1], err[1] / err[2]
+    assert 12.0 < r1 < 22.0 and 12.0 < r2 < 22.0, (err, r1, r2)
+
+
 def test_self_periodic_pairing_rule():
     """Reading R5 on the 1^3 self-periodic hex: every face pairs with the opposite face of the same
     element and the smaller local face (the -x, -y, -z faces) is L."""
