@@ -199,39 +199,49 @@ __global__ void __launch_bounds__(NT) k_disu_blk(HexArgs<T> a)
             s_u[i] = v;
         }
         __syncthreads();
-        // one thread per (element, flux point), all five variables: the face line is located once
+        // one thread per (element, flux point), all five variables: the face line is located once.
+        // FP32: the face values are evaluated with the float-float line operator (exact products,
+        // TwoSum accumulation) and rounded once; at low Mach the Rusanov dissipation
+        // (1/2)(|v.n| + c)(u_L - u_R), with c about 10 |v|, lifts any rounding of a face value into R.
         for (int it = threadIdx.x; it < nb * NF; it += NT) {
             const int el = it / NF, sp = it % NF, f = sp / (N * N);
             int base, stride;
             face_line<N>(f, sp % (N * N), base, stride);
-            const T *l = (f & 1) ? op.lR : op.lL;
             const long long fo = elem_f0(a, e0 + el, NF) + sp;
-#pragma unroll
-            for (int alpha = 0; alpha < FR_NV; alpha++) {
-                const T *u = s_u + (el * FR_NV + alpha) * NU + base;
-                T v = T(0);
-#pragma unroll
-                for (int i = 0; i < N; i++) v += l[i] * u[i * stride];
-                a.UF[alpha * a.nfpt + fo] = v;
-            }
             if constexpr (std::is_same<T, float>::value) {
+                const HexOpsFF &off = c_hexff[P - 2];
+                const ff *lf = (f & 1) ? off.lR : off.lL;
+                ff v[FR_NV];
+#pragma unroll
+                for (int alpha = 0; alpha < FR_NV; alpha++) {
+                    const T *u = s_u + (el * FR_NV + alpha) * NU + base;
+                    ff w = ff_of(0.0f);
+#pragma unroll
+                    for (int i = 0; i < N; i++) w = ff_fma_f(lf[i], u[i * stride], w);
+                    v[alpha] = w;
+                    a.UF[alpha * a.nfpt + fo] = w.hi + w.lo;
+                }
                 // low-Mach form: own-normal mass flux n.(rho v) at every flux point, in float-float
                 if (elem_phys(a, e0 + el).dev) {
-                    const HexOpsFF &off = c_hexff[P - 2];
-                    const ff *lf = (f & 1) ? off.lR : off.lL;
                     const ff *nt = a.fnrm64 + ((e0 + el) * 6 + f) * 4;
                     ff mf = ff_of(0.0f);
 #pragma unroll
                     for (int k = 0; k < 3; k++) {
                         const ff nk = nt[k];
                         if (nk.hi == 0.0f) continue;   // axis-aligned faces need one component
-                        const T *u = s_u + (el * FR_NV + 1 + k) * NU + base;
-                        ff v = ff_of(0.0f);
-#pragma unroll
-                        for (int i = 0; i < N; i++) v = ff_fma_f(lf[i], u[i * stride], v);
-                        mf = ff_fma(nk, v, mf);
+                        mf = ff_fma(nk, v[1 + k], mf);
                     }
                     a.MF[fo] = mf;
+                }
+            } else {
+                const T *l = (f & 1) ? op.lR : op.lL;
+#pragma unroll
+                for (int alpha = 0; alpha < FR_NV; alpha++) {
+                    const T *u = s_u + (el * FR_NV + alpha) * NU + base;
+                    T v = T(0);
+#pragma unroll
+                    for (int i = 0; i < N; i++) v += l[i] * u[i * stride];
+                    a.UF[alpha * a.nfpt + fo] = v;
                 }
             }
         }

@@ -67,25 +67,7 @@ __device__ __forceinline__ T face_value(const PriOps<T> &op, const T *fld, int s
     return v;
 }
 
-// Same, of the field minus a constant (the low-Mach deviation), subtracted at the solution points.
-template <typename T>
-__device__ __forceinline__ T face_value_off(const PriOps<T> &op, const T *fld, int s, T off)
-{
-    T v = T(0);
-    if (s < 20) {
-        const int t = s % 10;
-        const T *l = s < 10 ? op.lzL : op.lzR;
-#pragma unroll
-        for (int k = 0; k < NZ; k++) v += l[k] * (fld[t + 10 * k] - off);
-    } else {
-        const int f = (s - 20) / 16, loc = (s - 20) % 16, a = loc % 4, b = loc / 4;
-#pragma unroll
-        for (int t = 0; t < NT_; t++) v += op.Ef[f][a][t] * (fld[t + 10 * b] - off);
-    }
-    return v;
-}
-
-// Value at flux point s, in float-float, of an FP32 field at solution points.
+// An entry of the float-float table: its hi part and the lo part at the same offset.
 __device__ __forceinline__ ff ffop(const PriOpsFF &o, const float &hi)
 {
     // the lo part sits at the same offset in the second table
@@ -93,18 +75,20 @@ __device__ __forceinline__ ff ffop(const PriOpsFF &o, const float &hi)
     return ff{hi, *(reinterpret_cast<const float *>(&o.lo) + (h - reinterpret_cast<const float *>(&o.hi)))};
 }
 
-__device__ __forceinline__ ff face_value_ff(const PriOpsFF &o, const float *fld, int s)
+// Same, of the field minus a constant, with the float-float table (exact products of its hi part,
+// TwoSum accumulation): the face value to about 48 bits before its final rounding to FP32.
+__device__ __forceinline__ ff face_value_ff_off(const PriOpsFF &o, const float *fld, int s, float off)
 {
     ff v = ff_of(0.0f);
     if (s < 20) {
         const int t = s % 10;
         const float *l = s < 10 ? o.hi.lzL : o.hi.lzR;
 #pragma unroll
-        for (int k = 0; k < NZ; k++) v = ff_fma_f(ffop(o, l[k]), fld[t + 10 * k], v);
+        for (int k = 0; k < NZ; k++) v = ff_fma_f(ffop(o, l[k]), fld[t + 10 * k] - off, v);
     } else {
         const int f = (s - 20) / 16, loc = (s - 20) % 16, a = loc % 4, b = loc / 4;
 #pragma unroll
-        for (int t = 0; t < NT_; t++) v = ff_fma_f(ffop(o, o.hi.Ef[f][a][t]), fld[t + 10 * b], v);
+        for (int t = 0; t < NT_; t++) v = ff_fma_f(ffop(o, o.hi.Ef[f][a][t]), fld[t + 10 * b] - off, v);
     }
     return v;
 }
@@ -142,38 +126,55 @@ static_assert(16 * TC_SBO_P <= TC_HEAD + (5 * NU + 15 * NU + 5 * NF + 20 * NQ) *
 // -------------------------------------------------------------------------------------------------
 // Phase A: disu
 // -------------------------------------------------------------------------------------------------
-// Low-Mach form (ph.dev, FP32): the face solution of the deviations from the reference state, and
-// the own-normal mass flux n.(rho v) at every flux point in FP64 (from the FP64 operator table).
+// The reduced precisions evaluate the face values with the float-float operator table (compensated:
+// exact products, TwoSum accumulation) and round once: the quad-face rows of the triangle
+// interpolation extrapolate from interior points (row sums of |Ef| well above 1), and at low Mach
+// the Rusanov dissipation (1/2)(|v.n| + c)(u_L - u_R), with c about 10 |v|, lifts any rounding of a
+// face value into R. Low-Mach form (ph.dev): the face solution of the deviations from the reference
+// state, and the own-normal mass flux n.(rho v) at every flux point in float-float.
 template <typename T>
 __global__ void __launch_bounds__(256) k_pri_disu(HexArgs<T> a, const PriOps<T> *gops, const PriOpsFF *opsff)
 {
-    __shared__ PriOps<T> op;
-    load_ops<T, 256>(gops, op);
+    constexpr bool F32 = sizeof(T) == 4;
+    __shared__ __align__(16) unsigned char raw[F32 ? sizeof(PriOpsFF) : sizeof(PriOps<T>)];
+    if constexpr (F32) {
+        const float *src = reinterpret_cast<const float *>(opsff);
+        float *dst = reinterpret_cast<float *>(raw);
+        for (int i = threadIdx.x; i < (int)(sizeof(PriOpsFF) / sizeof(float)); i += 256) dst[i] = src[i];
+    } else {
+        load_ops<T, 256>(gops, *reinterpret_cast<PriOps<T> *>(raw));
+    }
     __syncthreads();
-    const long long total = a.ne * FR_NV * NF;
+    const long long total = a.ne * NF;
     for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
+        // one thread per (element, flux point), all five variables
         const int s = (int)(it % NF);
-        const long long ea = it / NF;
-        const int alpha = (int)(ea % FR_NV);
-        const long long e = ea / FR_NV;
+        const long long e = it / NF;
         const T *u = a.U + elem_u0(a, e, NU);
-        T off = T(0);
-        bool dev = false;
-        if constexpr (sizeof(T) == 4) {
+        const long long fo = elem_f0(a, e, NF) + s;
+        if constexpr (F32) {
+            const PriOpsFF &o = *reinterpret_cast<const PriOpsFF *>(raw);
             const Phys<T> ph = elem_phys(a, e);
-            dev = ph.dev != 0;
-            if (dev) off = alpha == 0 ? ph.rref : (alpha == 4 ? ph.eref : T(0));
-        }
-        a.UF[alpha * a.nfpt + elem_f0(a, e, NF) + s] = face_value_off(op, u + alpha * NU, s, off);
-        if constexpr (sizeof(T) == 4) {
-            if (dev && alpha == 0) {
+            const bool dev = ph.dev != 0;
+            ff v[FR_NV];
+#pragma unroll
+            for (int alpha = 0; alpha < FR_NV; alpha++) {
+                const float off = dev ? (alpha == 0 ? ph.rref : (alpha == 4 ? ph.eref : 0.0f)) : 0.0f;
+                v[alpha] = face_value_ff_off(o, u + alpha * NU, s, off);
+                a.UF[alpha * a.nfpt + fo] = v[alpha].hi + v[alpha].lo;
+            }
+            if (dev) {
                 const ff *nt = a.fnrm64 + (e * 6 + face_of(s)) * 4;
                 ff mf = ff_of(0.0f);
 #pragma unroll
                 for (int k = 0; k < 3; k++)
-                    if (nt[k].hi != 0.0f) mf = ff_fma(nt[k], face_value_ff(*opsff, u + (1 + k) * NU, s), mf);
-                a.MF[elem_f0(a, e, NF) + s] = mf;
+                    if (nt[k].hi != 0.0f) mf = ff_fma(nt[k], v[1 + k], mf);
+                a.MF[fo] = mf;
             }
+        } else {
+            const PriOps<T> &op = *reinterpret_cast<const PriOps<T> *>(raw);
+#pragma unroll
+            for (int alpha = 0; alpha < FR_NV; alpha++) a.UF[alpha * a.nfpt + fo] = face_value(op, u + alpha * NU, s);
         }
     }
 }
@@ -719,7 +720,7 @@ int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, const 
 {
     if (a.ne == 0) return 0;
     if (phase == 0) {
-        long long work = a.ne * FR_NV * NF;
+        long long work = a.ne * NF;
         long long g = (work + 255) / 256;
         if (g > 152LL * 64) g = 152LL * 64;
         k_pri_disu<T><<<(int)g, 256, 0, s>>>(a, ops, ops64);
