@@ -214,10 +214,14 @@ fr_status fr_diagnostics(fr_mesh *m, const void *U_dev, const void *R_dev, doubl
  * CUDA graph in global mode, where cudaMalloc is not allowed). The paper has no counterpart: this is
  * a service of the library. It allocates nothing: its accumulators are a fixed array of
  * 1024 x 8 doubles (64 KiB) compiled into the library, which every GPU that loads the library holds
- * until the process exits; handles with more than 1024 instances get FR_EINVAL. The first call on a
- * device looks up that array's device address, so make that first call before any stream capture.
- * All calls share the one array and each call clears only the slots it uses: calls that overlap on
- * the GPU (other streams, other threads) race and give wrong sums. Synchronises the stream. */
+ * until the process exits; handles with more than 1024 instances get FR_EINVAL. fr_mesh_create looks
+ * up that array's device address (with the handle's device current), so this call does no set-up of
+ * its own; the handle's device must be the current device (else FR_EINVAL). All calls share the one
+ * array and each call clears only the slots it uses: calls that overlap on the GPU (other streams,
+ * other threads) race and give wrong sums. While another thread captures a stream in global mode,
+ * pass a non-blocking stream: work on the legacy default stream (NULL) would join that capture's
+ * stream and invalidate it. An instance without elements reports 0 for E_k and eps. Synchronises
+ * the stream. */
 fr_status fr_diagnostics_noalloc(fr_mesh *m, const void *U_dev, const void *R_dev, double *out, void *stream);
 
 /* Copies an intermediate array of the last UNFUSED RHS to a host FP64 array, for stage-level
@@ -263,6 +267,55 @@ fr_status fr_set_dense_tensor_cores(fr_mesh *m, int on);
  * Arrays have n_ids entries. */
 fr_status fr_set_timing(fr_mesh *m, int on);
 fr_status fr_kernel_times(fr_mesh *m, double *ms, long long *count, int n_ids);
+
+/* ---------------------------------------------------------------------------------------------
+ * Partitioned single mesh (one part per GPU). The RHS needs neighbour data at two points only, the
+ * boundaries of the paper's kernel groups (Sec. 2.2, kernel-grouping figure): the face solution
+ * U^(f) before con_u, and the face data of comm_flux before it. A single-instance mesh is split
+ * into nparts contiguous ranges of its global element order (part r owns elements
+ * [floor(ne r / nparts), floor(ne (r+1) / nparts))); each part holds its own elements and flux
+ * points plus one halo slot per remote partner point. An RHS on part r is
+ *     fr_rhs_phase(0); fr_halo_pack(0) -> exchange -> fr_halo_unpack(0);
+ *     fr_rhs_phase(1); fr_halo_pack(1) -> exchange -> fr_halo_unpack(1);
+ *     fr_rhs_phase(2)
+ * where "exchange" sends the segment of peer q of the send buffer to q and receives q's segment
+ * into the same place of the receive buffer (any transport: NCCL, MPI, or device copies). Each side
+ * of a pair evaluates its own point's common flux with the pair's global L/R roles, so the parts'
+ * R concatenated equal the single-handle RHS bit for bit. Surface-flux anti-aliasing, the unfused
+ * form, fr_rhs and the RK4 entry points are FR_EUNSUPPORTED on a part of a mesh with nparts > 1.
+ * ------------------------------------------------------------------------------------------- */
+
+/* Exchange plan of part `part` of nparts, computed on the host only (no device is touched).
+ * info[0..5]: first and one-past-last own global element, own flux points, halo points, elements
+ * and flux points of the whole mesh. counts[q] (nparts entries, may be NULL): points exchanged with
+ * peer q (the same number in both directions). send_g / recv_g (cap entries each, may be NULL):
+ * whole-mesh flux-point indices (element-major, local face order) of the points this part sends and
+ * of the remote points it receives, in buffer order. */
+fr_status fr_partition_plan(const fr_mesh_desc *desc, const fr_params *prm, int nparts, int part,
+                            long long *info, long long *counts, long long *send_g, long long *recv_g,
+                            long long cap);
+
+/* Builds part `part` of nparts of a single-instance mesh on the current device (see above); U and R
+ * of the handle hold the own elements only, in the boundary layout. */
+fr_status fr_mesh_create_part(const fr_mesh_desc *desc, const fr_params *prm, int nparts, int part, fr_mesh **out);
+
+/* info[0..6]: nparts, part, first and one-past-last own global element, halo points, values per
+ * point of exchange 0 (5: the face solution) and of exchange 1 (4: the own-normal viscous flux, or
+ * 6 in the low-Mach FP32 form: plus the float-float mass flux as two floats). counts[q] (nparts
+ * entries, may be NULL): points exchanged with peer q. */
+fr_status fr_halo_info(const fr_mesh *m, long long *info, long long *counts);
+
+/* Packs (after fr_rhs_phase(what)) this part's face data that its peers need into the device buffer
+ * send_dev, or unpacks the peers' data from recv_dev into the halo slots (before fr_rhs_phase(what +
+ * 1)). Buffers hold, peer by peer in increasing rank order, nvar x counts[q] values of the compute
+ * precision (double for FR_FP64, float otherwise), var-major. Asynchronous on `stream`. */
+fr_status fr_halo_pack(fr_mesh *m, int what, void *send_dev, void *stream);
+fr_status fr_halo_unpack(fr_mesh *m, int what, const void *recv_dev, void *stream);
+
+/* One phase of the fused RHS: 0 face solution (disu), 1 volume group (con_u .. tdivtpcorf, writes
+ * R~ into R), 2 interface group (comm_flux, tdivtconf, negdivconf: finishes R). Same arguments as
+ * fr_rhs; phases 0, 1, 2 in order on one stream are one fr_rhs. */
+fr_status fr_rhs_phase(fr_mesh *m, int phase, const void *U_dev, void *R_dev, void *stream);
 
 /* Text of the last error on the calling thread ("" if none). */
 const char *fr_last_error(void);

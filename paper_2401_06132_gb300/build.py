@@ -20,18 +20,30 @@ def nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
+def _headers() -> list:
+    """Every header a translation unit can include: the library's own and the public ABI header."""
+    inc = os.path.join(HERE, "..", "include")
+    return sorted(os.path.join(d, f) for d in (CSRC, inc) for f in os.listdir(d) if f.endswith((".h", ".cuh")))
+
+
 def _compile(src: str, extra) -> str:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
     path = os.path.join(CSRC, src)
-    deps = [path, os.path.join(CSRC, "fr_internal.h"), os.path.join(CSRC, "fr_physics.cuh"), os.path.join(HERE, "..", "include", "fr_gb300.h")]
-    if os.path.exists(obj) and all(os.path.getmtime(obj) >= os.path.getmtime(d) for d in deps):
-        return obj
     cmd = [nvcc()] + NVCC_FLAGS + list(extra) + ["-c", path, "-o", obj]
     if src.endswith(".cpp"):
         cmd = [nvcc(), "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-x", "c++", "-c", path, "-o", obj]
+    # an object is reused only if it is newer than its source and every header, and was compiled
+    # with the same command line
+    stamp = obj + ".cmd"
+    deps = [path] + _headers()
+    if (os.path.exists(obj) and os.path.exists(stamp) and open(stamp).read() == " ".join(cmd)
+            and all(os.path.getmtime(obj) >= os.path.getmtime(d) for d in deps)):
+        return obj
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"compile failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+    with open(stamp, "w") as f:
+        f.write(" ".join(cmd))
     return obj
 
 

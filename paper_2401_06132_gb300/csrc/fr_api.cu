@@ -68,6 +68,14 @@ struct Group {
 
 struct fr_mesh {
     int dev = 0;
+    int nsm = 1;                         // streaming multiprocessors of the device
+    // partitioned single mesh (fr_mesh_create_part): this handle owns the global elements [E0, E1)
+    // of a mesh split into nparts contiguous ranges; flux points nfpt_own .. nfpt - 1 are halo slots
+    // holding the face data of remote partners, peer by peer (halo_off[q] .. halo_off[q + 1] - 1)
+    int nparts = 1, part = 0;
+    long long E0 = 0, E1 = 0, nfpt_own = 0;
+    std::vector<long long> halo_off;     // [nparts + 1] prefix sums of the points exchanged per peer
+    uint32_t *d_send = nullptr;          // own flux points sent to the peers, in buffer order
     int prec = FR_FP64;
     int form = FR_FUSED;
     std::vector<InstanceHost> inst;
@@ -1021,6 +1029,11 @@ static fr_status build_groups(fr_mesh *m, const std::vector<uint32_t> &partner)
     return FR_OK;
 }
 
+static cudaError_t diag_scratch_lookup(int dev);
+
+// Uploads everything a handle built on the host needs on the current device (m is deleted on failure).
+static fr_status finish_create(fr_mesh *m, std::vector<uint32_t> &partner, fr_mesh **out);
+
 extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst, const fr_params *prm, fr_mesh **out)
 {
     if (!out) return fail(FR_EINVAL, "out is null");
@@ -1029,8 +1042,21 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
     std::vector<uint32_t> partner;
     fr_status st = build_host(m, inst, n_inst, prm, partner);
     if (st) { delete m; return st; }
+    m->nfpt_own = m->nfpt;
+    m->E1 = m->ne;
+    return finish_create(m, partner, out);
+}
+
+static fr_status finish_create(fr_mesh *m, std::vector<uint32_t> &partner, fr_mesh **out)
+{
+    fr_status st = FR_OK;
     cudaError_t ce = cudaGetDevice(&m->dev);
     if (ce != cudaSuccess) { delete m; return fail(FR_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(ce)); }
+    ce = cudaDeviceGetAttribute(&m->nsm, cudaDevAttrMultiProcessorCount, m->dev);
+    if (ce != cudaSuccess || m->nsm < 1) { delete m; return fail(FR_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(ce)); }
+    // the device address of the fixed diagnostics array (fr_diagnostics_noalloc), looked up afresh for
+    // every handle so that it stays valid across a cudaDeviceReset
+    if (diag_scratch_lookup(m->dev) != cudaSuccess) { delete m; return fail(FR_ECUDA, "cudaGetSymbolAddress failed"); }
     for (size_t b = 0; b < m->blocks.size(); b++)
         if (m->blocks[b].type == 0 && hex_upload_ops(m->blocks[b].p, m->blocks[b].p + 2, m->hex1d[b])) { delete m; return fail(FR_ECUDA, "operator upload failed"); }
     size_t ts = tsize(m->prec);
@@ -1043,7 +1069,7 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
         for (const InstanceHost &I : m->inst) all = all && I.prm.p_ref > 0 && I.prm.rho_ref > 0;
         m->lowmach = all;
     }
-    if (!st && m->lowmach && m->has_pri) {
+    if (!st && m->prec != FR_FP64 && m->has_pri) {
         // float-float prism operators for the mass channel: hi = float(op), lo = float(op - hi)
         PriOps<double> o64;
         fill_priops<double>(m->pri, o64);
@@ -1071,7 +1097,8 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
     }
     if (!st) st = (m->prec == FR_FP64) ? build_groups<double>(m, partner) : build_groups<float>(m, partner);
     // FP64 hexahedral handles evaluate each interface pair once (split interface phase)
-    m->split_c = ((m->prec == FR_FP64) && !m->has_pri && !m->has_tet && !m->has_pyr) || m->surf;
+    // (a partitioned handle evaluates each side's own points: the pair's other side may be remote)
+    m->split_c = (((m->prec == FR_FP64) && !m->has_pri && !m->has_tet && !m->has_pyr) || m->surf) && m->nparts == 1;
     if (!st && m->surf) {
         std::vector<uint32_t> ql;
         for (long long q = 0; q < m->nqf; q++)
@@ -1096,6 +1123,10 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *const *inst, int n_inst,
         st = fail(FR_ECUDA, "partner upload failed");
     if (!st) st = dalloc(m, &m->d_UF, (size_t)5 * m->nfpt * ts);
     if (!st) st = dalloc(m, &m->d_FV, (size_t)4 * m->nfpt * ts);
+    // defined contents for the halo slots of a partitioned handle before its first exchange
+    if (!st && m->nparts > 1 && (cudaMemset(m->d_UF, 0, (size_t)5 * m->nfpt * ts) != cudaSuccess ||
+                                 cudaMemset(m->d_FV, 0, (size_t)4 * m->nfpt * ts) != cudaSuccess))
+        st = fail(FR_ECUDA, "memset");
     if (!st) st = dalloc(m, (void **)&m->d_status, sizeof(int));
     if (!st && cudaMemset(m->d_status, 0, sizeof(int)) != cudaSuccess) st = fail(FR_ECUDA, "memset");
     if (!st && cudaMallocHost((void **)&m->h_status, sizeof(int)) != cudaSuccess) st = fail(FR_ENOMEM, "pinned status");
@@ -1112,7 +1143,8 @@ extern "C" fr_status fr_destroy(fr_mesh *m)
     void **bufs[] = {&m->d_fnrm, (void **)&m->d_fnrm64, &m->d_geo64, (void **)&m->d_MF, (void **)&m->d_RL, &m->d_priops, &m->d_priops64, &m->d_tetops, &m->d_pyrops, &m->d_tetops64, &m->d_pyrops64, &m->d_geo, (void **)&m->d_partner, &m->d_UF, &m->d_FV, &m->d_CF, &m->d_QF, &m->d_DF, &m->d_Qu,
                      &m->d_UQ, &m->d_QQ, &m->d_Rt, &m->d_rk_k, &m->d_rk_us, (void **)&m->d_rk_acc, &m->d_io_U,
                      &m->d_io_R, (void **)&m->d_wsum, (void **)&m->d_status, &m->d_Qsnap, (void **)&m->d_qpartner,
-                     &m->d_UFQ, &m->d_FVQ, (void **)&m->d_qlpts, &m->d_DQ, &m->d_mu, &m->d_mq, &m->d_mfn};
+                     &m->d_UFQ, &m->d_FVQ, (void **)&m->d_qlpts, &m->d_DQ, &m->d_mu, &m->d_mq, &m->d_mfn,
+                     (void **)&m->d_send};
     for (void **b : bufs) dfree(*b);
     for (Group &g : m->groups) {
         dfree(g.d_geo); dfree((void *&)g.d_eu0); dfree((void *&)g.d_ef0); dfree((void *&)g.d_eph); dfree(g.d_phtab);
@@ -1186,6 +1218,262 @@ extern "C" fr_status fr_set_form(fr_mesh *m, int form)
     if (!m || (form != FR_FUSED && form != FR_UNFUSED)) return fail(FR_EINVAL, "bad handle or form");
     m->form = form;
     return FR_OK;
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// Partitioned single mesh
+//
+// The fused RHS needs neighbour data at exactly two points, the boundaries of the paper's kernel
+// groups (Sec. 2.2 and the kernel-grouping figure): the face solution U^(f) before con_u, and the
+// face data of comm_flux (here the own-normal viscous flux, and in the low-Mach form the mass flux)
+// before it. A mesh is split into nparts contiguous ranges of its global element order (hexahedra,
+// then prisms, tetrahedra, pyramids; x fastest in the box meshes, so the ranges are z slabs). Each
+// part owns its elements and flux points and holds, after them, one halo slot per remote partner
+// point, peer by peer; the two exchanges fill the halo slots between the phases. Each side of a pair
+// evaluates the common flux of its own point with the pair's global L/R roles, so a partitioned
+// RHS equals the single-handle RHS bit for bit.
+// ---------------------------------------------------------------------------------------------
+struct PartPlan {
+    long long E0 = 0, E1 = 0;              // own global elements [E0, E1)
+    long long nfpt_own = 0;
+    std::vector<long long> off;            // [nparts + 1]: first halo slot (and send entry) per peer
+    std::vector<long long> send_g, recv_g; // full-mesh flux points sent / received, in buffer order
+    std::vector<uint32_t> send_own;        // own flux index of every sent point
+    std::vector<uint32_t> partner;         // partner codes of the own points (halo slots for remote ones)
+};
+
+static long long part_begin(long long ne, int nparts, int r) { return (long long)((__int128)ne * r / nparts); }
+
+static fr_status part_plan(const fr_mesh *full, const std::vector<uint32_t> &pfull, int nparts, int part, PartPlan &pl)
+{
+    const long long ne = full->ne;
+    pl.E0 = part_begin(ne, nparts, part);
+    pl.E1 = part_begin(ne, nparts, part + 1);
+    if (pl.E1 <= pl.E0) return fail(FR_EINVAL, "part %d of %d owns no element (%lld elements)", part, nparts, ne);
+    auto rank_of = [&](long long ge) {
+        int r = (int)((__int128)ge * nparts / ne);
+        while (r + 1 < nparts && part_begin(ne, nparts, r + 1) <= ge) r++;
+        while (r > 0 && part_begin(ne, nparts, r) > ge) r--;
+        return r;
+    };
+    auto elem_of = [&](long long g) {
+        for (const Block &B : full->blocks)
+            if (g < B.f0 + B.ne * B.nf) return B.elem0 + (g - B.f0) / B.nf;
+        return -1LL;
+    };
+    // own flux points in the restricted numbering: the own part of each block, in block order
+    std::vector<long long> own_g;
+    for (const Block &B : full->blocks) {
+        const long long lo = std::max(B.elem0, pl.E0), hi = std::min(B.elem0 + B.ne, pl.E1);
+        for (long long g = B.f0 + (lo - B.elem0) * B.nf; hi > lo && g < B.f0 + (hi - B.elem0) * B.nf; g++) own_g.push_back(g);
+    }
+    pl.nfpt_own = (long long)own_g.size();
+    std::unordered_map<long long, uint32_t> own_idx;
+    own_idx.reserve(own_g.size() * 2);
+    for (size_t i = 0; i < own_g.size(); i++) own_idx[own_g[i]] = (uint32_t)i;
+    struct Remote { int rank; long long pg; uint32_t own; };
+    std::vector<Remote> rem;
+    pl.partner.assign(own_g.size(), 0u);
+    for (size_t i = 0; i < own_g.size(); i++) {
+        const uint32_t pc = pfull[(size_t)own_g[i]];
+        const long long pg = pc & ~FR_LFLAG;
+        auto it = own_idx.find(pg);
+        if (it != own_idx.end()) pl.partner[i] = it->second | (pc & FR_LFLAG);
+        else rem.push_back(Remote{rank_of(elem_of(pg)), pg, (uint32_t)i});
+    }
+    if (pl.nfpt_own + (long long)rem.size() >= (long long)FR_LFLAG) return fail(FR_EUNSUPPORTED, "more than 2^31 flux points");
+    pl.off.assign((size_t)nparts + 1, 0);
+    for (const Remote &r : rem) pl.off[(size_t)r.rank + 1]++;
+    for (int q = 0; q < nparts; q++) pl.off[(size_t)q + 1] += pl.off[(size_t)q];
+    // halo slots of peer q sorted by the remote point's full index; the matching send list of this
+    // part for q is its own points whose partner lies on q, sorted by their own full index: both
+    // sides order the same pairs the same way
+    std::vector<Remote> by_pg = rem, by_g = rem;
+    std::sort(by_pg.begin(), by_pg.end(), [](const Remote &a, const Remote &b) { return a.rank != b.rank ? a.rank < b.rank : a.pg < b.pg; });
+    std::sort(by_g.begin(), by_g.end(), [&](const Remote &a, const Remote &b) { return a.rank != b.rank ? a.rank < b.rank : own_g[a.own] < own_g[b.own]; });
+    pl.recv_g.resize(rem.size()); pl.send_g.resize(rem.size()); pl.send_own.resize(rem.size());
+    for (size_t k = 0; k < rem.size(); k++) {
+        const Remote &r = by_pg[k];
+        pl.recv_g[k] = r.pg;
+        pl.partner[r.own] = (uint32_t)(pl.nfpt_own + (long long)k) | (pfull[(size_t)own_g[r.own]] & FR_LFLAG);
+        pl.send_g[k] = own_g[by_g[k].own];
+        pl.send_own[k] = by_g[k].own;
+    }
+    return FR_OK;
+}
+
+// Host-only: the exchange plan of one part, with nothing built on the device.
+extern "C" fr_status fr_partition_plan(const fr_mesh_desc *desc, const fr_params *prm, int nparts, int part,
+                                       long long *info, long long *counts, long long *send_g, long long *recv_g,
+                                       long long cap)
+{
+    if (!desc || !prm || !info || nparts < 1 || part < 0 || part >= nparts) return fail(FR_EINVAL, "bad argument");
+    fr_mesh full;
+    std::vector<uint32_t> pfull;
+    fr_status st = build_host(&full, &desc, 1, prm, pfull);
+    if (st) return st;
+    if (full.surf) return fail(FR_EUNSUPPORTED, "partitioned meshes run without surface-flux anti-aliasing");
+    PartPlan pl;
+    st = part_plan(&full, pfull, nparts, part, pl);
+    if (st) return st;
+    const long long n = (long long)pl.recv_g.size();
+    info[0] = pl.E0; info[1] = pl.E1; info[2] = pl.nfpt_own; info[3] = n; info[4] = full.ne; info[5] = full.nfpt;
+    if (counts)
+        for (int q = 0; q < nparts; q++) counts[q] = pl.off[(size_t)q + 1] - pl.off[(size_t)q];
+    if ((send_g || recv_g) && cap < n) return fail(FR_EINVAL, "plan buffers hold %lld entries, %lld needed", cap, n);
+    for (long long k = 0; k < n; k++) {
+        if (send_g) send_g[k] = pl.send_g[(size_t)k];
+        if (recv_g) recv_g[k] = pl.recv_g[(size_t)k];
+    }
+    return FR_OK;
+}
+
+extern "C" fr_status fr_mesh_create_part(const fr_mesh_desc *desc, const fr_params *prm, int nparts, int part, fr_mesh **out)
+{
+    if (!out) return fail(FR_EINVAL, "out is null");
+    *out = nullptr;
+    if (!desc || !prm || nparts < 1 || part < 0 || part >= nparts) return fail(FR_EINVAL, "bad argument");
+    fr_mesh full;
+    std::vector<uint32_t> pfull;
+    fr_status st = build_host(&full, &desc, 1, prm, pfull);
+    if (st) return st;
+    if (full.surf) return fail(FR_EUNSUPPORTED, "partitioned meshes run without surface-flux anti-aliasing");
+    PartPlan pl;
+    st = part_plan(&full, pfull, nparts, part, pl);
+    if (st) return st;
+    fr_mesh *m = new fr_mesh();
+    m->nparts = nparts; m->part = part; m->E0 = pl.E0; m->E1 = pl.E1; m->nfpt_own = pl.nfpt_own;
+    m->halo_off = pl.off;
+    m->prec = full.prec; m->curved = full.curved;
+    m->pri = full.pri; m->has_pri = full.has_pri;
+    m->tet = full.tet; m->has_tet = full.has_tet;
+    m->pyr = full.pyr; m->has_pyr = full.has_pyr;
+    // the own elements of the single instance, block by block, with their geometry
+    const InstanceHost &F = full.inst[0];
+    InstanceHost I;
+    I.prm = F.prm;
+    I.n_hex = I.n_pri = I.n_tet = I.n_pyr = 0;
+    long long elem = 0, u = 0, f = 0;
+    for (size_t b = 0; b < full.blocks.size(); b++) {
+        const Block &B = full.blocks[b];
+        const long long lo = std::max(B.elem0, pl.E0), hi = std::min(B.elem0 + B.ne, pl.E1);
+        if (hi <= lo) continue;
+        Block nb = B;
+        nb.ne = hi - lo; nb.elem0 = elem; nb.u0 = u; nb.f0 = f;
+        (B.type == 0 ? I.n_hex : B.type == 1 ? I.n_pri : B.type == 2 ? I.n_tet : I.n_pyr) += (int)nb.ne;
+        for (long long ge = lo; ge < hi; ge++) {   // single instance: instance-local index = global index
+            I.x0J.insert(I.x0J.end(), F.x0J.begin() + ge * 12, F.x0J.begin() + ge * 12 + 12);
+            I.curved.push_back(F.curved[(size_t)ge]);
+            I.vx.insert(I.vx.end(), F.vx.begin() + ge * 24, F.vx.begin() + ge * 24 + 24);
+            m->geo_host.insert(m->geo_host.end(), full.geo_host.begin() + ge * 10, full.geo_host.begin() + ge * 10 + 10);
+        }
+        m->blocks.push_back(nb);
+        m->hex1d.push_back(full.hex1d[b]);
+        elem += nb.ne; u += nb.ne * FR_NV * nb.nu; f += nb.ne * nb.nf;
+    }
+    m->inst.push_back(I);
+    m->ne = elem; m->nU = u;
+    m->nfpt = f + (pl.off.back());
+    m->inst_u0 = {0, u};
+    if (f != pl.nfpt_own) { delete m; return fail(FR_EMESH, "partition bookkeeping mismatch"); }
+    st = finish_create(m, pl.partner, out);
+    if (st) return st;
+    m = *out;
+    if (!pl.send_own.empty()) {
+        st = dalloc(m, (void **)&m->d_send, pl.send_own.size() * sizeof(uint32_t));
+        if (!st && cudaMemcpy(m->d_send, pl.send_own.data(), pl.send_own.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+            st = fail(FR_ECUDA, "send list upload failed");
+        if (st) { fr_destroy(m); *out = nullptr; return st; }
+    }
+    return FR_OK;
+}
+
+extern "C" fr_status fr_halo_info(const fr_mesh *m, long long *info, long long *counts)
+{
+    if (!m || !info) return fail(FR_EINVAL, "null argument");
+    info[0] = m->nparts; info[1] = m->part; info[2] = m->E0; info[3] = m->E1;
+    info[4] = m->nfpt - m->nfpt_own;
+    info[5] = FR_NV;                                                    // values per point, exchange 0
+    info[6] = 4 + ((m->prec != FR_FP64 && m->lowmach) ? 2 : 0);         // values per point, exchange 1
+    if (counts)
+        for (int q = 0; q < m->nparts; q++)
+            counts[q] = m->halo_off.empty() ? 0 : m->halo_off[(size_t)q + 1] - m->halo_off[(size_t)q];
+    return FR_OK;
+}
+
+// Halo buffers: peer by peer (increasing rank), a segment of nvar x count values, var-major.
+// what = 0: the face solution (5 values); what = 1: the own-normal viscous flux (4 values) and, in
+// the low-Mach form, the float-float mass flux (2 floats).
+template <typename T>
+__global__ void k_halo_pack(const T *UF, const T *FV, const ff *MF, long long nfpt, int what, int nvar,
+                            const uint32_t *idx, long long n, T *buf)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nvar * n; i += (long long)gridDim.x * blockDim.x) {
+        const int v = (int)(i / n);
+        const long long g = idx[i % n];
+        T val;
+        if (what == 0) val = UF[v * nfpt + g];
+        else if (v < 4) val = FV[v * nfpt + g];
+        else val = (T)(v == 4 ? MF[g].hi : MF[g].lo);
+        buf[i] = val;
+    }
+}
+
+template <typename T>
+__global__ void k_halo_unpack(T *UF, T *FV, ff *MF, long long nfpt, int what, int nvar, long long slot0, long long n,
+                              const T *buf)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nvar * n; i += (long long)gridDim.x * blockDim.x) {
+        const int v = (int)(i / n);
+        const long long g = slot0 + i % n;
+        const T val = buf[i];
+        if (what == 0) UF[v * nfpt + g] = val;
+        else if (v < 4) FV[v * nfpt + g] = val;
+        else if (v == 4) MF[g].hi = (float)val;
+        else MF[g].lo = (float)val;
+    }
+}
+
+template <typename T>
+static fr_status halo_impl(fr_mesh *m, int what, void *buf, bool pack, cudaStream_t s)
+{
+    long long info[7];
+    fr_halo_info(m, info, nullptr);
+    const int nvar = (int)info[5 + what];
+    for (int q = 0; q < m->nparts; q++) {
+        const long long o = m->halo_off[(size_t)q], n = m->halo_off[(size_t)q + 1] - o;
+        if (n == 0) continue;
+        T *seg = reinterpret_cast<T *>(buf) + nvar * o;
+        const int grid = (int)std::min<long long>((nvar * n + 255) / 256, 8LL * m->nsm);
+        if (pack)
+            k_halo_pack<T><<<grid, 256, 0, s>>>(reinterpret_cast<const T *>(m->d_UF), reinterpret_cast<const T *>(m->d_FV),
+                                                reinterpret_cast<const ff *>(m->d_MF), m->nfpt, what, nvar, m->d_send + o, n, seg);
+        else
+            k_halo_unpack<T><<<grid, 256, 0, s>>>(reinterpret_cast<T *>(m->d_UF), reinterpret_cast<T *>(m->d_FV),
+                                                  reinterpret_cast<ff *>(m->d_MF), m->nfpt, what, nvar, m->nfpt_own + o, n, seg);
+        CU(cudaPeekAtLastError());
+    }
+    return FR_OK;
+}
+
+extern "C" fr_status fr_halo_pack(fr_mesh *m, int what, void *send_dev, void *stream)
+{
+    if (!m || (what != 0 && what != 1)) return fail(FR_EINVAL, "bad argument");
+    if (m->nfpt == m->nfpt_own) return FR_OK;
+    if (!send_dev) return fail(FR_EINVAL, "null buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    return m->prec == FR_FP64 ? halo_impl<double>(m, what, send_dev, true, s) : halo_impl<float>(m, what, send_dev, true, s);
+}
+
+extern "C" fr_status fr_halo_unpack(fr_mesh *m, int what, const void *recv_dev, void *stream)
+{
+    if (!m || (what != 0 && what != 1)) return fail(FR_EINVAL, "bad argument");
+    if (m->nfpt == m->nfpt_own) return FR_OK;
+    if (!recv_dev) return fail(FR_EINVAL, "null buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    return m->prec == FR_FP64 ? halo_impl<double>(m, what, const_cast<void *>(recv_dev), false, s)
+                              : halo_impl<float>(m, what, const_cast<void *>(recv_dev), false, s);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1294,16 +1582,24 @@ struct RkFold {
     void *us = nullptr;
 };
 
+// only >= 0: just that phase of the fused form (0 face solution, 1 volume group, 2 interface group).
 template <typename T>
-static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, const RkFold &rk = RkFold())
+static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, const RkFold &rk = RkFold(), int only = -1)
 {
+    if (m->nparts > 1 && (m->form != FR_FUSED || only < 0))
+        return fail(FR_EUNSUPPORTED, "a partitioned mesh runs the fused phases one at a time (fr_rhs_phase) with "
+                                     "halo exchanges between them");
     if (m->form == FR_FUSED && m->curved && m->lowmach)
         return fail(FR_EUNSUPPORTED, "curved (non-affine) hexahedra: the low-Mach FP32 form is not built for them "
                                      "(set rho_ref = 0 for the plain FP32 form)");
     if (m->form == FR_FUSED) {
         static const int plain[3] = {0, 1, 2}, split[4] = {0, 1, 3, 4};
         const int *phases = m->split_c ? split : plain;
-        const int nph = m->split_c ? 4 : 3;
+        int nph = m->split_c ? 4 : 3;
+        if (only >= 0) {   // one phase: 0 -> A, 1 -> B, 2 -> C (or C1 + C2)
+            phases += only;
+            nph = only < 2 ? 1 : nph - 2;
+        }
         for (int pi = 0; pi < nph; pi++) {
             const int ph = phases[pi];
             TimeScope ts(m, ph, s);
@@ -1358,6 +1654,20 @@ static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, co
 static fr_status rhs_dispatch(fr_mesh *m, const void *U, void *R, cudaStream_t s)
 {
     return m->prec == FR_FP64 ? rhs_impl<double>(m, U, R, s) : rhs_impl<float>(m, U, R, s);
+}
+
+extern "C" fr_status fr_rhs_phase(fr_mesh *m, int phase, const void *U_dev, void *R_dev, void *stream)
+{
+    if (!m || !U_dev || !R_dev || phase < 0 || phase > 2) return fail(FR_EINVAL, "bad argument");
+    if (U_dev == R_dev) return fail(FR_EINVAL, "U and R must not alias");
+    if (m->form != FR_FUSED) return fail(FR_EUNSUPPORTED, "fr_rhs_phase runs the fused form");
+    fr_status st = check_status(m);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = m->prec == FR_FP64 ? rhs_impl<double>(m, U_dev, R_dev, s, RkFold(), phase)
+                            : rhs_impl<float>(m, U_dev, R_dev, s, RkFold(), phase);
+    if (st) return st;
+    return phase == 2 ? post_status(m, s) : FR_OK;
 }
 
 // Times every launch shape of the volume kernel of each hexahedral group on the caller's state and
@@ -1618,6 +1928,8 @@ static fr_status rk4_impl(fr_mesh *m, double *U, double dt, int nsteps, cudaStre
 extern "C" fr_status fr_rk4_step(fr_mesh *m, void *U_dev, double dt, int nsteps, void *stream)
 {
     if (!m || !U_dev || nsteps < 0 || !(dt == dt)) return fail(FR_EINVAL, "bad argument");
+    if (m->nparts > 1)
+        return fail(FR_EUNSUPPORTED, "a partitioned mesh advances through fr_rhs_phase and halo exchanges");
     fr_status st = check_status(m);
     if (st) return st;
     size_t ts = tsize(m->prec);
@@ -1743,7 +2055,7 @@ extern "C" fr_status fr_diagnostics(fr_mesh *m, const void *U, const void *R, do
         for (int z = 0; z < b.nu; z++)
             wp.w[z] = b.type == 0 ? h.w[z % h.n] * h.w[(z / h.n) % h.n] * h.w[z / (h.n * h.n)]
                     : b.type == 1 ? m->pri.wt[z % FR_PT] * h.w[z / FR_PT] : (b.type == 2 ? m->tet.w[z] : m->pyr.w[z]);
-        int grid = (int)std::min<long long>(std::max<long long>(b.ne, 1), 152LL * 8);
+        int grid = (int)std::min<long long>(std::max<long long>(b.ne, 1), 8LL * m->nsm);
         double *o = m->d_wsum + 8 * b.inst;
         size_t ts = tsize(m->prec);
         const char *u = (const char *)U + b.u0 * ts;
@@ -1765,8 +2077,8 @@ extern "C" fr_status fr_diagnostics(fr_mesh *m, const void *U, const void *R, do
         const double *a = &h[8 * i];
         double *o = out + 8 * i;
         o[0] = a[0];
-        o[1] = a[1] / a[0];
-        o[2] = a[2] / a[0];
+        o[1] = a[0] > 0 ? a[1] / a[0] : 0.0;   // an instance without elements has no mean
+        o[2] = a[0] > 0 ? a[2] / a[0] : 0.0;
         for (int k = 0; k < 5; k++) o[3 + k] = a[3 + k];
     }
     return FR_OK;
@@ -1785,20 +2097,18 @@ extern "C" fr_status fr_diagnostics(fr_mesh *m, const void *U, const void *R, do
 #define FR_NOALLOC_MAX_INST 1024
 static __device__ __align__(256) double g_diag_scratch[FR_NOALLOC_MAX_INST * 8];
 
-// Device address of g_diag_scratch, looked up once per device (the host-side symbol is only a
-// stand-in and must never be handed to a kernel).
-static double *diag_scratch_ptr(int dev, cudaError_t *err)
+// Device address of g_diag_scratch per device (the host-side symbol is only a stand-in and must
+// never be handed to a kernel). fr_mesh_create looks it up with the handle's device current, so every
+// live handle finds the address of the current context's copy, also after a cudaDeviceReset.
+static double *g_diag_ptrs[64] = {nullptr};
+
+static cudaError_t diag_scratch_lookup(int dev)
 {
-    static double *ptrs[64] = {nullptr};
-    *err = cudaSuccess;
-    if (dev < 0 || dev >= 64) { *err = cudaErrorInvalidDevice; return nullptr; }
-    if (!ptrs[dev]) {
-        double *p = nullptr;
-        *err = cudaGetSymbolAddress((void **)&p, g_diag_scratch);
-        if (*err != cudaSuccess) return nullptr;
-        ptrs[dev] = p;
-    }
-    return ptrs[dev];
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    double *p = nullptr;
+    const cudaError_t err = cudaGetSymbolAddress((void **)&p, g_diag_scratch);
+    g_diag_ptrs[dev] = err == cudaSuccess ? p : nullptr;
+    return err;
 }
 
 extern "C" fr_status fr_diagnostics_noalloc(fr_mesh *m, const void *U, const void *R, double *out, void *stream)
@@ -1810,9 +2120,10 @@ extern "C" fr_status fr_diagnostics_noalloc(fr_mesh *m, const void *U, const voi
                     FR_NOALLOC_MAX_INST);
     int dev = 0;
     CU(cudaGetDevice(&dev));
-    cudaError_t ce;
-    double *acc = diag_scratch_ptr(dev, &ce);
-    if (!acc) return fail(FR_ECUDA, "cudaGetSymbolAddress(g_diag_scratch): %s", cudaGetErrorString(ce));
+    if (dev != m->dev)
+        return fail(FR_EINVAL, "fr_diagnostics_noalloc: device %d is current, the handle lives on device %d", dev, m->dev);
+    double *acc = g_diag_ptrs[dev];
+    if (!acc) return fail(FR_ECUDA, "fr_diagnostics_noalloc: no device address of the diagnostics array");
     cudaStream_t s = (cudaStream_t)stream;
     // the array keeps the previous call's sums: clear the slots this call accumulates into
     CU(cudaMemsetAsync(acc, 0, (size_t)ni * 8 * sizeof(double), s));
@@ -1823,7 +2134,7 @@ extern "C" fr_status fr_diagnostics_noalloc(fr_mesh *m, const void *U, const voi
         for (int z = 0; z < b.nu; z++)
             wp.w[z] = b.type == 0 ? h.w[z % h.n] * h.w[(z / h.n) % h.n] * h.w[z / (h.n * h.n)]
                     : b.type == 1 ? m->pri.wt[z % FR_PT] * h.w[z / FR_PT] : (b.type == 2 ? m->tet.w[z] : m->pyr.w[z]);
-        int grid = (int)std::min<long long>(std::max<long long>(b.ne, 1), 152LL * 8);
+        int grid = (int)std::min<long long>(std::max<long long>(b.ne, 1), 8LL * m->nsm);
         double *o = acc + 8 * b.inst;
         size_t ts = tsize(m->prec);
         const char *u = (const char *)U + b.u0 * ts;
@@ -1843,8 +2154,8 @@ extern "C" fr_status fr_diagnostics_noalloc(fr_mesh *m, const void *U, const voi
     CU(cudaStreamSynchronize(s));
     for (int i = 0; i < ni; i++) {
         double *o = out + 8 * i;
-        o[1] /= o[0];
-        o[2] /= o[0];
+        o[1] = o[0] > 0 ? o[1] / o[0] : 0.0;   // an instance without elements has no mean
+        o[2] = o[0] > 0 ? o[2] / o[0] : 0.0;
     }
     return FR_OK;
 }

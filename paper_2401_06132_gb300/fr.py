@@ -243,7 +243,9 @@ class FRMesh:
         return {i: (ms[i], cnt[i]) for i in range(n_ids) if cnt[i]}
 
     def diagnostics_noalloc(self, U, R=None, stream=None):
-        """fr_diagnostics_noalloc: the same sums through the entry point that allocates nothing."""
+        """fr_diagnostics_noalloc: the same sums through the entry point that allocates nothing. While
+        another thread captures a stream in global mode, pass a non-blocking stream here (work on the
+        legacy default stream would join that capture)."""
         out = np.zeros(8 * self.n_inst)
         _check(lib().fr_diagnostics_noalloc(self.h, C.c_void_p(U.data_ptr()),
                                             C.c_void_p(R.data_ptr() if R is not None else 0),

@@ -75,6 +75,33 @@ def test_noalloc_diagnostics_per_instance_slots():
         _same(a, b)
 
 
+def test_noalloc_allocates_nothing_on_a_fresh_handle():
+    """A handle that has never run the allocating entry point: its first fr_diagnostics_noalloc call
+    changes neither the device bytes the handle owns (fr_mesh_info) nor the device's free memory
+    (cudaMemGetInfo); the allocating entry point, run afterwards, gives the same sums. A first handle
+    loads the diagnostics kernel (lazy module loading may place code in device memory) and evaluates
+    the RHS, so that the fresh handle does nothing before the call under test."""
+    mesh = W.box_hex_mesh(4)
+    o = O.Oracle(mesh, 3, 5)
+    U = W.tgv_state(o.sol_coords(), [(64, 64)], perturb=1e-2)
+    warm = fr.FRMesh(mesh, fr.make_params(p=3))
+    Ud = torch.from_numpy(U).cuda()
+    Rd = torch.empty_like(Ud)
+    warm.rhs(Ud, Rd)
+    warm.diagnostics_noalloc(Ud, Rd)
+    m = fr.FRMesh(mesh, fr.make_params(p=3))
+    torch.cuda.synchronize()
+    owned0, free0 = m.info()["device_bytes"], torch.cuda.mem_get_info()[0]
+    got = m.diagnostics_noalloc(Ud, Rd)[0]
+    torch.cuda.synchronize()
+    owned1, free1 = m.info()["device_bytes"], torch.cuda.mem_get_info()[0]
+    assert owned1 == owned0, (owned0, owned1)
+    assert free1 == free0, (free0, free1)
+    ref = m.diagnostics(Ud, Rd)[0]
+    _same(got, ref)
+    _same(m.diagnostics_noalloc(Ud, Rd)[0], ref)
+
+
 def test_noalloc_rejects_more_instances_than_its_scratch_holds():
     meshes = [W.box_hex_mesh(1)] * 1025
     m = fr.FRMesh(meshes, fr.make_params(p=3))
