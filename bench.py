@@ -31,6 +31,7 @@ UNIT = "GDOF*RHS/s"
 N_EDGE, P, MQ = 48, 3, 5
 DT = 2e-4
 RHS_PER_STEP = 4
+FR_NV_DOF_PER_ELEMENT = 5 * (P + 1) ** 3
 
 
 def workload_name(n=N_EDGE, p=P, m=MQ):
@@ -225,6 +226,32 @@ def _time_steps(m, U, steps, warmup, torch):
     return e0.elapsed_time(e1) / steps
 
 
+def rhs_error(m64, mred, U0, blocks, torch):
+    """Max per-variable relative L-inf error of a reduced-precision RHS: |R_red - R_64| over all
+    points of the blocks [(first value, elements, points per element)], divided by max |R_64|, per
+    conserved variable (blocks of one instance share the normalisation; the maximum over instances
+    is returned). Both RHS are evaluated on the FP32-rounded state; R_64 is the FP64 GPU form, which
+    the parity tests pin to the FP64 oracle at 1e-12."""
+    U32 = torch.from_numpy(U0.astype(np.float32)).cuda()
+    U64 = U32.double()
+    R64, R32 = torch.empty_like(U64), torch.empty_like(U32)
+    m64.rhs(U64, R64)
+    mred.rhs(U32, R32)
+    m64.sync_status()
+    mred.sync_status()
+    a, b = R32.double().cpu().numpy(), R64.cpu().numpy()
+    worst = 0.0
+    for inst in blocks:
+        d, sc = np.zeros(5), np.zeros(5)
+        for off, ne, nu in inst:
+            x = a[off:off + ne * 5 * nu].reshape(ne, 5, nu)
+            y = b[off:off + ne * 5 * nu].reshape(ne, 5, nu)
+            d = np.maximum(d, np.abs(x - y).max(axis=(0, 2)))
+            sc = np.maximum(sc, np.abs(y).max(axis=(0, 2)))
+        worst = max(worst, float((d / sc).max()))
+    return {"rhs_err_vs_fp64": worst, "within_2e-5": worst <= 2e-5}
+
+
 def other_configs(args, torch, fr, W):
     """Mixed hex/prism TGV (40^3 box: 32,000 hexes + 64,000 prisms, p = 3), the 48^3 TGV without
     anti-aliasing and with full (flux + surface-flux) anti-aliasing, a tetrahedral and a pyramidal TGV
@@ -236,6 +263,8 @@ def other_configs(args, torch, fr, W):
     mesh = W.mixed_box_mesh(40)
     p0 = W.tgv_p0()
     blocks = [(mesh["hex_v"].shape[0], 64), (mesh["pri_v"].shape[0], 40)]
+    eb = [[(0, blocks[0][0], 64), (blocks[0][0] * 5 * 64, blocks[1][0], 40)]]
+    m64 = None
     for prec in ("fp64", "fp32", "mixed_fp16", "mixed_bf16"):
         # reduced precisions in the low-Mach form (rho_ref = 1; FP64 ignores it)
         m = fr.FRMesh(mesh, fr.make_params(p=3, prec=prec, p_ref=p0, rho_ref=1.0))
@@ -247,10 +276,16 @@ def other_configs(args, torch, fr, W):
                                   "dof": int(U0.size), "elements": sum(b[0] for b in blocks)}
         if prec != "fp64":
             out[f"mixed40_{prec}"]["speedup_vs_fp64"] = out["mixed40_fp64"]["ms_per_step"] / ms
-        m.close()
+            out[f"mixed40_{prec}"].update(rhs_error(m64, m, U0, eb, torch))
+            m.close()
+        else:
+            m64 = m
+        del U
+    m64.close()
     # the same 48^3 p = 3 TGV without flux anti-aliasing (flux at the solution points), the paper's
     # "AA off" discretisation, FP64 and FP32 low-Mach
     mesh48 = W.box_hex_mesh(N_EDGE)
+    eb48 = [[(0, N_EDGE ** 3, (P + 1) ** 3)]]
     for prec in ("fp64", "fp32"):
         m = fr.FRMesh(mesh48, fr.make_params(p=P, nq1d=P + 1, prec=prec, p_ref=p0, rho_ref=1.0))
         U0 = W.tgv_state(m.sol_coords(), [(N_EDGE ** 3, (P + 1) ** 3)], perturb=1e-3)
@@ -259,7 +294,12 @@ def other_configs(args, torch, fr, W):
         m.sync_status()
         out[f"aa_off48_{prec}"] = {"gdof_rhs_per_s": U0.size * RHS_PER_STEP / (ms * 1e-3) / 1e9, "ms_per_step": ms,
                                    "dof": int(U0.size), "elements": N_EDGE ** 3}
-        m.close()
+        if prec == "fp64":
+            m64 = m
+        else:
+            out[f"aa_off48_{prec}"].update(rhs_error(m64, m, U0, eb48, torch))
+            m.close()
+            m64.close()
         del U
     # ... and with full anti-aliasing (flux + surface flux), FP64 and plain FP32
     for prec in ("fp64", "fp32"):
@@ -270,7 +310,12 @@ def other_configs(args, torch, fr, W):
         m.sync_status()
         out[f"aa_full48_{prec}"] = {"gdof_rhs_per_s": U0.size * RHS_PER_STEP / (ms * 1e-3) / 1e9, "ms_per_step": ms,
                                     "dof": int(U0.size), "elements": N_EDGE ** 3}
-        m.close()
+        if prec == "fp64":
+            m64 = m
+        else:   # the plain FP32 form: the low-Mach form is not built for surface-flux anti-aliasing
+            out[f"aa_full48_{prec}"].update(rhs_error(m64, m, U0, eb48, torch))
+            m.close()
+            m64.close()
         del U
     # tetrahedra: the 24^3 box split into 82,944 Kuhn tetrahedra (p = 3, dense operators, collapsed
     # 5^3 quadrature), FP64, FP32 and the mixed FP16 form with the interpolation on the tensor cores
@@ -303,10 +348,14 @@ def other_configs(args, torch, fr, W):
         del Uc, Rc
         if prec != "fp64":
             out[f"tet24_{name}"]["speedup_vs_fp64"] = out["tet24_fp64"]["ms_per_step"] / ms
-        m.close()
+            out[f"tet24_{name}"].update(rhs_error(m64, m, U0, [[(0, nt, 20)]], torch))
+            m.close()
+        else:
+            m64 = m
         del U
     # curved (trilinear) hexahedra, 48^3 p = 3: metric terms at every point; fused FP64 and plain
     # FP32, and the unfused FP64 form
+    m64.close()
     mesh_c = W.curved_box_mesh(N_EDGE)
     for name, prec, form in (("fp64", "fp64", "fused"), ("fp32", "fp32", "fused"), ("unfused_fp64", "fp64", "unfused")):
         m = fr.FRMesh(mesh_c, fr.make_params(p=P, prec=prec, p_ref=p0))
@@ -317,9 +366,15 @@ def other_configs(args, torch, fr, W):
         m.sync_status()
         out[f"curved48_{name}"] = {"gdof_rhs_per_s": U0.size * RHS_PER_STEP / (ms * 1e-3) / 1e9,
                                    "ms_per_step": ms, "dof": int(U0.size), "elements": N_EDGE ** 3}
-        m.close()
+        if name == "fp64":
+            m64 = m
+        else:
+            if name == "fp32":   # the plain FP32 form: the low-Mach form is not built for curved elements
+                out[f"curved48_{name}"].update(rhs_error(m64, m, U0, eb48, torch))
+            m.close()
         del U
         torch.cuda.empty_cache()
+    m64.close()
     # pyramids: the 20^3 box, every cell split into six pyramids (48,000 pyramids, 7.2M DOF)
     mesh_y = W.box_pyr_mesh(20)
     ny = mesh_y["pyr_v"].shape[0]
@@ -341,12 +396,16 @@ def other_configs(args, torch, fr, W):
         out[f"pyr20_{prec}"] = {"gdof_rhs_per_s": U0.size * RHS_PER_STEP / (ms * 1e-3) / 1e9, "ms_per_step": ms,
                                 "dof": int(U0.size), "elements": ny, "volume_kernel_ms": b_ms,
                                 "volume_tflops": fl_y * ny / (b_ms * 1e-3) / 1e12, "flops_per_element": fl_y}
+        del Uc, Rc
         if prec == "fp64":
             out["pyr20_fp64"]["volume_frac_of_fp64_peak"] = out["pyr20_fp64"]["volume_tflops"] / FP64_PEAK_TFLOPS
+            m64 = m
         else:
             out[f"pyr20_{prec}"]["speedup_vs_fp64"] = out["pyr20_fp64"]["ms_per_step"] / ms
-        m.close()
-        del U, Uc, Rc
+            out[f"pyr20_{prec}"].update(rhs_error(m64, m, U0, [[(0, ny, 30)]], torch))
+            m.close()
+            m64.close()
+        del U
     draws = W.ensemble_draws(64)
     meshes = [W.box_hex_mesh(d["edge"]) for d in draws]
     for prec in ("fp64", "fp32"):
@@ -371,10 +430,77 @@ def other_configs(args, torch, fr, W):
                                      "launches_per_rhs": int(info["launches_per_rhs"])}
         if prec != "fp64":
             out[f"ensemble64_{prec}"]["speedup_vs_fp64"] = out["ensemble64_fp64"]["ms_per_step"] / ms
-        m.close()
+            eb = [[(int(off[i]), d["edge"] ** 3, (d["p"] + 1) ** 3)] for i, d in enumerate(draws)]
+            out[f"ensemble64_{prec}"].update(rhs_error(m64, m, U0, eb, torch))
+            m.close()
+            m64.close()
+        else:
+            m64 = m
         del U
         torch.cuda.empty_cache()
     return out
+
+
+def run_partitioned(args, rank, world):
+    """The 48^3 mesh split into `world` z slabs, one per GPU: every RHS evaluation runs phase A,
+    a halo exchange of the face solution, phase B, an exchange of the face viscous flux, phase C
+    (partition.py; NCCL send/recv under torchrun). A step here is one RHS evaluation (the partitioned
+    handle has no RK4 entry point); strong scaling: the whole mesh is the same for every N."""
+    import torch
+
+    from paper_2401_06132_gb300 import build as B
+    from paper_2401_06132_gb300 import fr, partition, replicas, workloads as W
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    mesh = W.box_hex_mesh(N_EDGE)
+    prm = fr.make_params(p=P, prec="fp64", p_ref=W.tgv_p0())
+    m = fr.FRMesh.part(mesh, prm, world, rank)
+    info = m.halo_info()
+    e0, _ = info["elements"]
+    U0 = W.tgv_state(m.sol_coords(), [(m.info()["elements"], (P + 1) ** 3)], perturb=1e-3,
+                     dof_offset=e0 * FR_NV_DOF_PER_ELEMENT)
+    U = torch.from_numpy(U0).cuda()
+    R = torch.empty_like(U)
+    pr = partition.PartRHS(m)
+
+    def exchange(what):
+        if world > 1:
+            partition.dist_exchange(pr.send[what], pr.recv[what], pr.counts, pr.nvar[what], rank)
+
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(args.warmup):
+            pr.rhs(U, R, exchange)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        e0v, e1v = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            e0v.record(s)
+            for _ in range(args.steps):
+                pr.rhs(U, R, exchange)
+            e1v.record(s)
+            torch.cuda.synchronize()
+    m.sync_status(stream=s)
+    ms = replicas.max_over_ranks(e0v.elapsed_time(e1v) / args.steps, device="cuda")
+    dof_total = N_EDGE ** 3 * FR_NV_DOF_PER_ELEMENT
+    if rank != 0:
+        return
+    value = dof_total / (ms * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(), "mode": "partitioned single mesh (z slabs), step = one RHS",
+                       "parallelism": f"{world} parts, 2 halo exchanges per RHS", "halo_points": info["nhalo"],
+                       "l2": "inputs larger than L2 (283 MB FP64 state, 129 MB L2)"},
+            "gpu_launches": (3 + 4 * sum(1 for c in info["counts"] if c)) * args.steps,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
 
 
 def run_ours(args, rank, world):
@@ -465,9 +591,10 @@ def run_ours(args, rank, world):
     m.set_form("unfused")
     forms["unfused_fp64"] = dof * RHS_PER_STEP / (time_rk4(m, U, ksteps, 1, torch) * 1e-3) / 1e9
     m.set_form("fused")
-    m.close()
-    del m
+    del U
     torch.cuda.empty_cache()
+    errs = {}
+    eb = [[(0, N_EDGE ** 3, (P + 1) ** 3)]]
     m32 = fr.FRMesh(mesh, fr.make_params(p=P, prec="fp32", p_ref=p0, rho_ref=1.0))
     U = torch.from_numpy(U0).cuda()
     U32 = U.float()
@@ -475,8 +602,10 @@ def run_ours(args, rank, world):
     del U32
     # FP32 fused: low-Mach form (<= 2e-5 relative RHS error against the FP64 oracle)
     forms["fused_fp32"] = dof * RHS_PER_STEP / (time_rk4(m32, U, ksteps, 2, torch) * 1e-3) / 1e9
+    errs["fused_fp32"] = rhs_error(m, m32, U0, eb, torch)
     m32.set_form("unfused")   # plain FP32, one kernel per paper kernel
     forms["unfused_fp32"] = dof * RHS_PER_STEP / (time_rk4(m32, U, ksteps, 1, torch) * 1e-3) / 1e9
+    errs["unfused_fp32"] = rhs_error(m, m32, U0, eb, torch)
     m32.close()
     del m32
     # mixed forms with the hexahedral x-y plane contractions moved to the tensor cores as split
@@ -485,8 +614,11 @@ def run_ours(args, rank, world):
         mm = fr.FRMesh(mesh, fr.make_params(p=P, prec=prec, p_ref=p0, rho_ref=1.0))
         mm.set_hex_tensor_cores(True)
         forms[f"fused_{prec}_hex_tensor_cores"] = dof * RHS_PER_STEP / (time_rk4(mm, U, ksteps, 2, torch) * 1e-3) / 1e9
+        errs[f"fused_{prec}_hex_tensor_cores"] = rhs_error(m, mm, U0, eb, torch)
         mm.close()
         del mm
+    m.close()
+    del m, U
     torch.cuda.empty_cache()
 
     # --- the other workloads: mixed hex/prism grid and the batched ensemble -----------------------
@@ -528,6 +660,7 @@ def run_ours(args, rank, world):
         "hbm_roofline": {"compulsory_bytes_per_rhs": compulsory, "peak_gbs": hbm_peak,
                          "frac": hbm_frac, "note": "compulsory bytes (U read + R written) / RHS time / measured copy peak"},
         "forms_gdof_rhs_per_s": forms,
+        "forms_rhs_error": errs,
         "other_workloads": others,
         "kernel_share": share,
         "probe": probe,
@@ -547,6 +680,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--skip-configs", action="store_true", help="skip the mixed-grid and ensemble workloads")
+    ap.add_argument("--mode", default="replicas", choices=["replicas", "partitioned"],
+                    help="N > 1: independent replicas (weak scaling) or one mesh split over the GPUs (strong)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -558,6 +693,8 @@ def main():
         torch.distributed.init_process_group(backend)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.mode == "partitioned":
+        run_partitioned(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1:

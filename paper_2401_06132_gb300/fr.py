@@ -76,6 +76,13 @@ def lib():
             "fr_autotune": ([vp, vp, vp, C.POINTER(C.c_int), C.c_int, vp], C.c_int),
             "fr_kernel_times": ([vp, C.POINTER(C.c_double), llp, C.c_int], C.c_int),
             "fr_probe_fma": ([dp, vp], C.c_int),
+            "fr_partition_plan": ([C.POINTER(MeshDesc), C.POINTER(Params), C.c_int, C.c_int, llp, llp, llp, llp,
+                                   C.c_longlong], C.c_int),
+            "fr_mesh_create_part": ([C.POINTER(MeshDesc), C.POINTER(Params), C.c_int, C.c_int, C.POINTER(vp)], C.c_int),
+            "fr_halo_info": ([vp, llp, llp], C.c_int),
+            "fr_halo_pack": ([vp, C.c_int, vp, vp], C.c_int),
+            "fr_halo_unpack": ([vp, C.c_int, vp, vp], C.c_int),
+            "fr_rhs_phase": ([vp, C.c_int, vp, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -101,6 +108,39 @@ def make_params(p=3, gamma=1.4, Pr=0.71, mu=1.0 / 1600, beta=0.5, tau=0.1, prec=
                   int(bool(surface_aa)))
 
 
+def _mesh_desc(m: dict, keep: list) -> MeshDesc:
+    """fr_mesh_desc of a mesh dict; the arrays it points to are appended to `keep`."""
+    verts = np.ascontiguousarray(m["verts"], dtype=np.float64)
+    hex_v = np.ascontiguousarray(m.get("hex_v", np.zeros((0, 8))), dtype=np.int32)
+    pri_v = np.ascontiguousarray(m.get("pri_v", np.zeros((0, 6))), dtype=np.int32)
+    tet_v = np.ascontiguousarray(m.get("tet_v", np.zeros((0, 4))), dtype=np.int32)
+    pyr_v = np.ascontiguousarray(m.get("pyr_v", np.zeros((0, 5))), dtype=np.int32)
+    keep += [verts, hex_v, pri_v, tet_v, pyr_v]
+    ip = C.POINTER(C.c_int)
+    return MeshDesc(hex_v.shape[0], pri_v.shape[0], verts.shape[0], verts.ctypes.data_as(C.POINTER(C.c_double)),
+                    hex_v.ctypes.data_as(ip), pri_v.ctypes.data_as(ip),
+                    (C.c_double * 3)(*m.get("period", (0.0, 0.0, 0.0))), tet_v.shape[0], tet_v.ctypes.data_as(ip),
+                    pyr_v.shape[0], pyr_v.ctypes.data_as(ip))
+
+
+def partition_plan(mesh: dict, params: Params, nparts: int, part: int) -> dict:
+    """fr_partition_plan (host only): own element range, per-peer counts, and the whole-mesh flux
+    points this part sends and receives, in buffer order."""
+    keep = []
+    d = _mesh_desc(mesh, keep)
+    info = (C.c_longlong * 6)()
+    counts = (C.c_longlong * nparts)()
+    _check(lib().fr_partition_plan(C.byref(d), C.byref(params), nparts, part, info, counts, None, None, 0))
+    n = info[3]
+    send = np.zeros(max(n, 1), dtype=np.int64)
+    recv = np.zeros(max(n, 1), dtype=np.int64)
+    llp = C.POINTER(C.c_longlong)
+    _check(lib().fr_partition_plan(C.byref(d), C.byref(params), nparts, part, info, counts,
+                                   send.ctypes.data_as(llp), recv.ctypes.data_as(llp), n))
+    return dict(elements=(info[0], info[1]), nfpt_own=info[2], nhalo=n, ne_total=info[4], nfpt_total=info[5],
+                counts=list(counts), send=send[:n].copy(), recv=recv[:n].copy())
+
+
 class FRMesh:
     """One handle over one or more independent mesh instances (batched ensemble when several)."""
 
@@ -111,20 +151,7 @@ class FRMesh:
             params = [params] * len(meshes)
         assert len(params) == len(meshes)
         self._keep = []
-        descs = []
-        for m in meshes:
-            verts = np.ascontiguousarray(m["verts"], dtype=np.float64)
-            hex_v = np.ascontiguousarray(m.get("hex_v", np.zeros((0, 8))), dtype=np.int32)
-            pri_v = np.ascontiguousarray(m.get("pri_v", np.zeros((0, 6))), dtype=np.int32)
-            tet_v = np.ascontiguousarray(m.get("tet_v", np.zeros((0, 4))), dtype=np.int32)
-            pyr_v = np.ascontiguousarray(m.get("pyr_v", np.zeros((0, 5))), dtype=np.int32)
-            self._keep += [verts, hex_v, pri_v, tet_v, pyr_v]
-            ip = C.POINTER(C.c_int)
-            d = MeshDesc(hex_v.shape[0], pri_v.shape[0], verts.shape[0], verts.ctypes.data_as(C.POINTER(C.c_double)),
-                         hex_v.ctypes.data_as(ip), pri_v.ctypes.data_as(ip),
-                         (C.c_double * 3)(*m.get("period", (0.0, 0.0, 0.0))), tet_v.shape[0], tet_v.ctypes.data_as(ip),
-                         pyr_v.shape[0], pyr_v.ctypes.data_as(ip))
-            descs.append(d)
+        descs = [_mesh_desc(m, self._keep) for m in meshes]
         arr = (C.POINTER(MeshDesc) * len(descs))(*[C.pointer(d) for d in descs])
         self._descs = descs
         prm = (Params * len(params))(*params)
@@ -133,6 +160,44 @@ class FRMesh:
         self.h = h
         self.prec = params[0].prec
         self.n_inst = len(meshes)
+
+    @classmethod
+    def part(cls, mesh: dict, params: Params, nparts: int, part: int) -> "FRMesh":
+        """fr_mesh_create_part: part `part` of nparts of a single-instance mesh (own elements only)."""
+        self = cls.__new__(cls)
+        self._keep = []
+        self._descs = [_mesh_desc(mesh, self._keep)]
+        h = C.c_void_p()
+        _check(lib().fr_mesh_create_part(C.byref(self._descs[0]), C.byref(params), nparts, part, C.byref(h)))
+        self.h = h
+        self.prec = params.prec
+        self.n_inst = 1
+        return self
+
+    def halo_info(self) -> dict:
+        info = (C.c_longlong * 7)()
+        n = max(1, int(self._halo_nparts()))
+        counts = (C.c_longlong * n)()
+        _check(lib().fr_halo_info(self.h, info, counts))
+        return dict(nparts=info[0], part=info[1], elements=(info[2], info[3]), nhalo=info[4],
+                    nvar=(info[5], info[6]), counts=list(counts)[:info[0]])
+
+    def _halo_nparts(self) -> int:
+        info = (C.c_longlong * 7)()
+        _check(lib().fr_halo_info(self.h, info, None))
+        return info[0]
+
+    def halo_pack(self, what: int, send, stream=None):
+        _check(lib().fr_halo_pack(self.h, what, C.c_void_p(send.data_ptr()), _stream_ptr(stream)))
+
+    def halo_unpack(self, what: int, recv, stream=None):
+        _check(lib().fr_halo_unpack(self.h, what, C.c_void_p(recv.data_ptr()), _stream_ptr(stream)))
+
+    def rhs_phase(self, phase: int, U, R, stream=None):
+        self._check_tensor(U)
+        self._check_tensor(R)
+        _check(lib().fr_rhs_phase(self.h, phase, C.c_void_p(U.data_ptr()), C.c_void_p(R.data_ptr()),
+                                  _stream_ptr(stream)))
 
     def close(self):
         if getattr(self, "h", None):
