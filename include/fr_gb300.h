@@ -231,7 +231,13 @@ fr_status fr_diagnostics_noalloc(fr_mesh *m, const void *U_dev, const void *R_de
  * n_host is the capacity in doubles; the needed size is returned in *n_needed. Synchronises. */
 fr_status fr_stage(fr_mesh *m, int which, double *host, long long n_host, long long *n_needed);
 
-/* Debug flags: bit 0 keeps a copy of the unfused form's physical gradient Q^(u) for fr_stage(2). */
+/* Debug flags: bit 0 keeps a copy of the unfused form's physical gradient Q^(u) for fr_stage(2).
+ * Bit 1 makes the first bounded device wait of every CTA give up at once (the tensor-core completion
+ * wait of the mixed forms' volume kernels and the hexahedral state prefetch of p = 3): the kernel
+ * reports it (FR_ETIMEOUT at the next fr_sync_status or call), waits for its own asynchronous work
+ * with the normal bound, releases its tensor memory and returns (the tensor-core kernels leave their
+ * remaining elements unevaluated; the prefetch falls back to a global-memory read, so R stays
+ * correct). It exercises the failure path without any fault. */
 fr_status fr_set_debug(fr_mesh *m, int flags);
 
 /* RK4 CUDA graphs (on = 1, the default): fr_rk4_step captures one step (stage states, RHS launches,

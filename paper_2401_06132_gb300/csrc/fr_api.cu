@@ -1166,6 +1166,7 @@ extern "C" fr_status fr_set_debug(fr_mesh *m, int flags)
 {
     if (!m) return fail(FR_EINVAL, "null handle");
     m->debug = flags;
+    if (m->graph) { cudaGraphExecDestroy(m->graph); m->graph = nullptr; }   // recapture with the new arguments
     return FR_OK;
 }
 
@@ -1501,6 +1502,7 @@ static HexArgs<T> make_args(fr_mesh *m, const Block &b, const void *U, void *R)
     a.Qu = reinterpret_cast<T *>(m->d_Qu); a.UQ = reinterpret_cast<T *>(m->d_UQ); a.QQ = reinterpret_cast<T *>(m->d_QQ);
     a.Rt = reinterpret_cast<T *>(m->d_Rt);
     a.status = m->d_status;
+    a.dbg_wait0 = (m->debug & 2) ? 1 : 0;
     a.tcmode = m->prec == FR_MIXED_FP16 ? 1 : (m->prec == FR_MIXED_BF16 ? 2 : 0);
     if (b.type == 0 && !m->hex_tc) a.tcmode = 0;
     if ((b.type == 2 || b.type == 3) && !m->dense_tc) a.tcmode = 0;

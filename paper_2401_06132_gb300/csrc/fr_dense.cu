@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? (TCM == 0 ? 8 : 6) : 0) 
     int *s_sh = nullptr;
     uint64_t *mbar = nullptr;
     uint32_t *s_tmem = nullptr, tmem = 0, parity = 0;
-    bool tc_fail = false;
+    bool tc_fail = false, first_wait = true;
     if constexpr (TCM != 0) {
         const uint32_t raw = tc::smem_u32(arr);
         tA = arr + ((128 - (raw & 127)) & 127);
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? (TCM == 0 ? 8 : 6) : 0) 
         }
         if constexpr (TCM != 0) {
             // the interpolation issued above: wait (bounded) and read lane q = this thread
-            const bool done = tc::mbar_wait(mbar, parity);
+            const bool done = tc::mbar_wait(mbar, parity, tc::first_limit(first_wait, a.dbg_wait0));
             if (!__syncthreads_and(done)) {
                 tc_fail = true;
                 break;

@@ -610,6 +610,7 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
     __shared__ uint64_t s_ubar;
     bool pending = false;
     uint32_t uparity = 0;
+    bool first_wait = true;
     if constexpr (TMA_U) {
         if (threadIdx.x == 0) tc::mbar_init(&s_ubar, 1);
         __syncthreads();
@@ -654,7 +655,7 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
         const T *usrc = U;
         if constexpr (TMA_U) {
             if (pending) {
-                const bool landed = tc::mbar_wait(&s_ubar, uparity);
+                const bool landed = tc::mbar_wait(&s_ubar, uparity, tc::first_limit(first_wait, a.dbg_wait0));
                 uparity ^= 1;
                 pending = false;
                 if (__syncthreads_and(landed)) {
@@ -950,7 +951,8 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
                 s_sh[r] = split_row<TCM, TC::N2>(x, hl);
                 store_split_row<TC::KI, TC::N2>(tA, r, hl);
             }
-            if (!tc::mma_chain<TC::KI / 16>(tmem, tA, TC::SBO_I, tBi, TC::SBO_I, tc::idesc_f16(TCM - 1, 128, TC::NI), s_mbar, parity)) {
+            if (!tc::mma_chain<TC::KI / 16>(tmem, tA, TC::SBO_I, tBi, TC::SBO_I, tc::idesc_f16(TCM - 1, 128, TC::NI), s_mbar, parity,
+                                            tc::first_limit(first_wait, a.dbg_wait0))) {
                 tc_fail = true;
                 break;
             }
@@ -1062,7 +1064,8 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
                 s_sh[r] = split_row<TCM, TC::M2>(x, hl);
                 store_split_row<TC::KP, TC::M2>(tA, r, hl);
             }
-            if (!tc::mma_chain<TC::KP / 16>(tmem, tA, TC::SBO_P, tBp, TC::SBO_P, tc::idesc_f16(TCM - 1, 128, TC::NP), s_mbar, parity)) {
+            if (!tc::mma_chain<TC::KP / 16>(tmem, tA, TC::SBO_P, tBp, TC::SBO_P, tc::idesc_f16(TCM - 1, 128, TC::NP), s_mbar, parity,
+                                            tc::first_limit(first_wait, a.dbg_wait0))) {
                 tc_fail = true;
                 break;
             }

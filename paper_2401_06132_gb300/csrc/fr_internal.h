@@ -282,6 +282,9 @@ struct HexArgs {
     const T *mu;              // [elem][nu][10]: J^-1 (row-major dxi_i/dx_j) and det J at solution points
     const T *mq;              // [elem][nq][9]: det J J^-1 at quadrature points
     const T *mfn;             // [elem][nf][4]: unit outward normal and |n_s| at flux points
+    // Debug: the first bounded wait of every CTA (tensor-core completion or state prefetch) gives up
+    // at once, so that the FR_ETIMEOUT path runs without any fault; the drain wait keeps its bound.
+    int dbg_wait0;
 };
 
 #ifdef __CUDACC__

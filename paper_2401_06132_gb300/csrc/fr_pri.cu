@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
     int *s_sh = nullptr;
     uint64_t *mbar = nullptr;
     uint32_t *s_tmem = nullptr, tmem = 0, parity = 0;
-    bool tc_fail = false;
+    bool tc_fail = false, first_wait = true;
     if constexpr (TCM != 0) {
         const uint32_t raw = tc::smem_u32(arr);
         tA = arr + ((128 - (raw & 127)) & 127);
@@ -481,7 +481,8 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
                 tc::store_row<TC_KI>(tA, r, kv);
                 s_sh[r] = sh;
             }
-            if (!tc::mma_chain<TC_KI / 16>(tmem, tA, TC_SBO_I, tBi, TC_SBO_I, TCM == 1 ? TC_IDESC_I1 : TC_IDESC_I2, mbar, parity)) {
+            if (!tc::mma_chain<TC_KI / 16>(tmem, tA, TC_SBO_I, tBi, TC_SBO_I, TCM == 1 ? TC_IDESC_I1 : TC_IDESC_I2, mbar, parity,
+                                            tc::first_limit(first_wait, a.dbg_wait0))) {
                 tc_fail = true;
                 break;
             }
@@ -552,7 +553,8 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
                 tc::store_row<TC_KP>(tA, r, kv);
                 s_sh[r] = sh;
             }
-            if (!tc::mma_chain<TC_KP / 16>(tmem, tA, TC_SBO_P, tBp, TC_SBO_P, TCM == 1 ? TC_IDESC_P1 : TC_IDESC_P2, mbar, parity)) {
+            if (!tc::mma_chain<TC_KP / 16>(tmem, tA, TC_SBO_P, tBp, TC_SBO_P, TCM == 1 ? TC_IDESC_P1 : TC_IDESC_P2, mbar, parity,
+                                            tc::first_limit(first_wait, a.dbg_wait0))) {
                 tc_fail = true;
                 break;
             }

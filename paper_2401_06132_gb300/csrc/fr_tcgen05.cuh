@@ -179,11 +179,11 @@ __device__ __forceinline__ void store_row(unsigned char *base, int r, const uint
 
 // One MMA chain D = A B^T over KSTEPS slices of K = 16 (M = 128 rows of A, N rows of B, both K-major
 // with lbo = 128), issued by thread 0 after every thread's operand stores are made visible to the
-// tensor core; then every thread waits (bounded) for completion. Returns false, uniformly across
-// the CTA, if the wait gave up; the phase parity advances only on success.
+// tensor core; then every thread waits (at most `limit` polls) for completion. Returns false,
+// uniformly across the CTA, if the wait gave up; the phase parity advances only on success.
 template <int KSTEPS>
 __device__ __forceinline__ bool mma_chain(uint32_t tmem, const unsigned char *A, int sbo_a, const unsigned char *B, int sbo_b,
-                                          uint32_t idesc, uint64_t *mbar, uint32_t &parity)
+                                          uint32_t idesc, uint64_t *mbar, uint32_t &parity, uint32_t limit = 1u << 24)
 {
     fence_async_smem();
     fence_before_sync();
@@ -196,7 +196,7 @@ __device__ __forceinline__ bool mma_chain(uint32_t tmem, const unsigned char *A,
             mma_f16(tmem, sdesc(aA + 256 * j, 128, sbo_a), sdesc(aB + 256 * j, 128, sbo_b), idesc, j);
         commit(mbar);
     }
-    const bool done = mbar_wait(mbar, parity);
+    const bool done = mbar_wait(mbar, parity, limit);
     if (!__syncthreads_and(done)) return false;
     parity ^= 1;
     fence_after_sync();
@@ -209,6 +209,15 @@ __device__ __forceinline__ void setup(uint64_t *mbar, uint32_t *s_tmem, uint32_t
     if (threadIdx.x == 0) mbar_init(mbar, 1);
     __syncwarp();
     if (threadIdx.x < 32) tmem_alloc(s_tmem, ncols);
+}
+
+// Poll limit of a CTA's first bounded wait: 0 when the debug switch that makes it give up at once is on
+// (exercises the give-up path: report, drain with the normal bound, release, return).
+__device__ __forceinline__ uint32_t first_limit(bool &first, int give_up)
+{
+    const uint32_t l = (first && give_up) ? 0u : (1u << 24);
+    first = false;
+    return l;
 }
 
 // Per-CTA teardown; `failed`: a chain gave up, so its completion gets one more bounded wait first.

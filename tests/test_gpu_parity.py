@@ -174,6 +174,50 @@ def test_nonphysical_state_is_reported_not_faulted():
     m.sync_status()                   # the status word was cleared
 
 
+def test_bounded_waits_give_up_and_report_timeout():
+    """Debug bit 1: the first bounded device wait of every CTA gives up at once (no fault: the kernel
+    reports it, drains its own asynchronous work with the normal bound, releases its tensor memory and
+    returns). Mixed FP16 form on the 2^3 mixed grid (the prism volume kernel's tensor-core waits):
+    fr_sync_status reports FR_ETIMEOUT, and the next call with the switch off is correct again. FP64
+    hexahedra on the 24^3 box (the state-prefetch wait of CTAs that own more than one element): FR_ETIMEOUT
+    is reported and R is unchanged bit for bit, since the kernel falls back to reading the state from
+    global memory."""
+    N = 2
+    mesh = W.mixed_box_mesh(N)
+    blocks = [(mesh["hex_v"].shape[0], 64), (mesh["pri_v"].shape[0], 40)]
+    p0 = W.tgv_p0()
+    o = O.Oracle(mesh, 3, 5, threads=NCPU, p_ref=p0)
+    U = W.tgv_state(o.sol_coords(), blocks, perturb=1e-3).astype(np.float32)
+    Ro = o.rhs(U.astype(np.float64))
+    m = fr.FRMesh(mesh, fr.make_params(p=3, prec="mixed_fp16", p_ref=p0, rho_ref=1.0))
+    Ud = torch.from_numpy(U).cuda()
+    Rd = torch.empty_like(Ud)
+    m.set_debug(2)
+    m.rhs(Ud, Rd)
+    with pytest.raises(fr.FRError) as e:
+        m.sync_status()
+    assert e.value.status == fr.FR_ETIMEOUT
+    m.set_debug(0)
+    m.rhs(Ud, Rd)
+    m.sync_status()
+    err = _rel_linf_blocks(Rd.cpu().numpy().astype(np.float64), Ro, blocks)
+    assert err.max() <= 2e-5, err
+    # FP64 hexahedra: the prefetch falls back to global memory
+    mesh = W.box_hex_mesh(24)
+    m = fr.FRMesh(mesh, fr.make_params(p=3, p_ref=p0))
+    U = W.tgv_state(m.sol_coords(), [(24 ** 3, 64)], perturb=1e-3)
+    Ud = torch.from_numpy(U).cuda()
+    R0, R1 = torch.empty_like(Ud), torch.empty_like(Ud)
+    m.rhs(Ud, R0)
+    m.sync_status()
+    m.set_debug(2)
+    m.rhs(Ud, R1)
+    with pytest.raises(fr.FRError) as e:
+        m.sync_status()
+    assert e.value.status == fr.FR_ETIMEOUT
+    assert torch.equal(R0, R1)
+
+
 @pytest.mark.parametrize("form", ["fused", "unfused"])
 def test_full_size_48cubed_fp64_parity(form):
     """The benchmark workload itself: 48^3 hex p=3, 5^3 quadrature, FP64, in the launch configuration
