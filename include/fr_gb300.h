@@ -176,12 +176,21 @@ fr_status fr_rk4_step(fr_mesh *m, void *U_dev, double dt, int nsteps, void *stre
  * synchronises the stream. */
 fr_status fr_rk4_step_host(fr_mesh *m, void *U_host, double dt, int nsteps, void *stream);
 
-/* Autotuner: times every launch shape of the volume kernel (64, 128 or 256 threads per element) of
- * each hexahedral group (one element type and order) on the given device state U_dev (R_dev is
- * scratch output) and keeps the fastest for later calls. chosen[i] (n_chosen entries, may be NULL)
- * receives the shape index 0, 1, 2 of group i. Results of later calls do not depend on the choice:
- * every shape evaluates each output with the same operations. Synchronises the stream. */
+/* Autotuner: times every launch shape of the volume kernel of each hexahedral group (one element
+ * type and order) on the given device state U_dev (R_dev is scratch output) and keeps the fastest
+ * for later calls. Shapes: 0, 1, 2 = one element per CTA of 64, 128 or 256 threads; for FP32 (and
+ * the mixed forms without hexahedral tensor cores) at p = 3 with flux anti-aliasing on affine
+ * elements also 3, 4 = eight elements per CTA of 160 threads, each sum-factorised operator applied
+ * to a whole field by one thread from registers (one CTA per SM with up to 255 registers, or two).
+ * chosen[i] (n_chosen entries, may be NULL) receives the shape index of group i. Shapes 0, 1 and 2
+ * evaluate each output with the same operations (results do not depend on the choice among them);
+ * shapes 3 and 4 sum the projection's 1D factors in another order (the factors commute), so FP32
+ * results then differ at the FP32 rounding level. Synchronises the stream. */
 fr_status fr_autotune(fr_mesh *m, const void *U_dev, void *R_dev, int *chosen, int n_chosen, void *stream);
+
+/* Sets the volume-kernel launch shape (0..4, as for fr_autotune) of every hexahedral group;
+ * FR_EUNSUPPORTED if a group cannot run it. Takes effect at the next launch (recaptures the RK4 graph). */
+fr_status fr_set_volume_shape(fr_mesh *m, int shape);
 
 /* Blocks until the stream's work on this handle has finished and returns the latched device
  * status (FR_OK or FR_ENONPHYS), clearing it. */

@@ -1672,6 +1672,31 @@ extern "C" fr_status fr_rhs_phase(fr_mesh *m, int phase, const void *U_dev, void
     return phase == 2 ? post_status(m, s) : FR_OK;
 }
 
+// Launch shapes of a hexahedral group's volume kernel: 0, 1, 2 = one element per CTA of 64, 128,
+// 256 threads; FP32 p = 3 with flux anti-aliasing on the CUDA cores also 3, 4 = eight elements per
+// CTA with register-resident line sweeps (one or two CTAs per SM).
+static int volume_shapes(const fr_mesh *m, const Block &b)
+{
+    const bool b32 = m->prec != FR_FP64 && b.p == 3 && b.m == b.p + 2 && !m->surf && !m->curved &&
+                     (m->prec == FR_FP32 || !m->hex_tc);
+    return b32 ? 6 : 3;
+}
+
+extern "C" fr_status fr_set_volume_shape(fr_mesh *m, int shape)
+{
+    if (!m || shape < 0 || shape > 5) return fail(FR_EINVAL, "bad argument");
+    for (Group &g : m->groups) {
+        const Block &b = m->blocks[g.blks[0]];
+        if (b.type != 0) continue;
+        if (shape >= volume_shapes(m, b))
+            return fail(FR_EUNSUPPORTED, "volume-kernel shape %d needs FP32, p = 3, flux anti-aliasing, affine elements", shape);
+    }
+    for (Group &g : m->groups)
+        if (m->blocks[g.blks[0]].type == 0) g.variant = shape;
+    if (m->graph) { cudaGraphExecDestroy(m->graph); m->graph = nullptr; }
+    return FR_OK;
+}
+
 // Times every launch shape of the volume kernel of each hexahedral group on the caller's state and
 // keeps the fastest. Every shape computes each output with the same operations, so results do not
 // depend on the choice.
@@ -1720,7 +1745,7 @@ static fr_status autotune_impl(fr_mesh *m, const void *U, void *R, cudaStream_t 
         }
         float best = 1e30f;
         int bestv = gr.variant;
-        for (int v = 0; v < 3; v++) {
+        for (int v = 0; v < volume_shapes(m, b); v++) {
             if (hex_fused_phase<T>(b.p, 1, a, s, v)) return fail(FR_ECUDA, "autotune: volume launch failed");  // warm-up
             CU(cudaEventRecord(e0, s));
             for (int r = 0; r < 2; r++) hex_fused_phase<T>(b.p, 1, a, s, v);

@@ -1648,6 +1648,449 @@ __global__ void __launch_bounds__(256) k_tdivtconf(HexArgs<T> a)
 }
 
 // ---------------------------------------------------------------------------------------------
+// FP32 volume group, p = 3, several elements per CTA with register-resident line sweeps
+//
+// The same computation as k_fused_B<float, 3, ...> (flux anti-aliasing, affine elements, CUDA
+// cores), organised for the FP32 pipe: a CTA takes EPB elements at a time, and every sum-factorised
+// operator is applied by one thread to one whole field of one element from registers -- the
+// interpolation of field f (4^3 -> 5^3: x and y sweeps plane by plane, then z) and the projection
+// of transformed-flux component (alpha, d) (5^3 -> 4^3: first along d with the corrected derivative
+// folded in, Dh Pj, then along the other two directions with Pj; the 1D factors of the tensor
+// product commute). Every thread of a warp then applies the same operator entry at the same time, so
+// the coefficients are uniform constant-memory operands; shared memory only carries the
+// transpositions between a field-per-thread and a point-per-thread view (the pointwise flux), and
+// a CTA crosses about eleven barriers per EPB elements instead of about twenty per element.
+// Per element the shared workspace is one region of 2580 floats: the state and gradient (20 fields
+// at stride 65), the common solution, then the 20 fields at the 125 quadrature points (stride 129),
+// then the projected components; field strides of 1 modulo 32 keep a warp's (element, field)
+// threads on distinct banks.
+// ---------------------------------------------------------------------------------------------
+namespace b32 {
+constexpr int N = 4, M = 5, NU = 64, NF = 96, NQ = 125;
+constexpr int FS = 65;      // field stride of the solution-point fields
+constexpr int QS = 129;     // field stride of the quadrature-point fields
+constexpr int CO = 20 * FS; // common solution C^(f): 5 x 96
+constexpr int MO = CO + 5 * NF;   // low-Mach mass channel: 3 x 64 float-float values
+constexpr int ES = 20 * QS; // element stride (2580 = 20 mod 32)
+static_assert(MO + 3 * NU * 2 <= ES, "the mass channel fits below the quadrature-point fields' end");
+}
+
+// SPLIT: the interpolation of a field is shared by five threads (one per z quadrature level: the
+// z sweep of that level, then its y and x sweeps) and the projection of a component by four (one
+// per solution level along d), with the same multiply-adds in total and each operator row that
+// differs between the threads held in registers.
+template <int EPB, int NT, int MB, bool SPLIT = false>
+__global__ void __launch_bounds__(NT, MB) k_hex_B32(HexArgs<float> a)
+{
+    using namespace b32;
+    extern __shared__ __align__(16) float s_ws[];
+    __shared__ Geo<float> s_geo[EPB];
+    __shared__ Phys<float> s_ph[EPB];
+    __shared__ long long s_u0[EPB], s_f0[EPB];
+    __shared__ unsigned char s_diag[EPB];
+    __shared__ short s_list[EPB * NF];
+    __shared__ int s_cnt;
+    const HexOps<float> &op = OPS<float>(1);
+    const int tid = threadIdx.x;
+    for (long long e0 = (long long)blockIdx.x * EPB; e0 < a.ne; e0 += (long long)gridDim.x * EPB) {
+        const int nb = (int)((a.ne - e0) < EPB ? (a.ne - e0) : EPB);
+        if (tid < nb) {
+            const long long e = e0 + tid;
+            const Geo<float> g = a.geo[e];
+            s_geo[tid] = g;
+            s_ph[tid] = elem_phys(a, e);
+            s_u0[tid] = elem_u0(a, e, NU);
+            s_f0[tid] = elem_f0(a, e, NF);
+            s_diag[tid] = g.Ji[1] == 0.f && g.Ji[2] == 0.f && g.Ji[3] == 0.f && g.Ji[5] == 0.f && g.Ji[6] == 0.f &&
+                          g.Ji[7] == 0.f;
+        }
+        if (tid == 0) s_cnt = 0;
+        __syncthreads();
+        // 1. the state (deviations from the reference state in the low-Mach form), coalesced
+        for (int i = tid; i < nb * 5 * NU; i += NT) {
+            const int el = i / (5 * NU), r = i % (5 * NU), alpha = r / NU, z = r % NU;
+            const Phys<float> &ph = s_ph[el];
+            float v = a.U[s_u0[el] + r];
+            if (ph.dev) v -= alpha == 0 ? ph.rref : (alpha == 4 ? ph.eref : 0.f);
+            s_ws[el * ES + alpha * FS + z] = v;
+        }
+        // 2. con_u: common solution at the own flux points, (1/2 - beta) uL + (1/2 + beta) uR
+        for (int i = tid; i < nb * 5 * NF; i += NT) {
+            const int el = i / (5 * NF), r = i % (5 * NF), alpha = r / NF, s = r % NF;
+            const long long gf = s_f0[el] + s;
+            const uint32_t pc = a.partner[gf];
+            const bool isL = (pc & FR_LFLAG) != 0;
+            const float own = a.UF[alpha * a.nfpt + gf], oth = a.UF[alpha * a.nfpt + (pc & ~FR_LFLAG)];
+            const float beta = s_ph[el].beta;
+            s_ws[el * ES + CO + r] = (0.5f - beta) * (isL ? own : oth) + (0.5f + beta) * (isL ? oth : own);
+        }
+        __syncthreads();
+        // 3. corrected gradient along lines, q~ = Dh u + liftR C_R - liftL C_L, and J^-T on diagonal
+        //    metrics (the other elements take the full J^-T in a pass of their own below)
+        for (int i = tid; i < nb * 15 * N * N; i += NT) {
+            const int el = i / (15 * N * N), r = i % (15 * N * N), alpha = r / (3 * N * N), r2 = r % (3 * N * N);
+            const int d = r2 / (N * N), loc = r2 % (N * N);
+            int base, stride;
+            face_line<N>(2 * d, loc, base, stride);
+            float *w = s_ws + el * ES;
+            float u[N];
+#pragma unroll
+            for (int k = 0; k < N; k++) u[k] = w[alpha * FS + base + k * stride];
+            const float cL = w[CO + alpha * NF + 2 * d * N * N + loc], cR = w[CO + alpha * NF + (2 * d + 1) * N * N + loc];
+            const float sc = s_diag[el] ? s_geo[el].Ji[4 * d] : 1.f;
+#pragma unroll
+            for (int k = 0; k < N; k++) {
+                float v = op.liftR[k] * cR - op.liftL[k] * cL;
+#pragma unroll
+                for (int j = 0; j < N; j++) v += op.Dh[k][j] * u[j];
+                w[(5 + alpha * 3 + d) * FS + base + k * stride] = v * sc;
+            }
+        }
+        if (__syncthreads_or(tid < nb && !s_diag[tid])) {
+            for (int i = tid; i < nb * 5 * NU; i += NT) {
+                const int el = i / (5 * NU), r = i % (5 * NU), alpha = r / NU, z = r % NU;
+                if (s_diag[el]) continue;
+                const float *Ji = s_geo[el].Ji;
+                float *q = s_ws + el * ES + (5 + alpha * 3) * FS + z;
+                const float q0 = q[0], q1 = q[FS], q2 = q[2 * FS];
+#pragma unroll
+                for (int k = 0; k < 3; k++) q[k * FS] = Ji[k] * q0 + Ji[3 + k] * q1 + Ji[6 + k] * q2;
+            }
+            __syncthreads();
+        }
+        // 4. own-normal viscous flux at the own flux points on the side whose LDG weight is not zero
+        //    (compacted over the EPB elements so that whole warps work)
+        for (int i = tid; i < nb * NF; i += NT) {
+            const int el = i / NF, s = i % NF;
+            const long long gf = s_f0[el] + s;
+            const bool isL = (a.partner[gf] & FR_LFLAG) != 0;
+            const float wgt = isL ? 0.5f + s_ph[el].beta : 0.5f - s_ph[el].beta;
+            if (wgt == 0.f) {
+#pragma unroll
+                for (int k = 0; k < 4; k++) a.FV[k * a.nfpt + gf] = 0.f;
+            } else {
+                s_list[atomicAdd(&s_cnt, 1)] = (short)i;
+            }
+        }
+        __syncthreads();
+        const int nlist = s_cnt;
+        for (int li = tid; li < nlist; li += NT) {
+            const int i = s_list[li], el = i / NF, s = i % NF, f = s / (N * N);
+            int base, stride;
+            face_line<N>(f, s % (N * N), base, stride);
+            const float *l = (f & 1) ? op.lR : op.lL;
+            const float *w = s_ws + el * ES + base;
+            float uf[5], qf[5][3];
+#pragma unroll
+            for (int alpha = 0; alpha < 5; alpha++) {
+                float v = 0.f;
+#pragma unroll
+                for (int k = 0; k < N; k++) v += l[k] * w[alpha * FS + k * stride];
+                uf[alpha] = v;
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    float x = 0.f;
+#pragma unroll
+                    for (int k = 0; k < N; k++) x += l[k] * w[(5 + alpha * 3 + d) * FS + k * stride];
+                    qf[alpha][d] = x;
+                }
+            }
+            const Phys<float> &ph = s_ph[el];
+            if (ph.dev) { uf[0] += ph.rref; uf[4] += ph.eref; }
+            float n[3], mag;
+            face_nrm<float, float>(a.fnrm, e0 + el, f, n, mag);
+            float fvn[4];
+            viscous_normal_flux(ph, uf, qf, n, fvn);
+            const long long gf = s_f0[el] + s;
+#pragma unroll
+            for (int k = 0; k < 4; k++) a.FV[k * a.nfpt + gf] = fvn[k];
+        }
+        // 5. low-Mach form: the volume part of R~_rho in float-float (rho v lies in the solution
+        //    space: its L2 projection is itself), Dh applied along each direction at the solution points
+        if (s_ph[0].dev) {
+            const HexOpsFF &off = c_hexff[1];
+            for (int i = tid; i < nb * NU; i += NT) {
+                const int el = i / NU, z = i % NU;
+                const ff *cm = a.geo64[e0 + el].cm;
+                float *w = s_ws + el * ES;
+                ff *mf = reinterpret_cast<ff *>(w + MO);
+                const float m0 = w[FS + z], m1 = w[2 * FS + z], m2 = w[3 * FS + z];
+                if (s_diag[el]) {
+                    mf[z] = ff_mul_f(cm[0], m0);
+                    mf[NU + z] = ff_mul_f(cm[4], m1);
+                    mf[2 * NU + z] = ff_mul_f(cm[8], m2);
+                } else {
+#pragma unroll
+                    for (int d = 0; d < 3; d++)
+                        mf[d * NU + z] = ff_add(ff_add(ff_mul_f(cm[3 * d], m0), ff_mul_f(cm[3 * d + 1], m1)), ff_mul_f(cm[3 * d + 2], m2));
+                }
+            }
+            __syncthreads();
+            for (int i = tid; i < nb * NU; i += NT) {
+                const int el = i / NU, z = i % NU, x = z % N, y = (z / N) % N, k = z / (N * N);
+                const ff *mf = reinterpret_cast<const ff *>(s_ws + el * ES + MO);
+                ff v = ff_of(0.0f);
+#pragma unroll
+                for (int b = 0; b < N; b++) {
+                    v = ff_fma(off.Dh[x][b], mf[b + N * y + N * N * k], v);
+                    v = ff_fma(off.Dh[y][b], mf[NU + x + N * b + N * N * k], v);
+                    v = ff_fma(off.Dh[k][b], mf[2 * NU + x + N * y + N * N * b], v);
+                }
+                a.RL[s_u0[el] / FR_NV + z] = v;
+            }
+        }
+        // 6. uqpts + gradcoru_qpts: one thread per (element, field) interpolates the field to the
+        //    125 quadrature points from registers: the z sweep column by column (4 -> 5; every
+        //    input read), then, once every thread has read its inputs, the y and x sweeps plane by
+        //    plane straight into the quadrature-point layout over the consumed inputs
+        if constexpr (SPLIT) {
+            // x index i outermost: per i the z sweep of the x-line i at level qc, its y sweep, and
+            // the x sweep accumulated into the level's 25 outputs (i ascending, as a dense sum)
+            const bool itask = tid < nb * 5 * 20;
+            const int iel = tid / 100, ifld = (tid % 100) / 5, qc = tid % 5;
+            float out[M][M];   // [qa][qb]
+#pragma unroll
+            for (int qa = 0; qa < M; qa++)
+#pragma unroll
+                for (int qb = 0; qb < M; qb++) out[qa][qb] = 0.f;
+            if (itask) {
+                float bz[N];
+#pragma unroll
+                for (int k = 0; k < N; k++) bz[k] = op.B[qc][k];
+                const float *w = s_ws + iel * ES + ifld * FS;
+#pragma unroll 1
+                for (int i = 0; i < N; i++) {
+                    float zi[N];   // [j]
+#pragma unroll
+                    for (int j = 0; j < N; j++) {
+                        float v = 0.f;
+#pragma unroll
+                        for (int k = 0; k < N; k++) v += bz[k] * w[i + N * j + N * N * k];
+                        zi[j] = v;
+                    }
+#pragma unroll
+                    for (int qb = 0; qb < M; qb++) {
+                        float v = 0.f;
+#pragma unroll
+                        for (int j = 0; j < N; j++) v += op.B[qb][j] * zi[j];
+#pragma unroll
+                        for (int qa = 0; qa < M; qa++) out[qa][qb] += op.B[qa][i] * v;
+                    }
+                }
+            }
+            __syncthreads();
+            if (itask) {
+                float *w = s_ws + iel * ES + ifld * QS + M * M * qc;
+#pragma unroll
+                for (int qb = 0; qb < M; qb++)
+#pragma unroll
+                    for (int qa = 0; qa < M; qa++) w[qa + M * qb] = out[qa][qb];
+            }
+            __syncthreads();
+        } else {
+        float zt[N][N][M];   // [i][j][qc]
+            const bool itask = tid < nb * 20;
+            const int iel = tid / 20, ifld = tid % 20;
+            if (itask) {
+                const float *w = s_ws + iel * ES + ifld * FS;
+    #pragma unroll
+                for (int i = 0; i < N; i++)
+    #pragma unroll
+                    for (int j = 0; j < N; j++) {
+                        float u[N];
+    #pragma unroll
+                        for (int k = 0; k < N; k++) u[k] = w[i + N * j + N * N * k];
+    #pragma unroll
+                        for (int qc = 0; qc < M; qc++) {
+                            float v = 0.f;
+    #pragma unroll
+                            for (int k = 0; k < N; k++) v += op.B[qc][k] * u[k];
+                            zt[i][j][qc] = v;
+                        }
+                    }
+            }
+            __syncthreads();
+            if (itask) {
+                float *w = s_ws + iel * ES + ifld * QS;
+    #pragma unroll
+                for (int qc = 0; qc < M; qc++) {
+                    float yt[N][M];   // [i][qb]
+    #pragma unroll
+                    for (int i = 0; i < N; i++)
+    #pragma unroll
+                        for (int qb = 0; qb < M; qb++) {
+                            float v = 0.f;
+    #pragma unroll
+                            for (int j = 0; j < N; j++) v += op.B[qb][j] * zt[i][j][qc];
+                            yt[i][qb] = v;
+                        }
+    #pragma unroll
+                    for (int qb = 0; qb < M; qb++)
+    #pragma unroll
+                        for (int qa = 0; qa < M; qa++) {
+                            float v = 0.f;
+    #pragma unroll
+                            for (int i = 0; i < N; i++) v += op.B[qa][i] * yt[i][qb];
+                            w[qa + M * qb + M * M * qc] = v;
+                        }
+                }
+            }
+            __syncthreads();
+        }
+        // 7. tdisf: transformed flux at each quadrature point, in place (fields alpha 3 + d)
+        bool ok = true;
+        for (int i = tid; i < nb * NQ; i += NT) {
+            const int el = i / NQ, q = i % NQ;
+            float *w = s_ws + el * ES + q;
+            const Phys<float> &ph = s_ph[el];
+            const Geo<float> &g = s_geo[el];
+            float u[5], gq[5][3], f[3][5];
+#pragma unroll
+            for (int alpha = 0; alpha < 5; alpha++) {
+                u[alpha] = w[alpha * QS];
+#pragma unroll
+                for (int d = 0; d < 3; d++) gq[alpha][d] = w[(5 + alpha * 3 + d) * QS];
+            }
+            if (ph.dev) ok &= total_flux_dev(ph, u, gq, f);
+            else ok &= total_flux(ph, u, gq, f);
+            if (s_diag[el]) {
+                const float s0 = g.det * g.Ji[0], s1 = g.det * g.Ji[4], s2 = g.det * g.Ji[8];
+#pragma unroll
+                for (int alpha = 0; alpha < 5; alpha++) {
+                    w[(alpha * 3 + 0) * QS] = s0 * f[0][alpha];
+                    w[(alpha * 3 + 1) * QS] = s1 * f[1][alpha];
+                    w[(alpha * 3 + 2) * QS] = s2 * f[2][alpha];
+                }
+            } else {
+#pragma unroll
+                for (int alpha = 0; alpha < 5; alpha++)
+#pragma unroll
+                    for (int d = 0; d < 3; d++)
+                        w[(alpha * 3 + d) * QS] = g.det * (g.Ji[3 * d] * f[0][alpha] + g.Ji[3 * d + 1] * f[1][alpha] + g.Ji[3 * d + 2] * f[2][alpha]);
+            }
+        }
+        flag_status(a.status, ok);
+        __syncthreads();
+        // 8. tdivtpcorf: one thread per (element, alpha, d) projects component d of the flux of
+        //    variable alpha, first along d with Dh Pj (projection and corrected derivative), then
+        //    along the other two directions p < r with Pj, into solution-point component slots
+        if constexpr (SPLIT) {
+            // four threads per component: thread k2 produces the solution level k2 along d
+            const bool ptask = tid < nb * 60;
+            const int pel = tid / 60, pc = (tid % 60) / 4, k2 = tid % 4, pd = pc % 3;
+            const int qd = pd == 0 ? 1 : (pd == 1 ? M : M * M), qp = pd == 0 ? M : 1, qr = pd == 2 ? M : M * M;
+            const int zd = pd == 0 ? 1 : (pd == 1 ? N : N * N), zp = pd == 0 ? N : 1, zr = pd == 2 ? N : N * N;
+            // r index outermost: per ir the d sweep of the slice, its p sweep, and the r sweep
+            // accumulated into the 16 outputs (ir ascending, as a dense sum)
+            float out[N][N];   // [jp][jr]
+#pragma unroll
+            for (int jp = 0; jp < N; jp++)
+#pragma unroll
+                for (int jr = 0; jr < N; jr++) out[jp][jr] = 0.f;
+            if (ptask) {
+                float dp[M];
+#pragma unroll
+                for (int m = 0; m < M; m++) dp[m] = op.DP[k2][m];
+                const float *w = s_ws + pel * ES + pc * QS;
+#pragma unroll 1
+                for (int ir = 0; ir < M; ir++) {
+                    const float *wr = w + ir * qr;
+                    float pt[M];   // [ip]
+#pragma unroll
+                    for (int ip = 0; ip < M; ip++) {
+                        float v = 0.f;
+#pragma unroll
+                        for (int m = 0; m < M; m++) v += dp[m] * wr[m * qd + ip * qp];
+                        pt[ip] = v;
+                    }
+#pragma unroll
+                    for (int jp = 0; jp < N; jp++) {
+                        float v = 0.f;
+#pragma unroll
+                        for (int ip = 0; ip < M; ip++) v += op.Pj[jp][ip] * pt[ip];
+#pragma unroll
+                        for (int jr = 0; jr < N; jr++) out[jp][jr] += op.Pj[jr][ir] * v;
+                    }
+                }
+            }
+            __syncthreads();
+            if (ptask) {
+                float *w = s_ws + pel * ES + pc * FS + k2 * zd;
+#pragma unroll
+                for (int jp = 0; jp < N; jp++)
+#pragma unroll
+                    for (int jr = 0; jr < N; jr++) w[jp * zp + jr * zr] = out[jp][jr];
+            }
+            __syncthreads();
+        } else {
+        const bool ptask = tid < nb * 15;
+            const int pel = tid / 15, pc = tid % 15, pd = pc % 3;
+            // quadrature strides (1, M, M^2) and solution strides (1, N, N^2) of d, p and r
+            const int qd = pd == 0 ? 1 : (pd == 1 ? M : M * M), qp = pd == 0 ? M : 1, qr = pd == 2 ? M : M * M;
+            const int zd = pd == 0 ? 1 : (pd == 1 ? N : N * N), zp = pd == 0 ? N : 1, zr = pd == 2 ? N : N * N;
+            // the r sweep accumulates slice by slice (ir ascending, as a dense sum would), so only the
+            // 64 outputs, one slice and one column stay in registers
+            float acc[N][N][N];   // [jp][jr][k along d]
+    #pragma unroll
+            for (int jp = 0; jp < N; jp++)
+    #pragma unroll
+                for (int jr = 0; jr < N; jr++)
+    #pragma unroll
+                    for (int k = 0; k < N; k++) acc[jp][jr][k] = 0.f;
+            if (ptask) {
+                const float *w = s_ws + pel * ES + pc * QS;
+    #pragma unroll 1
+                for (int ir = 0; ir < M; ir++) {
+                    const float *wr = w + ir * qr;
+                    float pt[M][N];   // [ip][k]
+    #pragma unroll
+                    for (int ip = 0; ip < M; ip++) {
+                        float c[M];
+    #pragma unroll
+                        for (int m = 0; m < M; m++) c[m] = wr[m * qd + ip * qp];
+    #pragma unroll
+                        for (int k = 0; k < N; k++) {
+                            float v = 0.f;
+    #pragma unroll
+                            for (int m = 0; m < M; m++) v += op.DP[k][m] * c[m];
+                            pt[ip][k] = v;
+                        }
+                    }
+    #pragma unroll
+                    for (int jp = 0; jp < N; jp++)
+    #pragma unroll
+                        for (int k = 0; k < N; k++) {
+                            float v = 0.f;
+    #pragma unroll
+                            for (int ip = 0; ip < M; ip++) v += op.Pj[jp][ip] * pt[ip][k];
+    #pragma unroll
+                            for (int jr = 0; jr < N; jr++) acc[jp][jr][k] += op.Pj[jr][ir] * v;
+                        }
+                }
+            }
+            __syncthreads();
+            if (ptask) {
+                float *w = s_ws + pel * ES + pc * FS;
+    #pragma unroll
+                for (int jp = 0; jp < N; jp++)
+    #pragma unroll
+                    for (int jr = 0; jr < N; jr++)
+    #pragma unroll
+                        for (int k = 0; k < N; k++) w[k * zd + jp * zp + jr * zr] = acc[jp][jr][k];
+            }
+            __syncthreads();
+        }
+        // 9. R~[alpha] = sum over d of the projected components, written to R (finished in phase C)
+        for (int i = tid; i < nb * 5 * NU; i += NT) {
+            const int el = i / (5 * NU), r = i % (5 * NU), alpha = r / NU, z = r % NU;
+            const float *w = s_ws + el * ES + alpha * 3 * FS + z;
+            a.R[s_u0[el] + r] = (w[0] + w[FS]) + w[2 * FS];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------------------------
 static int grid_for(long long work, int threads)
@@ -1712,6 +2155,25 @@ static int launch_B_tc(const HexArgs<float> &a, cudaStream_t s)
     return 0;
 }
 
+template <int EPB, int NT, int MB, bool SPLIT = false>
+static int launch_B32(const HexArgs<float> &a, cudaStream_t s)
+{
+    const size_t smem = (size_t)EPB * b32::ES * sizeof(float);
+    static int occ = -1, nsm = 0;
+    if (occ < 0) {
+        cudaFuncSetAttribute(k_hex_B32<EPB, NT, MB, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return -1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hex_B32<EPB, NT, MB, SPLIT>, NT, smem) != cudaSuccess || occ < 1)
+            return -4;
+    }
+    long long g = (a.ne + EPB - 1) / EPB;   // persistent: at most the resident CTAs
+    if (g > (long long)nsm * occ) g = (long long)nsm * occ;
+    k_hex_B32<EPB, NT, MB, SPLIT><<<(int)g, NT, smem, s>>>(a);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
 template <typename T, int P>
 static int fused_phase(int phase, const HexArgs<T> &a, cudaStream_t s, int variant)
 {
@@ -1745,6 +2207,13 @@ static int fused_phase(int phase, const HexArgs<T> &a, cudaStream_t s, int varia
             else if (variant == 2) launch_B<T, P, 256, false>(a, s);
             else launch_B<T, P, 128, false>(a, s);
             return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+        }
+        if constexpr (std::is_same<T, float>::value && P == 3) {
+            // several elements per CTA, register-resident line sweeps: 3 = one CTA of 8 elements
+            // per SM (all 255 registers), 4 = two per SM (registers capped at 204)
+            if (variant == 3) return launch_B32<8, 160, 1>(a, s);
+            if (variant == 4) return launch_B32<8, 160, 2>(a, s);
+            if (variant == 5) return launch_B32<2, 224, 3, true>(a, s);
         }
         if (variant == 0) launch_B<T, P, 64>(a, s);
         else if (variant == 2) launch_B<T, P, 256>(a, s);

@@ -18,6 +18,9 @@ FR_OK, FR_EINVAL, FR_ENOMEM, FR_ECUDA, FR_EMESH, FR_ETIMEOUT, FR_ENONPHYS, FR_EU
 STATUS_NAMES = ["FR_OK", "FR_EINVAL", "FR_ENOMEM", "FR_ECUDA", "FR_EMESH", "FR_ETIMEOUT", "FR_ENONPHYS",
                 "FR_EUNSUPPORTED"]
 PRECISIONS = {"fp64": 0, "fp32": 1, "mixed_bf16": 2, "mixed_fp16": 3}
+# volume-kernel launch shapes (fr_autotune, fr_set_volume_shape): threads per element, or elements per
+# CTA with register-resident sweeps and the CTAs per SM
+SHAPES = (64, 128, 256, "8/CTA x1", "8/CTA x2", "2/CTA split")
 FORMS = {"fused": 0, "unfused": 1}
 
 
@@ -74,6 +77,7 @@ def lib():
             "fr_set_hex_tensor_cores": ([vp, C.c_int], C.c_int),
             "fr_set_dense_tensor_cores": ([vp, C.c_int], C.c_int),
             "fr_autotune": ([vp, vp, vp, C.POINTER(C.c_int), C.c_int, vp], C.c_int),
+            "fr_set_volume_shape": ([vp, C.c_int], C.c_int),
             "fr_kernel_times": ([vp, C.POINTER(C.c_double), llp, C.c_int], C.c_int),
             "fr_probe_fma": ([dp, vp], C.c_int),
             "fr_partition_plan": ([C.POINTER(MeshDesc), C.POINTER(Params), C.c_int, C.c_int, llp, llp, llp, llp,
@@ -286,7 +290,11 @@ class FRMesh:
         out = (C.c_int * 16)(*([-1] * 16))
         _check(lib().fr_autotune(self.h, C.c_void_p(U.data_ptr()), C.c_void_p(R.data_ptr()), out, 16,
                                  _stream_ptr(stream)))
-        return [(64, 128, 256)[v] for v in out if v >= 0]
+        return [SHAPES[v] for v in out if v >= 0]
+
+    def set_volume_shape(self, shape: int):
+        """fr_set_volume_shape: the volume-kernel launch shape of every hexahedral group (0..4)."""
+        _check(lib().fr_set_volume_shape(self.h, shape))
 
     def set_graph(self, on: bool):
         _check(lib().fr_set_graph(self.h, int(on)))
