@@ -70,7 +70,10 @@ typedef enum {
     FR_ETIMEOUT = 5,      /* a bounded device wait gave up (the tensor-core completion wait of the
                            * mixed forms; latched on the device like FR_ENONPHYS) */
     FR_ENONPHYS = 6,      /* non-physical state met on the device */
-    FR_EUNSUPPORTED = 7   /* valid request outside what this build implements */
+    FR_EUNSUPPORTED = 7,  /* valid request outside what this build implements */
+    FR_EBOUNDS = 8        /* the bounds-checking build (compiled with FR_DEBUG_BOUNDS) met an element
+                           * offset or partner index outside the handle's arrays; the access was
+                           * skipped (latched on the device like FR_ENONPHYS) */
 } fr_status;
 
 typedef enum {

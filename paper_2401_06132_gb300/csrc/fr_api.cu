@@ -1503,6 +1503,7 @@ static HexArgs<T> make_args(fr_mesh *m, const Block &b, const void *U, void *R)
     a.Rt = reinterpret_cast<T *>(m->d_Rt);
     a.status = m->d_status;
     a.dbg_wait0 = (m->debug & 2) ? 1 : 0;
+    a.nU = m->nU;
     a.tcmode = m->prec == FR_MIXED_FP16 ? 1 : (m->prec == FR_MIXED_BF16 ? 2 : 0);
     if (b.type == 0 && !m->hex_tc) a.tcmode = 0;
     if ((b.type == 2 || b.type == 3) && !m->dense_tc) a.tcmode = 0;
@@ -1550,6 +1551,7 @@ static fr_status ensure_unfused(fr_mesh *m)
 
 static fr_status status_error(int v)
 {
+    if (v & 4) return fail(FR_EBOUNDS, "an index check of the bounds-checking build failed on the device");
     if (v & 2) return fail(FR_ETIMEOUT, "a bounded tensor-core completion wait gave up on the device");
     return fail(FR_ENONPHYS, "non-physical state met on the device");
 }

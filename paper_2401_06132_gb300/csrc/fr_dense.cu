@@ -98,6 +98,11 @@ __global__ void __launch_bounds__(OPS::NF * EPB) k_dense_disu(HexArgs<T> a, cons
     for (long long g = blockIdx.x; g < ng; g += gridDim.x) {
         const long long e0 = g * EPB;
         const int nel = (int)(a.ne - e0 < EPB ? a.ne - e0 : EPB);
+        {
+            bool blk_ok = true;
+            for (int k = 0; k < nel; k++) blk_ok = blk_ok && fr_elem_ok(a, e0 + k, NU, NF);
+            if (!blk_ok) continue;
+        }
         for (int i = threadIdx.x; i < nel * FR_NV * NU; i += NTH) {
             const int l = i / (FR_NV * NU), r = i % (FR_NV * NU), alpha = r / NU;
             const long long e = e0 + l;
@@ -222,6 +227,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? (TCM == 0 ? 8 : 6) : 0) 
     if constexpr (NUS > NU)
         for (int it = threadIdx.x; it < 20 * (NUS - NU); it += NTH) s_u[(it / (NUS - NU)) * NUS + NU + it % (NUS - NU)] = T(0);
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
+        if (!fr_elem_ok(a, e, NU, NF)) continue;
         const Geo<T> g = a.geo[e];
         const Phys<T> ph = elem_phys(a, e);
         const T *U = a.U + elem_u0(a, e, NU);
@@ -264,7 +270,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? (TCM == 0 ? 8 : 6) : 0) 
             const int alpha = it / NF, s = it % NF;
             const uint32_t pc = a.partner[gf0 + s];
             const bool isL = (pc & FR_LFLAG) != 0;
-            const long long pg = pc & ~FR_LFLAG;
+            const long long pg = fr_partner(a, pc, gf0 + s);
             const T own = a.UF[alpha * a.nfpt + gf0 + s], oth = a.UF[alpha * a.nfpt + pg];
             const T uL = isL ? own : oth, uR = isL ? oth : own;
             s_c[it] = (T(0.5) - ph.beta) * uL + (T(0.5) + ph.beta) * uR;
@@ -564,6 +570,11 @@ __global__ void __launch_bounds__(OPS::NF * EPB) k_dense_C(HexArgs<T> a, const O
     for (long long g = blockIdx.x; g < ng; g += gridDim.x) {
         const long long e0 = g * EPB;
         const int nel = (int)(a.ne - e0 < EPB ? a.ne - e0 : EPB);
+        {
+            bool blk_ok = true;
+            for (int k = 0; k < nel; k++) blk_ok = blk_ok && fr_elem_ok(a, e0 + k, NU, NF);
+            if (!blk_ok) continue;
+        }
         bool ok = true;
         if (el < nel) {
             const long long e = e0 + el;
@@ -571,7 +582,7 @@ __global__ void __launch_bounds__(OPS::NF * EPB) k_dense_C(HexArgs<T> a, const O
             const long long og = elem_f0(a, e, NF) + s;
             const uint32_t pc = a.partner[og];
             const bool isL = (pc & FR_LFLAG) != 0;
-            const long long pg = pc & ~FR_LFLAG;
+            const long long pg = fr_partner(a, pc, og);
             T uo[5], up[5], fvo[4], fvp[4];
 #pragma unroll
             for (int k = 0; k < 5; k++) { uo[k] = a.UF[k * a.nfpt + og]; up[k] = a.UF[k * a.nfpt + pg]; }

@@ -186,6 +186,11 @@ __global__ void __launch_bounds__(NT) k_disu_blk(HexArgs<T> a)
     const HexOps<T> &op = OPS<T>(P - 2);
     for (long long e0 = (long long)blockIdx.x * EB; e0 < a.ne; e0 += (long long)gridDim.x * EB) {
         const int nb = (int)((a.ne - e0) < EB ? (a.ne - e0) : EB);
+        {
+            bool blk_ok = true;
+            for (int k = 0; k < nb; k++) blk_ok = blk_ok && fr_elem_ok(a, e0 + k, NU, NF);
+            if (!blk_ok) continue;
+        }
         for (int i = threadIdx.x; i < nb * FR_NV * NU; i += NT) {
             const int el = i / (FR_NV * NU), r = i % (FR_NV * NU);
             T v = a.eu0 == nullptr ? a.U[a.u0 + e0 * FR_NV * NU + i] : a.U[a.eu0[e0 + el] + r];
@@ -668,6 +673,8 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
                 }
             }
         }
+        // (after any prefetch of this element has landed: nothing is left in flight when it is skipped)
+        if (!fr_elem_ok(a, e, NU, NF)) continue;
         for (int it = threadIdx.x; it < 5 * NU; it += NT) {
             T v = usrc[it];
             if constexpr (std::is_same<T, float>::value) {
@@ -682,7 +689,7 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
             const int alpha = it / NF, s = it % NF;
             const uint32_t pc = a.partner[gf0 + s];
             const bool isL = (pc & FR_LFLAG) != 0;
-            const long long pg = pc & ~FR_LFLAG;
+            const long long pg = fr_partner(a, pc, gf0 + s);
             const T own = a.UF[alpha * a.nfpt + gf0 + s], oth = a.UF[alpha * a.nfpt + pg];
             const T uL = isL ? own : oth, uR = isL ? oth : own;
             s_c[it] = (T(0.5) - ph.beta) * uL + (T(0.5) + ph.beta) * uR;
@@ -710,7 +717,14 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
         if constexpr (TMA_U) {
             // prefetch the next element's state into s_c
             const long long en = e + gridDim.x;
-            if (en < a.ne) {
+            bool en_ok = en < a.ne;
+#ifdef FR_DEBUG_BOUNDS
+            if (en_ok) {   // the bounds-checking build prefetches only elements inside U
+                const long long un = elem_u0(a, en, NU);
+                en_ok = un >= 0 && un + (long long)FR_NV * NU <= a.nU;
+            }
+#endif
+            if (en_ok) {
                 const T *Un = a.U + elem_u0(a, en, NU);
                 if ((reinterpret_cast<uintptr_t>(Un) & 15) == 0) {
                     if (threadIdx.x == 0) tc::bulk_g2s(s_c, Un, 5 * NU * sizeof(T), &s_ubar);
@@ -1129,6 +1143,7 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
     __shared__ ff s_dff[std::is_same<T, float>::value ? NF : 1];   // low-Mach form: transformed mass flux
     const HexOps<T> &op = OPS<T>(P - 2);
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
+        if (!fr_elem_ok(a, e, (P + 1) * (P + 1) * (P + 1), 6 * (P + 1) * (P + 1))) continue;
         const Geo<T> g = a.geo[e];
         const Phys<T> ph = elem_phys(a, e);
         bool dev = false;
@@ -1139,7 +1154,7 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
             const int f = s / (N * N);
             const uint32_t pc = a.partner[gf0 + s];
             const bool isL = (pc & FR_LFLAG) != 0;
-            const long long pg = pc & ~FR_LFLAG, og = gf0 + s;
+            const long long og = gf0 + s, pg = fr_partner(a, pc, og);
             T uo[5], up[5], fvo[4], fvp[4];
 #pragma unroll
             for (int k = 0; k < 5; k++) { uo[k] = a.UF[k * a.nfpt + og]; up[k] = a.UF[k * a.nfpt + pg]; }
@@ -1279,6 +1294,7 @@ __global__ void __launch_bounds__(NT) k_surf_lift(HexArgs<T> a)
     __shared__ T s_d[5 * NF];
     const HexOps<T> &op = OPS<T>(P - 2);
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
+        if (!fr_elem_ok(a, e, (P + 1) * (P + 1) * (P + 1), 6 * (P + 1) * (P + 1))) continue;
         const Geo<T> g = a.geo[e];
         for (int it = threadIdx.x; it < 5 * NQF; it += NT) {
             const int alpha = it / NQF, s = it % NQF;
@@ -1332,7 +1348,7 @@ __global__ void __launch_bounds__(128) k_pair_flux(HexArgs<T> a)
         const long long e = code >> 8;
         const int s = code & 255, f = s / (N * N);
         const long long gl = elem_f0(a, e, NF) + s;
-        const long long gr = a.partner[gl] & ~FR_LFLAG;
+        const long long gr = fr_partner(a, a.partner[gl], gl);
         const Phys<T> ph = elem_phys(a, e);
         T uL[5], uR[5], fvL[4], fvR[4];
 #pragma unroll
@@ -1361,12 +1377,13 @@ __global__ void __launch_bounds__(NT) k_lift(HexArgs<T> a)
     __shared__ T s_d[5 * NF];
     const HexOps<T> &op = OPS<T>(P - 2);
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
+        if (!fr_elem_ok(a, e, (P + 1) * (P + 1) * (P + 1), 6 * (P + 1) * (P + 1))) continue;
         const Geo<T> g = a.geo[e];
         const long long gf0 = elem_f0(a, e, NF);
         for (int s = threadIdx.x; s < NF; s += NT) {
             const uint32_t pc = a.partner[gf0 + s];
             const bool isL = (pc & FR_LFLAG) != 0;
-            const long long src = isL ? gf0 + s : (long long)(pc & ~FR_LFLAG);
+            const long long src = isL ? gf0 + s : fr_partner(a, pc, gf0 + s);
             const T mag = CURV ? a.mfn[(e * NF + s) * 4 + 3] : a.fnrm[(e * 6 + s / (N * N)) * 4 + 3];
             const T sc = isL ? mag : -mag;
 #pragma unroll
@@ -1405,7 +1422,7 @@ __global__ void __launch_bounds__(256) k_con_u(HexArgs<T> a)
         const long long gl = a.f0 + it;
         const uint32_t pc = a.partner[gl];
         if (!(pc & FR_LFLAG)) continue;
-        const long long gr = pc & ~FR_LFLAG;
+        const long long gr = fr_partner(a, pc, gl);
 #pragma unroll
         for (int k = 0; k < 5; k++) {
             const T c = (T(0.5) - a.ph.beta) * a.UF[k * a.nfpt + gl] + (T(0.5) + a.ph.beta) * a.UF[k * a.nfpt + gr];
@@ -1497,6 +1514,7 @@ __global__ void __launch_bounds__(NT) k_qpts(HexArgs<T> a)
     __shared__ T s_src[5 * NU], s_t1[5 * M * N * N], s_t2[5 * M * M * N], s_dst[5 * NQ];
     const HexOps<T> &op = OPS<T>(P - 2);
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
+        if (!fr_elem_ok(a, e, (P + 1) * (P + 1) * (P + 1), 6 * (P + 1) * (P + 1))) continue;
         for (int c = 0; c < NFLD / 5; c++) {
             const T *src = (NFLD == 5) ? a.U + a.u0 + e * 5 * NU : a.Qu + (e * 15 + 5 * c) * NU;
             T *dst = (NFLD == 5) ? a.UQ + e * 5 * NQ : a.QQ + (e * 15 + 5 * c) * NQ;
@@ -1555,6 +1573,7 @@ __global__ void __launch_bounds__(NT) k_tdivtpcorf(HexArgs<T> a)
     __shared__ T s_src[5 * NQ], s_t1[5 * M * N * N], s_t2[5 * M * M * N], s_F[15 * NU];
     const HexOps<T> &op = OPS<T>(P - 2);
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
+        if (!fr_elem_ok(a, e, (P + 1) * (P + 1) * (P + 1), 6 * (P + 1) * (P + 1))) continue;
         for (int c = 0; c < 3; c++) {
             const T *src = a.QQ + (e * 15 + 5 * c) * NQ;
             for (int it = threadIdx.x; it < 5 * NQ; it += NT) s_src[it] = src[it];
@@ -1589,7 +1608,7 @@ __global__ void __launch_bounds__(128) k_comm_flux(HexArgs<T> a)
         const long long gl = a.f0 + it;
         const uint32_t pc = a.partner[gl];
         if (!(pc & FR_LFLAG)) continue;
-        const long long gr = pc & ~FR_LFLAG;
+        const long long gr = fr_partner(a, pc, gl);
         const long long e = it / NF;
         const int f = (int)(it % NF) / (N * N);
         T uL[5], uR[5], qL[5][3], qR[5][3];
@@ -1694,6 +1713,11 @@ __global__ void __launch_bounds__(NT, MB) k_hex_B32(HexArgs<float> a)
     const int tid = threadIdx.x;
     for (long long e0 = (long long)blockIdx.x * EPB; e0 < a.ne; e0 += (long long)gridDim.x * EPB) {
         const int nb = (int)((a.ne - e0) < EPB ? (a.ne - e0) : EPB);
+        {
+            bool blk_ok = true;
+            for (int k = 0; k < nb; k++) blk_ok = blk_ok && fr_elem_ok(a, e0 + k, NU, NF);
+            if (!blk_ok) continue;
+        }
         if (tid < nb) {
             const long long e = e0 + tid;
             const Geo<float> g = a.geo[e];
@@ -1720,7 +1744,7 @@ __global__ void __launch_bounds__(NT, MB) k_hex_B32(HexArgs<float> a)
             const long long gf = s_f0[el] + s;
             const uint32_t pc = a.partner[gf];
             const bool isL = (pc & FR_LFLAG) != 0;
-            const float own = a.UF[alpha * a.nfpt + gf], oth = a.UF[alpha * a.nfpt + (pc & ~FR_LFLAG)];
+            const float own = a.UF[alpha * a.nfpt + gf], oth = a.UF[alpha * a.nfpt + fr_partner(a, pc, gf)];
             const float beta = s_ph[el].beta;
             s_ws[el * ES + CO + r] = (0.5f - beta) * (isL ? own : oth) + (0.5f + beta) * (isL ? oth : own);
         }

@@ -285,6 +285,7 @@ struct HexArgs {
     // Debug: the first bounded wait of every CTA (tensor-core completion or state prefetch) gives up
     // at once, so that the FR_ETIMEOUT path runs without any fault; the drain wait keeps its bound.
     int dbg_wait0;
+    long long nU;             // values of U and R in the handle (index checks of the bounds-checking build)
 };
 
 #ifdef __CUDACC__
@@ -319,6 +320,41 @@ template <typename T>
 __device__ __forceinline__ Phys<T> elem_phys(const HexArgs<T> &a, long long e)
 {
     return a.eph ? a.phtab[a.eph[e]] : a.ph;
+}
+
+// Index checks of the bounds-checking build (compiled with FR_DEBUG_BOUNDS; a release build compiles
+// them away). A failed check sets bit 2 of the status word (reported as FR_EBOUNDS) and the access is
+// redirected or skipped, so the check itself never touches memory out of bounds.
+// The partner flux point of partner code pc (own: this point's index, used if the partner is outside
+// the handle's face arrays).
+template <typename T>
+__device__ __forceinline__ long long fr_partner(const HexArgs<T> &a, uint32_t pc, long long own)
+{
+    const long long pg = pc & ~FR_LFLAG;
+#ifdef FR_DEBUG_BOUNDS
+    if (pg >= a.nfpt) {
+        atomicOr(a.status, 4);
+        return own;
+    }
+#endif
+    return pg;
+}
+
+// Element e's values and flux points lie inside U/R and the face arrays (call with every thread of
+// the CTA; the first thread reports a failure).
+template <typename T>
+__device__ __forceinline__ bool fr_elem_ok(const HexArgs<T> &a, long long e, int nu, int nf)
+{
+#ifdef FR_DEBUG_BOUNDS
+    const long long u0 = elem_u0(a, e, nu), f0 = elem_f0(a, e, nf);
+    if (u0 < 0 || u0 + (long long)FR_NV * nu > a.nU || f0 < 0 || f0 + nf > a.nfpt) {
+        if (threadIdx.x == 0) atomicOr(a.status, 4);
+        return false;
+    }
+#else
+    (void)a; (void)e; (void)nu; (void)nf;
+#endif
+    return true;
 }
 #endif
 

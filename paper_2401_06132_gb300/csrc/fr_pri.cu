@@ -150,6 +150,15 @@ __global__ void __launch_bounds__(256) k_pri_disu(HexArgs<T> a, const PriOps<T> 
         // one thread per (element, flux point), all five variables
         const int s = (int)(it % NF);
         const long long e = it / NF;
+#ifdef FR_DEBUG_BOUNDS
+        {
+            const long long u0 = elem_u0(a, e, NU), f0 = elem_f0(a, e, NF);
+            if (u0 < 0 || u0 + (long long)FR_NV * NU > a.nU || f0 < 0 || f0 + NF > a.nfpt) {
+                atomicOr(a.status, 4);
+                continue;
+            }
+        }
+#endif
         const T *u = a.U + elem_u0(a, e, NU);
         const long long fo = elem_f0(a, e, NF) + s;
         if constexpr (F32) {
@@ -323,6 +332,7 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
         tmem = *s_tmem;
     }
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
+        if (!fr_elem_ok(a, e, NU, NF)) continue;
         const Geo<T> g = a.geo[e];
         const Phys<T> ph = elem_phys(a, e);
         const T *U = a.U + elem_u0(a, e, NU);
@@ -339,7 +349,7 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
             const int alpha = it / NF, s = it % NF;
             const uint32_t pc = a.partner[gf0 + s];
             const bool isL = (pc & FR_LFLAG) != 0;
-            const long long pg = pc & ~FR_LFLAG;
+            const long long pg = fr_partner(a, pc, gf0 + s);
             const T own = a.UF[alpha * a.nfpt + gf0 + s], oth = a.UF[alpha * a.nfpt + pg];
             const T uL = isL ? own : oth, uR = isL ? oth : own;
             s_c[it] = (T(0.5) - ph.beta) * uL + (T(0.5) + ph.beta) * uR;
@@ -609,6 +619,7 @@ __global__ void __launch_bounds__(NTH) k_pri_C(HexArgs<T> a, const PriOps<T> *go
     load_ops<T, NTH>(gops, op);
     __syncthreads();
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
+        if (!fr_elem_ok(a, e, NU, NF)) continue;
         const Geo<T> g = a.geo[e];
         const Phys<T> ph = elem_phys(a, e);
         const long long gf0 = elem_f0(a, e, NF);
@@ -618,7 +629,7 @@ __global__ void __launch_bounds__(NTH) k_pri_C(HexArgs<T> a, const PriOps<T> *go
         for (int s = threadIdx.x; s < NF; s += NTH) {
             const uint32_t pc = a.partner[gf0 + s];
             const bool isL = (pc & FR_LFLAG) != 0;
-            const long long pg = pc & ~FR_LFLAG, og = gf0 + s;
+            const long long og = gf0 + s, pg = fr_partner(a, pc, og);
             T uo[5], up[5], fvo[4], fvp[4];
 #pragma unroll
             for (int k = 0; k < 5; k++) { uo[k] = a.UF[k * a.nfpt + og]; up[k] = a.UF[k * a.nfpt + pg]; }

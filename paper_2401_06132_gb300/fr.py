@@ -12,11 +12,12 @@ from typing import Sequence
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libfrgb300.so")
+# FR_LIBRARY=bounds selects the bounds-checking build (libfrgb300_bounds.so, build(variant="bounds"))
+LIB_PATH = os.path.join(HERE, "libfrgb300_bounds.so" if os.environ.get("FR_LIBRARY") == "bounds" else "libfrgb300.so")
 
-FR_OK, FR_EINVAL, FR_ENOMEM, FR_ECUDA, FR_EMESH, FR_ETIMEOUT, FR_ENONPHYS, FR_EUNSUPPORTED = range(8)
+FR_OK, FR_EINVAL, FR_ENOMEM, FR_ECUDA, FR_EMESH, FR_ETIMEOUT, FR_ENONPHYS, FR_EUNSUPPORTED, FR_EBOUNDS = range(9)
 STATUS_NAMES = ["FR_OK", "FR_EINVAL", "FR_ENOMEM", "FR_ECUDA", "FR_EMESH", "FR_ETIMEOUT", "FR_ENONPHYS",
-                "FR_EUNSUPPORTED"]
+                "FR_EUNSUPPORTED", "FR_EBOUNDS"]
 PRECISIONS = {"fp64": 0, "fp32": 1, "mixed_bf16": 2, "mixed_fp16": 3}
 # volume-kernel launch shapes (fr_autotune, fr_set_volume_shape): threads per element, or elements per
 # CTA with register-resident sweeps and the CTAs per SM
@@ -26,7 +27,7 @@ FORMS = {"fused": 0, "unfused": 1}
 
 class FRError(RuntimeError):
     def __init__(self, status, msg):
-        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
         self.status = status
 
 
