@@ -1084,8 +1084,10 @@ static fr_status finish_create(fr_mesh *m, std::vector<uint32_t> &partner, fr_me
         if (!st && cudaMemcpy(m->d_priops64, &pff, sizeof(pff), cudaMemcpyHostToDevice) != cudaSuccess)
             st = fail(FR_ECUDA, "prism operator upload failed");
     }
-    if (!st && m->lowmach && m->has_tet) st = upload_dense_ff<frb::Tet3D, TetOps<float>>(m, m->tet, &m->d_tetops64);
-    if (!st && m->lowmach && m->has_pyr) st = upload_dense_ff<frb::Pyr3D, PyrOps<float>>(m, m->pyr, &m->d_pyrops64);
+    // float-float dense tables: the compensated face values of every reduced precision, and the
+    // low-Mach form's mass channel
+    if (!st && m->prec != FR_FP64 && m->has_tet) st = upload_dense_ff<frb::Tet3D, TetOps<float>>(m, m->tet, &m->d_tetops64);
+    if (!st && m->prec != FR_FP64 && m->has_pyr) st = upload_dense_ff<frb::Pyr3D, PyrOps<float>>(m, m->pyr, &m->d_pyrops64);
     if (!st && m->lowmach) {
         std::vector<GeoLM> g64((size_t)m->ne);
         for (long long e = 0; e < m->ne; e++) g64[e] = geo_lm(&m->geo_host[(size_t)e * 10]);

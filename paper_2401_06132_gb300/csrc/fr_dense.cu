@@ -72,10 +72,13 @@ __device__ __forceinline__ ff ffat(const FF &o, const float &hi)
 // EPB elements per CTA iteration, one thread per (element, flux point). The states of the EPB
 // elements are staged in shared memory with coalesced loads; each thread keeps its column of M0 in
 // registers for the whole persistent loop and reads the state with 16-byte broadcast loads.
-// Low-Mach FP32 form (ph.dev): the face solution of the deviations from the reference state, and the
-// own-normal mass flux n.(rho v) at every flux point in float-float: first m_f = n_f . (rho v) at the
-// solution points per face (the face normal is constant on an affine element), then the compensated
-// dot product (Dot2 of Ogita, Rump and Oishi) of the float-float M0 row with m_f.
+// The reduced precisions evaluate every face value as a compensated dot product (Dot2 of Ogita, Rump
+// and Oishi) of the float-float M0 row (hi + lo) with the FP32 state, rounded once: at low Mach the
+// Rusanov dissipation (1/2)(|v.n| + c)(u_L - u_R), c about 10 |v|, lifts any rounding of a face
+// value into R. Low-Mach FP32 form (ph.dev): the face solution of the deviations from the reference
+// state, and the own-normal mass flux n.(rho v) at every flux point in float-float: first
+// m_f = n_f . (rho v) at the solution points per face (the face normal is constant on an affine
+// element), then the same compensated dot product with m_f.
 template <typename T, typename OPS, int EPB>
 __global__ void __launch_bounds__(OPS::NF * EPB) k_dense_disu(HexArgs<T> a, const OPS *__restrict__ op, const FFOf<OPS> *__restrict__ opsff)
 {
@@ -88,6 +91,11 @@ __global__ void __launch_bounds__(OPS::NF * EPB) k_dense_disu(HexArgs<T> a, cons
     T col[NUS];
 #pragma unroll
     for (int z = 0; z < NUS; z++) col[z] = op->M0t[z][s];   // pad rows are zero
+    float col_lo[F32 ? NUS : 1];                              // lo parts of the FP32 column
+    if constexpr (F32) {
+#pragma unroll
+        for (int z = 0; z < NUS; z++) col_lo[z] = opsff->lo.M0t[z][s];
+    }
     if constexpr (NUS > NU) {
         for (int i = threadIdx.x; i < EPB * FR_NV * (NUS - NU); i += NTH) {
             const int l = i / (FR_NV * (NUS - NU)), r = i % (FR_NV * (NUS - NU));
@@ -131,20 +139,45 @@ __global__ void __launch_bounds__(OPS::NF * EPB) k_dense_disu(HexArgs<T> a, cons
             const long long e = e0 + el;
             const long long f0 = elem_f0(a, e, NF);
             const T *u = s_u[el];
-            T v[FR_NV];
+            if constexpr (F32) {
+                // sh + c = sum_z (col + col_lo)[z] x[z]: exact products (one FMA each), TwoSum
+                // accumulation of the high parts, the errors summed in c
+                float sh[FR_NV], c[FR_NV];
 #pragma unroll
-            for (int alpha = 0; alpha < FR_NV; alpha++) v[alpha] = T(0);
+                for (int alpha = 0; alpha < FR_NV; alpha++) { sh[alpha] = 0.0f; c[alpha] = 0.0f; }
 #pragma unroll
-            for (int z = 0; z < NUS; z += VN) {
+                for (int z = 0; z < NUS; z += VN) {
 #pragma unroll
-                for (int alpha = 0; alpha < FR_NV; alpha++) {
-                    const V16<T> x = ld16(u + alpha * NUS + z);
+                    for (int alpha = 0; alpha < FR_NV; alpha++) {
+                        const V16<T> x = ld16(u + alpha * NUS + z);
 #pragma unroll
-                    for (int j = 0; j < VN; j++) v[alpha] += col[z + j] * x.v[j];
+                        for (int j = 0; j < VN; j++) {
+                            const float pr = col[z + j] * x.v[j];
+                            const float er = __fmaf_rn(col_lo[z + j], x.v[j], __fmaf_rn(col[z + j], x.v[j], -pr));
+                            const ff t = two_sum(sh[alpha], pr);
+                            sh[alpha] = t.hi;
+                            c[alpha] += t.lo + er;
+                        }
+                    }
                 }
-            }
 #pragma unroll
-            for (int alpha = 0; alpha < FR_NV; alpha++) a.UF[alpha * a.nfpt + f0 + s] = v[alpha];
+                for (int alpha = 0; alpha < FR_NV; alpha++) a.UF[alpha * a.nfpt + f0 + s] = sh[alpha] + c[alpha];
+            } else {
+                T v[FR_NV];
+#pragma unroll
+                for (int alpha = 0; alpha < FR_NV; alpha++) v[alpha] = T(0);
+#pragma unroll
+                for (int z = 0; z < NUS; z += VN) {
+#pragma unroll
+                    for (int alpha = 0; alpha < FR_NV; alpha++) {
+                        const V16<T> x = ld16(u + alpha * NUS + z);
+#pragma unroll
+                        for (int j = 0; j < VN; j++) v[alpha] += col[z + j] * x.v[j];
+                    }
+                }
+#pragma unroll
+                for (int alpha = 0; alpha < FR_NV; alpha++) a.UF[alpha * a.nfpt + f0 + s] = v[alpha];
+            }
             if constexpr (F32) {
                 if (elem_phys(a, e).dev) {
                     const ff *m = s_m[el] + OPS::FACE(s) * NUS;

@@ -355,34 +355,38 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
             s_c[it] = (T(0.5) - ph.beta) * uL + (T(0.5) + ph.beta) * uR;
         }
         __syncthreads();
-        if constexpr (sizeof(T) == 4) {
-            // low-Mach form: volume part of R~_rho in FP64 (rho v lies in the solution space, so its
-            // projection is itself and the corrected divergence applies at the solution points)
-            if (dev) {
-                const ff *cm = a.geo64[e].cm;   // det J J^-1, per element
-                for (int z = threadIdx.x; z < NU; z += NTH) {
-                    const float m0 = s_u[NU + z], m1 = s_u[2 * NU + z], m2 = s_u[3 * NU + z];
+        // low-Mach form: volume part of R~_rho in float-float (rho v lies in the solution space, so
+        // its projection is itself and the corrected divergence applies at the solution points).
+        // The tensor-core forms run it while the projection's MMA chain is in flight.
+        auto mass_channel = [&]() {
+            if constexpr (sizeof(T) == 4) {
+                if (dev) {
+                    const ff *cm = a.geo64[e].cm;   // det J J^-1, per element
+                    for (int z = threadIdx.x; z < NU; z += NTH) {
+                        const float m0 = s_u[NU + z], m1 = s_u[2 * NU + z], m2 = s_u[3 * NU + z];
 #pragma unroll
-                    for (int d = 0; d < 3; d++)
-                        s_mf[d * NU + z] = ff_add(ff_add(ff_mul_f(cm[3 * d], m0), ff_mul_f(cm[3 * d + 1], m1)), ff_mul_f(cm[3 * d + 2], m2));
-                }
-                __syncthreads();
-                const PriOpsFF &o = *opsff;
-                const long long pbase = elem_u0(a, e, NU) / FR_NV;
-                for (int z = threadIdx.x; z < NU; z += NTH) {
-                    const int k = z / NT_, t = z % NT_;
-                    ff v = ff_of(0.0f);
-#pragma unroll
-                    for (int j = 0; j < NT_; j++) {
-                        v = ff_fma(ffop(o, o.hi.Dhx[t][j]), s_mf[j + 10 * k], v);
-                        v = ff_fma(ffop(o, o.hi.Dhy[t][j]), s_mf[NU + j + 10 * k], v);
+                        for (int d = 0; d < 3; d++)
+                            s_mf[d * NU + z] = ff_add(ff_add(ff_mul_f(cm[3 * d], m0), ff_mul_f(cm[3 * d + 1], m1)), ff_mul_f(cm[3 * d + 2], m2));
                     }
+                    __syncthreads();
+                    const PriOpsFF &o = *opsff;
+                    const long long pbase = elem_u0(a, e, NU) / FR_NV;
+                    for (int z = threadIdx.x; z < NU; z += NTH) {
+                        const int k = z / NT_, t = z % NT_;
+                        ff v = ff_of(0.0f);
 #pragma unroll
-                    for (int j = 0; j < NZ; j++) v = ff_fma(ffop(o, o.hi.Dhz[k][j]), s_mf[2 * NU + t + 10 * j], v);
-                    a.RL[pbase + z] = v;
+                        for (int j = 0; j < NT_; j++) {
+                            v = ff_fma(ffop(o, o.hi.Dhx[t][j]), s_mf[j + 10 * k], v);
+                            v = ff_fma(ffop(o, o.hi.Dhy[t][j]), s_mf[NU + j + 10 * k], v);
+                        }
+#pragma unroll
+                        for (int j = 0; j < NZ; j++) v = ff_fma(ffop(o, o.hi.Dhz[k][j]), s_mf[2 * NU + t + 10 * j], v);
+                        a.RL[pbase + z] = v;
+                    }
                 }
             }
-        }
+        };
+        if constexpr (TCM == 0) mass_channel();
         // corrected gradient: z lines (alpha, t) and triangle planes (alpha, k, t)
         for (int it = threadIdx.x; it < 5 * NT_; it += NTH) {
             const int alpha = it / NT_, t = it % NT_;
@@ -426,35 +430,39 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
         __syncthreads();
         // viscous normal flux at own flux points, on the side whose LDG weight 1/2 +- beta is not
         // zero (the other side's is never used); the points are compacted so whole warps work
-        for (int s = threadIdx.x; s < NF; s += NTH) {
-            const bool isL = (a.partner[gf0 + s] & FR_LFLAG) != 0;
-            const T wgt = isL ? T(0.5) + ph.beta : T(0.5) - ph.beta;
-            if (wgt == T(0)) {
+        // (the tensor-core forms run it while the interpolation's MMA chain is in flight)
+        auto viscous_faces = [&]() {
+            for (int s = threadIdx.x; s < NF; s += NTH) {
+                const bool isL = (a.partner[gf0 + s] & FR_LFLAG) != 0;
+                const T wgt = isL ? T(0.5) + ph.beta : T(0.5) - ph.beta;
+                if (wgt == T(0)) {
 #pragma unroll
-                for (int k = 0; k < 4; k++) a.FV[k * a.nfpt + gf0 + s] = T(0);
-            } else {
-                s_plist[atomicAdd(&s_pcnt, 1)] = (short)s;
+                    for (int k = 0; k < 4; k++) a.FV[k * a.nfpt + gf0 + s] = T(0);
+                } else {
+                    s_plist[atomicAdd(&s_pcnt, 1)] = (short)s;
+                }
             }
-        }
-        __syncthreads();
-        const int nplist = s_pcnt;
-        for (int li = threadIdx.x; li < nplist; li += NTH) {
-            const int s = s_plist[li];
-            T uf[5], qf[5][3];
+            __syncthreads();
+            const int nplist = s_pcnt;
+            for (int li = threadIdx.x; li < nplist; li += NTH) {
+                const int s = s_plist[li];
+                T uf[5], qf[5][3];
 #pragma unroll
-            for (int alpha = 0; alpha < 5; alpha++) {
-                uf[alpha] = face_value(op, s_u + alpha * NU, s);
+                for (int alpha = 0; alpha < 5; alpha++) {
+                    uf[alpha] = face_value(op, s_u + alpha * NU, s);
 #pragma unroll
-                for (int d = 0; d < 3; d++) qf[alpha][d] = face_value(op, s_q + (alpha * 3 + d) * NU, s);
+                    for (int d = 0; d < 3; d++) qf[alpha][d] = face_value(op, s_q + (alpha * 3 + d) * NU, s);
+                }
+                const T *nt = a.fnrm + (e * 6 + face_of(s)) * 4;
+                T n[3] = {nt[0], nt[1], nt[2]};
+                if (dev) { uf[0] += ph.rref; uf[4] += ph.eref; }
+                T fvn[4];
+                viscous_normal_flux(ph, uf, qf, n, fvn);
+#pragma unroll
+                for (int k = 0; k < 4; k++) a.FV[k * a.nfpt + gf0 + s] = fvn[k];
             }
-            const T *nt = a.fnrm + (e * 6 + face_of(s)) * 4;
-            T n[3] = {nt[0], nt[1], nt[2]};
-            if (dev) { uf[0] += ph.rref; uf[4] += ph.eref; }
-            T fvn[4];
-            viscous_normal_flux(ph, uf, qf, n, fvn);
-#pragma unroll
-            for (int k = 0; k < 4; k++) a.FV[k * a.nfpt + gf0 + s] = fvn[k];
-        }
+        };
+        if constexpr (TCM == 0) viscous_faces();
         if constexpr (TCM == 0 && sizeof(T) == 4) {
             pri_interp_all<T, NTH>(op, s_u, s_t, s_w);   // s_q follows s_u
         } else if constexpr (TCM == 0) {
@@ -491,8 +499,9 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
                 tc::store_row<TC_KI>(tA, r, kv);
                 s_sh[r] = sh;
             }
-            if (!tc::mma_chain<TC_KI / 16>(tmem, tA, TC_SBO_I, tBi, TC_SBO_I, TCM == 1 ? TC_IDESC_I1 : TC_IDESC_I2, mbar, parity,
-                                            tc::first_limit(first_wait, a.dbg_wait0))) {
+            tc::mma_issue<TC_KI / 16>(tmem, tA, TC_SBO_I, tBi, TC_SBO_I, TCM == 1 ? TC_IDESC_I1 : TC_IDESC_I2, mbar);
+            viscous_faces();   // CUDA-core work while the chain runs (touches no operand tile)
+            if (!tc::mma_wait(mbar, parity, tc::first_limit(first_wait, a.dbg_wait0))) {
                 tc_fail = true;
                 break;
             }
@@ -563,8 +572,12 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
                 tc::store_row<TC_KP>(tA, r, kv);
                 s_sh[r] = sh;
             }
-            if (!tc::mma_chain<TC_KP / 16>(tmem, tA, TC_SBO_P, tBp, TC_SBO_P, TCM == 1 ? TC_IDESC_P1 : TC_IDESC_P2, mbar, parity,
-                                            tc::first_limit(first_wait, a.dbg_wait0))) {
+            tc::mma_issue<TC_KP / 16>(tmem, tA, TC_SBO_P, tBp, TC_SBO_P, TCM == 1 ? TC_IDESC_P1 : TC_IDESC_P2, mbar);
+            // CUDA-core work while the chain runs: it reads the state and writes only static shared
+            // memory and global memory, which the chain's rows (they run on past the operand tile
+            // into the dynamic shared arrays) never reach
+            mass_channel();
+            if (!tc::mma_wait(mbar, parity, tc::first_limit(first_wait, a.dbg_wait0))) {
                 tc_fail = true;
                 break;
             }

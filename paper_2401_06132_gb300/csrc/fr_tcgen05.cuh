@@ -203,6 +203,36 @@ __device__ __forceinline__ bool mma_chain(uint32_t tmem, const unsigned char *A,
     return true;
 }
 
+// The two halves of mma_chain, for callers that do independent CUDA-core work while the chain runs:
+// mma_issue makes every thread's operand stores visible and issues the chain from thread 0 (call with
+// every thread); mma_wait waits for it as mma_chain does (the caller must not write the operand
+// tiles, or shared memory the chain's rows run into, between the two).
+template <int KSTEPS>
+__device__ __forceinline__ void mma_issue(uint32_t tmem, const unsigned char *A, int sbo_a, const unsigned char *B, int sbo_b,
+                                          uint32_t idesc, uint64_t *mbar)
+{
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        fence_after_sync();
+        const uint32_t aA = smem_u32(A), aB = smem_u32(B);
+#pragma unroll
+        for (int j = 0; j < KSTEPS; j++)
+            mma_f16(tmem, sdesc(aA + 256 * j, 128, sbo_a), sdesc(aB + 256 * j, 128, sbo_b), idesc, j);
+        commit(mbar);
+    }
+}
+
+__device__ __forceinline__ bool mma_wait(uint64_t *mbar, uint32_t &parity, uint32_t limit = 1u << 24)
+{
+    const bool done = mbar_wait(mbar, parity, limit);
+    if (!__syncthreads_and(done)) return false;
+    parity ^= 1;
+    fence_after_sync();
+    return true;
+}
+
 // Per-CTA setup: mbarrier (thread 0) and tensor-memory columns (warp 0). Call with every thread.
 __device__ __forceinline__ void setup(uint64_t *mbar, uint32_t *s_tmem, uint32_t ncols)
 {
