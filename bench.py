@@ -443,10 +443,11 @@ def other_configs(args, torch, fr, W):
 
 
 def run_partitioned(args, rank, world):
-    """The 48^3 mesh split into `world` z slabs, one per GPU: every RHS evaluation runs phase A,
-    a halo exchange of the face solution, phase B, an exchange of the face viscous flux, phase C
-    (partition.py; NCCL send/recv under torchrun). A step here is one RHS evaluation (the partitioned
-    handle has no RK4 entry point); strong scaling: the whole mesh is the same for every N."""
+    """The 48^3 mesh split into `world` z slabs, one per GPU: every RHS evaluation of the RK4 step
+    runs phase A, a halo exchange of the face solution, phase B, an exchange of the face viscous flux,
+    phase C with the stage update (fr_rk4_stage; partition.py, NCCL send/recv under torchrun). A step
+    is one RK4 step (4 RHS), as in the default mode; strong scaling: the whole mesh is the same for
+    every N."""
     import torch
 
     from paper_2401_06132_gb300 import build as B
@@ -466,7 +467,6 @@ def run_partitioned(args, rank, world):
     U0 = W.tgv_state(m.sol_coords(), [(m.info()["elements"], (P + 1) ** 3)], perturb=1e-3,
                      dof_offset=e0 * FR_NV_DOF_PER_ELEMENT)
     U = torch.from_numpy(U0).cuda()
-    R = torch.empty_like(U)
     pr = partition.PartRHS(m)
 
     def exchange(what):
@@ -476,7 +476,7 @@ def run_partitioned(args, rank, world):
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         for _ in range(args.warmup):
-            pr.rhs(U, R, exchange)
+            pr.rk4_step(U, DT, exchange)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
@@ -484,7 +484,7 @@ def run_partitioned(args, rank, world):
         with ClockSampler(local) as clk:
             e0v.record(s)
             for _ in range(args.steps):
-                pr.rhs(U, R, exchange)
+                pr.rk4_step(U, DT, exchange)
             e1v.record(s)
             torch.cuda.synchronize()
     m.sync_status(stream=s)
@@ -492,14 +492,16 @@ def run_partitioned(args, rank, world):
     dof_total = N_EDGE ** 3 * FR_NV_DOF_PER_ELEMENT
     if rank != 0:
         return
-    value = dof_total / (ms * 1e-3) / 1e9
+    value = dof_total * RHS_PER_STEP / (ms * 1e-3) / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(), "mode": "partitioned single mesh (z slabs), step = one RHS",
+            "config": {"workload": workload_name(), "mode": "partitioned single mesh (z slabs)",
                        "parallelism": f"{world} parts, 2 halo exchanges per RHS", "halo_points": info["nhalo"],
                        "l2": "inputs larger than L2 (283 MB FP64 state, 129 MB L2)"},
-            "gpu_launches": (3 + 4 * sum(1 for c in info["counts"] if c)) * args.steps,
+            # per RHS: 3 phases, and a pack and an unpack per exchange and peer; the FP64 stage update is
+            # folded into phase C
+            "gpu_launches": RHS_PER_STEP * (3 + 4 * sum(1 for c in info["counts"] if c)) * args.steps,
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 

@@ -191,7 +191,15 @@ fr_status fr_rk4_step_host(fr_mesh *m, void *U_host, double dt, int nsteps, void
  * results then differ at the FP32 rounding level. Synchronises the stream. */
 fr_status fr_autotune(fr_mesh *m, const void *U_dev, void *R_dev, int *chosen, int n_chosen, void *stream);
 
-/* Sets the volume-kernel launch shape (0..4, as for fr_autotune) of every hexahedral group;
+/* Kernel groups (blocks of one element type and order, launched together): info[0..5] of group
+ * `group` = element type (0 hex, 1 prism, 2 tetrahedron, 3 pyramid), order p, quadrature points per
+ * line, elements, current volume-kernel shape, number of shapes it can run. FR_EINVAL past the last
+ * group. fr_set_group_shape sets one hexahedral group's shape (e.g. a choice of fr_autotune kept from
+ * an earlier run); FR_EUNSUPPORTED for a shape the group cannot run. */
+fr_status fr_group_info(const fr_mesh *m, int group, long long *info);
+fr_status fr_set_group_shape(fr_mesh *m, int group, int shape);
+
+/* Sets the volume-kernel launch shape (0..5, as for fr_autotune) of every hexahedral group;
  * FR_EUNSUPPORTED if a group cannot run it. Takes effect at the next launch (recaptures the RK4 graph). */
 fr_status fr_set_volume_shape(fr_mesh *m, int shape);
 
@@ -299,8 +307,9 @@ fr_status fr_kernel_times(fr_mesh *m, double *ms, long long *count, int n_ids);
  * where "exchange" sends the segment of peer q of the send buffer to q and receives q's segment
  * into the same place of the receive buffer (any transport: NCCL, MPI, or device copies). Each side
  * of a pair evaluates its own point's common flux with the pair's global L/R roles, so the parts'
- * R concatenated equal the single-handle RHS bit for bit. Surface-flux anti-aliasing, the unfused
- * form, fr_rhs and the RK4 entry points are FR_EUNSUPPORTED on a part of a mesh with nparts > 1.
+ * R concatenated equal the single-handle RHS bit for bit. RK4 steps go the same way through
+ * fr_rk4_stage. Surface-flux anti-aliasing, the unfused form, fr_rhs and fr_rk4_step are
+ * FR_EUNSUPPORTED on a part of a mesh with nparts > 1.
  * ------------------------------------------------------------------------------------------- */
 
 /* Exchange plan of part `part` of nparts, computed on the host only (no device is touched).
@@ -334,6 +343,13 @@ fr_status fr_halo_unpack(fr_mesh *m, int what, const void *recv_dev, void *strea
  * R~ into R), 2 interface group (comm_flux, tdivtconf, negdivconf: finishes R). Same arguments as
  * fr_rhs; phases 0, 1, 2 in order on one stream are one fr_rhs. */
 fr_status fr_rhs_phase(fr_mesh *m, int phase, const void *U_dev, void *R_dev, void *stream);
+
+/* One phase (0, 1, 2 as for fr_rhs_phase) of stage `stage` (0..3) of a classical RK4 step on the
+ * FP64 master state U_dev, with the stage update after phase 2 (as fr_rk4_step does it); stages 0..3
+ * with phases 0, 1, 2 each, in order, are one fr_rk4_step(nsteps = 1). The stage states and the
+ * Runge-Kutta sum live in the handle. On a part of a partitioned mesh the halo exchanges go between
+ * the phases, as for an RHS. Fused form; asynchronous on `stream`. */
+fr_status fr_rk4_stage(fr_mesh *m, int stage, int phase, void *U_dev, double dt, void *stream);
 
 /* Text of the last error on the calling thread ("" if none). */
 const char *fr_last_error(void);

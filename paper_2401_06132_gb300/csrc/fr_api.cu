@@ -1592,12 +1592,12 @@ struct RkFold {
 template <typename T>
 static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, const RkFold &rk = RkFold(), int only = -1)
 {
-    if (m->nparts > 1 && (m->form != FR_FUSED || only < 0))
-        return fail(FR_EUNSUPPORTED, "a partitioned mesh runs the fused phases one at a time (fr_rhs_phase) with "
-                                     "halo exchanges between them");
     if (m->form == FR_FUSED && m->curved && m->lowmach)
         return fail(FR_EUNSUPPORTED, "curved (non-affine) hexahedra: the low-Mach FP32 form is not built for them "
                                      "(set rho_ref = 0 for the plain FP32 form)");
+    if (m->nparts > 1 && (m->form != FR_FUSED || only < 0))
+        return fail(FR_EUNSUPPORTED, "a partitioned mesh runs the fused phases one at a time (fr_rhs_phase) with "
+                                     "halo exchanges between them");
     if (m->form == FR_FUSED) {
         static const int plain[3] = {0, 1, 2}, split[4] = {0, 1, 3, 4};
         const int *phases = m->split_c ? split : plain;
@@ -1697,6 +1697,30 @@ extern "C" fr_status fr_set_volume_shape(fr_mesh *m, int shape)
     }
     for (Group &g : m->groups)
         if (m->blocks[g.blks[0]].type == 0) g.variant = shape;
+    if (m->graph) { cudaGraphExecDestroy(m->graph); m->graph = nullptr; }
+    return FR_OK;
+}
+
+extern "C" fr_status fr_group_info(const fr_mesh *m, int group, long long *info)
+{
+    if (!m || !info) return fail(FR_EINVAL, "null argument");
+    if (group < 0 || group >= (int)m->groups.size()) return fail(FR_EINVAL, "group %d of %d", group, (int)m->groups.size());
+    const Group &g = m->groups[(size_t)group];
+    const Block &b = m->blocks[g.blks[0]];
+    info[0] = b.type; info[1] = b.p; info[2] = b.m; info[3] = g.ne; info[4] = g.variant;
+    info[5] = b.type == 0 ? volume_shapes(m, b) : 1;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_set_group_shape(fr_mesh *m, int group, int shape)
+{
+    if (!m) return fail(FR_EINVAL, "null handle");
+    if (group < 0 || group >= (int)m->groups.size()) return fail(FR_EINVAL, "group %d of %d", group, (int)m->groups.size());
+    Group &g = m->groups[(size_t)group];
+    const Block &b = m->blocks[g.blks[0]];
+    if (b.type != 0 || shape < 0 || shape >= volume_shapes(m, b))
+        return fail(FR_EUNSUPPORTED, "group %d has no volume-kernel shape %d", group, shape);
+    g.variant = shape;
     if (m->graph) { cudaGraphExecDestroy(m->graph); m->graph = nullptr; }
     return FR_OK;
 }
@@ -1876,46 +1900,61 @@ __global__ void k_rk_update(double *__restrict__ U, const T *__restrict__ k, flo
     }
 }
 
+// One RK4 stage st (0..3) of the step U -> U + dt sum_s b_s k_s, or one phase of it (only = 0, 1, 2:
+// face solution, volume group, interface group with the stage update; only < 0: all of it). The
+// stage's RHS input is U (FP64) or fl32(U) (reduced precisions, split off at the start of stage 0)
+// for st = 0 and the stage state us otherwise.
 template <typename T>
-static fr_status rk4_enqueue_step(fr_mesh *m, double *U, double dt, cudaStream_t s)
+static fr_status rk4_enqueue_stage(fr_mesh *m, double *U, double dt, cudaStream_t s, int st, int only)
 {
     const long long n = m->nU;
     const int thr = 256;
-    const int grid = (int)std::min<long long>((n + thr - 1) / thr, 152LL * 16);
-    const void *u0 = U;
+    const int grid = (int)std::min<long long>((n + thr - 1) / thr, 16LL * m->nsm);
     // reduced precisions: d_rk_acc holds the FP32 Runge-Kutta sum and fl32(U)
     float *accf = reinterpret_cast<float *>(m->d_rk_acc);
     float *uhi = m->prec == FR_FP64 ? nullptr : accf + n;
+    const void *u0 = U;
     if (m->prec != FR_FP64) {
-        k_rk_split<T><<<grid, thr, 0, s>>>(U, uhi, reinterpret_cast<T *>(m->d_rk_us), n);
+        if (st == 0 && only <= 0) k_rk_split<T><<<grid, thr, 0, s>>>(U, uhi, reinterpret_cast<T *>(m->d_rk_us), n);
         u0 = m->d_rk_us;
     }
-    for (int st = 0; st < 4; st++) {
-        if (m->form == FR_FUSED && m->prec == FR_FP64) {
-            // FP64: the stage update is folded into the interface kernel (no RHS array, no extra
-            // launch). The reduced precisions write R and run the update as its own streaming
-            // kernel: their latency-bound interface kernels would stall on the FP64 master-state
-            // and accumulator traffic, which the element-wise kernel moves near the HBM peak.
-            RkFold rk;
-            rk.stage = st; rk.dt = dt; rk.U = U; rk.acc = m->d_rk_acc; rk.us = m->d_rk_us;
-            fr_status r = rhs_impl<T>(m, st == 0 ? u0 : m->d_rk_us, m->d_rk_k, s, rk);
-            if (r) return r;
-            continue;
-        }
-        fr_status r = rhs_dispatch(m, st == 0 ? u0 : m->d_rk_us, m->d_rk_k, s);
+    const void *in = st == 0 ? u0 : m->d_rk_us;
+    if (m->form == FR_FUSED && m->prec == FR_FP64) {
+        // FP64: the stage update is folded into the interface kernel (no RHS array, no extra
+        // launch). The reduced precisions write R and run the update as its own streaming
+        // kernel: their latency-bound interface kernels would stall on the FP64 master-state
+        // and accumulator traffic, which the element-wise kernel moves near the HBM peak.
+        RkFold rk;
+        rk.stage = st; rk.dt = dt; rk.U = U; rk.acc = m->d_rk_acc; rk.us = m->d_rk_us;
+        fr_status r = rhs_impl<T>(m, in, m->d_rk_k, s, rk, only);
         if (r) return r;
-        TimeScope ts(m, 30, s);
-        if constexpr (sizeof(T) == 8) {
-            k_rk_update64<<<grid, thr, 0, s>>>(U, reinterpret_cast<const double *>(m->d_rk_k), m->d_rk_acc,
-                                               reinterpret_cast<double *>(m->d_rk_us), n, dt, st);
-        } else {
-            const double bs[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0}, cnext[4] = {0.5, 0.5, 1.0, 0.0};
-            k_rk_update<T><<<grid, thr, 0, s>>>(U, reinterpret_cast<const T *>(m->d_rk_k), accf, uhi,
-                                                reinterpret_cast<T *>(m->d_rk_us), n, dt, (float)(cnext[st] * dt),
-                                                (float)bs[st], st);
-        }
+        CU(cudaPeekAtLastError());
+        return FR_OK;
+    }
+    fr_status r = only < 0 ? rhs_dispatch(m, in, m->d_rk_k, s) : rhs_impl<T>(m, in, m->d_rk_k, s, RkFold(), only);
+    if (r) return r;
+    if (only >= 0 && only != 2) return FR_OK;
+    TimeScope ts(m, 30, s);
+    if constexpr (sizeof(T) == 8) {
+        k_rk_update64<<<grid, thr, 0, s>>>(U, reinterpret_cast<const double *>(m->d_rk_k), m->d_rk_acc,
+                                           reinterpret_cast<double *>(m->d_rk_us), n, dt, st);
+    } else {
+        const double bs[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0}, cnext[4] = {0.5, 0.5, 1.0, 0.0};
+        k_rk_update<T><<<grid, thr, 0, s>>>(U, reinterpret_cast<const T *>(m->d_rk_k), accf, uhi,
+                                            reinterpret_cast<T *>(m->d_rk_us), n, dt, (float)(cnext[st] * dt),
+                                            (float)bs[st], st);
     }
     CU(cudaPeekAtLastError());
+    return FR_OK;
+}
+
+template <typename T>
+static fr_status rk4_enqueue_step(fr_mesh *m, double *U, double dt, cudaStream_t s)
+{
+    for (int st = 0; st < 4; st++) {
+        fr_status r = rk4_enqueue_stage<T>(m, U, dt, s, st, -1);
+        if (r) return r;
+    }
     return FR_OK;
 }
 
@@ -1956,18 +1995,39 @@ static fr_status rk4_impl(fr_mesh *m, double *U, double dt, int nsteps, cudaStre
     return FR_OK;
 }
 
+static fr_status rk4_buffers(fr_mesh *m)
+{
+    size_t ts = tsize(m->prec);
+    fr_status st = dalloc(m, &m->d_rk_k, (size_t)m->nU * ts);
+    if (!st) st = dalloc(m, &m->d_rk_us, (size_t)m->nU * ts);
+    // FP64: the Runge-Kutta sum; reduced precisions: its FP32 form and fl32(U) (the same bytes)
+    if (!st) st = dalloc(m, (void **)&m->d_rk_acc, (size_t)m->nU * sizeof(double));
+    return st;
+}
+
+extern "C" fr_status fr_rk4_stage(fr_mesh *m, int stage, int phase, void *U_dev, double dt, void *stream)
+{
+    if (!m || !U_dev || stage < 0 || stage > 3 || phase < 0 || phase > 2 || !(dt == dt))
+        return fail(FR_EINVAL, "bad argument");
+    if (m->form != FR_FUSED) return fail(FR_EUNSUPPORTED, "fr_rk4_stage runs the fused form");
+    fr_status st = check_status(m);
+    if (!st) st = rk4_buffers(m);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = m->prec == FR_FP64 ? rk4_enqueue_stage<double>(m, (double *)U_dev, dt, s, stage, phase)
+                            : rk4_enqueue_stage<float>(m, (double *)U_dev, dt, s, stage, phase);
+    if (st) return st;
+    return phase == 2 ? post_status(m, s) : FR_OK;
+}
+
 extern "C" fr_status fr_rk4_step(fr_mesh *m, void *U_dev, double dt, int nsteps, void *stream)
 {
     if (!m || !U_dev || nsteps < 0 || !(dt == dt)) return fail(FR_EINVAL, "bad argument");
     if (m->nparts > 1)
-        return fail(FR_EUNSUPPORTED, "a partitioned mesh advances through fr_rhs_phase and halo exchanges");
+        return fail(FR_EUNSUPPORTED, "a partitioned mesh advances through fr_rk4_stage and halo exchanges");
     fr_status st = check_status(m);
     if (st) return st;
-    size_t ts = tsize(m->prec);
-    st = dalloc(m, &m->d_rk_k, (size_t)m->nU * ts);
-    if (!st) st = dalloc(m, &m->d_rk_us, (size_t)m->nU * ts);
-    // FP64: the Runge-Kutta sum; reduced precisions: its FP32 form and fl32(U) (the same bytes)
-    if (!st) st = dalloc(m, (void **)&m->d_rk_acc, (size_t)m->nU * sizeof(double));
+    st = rk4_buffers(m);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
     st = m->prec == FR_FP64 ? rk4_impl<double>(m, (double *)U_dev, dt, nsteps, s) : rk4_impl<float>(m, (double *)U_dev, dt, nsteps, s);

@@ -79,6 +79,8 @@ def lib():
             "fr_set_dense_tensor_cores": ([vp, C.c_int], C.c_int),
             "fr_autotune": ([vp, vp, vp, C.POINTER(C.c_int), C.c_int, vp], C.c_int),
             "fr_set_volume_shape": ([vp, C.c_int], C.c_int),
+            "fr_group_info": ([vp, C.c_int, llp], C.c_int),
+            "fr_set_group_shape": ([vp, C.c_int, C.c_int], C.c_int),
             "fr_kernel_times": ([vp, C.POINTER(C.c_double), llp, C.c_int], C.c_int),
             "fr_probe_fma": ([dp, vp], C.c_int),
             "fr_partition_plan": ([C.POINTER(MeshDesc), C.POINTER(Params), C.c_int, C.c_int, llp, llp, llp, llp,
@@ -88,6 +90,7 @@ def lib():
             "fr_halo_pack": ([vp, C.c_int, vp, vp], C.c_int),
             "fr_halo_unpack": ([vp, C.c_int, vp, vp], C.c_int),
             "fr_rhs_phase": ([vp, C.c_int, vp, vp, vp], C.c_int),
+            "fr_rk4_stage": ([vp, C.c_int, C.c_int, vp, C.c_double, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -204,6 +207,12 @@ class FRMesh:
         _check(lib().fr_rhs_phase(self.h, phase, C.c_void_p(U.data_ptr()), C.c_void_p(R.data_ptr()),
                                   _stream_ptr(stream)))
 
+    def rk4_stage(self, stage: int, phase: int, U, dt: float, stream=None):
+        """fr_rk4_stage: one phase of one RK4 stage on the FP64 master state U."""
+        self._check_tensor(U, dtype=U.dtype)
+        assert U.dtype.itemsize == 8, "the RK4 master state is FP64"
+        _check(lib().fr_rk4_stage(self.h, stage, phase, C.c_void_p(U.data_ptr()), dt, _stream_ptr(stream)))
+
     def close(self):
         if getattr(self, "h", None):
             lib().fr_destroy(self.h)
@@ -284,17 +293,53 @@ class FRMesh:
             res.append(dict(volume=o[0], Ek=o[1], eps=o[2], sums=o[3:8].copy()))
         return res
 
-    def autotune(self, U, R, stream=None):
-        """Pick the fastest volume-kernel launch shape per group on this state; returns the choices."""
+    def groups(self) -> list[dict]:
+        """fr_group_info of every kernel group."""
+        out, info = [], (C.c_longlong * 6)()
+        while lib().fr_group_info(self.h, len(out), info) == FR_OK:
+            out.append(dict(type=info[0], p=info[1], m=info[2], elements=info[3], shape=info[4], shapes=info[5]))
+        return out
+
+    def autotune(self, U, R, stream=None, cache: str | None = None):
+        """Pick the fastest volume-kernel launch shape per group on this state; returns the choices.
+        With `cache` (a JSON file), a choice stored there for the same device, precision, element type
+        and order is applied without timing, and new choices are added to it."""
         self._check_tensor(U)
         self._check_tensor(R)
+        keys = self._shape_keys() if cache else None
+        if cache:
+            import json
+            stored = {}
+            if os.path.exists(cache):
+                with open(cache) as f:
+                    stored = json.load(f)
+            if all(k is None or k in stored for k in keys):
+                for g, k in enumerate(keys):
+                    if k is not None:
+                        _check(lib().fr_set_group_shape(self.h, g, int(stored[k])))
+                return [SHAPES[g["shape"]] for g in self.groups()]
         out = (C.c_int * 16)(*([-1] * 16))
         _check(lib().fr_autotune(self.h, C.c_void_p(U.data_ptr()), C.c_void_p(R.data_ptr()), out, 16,
                                  _stream_ptr(stream)))
+        if cache:
+            for g, k in enumerate(keys):
+                if k is not None:
+                    stored[k] = int(out[g])
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(stored, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
         return [SHAPES[v] for v in out if v >= 0]
 
+    def _shape_keys(self):
+        """Cache key of each group's volume-kernel shape (None for groups without a choice)."""
+        import torch
+        dev = torch.cuda.get_device_name()
+        prec = {v: k for k, v in PRECISIONS.items()}[self.prec]
+        return [f"{dev}|{prec}|type{g['type']}|p{g['p']}|m{g['m']}" if g["shapes"] > 1 else None for g in self.groups()]
+
     def set_volume_shape(self, shape: int):
-        """fr_set_volume_shape: the volume-kernel launch shape of every hexahedral group (0..4)."""
+        """fr_set_volume_shape: the volume-kernel launch shape of every hexahedral group (0..5)."""
         _check(lib().fr_set_volume_shape(self.h, shape))
 
     def set_graph(self, on: bool):

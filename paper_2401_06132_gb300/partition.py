@@ -81,3 +81,18 @@ class PartRHS:
         exchange(1)
         m.halo_unpack(1, self.recv[1], stream)
         m.rhs_phase(2, U, R, stream)
+
+    def rk4_step(self, U, dt: float, exchange: Callable[[int], None], stream=None) -> None:
+        """One classical RK4 step of this part's FP64 master state U: per stage phase A, exchange 0,
+        phase B, exchange 1, phase C with the stage update (fr_rk4_stage)."""
+        m = self.m
+        for st in range(4):
+            m.rk4_stage(st, 0, U, dt, stream)
+            m.halo_pack(0, self.send[0], stream)
+            exchange(0)
+            m.halo_unpack(0, self.recv[0], stream)
+            m.rk4_stage(st, 1, U, dt, stream)
+            m.halo_pack(1, self.send[1], stream)
+            exchange(1)
+            m.halo_unpack(1, self.recv[1], stream)
+            m.rk4_stage(st, 2, U, dt, stream)

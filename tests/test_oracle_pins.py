@@ -891,3 +891,26 @@ def test_surface_aa_leaves_the_corrected_gradient_unchanged():
     np.testing.assert_allclose(cfs, np.einsum("qs,evfs->evfq", B2, cf), atol=1e-12 * np.abs(cf).max())
     dR = np.abs(a["R"] - b["R"]).max() / np.abs(a["R"]).max()
     assert 1e-9 < dR < 1e-1, dR
+
+
+def test_golden_dissipation_rate_matches_the_oracle_as_it_stands():
+    """tests/golden/eps_tgv32_p4.txt (written by make_eps_32p4.py) holds the oracle's kinetic energy
+    and dissipation rate of the 32^3 p = 4 sweep at step 0 and after 100 RK4 steps. The step-0 row
+    must be what the oracle computes now (one RHS), so the stored trajectory cannot go stale after an
+    oracle change unnoticed; the rates are near the closed form eps(0) = 3 mu / 4 (the 1e-3
+    perturbation adds dissipation) and E_k near 1/8; both stored rates are positive and E_k decays."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "eps_tgv32_p4.txt")
+    rows = {}
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, ek, eps = line.split()
+                rows[int(k)] = (float(ek), float(eps))
+    assert set(rows) == {0, 100}
+    mesh = W.box_hex_mesh(32)
+    o = O.Oracle(mesh, 4, 6, threads=os.cpu_count(), p_ref=W.tgv_p0())
+    U = W.tgv_state(o.sol_coords(), [(32 ** 3, 125)], perturb=1e-3)
+    d = o.diagnostics(U, o.rhs(U))
+    assert abs(d["Ek"] / rows[0][0] - 1) <= 1e-13 and abs(d["eps"] / rows[0][1] - 1) <= 1e-11, (d, rows[0])
+    assert abs(rows[0][0] - 0.125) < 1e-3 and 0.75 / 1600 < rows[0][1] < 2 * 0.75 / 1600
+    assert rows[100][0] < rows[0][0] and rows[100][1] > 0

@@ -96,7 +96,7 @@ def test_partitioned_handle_refuses_whole_rhs_and_rk4():
         m.rhs(U, R)
     assert e.value.status == fr.FR_EUNSUPPORTED
     with pytest.raises(fr.FRError) as e:
-        m.rk4_step(U, 1e-3, 1)
+        m.rk4_step(U, 1e-3, 1)        # parts step through fr_rk4_stage with exchanges
     assert e.value.status == fr.FR_EUNSUPPORTED
     # a one-part "partition" is the whole mesh: fr_rhs_phase 0, 1, 2 equal fr_rhs
     o = O.Oracle(mesh, 3, 5)
@@ -108,3 +108,41 @@ def test_partitioned_handle_refuses_whole_rhs_and_rk4():
         m1.rhs_phase(ph, Ud, R1)
     m1.sync_status()
     assert np.array_equal(R1.cpu().numpy(), _single_rhs(mesh, fr.make_params(p=3), Uh))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_partitioned_rk4_equals_single_handle(prec):
+    """Three RK4 steps of a 3-part mesh (fr_rk4_stage, halo exchanges between the phases of every
+    stage) equal three fr_rk4_step steps of the single handle bit for bit, FP64 and the low-Mach FP32
+    form (FP64 master state either way)."""
+    mesh = W.mixed_box_mesh(4)
+    p0 = W.tgv_p0()
+    prm = fr.make_params(p=3, prec=prec, p_ref=p0, rho_ref=1.0)
+    single = fr.FRMesh(mesh, prm)
+    blocks = [(mesh["hex_v"].shape[0], 64), (mesh["pri_v"].shape[0], 40)]
+    U0 = W.tgv_state(single.sol_coords(), blocks, perturb=1e-2)
+    Us = torch.from_numpy(U0).cuda()
+    single.rk4_step(Us, 1e-3, 3)
+    single.sync_status()
+    parts = [fr.FRMesh.part(mesh, prm, 3, r) for r in range(3)]
+    rhs = [partition.PartRHS(m) for m in parts]
+    Up, off = [], 0
+    for m in parts:
+        Up.append(torch.from_numpy(np.ascontiguousarray(U0[off:off + m.num_values])).cuda())
+        off += m.num_values
+    counts = [x.counts for x in rhs]
+    for _ in range(3):
+        for st in range(4):
+            for ph in range(3):
+                for m, u in zip(parts, Up):
+                    m.rk4_stage(st, ph, u, 1e-3)
+                if ph < 2:
+                    for x in rhs:
+                        x.m.halo_pack(ph, x.send[ph])
+                    partition.local_exchange([x.send[ph] for x in rhs], [x.recv[ph] for x in rhs], counts,
+                                             rhs[0].nvar[ph])
+                    for x in rhs:
+                        x.m.halo_unpack(ph, x.recv[ph])
+    for m in parts:
+        m.sync_status()
+    assert torch.equal(torch.cat(Up), Us)
