@@ -302,9 +302,9 @@ def other_configs(args, torch, fr, W):
             m.close()
             m64.close()
         del U
-    # ... and with full anti-aliasing (flux + surface flux), FP64 and plain FP32
+    # ... and with full anti-aliasing (flux + surface flux), FP64 and the low-Mach FP32 form
     for prec in ("fp64", "fp32"):
-        m = fr.FRMesh(mesh48, fr.make_params(p=P, prec=prec, p_ref=p0, surface_aa=True))
+        m = fr.FRMesh(mesh48, fr.make_params(p=P, prec=prec, p_ref=p0, rho_ref=1.0, surface_aa=True))
         U0 = W.tgv_state(m.sol_coords(), [(N_EDGE ** 3, (P + 1) ** 3)], perturb=1e-3)
         U = torch.from_numpy(U0).cuda()
         ms = _time_steps(m, U, steps, 2, torch)
@@ -313,7 +313,7 @@ def other_configs(args, torch, fr, W):
                                     "dof": int(U0.size), "elements": N_EDGE ** 3}
         if prec == "fp64":
             m64 = m
-        else:   # the plain FP32 form: the low-Mach form is not built for surface-flux anti-aliasing
+        else:   # the low-Mach FP32 form (FP64 ignores rho_ref)
             out[f"aa_full48_{prec}"].update(rhs_error(m64, m, U0, eb48, torch))
             m.close()
             m64.close()
@@ -354,12 +354,12 @@ def other_configs(args, torch, fr, W):
         else:
             m64 = m
         del U
-    # curved (trilinear) hexahedra, 48^3 p = 3: metric terms at every point; fused FP64 and plain
-    # FP32, and the unfused FP64 form
+    # curved (trilinear) hexahedra, 48^3 p = 3: metric terms at every point; fused FP64 and the
+    # low-Mach FP32 form, and the unfused FP64 form
     m64.close()
     mesh_c = W.curved_box_mesh(N_EDGE)
     for name, prec, form in (("fp64", "fp64", "fused"), ("fp32", "fp32", "fused"), ("unfused_fp64", "fp64", "unfused")):
-        m = fr.FRMesh(mesh_c, fr.make_params(p=P, prec=prec, p_ref=p0))
+        m = fr.FRMesh(mesh_c, fr.make_params(p=P, prec=prec, p_ref=p0, rho_ref=1.0))
         m.set_form(form)
         U0 = W.tgv_state(m.sol_coords(), [(N_EDGE ** 3, (P + 1) ** 3)], perturb=1e-3)
         U = torch.from_numpy(U0).cuda()
@@ -370,7 +370,7 @@ def other_configs(args, torch, fr, W):
         if name == "fp64":
             m64 = m
         else:
-            if name == "fp32":   # the plain FP32 form: the low-Mach form is not built for curved elements
+            if name == "fp32":   # the low-Mach FP32 form (FP64 ignores rho_ref)
                 out[f"curved48_{name}"].update(rhs_error(m64, m, U0, eb48, torch))
             m.close()
         del U

@@ -122,13 +122,15 @@ typedef struct {
                            * in FP32 and the mass equation in float-float (about 48 bits), then
                            * returns R_E = R_(E-H0 rho) + H0 R_rho. All of it is exact in exact
                            * arithmetic; it removes the O(1/M^2) cancellations of low-Mach flows from
-                           * the FP32 rounding. Fused form, every element type (curved hexahedra:
-                           * FR_EUNSUPPORTED at the first RHS call); ignored in FP64. */
+                           * the FP32 rounding. Fused form, every element type; on curved hexahedra
+                           * and with surface-flux anti-aliasing the mass equation takes the FP32 flux
+                           * path instead of the float-float one (their metric or face quadrature
+                           * takes rho v out of the solution space); ignored in FP64. */
     int surface_aa;       /* 1: surface-flux anti-aliasing as well (Sec. 2.2.1: the interface flux points
                            * are replaced by the m x m Gauss-Legendre points of each face, m = nq1d; the
                            * common flux is evaluated there and lifted through the face L2 projection).
-                           * Single-instance hexahedral meshes, FP64 or FP32 without the low-Mach form,
-                           * fused form. 0: flux points are the n x n solution-point traces. */
+                           * Single-instance hexahedral meshes, fused form (FP64, FP32, the low-Mach
+                           * form). 0: flux points are the n x n solution-point traces. */
 } fr_params;
 
 /* Host description of one mesh instance (copied by fr_mesh_create). */

@@ -598,8 +598,6 @@ static fr_status build_host(fr_mesh *m, const fr_mesh_desc *const *inst, int n_i
         if (P.surface_aa) {
             if (n_inst != 1 || !d || d->n_pri > 0 || d->n_tet > 0 || d->n_pyr > 0 || m1 != P.p + 2)
                 return fail(FR_EUNSUPPORTED, "surface-flux anti-aliasing runs single-instance hexahedral meshes with m = p + 2");
-            if (P.prec != FR_FP64 && P.p_ref > 0 && P.rho_ref > 0)
-                return fail(FR_EUNSUPPORTED, "surface-flux anti-aliasing runs without the low-Mach form");
             m->surf = true;
         }
         if (!(P.gamma > 1.0) || !(P.Pr > 0.0) || P.mu < 0.0 || P.tau < 0.0 || !(P.p_ref == P.p_ref) ||
@@ -1592,9 +1590,6 @@ struct RkFold {
 template <typename T>
 static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, const RkFold &rk = RkFold(), int only = -1)
 {
-    if (m->form == FR_FUSED && m->curved && m->lowmach)
-        return fail(FR_EUNSUPPORTED, "curved (non-affine) hexahedra: the low-Mach FP32 form is not built for them "
-                                     "(set rho_ref = 0 for the plain FP32 form)");
     if (m->nparts > 1 && (m->form != FR_FUSED || only < 0))
         return fail(FR_EUNSUPPORTED, "a partitioned mesh runs the fused phases one at a time (fr_rhs_phase) with "
                                      "halo exchanges between them");

@@ -227,7 +227,8 @@ __global__ void __launch_bounds__(NT) k_disu_blk(HexArgs<T> a)
                     a.UF[alpha * a.nfpt + fo] = w.hi + w.lo;
                 }
                 // low-Mach form: own-normal mass flux n.(rho v) at every flux point, in float-float
-                if (elem_phys(a, e0 + el).dev) {
+                // (curved elements carry their mass flux through the FP32 flux path instead)
+                if (elem_phys(a, e0 + el).dev && !a.mu && !a.surf) {
                     const ff *nt = a.fnrm64 + ((e0 + el) * 6 + f) * 4;
                     ff mf = ff_of(0.0f);
 #pragma unroll
@@ -770,6 +771,19 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
                 face_line_p<N, XS, PS>(f, loc, base, stride);
                 const T *l = (f & 1) ? op.lR : op.lL;
                 const T *src = s_u + fld * FS + base;
+                if constexpr (std::is_same<T, float>::value) {
+                    if (fld < 5) {
+                        // the state's traces as compensated products (float-float line operator),
+                        // rounded once: the face values feed the Rusanov dissipation
+                        const HexOpsFF &off = c_hexff[P - 2];
+                        const ff *lf = (f & 1) ? off.lR : off.lL;
+                        ff w = ff_of(0.0f);
+#pragma unroll
+                        for (int i = 0; i < N; i++) w = ff_fma_f(lf[i], src[i * stride], w);
+                        tr[it] = w.hi + w.lo;
+                        continue;
+                    }
+                }
                 T v = T(0);
 #pragma unroll
                 for (int i = 0; i < N; i++) v += l[i] * src[i * stride];
@@ -801,6 +815,10 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
                     for (int k = 0; k < N; k++) v += op.B[qb][k] * tf[alpha * M * N + M * k];
                     uf[alpha] = v;
                     a.UFQ[alpha * a.nqf + gq] = v;
+                }
+                if constexpr (std::is_same<T, float>::value) {
+                    // low-Mach form: the face values are deviations; the viscous flux takes the state
+                    if (dev) { uf[0] += ph.rref; uf[4] += ph.eref; }
                 }
                 if (wgt == T(0)) {
 #pragma unroll
@@ -901,8 +919,10 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
         }   // surface-flux anti-aliasing or not
         if constexpr (std::is_same<T, float>::value) {
             // low-Mach form: volume part of R~_rho in float-float (the mass flux rho v is a
-            // polynomial of the solution space, so its L2 projection is itself: no quadrature points)
-            if (dev) {
+            // polynomial of the solution space, so its L2 projection is itself: no quadrature points).
+            // Curved elements: det J J^-1 varies over the element, so the mass flux takes the FP32
+            // quadrature-point path with the other fluxes instead.
+            if (dev && !CURV && !SURF) {
                 const HexOpsFF &off = c_hexff[P - 2];
                 const ff *cm = a.geo64[e].cm;   // det J J^-1, per element
                 ff *s_mf = reinterpret_cast<ff *>(s_m64);
@@ -1028,7 +1048,7 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
                 for (int d = 0; d < 3; d++) gq[alpha][d] = s_w[(5 + alpha * 3 + d) * NQ + q];
             }
             if constexpr (std::is_same<T, float>::value) {
-                if (dev) ok &= total_flux_dev(ph, u, gq, f);
+                if (dev) ok &= total_flux_dev(ph, u, gq, f, CURV || SURF);
                 else ok &= total_flux(ph, u, gq, f);
             } else {
                 ok &= total_flux(ph, u, gq, f);
@@ -1173,14 +1193,19 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
                 if (dev) {
                     float sw;
                     ok &= isL ? common_flux_dev(ph, uo, up, fvo, fvp, nL, F, sw) : common_flux_dev(ph, up, uo, fvp, fvo, nL, F, sw);
-                    // mass flux in float-float: 1/2 (mL - mR) + (s/2 + tau)(rho_L - rho_R),
-                    // mX = own-normal n.(rho v)
-                    const ff mo = a.MF[og], mp = a.MF[pg];
-                    const ff mL = isL ? mo : mp, mR = isL ? mp : mo;
-                    const float rL = isL ? uo[0] : up[0], rR = isL ? up[0] : uo[0];
-                    const ff Fr = ff_add(ff_mul_f(ff_sub(mL, mR), 0.5f), ff_mul_f(two_sum(rL, -rR), 0.5f * sw + ph.tau));
-                    const ff mag = a.fnrm64[(e * 6 + f) * 4 + 3];
-                    s_dff[s] = isL ? ff_mul(mag, Fr) : ff_neg(ff_mul(mag, Fr));
+                    if constexpr (CURV) {
+                        // curved elements: the mass equation runs through the FP32 flux path
+                        F[0] = isL ? common_mass_flux_dev(ph, uo, up, nL, sw) : common_mass_flux_dev(ph, up, uo, nL, sw);
+                    } else {
+                        // mass flux in float-float: 1/2 (mL - mR) + (s/2 + tau)(rho_L - rho_R),
+                        // mX = own-normal n.(rho v)
+                        const ff mo = a.MF[og], mp = a.MF[pg];
+                        const ff mL = isL ? mo : mp, mR = isL ? mp : mo;
+                        const float rL = isL ? uo[0] : up[0], rR = isL ? up[0] : uo[0];
+                        const ff Fr = ff_add(ff_mul_f(ff_sub(mL, mR), 0.5f), ff_mul_f(two_sum(rL, -rR), 0.5f * sw + ph.tau));
+                        const ff mag = a.fnrm64[(e * 6 + f) * 4 + 3];
+                        s_dff[s] = isL ? ff_mul(mag, Fr) : ff_neg(ff_mul(mag, Fr));
+                    }
                 } else {
                     ok &= isL ? common_flux(ph, uo, up, fvo, fvp, nL, F) : common_flux(ph, up, uo, fvp, fvo, nL, F);
                 }
@@ -1207,6 +1232,28 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
                 const T sc = CURV ? T(-1) / a.mu[(e * NU + z) * 10 + 9] : idet;
                 if (a.rkstage == 0) R[it] = v * sc;
                 else rk_fold(a, elem_u0(a, e, NU) + it, v * sc);
+            }
+        } else if constexpr (std::is_same<T, float>::value && CURV) {
+            // low-Mach form on curved elements: every variable in FP32, then R_E = R_(E - H0 rho) + H0 R_rho
+            for (int z = threadIdx.x; z < NU; z += NT) {
+                const int i = z % N, j = (z / N) % N, k = z / (N * N);
+                const T sc = T(-1) / a.mu[(e * NU + z) * 10 + 9];
+                float out[5];
+#pragma unroll
+                for (int alpha = 0; alpha < 5; alpha++) {
+                    const T *D = s_d + alpha * NF;
+                    T v = R[alpha * NU + z];
+                    v += op.liftL[i] * D[0 * N * N + j + N * k] + op.liftR[i] * D[1 * N * N + j + N * k];
+                    v += op.liftL[j] * D[2 * N * N + i + N * k] + op.liftR[j] * D[3 * N * N + i + N * k];
+                    v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
+                    out[alpha] = v * sc;
+                }
+                out[4] += ph.H0 * out[0];
+#pragma unroll
+                for (int alpha = 0; alpha < 5; alpha++) {
+                    if (a.rkstage == 0) R[alpha * NU + z] = out[alpha];
+                    else rk_fold(a, elem_u0(a, e, NU) + alpha * NU + z, out[alpha]);
+                }
             }
         } else if constexpr (std::is_same<T, float>::value) {
             // low-Mach form: R_rho in float-float, R_E = R_(E - H0 rho) + H0 R_rho
@@ -1275,7 +1322,18 @@ __global__ void __launch_bounds__(128) k_surf_pair(HexArgs<T> a)
         face_nrm<T, T>(a.fnrm, eL, fL, n, magL);
         face_nrm<T, T>(a.fnrm, eR, fR, nR, magR);
         T F[5];
-        ok &= common_flux(ph, uL, uR, fvL, fvR, n, F);
+        bool dev = false;
+        if constexpr (std::is_same<T, float>::value) dev = ph.dev != 0;
+        if (dev) {
+            if constexpr (std::is_same<T, float>::value) {
+                // low-Mach form: deviation states, reduced energy; the mass in FP32 here
+                float sw;
+                ok &= common_flux_dev(ph, uL, uR, fvL, fvR, n, F, sw);
+                F[0] = common_mass_flux_dev(ph, uL, uR, n, sw);
+            }
+        } else {
+            ok &= common_flux(ph, uL, uR, fvL, fvR, n, F);
+        }
 #pragma unroll
         for (int k = 0; k < 5; k++) {
             a.DQ[k * a.nqf + gl] = magL * F[k];
@@ -1321,15 +1379,41 @@ __global__ void __launch_bounds__(NT) k_surf_lift(HexArgs<T> a)
         __syncthreads();
         T *R = a.R + elem_u0(a, e, NU);
         const T idet = g.nidet;
-        for (int it = threadIdx.x; it < 5 * NU; it += NT) {
-            const int alpha = it / NU, z = it % NU, i = z % N, j = (z / N) % N, k = z / (N * N);
-            const T *D = s_d + alpha * NF;
-            T v = R[it];
-            v += op.liftL[i] * D[0 * N * N + j + N * k] + op.liftR[i] * D[1 * N * N + j + N * k];
-            v += op.liftL[j] * D[2 * N * N + i + N * k] + op.liftR[j] * D[3 * N * N + i + N * k];
-            v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
-            if (a.rkstage == 0) R[it] = v * idet;
-            else rk_fold(a, elem_u0(a, e, NU) + it, v * idet);
+        bool dev = false;
+        if constexpr (std::is_same<T, float>::value) dev = elem_phys(a, e).dev != 0;
+        if (!dev) {
+            for (int it = threadIdx.x; it < 5 * NU; it += NT) {
+                const int alpha = it / NU, z = it % NU, i = z % N, j = (z / N) % N, k = z / (N * N);
+                const T *D = s_d + alpha * NF;
+                T v = R[it];
+                v += op.liftL[i] * D[0 * N * N + j + N * k] + op.liftR[i] * D[1 * N * N + j + N * k];
+                v += op.liftL[j] * D[2 * N * N + i + N * k] + op.liftR[j] * D[3 * N * N + i + N * k];
+                v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
+                if (a.rkstage == 0) R[it] = v * idet;
+                else rk_fold(a, elem_u0(a, e, NU) + it, v * idet);
+            }
+        } else {
+            // low-Mach form: every variable in FP32, then R_E = R_(E - H0 rho) + H0 R_rho
+            const T H0 = elem_phys(a, e).H0;
+            for (int z = threadIdx.x; z < NU; z += NT) {
+                const int i = z % N, j = (z / N) % N, k = z / (N * N);
+                T out[5];
+#pragma unroll
+                for (int alpha = 0; alpha < 5; alpha++) {
+                    const T *D = s_d + alpha * NF;
+                    T v = R[alpha * NU + z];
+                    v += op.liftL[i] * D[0 * N * N + j + N * k] + op.liftR[i] * D[1 * N * N + j + N * k];
+                    v += op.liftL[j] * D[2 * N * N + i + N * k] + op.liftR[j] * D[3 * N * N + i + N * k];
+                    v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
+                    out[alpha] = v * idet;
+                }
+                out[4] += H0 * out[0];
+#pragma unroll
+                for (int alpha = 0; alpha < 5; alpha++) {
+                    if (a.rkstage == 0) R[alpha * NU + z] = out[alpha];
+                    else rk_fold(a, elem_u0(a, e, NU) + alpha * NU + z, out[alpha]);
+                }
+            }
         }
         __syncthreads();
     }

@@ -125,9 +125,12 @@ __device__ __forceinline__ void flag_status(int *status, bool ok)
 // by the callers, and R_E = R_(E - H0 rho) + H0 R_rho. All of this is exact in exact arithmetic.
 // -------------------------------------------------------------------------------------------------
 
-// Fluxes f[d][a] of (unused, rho v, E - H0 rho) from the deviations w and the physical gradient g
-// (gradients of deviations equal gradients of the conserved variables).
-__device__ __forceinline__ bool total_flux_dev(const Phys<float> &ph, const float *w, const float (*g)[3], float (*f)[5])
+// Fluxes f[d][a] of (rho, rho v, E - H0 rho) from the deviations w and the physical gradient g
+// (gradients of deviations equal gradients of the conserved variables). The mass flux f[d][0] = rho v
+// is written only with `mass` (elements whose mass equation runs through the FP32 flux path);
+// otherwise it is 0 and the float-float mass channel carries it.
+__device__ __forceinline__ bool total_flux_dev(const Phys<float> &ph, const float *w, const float (*g)[3], float (*f)[5],
+                                               bool mass = false)
 {
     const float rho = ph.rref + w[0], ir = 1.0f / rho;
     const float v[3] = {w[1] * ir, w[2] * ir, w[3] * ir};
@@ -140,7 +143,7 @@ __device__ __forceinline__ bool total_flux_dev(const Phys<float> &ph, const floa
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         const float phi = hr * ((g[4][d] - er * g[0][d]) - (v[0] * rw[0][d] + v[1] * rw[1][d] + v[2] * rw[2][d]));
-        f[d][0] = 0.0f;
+        f[d][0] = mass ? w[1 + d] : 0.0f;
         f[d][1] = w[1] * v[d] + (d == 0 ? pd : 0.0f) - tau[0][d];
         f[d][2] = w[2] * v[d] + (d == 1 ? pd : 0.0f) - tau[1][d];
         f[d][3] = w[3] * v[d] + (d == 2 ? pd : 0.0f) - tau[2][d];
@@ -179,4 +182,15 @@ __device__ __forceinline__ bool common_flux_dev(const Phys<float> &ph, const flo
     for (int a = 1; a < 5; a++)
         F[a] = 0.5f * (fnL[a] + fnR[a]) + 0.5f * s * du[a] - (wl * fvL[a - 1] - wr * fvR[a - 1]) + ph.tau * du[a];
     return pL > 0.0f && pR > 0.0f && rL > 0.0f && rR > 0.0f && isfinite(s);
+}
+
+// The common normal mass flux in FP32 from deviation states (the Rusanov and penalty terms of
+// common_flux; the mass has no viscous flux), with the wave speed s returned by common_flux_dev:
+// 1/2 nL.(rho v_L + rho v_R) + (s/2 + tau)(rho_L - rho_R).
+__device__ __forceinline__ float common_mass_flux_dev(const Phys<float> &ph, const float *wL, const float *wR,
+                                                      const float *n, float s)
+{
+    const float mL = wL[1] * n[0] + wL[2] * n[1] + wL[3] * n[2], mR = wR[1] * n[0] + wR[2] * n[1] + wR[3] * n[2];
+    const float du = wL[0] - wR[0];
+    return 0.5f * (mL + mR) + 0.5f * s * du + ph.tau * du;
 }

@@ -666,9 +666,19 @@ def test_full_anti_aliasing_matches_oracle(meshname, N, p):
     err = rel_linf(Rd.cpu().numpy(), Ro, nu)
     print(f"full AA {meshname} N={N} p={p}: fp64 {err}")
     assert err.max() <= (1e-12 if N < 48 else 2e-12), err
+    U32 = U.astype(np.float32)
+    Ro32 = o.rhs(U32.astype(np.float64))
+    if N == 48:
+        # the benchmark grid: the low-Mach FP32 form, every element compared
+        mlm = fr.FRMesh(mesh, fr.make_params(p=p, prec="fp32", p_ref=p0, rho_ref=1.0, surface_aa=True))
+        Ud = torch.from_numpy(U32).cuda()
+        Rd = torch.empty_like(Ud)
+        mlm.rhs(Ud, Rd)
+        mlm.sync_status()
+        elm = rel_linf(Rd.cpu().numpy().astype(np.float64), Ro32, nu)
+        print(f"full AA {meshname} N={N} p={p}: fp32 low-Mach {elm}")
+        assert elm.max() <= 2e-5, elm
     if N < 48:
-        U32 = U.astype(np.float32)
-        Ro32 = o.rhs(U32.astype(np.float64))
         m32 = fr.FRMesh(mesh, fr.make_params(p=p, prec="fp32", p_ref=p0, surface_aa=True))
         Ud = torch.from_numpy(U32).cuda()
         Rd = torch.empty_like(Ud)
@@ -677,6 +687,13 @@ def test_full_anti_aliasing_matches_oracle(meshname, N, p):
         e32 = rel_linf(Rd.cpu().numpy().astype(np.float64), Ro32, nu)
         print(f"full AA {meshname} N={N} p={p}: fp32 plain {e32}")
         assert e32.max() <= 1e-3, e32
+        # the low-Mach form: deviation state and reduced energy, the mass through the FP32 flux path
+        mlm = fr.FRMesh(mesh, fr.make_params(p=p, prec="fp32", p_ref=p0, rho_ref=1.0, surface_aa=True))
+        mlm.rhs(Ud, Rd)
+        mlm.sync_status()
+        elm = rel_linf(Rd.cpu().numpy().astype(np.float64), Ro32, nu)
+        print(f"full AA {meshname} N={N} p={p}: fp32 low-Mach {elm}")
+        assert elm.max() <= 2e-5, elm
 
 
 def test_full_anti_aliasing_rk4_matches_oracle():
@@ -907,10 +924,37 @@ def test_curved_rhs_fp64_matches_oracle(N, amp, p, pref, form):
     assert err.max() <= 1e-12, err
 
 
+def test_curved_48cubed_fp64_and_lowmach_fp32():
+    """The 48^3 curved benchmark box (110,592 trilinear hexahedra), every element compared with the
+    oracle: FP64 to 2e-12 (as for the other 48^3 grids) and the low-Mach FP32 form to 2e-5."""
+    mesh = W.curved_box_mesh(48)
+    p0 = W.tgv_p0()
+    o = O.Oracle(mesh, 3, 5, threads=NCPU, p_ref=p0)
+    U = W.tgv_state(o.sol_coords(), [(48 ** 3, 64)], perturb=1e-3)
+    m = fr.FRMesh(mesh, fr.make_params(p=3, p_ref=p0))
+    Ud = torch.from_numpy(U).cuda()
+    Rd = torch.empty_like(Ud)
+    m.rhs(Ud, Rd)
+    m.sync_status()
+    err = rel_linf(Rd.cpu().numpy(), o.rhs(U), 64)
+    m.close()
+    U32 = U.astype(np.float32)
+    Ro32 = o.rhs(U32.astype(np.float64))
+    m32 = fr.FRMesh(mesh, fr.make_params(p=3, prec="fp32", p_ref=p0, rho_ref=1.0))
+    Ud = torch.from_numpy(U32).cuda()
+    Rd = torch.empty_like(Ud)
+    m32.rhs(Ud, Rd)
+    m32.sync_status()
+    e32 = rel_linf(Rd.cpu().numpy().astype(np.float64), Ro32, 64)
+    print(f"curved 48^3: fp64 {err.max():.3e}, fp32 low-Mach {e32}")
+    assert err.max() <= 2e-12, err
+    assert e32.max() <= 2e-5, e32
+
+
 def test_curved_rk4_diagnostics_and_fp32():
     """RK4 (both forms) and the diagnostics (weights W det J at each solution point) on the curved
-    4^3 box against the oracle; the plain FP32 form (both forms) against the oracle on the
-    FP32-rounded input."""
+    4^3 box against the oracle; the plain FP32 form (both forms) and the low-Mach FP32 form (fused;
+    RHS within 2e-5, and 5 RK4 steps) against the oracle on the FP32-rounded input."""
     mesh = W.curved_box_mesh(4)
     p0 = W.tgv_p0()
     o = O.Oracle(mesh, 3, 5, threads=NCPU, p_ref=p0)
@@ -941,11 +985,22 @@ def test_curved_rk4_diagnostics_and_fp32():
         err = rel_linf(Rd.cpu().numpy().astype(np.float64), Ro, 64)
         print(f"curved fp32 {form}: {err}")
         assert err.max() <= 5e-5, err
-    # the low-Mach FP32 form is not built for curved elements
+    # the low-Mach FP32 form on curved elements: deviation state and reduced energy, the mass
+    # through the FP32 flux path (the metric varies over the element)
     m32 = fr.FRMesh(mesh, fr.make_params(p=3, prec="fp32", p_ref=p0, rho_ref=1.0))
-    with pytest.raises(fr.FRError) as e:
-        m32.rhs(Ud, Rd)
-    assert e.value.status == fr.FR_EUNSUPPORTED
+    Ud = torch.from_numpy(U32).cuda()
+    Rd = torch.empty_like(Ud)
+    m32.rhs(Ud, Rd)
+    m32.sync_status()
+    err = rel_linf(Rd.cpu().numpy().astype(np.float64), Ro, 64)
+    print(f"curved fp32 low-Mach fused: {err}")
+    assert err.max() <= 2e-5, err
+    Ul = torch.from_numpy(U).cuda()
+    m32.rk4_step(Ul, 1e-3, 5)
+    m32.sync_status()
+    drl = np.abs(Ul.cpu().numpy() - Uo).max() / np.abs(Uo).max()
+    print(f"curved fp32 low-Mach RK4 (5 steps) vs oracle: {drl:.3e}")
+    assert drl <= 1e-6, drl
     # the fused RK4 (graph-replayed, stage update folded into the interface kernel)
     m = fr.FRMesh(mesh, fr.make_params(p=3, p_ref=p0))
     Ud = torch.from_numpy(U).cuda()
