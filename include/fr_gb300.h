@@ -187,7 +187,9 @@ fr_status fr_rk4_step_host(fr_mesh *m, void *U_host, double dt, int nsteps, void
  * the mixed forms without hexahedral tensor cores) at p = 3 with flux anti-aliasing on affine
  * elements also 3, 4 = eight elements per CTA of 160 threads, each sum-factorised operator applied
  * to a whole field by one thread from registers (one CTA per SM with up to 255 registers, or two).
- * chosen[i] (n_chosen entries, may be NULL) receives the shape index of group i. Shapes 0, 1 and 2
+ * chosen[i] (n_chosen entries, may be NULL) receives the shape index of group i. Where the groups can
+ * share one launch per phase (fr_set_merged), it also times a whole RHS both ways and keeps the faster
+ * (fr_mesh_info reports the launches per RHS). Shapes 0, 1 and 2
  * evaluate each output with the same operations (results do not depend on the choice among them);
  * shapes 3 and 4 sum the projection's 1D factors in another order (the factors commute), so FP32
  * results then differ at the FP32 rounding level. Synchronises the stream. */
@@ -200,6 +202,18 @@ fr_status fr_autotune(fr_mesh *m, const void *U_dev, void *R_dev, int *chosen, i
  * an earlier run); FR_EUNSUPPORTED for a shape the group cannot run. */
 fr_status fr_group_info(const fr_mesh *m, int group, long long *info);
 fr_status fr_set_group_shape(fr_mesh *m, int group, int shape);
+
+/* on = 1: one launch per phase over all the handle's element groups (hexahedra p = 3 and 4 and prisms,
+ * flux anti-aliasing on the CUDA cores, affine elements, 2 to 4 groups; else FR_EUNSUPPORTED): three
+ * launches per RHS whatever the number of instances, element types and orders, each CTA taking its
+ * share of every group in turn. The kernel's registers and shared memory are those of its largest
+ * group, so it can run fewer CTAs per SM than the per-group launches (on = 0, the default);
+ * fr_autotune times both on the caller's state and keeps the faster. Results are bit for bit those of
+ * the per-group launches, except on FP64 hexahedral-only handles, whose per-group launches evaluate
+ * each interface pair once with the L side's normal while the merged launch evaluates each side with
+ * its own: where the two normals are negatives only to the last bit (sheared meshes) the results agree
+ * to rounding. Recaptures the RK4 graph. */
+fr_status fr_set_merged(fr_mesh *m, int on);
 
 /* Sets the volume-kernel launch shape (0..5, as for fr_autotune) of every hexahedral group;
  * FR_EUNSUPPORTED if a group cannot run it. Takes effect at the next launch (recaptures the RK4 graph). */

@@ -134,6 +134,7 @@ struct fr_mesh {
     cudaStream_t graph_stream = nullptr;
     int graph_form = -1;
     int hex_tc = 0;                      // mixed forms: hexahedral plane contractions on the tensor cores
+    int merged = 0;                      // one launch per phase over all groups (fr_set_merged, fr_autotune)
     int dense_tc = 0;                    // mixed forms: tetrahedral / pyramidal interpolation on the tensor cores
     // surface-flux anti-aliasing: face quadrature points (m x m per hex face) as interface points
     bool surf = false;
@@ -1578,6 +1579,23 @@ static fr_status post_status(fr_mesh *m, cudaStream_t s)
     return FR_OK;
 }
 
+// The groups can share one launch per phase: two to FR_MULTI_MAX groups of hexahedra (p = 3 or 4)
+// and prisms with flux anti-aliasing on the CUDA cores (no tensor-core split products, no surface-flux
+// anti-aliasing, affine elements).
+static bool can_merge(const fr_mesh *m)
+{
+    if (m->form != FR_FUSED || m->surf || m->curved || m->groups.size() < 2 || m->groups.size() > FR_MULTI_MAX)
+        return false;
+    for (const Group &g : m->groups) {
+        const Block &b = m->blocks[g.blks[0]];
+        if (b.m != b.p + 2) return false;
+        if (b.type == 0 && (b.p < 3 || b.p > 4 || (m->prec >= FR_MIXED_BF16 && m->hex_tc))) return false;
+        if (b.type == 1 && m->prec >= FR_MIXED_BF16) return false;   // the mixed forms' prisms use the tensor cores
+        if (b.type > 1) return false;
+    }
+    return true;
+}
+
 // RK4 stage folded into the fused interface kernel (stage < 0: plain RHS).
 struct RkFold {
     int stage = -1;
@@ -1593,7 +1611,39 @@ static fr_status rhs_impl(fr_mesh *m, const void *U, void *R, cudaStream_t s, co
     if (m->nparts > 1 && (m->form != FR_FUSED || only < 0))
         return fail(FR_EUNSUPPORTED, "a partitioned mesh runs the fused phases one at a time (fr_rhs_phase) with "
                                      "halo exchanges between them");
-    if (m->form == FR_FUSED) {
+    if (m->form == FR_FUSED && m->merged && can_merge(m)) {
+        // one launch per phase over every group (each side evaluates its own points' common flux)
+        for (int ph = 0; ph < 3; ph++) {
+            if (only >= 0 && ph != only) continue;
+            TimeScope ts(m, ph, s);
+            MultiArgs<T> ma{};
+            ma.ng = (int)m->groups.size();
+            ma.pops = reinterpret_cast<const PriOps<T> *>(m->d_priops);
+            ma.pff = reinterpret_cast<const PriOpsFF *>(m->d_priops64);
+            for (int gi = 0; gi < ma.ng; gi++) {
+                const Group &gr = m->groups[(size_t)gi];
+                const Block &b = m->blocks[gr.blks[0]];
+                HexArgs<T> a = make_args<T>(m, b, U, R);
+                if (gr.blks.size() > 1) {
+                    a.ne = gr.ne; a.u0 = 0; a.f0 = 0;
+                    a.geo = reinterpret_cast<const Geo<T> *>(gr.d_geo);
+                    a.eu0 = gr.d_eu0; a.ef0 = gr.d_ef0; a.eph = gr.d_eph;
+                    if (m->lowmach) a.geo64 = reinterpret_cast<const GeoLM *>(gr.d_geo64);
+                    a.fnrm = reinterpret_cast<const T *>(gr.d_fnrm);
+                    a.fnrm64 = reinterpret_cast<const ff *>(gr.d_fnrm64);
+                    a.phtab = reinterpret_cast<const Phys<T> *>(gr.d_phtab);
+                }
+                a.tcmode = 0;
+                if (ph == 2 && rk.stage >= 0) {
+                    a.rkstage = rk.stage + 1; a.rkdt = rk.dt; a.rkU = rk.U; a.rkacc = rk.acc;
+                    a.rkus = reinterpret_cast<T *>(rk.us);
+                }
+                ma.kind[gi] = b.type == 1 ? 1 : b.p;
+                ma.a[gi] = a;
+            }
+            if (multi_phase<T>(ph, ma, s)) return fail(FR_ECUDA, "merged phase %d launch: %s", ph, cudaGetErrorString(cudaGetLastError()));
+        }
+    } else if (m->form == FR_FUSED) {
         static const int plain[3] = {0, 1, 2}, split[4] = {0, 1, 3, 4};
         const int *phases = m->split_c ? split : plain;
         int nph = m->split_c ? 4 : 3;
@@ -1679,6 +1729,17 @@ static int volume_shapes(const fr_mesh *m, const Block &b)
     const bool b32 = m->prec != FR_FP64 && b.p == 3 && b.m == b.p + 2 && !m->surf && !m->curved &&
                      (m->prec == FR_FP32 || !m->hex_tc);
     return b32 ? 6 : 3;
+}
+
+extern "C" fr_status fr_set_merged(fr_mesh *m, int on)
+{
+    if (!m) return fail(FR_EINVAL, "null handle");
+    if (on && !can_merge(m))
+        return fail(FR_EUNSUPPORTED, "one launch per phase needs 2 to %d groups of hexahedra (p = 3, 4) and prisms "
+                                     "on the CUDA cores, flux anti-aliasing, affine elements", FR_MULTI_MAX);
+    m->merged = on != 0;
+    if (m->graph) { cudaGraphExecDestroy(m->graph); m->graph = nullptr; }
+    return FR_OK;
 }
 
 extern "C" fr_status fr_set_volume_shape(fr_mesh *m, int shape)
@@ -1780,6 +1841,21 @@ static fr_status autotune_impl(fr_mesh *m, const void *U, void *R, cudaStream_t 
         }
         gr.variant = bestv;
         chosen[gi++] = bestv;
+    }
+    if (can_merge(m)) {
+        // whole RHS with per-group launches against one launch per phase over all groups
+        float t[2] = {0.f, 0.f};
+        for (int mg = 0; mg < 2; mg++) {
+            m->merged = mg;
+            fr_status r = rhs_impl<T>(m, U, R, s);   // warm-up
+            if (r) { cudaEventDestroy(e0); cudaEventDestroy(e1); return r; }
+            CU(cudaEventRecord(e0, s));
+            for (int rep = 0; rep < 3; rep++) rhs_impl<T>(m, U, R, s);
+            CU(cudaEventRecord(e1, s));
+            CU(cudaEventSynchronize(e1));
+            CU(cudaEventElapsedTime(&t[mg], e0, e1));
+        }
+        m->merged = t[1] < t[0];
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -2054,7 +2130,7 @@ extern "C" fr_status fr_mesh_info(const fr_mesh *m, long long *info)
 {
     if (!m || !info) return fail(FR_EINVAL, "null argument");
     info[0] = m->ne; info[1] = m->nU; info[2] = m->nfpt; info[3] = m->npair; info[4] = (long long)m->inst.size();
-    info[5] = m->form == FR_FUSED ? (m->split_c ? 4 : 3) * (long long)m->groups.size() : 13;
+    info[5] = m->form != FR_FUSED ? 13 : (m->merged && can_merge(m)) ? 3 : (m->split_c ? 4 : 3) * (long long)m->groups.size();
     info[6] = m->bytes;
     return FR_OK;
 }

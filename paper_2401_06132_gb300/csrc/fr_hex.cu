@@ -19,6 +19,7 @@
 #include "fr_internal.h"
 #include "fr_physics.cuh"
 #include "fr_tcgen05.cuh"
+#include "fr_pri_body.cuh"   // the prism phase bodies, for the launches that serve several groups
 
 __constant__ HexOps<double> c_hex64[3];  // slot p - 2
 __constant__ HexOps<float> c_hex32[3];
@@ -179,12 +180,12 @@ __global__ void __launch_bounds__(256) k_disu(HexArgs<T> a)
 // memory with coalesced loads (each element's 5 x n^3 values are contiguous), then every thread
 // writes one flux-point value; consecutive threads write consecutive flux points of one variable.
 template <typename T, int P, int EB, int NT>
-__global__ void __launch_bounds__(NT) k_disu_blk(HexArgs<T> a)
+__device__ __forceinline__ void disu_blk_body(const HexArgs<T> &a, long long first, long long stride)
 {
     constexpr int N = P + 1, NU = N * N * N, NF = 6 * N * N;
     __shared__ T s_u[EB * FR_NV * NU];
     const HexOps<T> &op = OPS<T>(P - 2);
-    for (long long e0 = (long long)blockIdx.x * EB; e0 < a.ne; e0 += (long long)gridDim.x * EB) {
+    for (long long e0 = (long long)first * EB; e0 < a.ne; e0 += (long long)stride * EB) {
         const int nb = (int)((a.ne - e0) < EB ? (a.ne - e0) : EB);
         {
             bool blk_ok = true;
@@ -253,6 +254,12 @@ __global__ void __launch_bounds__(NT) k_disu_blk(HexArgs<T> a)
         }
         __syncthreads();
     }
+}
+
+template <typename T, int P, int EB, int NT>
+__global__ void __launch_bounds__(NT) k_disu_blk(HexArgs<T> a)
+{
+    disu_blk_body<T, P, EB, NT>(a, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -570,7 +577,7 @@ __device__ __forceinline__ void project_5(const HexOps<T> &op, const T *src, T *
 }
 
 template <typename T, int P, int NT, int TCM = 0, bool AA = true, bool SURF = false, bool CURV = false>
-__global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
+__device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long first, long long stride)
 {
     static_assert(AA || TCM == 0, "the collocation form has no interpolation or projection");
     static_assert(!SURF || (AA && TCM == 0), "surface-flux anti-aliasing runs with flux anti-aliasing on the CUDA cores");
@@ -650,7 +657,7 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
         tmem = s_tmem[0];
     }
 
-    for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
+    for (long long e = first; e < a.ne; e += stride) {
         const Geo<T> g = a.geo[e];
         const Phys<T> ph = elem_phys(a, e);
         const T *U = a.U + elem_u0(a, e, NU);
@@ -717,7 +724,7 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
         __syncthreads();
         if constexpr (TMA_U) {
             // prefetch the next element's state into s_c
-            const long long en = e + gridDim.x;
+            const long long en = e + stride;
             bool en_ok = en < a.ne;
 #ifdef FR_DEBUG_BOUNDS
             if (en_ok) {   // the bounds-checking build prefetches only elements inside U
@@ -1152,17 +1159,23 @@ __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
     }
 }
 
+template <typename T, int P, int NT, int TCM = 0, bool AA = true, bool SURF = false, bool CURV = false>
+__global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
+{
+    fused_B_body<T, P, NT, TCM, AA, SURF, CURV>(a, blockIdx.x, gridDim.x);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Fused phase C: comm_flux + tdivtconf + negdivconf per element
 // ---------------------------------------------------------------------------------------------
 template <typename T, int P, int NT, bool CURV = false>
-__global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
+__device__ __forceinline__ void fused_C_body(const HexArgs<T> &a, long long first, long long stride)
 {
     constexpr int N = P + 1, NU = N * N * N, NF = 6 * N * N;
     __shared__ T s_d[5 * NF];
     __shared__ ff s_dff[std::is_same<T, float>::value ? NF : 1];   // low-Mach form: transformed mass flux
     const HexOps<T> &op = OPS<T>(P - 2);
-    for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
+    for (long long e = first; e < a.ne; e += stride) {
         if (!fr_elem_ok(a, e, (P + 1) * (P + 1) * (P + 1), 6 * (P + 1) * (P + 1))) continue;
         const Geo<T> g = a.geo[e];
         const Phys<T> ph = elem_phys(a, e);
@@ -1293,6 +1306,12 @@ __global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
         }
         __syncthreads();
     }
+}
+
+template <typename T, int P, int NT, bool CURV = false>
+__global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
+{
+    fused_C_body<T, P, NT, CURV>(a, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -2340,6 +2359,88 @@ static int fused_phase(int phase, const HexArgs<T> &a, cudaStream_t s, int varia
     }
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
+
+// ---------------------------------------------------------------------------------------------
+// One launch per phase over several element groups (hexahedra p = 3 / 4 and prisms, CUDA cores):
+// every CTA runs each group's phase body on its share of that group's elements in turn. The
+// dynamic shared memory is the largest group's; each body uses it from the start.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_multi_A(MultiArgs<T> ma)
+{
+    for (int g = 0; g < ma.ng; g++) {
+        if (ma.kind[g] == 3) disu_blk_body<T, 3, 8, 256>(ma.a[g], blockIdx.x, gridDim.x);
+        else if (ma.kind[g] == 4) disu_blk_body<T, 4, 8, 256>(ma.a[g], blockIdx.x, gridDim.x);
+        else pri::pri_disu_body<T>(ma.a[g], ma.pops, ma.pff, blockIdx.x, gridDim.x);
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_multi_B(MultiArgs<T> ma)
+{
+    for (int g = 0; g < ma.ng; g++) {
+        if (ma.kind[g] == 3) fused_B_body<T, 3, 128>(ma.a[g], blockIdx.x, gridDim.x);
+        else if (ma.kind[g] == 4) fused_B_body<T, 4, 128>(ma.a[g], blockIdx.x, gridDim.x);
+        else pri::pri_B_body<T, 128, 0>(ma.a[g], ma.pops, ma.pff, blockIdx.x, gridDim.x);
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_multi_C(MultiArgs<T> ma)
+{
+    for (int g = 0; g < ma.ng; g++) {
+        if (ma.kind[g] == 3) fused_C_body<T, 3, 128>(ma.a[g], blockIdx.x, gridDim.x);
+        else if (ma.kind[g] == 4) fused_C_body<T, 4, 128>(ma.a[g], blockIdx.x, gridDim.x);
+        else pri::pri_C_body<T, 128>(ma.a[g], ma.pops, ma.pff, blockIdx.x, gridDim.x);
+        __syncthreads();
+    }
+}
+
+// Dynamic shared memory of the volume bodies: a hexahedral group of order P, and the prism group
+// (its operator table, the element arrays, the 20-field staging buffer of the FP32 interpolation).
+template <typename T>
+static size_t multi_B_smem(const MultiArgs<T> &ma)
+{
+    size_t need = 0;
+    for (int g = 0; g < ma.ng; g++) {
+        size_t v;
+        if (ma.kind[g] == 3) v = HexSmem<T, 3>::SIZE * sizeof(T);
+        else if (ma.kind[g] == 4) v = HexSmem<T, 4>::SIZE * sizeof(T);
+        else v = ((sizeof(PriOps<T>) + 15) / 16) * 16 +
+                 (size_t)(5 * pri::NU + 15 * pri::NU + 5 * pri::NF + 20 * pri::NQ) * sizeof(T) +
+                 (size_t)((sizeof(T) == 4 ? 20 : 5) * pri::NZ * pri::NQT) * sizeof(T);
+        need = v > need ? v : need;
+    }
+    return need;
+}
+
+template <typename T>
+int multi_phase(int phase, const MultiArgs<T> &ma, cudaStream_t s)
+{
+    if (ma.ng < 1 || ma.ng > FR_MULTI_MAX) return -1;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return -1;
+    int occ = 0;
+    if (phase == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_multi_A<T>, 256, 0) != cudaSuccess || occ < 1) return -4;
+        k_multi_A<T><<<nsm * occ, 256, 0, s>>>(ma);
+    } else if (phase == 1) {
+        const size_t smem = multi_B_smem(ma);
+        if (cudaFuncSetAttribute(k_multi_B<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_multi_B<T>, 128, smem) != cudaSuccess || occ < 1) return -4;
+        k_multi_B<T><<<nsm * occ, 128, smem, s>>>(ma);
+    } else {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_multi_C<T>, 128, 0) != cudaSuccess || occ < 1) return -4;
+        k_multi_C<T><<<nsm * occ, 128, 0, s>>>(ma);
+    }
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+template int multi_phase<double>(int, const MultiArgs<double> &, cudaStream_t);
+template int multi_phase<float>(int, const MultiArgs<float> &, cudaStream_t);
 
 template <typename T, int P>
 static int unfused_kernel(int k, const HexArgs<T> &a, cudaStream_t s)

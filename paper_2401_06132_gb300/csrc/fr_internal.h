@@ -358,6 +358,20 @@ __device__ __forceinline__ bool fr_elem_ok(const HexArgs<T> &a, long long e, int
 }
 #endif
 
+// One launch per phase over several element groups (fr_hex.cu): hexahedra p = 3 (kind 3), p = 4
+// (kind 4) and prisms (kind 1), flux anti-aliasing on the CUDA cores; every CTA takes its share of
+// each group in turn (elements first, first + grid, ... of the group).
+#define FR_MULTI_MAX 4
+template <typename T>
+struct MultiArgs {
+    int ng;
+    int kind[FR_MULTI_MAX];
+    HexArgs<T> a[FR_MULTI_MAX];
+    const PriOps<T> *pops;        // prism operator tables (prism groups)
+    const PriOpsFF *pff;
+};
+template <typename T> int multi_phase(int phase, const MultiArgs<T> &ma, cudaStream_t s);
+
 // Launchers (fr_hex.cu). phase: 0 = A (face solution), 1 = B (volume group), 2 = C (interfaces),
 // 3 = C1 (common flux once per pair, into DF), 4 = C2 (lift and scale from DF).
 // variant: launch shape of the volume kernel (0, 1, 2 = 64, 128, 256 threads per element)

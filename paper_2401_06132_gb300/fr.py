@@ -79,6 +79,7 @@ def lib():
             "fr_set_dense_tensor_cores": ([vp, C.c_int], C.c_int),
             "fr_autotune": ([vp, vp, vp, C.POINTER(C.c_int), C.c_int, vp], C.c_int),
             "fr_set_volume_shape": ([vp, C.c_int], C.c_int),
+            "fr_set_merged": ([vp, C.c_int], C.c_int),
             "fr_group_info": ([vp, C.c_int, llp], C.c_int),
             "fr_set_group_shape": ([vp, C.c_int, C.c_int], C.c_int),
             "fr_kernel_times": ([vp, C.POINTER(C.c_double), llp, C.c_int], C.c_int),
@@ -337,6 +338,10 @@ class FRMesh:
         dev = torch.cuda.get_device_name()
         prec = {v: k for k, v in PRECISIONS.items()}[self.prec]
         return [f"{dev}|{prec}|type{g['type']}|p{g['p']}|m{g['m']}" if g["shapes"] > 1 else None for g in self.groups()]
+
+    def set_merged(self, on: bool):
+        """fr_set_merged: one launch per phase over all element groups."""
+        _check(lib().fr_set_merged(self.h, int(bool(on))))
 
     def set_volume_shape(self, shape: int):
         """fr_set_volume_shape: the volume-kernel launch shape of every hexahedral group (0..5)."""

@@ -1298,3 +1298,63 @@ def test_autotuner_choices_persist_in_a_cache(tmp_path):
     assert torch.equal(R1, R2)
     with pytest.raises(fr.FRError):
         fr._check(fr.lib().fr_set_group_shape(m2.h, 0, 7))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_merged_launches_equal_per_group_launches(prec):
+    """One launch per phase over all groups (fr_set_merged): the 4^3 mixed hex/prism grid and
+    hexahedral ensembles mixing p = 3 and p = 4 take three launches per RHS and give the per-group
+    launches' RHS and RK4 steps bit for bit (low-Mach form in FP32). FP64 hexahedral handles launched
+    per group evaluate each interface pair once with the L side's normal, the merged launch each side
+    with its own: on a sheared mesh the two elements' normals are negatives of each other only to the
+    last bit, so there the two agree to rounding (1e-14) instead of bit for bit. The autotuner keeps
+    one of the two forms."""
+    p0 = W.tgv_p0()
+    cases = [([W.mixed_box_mesh(4)], [fr.make_params(p=3, prec=prec, p_ref=p0, rho_ref=1.0)], True),
+             ([W.box_hex_mesh(3), W.box_hex_mesh(2), W.box_hex_mesh(4)],
+              [fr.make_params(p=3, prec=prec, p_ref=p0, rho_ref=1.0),
+               fr.make_params(p=4, prec=prec, p_ref=W.tgv_p0(mach=0.05), rho_ref=1.0),
+               fr.make_params(p=3, prec=prec, p_ref=p0, rho_ref=1.0)], True),
+             ([W.sheared_box_mesh(3), W.box_hex_mesh(2)],
+              [fr.make_params(p=3, prec=prec, p_ref=p0, rho_ref=1.0),
+               fr.make_params(p=4, prec=prec, p_ref=p0, rho_ref=1.0)], prec == "fp32")]
+    for meshes, params, bitwise in cases:
+        m = fr.FRMesh(meshes, params)
+        xyz = m.sol_coords()
+        off = m.instance_offsets()
+        parts = []
+        for i, mesh in enumerate(meshes):
+            blocks = [(mesh["hex_v"].shape[0], (params[i].p + 1) ** 3)]
+            if mesh["pri_v"].shape[0]:
+                blocks.append((mesh["pri_v"].shape[0], 40))
+            parts.append(W.tgv_state(xyz[off[i] // 5:off[i + 1] // 5], blocks, perturb=1e-2))
+        U0 = np.concatenate(parts)
+        Uin = torch.from_numpy(U0.astype(np.float64 if prec == "fp64" else np.float32)).cuda()
+        per_group = (3 if prec == "fp32" or mesh_has_prisms(meshes) else 4) * len(m.groups())
+        R, Us = {}, {}
+        for merged in (False, True):
+            m.set_merged(merged)
+            assert m.info()["launches_per_rhs"] == (3 if merged else per_group)
+            Rd = torch.empty_like(Uin)
+            m.rhs(Uin, Rd)
+            m.sync_status()
+            R[merged] = Rd.double().cpu().numpy()
+            Ud = torch.from_numpy(U0).cuda()
+            s = torch.cuda.Stream()
+            m.rk4_step(Ud, 1e-3, 3, stream=s)     # graph-replayed
+            m.sync_status(stream=s)
+            Us[merged] = Ud.cpu().numpy()
+        if bitwise:
+            assert np.array_equal(R[False], R[True]) and np.array_equal(Us[False], Us[True])
+        else:
+            assert np.abs(R[False] - R[True]).max() <= 1e-14 * np.abs(R[False]).max()
+            assert np.abs(Us[False] - Us[True]).max() <= 1e-14 * np.abs(Us[False]).max()
+        m.autotune(Uin, torch.empty_like(Uin))
+        assert m.info()["launches_per_rhs"] in (3, per_group)
+    with pytest.raises(fr.FRError) as e:
+        fr.FRMesh(W.box_hex_mesh(2), fr.make_params(p=3, prec=prec)).set_merged(True)   # a single group
+    assert e.value.status == fr.FR_EUNSUPPORTED
+
+
+def mesh_has_prisms(meshes):
+    return any(mm["pri_v"].shape[0] for mm in meshes)
