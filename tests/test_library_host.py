@@ -88,13 +88,13 @@ def test_host_validation_rejects_bad_meshes_before_any_device_work(lib):
     with pytest.raises(fr.FRError) as e:
         _create(W.mixed_box_mesh(2), p=3, nq1d=4)
     assert e.value.status == fr.FR_EUNSUPPORTED and "anti-aliasing" in str(e.value)
-    # surface-flux anti-aliasing: single-instance hexahedral meshes without the low-Mach form
+    # surface-flux anti-aliasing: single-instance hexahedral meshes with m = p + 2
     with pytest.raises(fr.FRError) as e:
         _create(W.mixed_box_mesh(2), p=3, surface_aa=True)
-    assert e.value.status == fr.FR_EUNSUPPORTED
+    assert e.value.status == fr.FR_EUNSUPPORTED and "surface-flux" in str(e.value)
     with pytest.raises(fr.FRError) as e:
-        _create(W.box_hex_mesh(2), p=3, prec="fp32", p_ref=70.0, rho_ref=1.0, surface_aa=True)
-    assert e.value.status == fr.FR_EUNSUPPORTED and "low-Mach" in str(e.value)
+        _create(W.box_hex_mesh(2), p=3, nq1d=4, surface_aa=True)
+    assert e.value.status == fr.FR_EUNSUPPORTED and "surface-flux" in str(e.value)
 
 
 def test_splitmix64_reference_vectors():
