@@ -606,6 +606,11 @@ def run_ours(args, rank, world):
     # FP32 fused: low-Mach form (<= 2e-5 relative RHS error against the FP64 oracle)
     forms["fused_fp32"] = dof * RHS_PER_STEP / (time_rk4(m32, U, ksteps, 2, torch) * 1e-3) / 1e9
     errs["fused_fp32"] = rhs_error(m, m32, U0, eb, torch)
+    # the same with the RK4 stage states and sum formed in FP64 (fr_set_rk_fp64_stages): the cost of
+    # keeping FP64 in the stage arithmetic (its accuracy effect: the 100-step dissipation tests)
+    m32.set_rk_fp64_stages(True)
+    forms["fused_fp32_fp64_stage_sums"] = dof * RHS_PER_STEP / (time_rk4(m32, U, ksteps, 2, torch) * 1e-3) / 1e9
+    m32.set_rk_fp64_stages(False)
     m32.set_form("unfused")   # plain FP32, one kernel per paper kernel
     forms["unfused_fp32"] = dof * RHS_PER_STEP / (time_rk4(m32, U, ksteps, 1, torch) * 1e-3) / 1e9
     errs["unfused_fp32"] = rhs_error(m, m32, U0, eb, torch)

@@ -215,6 +215,14 @@ fr_status fr_set_group_shape(fr_mesh *m, int group, int shape);
  * to rounding. Recaptures the RK4 graph. */
 fr_status fr_set_merged(fr_mesh *m, int on);
 
+/* Reduced precisions (FP32 and the mixed forms): on = 1 forms the RK4 stage states
+ * u_{s+1} = U + c_{s+1} dt k_s and the Runge-Kutta sum sum_s b_s k_s in FP64 from the FP64 master
+ * state (Sec. 3's RK4 with only the RHS evaluations in the reduced precision); on = 0, the default,
+ * forms both in FP32 from fl32(U) and keeps FP64 for the update of U at the end of the step, which
+ * moves about half the bytes per stage. No effect on FP64 handles. Takes effect from the next step
+ * (switch between steps, not between the stages of one); recaptures the RK4 graph. */
+fr_status fr_set_rk_fp64_stages(fr_mesh *m, int on);
+
 /* Sets the volume-kernel launch shape (0..5, as for fr_autotune) of every hexahedral group;
  * FR_EUNSUPPORTED if a group cannot run it. Takes effect at the next launch (recaptures the RK4 graph). */
 fr_status fr_set_volume_shape(fr_mesh *m, int shape);

@@ -135,6 +135,7 @@ struct fr_mesh {
     int graph_form = -1;
     int hex_tc = 0;                      // mixed forms: hexahedral plane contractions on the tensor cores
     int merged = 0;                      // one launch per phase over all groups (fr_set_merged, fr_autotune)
+    int rk_wide = 0;                     // reduced precisions: RK4 stage states and sum in FP64 (fr_set_rk_fp64_stages)
     int dense_tc = 0;                    // mixed forms: tetrahedral / pyramidal interpolation on the tensor cores
     // surface-flux anti-aliasing: face quadrature points (m x m per hex face) as interface points
     bool surf = false;
@@ -1742,6 +1743,14 @@ extern "C" fr_status fr_set_merged(fr_mesh *m, int on)
     return FR_OK;
 }
 
+extern "C" fr_status fr_set_rk_fp64_stages(fr_mesh *m, int on)
+{
+    if (!m) return fail(FR_EINVAL, "null handle");
+    m->rk_wide = on != 0;
+    if (m->graph) { cudaGraphExecDestroy(m->graph); m->graph = nullptr; }
+    return FR_OK;
+}
+
 extern "C" fr_status fr_set_volume_shape(fr_mesh *m, int shape)
 {
     if (!m || shape < 0 || shape > 5) return fail(FR_EINVAL, "bad argument");
@@ -1971,6 +1980,34 @@ __global__ void k_rk_update(double *__restrict__ U, const T *__restrict__ k, flo
     }
 }
 
+// The same steps with the stage arithmetic in FP64 (fr_set_rk_fp64_stages): the stage states
+// u_{s+1} = fl(U + c_{s+1} dt k_s) and the sum acc = sum b_s k_s are formed in FP64 from the FP64
+// master state, as in the FP64 form; only the RHS evaluations run in the reduced precision. At the
+// start of a step the RHS input is fl(U).
+template <typename T>
+__global__ void k_rk_cast(const double *__restrict__ U, T *__restrict__ us, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        us[i] = (T)U[i];
+}
+
+template <typename T>
+__global__ void k_rk_update_wide(double *__restrict__ U, const T *__restrict__ k, double *__restrict__ acc,
+                                 T *__restrict__ us, long long n, double dt, int stage)
+{
+    const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    const double cnext[4] = {0.5, 0.5, 1.0, 0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double kv = (double)k[i];
+        if (stage == 3) {
+            U[i] += dt * (acc[i] + b[3] * kv);
+        } else {
+            acc[i] = (stage == 0 ? 0.0 : acc[i]) + b[stage] * kv;
+            us[i] = (T)(U[i] + cnext[stage] * dt * kv);
+        }
+    }
+}
+
 // One RK4 stage st (0..3) of the step U -> U + dt sum_s b_s k_s, or one phase of it (only = 0, 1, 2:
 // face solution, volume group, interface group with the stage update; only < 0: all of it). The
 // stage's RHS input is U (FP64) or fl32(U) (reduced precisions, split off at the start of stage 0)
@@ -1986,7 +2023,10 @@ static fr_status rk4_enqueue_stage(fr_mesh *m, double *U, double dt, cudaStream_
     float *uhi = m->prec == FR_FP64 ? nullptr : accf + n;
     const void *u0 = U;
     if (m->prec != FR_FP64) {
-        if (st == 0 && only <= 0) k_rk_split<T><<<grid, thr, 0, s>>>(U, uhi, reinterpret_cast<T *>(m->d_rk_us), n);
+        if (st == 0 && only <= 0) {
+            if (m->rk_wide) k_rk_cast<T><<<grid, thr, 0, s>>>(U, reinterpret_cast<T *>(m->d_rk_us), n);
+            else k_rk_split<T><<<grid, thr, 0, s>>>(U, uhi, reinterpret_cast<T *>(m->d_rk_us), n);
+        }
         u0 = m->d_rk_us;
     }
     const void *in = st == 0 ? u0 : m->d_rk_us;
@@ -2009,6 +2049,9 @@ static fr_status rk4_enqueue_stage(fr_mesh *m, double *U, double dt, cudaStream_
     if constexpr (sizeof(T) == 8) {
         k_rk_update64<<<grid, thr, 0, s>>>(U, reinterpret_cast<const double *>(m->d_rk_k), m->d_rk_acc,
                                            reinterpret_cast<double *>(m->d_rk_us), n, dt, st);
+    } else if (m->rk_wide) {
+        k_rk_update_wide<T><<<grid, thr, 0, s>>>(U, reinterpret_cast<const T *>(m->d_rk_k), m->d_rk_acc,
+                                                 reinterpret_cast<T *>(m->d_rk_us), n, dt, st);
     } else {
         const double bs[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0}, cnext[4] = {0.5, 0.5, 1.0, 0.0};
         k_rk_update<T><<<grid, thr, 0, s>>>(U, reinterpret_cast<const T *>(m->d_rk_k), accf, uhi,
@@ -2071,7 +2114,8 @@ static fr_status rk4_buffers(fr_mesh *m)
     size_t ts = tsize(m->prec);
     fr_status st = dalloc(m, &m->d_rk_k, (size_t)m->nU * ts);
     if (!st) st = dalloc(m, &m->d_rk_us, (size_t)m->nU * ts);
-    // FP64: the Runge-Kutta sum; reduced precisions: its FP32 form and fl32(U) (the same bytes)
+    // FP64 (and reduced precisions with FP64 stage arithmetic): the Runge-Kutta sum; reduced
+    // precisions otherwise: its FP32 form and fl32(U) (the same bytes)
     if (!st) st = dalloc(m, (void **)&m->d_rk_acc, (size_t)m->nU * sizeof(double));
     return st;
 }

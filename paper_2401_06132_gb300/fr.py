@@ -80,6 +80,7 @@ def lib():
             "fr_autotune": ([vp, vp, vp, C.POINTER(C.c_int), C.c_int, vp], C.c_int),
             "fr_set_volume_shape": ([vp, C.c_int], C.c_int),
             "fr_set_merged": ([vp, C.c_int], C.c_int),
+            "fr_set_rk_fp64_stages": ([vp, C.c_int], C.c_int),
             "fr_group_info": ([vp, C.c_int, llp], C.c_int),
             "fr_set_group_shape": ([vp, C.c_int, C.c_int], C.c_int),
             "fr_kernel_times": ([vp, C.POINTER(C.c_double), llp, C.c_int], C.c_int),
@@ -342,6 +343,10 @@ class FRMesh:
     def set_merged(self, on: bool):
         """fr_set_merged: one launch per phase over all element groups."""
         _check(lib().fr_set_merged(self.h, int(bool(on))))
+
+    def set_rk_fp64_stages(self, on: bool):
+        """fr_set_rk_fp64_stages: reduced precisions form the RK4 stage states and sum in FP64."""
+        _check(lib().fr_set_rk_fp64_stages(self.h, int(bool(on))))
 
     def set_volume_shape(self, shape: int):
         """fr_set_volume_shape: the volume-kernel launch shape of every hexahedral group (0..5)."""

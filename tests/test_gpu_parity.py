@@ -316,6 +316,44 @@ def test_ke_dissipation_after_100_rk4_steps(prec):
     assert rel <= (1e-9 if prec == "fp64" else 1e-3), rel
 
 
+@pytest.mark.parametrize("prec", ["fp32", "mixed_fp16"])
+def test_rk4_fp64_stage_sums_against_fp32_stage_sums(prec):
+    """The reduced precisions form the RK4 stage states and the Runge-Kutta sum in FP32 from fl32(U)
+    by default, and in FP64 from the FP64 master state with fr_set_rk_fp64_stages; the RHS runs in
+    the reduced precision either way. 8^3 hex p=3 TGV, 100 steps at dt = 1e-3 in the low-Mach form,
+    against the oracle's trajectory: both meet 1e-3 on the final dissipation rate, and what the FP32
+    stage arithmetic itself costs, the difference of the two final states and of their rates, stays
+    at the level of FP32 rounding of the state (1e-5 relative per variable; 1e-4 on the rate)."""
+    mesh = W.box_hex_mesh(8)
+    p0 = W.tgv_p0()
+    o = O.Oracle(mesh, 3, 5, threads=NCPU, p_ref=p0)
+    U = W.tgv_state(o.sol_coords(), [(512, 64)])
+    Uo = o.rk4(U, 1e-3, 100)
+    eps_o = o.diagnostics(Uo, o.rhs(Uo))["eps"]
+    m = fr.FRMesh(mesh, fr.make_params(p=3, prec=prec, p_ref=p0, rho_ref=1.0))
+    m.set_hex_tensor_cores(prec != "fp32")
+    fin = {}
+    for wide in (False, True):
+        m.set_rk_fp64_stages(wide)
+        Ud = torch.from_numpy(U).cuda()
+        m.rk4_step(Ud, 1e-3, 100)
+        m.sync_status()
+        fin[wide] = Ud.cpu().numpy()
+    eps = {w: o.diagnostics(fin[w], o.rhs(fin[w]))["eps"] for w in fin}
+    rel = {w: abs(eps[w] / eps_o - 1.0) for w in eps}
+    # per variable, relative to its largest magnitude (the three momenta to the largest of them: w
+    # starts at zero in the vortex and stays small)
+    A, B = fin[False].reshape(-1, 5, 64), fin[True].reshape(-1, 5, 64)
+    scale = np.abs(B).max(axis=(0, 2))
+    scale[1:4] = scale[1:4].max()
+    dstate = np.abs(A - B).max(axis=(0, 2)) / scale
+    print(f"{prec}: eps oracle {eps_o:.9e}; FP32 stage sums {eps[False]:.9e} (rel {rel[False]:.2e}), "
+          f"FP64 stage sums {eps[True]:.9e} (rel {rel[True]:.2e}); final states differ by {dstate}")
+    assert rel[False] <= 1e-3 and rel[True] <= 1e-3, rel
+    assert abs(eps[True] / eps[False] - 1.0) <= 1e-4
+    assert dstate.max() <= 1e-5, dstate
+
+
 def _rel_linf_blocks(R, Ro, blocks):
     """Per-variable relative L-inf over several element blocks [(n_elem, n_pts), ...]."""
     d = np.zeros(5)
@@ -747,9 +785,10 @@ def test_precision_sweep_ke_dissipation_32cubed_p4():
     e0 = eps_of(torch.from_numpy(U0).cuda())
     assert abs(e0 / gold[0][1] - 1.0) <= 1e-9, (e0, gold[0])
 
-    def final_eps(prec, rho_ref, hex_tc):
+    def final_eps(prec, rho_ref, hex_tc, wide=False):
         m = fr.FRMesh(mesh, fr.make_params(p=p, prec=prec, p_ref=p0, rho_ref=rho_ref))
         m.set_hex_tensor_cores(hex_tc)
+        m.set_rk_fp64_stages(wide)
         Ud = torch.from_numpy(U0).cuda()
         m.rk4_step(Ud, 2e-4, 100)
         m.sync_status()
@@ -758,10 +797,11 @@ def test_precision_sweep_ke_dissipation_32cubed_p4():
 
     ref = gold[100][1]
     res = {}
-    for name, prec, rr, tc in (("fp64", "fp64", 0.0, False), ("fp32_lowmach", "fp32", 1.0, False),
-                               ("fp32_plain", "fp32", 0.0, False), ("mixed_fp16", "mixed_fp16", 1.0, True),
-                               ("mixed_bf16", "mixed_bf16", 1.0, True)):
-        res[name] = abs(final_eps(prec, rr, tc) / ref - 1.0)
+    for name, prec, rr, tc, wide in (("fp64", "fp64", 0.0, False, False), ("fp32_lowmach", "fp32", 1.0, False, False),
+                                     ("fp32_lowmach_fp64_stages", "fp32", 1.0, False, True),
+                                     ("fp32_plain", "fp32", 0.0, False, False), ("mixed_fp16", "mixed_fp16", 1.0, True, False),
+                                     ("mixed_bf16", "mixed_bf16", 1.0, True, False)):
+        res[name] = abs(final_eps(prec, rr, tc, wide) / ref - 1.0)
     print(f"precision sweep 32^3 p=4, eps after 100 steps: oracle {ref:.9e}; relative errors {res}")
     assert res.pop("fp64") <= 1e-9
     for k, v in res.items():
