@@ -727,6 +727,10 @@ static fr_status upload_priops(fr_mesh *m, void **dst)
     fr_status st = dalloc(m, dst, sizeof(o));
     if (st) return st;
     CU(cudaMemcpy(*dst, &o, sizeof(o), cudaMemcpyHostToDevice));
+    if constexpr (sizeof(T) == 4) {
+        // the FP32 volume kernels read the interpolation and projection blocks from constant memory
+        if (pri_set_const_ops(&o) || multi_set_pri_const_ops(&o)) return fail(FR_ECUDA, "prism operator upload failed");
+    }
     return FR_OK;
 }
 

@@ -139,6 +139,19 @@ __device__ __forceinline__ void line_eo(const HexEO<T> &A, const T (&x)[C], T (&
     }
 }
 
+// y = A x along one line for a constant operator with R <= FR_MAXN rows (indices fixed at compile time)
+template <typename T, int R, int C>
+__device__ __forceinline__ void line_rows(const T (&A)[FR_MAXN][FR_MAXM], const T (&x)[C], T (&y)[R])
+{
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        T v = T(0);
+#pragma unroll
+        for (int c = 0; c < C; c++) v += A[r][c] * x[c];
+        y[r] = v;
+    }
+}
+
 template <int N>
 __device__ __forceinline__ void face_line(int f, int local, int &base, int &stride)
 {
@@ -184,7 +197,18 @@ __device__ __forceinline__ void disu_blk_body(const HexArgs<T> &a, long long fir
 {
     constexpr int N = P + 1, NU = N * N * N, NF = 6 * N * N;
     __shared__ T s_u[EB * FR_NV * NU];
-    const HexOps<T> &op = OPS<T>(P - 2);
+    // the trace rows, selected by each flux point's run-time face side, from shared memory (a
+    // constant-memory load is serialised over the distinct addresses of a warp)
+    __shared__ T s_l[2 * N];
+    __shared__ ff s_lff[std::is_same<T, float>::value ? 2 * N : 1];
+    {
+        const HexOps<T> &op = OPS<T>(P - 2);
+        for (int i = threadIdx.x; i < 2 * N; i += NT) {
+            s_l[i] = i < N ? op.lL[i] : op.lR[i - N];
+            if constexpr (std::is_same<T, float>::value) s_lff[i] = i < N ? c_hexff[P - 2].lL[i] : c_hexff[P - 2].lR[i - N];
+        }
+        __syncthreads();
+    }
     for (long long e0 = (long long)first * EB; e0 < a.ne; e0 += (long long)stride * EB) {
         const int nb = (int)((a.ne - e0) < EB ? (a.ne - e0) : EB);
         {
@@ -215,8 +239,7 @@ __device__ __forceinline__ void disu_blk_body(const HexArgs<T> &a, long long fir
             face_line<N>(f, sp % (N * N), base, stride);
             const long long fo = elem_f0(a, e0 + el, NF) + sp;
             if constexpr (std::is_same<T, float>::value) {
-                const HexOpsFF &off = c_hexff[P - 2];
-                const ff *lf = (f & 1) ? off.lR : off.lL;
+                const ff *lf = s_lff + (f & 1) * N;
                 ff v[FR_NV];
 #pragma unroll
                 for (int alpha = 0; alpha < FR_NV; alpha++) {
@@ -241,7 +264,7 @@ __device__ __forceinline__ void disu_blk_body(const HexArgs<T> &a, long long fir
                     a.MF[fo] = mf;
                 }
             } else {
-                const T *l = (f & 1) ? op.lR : op.lL;
+                const T *l = s_l + (f & 1) * N;
 #pragma unroll
                 for (int alpha = 0; alpha < FR_NV; alpha++) {
                     const T *u = s_u + (el * FR_NV + alpha) * NU + base;
@@ -519,6 +542,63 @@ __device__ __forceinline__ void project_div(const HexOps<T> &op, T *src, T *tmp,
 #pragma unroll
                 for (int i = 0; i < N; i++) v[i] += y[i];
             }
+        }
+#pragma unroll
+        for (int i = 0; i < N; i++) R[alpha * NU + i + N * jk] = v[i];
+    }
+}
+
+// FP32: the same with all 15 flux fields per pass. The loops over the three directions are
+// unrolled, so that each sweep's operator (Pj, or Dh Pj along the flux component's own direction)
+// is known at compile time: its coefficients are constant-bank operands of the multiply-adds, not
+// run-time loads from constant memory (one per coefficient and line, serialised over the distinct
+// addresses of a warp).
+template <typename T, int P, int NT>
+__device__ __forceinline__ void project_div_all(const HexOps<T> &op, T *src, T *tmp, T *R)
+{
+    constexpr int N = P + 1, M = P + 2, NQ = M * M * M, NU = N * N * N;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const T(&Z)[FR_MAXN][FR_MAXM] = d == 2 ? op.DP : op.Pj;
+        for (int it = threadIdx.x; it < 5 * M * M; it += NT) {   // z: (alpha, qa qb) -> k
+            const int alpha = it / (M * M), ab = it % (M * M);
+            T u[M], v[N];
+#pragma unroll
+            for (int c = 0; c < M; c++) u[c] = src[(alpha * 3 + d) * NQ + ab + M * M * c];
+            line_rows<T, N, M>(Z, u, v);
+#pragma unroll
+            for (int k = 0; k < N; k++) tmp[(d * 5 + alpha) * M * M * N + ab + M * M * k] = v[k];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const T(&Y)[FR_MAXN][FR_MAXM] = d == 1 ? op.DP : op.Pj;
+        for (int it = threadIdx.x; it < 5 * M * N; it += NT) {   // y: (alpha, qa, k) -> j
+            const int alpha = it / (M * N), r2 = it % (M * N), qa = r2 % M, k = r2 / M;
+            T u[M], v[N];
+#pragma unroll
+            for (int b = 0; b < M; b++) u[b] = tmp[(d * 5 + alpha) * M * M * N + qa + M * b + M * M * k];
+            line_rows<T, N, M>(Y, u, v);
+#pragma unroll
+            for (int j = 0; j < N; j++) src[(alpha * 3 + d) * NQ + qa + M * j + M * N * k] = v[j];   // over the consumed input
+        }
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < 5 * N * N; it += NT) {   // x: (alpha, j, k), sum over d -> i
+        const int alpha = it / (N * N), jk = it % (N * N);
+        T v[N];
+#pragma unroll
+        for (int i = 0; i < N; i++) v[i] = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const T(&X)[FR_MAXN][FR_MAXM] = d == 0 ? op.DP : op.Pj;
+            T u[M], y[N];
+#pragma unroll
+            for (int q = 0; q < M; q++) u[q] = src[(alpha * 3 + d) * NQ + q + M * jk];
+            line_rows<T, N, M>(X, u, y);
+#pragma unroll
+            for (int i = 0; i < N; i++) v[i] += y[i];
         }
 #pragma unroll
         for (int i = 0; i < N; i++) R[alpha * NU + i + N * jk] = v[i];
@@ -1091,7 +1171,8 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
         if constexpr (!AA) {
             // collocation form: the flux already sits at the solution points
         } else if constexpr (TCM == 0) {
-            project_div<T, P, NT, S::WIDE>(op, s_w, s_t2, R);
+            if constexpr (S::WIDE) project_div_all<T, P, NT>(op, s_w, s_t2, R);
+            else project_div<T, P, NT, false>(op, s_w, s_t2, R);
         } else {
             // x-y factor on the tensor cores: row r = f M + c holds flux component f at quadrature
             // level c on the M^2 in-plane points; then the z factor on the CUDA cores
@@ -1174,7 +1255,19 @@ __device__ __forceinline__ void fused_C_body(const HexArgs<T> &a, long long firs
     constexpr int N = P + 1, NU = N * N * N, NF = 6 * N * N;
     __shared__ T s_d[5 * NF];
     __shared__ ff s_dff[std::is_same<T, float>::value ? NF : 1];   // low-Mach form: transformed mass flux
-    const HexOps<T> &op = OPS<T>(P - 2);
+    // the lift rows, read with each solution point's run-time (i, j, k), from shared memory: a
+    // constant-memory load is serialised over the distinct addresses of a warp
+    __shared__ T s_lift[2 * N];                                          // liftL | liftR
+    __shared__ ff s_liftff[std::is_same<T, float>::value ? 2 * N : 1];
+    {
+        const HexOps<T> &op = OPS<T>(P - 2);
+        for (int i = threadIdx.x; i < 2 * N; i += NT) {
+            s_lift[i] = i < N ? op.liftL[i] : op.liftR[i - N];
+            if constexpr (std::is_same<T, float>::value) s_liftff[i] = i < N ? c_hexff[P - 2].liftL[i] : c_hexff[P - 2].liftR[i - N];
+        }
+        __syncthreads();
+    }
+    const T *liftL = s_lift, *liftR = s_lift + N;
     for (long long e = first; e < a.ne; e += stride) {
         if (!fr_elem_ok(a, e, (P + 1) * (P + 1) * (P + 1), 6 * (P + 1) * (P + 1))) continue;
         const Geo<T> g = a.geo[e];
@@ -1238,9 +1331,9 @@ __device__ __forceinline__ void fused_C_body(const HexArgs<T> &a, long long firs
                 const int alpha = it / NU, z = it % NU, i = z % N, j = (z / N) % N, k = z / (N * N);
                 const T *D = s_d + alpha * NF;
                 T v = R[it];
-                v += op.liftL[i] * D[0 * N * N + j + N * k] + op.liftR[i] * D[1 * N * N + j + N * k];
-                v += op.liftL[j] * D[2 * N * N + i + N * k] + op.liftR[j] * D[3 * N * N + i + N * k];
-                v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
+                v += liftL[i] * D[0 * N * N + j + N * k] + liftR[i] * D[1 * N * N + j + N * k];
+                v += liftL[j] * D[2 * N * N + i + N * k] + liftR[j] * D[3 * N * N + i + N * k];
+                v += liftL[k] * D[4 * N * N + i + N * j] + liftR[k] * D[5 * N * N + i + N * j];
                 // curved elements: det J at this solution point
                 const T sc = CURV ? T(-1) / a.mu[(e * NU + z) * 10 + 9] : idet;
                 if (a.rkstage == 0) R[it] = v * sc;
@@ -1256,9 +1349,9 @@ __device__ __forceinline__ void fused_C_body(const HexArgs<T> &a, long long firs
                 for (int alpha = 0; alpha < 5; alpha++) {
                     const T *D = s_d + alpha * NF;
                     T v = R[alpha * NU + z];
-                    v += op.liftL[i] * D[0 * N * N + j + N * k] + op.liftR[i] * D[1 * N * N + j + N * k];
-                    v += op.liftL[j] * D[2 * N * N + i + N * k] + op.liftR[j] * D[3 * N * N + i + N * k];
-                    v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
+                    v += liftL[i] * D[0 * N * N + j + N * k] + liftR[i] * D[1 * N * N + j + N * k];
+                    v += liftL[j] * D[2 * N * N + i + N * k] + liftR[j] * D[3 * N * N + i + N * k];
+                    v += liftL[k] * D[4 * N * N + i + N * j] + liftR[k] * D[5 * N * N + i + N * j];
                     out[alpha] = v * sc;
                 }
                 out[4] += ph.H0 * out[0];
@@ -1270,19 +1363,19 @@ __device__ __forceinline__ void fused_C_body(const HexArgs<T> &a, long long firs
             }
         } else if constexpr (std::is_same<T, float>::value) {
             // low-Mach form: R_rho in float-float, R_E = R_(E - H0 rho) + H0 R_rho
-            const HexOpsFF &off = c_hexff[P - 2];
+            const ff *fliftL = s_liftff, *fliftR = s_liftff + N;
             const ff idet64 = a.geo64[e].idet;
             const ff H0 = ph.H0ff;
             const long long pbase = elem_u0(a, e, NU) / FR_NV;
             for (int z = threadIdx.x; z < NU; z += NT) {
                 const int i = z % N, j = (z / N) % N, k = z / (N * N);
                 ff r = a.RL[pbase + z];
-                r = ff_fma(off.liftL[i], s_dff[0 * N * N + j + N * k], r);
-                r = ff_fma(off.liftR[i], s_dff[1 * N * N + j + N * k], r);
-                r = ff_fma(off.liftL[j], s_dff[2 * N * N + i + N * k], r);
-                r = ff_fma(off.liftR[j], s_dff[3 * N * N + i + N * k], r);
-                r = ff_fma(off.liftL[k], s_dff[4 * N * N + i + N * j], r);
-                r = ff_fma(off.liftR[k], s_dff[5 * N * N + i + N * j], r);
+                r = ff_fma(fliftL[i], s_dff[0 * N * N + j + N * k], r);
+                r = ff_fma(fliftR[i], s_dff[1 * N * N + j + N * k], r);
+                r = ff_fma(fliftL[j], s_dff[2 * N * N + i + N * k], r);
+                r = ff_fma(fliftR[j], s_dff[3 * N * N + i + N * k], r);
+                r = ff_fma(fliftL[k], s_dff[4 * N * N + i + N * j], r);
+                r = ff_fma(fliftR[k], s_dff[5 * N * N + i + N * j], r);
                 const ff Rrho = ff_mul(r, idet64);
                 float out[5];
                 out[0] = Rrho.hi + Rrho.lo;
@@ -1290,9 +1383,9 @@ __device__ __forceinline__ void fused_C_body(const HexArgs<T> &a, long long firs
                 for (int alpha = 1; alpha < 5; alpha++) {
                     const T *D = s_d + alpha * NF;
                     T v = R[alpha * NU + z];
-                    v += op.liftL[i] * D[0 * N * N + j + N * k] + op.liftR[i] * D[1 * N * N + j + N * k];
-                    v += op.liftL[j] * D[2 * N * N + i + N * k] + op.liftR[j] * D[3 * N * N + i + N * k];
-                    v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
+                    v += liftL[i] * D[0 * N * N + j + N * k] + liftR[i] * D[1 * N * N + j + N * k];
+                    v += liftL[j] * D[2 * N * N + i + N * k] + liftR[j] * D[3 * N * N + i + N * k];
+                    v += liftL[k] * D[4 * N * N + i + N * j] + liftR[k] * D[5 * N * N + i + N * j];
                     out[alpha] = v * idet;
                 }
                 const ff e4 = ff_fma(H0, Rrho, ff_of(out[4]));
@@ -1478,7 +1571,13 @@ __global__ void __launch_bounds__(NT) k_lift(HexArgs<T> a)
 {
     constexpr int N = P + 1, NU = N * N * N, NF = 6 * N * N;
     __shared__ T s_d[5 * NF];
-    const HexOps<T> &op = OPS<T>(P - 2);
+    __shared__ T s_lift[2 * N];   // liftL | liftR, read with run-time (i, j, k)
+    {
+        const HexOps<T> &op = OPS<T>(P - 2);
+        for (int i = threadIdx.x; i < 2 * N; i += NT) s_lift[i] = i < N ? op.liftL[i] : op.liftR[i - N];
+        __syncthreads();
+    }
+    const T *liftL = s_lift, *liftR = s_lift + N;
     for (long long e = blockIdx.x; e < a.ne; e += gridDim.x) {
         if (!fr_elem_ok(a, e, (P + 1) * (P + 1) * (P + 1), 6 * (P + 1) * (P + 1))) continue;
         const Geo<T> g = a.geo[e];
@@ -1499,9 +1598,9 @@ __global__ void __launch_bounds__(NT) k_lift(HexArgs<T> a)
             const int alpha = it / NU, z = it % NU, i = z % N, j = (z / N) % N, k = z / (N * N);
             const T *D = s_d + alpha * NF;
             T v = R[it];
-            v += op.liftL[i] * D[0 * N * N + j + N * k] + op.liftR[i] * D[1 * N * N + j + N * k];
-            v += op.liftL[j] * D[2 * N * N + i + N * k] + op.liftR[j] * D[3 * N * N + i + N * k];
-            v += op.liftL[k] * D[4 * N * N + i + N * j] + op.liftR[k] * D[5 * N * N + i + N * j];
+            v += liftL[i] * D[0 * N * N + j + N * k] + liftR[i] * D[1 * N * N + j + N * k];
+            v += liftL[j] * D[2 * N * N + i + N * k] + liftR[j] * D[3 * N * N + i + N * k];
+            v += liftL[k] * D[4 * N * N + i + N * j] + liftR[k] * D[5 * N * N + i + N * j];
             // curved elements: det J at this solution point
             const T sc = CURV ? T(-1) / a.mu[(e * NU + z) * 10 + 9] : idet;
             if (a.rkstage == 0) R[it] = v * sc;
@@ -2365,6 +2464,8 @@ static int fused_phase(int phase, const HexArgs<T> &a, cudaStream_t s, int varia
 // every CTA runs each group's phase body on its share of that group's elements in turn. The
 // dynamic shared memory is the largest group's; each body uses it from the start.
 // ---------------------------------------------------------------------------------------------
+int multi_set_pri_const_ops(const PriOps<float> *h) { return pri::set_const_ops(*h); }
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_multi_A(MultiArgs<T> ma)
 {

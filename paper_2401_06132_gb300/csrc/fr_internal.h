@@ -382,6 +382,10 @@ int hex_upload_ops(int p, int m, const frb::Hex1D &h);
 // Prism kernels (fr_pri.cu); the operator tables are passed by device pointer (opsff: the
 // float-float table of the low-Mach FP32 form's mass channel; null otherwise).
 template <typename T> int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, const PriOpsFF *opsff, cudaStream_t s);
+// The FP32 prism operator table in the constant memory of the current device, for the prism kernels
+// (fr_pri.cu) and the launches that serve several element groups (fr_hex.cu); 0 on success.
+int pri_set_const_ops(const PriOps<float> *h);
+int multi_set_pri_const_ops(const PriOps<float> *h);
 // Dense-element kernels (fr_dense.cu): tetrahedra and pyramids, operator table by device pointer.
 // (opsff: the float-float FP32 table of the low-Mach form's mass channel; null otherwise).
 template <typename T>

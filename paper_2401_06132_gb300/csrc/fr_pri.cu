@@ -55,6 +55,8 @@ int grid_elems(long long ne, int per_sm)
 
 using namespace pri;
 
+int pri_set_const_ops(const PriOps<float> *h) { return pri::set_const_ops(*h); }
+
 template <typename T>
 int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, const PriOpsFF *ops64, cudaStream_t s)
 {

@@ -20,6 +20,16 @@ constexpr int NQ = NQT * MZ;                  // 125
 
 __device__ __forceinline__ int face_of(int s) { return s < 10 ? 0 : s < 20 ? 1 : 2 + (s - 20) / 16; }
 
+// The FP32 operator table in constant memory (one copy per translation unit that includes this
+// file, filled by set_const_ops on each device): read with compile-time indices, its entries are
+// constant-bank operands of the multiply-adds instead of a shared-memory load per coefficient.
+__constant__ PriOps<float> c_pri32;
+
+inline int set_const_ops(const PriOps<float> &h)
+{
+    return cudaMemcpyToSymbol(c_pri32, &h, sizeof(h)) == cudaSuccess ? 0 : -1;
+}
+
 template <typename T>
 __device__ __forceinline__ void pri_normal(const Geo<T> &g, int f, T *n, T &mag)
 {
@@ -246,6 +256,81 @@ __device__ __forceinline__ void pri_interp_all(const PriOps<T> &op, const T *src
     __syncthreads();
 }
 
+// FP32 without tensor cores, all 20 fields: the triangle-plane factor with one thread per (field, z
+// level) line, its 10 values in registers and all 25 quadrature points formed from them, then z with
+// one thread per (field, triangle quadrature point); the operators from the constant-memory table
+// with compile-time indices. The sums run in the same order as pri_interp_all.
+template <int NTH>
+__device__ __forceinline__ void pri_interp_all_c(const float *src, float *tmp, float *dst)
+{
+    for (int it = threadIdx.x; it < 20 * NZ; it += NTH) {   // triangle plane: (f, k)
+        const float *s = src + (it / NZ) * NU + 10 * (it % NZ);
+        float u[NT_];
+#pragma unroll
+        for (int t = 0; t < NT_; t++) u[t] = s[t];
+        float *d = tmp + it * NQT;   // (f NZ + k) NQT + q
+#pragma unroll
+        for (int q = 0; q < NQT; q++) {
+            float v = 0.f;
+#pragma unroll
+            for (int t = 0; t < NT_; t++) v += c_pri32.Bt[q][t] * u[t];
+            d[q] = v;
+        }
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < 20 * NQT; it += NTH) {   // z: (f, q)
+        const int f = it / NQT, q = it % NQT;
+        float u[NZ];
+#pragma unroll
+        for (int k = 0; k < NZ; k++) u[k] = tmp[(f * NZ + k) * NQT + q];
+#pragma unroll
+        for (int c = 0; c < MZ; c++) {
+            float v = 0.f;
+#pragma unroll
+            for (int k = 0; k < NZ; k++) v += c_pri32.Bz[c][k] * u[k];
+            dst[f * NQ + q + NQT * c] = v;
+        }
+    }
+    __syncthreads();
+}
+
+// The projection of the 15 flux fields in the same form: z with one thread per (field, triangle
+// quadrature point), then the triangle plane with one thread per (field, z level) line, its 25
+// values in registers; sums in the order of pri_project_all.
+template <int NTH>
+__device__ __forceinline__ void pri_project_all_c(const float *src, float *tmp, float *dst)
+{
+    for (int it = threadIdx.x; it < 15 * NQT; it += NTH) {   // z: (f, q)
+        const int f = it / NQT, q = it % NQT;
+        float u[MZ];
+#pragma unroll
+        for (int c = 0; c < MZ; c++) u[c] = src[f * NQ + q + NQT * c];
+#pragma unroll
+        for (int k = 0; k < NZ; k++) {
+            float v = 0.f;
+#pragma unroll
+            for (int c = 0; c < MZ; c++) v += c_pri32.Pz[k][c] * u[c];
+            tmp[(f * NZ + k) * NQT + q] = v;
+        }
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < 15 * NZ; it += NTH) {   // triangle plane: (f, k)
+        const float *s = tmp + it * NQT;
+        float u[NQT];
+#pragma unroll
+        for (int q = 0; q < NQT; q++) u[q] = s[q];
+        float *d = dst + (it / NZ) * NU + 10 * (it % NZ);
+#pragma unroll
+        for (int t = 0; t < NT_; t++) {
+            float v = 0.f;
+#pragma unroll
+            for (int q = 0; q < NQT; q++) v += c_pri32.Pt[t][q] * u[q];
+            d[t] = v;
+        }
+    }
+    __syncthreads();
+}
+
 // All 15 flux fields at once (FP32): z then the triangle plane.
 template <typename T, int NTH>
 __device__ __forceinline__ void pri_project_all(const PriOps<T> &op, const T *src, T *tmp, T *dst)
@@ -455,7 +540,7 @@ __device__ __forceinline__ void pri_B_body(const HexArgs<T> &a, const PriOps<T> 
         };
         if constexpr (TCM == 0) viscous_faces();
         if constexpr (TCM == 0 && sizeof(T) == 4) {
-            pri_interp_all<T, NTH>(op, s_u, s_t, s_w);   // s_q follows s_u
+            pri_interp_all_c<NTH>(s_u, s_t, s_w);   // s_q follows s_u
         } else if constexpr (TCM == 0) {
             pri_interp_5<T, NTH>(op, s_u, s_t, s_w);
 #pragma unroll 1
@@ -536,7 +621,7 @@ __device__ __forceinline__ void pri_B_body(const HexArgs<T> &a, const PriOps<T> 
         flag_status(a.status, ok);
         __syncthreads();
         if constexpr (TCM == 0 && sizeof(T) == 4) {
-            pri_project_all<T, NTH>(op, s_w, s_t, s_q);
+            pri_project_all_c<NTH>(s_w, s_t, s_q);
         } else if constexpr (TCM == 0) {
 #pragma unroll 1
             for (int c = 0; c < 3; c++) pri_project_5<T, NTH>(op, s_w + 5 * c * NQ, s_t, s_q + 5 * c * NU);
