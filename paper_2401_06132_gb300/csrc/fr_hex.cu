@@ -1402,7 +1402,7 @@ __device__ __forceinline__ void fused_C_body(const HexArgs<T> &a, long long firs
 }
 
 template <typename T, int P, int NT, bool CURV = false>
-__global__ void __launch_bounds__(NT) k_fused_C(HexArgs<T> a)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 960 / NT : 1) k_fused_C(HexArgs<T> a)
 {
     fused_C_body<T, P, NT, CURV>(a, blockIdx.x, gridDim.x);
 }
@@ -2446,6 +2446,7 @@ static int fused_phase(int phase, const HexArgs<T> &a, cudaStream_t s, int varia
         else launch_B<T, P, 128>(a, s);
     } else if (phase == 2) {
         if (a.mu) k_fused_C<T, P, 128, true><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
+        else if (P == 3) k_fused_C<T, P, 96><<<grid_elems(a.ne, 10), 96, 0, s>>>(a);
         else k_fused_C<T, P, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a);
     } else if (phase == 3) {
         if (a.surf) { if (a.nqlpts > 0) k_surf_pair<T, P><<<grid_for(a.nqlpts, 128), 128, 0, s>>>(a); }

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
 }
 
 template <typename T, int NTH>
-__global__ void __launch_bounds__(NTH) k_pri_C(HexArgs<T> a, const PriOps<T> *gops, const PriOpsFF *opsff)
+__global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 960 / NTH : 1) k_pri_C(HexArgs<T> a, const PriOps<T> *gops, const PriOpsFF *opsff)
 {
     pri_C_body<T, NTH>(a, gops, opsff, blockIdx.x, gridDim.x);
 }
@@ -106,7 +106,8 @@ int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, const 
             k_pri_B<T, NTH, 0><<<grid_elems(a.ne, 8), NTH, smem, s>>>(a, ops, ops64);
         }
     } else {
-        k_pri_C<T, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a, ops, ops64);
+        if constexpr (sizeof(T) == 4) k_pri_C<T, 96><<<grid_elems(a.ne, 10), 96, 0, s>>>(a, ops, ops64);
+        else k_pri_C<T, 128><<<grid_elems(a.ne, 8), 128, 0, s>>>(a, ops, ops64);
     }
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
