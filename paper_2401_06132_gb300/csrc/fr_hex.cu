@@ -293,11 +293,10 @@ struct HexSmem {
     static constexpr int N = P + 1, M = P + 2, NU = N * N * N, NF = 6 * N * N, NQ = M * M * M;
     // solution-point fields are padded so that x-lines of even length do not start on the same banks
     static constexpr int XS = (N % 2 == 0) ? N + 1 : N, PS = XS * N, FS = PS * N;
-    // FP32 sweeps all 20 (15) fields per pass with one staging buffer (the first sweep's output
-    // goes to the quadrature-point buffer); FP64, bound by its FMA pipe rather than by barriers,
-    // keeps five fields per pass and the smaller footprint (more resident CTAs)
-    static constexpr bool WIDE = sizeof(T) == 4;
-    static constexpr int T1 = WIDE ? 0 : 5 * M * N * N, T2 = WIDE ? 20 * M * M * N : 5 * M * M * N;
+    // the sweeps take all 20 (15) fields per pass with one staging buffer (the first sweep's output
+    // goes to the quadrature-point buffer): fewer barriers, and work-item counts (20 n^2, 20 m n,
+    // 20 m^2 lines) that fill whole warps, which FP64, bound by its pipe, needs more than resident CTAs
+    static constexpr int T1 = 0, T2 = 20 * M * M * N;
     static constexpr int SIZE = 5 * FS + 15 * FS + 5 * NF + 20 * NQ + T1 + T2;
 };
 
@@ -406,7 +405,8 @@ __device__ __forceinline__ void interp_5(const HexOps<T> &op, const T *src, T *t
 
 // Sum-factorised interpolation of all 20 fields at once (src: fields at stride FS, padded layout)
 // to the quadrature points (dst, stride NQ), x then y then z; the x sweep is staged in dst itself,
-// the y sweep in tmp (20 M^2 N values). Three barriers instead of twelve.
+// the y sweep in tmp (20 M^2 N values). Three barriers instead of twelve. FP64 applies B in its
+// even/odd form (B is centro-symmetric), FP32 the plain rows.
 template <typename T, int P, int NT, int XS, int PS, int FS>
 __device__ __forceinline__ void interp_all(const HexOps<T> &op, const T *src, T *tmp, T *dst)
 {
@@ -418,12 +418,19 @@ __device__ __forceinline__ void interp_all(const HexOps<T> &op, const T *src, T 
         T u[N];
 #pragma unroll
         for (int i = 0; i < N; i++) u[i] = src[sb + i];
+        if constexpr (sizeof(T) == 8) {
+            T v[M];
+            line_eo<T, N, M, 1>(op.Beo, u, v);
+#pragma unroll
+            for (int q = 0; q < M; q++) xs[f * M * N * N + q + M * jk] = v[q];
+        } else {
 #pragma unroll
         for (int q = 0; q < M; q++) {
             T v = T(0);
 #pragma unroll
             for (int i = 0; i < N; i++) v += op.B[q][i] * u[i];
             xs[f * M * N * N + q + M * jk] = v;
+        }
         }
     }
     __syncthreads();
@@ -432,12 +439,19 @@ __device__ __forceinline__ void interp_all(const HexOps<T> &op, const T *src, T 
         T u[N];
 #pragma unroll
         for (int j = 0; j < N; j++) u[j] = xs[f * M * N * N + qa + M * j + M * N * k];
+        if constexpr (sizeof(T) == 8) {
+            T v[M];
+            line_eo<T, N, M, 1>(op.Beo, u, v);
+#pragma unroll
+            for (int q = 0; q < M; q++) tmp[f * M * M * N + qa + M * q + M * M * k] = v[q];
+        } else {
 #pragma unroll
         for (int q = 0; q < M; q++) {
             T v = T(0);
 #pragma unroll
             for (int j = 0; j < N; j++) v += op.B[q][j] * u[j];
             tmp[f * M * M * N + qa + M * q + M * M * k] = v;
+        }
         }
     }
     __syncthreads();
@@ -446,12 +460,19 @@ __device__ __forceinline__ void interp_all(const HexOps<T> &op, const T *src, T 
         T u[N];
 #pragma unroll
         for (int k = 0; k < N; k++) u[k] = tmp[f * M * M * N + ab + M * M * k];
+        if constexpr (sizeof(T) == 8) {
+            T v[M];
+            line_eo<T, N, M, 1>(op.Beo, u, v);
+#pragma unroll
+            for (int q = 0; q < M; q++) dst[f * NQ + ab + M * M * q] = v[q];
+        } else {
 #pragma unroll
         for (int q = 0; q < M; q++) {
             T v = T(0);
 #pragma unroll
             for (int k = 0; k < N; k++) v += op.B[q][k] * u[k];
             dst[f * NQ + ab + M * M * q] = v;
+        }
         }
     }
     __syncthreads();
@@ -460,99 +481,13 @@ __device__ __forceinline__ void interp_all(const HexOps<T> &op, const T *src, T 
 // tdivtpcorf with the corrected divergence folded into the projection: the projection of the
 // flux component along direction d uses Dh Pj instead of Pj along d, and the last (x) sweep sums
 // the three components, so R~[alpha] = sum_d Dh_d (Pj x Pj x Pj) F~[alpha][d] lands in R directly.
-// src: the 15 transformed-flux fields at the quadrature points (field alpha 3 + d, stride NQ);
-// every sweep stages its output where its input has been consumed. FP64: one direction (5 fields)
-// per pass through tmp (5 M^2 N values); FP32 (ALL): all 15 fields per pass (tmp 15 M^2 N).
-template <typename T, int P, int NT, bool ALL>
-__device__ __forceinline__ void project_div(const HexOps<T> &op, T *src, T *tmp, T *R)
-{
-    constexpr int N = P + 1, M = P + 2, NQ = M * M * M, NU = N * N * N;
-    constexpr int NG = ALL ? 3 : 1;   // directions per pass
-#pragma unroll 1
-    for (int d0 = 0; d0 < 3; d0 += NG) {
-        for (int it = threadIdx.x; it < 5 * NG * M * M; it += NT) {   // z: (direction, alpha, qa qb) -> k
-            const int g = it / (5 * M * M), r = it % (5 * M * M), alpha = r / (M * M), ab = r % (M * M);
-            const int d = d0 + g;
-            T u[M];
-#pragma unroll
-            for (int c = 0; c < M; c++) u[c] = src[(alpha * 3 + d) * NQ + ab + M * M * c];
-            if constexpr (ALL) {
-                const T(*Z)[FR_MAXM] = d == 2 ? op.DP : op.Pj;
-#pragma unroll
-                for (int k = 0; k < N; k++) {
-                    T v = T(0);
-#pragma unroll
-                    for (int c = 0; c < M; c++) v += Z[k][c] * u[c];
-                    tmp[(g * 5 + alpha) * M * M * N + ab + M * M * k] = v;
-                }
-            } else {   // one direction per pass: the even/odd forms (DP is antisymmetric, Pj symmetric)
-                T v[N];
-                if (d == 2) line_eo<T, M, N, -1>(op.DPeo, u, v);
-                else line_eo<T, M, N, 1>(op.Peo, u, v);
-#pragma unroll
-                for (int k = 0; k < N; k++) tmp[(g * 5 + alpha) * M * M * N + ab + M * M * k] = v[k];
-            }
-        }
-        __syncthreads();
-        for (int it = threadIdx.x; it < 5 * NG * M * N; it += NT) {   // y: (direction, alpha, qa, k) -> j
-            const int g = it / (5 * M * N), r = it % (5 * M * N), alpha = r / (M * N), r2 = r % (M * N);
-            const int qa = r2 % M, k = r2 / M, d = d0 + g;
-            T u[M];
-#pragma unroll
-            for (int b = 0; b < M; b++) u[b] = tmp[(g * 5 + alpha) * M * M * N + qa + M * b + M * M * k];
-            if constexpr (ALL) {
-                const T(*Y)[FR_MAXM] = d == 1 ? op.DP : op.Pj;
-#pragma unroll
-                for (int j = 0; j < N; j++) {
-                    T v = T(0);
-#pragma unroll
-                    for (int b = 0; b < M; b++) v += Y[j][b] * u[b];
-                    src[(alpha * 3 + d) * NQ + qa + M * j + M * N * k] = v;   // over the consumed input
-                }
-            } else {
-                T v[N];
-                if (d == 1) line_eo<T, M, N, -1>(op.DPeo, u, v);
-                else line_eo<T, M, N, 1>(op.Peo, u, v);
-#pragma unroll
-                for (int j = 0; j < N; j++) src[(alpha * 3 + d) * NQ + qa + M * j + M * N * k] = v[j];   // over the consumed input
-            }
-        }
-        __syncthreads();
-    }
-    for (int it = threadIdx.x; it < 5 * N * N; it += NT) {   // x: (alpha, j, k), sum over d -> i
-        const int alpha = it / (N * N), jk = it % (N * N);
-        T v[N];
-#pragma unroll
-        for (int i = 0; i < N; i++) v[i] = T(0);
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            T u[M];
-#pragma unroll
-            for (int q = 0; q < M; q++) u[q] = src[(alpha * 3 + d) * NQ + q + M * jk];
-            if constexpr (ALL) {
-                const T(*X)[FR_MAXM] = d == 0 ? op.DP : op.Pj;
-#pragma unroll
-                for (int i = 0; i < N; i++)
-#pragma unroll
-                    for (int q = 0; q < M; q++) v[i] += X[i][q] * u[q];
-            } else {
-                T y[N];
-                if (d == 0) line_eo<T, M, N, -1>(op.DPeo, u, y);
-                else line_eo<T, M, N, 1>(op.Peo, u, y);
-#pragma unroll
-                for (int i = 0; i < N; i++) v[i] += y[i];
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < N; i++) R[alpha * NU + i + N * jk] = v[i];
-    }
-}
-
-// FP32: the same with all 15 flux fields per pass. The loops over the three directions are
-// unrolled, so that each sweep's operator (Pj, or Dh Pj along the flux component's own direction)
-// is known at compile time: its coefficients are constant-bank operands of the multiply-adds, not
-// run-time loads from constant memory (one per coefficient and line, serialised over the distinct
-// addresses of a warp).
+// src: the 15 transformed-flux fields at the quadrature points (field alpha 3 + d, stride NQ), all
+// in one pass through tmp (15 M^2 N values); every sweep stages its output where its input has been
+// consumed. The loops over the three directions are unrolled, so that each sweep's operator is known
+// at compile time: its coefficients are constant-bank operands of the multiply-adds, not run-time
+// loads from constant memory (one per coefficient and line, serialised over the distinct addresses
+// of a warp). FP64 applies the even/odd forms (Pj symmetric, Dh Pj antisymmetric: fewer
+// multiply-adds on its slow pipe), FP32 the plain rows.
 template <typename T, int P, int NT>
 __device__ __forceinline__ void project_div_all(const HexOps<T> &op, T *src, T *tmp, T *R)
 {
@@ -565,7 +500,10 @@ __device__ __forceinline__ void project_div_all(const HexOps<T> &op, T *src, T *
             T u[M], v[N];
 #pragma unroll
             for (int c = 0; c < M; c++) u[c] = src[(alpha * 3 + d) * NQ + ab + M * M * c];
-            line_rows<T, N, M>(Z, u, v);
+            if constexpr (sizeof(T) == 8) {
+                if (d == 2) line_eo<T, M, N, -1>(op.DPeo, u, v);
+                else line_eo<T, M, N, 1>(op.Peo, u, v);
+            } else line_rows<T, N, M>(Z, u, v);
 #pragma unroll
             for (int k = 0; k < N; k++) tmp[(d * 5 + alpha) * M * M * N + ab + M * M * k] = v[k];
         }
@@ -579,7 +517,10 @@ __device__ __forceinline__ void project_div_all(const HexOps<T> &op, T *src, T *
             T u[M], v[N];
 #pragma unroll
             for (int b = 0; b < M; b++) u[b] = tmp[(d * 5 + alpha) * M * M * N + qa + M * b + M * M * k];
-            line_rows<T, N, M>(Y, u, v);
+            if constexpr (sizeof(T) == 8) {
+                if (d == 1) line_eo<T, M, N, -1>(op.DPeo, u, v);
+                else line_eo<T, M, N, 1>(op.Peo, u, v);
+            } else line_rows<T, N, M>(Y, u, v);
 #pragma unroll
             for (int j = 0; j < N; j++) src[(alpha * 3 + d) * NQ + qa + M * j + M * N * k] = v[j];   // over the consumed input
         }
@@ -596,7 +537,10 @@ __device__ __forceinline__ void project_div_all(const HexOps<T> &op, T *src, T *
             T u[M], y[N];
 #pragma unroll
             for (int q = 0; q < M; q++) u[q] = src[(alpha * 3 + d) * NQ + q + M * jk];
-            line_rows<T, N, M>(X, u, y);
+            if constexpr (sizeof(T) == 8) {
+                if (d == 0) line_eo<T, M, N, -1>(op.DPeo, u, y);
+                else line_eo<T, M, N, 1>(op.Peo, u, y);
+            } else line_rows<T, N, M>(X, u, y);
 #pragma unroll
             for (int i = 0; i < N; i++) v[i] += y[i];
         }
@@ -1044,12 +988,8 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
         // 6. uqpts + gradcoru_qpts: 20 fields to quadrature points, 5 at a time
         if constexpr (!AA) {
             // collocation form: the flux is evaluated at the solution points (step 7b below)
-        } else if constexpr (TCM == 0 && S::WIDE) {
-            interp_all<T, P, NT, XS, PS, FS>(op, s_u, s_t2, s_w);   // s_q follows s_u
         } else if constexpr (TCM == 0) {
-            interp_5<T, P, NT, XS, PS, FS>(op, s_u, s_t1, s_t2, s_w);
-#pragma unroll 1
-            for (int c = 0; c < 3; c++) interp_5<T, P, NT, XS, PS, FS>(op, s_q + 5 * c * FS, s_t1, s_t2, s_w + (5 + 5 * c) * NQ);
+            interp_all<T, P, NT, XS, PS, FS>(op, s_u, s_t2, s_w);   // s_q follows s_u
         } else {
             // z factor on the CUDA cores: row r = f M + c holds field f (s_q follows s_u) at z
             // quadrature level c on the N^2 in-plane points
@@ -1171,8 +1111,7 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
         if constexpr (!AA) {
             // collocation form: the flux already sits at the solution points
         } else if constexpr (TCM == 0) {
-            if constexpr (S::WIDE) project_div_all<T, P, NT>(op, s_w, s_t2, R);
-            else project_div<T, P, NT, false>(op, s_w, s_t2, R);
+            project_div_all<T, P, NT>(op, s_w, s_t2, R);
         } else {
             // x-y factor on the tensor cores: row r = f M + c holds flux component f at quadrature
             // level c on the M^2 in-plane points; then the z factor on the CUDA cores
@@ -1244,6 +1183,14 @@ template <typename T, int P, int NT, int TCM = 0, bool AA = true, bool SURF = fa
 __global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
 {
     fused_B_body<T, P, NT, TCM, AA, SURF, CURV>(a, blockIdx.x, gridDim.x);
+}
+
+// FP32 with surface-flux anti-aliasing: registers capped so that 896 threads' worth of CTAs (seven
+// of 128) stay resident, as many as its shared memory allows at 128 threads
+template <int P, int NT>
+__global__ void __launch_bounds__(NT, 896 / NT) k_fused_B_surf32(HexArgs<float> a)
+{
+    fused_B_body<float, P, NT, 0, true, true, false>(a, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -2343,11 +2290,19 @@ static void launch_B(const HexArgs<T> &a, cudaStream_t s)
     constexpr int TAIL = S::T1 + S::T2 > TI ? S::T1 + S::T2 : TI;
     const size_t smem = (!AA ? 20 * S::FS + 5 * S::NF : (SURF ? S::SIZE - S::T1 - S::T2 + TAIL : S::SIZE)) * sizeof(T);
     static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_fused_B<T, P, NT, 0, AA, SURF, CURV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
+    if constexpr (SURF && sizeof(T) == 4) {
+        if (!attr) {
+            cudaFuncSetAttribute(k_fused_B_surf32<P, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr = true;
+        }
+        k_fused_B_surf32<P, NT><<<grid_elems(a.ne, 8), NT, smem, s>>>(a);
+    } else {
+        if (!attr) {
+            cudaFuncSetAttribute(k_fused_B<T, P, NT, 0, AA, SURF, CURV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr = true;
+        }
+        k_fused_B<T, P, NT, 0, AA, SURF, CURV><<<grid_elems(a.ne, 8), NT, smem, s>>>(a);
     }
-    k_fused_B<T, P, NT, 0, AA, SURF, CURV><<<grid_elems(a.ne, 8), NT, smem, s>>>(a);
 }
 
 // Tensor-core form of the volume kernel (FP32, 128 threads, persistent: at most as many CTAs as
