@@ -296,8 +296,18 @@ struct HexSmem {
     // the sweeps take all 20 (15) fields per pass with one staging buffer (the first sweep's output
     // goes to the quadrature-point buffer): fewer barriers, and work-item counts (20 n^2, 20 m n,
     // 20 m^2 lines) that fill whole warps, which FP64, bound by its pipe, needs more than resident CTAs
-    static constexpr int T1 = 0, T2 = 20 * M * M * N;
-    static constexpr int SIZE = 5 * FS + 15 * FS + 5 * NF + 20 * NQ + T1 + T2;
+    // s_u, s_q, s_c (the state, the gradient, the common solution): free once the interpolation's
+    // first sweep has read them, so its second sweep (where it fits) and the projection stage their
+    // outputs there
+    static constexpr int LOW = 20 * FS + 5 * NF;
+    // the next element's state, fetched by the bulk-copy engine while this one computes (the copy
+    // must be a whole number of 16-byte units)
+    static constexpr bool TMA = (5 * NU * sizeof(T)) % 16 == 0;
+    static constexpr int PF = TMA ? 5 * NU : 0;
+    static constexpr bool TMP_LOW = 20 * M * M * N <= LOW;
+    static constexpr int T2 = TMP_LOW ? 0 : 20 * M * M * N;   // else after the quadrature-point buffer
+    static constexpr int SIZE = LOW + PF + 20 * NQ + T2;
+    static_assert(15 * M * M * N <= LOW, "the projection stages its sweeps over s_u, s_q, s_c");
 };
 
 // Mixed forms (tcmode 1 = FP16, 2 = BF16 halves): the x-y factor of the interpolation, B (x) B
@@ -628,9 +638,10 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
     T *s_u = reinterpret_cast<T *>(arr);
     T *s_q = s_u + 5 * FS;
     T *s_c = s_q + 15 * FS;
-    T *s_w = s_c + 5 * NF;
-    T *s_t1 = s_w + 20 * NQ;
-    T *s_t2 = s_t1 + S::T1;
+    T *s_pf = s_c + 5 * NF;                    // prefetched state of the next element
+    T *s_w = s_pf + S::PF;
+    T *s_t1 = s_w + 20 * NQ;                   // scratch of the surface-flux and tensor-core paths
+    T *s_t2 = S::TMP_LOW ? s_u : s_t1;         // the interpolation's second sweep
     __shared__ short s_list[NF];
     __shared__ int s_cnt;
     __shared__ double s_m64[std::is_same<T, float>::value ? 3 * NU : 1];
@@ -641,9 +652,10 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
     uint32_t tmem = 0, parity = 0;
     bool tc_fail = false;
     // The next element's state is fetched by the bulk-copy engine while this element computes: the
-    // copy goes into s_c (free from the gradient step on) and lands on s_ubar. Needs the tile to be
-    // a whole number of 16-byte units (p = 3) and 16-byte aligned in memory (checked per element).
-    constexpr bool TMA_U = (5 * NU * sizeof(T)) % 16 == 0 && 5 * NF >= 5 * NU;
+    // copy goes into s_pf (issued as soon as this element's state has been read from it) and lands on
+    // s_ubar. Needs the tile to be a whole number of 16-byte units (p = 3) and 16-byte aligned in
+    // memory (checked per element).
+    constexpr bool TMA_U = S::TMA;
     __shared__ uint64_t s_ubar;
     bool pending = false;
     uint32_t uparity = 0;
@@ -696,7 +708,7 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
                 uparity ^= 1;
                 pending = false;
                 if (__syncthreads_and(landed)) {
-                    usrc = s_c;
+                    usrc = s_pf;
                 } else {
                     // the copy did not land within the bound: report it, give it one more bounded
                     // wait, and read the state from global memory
@@ -715,7 +727,26 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
             const int alpha = it / NU, z = it % NU;
             s_u[alpha * FS + z % N + XS * ((z / N) % N) + PS * (z / (N * N))] = v;
         }
-        if constexpr (TMA_U) __syncthreads();   // s_c is overwritten next
+        if constexpr (TMA_U) {
+            tc::fence_async_smem();   // this element's reads of s_pf before the copy that overwrites it
+            __syncthreads();
+            // prefetch the next element's state into s_pf
+            const long long en = e + stride;
+            bool en_ok = en < a.ne;
+#ifdef FR_DEBUG_BOUNDS
+            if (en_ok) {   // the bounds-checking build prefetches only elements inside U
+                const long long un = elem_u0(a, en, NU);
+                en_ok = un >= 0 && un + (long long)FR_NV * NU <= a.nU;
+            }
+#endif
+            if (en_ok) {
+                const T *Un = a.U + elem_u0(a, en, NU);
+                if ((reinterpret_cast<uintptr_t>(Un) & 15) == 0) {
+                    if (threadIdx.x == 0) tc::bulk_g2s(s_pf, Un, 5 * NU * sizeof(T), &s_ubar);
+                    pending = true;
+                }
+            }
+        }
         // 2. con_u: common solution at own flux points, C = (1/2 - beta) uL + (1/2 + beta) uR
         for (int it = threadIdx.x; it < 5 * NF; it += NT) {
             const int alpha = it / NF, s = it % NF;
@@ -744,26 +775,7 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
                 s_q[(alpha * 3 + d) * FS + base + i * stride] = v;
             }
         }
-        if constexpr (TMA_U) tc::fence_async_smem();   // s_c's reads before the copy that overwrites it
         __syncthreads();
-        if constexpr (TMA_U) {
-            // prefetch the next element's state into s_c
-            const long long en = e + stride;
-            bool en_ok = en < a.ne;
-#ifdef FR_DEBUG_BOUNDS
-            if (en_ok) {   // the bounds-checking build prefetches only elements inside U
-                const long long un = elem_u0(a, en, NU);
-                en_ok = un >= 0 && un + (long long)FR_NV * NU <= a.nU;
-            }
-#endif
-            if (en_ok) {
-                const T *Un = a.U + elem_u0(a, en, NU);
-                if ((reinterpret_cast<uintptr_t>(Un) & 15) == 0) {
-                    if (threadIdx.x == 0) tc::bulk_g2s(s_c, Un, 5 * NU * sizeof(T), &s_ubar);
-                    pending = true;
-                }
-            }
-        }
         // 4. gradcoru: q = J^-T q~ (per point, all three components; diagonal J^-1 is common)
         const bool diagJ = g.Ji[1] == T(0) && g.Ji[2] == T(0) && g.Ji[3] == T(0) && g.Ji[5] == T(0) &&
                            g.Ji[6] == T(0) && g.Ji[7] == T(0);
@@ -989,7 +1001,7 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
         if constexpr (!AA) {
             // collocation form: the flux is evaluated at the solution points (step 7b below)
         } else if constexpr (TCM == 0) {
-            interp_all<T, P, NT, XS, PS, FS>(op, s_u, s_t2, s_w);   // s_q follows s_u
+            interp_all<T, P, NT, XS, PS, FS>(op, s_u, s_t2, s_w);   // s_q follows s_u; s_t2 may be s_u
         } else {
             // z factor on the CUDA cores: row r = f M + c holds field f (s_q follows s_u) at z
             // quadrature level c on the N^2 in-plane points
@@ -1111,7 +1123,7 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
         if constexpr (!AA) {
             // collocation form: the flux already sits at the solution points
         } else if constexpr (TCM == 0) {
-            project_div_all<T, P, NT>(op, s_w, s_t2, R);
+            project_div_all<T, P, NT>(op, s_w, s_u, R);   // staged over s_u, s_q, s_c
         } else {
             // x-y factor on the tensor cores: row r = f M + c holds flux component f at quadrature
             // level c on the M^2 in-plane points; then the z factor on the CUDA cores
@@ -2287,8 +2299,8 @@ static void launch_B(const HexArgs<T> &a, cudaStream_t s)
     // the collocation form needs no quadrature-point buffers; surface-flux anti-aliasing stages its
     // in-plane interpolation (6 faces x 20 fields x m x n values) where the sweep buffers start
     constexpr int TI = 6 * 20 * S::M * S::N;
-    constexpr int TAIL = S::T1 + S::T2 > TI ? S::T1 + S::T2 : TI;
-    const size_t smem = (!AA ? 20 * S::FS + 5 * S::NF : (SURF ? S::SIZE - S::T1 - S::T2 + TAIL : S::SIZE)) * sizeof(T);
+    constexpr int TAIL = S::T2 > TI ? S::T2 : TI;
+    const size_t smem = (!AA ? S::LOW + S::PF : (SURF ? S::SIZE - S::T2 + TAIL : S::SIZE)) * sizeof(T);
     static bool attr = false;
     if constexpr (SURF && sizeof(T) == 4) {
         if (!attr) {
@@ -2314,7 +2326,8 @@ static int launch_B_tc(const HexArgs<float> &a, cudaStream_t s)
     static_assert(16 * (TC::SBO_I > TC::SBO_P ? TC::SBO_I : TC::SBO_P) <=
                       TC::A_BYTES + TC::BI_BYTES + TC::BP_BYTES + HexSmem<float, P>::SIZE * (int)sizeof(float),
                   "the 128 rows an MMA reads stay inside the CTA's shared memory");
-    const size_t tt = (size_t)(TC::TT > HexSmem<float, P>::T1 + HexSmem<float, P>::T2 ? TC::TT - HexSmem<float, P>::T1 - HexSmem<float, P>::T2 : 0);
+    // the staged rows of the plane contractions sit after the quadrature-point buffer
+    const size_t tt = (size_t)(TC::TT > HexSmem<float, P>::T2 ? TC::TT - HexSmem<float, P>::T2 : 0);
     const size_t smem = TC::HEAD + (HexSmem<float, P>::SIZE + tt) * sizeof(float);
     static int occ = -1;
     if (occ < 0) {
