@@ -1191,8 +1191,17 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
     }
 }
 
+// The FP32 affine p = 3 volume kernel is capped at 48 registers per thread: ten CTAs of 128 threads
+// per SM, as many as its shared memory allows (more warps to hide its shared-memory latency). A
+// minimum of 0 CTAs leaves the register count to the compiler (an explicit 1 lets it take up to 255)
+template <typename T, int P, int NT, int TCM, bool AA, bool SURF, bool CURV>
+constexpr int fused_B_min_ctas()
+{
+    return (sizeof(T) == 4 && TCM == 0 && AA && !SURF && !CURV && P == 3) ? 10 * 128 / NT : 0;
+}
+
 template <typename T, int P, int NT, int TCM = 0, bool AA = true, bool SURF = false, bool CURV = false>
-__global__ void __launch_bounds__(NT) k_fused_B(HexArgs<T> a)
+__global__ void __launch_bounds__(NT, (fused_B_min_ctas<T, P, NT, TCM, AA, SURF, CURV>())) k_fused_B(HexArgs<T> a)
 {
     fused_B_body<T, P, NT, TCM, AA, SURF, CURV>(a, blockIdx.x, gridDim.x);
 }
@@ -1360,8 +1369,11 @@ __device__ __forceinline__ void fused_C_body(const HexArgs<T> &a, long long firs
     }
 }
 
+// FP32: registers capped for 960 resident threads per SM (ten CTAs of 96, one thread per flux point
+// of a p = 3 element): the kernel waits on its partner gathers, and more warps keep more of them in
+// flight. FP64 (0): the compiler's own register count.
 template <typename T, int P, int NT, bool CURV = false>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 960 / NT : 1) k_fused_C(HexArgs<T> a)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 960 / NT : 0) k_fused_C(HexArgs<T> a)
 {
     fused_C_body<T, P, NT, CURV>(a, blockIdx.x, gridDim.x);
 }

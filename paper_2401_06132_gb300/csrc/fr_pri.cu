@@ -37,8 +37,9 @@ __global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *go
     pri_B_body<T, NTH, TCM>(a, gops, opsff, blockIdx.x, gridDim.x);
 }
 
+// FP32: registers capped for 960 resident threads per SM (ten CTAs of 96), as for the hexahedra
 template <typename T, int NTH>
-__global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 960 / NTH : 1) k_pri_C(HexArgs<T> a, const PriOps<T> *gops, const PriOpsFF *opsff)
+__global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 960 / NTH : 0) k_pri_C(HexArgs<T> a, const PriOps<T> *gops, const PriOpsFF *opsff)
 {
     pri_C_body<T, NTH>(a, gops, opsff, blockIdx.x, gridDim.x);
 }
