@@ -297,17 +297,14 @@ struct HexSmem {
     // goes to the quadrature-point buffer): fewer barriers, and work-item counts (20 n^2, 20 m n,
     // 20 m^2 lines) that fill whole warps, which FP64, bound by its pipe, needs more than resident CTAs
     // s_u, s_q, s_c (the state, the gradient, the common solution): free once the interpolation's
-    // first sweep has read them, so its second sweep (where it fits) and the projection stage their
-    // outputs there
-    static constexpr int LOW = 20 * FS + 5 * NF;
+    // first sweep has read them, so its second sweep and the projection stage their outputs there
+    // (the region is sized for the larger of the two uses)
+    static constexpr int LOW = (20 * FS + 5 * NF) > 20 * M * M * N ? 20 * FS + 5 * NF : 20 * M * M * N;
     // the next element's state, fetched by the bulk-copy engine while this one computes (the copy
     // must be a whole number of 16-byte units)
     static constexpr bool TMA = (5 * NU * sizeof(T)) % 16 == 0;
     static constexpr int PF = TMA ? 5 * NU : 0;
-    static constexpr bool TMP_LOW = 20 * M * M * N <= LOW;
-    static constexpr int T2 = TMP_LOW ? 0 : 20 * M * M * N;   // else after the quadrature-point buffer
-    static constexpr int SIZE = LOW + PF + 20 * NQ + T2;
-    static_assert(15 * M * M * N <= LOW, "the projection stages its sweeps over s_u, s_q, s_c");
+    static constexpr int SIZE = LOW + PF + 20 * NQ;
 };
 
 // Mixed forms (tcmode 1 = FP16, 2 = BF16 halves): the x-y factor of the interpolation, B (x) B
@@ -638,10 +635,9 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
     T *s_u = reinterpret_cast<T *>(arr);
     T *s_q = s_u + 5 * FS;
     T *s_c = s_q + 15 * FS;
-    T *s_pf = s_c + 5 * NF;                    // prefetched state of the next element
+    T *s_pf = s_u + S::LOW;                    // prefetched state of the next element
     T *s_w = s_pf + S::PF;
     T *s_t1 = s_w + 20 * NQ;                   // scratch of the surface-flux and tensor-core paths
-    T *s_t2 = S::TMP_LOW ? s_u : s_t1;         // the interpolation's second sweep
     __shared__ short s_list[NF];
     __shared__ int s_cnt;
     __shared__ double s_m64[std::is_same<T, float>::value ? 3 * NU : 1];
@@ -1001,7 +997,7 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
         if constexpr (!AA) {
             // collocation form: the flux is evaluated at the solution points (step 7b below)
         } else if constexpr (TCM == 0) {
-            interp_all<T, P, NT, XS, PS, FS>(op, s_u, s_t2, s_w);   // s_q follows s_u; s_t2 may be s_u
+            interp_all<T, P, NT, XS, PS, FS>(op, s_u, s_u, s_w);   // s_q follows s_u; staged over them
         } else {
             // z factor on the CUDA cores: row r = f M + c holds field f (s_q follows s_u) at z
             // quadrature level c on the N^2 in-plane points
@@ -2309,10 +2305,9 @@ static void launch_B(const HexArgs<T> &a, cudaStream_t s)
 {
     using S = HexSmem<T, P>;
     // the collocation form needs no quadrature-point buffers; surface-flux anti-aliasing stages its
-    // in-plane interpolation (6 faces x 20 fields x m x n values) where the sweep buffers start
+    // in-plane interpolation (6 faces x 20 fields x m x n values) after the quadrature-point buffer
     constexpr int TI = 6 * 20 * S::M * S::N;
-    constexpr int TAIL = S::T2 > TI ? S::T2 : TI;
-    const size_t smem = (!AA ? S::LOW + S::PF : (SURF ? S::SIZE - S::T2 + TAIL : S::SIZE)) * sizeof(T);
+    const size_t smem = (!AA ? S::LOW + S::PF : (SURF ? S::SIZE + TI : S::SIZE)) * sizeof(T);
     static bool attr = false;
     if constexpr (SURF && sizeof(T) == 4) {
         if (!attr) {
@@ -2339,7 +2334,7 @@ static int launch_B_tc(const HexArgs<float> &a, cudaStream_t s)
                       TC::A_BYTES + TC::BI_BYTES + TC::BP_BYTES + HexSmem<float, P>::SIZE * (int)sizeof(float),
                   "the 128 rows an MMA reads stay inside the CTA's shared memory");
     // the staged rows of the plane contractions sit after the quadrature-point buffer
-    const size_t tt = (size_t)(TC::TT > HexSmem<float, P>::T2 ? TC::TT - HexSmem<float, P>::T2 : 0);
+    const size_t tt = (size_t)TC::TT;
     const size_t smem = TC::HEAD + (HexSmem<float, P>::SIZE + tt) * sizeof(float);
     static int occ = -1;
     if (occ < 0) {
