@@ -244,9 +244,11 @@ __device__ __forceinline__ void disu_blk_body(const HexArgs<T> &a, long long fir
 #pragma unroll
                 for (int alpha = 0; alpha < FR_NV; alpha++) {
                     const T *u = s_u + (el * FR_NV + alpha) * NU + base;
-                    ff w = ff_of(0.0f);
+                    float sh, c;
+                    dot2_first(lf[0], u[0], sh, c);
 #pragma unroll
-                    for (int i = 0; i < N; i++) w = ff_fma_f(lf[i], u[i * stride], w);
+                    for (int i = 1; i < N; i++) dot2_next(lf[i], u[i * stride], sh, c);
+                    const ff w = fast_two_sum(sh, c);
                     v[alpha] = w;
                     a.UF[alpha * a.nfpt + fo] = w.hi + w.lo;
                 }
@@ -816,9 +818,11 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
                         // rounded once: the face values feed the Rusanov dissipation
                         const HexOpsFF &off = c_hexff[P - 2];
                         const ff *lf = (f & 1) ? off.lR : off.lL;
-                        ff w = ff_of(0.0f);
+                        float sh, c;
+                        dot2_first(lf[0], src[0], sh, c);
 #pragma unroll
-                        for (int i = 0; i < N; i++) w = ff_fma_f(lf[i], src[i * stride], w);
+                        for (int i = 1; i < N; i++) dot2_next(lf[i], src[i * stride], sh, c);
+                        const ff w = fast_two_sum(sh, c);
                         tr[it] = w.hi + w.lo;
                         continue;
                     }

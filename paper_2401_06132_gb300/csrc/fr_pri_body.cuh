@@ -75,22 +75,24 @@ __device__ __forceinline__ ff ffop(const PriOpsFF &o, const float &hi)
     return ff{hi, *(reinterpret_cast<const float *>(&o.lo) + (h - reinterpret_cast<const float *>(&o.hi)))};
 }
 
-// Same, of the field minus a constant, with the float-float table (exact products of its hi part,
-// TwoSum accumulation): the face value to about 48 bits before its final rounding to FP32.
+// Same, of the field minus a constant, with the float-float table (a compensated dot product, Dot2):
+// the face value to about 48 bits before its final rounding to FP32.
 __device__ __forceinline__ ff face_value_ff_off(const PriOpsFF &o, const float *fld, int s, float off)
 {
-    ff v = ff_of(0.0f);
+    float sh, c;
     if (s < 20) {
         const int t = s % 10;
         const float *l = s < 10 ? o.hi.lzL : o.hi.lzR;
+        dot2_first(ffop(o, l[0]), fld[t] - off, sh, c);
 #pragma unroll
-        for (int k = 0; k < NZ; k++) v = ff_fma_f(ffop(o, l[k]), fld[t + 10 * k] - off, v);
+        for (int k = 1; k < NZ; k++) dot2_next(ffop(o, l[k]), fld[t + 10 * k] - off, sh, c);
     } else {
         const int f = (s - 20) / 16, loc = (s - 20) % 16, a = loc % 4, b = loc / 4;
+        dot2_first(ffop(o, o.hi.Ef[f][a][0]), fld[10 * b] - off, sh, c);
 #pragma unroll
-        for (int t = 0; t < NT_; t++) v = ff_fma_f(ffop(o, o.hi.Ef[f][a][t]), fld[t + 10 * b] - off, v);
+        for (int t = 1; t < NT_; t++) dot2_next(ffop(o, o.hi.Ef[f][a][t]), fld[t + 10 * b] - off, sh, c);
     }
-    return v;
+    return fast_two_sum(sh, c);
 }
 
 template <typename T, int NTH>
