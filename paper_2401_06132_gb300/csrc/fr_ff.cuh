@@ -75,8 +75,11 @@ __device__ __forceinline__ ff ff_fma_f(ff a, float f, ff acc) { return ff_add(ac
 // Compensated dot product sum_i a_i x_i of float-float coefficients and floats (Dot2 of Ogita, Rump
 // and Oishi, with each coefficient's low part folded into the correction): s carries the TwoSum of
 // the exact products' high parts, c their rounding errors, the TwoSum errors and lo(a_i) x_i; the
-// value is fast_two_sum(s, c), as accurate as a sum formed in twice the working precision. About
-// two thirds of the operations of accumulating with ff_fma_f.
+// value is two_sum(s, c), as accurate as a sum formed in twice the working precision. About two
+// thirds of the operations of accumulating with ff_fma_f. Where the sum is rounded to one float at
+// the end (face values), fast_two_sum(s, c) serves: its high part is the correctly rounded s + c
+// whatever the magnitudes, and its low part can be inexact only when the sum has cancelled to below
+// the rounding errors already in c.
 __device__ __forceinline__ void dot2_first(ff a, float x, float &s, float &c)
 {
     s = __fmul_rn(a.hi, x);
@@ -89,5 +92,16 @@ __device__ __forceinline__ void dot2_next(ff a, float x, float &s, float &c)
     const ff t = two_sum(s, p);
     s = t.hi;
     c = __fmaf_rn(a.lo, x, __fadd_rn(c, __fadd_rn(e, t.lo)));
+}
+// One term with float-float factors on both sides: the cross products hi lo and lo hi go into the
+// correction (lo lo, below 2^-48 of the product, is dropped, as ff_mul drops it). Start from s = hi,
+// c = lo of an initial value (or zeros).
+__device__ __forceinline__ void dot2ff_next(ff a, ff b, float &s, float &c)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = __fmaf_rn(a.hi, b.hi, -p);
+    const ff t = two_sum(s, p);
+    s = t.hi;
+    c = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, __fadd_rn(c, __fadd_rn(e, t.lo))));
 }
 #endif

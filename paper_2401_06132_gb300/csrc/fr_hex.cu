@@ -986,14 +986,14 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
                 const long long pbase = elem_u0(a, e, NU) / FR_NV;
                 for (int z = threadIdx.x; z < NU; z += NT) {
                     const int i = z % N, j = (z / N) % N, k = z / (N * N);
-                    ff v = ff_of(0.0f);
+                    float sh = 0.0f, c = 0.0f;   // compensated dot product (Dot2)
 #pragma unroll
                     for (int b = 0; b < N; b++) {
-                        v = ff_fma(off.Dh[i][b], s_mf[b + N * j + N * N * k], v);
-                        v = ff_fma(off.Dh[j][b], s_mf[NU + i + N * b + N * N * k], v);
-                        v = ff_fma(off.Dh[k][b], s_mf[2 * NU + i + N * j + N * N * b], v);
+                        dot2ff_next(off.Dh[i][b], s_mf[b + N * j + N * N * k], sh, c);
+                        dot2ff_next(off.Dh[j][b], s_mf[NU + i + N * b + N * N * k], sh, c);
+                        dot2ff_next(off.Dh[k][b], s_mf[2 * NU + i + N * j + N * N * b], sh, c);
                     }
-                    a.RL[pbase + z] = v;
+                    a.RL[pbase + z] = two_sum(sh, c);
                 }
             }
         }
@@ -2026,14 +2026,14 @@ __global__ void __launch_bounds__(NT, MB) k_hex_B32(HexArgs<float> a)
             for (int i = tid; i < nb * NU; i += NT) {
                 const int el = i / NU, z = i % NU, x = z % N, y = (z / N) % N, k = z / (N * N);
                 const ff *mf = reinterpret_cast<const ff *>(s_ws + el * ES + MO);
-                ff v = ff_of(0.0f);
+                float sh = 0.0f, c = 0.0f;   // compensated dot product (Dot2)
 #pragma unroll
                 for (int b = 0; b < N; b++) {
-                    v = ff_fma(off.Dh[x][b], mf[b + N * y + N * N * k], v);
-                    v = ff_fma(off.Dh[y][b], mf[NU + x + N * b + N * N * k], v);
-                    v = ff_fma(off.Dh[k][b], mf[2 * NU + x + N * y + N * N * b], v);
+                    dot2ff_next(off.Dh[x][b], mf[b + N * y + N * N * k], sh, c);
+                    dot2ff_next(off.Dh[y][b], mf[NU + x + N * b + N * N * k], sh, c);
+                    dot2ff_next(off.Dh[k][b], mf[2 * NU + x + N * y + N * N * b], sh, c);
                 }
-                a.RL[s_u0[el] / FR_NV + z] = v;
+                a.RL[s_u0[el] / FR_NV + z] = two_sum(sh, c);
             }
         }
         // 6. uqpts + gradcoru_qpts: one thread per (element, field) interpolates the field to the

@@ -451,15 +451,15 @@ __device__ __forceinline__ void pri_B_body(const HexArgs<T> &a, const PriOps<T> 
                     const long long pbase = elem_u0(a, e, NU) / FR_NV;
                     for (int z = threadIdx.x; z < NU; z += NTH) {
                         const int k = z / NT_, t = z % NT_;
-                        ff v = ff_of(0.0f);
+                        float sh = 0.0f, c = 0.0f;   // compensated dot product (Dot2)
 #pragma unroll
                         for (int j = 0; j < NT_; j++) {
-                            v = ff_fma(ffop(o, o.hi.Dhx[t][j]), s_mf[j + 10 * k], v);
-                            v = ff_fma(ffop(o, o.hi.Dhy[t][j]), s_mf[NU + j + 10 * k], v);
+                            dot2ff_next(ffop(o, o.hi.Dhx[t][j]), s_mf[j + 10 * k], sh, c);
+                            dot2ff_next(ffop(o, o.hi.Dhy[t][j]), s_mf[NU + j + 10 * k], sh, c);
                         }
 #pragma unroll
-                        for (int j = 0; j < NZ; j++) v = ff_fma(ffop(o, o.hi.Dhz[k][j]), s_mf[2 * NU + t + 10 * j], v);
-                        a.RL[pbase + z] = v;
+                        for (int j = 0; j < NZ; j++) dot2ff_next(ffop(o, o.hi.Dhz[k][j]), s_mf[2 * NU + t + 10 * j], sh, c);
+                        a.RL[pbase + z] = two_sum(sh, c);
                     }
                 }
             }
