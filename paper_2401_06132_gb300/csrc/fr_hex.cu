@@ -969,7 +969,10 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
                 const HexOpsFF &off = c_hexff[P - 2];
                 const ff *cm = a.geo64[e].cm;   // det J J^-1, per element
                 ff *s_mf = reinterpret_cast<ff *>(s_m64);
-                for (int it = threadIdx.x; it < NU; it += NT) {
+                // the upper half of the CTA takes the solution points first: the lower half is still
+                // on the viscous flux of the flux-point list (at most 96 points), so the two overlap
+                const int tr = (threadIdx.x + NT / 2) % NT;
+                for (int it = tr; it < NU; it += NT) {
                     const int pz = it % N + XS * ((it / N) % N) + PS * (it / (N * N));
                     const float m0 = s_u[FS + pz], m1 = s_u[2 * FS + pz], m2 = s_u[3 * FS + pz];
                     if (diagJ) {
@@ -984,7 +987,7 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
                 }
                 __syncthreads();
                 const long long pbase = elem_u0(a, e, NU) / FR_NV;
-                for (int z = threadIdx.x; z < NU; z += NT) {
+                for (int z = tr; z < NU; z += NT) {
                     const int i = z % N, j = (z / N) % N, k = z / (N * N);
                     float sh = 0.0f, c = 0.0f;   // compensated dot product (Dot2)
 #pragma unroll
