@@ -711,14 +711,14 @@ __global__ void __launch_bounds__(OPS::NF * EPB) k_dense_C(HexArgs<T> a, const O
 int grid_groups(long long ne, int epb, int per_sm)
 {
     long long g = (ne + epb - 1) / epb;
-    if (g > 152LL * per_sm * 8) g = 152LL * per_sm * 8;
+    if (g > fr_sms() * per_sm * 8) g = fr_sms() * per_sm * 8;
     return (int)(g < 1 ? 1 : g);
 }
 
 int grid_elems(long long ne, int per_sm)
 {
     long long g = ne;
-    if (g > 152LL * per_sm * 8) g = 152LL * per_sm * 8;
+    if (g > fr_sms() * per_sm * 8) g = fr_sms() * per_sm * 8;
     return (int)(g < 1 ? 1 : g);
 }
 
@@ -753,7 +753,7 @@ int dense_phase(int phase, const HexArgs<T> &a, const OPS *ops, const FFOf<OPS> 
                     if (v < 1) return -4;
                     o = v;
                 }
-                const long long g = a.ne < 152LL * o ? a.ne : 152LL * o;
+                const long long g = a.ne < fr_sms() * o ? a.ne : fr_sms() * o;
                 kern<<<(int)g, NTH, smem, s>>>(a, ops, opsff);
             }
         }

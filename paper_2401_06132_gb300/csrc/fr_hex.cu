@@ -642,7 +642,6 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
     T *s_t1 = s_w + 20 * NQ;                   // scratch of the surface-flux and tensor-core paths
     __shared__ short s_list[NF];
     __shared__ int s_cnt;
-    __shared__ double s_m64[std::is_same<T, float>::value ? 3 * NU : 1];
     __shared__ int s_sh[TCM ? 128 : 1];
     __shared__ uint64_t s_mbar[1];
     __shared__ uint32_t s_tmem[1];
@@ -968,7 +967,10 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
             if (dev && !CURV && !SURF) {
                 const HexOpsFF &off = c_hexff[P - 2];
                 const ff *cm = a.geo64[e].cm;   // det J J^-1, per element
-                ff *s_mf = reinterpret_cast<ff *>(s_m64);
+                // the transformed mass flux (3 NU float-float values) over the common solution
+                // (5 NF values), consumed by the gradient step
+                static_assert(3 * NU * sizeof(ff) <= 5 * NF * sizeof(T), "mass flux over s_c");
+                ff *s_mf = reinterpret_cast<ff *>(s_c);
                 // the upper half of the CTA takes the solution points first: the lower half is still
                 // on the viscous flux of the flux-point list (at most 96 points), so the two overlap
                 const int tr = (threadIdx.x + NT / 2) % NT;
@@ -2296,14 +2298,14 @@ __global__ void __launch_bounds__(NT, MB) k_hex_B32(HexArgs<float> a)
 static int grid_for(long long work, int threads)
 {
     long long g = (work + threads - 1) / threads;
-    if (g > 152LL * 64) g = 152LL * 64;
+    if (g > fr_sms() * 64) g = fr_sms() * 64;
     return (int)(g < 1 ? 1 : g);
 }
 
 static int grid_elems(long long ne, int per_sm)
 {
     long long g = ne;
-    if (g > 152LL * per_sm * 8) g = 152LL * per_sm * 8;
+    if (g > fr_sms() * per_sm * 8) g = fr_sms() * per_sm * 8;
     return (int)(g < 1 ? 1 : g);
 }
 
@@ -2358,7 +2360,7 @@ static int launch_B_tc(const HexArgs<float> &a, cudaStream_t s)
         if (o < 1) return -4;
         occ = o;
     }
-    long long g = a.ne < 152LL * occ ? a.ne : 152LL * occ;
+    long long g = a.ne < fr_sms() * occ ? a.ne : fr_sms() * occ;
     k_fused_B<float, P, 128, TCM><<<(int)g, 128, smem, s>>>(a);
     return 0;
 }
@@ -2389,7 +2391,7 @@ static int fused_phase(int phase, const HexArgs<T> &a, cudaStream_t s, int varia
     if (phase == 0) {
         constexpr int EB = 8;
         long long g = (a.ne + EB - 1) / EB;
-        if (g > 152LL * 16) g = 152LL * 16;
+        if (g > fr_sms() * 16) g = fr_sms() * 16;
         k_disu_blk<T, P, EB, 256><<<(int)g, 256, 0, s>>>(a);
     } else if (phase == 1) {
         if constexpr (std::is_same<T, float>::value) {

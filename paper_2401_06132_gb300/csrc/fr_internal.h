@@ -288,6 +288,21 @@ struct HexArgs {
     long long nU;             // values of U and R in the handle (index checks of the bounds-checking build)
 };
 
+// SM count of the calling thread's current device, cached per device: the kernels' grids are sized
+// in multiples of it (resident CTAs per SM times the SMs, or a few waves of them)
+inline long long fr_sms()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (cache[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 152;
+        cache[dev] = v;
+    }
+    return cache[dev];
+}
+
 #ifdef __CUDACC__
 template <typename T>
 __device__ __forceinline__ void rk_fold(const HexArgs<T> &a, long long i, T val)

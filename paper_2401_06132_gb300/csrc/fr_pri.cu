@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 960 / NTH : 0) k_pri_C(H
 int grid_elems(long long ne, int per_sm)
 {
     long long g = ne;
-    if (g > 152LL * per_sm * 8) g = 152LL * per_sm * 8;
+    if (g > fr_sms() * per_sm * 8) g = fr_sms() * per_sm * 8;
     return (int)(g < 1 ? 1 : g);
 }
 
@@ -65,7 +65,7 @@ int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, const 
     if (phase == 0) {
         long long work = a.ne * NF;
         long long g = (work + 255) / 256;
-        if (g > 152LL * 64) g = 152LL * 64;
+        if (g > fr_sms() * 64) g = fr_sms() * 64;
         k_pri_disu<T><<<(int)g, 256, 0, s>>>(a, ops, ops64);
     } else if (phase == 1) {
         constexpr int NTH = 128;
@@ -92,7 +92,7 @@ int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, const 
                 if (v < 1) return -4;
                 o = v;
             }
-            const long long g = a.ne < 152LL * o ? a.ne : 152LL * o;
+            const long long g = a.ne < fr_sms() * o ? a.ne : fr_sms() * o;
             kern<<<(int)g, NTH, smem, s>>>(a, ops, ops64);
           }
         }
