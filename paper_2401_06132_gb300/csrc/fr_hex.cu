@@ -1197,8 +1197,9 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
 }
 
 // The FP32 affine p = 3 volume kernel is capped at 48 registers per thread: ten CTAs of 128 threads
-// per SM, as many as its shared memory allows (more warps to hide its shared-memory latency). A
-// minimum of 0 CTAs leaves the register count to the compiler (an explicit 1 lets it take up to 255)
+// per SM (more warps to hide its shared-memory latency; an eleventh, which its shared memory would
+// allow, needs 40 registers, spills and measured slower). A minimum of 0 CTAs leaves the register
+// count to the compiler (an explicit 1 lets it take up to 255).
 template <typename T, int P, int NT, int TCM, bool AA, bool SURF, bool CURV>
 constexpr int fused_B_min_ctas()
 {
