@@ -31,8 +31,11 @@ __global__ void __launch_bounds__(256) k_pri_disu(HexArgs<T> a, const PriOps<T> 
     pri_disu_body<T>(a, gops, opsff, blockIdx.x, gridDim.x);
 }
 
+// FP32 on the CUDA cores: registers capped for eight CTAs of 128 threads per SM, as many as its
+// shared memory allows (64 registers, a few spilled values in L1; 72 registers measured slower).
+// Otherwise (0) the compiler's own register count.
 template <typename T, int NTH, int TCM>
-__global__ void __launch_bounds__(NTH) k_pri_B(HexArgs<T> a, const PriOps<T> *gops, const PriOpsFF *opsff)
+__global__ void __launch_bounds__(NTH, sizeof(T) == 4 && TCM == 0 ? 8 : 0) k_pri_B(HexArgs<T> a, const PriOps<T> *gops, const PriOpsFF *opsff)
 {
     pri_B_body<T, NTH, TCM>(a, gops, opsff, blockIdx.x, gridDim.x);
 }
