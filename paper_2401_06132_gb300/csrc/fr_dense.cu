@@ -79,8 +79,12 @@ __device__ __forceinline__ ff ffat(const FF &o, const float &hi)
 // state, and the own-normal mass flux n.(rho v) at every flux point in float-float: first
 // m_f = n_f . (rho v) at the solution points per face (the face normal is constant on an affine
 // element), then the same compensated dot product with m_f.
+// FP32 pyramids (224 threads per CTA): registers capped for five CTAs per SM, up from two at the
+// compiler's 112 (a few spilled values; the tetrahedral form is faster uncapped). Otherwise (0) the
+// compiler's own register count.
 template <typename T, typename OPS, int EPB>
-__global__ void __launch_bounds__(OPS::NF * EPB) k_dense_disu(HexArgs<T> a, const OPS *__restrict__ op, const FFOf<OPS> *__restrict__ opsff)
+__global__ void __launch_bounds__(OPS::NF * EPB, (sizeof(T) == 4 && OPS::NF * EPB > 192) ? 1280 / (OPS::NF * EPB) : 0)
+k_dense_disu(HexArgs<T> a, const OPS *__restrict__ op, const FFOf<OPS> *__restrict__ opsff)
 {
     constexpr int NU = OPS::NU, NF = OPS::NF, NUS = OPS::NUS, NFACE = OPS::NFACE, NTH = NF * EPB;
     constexpr bool F32 = sizeof(T) == 4;
@@ -587,8 +591,10 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? (TCM == 0 ? 8 : 6) : 0) 
 // -------------------------------------------------------------------------------------------------
 // Phase C: interface group (common flux at every own flux point, lift and scale)
 // -------------------------------------------------------------------------------------------------
+// FP32: registers capped for 1280 resident threads per SM (eight tetrahedral or five pyramidal CTAs):
+// the kernel waits on its partner gathers, and more warps keep more of them in flight.
 template <typename T, typename OPS, int EPB>
-__global__ void __launch_bounds__(OPS::NF * EPB) k_dense_C(HexArgs<T> a, const OPS *__restrict__ op, const FFOf<OPS> *__restrict__ opsff)
+__global__ void __launch_bounds__(OPS::NF * EPB, sizeof(T) == 4 ? 1280 / (OPS::NF * EPB) : 0) k_dense_C(HexArgs<T> a, const OPS *__restrict__ op, const FFOf<OPS> *__restrict__ opsff)
 {
     constexpr int NU = OPS::NU, NF = OPS::NF, NTH = NF * EPB;
     constexpr bool F32 = sizeof(T) == 4;
