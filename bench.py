@@ -41,10 +41,10 @@ def workload_name(n=N_EDGE, p=P, m=MQ):
 # FP64 peak of the chip from its unit counts and clock: 152 SMs x 2 FP64 FMA/clock x 2 FLOP x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + written) per element of one FP64 volume-kernel launch, from one Nsight Compute
-# capture of that kernel on the 40^3 p = 3 box (860.3 MB / 64,000 elements; the 164 MB state is
+# capture of that kernel on the 40^3 p = 3 box (859.1 MB / 64,000 elements; the 164 MB state is
 # larger than L2); the kernel touches each element's inputs and outputs once, so a launch's traffic
 # scales with its element count
-VOLUME_FP64_DRAM_BYTES_PER_ELEMENT = 860.261376e6 / 64000
+VOLUME_FP64_DRAM_BYTES_PER_ELEMENT = 859.063808e6 / 64000
 
 # ---------------------------------------------------------------------------------------------
 # FLOP model of the fused volume kernel (phase B), FMA = 2 FLOP; counted from its arithmetic
