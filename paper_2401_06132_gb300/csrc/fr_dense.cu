@@ -28,19 +28,20 @@ constexpr int NQ = FR_TQ, NQP = FR_TQP;
 
 // Tensor-core interpolation of the mixed forms: D[q][f] = sum_j B[q][j] x_f[j] for the 20 fields
 // (state and gradient) of one element, M = 128 quadrature-point rows (125 used), N = 32 field rows
-// (20 used), K = three NU-wide slices [B_hi | B_hi | B_lo] against [x_hi | x_lo | x_hi], zero-padded
-// to a multiple of 16. The operator tile is split once per CTA; each element writes its 20 field
-// rows (scaled by a power of two per row) and reads its quadrature point's 20 values back from
-// tensor memory, one lane per thread.
-template <typename OPS>
+// (20 used), K = the split form's NU-wide slices (tc::SplitForm; FP16: [B_hi | B_hi | B_lo] against
+// [x_hi | x_lo | x_hi]; BF16: six slices of three parts), zero-padded to a multiple of 16. The
+// operator tile is split once per CTA; each element writes its 20 field rows (scaled by a power of
+// two per row) and reads its quadrature point's 20 values back from tensor memory, one lane per
+// thread.
+template <typename OPS, int TCM>
 struct DenseTC {
-    static constexpr int KI = (3 * OPS::NU + 15) / 16 * 16;    // 64 (tetrahedron), 96 (pyramid)
+    static constexpr int KI = tc::split_k<TCM>(OPS::NU);       // FP16: 64 (tetrahedron), 96 (pyramid)
     static constexpr int SBO = KI / 8 * 128;
     static constexpr int A_BYTES = 16 * SBO;                   // 128 rows
     static constexpr int B_BYTES = 4 * SBO;                    // 32 rows
     static constexpr int HEAD = A_BYTES + B_BYTES + 32 * 4 + 16;   // tiles, row shifts, barrier, TMEM slot
     static constexpr int BYTES = HEAD + 128;                   // + alignment slack
-    static constexpr uint32_t IDESC1 = tc::idesc_f16(0, 128, 32), IDESC2 = tc::idesc_f16(1, 128, 32);
+    static constexpr uint32_t IDESC = tc::idesc_f16(TCM - 1, 128, 32);
 };
 
 // 16 bytes of T (4 floats or 2 doubles): one vector shared-memory load
@@ -212,7 +213,8 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? (TCM == 0 ? 8 : 6) : 0) 
     constexpr int NU = OPS::NU, NF = OPS::NF, NFACE = OPS::NFACE, NUS = OPS::NUS;
     static_assert(NTH >= NQ, "one thread per quadrature point");
     static_assert(TCM == 0 || (NTH == 128 && sizeof(T) == 4), "tensor-core form: FP32, one warpgroup per element");
-    using TC = DenseTC<OPS>;
+    using TC = DenseTC<OPS, TCM == 0 ? 1 : TCM>;
+    using SF = tc::SplitForm<TCM == 0 ? 1 : TCM>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ short s_plist[NF];
     __shared__ int s_pcnt;
@@ -236,11 +238,11 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? (TCM == 0 ? 8 : 6) : 0) 
         s_tmem = reinterpret_cast<uint32_t *>(mbar + 1);
         arr = tA + TC::HEAD;
         tc::setup(mbar, s_tmem, 32);
-        for (int i = threadIdx.x; i < 128 * TC::KI; i += NTH) {   // [B_hi | B_hi | B_lo], rows q
-            const int n = i / TC::KI, k = i % TC::KI;
-            uint16_t h = 0, l = 0;
-            if (n < NQ && k < 3 * NU) tc::split16<TCM>((float)op->Bt[k % NU][n], h, l);
-            *reinterpret_cast<uint16_t *>(tA + tc::core_offset(n, k, TC::SBO)) = k < 2 * NU ? h : l;
+        for (int i = threadIdx.x; i < 128 * TC::KI; i += NTH) {   // the split form's slices of B, rows q
+            const int n = i / TC::KI, k = i % TC::KI, sg = k / NU;
+            uint16_t pp[3] = {0, 0, 0};
+            if (n < NQ && sg < SF::SEGS) tc::split_parts<TCM>((float)op->Bt[k % NU][n], pp);
+            *reinterpret_cast<uint16_t *>(tA + tc::core_offset(n, k, TC::SBO)) = sg < SF::SEGS ? pp[SF::y_part(sg)] : (uint16_t)0;
         }
         for (int i = threadIdx.x; i < 32 * TC::KI; i += NTH)     // field rows 20..31 and the K pad stay zero
             *reinterpret_cast<uint16_t *>(tB + tc::core_offset(i / TC::KI, i % TC::KI, TC::SBO)) = 0;
@@ -417,11 +419,11 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? (TCM == 0 ? 8 : 6) : 0) 
                     for (int i = 0; i < NV; i++) {
                         const int j = sub + 4 * i;
                         if (j < NU) {
-                            uint16_t h, l;
-                            tc::split16<TCM>(x[i] * sc, h, l);
-                            *reinterpret_cast<uint16_t *>(tB + tc::core_offset(r, j, TC::SBO)) = h;
-                            *reinterpret_cast<uint16_t *>(tB + tc::core_offset(r, NU + j, TC::SBO)) = l;
-                            *reinterpret_cast<uint16_t *>(tB + tc::core_offset(r, 2 * NU + j, TC::SBO)) = h;
+                            uint16_t pp[3];
+                            tc::split_parts<TCM>(x[i] * sc, pp);
+#pragma unroll
+                            for (int sg = 0; sg < SF::SEGS; sg++)
+                                *reinterpret_cast<uint16_t *>(tB + tc::core_offset(r, sg * NU + j, TC::SBO)) = pp[SF::x_part(sg)];
                         }
                     }
                     if (sub == 0) s_sh[r] = sh;
@@ -438,7 +440,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? (TCM == 0 ? 8 : 6) : 0) 
 #pragma unroll
                 for (int j = 0; j < TC::KI / 16; j++)
                     tc::mma_f16(tmem, tc::sdesc(aA + 256 * j, 128, TC::SBO), tc::sdesc(aB + 256 * j, 128, TC::SBO),
-                                TCM == 1 ? TC::IDESC1 : TC::IDESC2, j);
+                                TC::IDESC, j);
                 tc::commit(mbar);
             }
         }
@@ -742,7 +744,7 @@ int dense_phase(int phase, const HexArgs<T> &a, const OPS *ops, const FFOf<OPS> 
         if constexpr (sizeof(T) == 4) {
             if (a.tcmode != 0) {
                 tcdone = true;
-                const size_t smem = base + DenseTC<OPS>::BYTES;
+                const size_t smem = base + (a.tcmode == 1 ? DenseTC<OPS, 1>::BYTES : DenseTC<OPS, 2>::BYTES);
                 // persistent: as many CTAs as fit on the SMs (shared memory, registers, and the 512
                 // tensor-memory columns at 32 per CTA)
                 auto kern = a.tcmode == 1 ? k_dense_B<T, NTH, OPS, 1> : k_dense_B<T, NTH, OPS, 2>;

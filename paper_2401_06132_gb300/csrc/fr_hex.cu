@@ -315,11 +315,12 @@ struct HexSmem {
 // chain each, as split products [x_hi | x_lo | x_hi] . [y_hi | y_hi | y_lo]; the z factor stays on
 // the CUDA cores. The dense block takes N M / (N + M) times the multiply-adds of two 1D sweeps (and
 // three for the split), paid on a unit with about 30 times the FP32 rate of the CUDA cores.
-template <int P>
+template <int P, int TCM>
 struct HexTc {
     static constexpr int N = P + 1, M = P + 2, N2 = N * N, M2 = M * M;
     static constexpr int RI = 20 * M, RP = 15 * M;                 // rows: field x z quadrature level
-    static constexpr int KI = (3 * N2 + 15) / 16 * 16, KP = (3 * M2 + 15) / 16 * 16;
+    // K: the split form's segments (tc::SplitForm: FP16 three, BF16 six) of N^2 or M^2 values
+    static constexpr int KI = tc::split_k<TCM>(N2), KP = tc::split_k<TCM>(M2);
     static constexpr int NI = (M2 + 15) / 16 * 16, NP = (N2 + 15) / 16 * 16;
     static constexpr int SBO_I = KI / 8 * 128, SBO_P = KP / 8 * 128;
     static constexpr int A_I = (RI + 7) / 8 * SBO_I, A_P = (RP + 7) / 8 * SBO_P;
@@ -332,31 +333,10 @@ struct HexTc {
     static_assert(RI <= 128 && RP <= 128, "one M = 128 tile per element");
 };
 
-// Writes row r of an operand as [hi | lo | hi | 0 ...] (L values per segment, K values in all)
-// from packed pairs hl[i] = hi | lo << 16.
-template <int K, int L>
-__device__ __forceinline__ void store_split_row(unsigned char *base, int r, const uint32_t (&hl)[L])
-{
-    auto val = [&](int k) -> uint32_t {
-        if (k < L) return hl[k] & 0xFFFFu;
-        if (k < 2 * L) return hl[k - L] >> 16;
-        if (k < 3 * L) return hl[k - 2 * L] & 0xFFFFu;
-        return 0u;
-    };
-#pragma unroll
-    for (int ch = 0; ch < K / 8; ch++) {
-        uint4 w;
-        w.x = val(8 * ch + 0) | (val(8 * ch + 1) << 16);
-        w.y = val(8 * ch + 2) | (val(8 * ch + 3) << 16);
-        w.z = val(8 * ch + 4) | (val(8 * ch + 5) << 16);
-        w.w = val(8 * ch + 6) | (val(8 * ch + 7) << 16);
-        *reinterpret_cast<uint4 *>(base + tc::core_offset(r, 8 * ch, K / 8 * 128)) = w;
-    }
-}
-
-// Splits the L values x of one operand row (scaled by 2^sh) into packed hi/lo pairs.
-template <int TCM, int L>
-__device__ __forceinline__ int split_row(const float (&x)[L], uint32_t (&hl)[L])
+// Scales the L values x of one operand row by 2^sh (its largest magnitude into [2^14, 2^15)) and
+// writes their split parts as row r of the tile (K values); returns sh.
+template <int TCM, int K, int L>
+__device__ __forceinline__ int split_store_row(unsigned char *base, int r, float (&x)[L])
 {
     float mx = 0.f;
 #pragma unroll
@@ -364,11 +344,8 @@ __device__ __forceinline__ int split_row(const float (&x)[L], uint32_t (&hl)[L])
     const int sh = tc::row_shift(mx);
     const float sc = tc::pow2f(sh);
 #pragma unroll
-    for (int i = 0; i < L; i++) {
-        uint16_t h, l;
-        tc::split16<TCM>(x[i] * sc, h, l);
-        hl[i] = (uint32_t)h | ((uint32_t)l << 16);
-    }
+    for (int i = 0; i < L; i++) x[i] *= sc;
+    tc::store_split_parts<TCM, K, L>(base, r, x);
     return sh;
 }
 
@@ -617,7 +594,7 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
     // CURV: curved (trilinear) elements of a single block, metric terms per point from a.mu, a.mq, a.mfn
     static_assert(!CURV || (AA && !SURF && TCM == 0), "curved elements: flux anti-aliasing on the CUDA cores");
     using S = HexSmem<T, P>;
-    using TC = HexTc<P>;
+    using TC = HexTc<P, TCM == 0 ? 1 : TCM>;
     static_assert(TCM == 0 || (NT == 128 && std::is_same<T, float>::value), "tensor-core form: FP32, one warpgroup");
     constexpr int N = S::N, M = S::M, NU = S::NU, NF = S::NF, NQ = S::NQ;
     constexpr int XS = S::XS, PS = S::PS, FS = S::FS;
@@ -663,25 +640,26 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
     }
     if constexpr (TCM != 0) {
         tc::setup(s_mbar, s_tmem, TC::COLS);
-        // operator blocks [hi | hi | lo] from the FP64 1D operators
+        // operator blocks in the split form's segments (FP16: [hi | hi | lo]) from the FP64 1D operators
+        using SF = tc::SplitForm<TCM>;
         const HexOps<double> &o64 = OPS<double>(P - 2);
         for (int i = threadIdx.x; i < TC::NI * TC::KI; i += NT) {
-            const int n = i / TC::KI, k = i % TC::KI;
-            uint16_t h = 0, l = 0;
-            if (n < TC::M2 && k < 3 * TC::N2) {
+            const int n = i / TC::KI, k = i % TC::KI, sg = k / TC::N2;
+            uint16_t pp[3] = {0, 0, 0};
+            if (n < TC::M2 && sg < SF::SEGS) {
                 const int kk = k % TC::N2;
-                tc::split16<TCM>((float)(o64.B[n % M][kk % N] * o64.B[n / M][kk / N]), h, l);
+                tc::split_parts<TCM>((float)(o64.B[n % M][kk % N] * o64.B[n / M][kk / N]), pp);
             }
-            *reinterpret_cast<uint16_t *>(tBi + tc::core_offset(n, k, TC::SBO_I)) = k < 2 * TC::N2 ? h : l;
+            *reinterpret_cast<uint16_t *>(tBi + tc::core_offset(n, k, TC::SBO_I)) = sg < SF::SEGS ? pp[SF::y_part(sg)] : (uint16_t)0;
         }
         for (int i = threadIdx.x; i < TC::NP * TC::KP; i += NT) {
-            const int n = i / TC::KP, k = i % TC::KP;
-            uint16_t h = 0, l = 0;
-            if (n < TC::N2 && k < 3 * TC::M2) {
+            const int n = i / TC::KP, k = i % TC::KP, sg = k / TC::M2;
+            uint16_t pp[3] = {0, 0, 0};
+            if (n < TC::N2 && sg < SF::SEGS) {
                 const int kk = k % TC::M2;
-                tc::split16<TCM>((float)(o64.Pj[n % N][kk % M] * o64.Pj[n / N][kk / M]), h, l);
+                tc::split_parts<TCM>((float)(o64.Pj[n % N][kk % M] * o64.Pj[n / N][kk / M]), pp);
             }
-            *reinterpret_cast<uint16_t *>(tBp + tc::core_offset(n, k, TC::SBO_P)) = k < 2 * TC::M2 ? h : l;
+            *reinterpret_cast<uint16_t *>(tBp + tc::core_offset(n, k, TC::SBO_P)) = sg < SF::SEGS ? pp[SF::y_part(sg)] : (uint16_t)0;
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -1023,11 +1001,9 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
             if (threadIdx.x < TC::RI) {
                 const int r = threadIdx.x;
                 float x[TC::N2];
-                uint32_t hl[TC::N2];
 #pragma unroll
                 for (int n = 0; n < TC::N2; n++) x[n] = s_tt[r * TC::ST + n];
-                s_sh[r] = split_row<TCM, TC::N2>(x, hl);
-                store_split_row<TC::KI, TC::N2>(tA, r, hl);
+                s_sh[r] = split_store_row<TCM, TC::KI, TC::N2>(tA, r, x);
             }
             if (!tc::mma_chain<TC::KI / 16>(tmem, tA, TC::SBO_I, tBi, TC::SBO_I, tc::idesc_f16(TCM - 1, 128, TC::NI), s_mbar, parity,
                                             tc::first_limit(first_wait, a.dbg_wait0))) {
@@ -1136,11 +1112,9 @@ __device__ __forceinline__ void fused_B_body(const HexArgs<T> &a, long long firs
             if (threadIdx.x < TC::RP) {
                 const int r = threadIdx.x;
                 float x[TC::M2];
-                uint32_t hl[TC::M2];
 #pragma unroll
                 for (int q = 0; q < TC::M2; q++) x[q] = s_w[TC::M2 * r + q];
-                s_sh[r] = split_row<TCM, TC::M2>(x, hl);
-                store_split_row<TC::KP, TC::M2>(tA, r, hl);
+                s_sh[r] = split_store_row<TCM, TC::KP, TC::M2>(tA, r, x);
             }
             if (!tc::mma_chain<TC::KP / 16>(tmem, tA, TC::SBO_P, tBp, TC::SBO_P, tc::idesc_f16(TCM - 1, 128, TC::NP), s_mbar, parity,
                                             tc::first_limit(first_wait, a.dbg_wait0))) {
@@ -2339,7 +2313,7 @@ static void launch_B(const HexArgs<T> &a, cudaStream_t s)
 template <int P, int TCM>
 static int launch_B_tc(const HexArgs<float> &a, cudaStream_t s)
 {
-    using TC = HexTc<P>;
+    using TC = HexTc<P, TCM>;
     static_assert(16 * (TC::SBO_I > TC::SBO_P ? TC::SBO_I : TC::SBO_P) <=
                       TC::A_BYTES + TC::BI_BYTES + TC::BP_BYTES + HexSmem<float, P>::SIZE * (int)sizeof(float),
                   "the 128 rows an MMA reads stay inside the CTA's shared memory");

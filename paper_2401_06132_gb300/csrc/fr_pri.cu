@@ -78,7 +78,7 @@ int pri_fused_phase(int phase, const HexArgs<T> &a, const PriOps<T> *ops, const 
           if (a.tcmode != 0) {
             tcdone = true;
             const int tcnt = TC_ROWS_P * TC_ST > 5 * NZ * NQT ? TC_ROWS_P * TC_ST : 5 * NZ * NQT;
-            const size_t smem = base + (size_t)tcnt * sizeof(T) + TC_BYTES;
+            const size_t smem = base + (size_t)tcnt * sizeof(T) + (a.tcmode == 1 ? PriTC<1>::BYTES : PriTC<2>::BYTES);
             // persistent: as many CTAs as fit on the SMs (shared memory, registers, and the 512
             // tensor-memory columns at 32 per CTA)
             auto kern = a.tcmode == 1 ? k_pri_B<T, NTH, 1> : k_pri_B<T, NTH, 2>;

@@ -105,25 +105,29 @@ __device__ __forceinline__ void load_ops(const PriOps<T> *g, PriOps<T> &s)
 }
 
 
-// Shared-memory operands of the tensor-core contractions (bytes, 128-byte aligned pieces).
-constexpr int TC_KI = 32, TC_NI = 32;          // interpolation: K = 3 x 10 (+2 zero), N = 25 (+7)
-constexpr int TC_KP = 80, TC_NP = 16;          // projection:    K = 3 x 25 (+5 zero), N = 10 (+6)
-constexpr int TC_SBO_I = TC_KI / 8 * 128, TC_SBO_P = TC_KP / 8 * 128;
+// Shared-memory operands of the tensor-core contractions (bytes, 128-byte aligned pieces), for the
+// split form TCM (1: FP16 in three K segments, 2: BF16 in six; tc::SplitForm).
 constexpr int TC_ROWS_I = 20 * MZ, TC_ROWS_P = 15 * MZ;    // 100 and 75 rows of M = 128
-// The A tile holds the rows an element writes (the projection layout is the larger); the MMA reads
-// all 128 rows, and the ones past the element's last run on into the buffers that follow the tile
-// (the operator tiles and the kernel's arrays), feeding accumulator lanes that are never read.
-constexpr int TC_A_I = (TC_ROWS_I + 7) / 8 * TC_SBO_I, TC_A_P = (TC_ROWS_P + 7) / 8 * TC_SBO_P;
-constexpr int TC_A_BYTES = ((TC_A_I > TC_A_P ? TC_A_I : TC_A_P) + 127) / 128 * 128;
-constexpr int TC_BI_BYTES = TC_NI / 8 * TC_SBO_I, TC_BP_BYTES = TC_NP / 8 * TC_SBO_P;
-constexpr int TC_HEAD = TC_A_BYTES + TC_BI_BYTES + TC_BP_BYTES + 128 * 4 + 16;   // tiles, row shifts, barrier, TMEM slot
-constexpr int TC_BYTES = TC_HEAD + 128;                                         // + alignment slack
 constexpr int TC_ST = 11;                                  // row stride of the projected rows
-constexpr uint32_t TC_IDESC_I1 = tc::idesc_f16(0, 128, TC_NI), TC_IDESC_I2 = tc::idesc_f16(1, 128, TC_NI);
-constexpr uint32_t TC_IDESC_P1 = tc::idesc_f16(0, 128, TC_NP), TC_IDESC_P2 = tc::idesc_f16(1, 128, TC_NP);
-static_assert(TC_ROWS_I <= 128 && TC_ROWS_P <= 128, "one M = 128 tile per element");
-static_assert(16 * TC_SBO_P <= TC_HEAD + (5 * NU + 15 * NU + 5 * NF + 20 * NQ) * 4,
-              "the 128 rows an MMA reads stay inside the CTA's shared memory");
+template <int TCM>
+struct PriTC {
+    static constexpr int KI = tc::split_k<TCM>(NT_), NI = 32;    // interpolation: K = segments x 10 (padded), N = 25 (+7)
+    static constexpr int KP = tc::split_k<TCM>(NQT), NP = 16;    // projection: K = segments x 25 (padded), N = 10 (+6)
+    static constexpr int SBO_I = KI / 8 * 128, SBO_P = KP / 8 * 128;
+    // The A tile holds the rows an element writes (the larger layout of the two); the MMA reads
+    // all 128 rows, and the ones past the element's last run on into the buffers that follow the
+    // tile (the operator tiles and the kernel's arrays), feeding accumulator lanes never read.
+    static constexpr int A_I = (TC_ROWS_I + 7) / 8 * SBO_I, A_P = (TC_ROWS_P + 7) / 8 * SBO_P;
+    static constexpr int A_BYTES = ((A_I > A_P ? A_I : A_P) + 127) / 128 * 128;
+    static constexpr int BI_BYTES = NI / 8 * SBO_I, BP_BYTES = NP / 8 * SBO_P;
+    static constexpr int HEAD = A_BYTES + BI_BYTES + BP_BYTES + 128 * 4 + 16;   // tiles, row shifts, barrier, TMEM slot
+    static constexpr int BYTES = HEAD + 128;                                     // + alignment slack
+    static constexpr uint32_t IDESC_I = tc::idesc_f16(TCM - 1, 128, NI), IDESC_P = tc::idesc_f16(TCM - 1, 128, NP);
+    static_assert(TC_ROWS_I <= 128 && TC_ROWS_P <= 128, "one M = 128 tile per element");
+    static_assert(16 * SBO_I <= HEAD + (5 * NU + 15 * NU + 5 * NF + 20 * NQ) * 4 &&
+                      16 * SBO_P <= HEAD + (5 * NU + 15 * NU + 5 * NF + 20 * NQ) * 4,
+                  "the 128 rows an MMA reads stay inside the CTA's shared memory");
+};
 
 // -------------------------------------------------------------------------------------------------
 // Phase A: disu
@@ -359,6 +363,7 @@ template <typename T, int NTH, int TCM>
 __device__ __forceinline__ void pri_B_body(const HexArgs<T> &a, const PriOps<T> *gops, const PriOpsFF *opsff, long long first, long long stride)
 {
     static_assert(TCM == 0 || (NTH == 128 && sizeof(T) == 4), "tensor-core form: FP32, one warpgroup per element");
+    using PT = PriTC<TCM == 0 ? 1 : TCM>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ ff s_mf[sizeof(T) == 4 ? 3 * NU : 1];   // low-Mach form: transformed mass flux
     __shared__ short s_plist[NF];                         // flux points that need the viscous flux
@@ -375,12 +380,12 @@ __device__ __forceinline__ void pri_B_body(const HexArgs<T> &a, const PriOps<T> 
     if constexpr (TCM != 0) {
         const uint32_t raw = tc::smem_u32(arr);
         tA = arr + ((128 - (raw & 127)) & 127);
-        tBi = tA + TC_A_BYTES;
-        tBp = tBi + TC_BI_BYTES;
-        s_sh = reinterpret_cast<int *>(tBp + TC_BP_BYTES);
+        tBi = tA + PT::A_BYTES;
+        tBp = tBi + PT::BI_BYTES;
+        s_sh = reinterpret_cast<int *>(tBp + PT::BP_BYTES);
         mbar = reinterpret_cast<uint64_t *>(s_sh + 128);
         s_tmem = reinterpret_cast<uint32_t *>(mbar + 1);
-        arr = tA + TC_HEAD;
+        arr = tA + PT::HEAD;
     }
     T *s_u = reinterpret_cast<T *>(arr);
     T *s_q = s_u + 5 * NU;
@@ -391,17 +396,19 @@ __device__ __forceinline__ void pri_B_body(const HexArgs<T> &a, const PriOps<T> 
     if constexpr (TCM != 0) {
         tc::setup(mbar, s_tmem, 32);
         __syncthreads();   // operators in shared memory
-        for (int i = threadIdx.x; i < TC_NI * TC_KI; i += NTH) {   // [B_hi | B_hi | B_lo]
-            const int n = i / TC_KI, k = i % TC_KI;
-            uint16_t h = 0, l = 0;
-            if (n < NQT && k < 3 * NT_) tc::split16<TCM>((float)op.Bt[n][k % NT_], h, l);
-            *reinterpret_cast<uint16_t *>(tBi + tc::core_offset(n, k, TC_SBO_I)) = k < 2 * NT_ ? h : l;
+        // operator tiles in the split form's segments (FP16: [B_hi | B_hi | B_lo])
+        using SF = tc::SplitForm<TCM>;
+        for (int i = threadIdx.x; i < PT::NI * PT::KI; i += NTH) {
+            const int n = i / PT::KI, k = i % PT::KI, sg = k / NT_;
+            uint16_t pp[3] = {0, 0, 0};
+            if (n < NQT && sg < SF::SEGS) tc::split_parts<TCM>((float)op.Bt[n][k % NT_], pp);
+            *reinterpret_cast<uint16_t *>(tBi + tc::core_offset(n, k, PT::SBO_I)) = sg < SF::SEGS ? pp[SF::y_part(sg)] : (uint16_t)0;
         }
-        for (int i = threadIdx.x; i < TC_NP * TC_KP; i += NTH) {   // [P_hi | P_hi | P_lo]
-            const int n = i / TC_KP, k = i % TC_KP;
-            uint16_t h = 0, l = 0;
-            if (n < NT_ && k < 3 * NQT) tc::split16<TCM>((float)op.Pt[n][k % NQT], h, l);
-            *reinterpret_cast<uint16_t *>(tBp + tc::core_offset(n, k, TC_SBO_P)) = k < 2 * NQT ? h : l;
+        for (int i = threadIdx.x; i < PT::NP * PT::KP; i += NTH) {
+            const int n = i / PT::KP, k = i % PT::KP, sg = k / NQT;
+            uint16_t pp[3] = {0, 0, 0};
+            if (n < NT_ && sg < SF::SEGS) tc::split_parts<TCM>((float)op.Pt[n][k % NQT], pp);
+            *reinterpret_cast<uint16_t *>(tBp + tc::core_offset(n, k, PT::SBO_P)) = sg < SF::SEGS ? pp[SF::y_part(sg)] : (uint16_t)0;
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -565,19 +572,12 @@ __device__ __forceinline__ void pri_B_body(const HexArgs<T> &a, const PriOps<T> 
                 }
                 const int sh = tc::row_shift(mx);
                 const float sc = tc::pow2f(sh);
-                uint16_t kv[TC_KI];
 #pragma unroll
-                for (int t = 0; t < NT_; t++) {
-                    uint16_t h, l;
-                    tc::split16<TCM>(x[t] * sc, h, l);
-                    kv[t] = h; kv[NT_ + t] = l; kv[2 * NT_ + t] = h;
-                }
-#pragma unroll
-                for (int k = 3 * NT_; k < TC_KI; k++) kv[k] = 0;
-                tc::store_row<TC_KI>(tA, r, kv);
+                for (int t = 0; t < NT_; t++) x[t] *= sc;
+                tc::store_split_parts<TCM, PT::KI, NT_>(tA, r, x);
                 s_sh[r] = sh;
             }
-            tc::mma_issue<TC_KI / 16>(tmem, tA, TC_SBO_I, tBi, TC_SBO_I, TCM == 1 ? TC_IDESC_I1 : TC_IDESC_I2, mbar);
+            tc::mma_issue<PT::KI / 16>(tmem, tA, PT::SBO_I, tBi, PT::SBO_I, PT::IDESC_I, mbar);
             viscous_faces();   // CUDA-core work while the chain runs (touches no operand tile)
             if (!tc::mma_wait(mbar, parity, tc::first_limit(first_wait, a.dbg_wait0))) {
                 tc_fail = true;
@@ -638,19 +638,12 @@ __device__ __forceinline__ void pri_B_body(const HexArgs<T> &a, const PriOps<T> 
                 for (int q = 0; q < NQT; q++) { x[q] = (float)src[q]; mx = fmaxf(mx, fabsf(x[q])); }
                 const int sh = tc::row_shift(mx);
                 const float sc = tc::pow2f(sh);
-                uint16_t kv[TC_KP];
 #pragma unroll
-                for (int q = 0; q < NQT; q++) {
-                    uint16_t h, l;
-                    tc::split16<TCM>(x[q] * sc, h, l);
-                    kv[q] = h; kv[NQT + q] = l; kv[2 * NQT + q] = h;
-                }
-#pragma unroll
-                for (int k = 3 * NQT; k < TC_KP; k++) kv[k] = 0;
-                tc::store_row<TC_KP>(tA, r, kv);
+                for (int q = 0; q < NQT; q++) x[q] *= sc;
+                tc::store_split_parts<TCM, PT::KP, NQT>(tA, r, x);
                 s_sh[r] = sh;
             }
-            tc::mma_issue<TC_KP / 16>(tmem, tA, TC_SBO_P, tBp, TC_SBO_P, TCM == 1 ? TC_IDESC_P1 : TC_IDESC_P2, mbar);
+            tc::mma_issue<PT::KP / 16>(tmem, tA, PT::SBO_P, tBp, PT::SBO_P, PT::IDESC_P, mbar);
             // CUDA-core work while the chain runs: it reads the state and writes only static shared
             // memory and global memory, which the chain's rows (they run on past the operand tile
             // into the dynamic shared arrays) never reach

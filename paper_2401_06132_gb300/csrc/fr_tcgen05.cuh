@@ -150,6 +150,44 @@ __device__ __forceinline__ void split16(float x, uint16_t &h, uint16_t &l)
     }
 }
 
+// The split forms of the operands, by K segment. FP16 (TCM = 1): x = x_hi + x_lo, three products
+// x_hi y_hi + x_lo y_hi + x_hi y_lo (segments [x_hi | x_lo | x_hi] against [y_hi | y_hi | y_lo]).
+// BF16 (TCM = 2), whose 8-bit significands leave about 16 bits in two terms: x = x_1 + x_2 + x_3,
+// y likewise, and the six products whose parts' orders sum to at most two (x_1 y_1, x_1 y_2,
+// x_2 y_1, x_1 y_3, x_2 y_2, x_3 y_1), about 24 bits like FP32. `x` is the data operand (the rows
+// split per element), `y` the operator.
+template <int TCM>
+struct SplitForm {
+    static constexpr int PARTS = TCM == 2 ? 3 : 2;
+    static constexpr int SEGS = TCM == 2 ? 6 : 3;
+    // the part of x, and of y, that K segment s holds
+    __host__ __device__ static constexpr int x_part(int s) { return TCM == 2 ? (s == 2 || s == 4 ? 1 : (s == 5 ? 2 : 0)) : (s == 1 ? 1 : 0); }
+    __host__ __device__ static constexpr int y_part(int s) { return TCM == 2 ? (s == 1 || s == 4 ? 1 : (s == 3 ? 2 : 0)) : (s == 2 ? 1 : 0); }
+};
+
+// The parts of x in the split form (FP16: hi, lo; BF16: x_1, x_2, x_3, each the rounding of what
+// the previous ones leave; the differences are exact in FP32).
+template <int TCM>
+__device__ __forceinline__ void split_parts(float x, uint16_t (&p)[3])
+{
+    if constexpr (TCM == 1) {
+        split16<1>(x, p[0], p[1]);
+        p[2] = 0;
+    } else {
+        const __nv_bfloat16 b1 = __float2bfloat16_rn(x);
+        const float r1 = x - __bfloat162float(b1);
+        const __nv_bfloat16 b2 = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(b2);
+        p[0] = __bfloat16_as_ushort(b1);
+        p[1] = __bfloat16_as_ushort(b2);
+        p[2] = __bfloat16_as_ushort(__float2bfloat16_rn(r2));
+    }
+}
+
+// K of a split operand row: SEGS segments of K0 values, padded to the MMA's K step of 16.
+template <int TCM>
+__host__ __device__ constexpr int split_k(int k0) { return (SplitForm<TCM>::SEGS * k0 + 15) / 16 * 16; }
+
 // Exponent s with max|x| 2^s in [2^14, 2^15) (0 for zero, subnormal or non-finite maxima).
 __device__ __forceinline__ int row_shift(float mx)
 {
@@ -174,6 +212,32 @@ __device__ __forceinline__ void store_row(unsigned char *base, int r, const uint
         w.z = pack2(v[8 * ch + 4], v[8 * ch + 5]);
         w.w = pack2(v[8 * ch + 6], v[8 * ch + 7]);
         *reinterpret_cast<uint4 *>(base + core_offset(r, 8 * ch, (K / 8) * 128)) = w;
+    }
+}
+
+// Row r of a split data operand: the parts of the L values x (already scaled) in the K segments
+// of the split form, zero-padded to K, as K/8 core-matrix rows of 16 bytes.
+template <int TCM, int K, int L>
+__device__ __forceinline__ void store_split_parts(unsigned char *base, int r, const float (&x)[L])
+{
+    using SF = SplitForm<TCM>;
+    uint16_t pp[L][3];
+#pragma unroll
+    for (int i = 0; i < L; i++) split_parts<TCM>(x[i], pp[i]);
+#pragma unroll
+    for (int ch = 0; ch < K / 8; ch++) {
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 4; h++) {
+            uint16_t v[2];
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                const int k = 8 * ch + 2 * h + j, sg = k / L, i = k % L;
+                v[j] = sg < SF::SEGS ? pp[i][SF::x_part(sg)] : (uint16_t)0;
+            }
+            w[h] = pack2(v[0], v[1]);
+        }
+        *reinterpret_cast<uint4 *>(base + core_offset(r, 8 * ch, (K / 8) * 128)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 
