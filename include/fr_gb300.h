@@ -81,14 +81,17 @@ typedef enum {
     FR_FP32 = 1,          /* FP32 state, operators and fluxes */
     FR_MIXED_BF16 = 2,    /* FR_FP32, except that the dense prism triangle-plane interpolation and
                            * projection (Sec. 4.1 factorisation; the M7 and M8 triangle blocks) run
-                           * on the tensor cores as split products x_hi y_hi + x_lo y_hi + x_hi y_lo
-                           * of bf16 halves with FP32 accumulation. Hexahedra run the FR_FP32
+                           * on the tensor cores as split products with FP32 accumulation: each
+                           * operand in three bf16 terms, x = x1 + x2 + x3, and the six products
+                           * x1 y1 + x1 y2 + x2 y1 + x1 y3 + x2 y2 + x3 y1 (about 24 significant
+                           * bits; two bf16 terms keep only about 16). Hexahedra run the FR_FP32
                            * kernels (their sum-factorised 1D operators are not dense contractions)
                            * unless fr_set_hex_tensor_cores() is on; tetrahedra and pyramids run
                            * the FR_FP32 kernels unless fr_set_dense_tensor_cores() is on. */
-    FR_MIXED_FP16 = 3     /* as FR_MIXED_BF16 with fp16 halves; every operand row is scaled by a
-                           * power of two first (removed exactly afterwards) so that fp16 keeps
-                           * its full precision in the low half */
+    FR_MIXED_FP16 = 3     /* as FR_MIXED_BF16 with fp16 halves, x = x_hi + x_lo, and the three
+                           * products x_hi y_hi + x_lo y_hi + x_hi y_lo; every operand row is
+                           * scaled by a power of two first (removed exactly afterwards) so that
+                           * fp16 keeps its full precision in the low half */
 } fr_precision;
 
 typedef enum {
