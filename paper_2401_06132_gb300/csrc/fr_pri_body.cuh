@@ -240,32 +240,10 @@ __device__ __forceinline__ void pri_project_5(const PriOps<T> &op, const T *src,
     __syncthreads();
 }
 
-// All 20 fields at once (FP32): triangle plane then z; tmp holds 20 x 4 x 25 values.
-template <typename T, int NTH>
-__device__ __forceinline__ void pri_interp_all(const PriOps<T> &op, const T *src, T *tmp, T *dst)
-{
-    for (int it = threadIdx.x; it < 20 * NZ * NQT; it += NTH) {   // triangle plane: (f, k, q)
-        const int f = it / (NZ * NQT), r = it % (NZ * NQT), k = r / NQT, q = r % NQT;
-        T v = T(0);
-#pragma unroll
-        for (int t = 0; t < NT_; t++) v += op.Bt[q][t] * src[f * NU + t + 10 * k];
-        tmp[it] = v;
-    }
-    __syncthreads();
-    for (int it = threadIdx.x; it < 20 * MZ * NQT; it += NTH) {   // z: (f, c, q)
-        const int f = it / (MZ * NQT), r = it % (MZ * NQT), c = r / NQT, q = r % NQT;
-        T v = T(0);
-#pragma unroll
-        for (int k = 0; k < NZ; k++) v += op.Bz[c][k] * tmp[f * NZ * NQT + q + NQT * k];
-        dst[f * NQ + q + NQT * c] = v;
-    }
-    __syncthreads();
-}
-
 // FP32 without tensor cores, all 20 fields: the triangle-plane factor with one thread per (field, z
 // level) line, its 10 values in registers and all 25 quadrature points formed from them, then z with
 // one thread per (field, triangle quadrature point); the operators from the constant-memory table
-// with compile-time indices. The sums run in the same order as pri_interp_all.
+// with compile-time indices.
 template <int NTH>
 __device__ __forceinline__ void pri_interp_all_c(const float *src, float *tmp, float *dst)
 {
@@ -302,7 +280,7 @@ __device__ __forceinline__ void pri_interp_all_c(const float *src, float *tmp, f
 
 // The projection of the 15 flux fields in the same form: z with one thread per (field, triangle
 // quadrature point), then the triangle plane with one thread per (field, z level) line, its 25
-// values in registers; sums in the order of pri_project_all.
+// values in registers.
 template <int NTH>
 __device__ __forceinline__ void pri_project_all_c(const float *src, float *tmp, float *dst)
 {
@@ -333,28 +311,6 @@ __device__ __forceinline__ void pri_project_all_c(const float *src, float *tmp, 
             for (int q = 0; q < NQT; q++) v += c_pri32.Pt[t][q] * u[q];
             d[t] = v;
         }
-    }
-    __syncthreads();
-}
-
-// All 15 flux fields at once (FP32): z then the triangle plane.
-template <typename T, int NTH>
-__device__ __forceinline__ void pri_project_all(const PriOps<T> &op, const T *src, T *tmp, T *dst)
-{
-    for (int it = threadIdx.x; it < 15 * NZ * NQT; it += NTH) {   // z: (f, k, q)
-        const int f = it / (NZ * NQT), r = it % (NZ * NQT), k = r / NQT, q = r % NQT;
-        T v = T(0);
-#pragma unroll
-        for (int c = 0; c < MZ; c++) v += op.Pz[k][c] * src[f * NQ + q + NQT * c];
-        tmp[it] = v;
-    }
-    __syncthreads();
-    for (int it = threadIdx.x; it < 15 * NU; it += NTH) {          // triangle plane: (f, k, t)
-        const int f = it / NU, r = it % NU, k = r / NT_, t = r % NT_;
-        T v = T(0);
-#pragma unroll
-        for (int q = 0; q < NQT; q++) v += op.Pt[t][q] * tmp[f * NZ * NQT + q + NQT * k];
-        dst[f * NU + t + 10 * k] = v;
     }
     __syncthreads();
 }

@@ -200,21 +200,6 @@ __device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t
 
 __device__ __forceinline__ uint32_t pack2(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
 
-// Writes the K values v[0..K) of row r as K/8 core-matrix rows of 16 bytes.
-template <int K>
-__device__ __forceinline__ void store_row(unsigned char *base, int r, const uint16_t (&v)[K])
-{
-#pragma unroll
-    for (int ch = 0; ch < K / 8; ch++) {
-        uint4 w;
-        w.x = pack2(v[8 * ch + 0], v[8 * ch + 1]);
-        w.y = pack2(v[8 * ch + 2], v[8 * ch + 3]);
-        w.z = pack2(v[8 * ch + 4], v[8 * ch + 5]);
-        w.w = pack2(v[8 * ch + 6], v[8 * ch + 7]);
-        *reinterpret_cast<uint4 *>(base + core_offset(r, 8 * ch, (K / 8) * 128)) = w;
-    }
-}
-
 // Row r of a split data operand: the parts of the L values x (already scaled) in the K segments
 // of the split form, zero-padded to K, as K/8 core-matrix rows of 16 bytes.
 template <int TCM, int K, int L>
