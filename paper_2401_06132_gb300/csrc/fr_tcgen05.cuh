@@ -165,6 +165,21 @@ struct SplitForm {
     __host__ __device__ static constexpr int y_part(int s) { return TCM == 2 ? (s == 1 || s == 4 ? 1 : (s == 3 ? 2 : 0)) : (s == 2 ? 1 : 0); }
 };
 
+// Each product x_i y_j whose parts' orders sum to at most PARTS - 1 appears in exactly one segment,
+// and no other product appears (checked at compile time for both forms).
+template <int TCM>
+constexpr bool split_form_complete()
+{
+    using SF = SplitForm<TCM>;
+    int seen[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int s = 0; s < SF::SEGS; s++) seen[SF::x_part(s)][SF::y_part(s)]++;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+            if (seen[i][j] != ((i < SF::PARTS && j < SF::PARTS && i + j <= SF::PARTS - 1) ? 1 : 0)) return false;
+    return true;
+}
+static_assert(split_form_complete<1>() && split_form_complete<2>(), "split forms: every product of order <= 1 (FP16) or <= 2 (BF16) once");
+
 // The parts of x in the split form (FP16: hi, lo; BF16: x_1, x_2, x_3, each the rounding of what
 // the previous ones leave; the differences are exact in FP32).
 template <int TCM>
